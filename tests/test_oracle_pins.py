@@ -1,0 +1,433 @@
+"""Pins of the FP64 oracle against facts fixed by the paper or by mathematics.
+
+Each test checks the oracle against something other than its own formulas:
+quadrature, the paper's binned identity (Eq. disa-b..d), a textbook spectral
+Poisson solve, closed-form 1-D solutions, Theorem 1's bounds, finite
+differences and the symmetries of the cosine basis.  A dropped term, a wrong
+sign, a swapped W/H or an off-by-one mode index fails at least one of them.
+"""
+import math
+
+import numpy as np
+import pytest
+from numpy.polynomial.legendre import leggauss
+from scipy.fft import dctn
+
+from oracle import series as O
+from paper_2307_12041_gb300 import synth
+
+PI = math.pi
+
+
+def rand_blocks(n, W, H, seed, charge=True, smin=0.02, smax=0.3):
+    g = np.random.default_rng(seed)
+    w = g.uniform(smin, smax, n) * W
+    h = g.uniform(smin, smax, n) * H
+    x = w / 2 + g.random(n) * (W - w)
+    y = h / 2 + g.random(n) * (H - h)
+    c = g.uniform(0.5, 2.0, n) if charge else None
+    return x, y, w, h, c
+
+
+# ---------------------------------------------------------------------------
+# 1. Rectangle integrals vs Gauss-Legendre quadrature
+# ---------------------------------------------------------------------------
+
+def _gl_integral(f, a, b, k):
+    panels = int(math.ceil((b - a) * k / PI * 2)) + 2      # >= 16 nodes per half period
+    t, wt = leggauss(16)
+    edges = np.linspace(a, b, panels + 1)
+    tot = 0.0
+    for lo, hi in zip(edges[:-1], edges[1:]):
+        xm = 0.5 * (hi + lo)
+        xr = 0.5 * (hi - lo)
+        tot += xr * np.sum(wt * f(xm + xr * t))
+    return tot
+
+
+def test_rect_integrals_match_quadrature():
+    L = 1.7
+    M = 300
+    x = np.array([0.01, 0.4, 0.85, 1.69, 0.5])
+    w = np.array([0.02, 0.003, 0.3, 0.02, 1.0])
+    Ic, Is = O.rect_integrals(x, w, L, M)
+    for i in range(len(x)):
+        a, b = x[i] - w[i] / 2, x[i] + w[i] / 2
+        for u in [0, 1, 2, 7, 64, 123, 299]:
+            k = u * PI / L
+            qc = _gl_integral(lambda t: np.cos(k * t), a, b, max(k, 1.0))
+            qs = _gl_integral(lambda t: np.sin(k * t), a, b, max(k, 1.0))
+            assert abs(Ic[i, u] - qc) <= 1e-12 * max(1.0, abs(qc)) * w[i] + 1e-15
+            assert abs(Is[i, u] - qs) <= 1e-12 * max(1.0, abs(qs)) * w[i] + 1e-15
+
+
+# ---------------------------------------------------------------------------
+# 2. Binned identity: Eq. (disa-b..d) for grid-aligned blocks is exact
+# ---------------------------------------------------------------------------
+
+def _binned_coefficients(P, W, H, Mx, My):
+    """Eq. (disa-a..d) evaluated by brute-force double sums over the bins."""
+    m = P.shape[0]
+    l = np.arange(m)
+    a = np.zeros((Mx, My))
+    cu = np.cos(np.outer(np.arange(Mx), (l + 0.5)) * PI / m)   # cos(u (l+1/2) pi / m)
+    cp = np.cos(np.outer(np.arange(My), (l + 0.5)) * PI / m)
+    D = cu @ P @ cp.T                                         # sum_{l,j} P cos cos
+    colsum = P.sum(axis=0)   # sum over l  -> function of j
+    rowsum = P.sum(axis=1)   # sum over j  -> function of l
+    for p in range(1, My):
+        a[0, p] = 4 * H * H / (p ** 3 * PI ** 3 * m) * math.sin(p * PI / (2 * m)) * (cp[p] @ colsum)
+    for u in range(1, Mx):
+        a[u, 0] = 4 * W * W / (u ** 3 * PI ** 3 * m) * math.sin(u * PI / (2 * m)) * (cu[u] @ rowsum)
+    for u in range(1, Mx):
+        for p in range(1, My):
+            a[u, p] = (16 * W * W * H * H / (u * p * (u * u * H * H + p * p * W * W) * PI ** 4)
+                       * math.sin(u * PI / (2 * m)) * math.sin(p * PI / (2 * m)) * D[u, p])
+    return a
+
+
+@pytest.mark.parametrize("W,H", [(2.0, 1.5), (1.0, 1.0), (0.7, 3.1)])
+def test_binned_identity_exact_for_grid_aligned_blocks(W, H):
+    m = 16
+    g = np.random.default_rng(11)
+    n = 25
+    P = np.zeros((m, m))
+    xs, ys, ws, hs, cs = [], [], [], [], []
+    for _ in range(n):
+        l0, l1 = sorted(g.choice(m + 1, 2, replace=False))
+        j0, j1 = sorted(g.choice(m + 1, 2, replace=False))
+        c = g.uniform(0.5, 2.0)
+        P[l0:l1, j0:j1] += c
+        xs.append((l0 + l1) / 2 * W / m)
+        ws.append((l1 - l0) * W / m)
+        ys.append((j0 + j1) / 2 * H / m)
+        hs.append((j1 - j0) * H / m)
+        cs.append(c)
+    Mx, My = 24, 21          # past m, so aliased modes are covered too
+    a = O.coefficients(W, H, xs, ys, ws, hs, cs, Mx, My)
+    ab = _binned_coefficients(P, W, H, Mx, My)
+    assert np.max(np.abs(a - ab)) <= 1e-12 * np.max(np.abs(ab))
+
+
+# ---------------------------------------------------------------------------
+# 3. Textbook spectral solve on a fine grid converges to the analytic series
+# ---------------------------------------------------------------------------
+
+def _overlap(lo, hi, edges):
+    return np.clip(np.minimum(hi, edges[1:]) - np.maximum(lo, edges[:-1]), 0.0, None)
+
+
+def _dct_solve(x, y, w, h, c, W, H, m, M):
+    """Cell-averaged density on an m x m grid, DCT-II, divide by the Laplacian
+    eigenvalues (u pi/W)^2 + (p pi/H)^2, cosine-series normalisation eps_u eps_p / (W H)."""
+    ex = np.linspace(0, W, m + 1)
+    ey = np.linspace(0, H, m + 1)
+    rho = np.zeros((m, m))
+    for i in range(len(x)):
+        ox = _overlap(x[i] - w[i] / 2, x[i] + w[i] / 2, ex)
+        oy = _overlap(y[i] - h[i] / 2, y[i] + h[i] / 2, ey)
+        rho += c[i] * np.outer(ox, oy) / ((W / m) * (H / m))
+    # integral of rho cos cos over the die by the midpoint rule:  (W H / m^2) * dctn / 4
+    S = (W * H / (m * m)) * dctn(rho, type=2)[:M, :M] / 4.0
+    u = np.arange(M)
+    eps_u = np.where(u == 0, 1.0, 2.0)
+    k2 = (u[:, None] * PI / W) ** 2 + (u[None, :] * PI / H) ** 2
+    k2[0, 0] = 1.0
+    a = eps_u[:, None] * eps_u[None, :] * S / (W * H * k2)
+    a[0, 0] = 0.0
+    return a, S
+
+
+def test_fine_grid_dct_poisson_solve_converges():
+    W, H = 1.3, 0.9
+    x, y, w, h, c = rand_blocks(12, W, H, seed=5)
+    M = 8
+    a = O.coefficients(W, H, x, y, w, h, c, M, M)
+    errs = []
+    for m in (128, 256, 512):
+        ah, _ = _dct_solve(x, y, w, h, c, W, H, m, M)
+        errs.append(np.max(np.abs(ah - a)) / np.max(np.abs(a)))
+    assert errs[2] < 2e-4
+    assert errs[0] / errs[1] > 2.5 and errs[1] / errs[2] > 2.5
+
+
+def test_energy_matches_fine_grid_parseval():
+    """E = 1/2 sum a S over the truncated modes equals the oracle's per-block sum."""
+    W, H = 1.3, 0.9
+    x, y, w, h, c = rand_blocks(12, W, H, seed=6)
+    M = 8
+    E = O.total_energy(W, H, x, y, w, h, c, M, M)
+    ah, Sh = _dct_solve(x, y, w, h, c, W, H, 512, M)
+    Eh = 0.5 * np.sum(ah * Sh)
+    assert abs(E - Eh) <= 1e-3 * abs(E)
+
+
+# ---------------------------------------------------------------------------
+# 4. Compatibility condition, textbook normalisation, energy identities
+# ---------------------------------------------------------------------------
+
+def test_whole_die_block_has_no_modes():
+    W, H = 1.4, 0.8
+    a = O.coefficients(W, H, [W / 2], [H / 2], [W], [H], None, 32, 32)
+    assert np.max(np.abs(a)) < 1e-14
+    x, y, w, h, c = rand_blocks(9, W, H, seed=1)
+    a1 = O.coefficients(W, H, x, y, w, h, c, 16, 16)
+    a2 = O.coefficients(W, H, np.r_[x, W / 2], np.r_[y, H / 2], np.r_[w, W], np.r_[h, H],
+                        np.r_[c, 3.0], 16, 16)
+    assert np.max(np.abs(a1 - a2)) <= 1e-13 * np.max(np.abs(a1))
+    assert a1[0, 0] == 0.0
+
+
+def test_psi_has_zero_mean_over_die():
+    W, H = 1.1, 0.7
+    x, y, w, h, c = rand_blocks(7, W, H, seed=2)
+    a = O.coefficients(W, H, x, y, w, h, c, 12, 12)
+    t, wt = leggauss(64)
+    px = W / 2 * (t + 1)
+    py = H / 2 * (t + 1)
+    X, Y = np.meshgrid(px, py, indexing="ij")
+    psi = O.potential(a, W, H, X.ravel(), Y.ravel()).reshape(X.shape)
+    integral = (W / 2) * (H / 2) * wt @ psi @ wt
+    assert abs(integral) <= 1e-12 * np.max(np.abs(psi)) * W * H
+
+
+def test_coefficients_equal_textbook_cosine_series():
+    """a = eps_u eps_p / (W H (k_u^2 + l_p^2)) * integral(rho cos cos), the Fourier-cosine
+    solution of -Lap psi = rho with Neumann walls; the integral is built from the
+    quadrature-pinned rectangle integrals."""
+    W, H = 1.9, 0.6
+    x, y, w, h, c = rand_blocks(15, W, H, seed=3)
+    Mx, My = 40, 33
+    a = O.coefficients(W, H, x, y, w, h, c, Mx, My)
+    Ix, _ = O.rect_integrals(x, w, W, Mx)
+    Iy, _ = O.rect_integrals(y, h, H, My)
+    S = (c[:, None] * Ix).T @ Iy
+    eu = np.where(np.arange(Mx) == 0, 1.0, 2.0)
+    ep = np.where(np.arange(My) == 0, 1.0, 2.0)
+    k2 = (np.arange(Mx)[:, None] * PI / W) ** 2 + (np.arange(My)[None, :] * PI / H) ** 2
+    k2[0, 0] = 1.0
+    G = eu[:, None] * ep[None, :] / (W * H * k2)
+    G[0, 0] = 0.0
+    assert np.max(np.abs(a - G * S)) <= 1e-12 * np.max(np.abs(a))
+    # Parseval: E = 1/2 sum_i N_i = 1/2 sum_{u,p} a S = 1/2 sum G S^2 >= 0
+    N, _, _ = O.energy_grad(W, H, x, y, w, h, c, a)
+    assert abs(0.5 * N.sum() - 0.5 * np.sum(a * S)) <= 1e-12 * abs(0.5 * np.sum(a * S))
+    assert 0.5 * N.sum() > 0
+
+
+def test_linearity_split_block_and_chunk_sum():
+    W, H = 1.0, 1.2
+    x, y, w, h, c = rand_blocks(10, W, H, seed=4)
+    a = O.coefficients(W, H, x, y, w, h, c, 20, 20)
+    # split block 0 into two abutting halves along x
+    xs = np.r_[x[0] - w[0] / 4, x[0] + w[0] / 4, x[1:]]
+    ws = np.r_[w[0] / 2, w[0] / 2, w[1:]]
+    ys = np.r_[y[0], y[0], y[1:]]
+    hs = np.r_[h[0], h[0], h[1:]]
+    cs = np.r_[c[0], c[0], c[1:]]
+    a_split = O.coefficients(W, H, xs, ys, ws, hs, cs, 20, 20)
+    assert np.max(np.abs(a - a_split)) <= 1e-12 * np.max(np.abs(a))
+    # sum over two disjoint halves of the block set
+    a1 = O.coefficients(W, H, x[:4], y[:4], w[:4], h[:4], c[:4], 20, 20)
+    a2 = O.coefficients(W, H, x[4:], y[4:], w[4:], h[4:], c[4:], 20, 20)
+    assert np.max(np.abs(a - a1 - a2)) <= 1e-13 * np.max(np.abs(a))
+    # permutation invariance
+    perm = np.random.default_rng(0).permutation(10)
+    ap = O.coefficients(W, H, x[perm], y[perm], w[perm], h[perm], c[perm], 20, 20)
+    assert np.max(np.abs(a - ap)) <= 1e-13 * np.max(np.abs(a))
+
+
+# ---------------------------------------------------------------------------
+# 5. Closed-form 1-D solutions: full-width and full-height strips
+# ---------------------------------------------------------------------------
+
+def _strip_psi(t, L, t0, s):
+    """psi(t) solving psi'' = -(theta(t) - s/L), psi'(0) = psi'(L) = 0, int psi = 0, where
+    theta is the indicator of [t0 - s/2, t0 + s/2]."""
+    t1, t2 = t0 - s / 2, t0 + s / 2
+    Q = np.where(t < t1, 0.0, np.where(t <= t2, (t - t1) ** 2 / 2, s * s / 2 + s * (t - t2)))
+    intQ = s ** 3 / 6 + (s * s / 2) * (L - t2) + s * (L - t2) ** 2 / 2
+    C = (intQ - s * L * L / 6) / L
+    return -Q + s * t * t / (2 * L) + C
+
+
+def _strip_energy(L, Lperp, t0, s):
+    """E = 1/2 * Lperp * int over the strip of psi (unit charge)."""
+    t1, t2 = t0 - s / 2, t0 + s / 2
+    intQ = s ** 3 / 6 + (s * s / 2) * (L - t2) + s * (L - t2) ** 2 / 2
+    C = (intQ - s * L * L / 6) / L
+    return 0.5 * Lperp * (-s ** 3 / 6 + s * (t2 ** 3 - t1 ** 3) / (6 * L) + C * s)
+
+
+def test_full_width_strip_matches_1d_solution():
+    W, H = 1.5, 1.1
+    y0, h = 0.37 * H, 0.21 * H
+    py = np.linspace(0, H, 101)
+    px = np.full_like(py, 0.3 * W)
+    exact = _strip_psi(py, H, y0, h)
+    E_exact = _strip_energy(H, W, y0, h)
+    perr, eerr = [], []
+    for M in (32, 64, 128, 256):
+        a = O.coefficients(W, H, [W / 2], [y0], [W], [h], None, 3, M)
+        assert np.max(np.abs(a[1:, :])) < 1e-14 * np.max(np.abs(a))
+        perr.append(np.max(np.abs(O.potential(a, W, H, px, py) - exact)))
+        eerr.append(abs(0.5 * O.energy_grad(W, H, [W / 2], [y0], [W], [h], None, a)[0][0]
+                        - E_exact))
+    assert perr[-1] < 1e-5 * np.max(np.abs(exact))
+    assert perr[0] / perr[-1] > 30.0                # O(M^-2): 64x over three doublings
+    for k in range(3):
+        assert perr[k] / perr[k + 1] > 2.0
+        assert eerr[k] / eerr[k + 1] > 6.0          # O(M^-3)
+    assert eerr[-1] < 1e-6 * abs(E_exact)
+
+
+def test_full_height_strip_matches_1d_solution():
+    W, H = 0.8, 1.6
+    x0, w = 0.61 * W, 0.13 * W
+    px = np.linspace(0, W, 77)
+    py = np.full_like(px, 0.9 * H)
+    exact = _strip_psi(px, W, x0, w)
+    E_exact = _strip_energy(W, H, x0, w)
+    a = O.coefficients(W, H, [x0], [H / 2], [w], [H], None, 256, 3)
+    assert np.max(np.abs(a[:, 1:])) < 1e-14 * np.max(np.abs(a))
+    assert np.max(np.abs(O.potential(a, W, H, px, py) - exact)) < 2e-5 * np.max(np.abs(exact))
+    E = 0.5 * O.energy_grad(W, H, [x0], [H / 2], [w], [H], None, a)[0][0]
+    assert abs(E - E_exact) < 1e-6 * abs(E_exact)
+
+
+# ---------------------------------------------------------------------------
+# 6. Theorem 1: coefficient bounds and the tail bound of Eq. (upper)
+# ---------------------------------------------------------------------------
+
+def _theorem1_bounds(W, H, w, h, c, Mx, My):
+    sc = np.sum(np.abs(c))
+    b = np.zeros((Mx, My))
+    u = np.arange(Mx)[:, None].astype(float)
+    p = np.arange(My)[None, :].astype(float)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        b[1:, 1:] = (16 * W * W * H * H * sc / (u[1:] * p[:, 1:] * (u[1:] ** 2 * H * H + p[:, 1:] ** 2 * W * W)
+                     * PI ** 4))
+        b[0, 1:] = 4 * H * H * np.sum(np.abs(c) * w) / (p[0, 1:] ** 3 * PI ** 3 * W)
+        b[1:, 0] = 4 * W * W * np.sum(np.abs(c) * h) / (u[1:, 0] ** 3 * PI ** 3 * H)
+    return b
+
+
+def test_theorem1_coefficient_bounds():
+    for seed, (W, H) in enumerate([(1.0, 1.0), (2.0, 0.5), (0.3, 0.9)]):
+        x, y, w, h, c = rand_blocks(40, W, H, seed=20 + seed, smin=0.2, smax=0.9)
+        a = O.coefficients(W, H, x, y, w, h, c, 48, 40)
+        b = _theorem1_bounds(W, H, w, h, c, 48, 40)
+        assert np.all(np.abs(a) <= b * (1 + 1e-12) + 1e-300)
+    # a single full-width... a tight case: one narrow block at the die edge saturates
+    # the sine-difference bound of 2 at the first mode only loosely; check bound holds
+    a = O.coefficients(1.0, 1.0, [0.25], [0.25], [0.5], [0.5], None, 8, 8)
+    b = _theorem1_bounds(1.0, 1.0, np.array([0.5]), np.array([0.5]), np.array([1.0]), 8, 8)
+    assert np.all(np.abs(a) <= b * (1 + 1e-12) + 1e-300)
+
+
+def test_series_is_cauchy_within_theorem1_tail():
+    W, H = 1.2, 0.9
+    x, y, w, h, c = rand_blocks(20, W, H, seed=30)
+    g = np.random.default_rng(3)
+    px = g.random(50) * W
+    py = g.random(50) * H
+    prev = None
+    for M in (8, 16, 32, 64, 128):
+        a = O.coefficients(W, H, x, y, w, h, c, M, M)
+        psi = O.potential(a, W, H, px, py)
+        if prev is not None:
+            Mp, psi_p = prev
+            b = _theorem1_bounds(W, H, w, h, c, M, M)
+            tail = b.sum() - b[:Mp, :Mp].sum()
+            assert np.max(np.abs(psi - psi_p)) <= tail
+        prev = (M, psi)
+
+
+# ---------------------------------------------------------------------------
+# 7. Gradient = derivative of E (finite differences), field = -grad psi
+# ---------------------------------------------------------------------------
+
+def test_gradient_matches_central_differences():
+    W, H = 1.0, 1.3
+    x, y, w, h, c = rand_blocks(12, W, H, seed=40, smin=0.05, smax=0.25)
+    M = 24
+    a = O.coefficients(W, H, x, y, w, h, c, M, M)
+    _, gx, gy = O.energy_grad(W, H, x, y, w, h, c, a)
+    d = 1e-5
+    for i in range(0, 12, 3):
+        for arr, g in ((x, gx), (y, gy)):
+            ap = arr.copy()
+            am = arr.copy()
+            ap[i] += d
+            am[i] -= d
+            args_p = [ap if arr is x else x, ap if arr is y else y]
+            args_m = [am if arr is x else x, am if arr is y else y]
+            Ep = O.total_energy(W, H, args_p[0], args_p[1], w, h, c, M, M)
+            Em = O.total_energy(W, H, args_m[0], args_m[1], w, h, c, M, M)
+            fd = (Ep - Em) / (2 * d)
+            assert abs(fd - g[i]) <= 1e-7 * max(np.max(np.abs(gx)), np.max(np.abs(gy)))
+
+
+def test_field_is_minus_gradient_of_potential():
+    W, H = 1.4, 1.0
+    x, y, w, h, c = rand_blocks(8, W, H, seed=41)
+    a = O.coefficients(W, H, x, y, w, h, c, 20, 16)
+    g = np.random.default_rng(9)
+    px = g.random(20) * W
+    py = g.random(20) * H
+    xi_x, xi_y = O.field(a, W, H, px, py)
+    d = 1e-6
+    fdx = -(O.potential(a, W, H, px + d, py) - O.potential(a, W, H, px - d, py)) / (2 * d)
+    fdy = -(O.potential(a, W, H, px, py + d) - O.potential(a, W, H, px, py - d)) / (2 * d)
+    scale = max(np.max(np.abs(xi_x)), np.max(np.abs(xi_y)))
+    assert np.max(np.abs(fdx - xi_x)) <= 1e-6 * scale
+    assert np.max(np.abs(fdy - xi_y)) <= 1e-6 * scale
+
+
+def test_center_sampling_is_point_potential_times_area():
+    W, H = 1.0, 1.0
+    x, y, w, h, c = rand_blocks(6, W, H, seed=42)
+    a = O.coefficients(W, H, x, y, w, h, c, 16, 16)
+    N, gx, gy = O.energy_grad(W, H, x, y, w, h, c, a, sample="center")
+    q = c * w * h
+    assert np.allclose(N, q * O.potential(a, W, H, x, y), rtol=1e-13, atol=0)
+    xi_x, xi_y = O.field(a, W, H, x, y)
+    assert np.allclose(gx, -q * xi_x, rtol=1e-13, atol=0)
+    # small blocks: centre sampling approaches the block integral
+    xs, ys, ws, hs, cs = rand_blocks(6, W, H, seed=43, smin=1e-4, smax=2e-4)
+    a2 = O.coefficients(W, H, xs, ys, ws, hs, cs, 16, 16)
+    Nr = O.energy_grad(W, H, xs, ys, ws, hs, cs, a2)[0]
+    Nc = O.energy_grad(W, H, xs, ys, ws, hs, cs, a2, sample="center")[0]
+    assert np.max(np.abs(Nr - Nc)) <= 1e-6 * np.max(np.abs(Nr))
+
+
+# ---------------------------------------------------------------------------
+# 8. Symmetries of the cosine basis
+# ---------------------------------------------------------------------------
+
+def test_mirror_and_transpose_symmetries():
+    W, H = 1.3, 0.8
+    x, y, w, h, c = rand_blocks(11, W, H, seed=50)
+    Mx, My = 18, 14
+    a = O.coefficients(W, H, x, y, w, h, c, Mx, My)
+    N, gx, gy = O.energy_grad(W, H, x, y, w, h, c, a)
+    am = O.coefficients(W, H, W - x, y, w, h, c, Mx, My)
+    sign = (-1.0) ** np.arange(Mx)
+    assert np.max(np.abs(am - sign[:, None] * a)) <= 1e-12 * np.max(np.abs(a))
+    Nm, gxm, gym = O.energy_grad(W, H, W - x, y, w, h, c, am)
+    assert np.max(np.abs(Nm - N)) <= 1e-12 * np.max(np.abs(N))
+    assert np.max(np.abs(gxm + gx)) <= 1e-12 * np.max(np.abs(gx))
+    assert np.max(np.abs(gym - gy)) <= 1e-12 * np.max(np.abs(gy))
+    # swap the axes of a square die: a transposes
+    at = O.coefficients(1.0, 1.0, y / H, x / W, h / H, w / W, c, My, Mx)
+    a1 = O.coefficients(1.0, 1.0, x / W, y / H, w / W, h / H, c, Mx, My)
+    assert np.max(np.abs(at - a1.T)) <= 1e-12 * np.max(np.abs(a1))
+
+
+def test_workload_generator_is_deterministic_and_in_die():
+    p = synth.workload(0)
+    q = synth.workload(0)
+    assert p.n == 2000 and np.array_equal(p.x, q.x)
+    for P in (p, synth.workload(1, n=5000), synth.workload(3, n=3000)):
+        assert np.all(P.x - P.w / 2 >= -1e-7) and np.all(P.x + P.w / 2 <= P.W + 1e-7)
+        assert np.all(P.y - P.h / 2 >= -1e-7) and np.all(P.y + P.h / 2 <= P.H + 1e-7)
