@@ -1,0 +1,416 @@
+#!/usr/bin/env python3
+"""Throughput of one energy + gradient evaluation of the analytical Poisson series.
+
+Metric: block * mode^2 terms per second, N * Mx * My / t, where t is the device
+time of one full evaluation through the C ABI (pp_grad with a = NULL: the
+coefficient contraction, the two energy contractions, the row dots, per-block
+energies and the FP64 total), mixed precision next to FP32 plain, with the
+error against the FP64 oracle.
+
+Workload: 200,000 blocks on a 1 x 1 die (99% standard cells h = 0.001,
+w lognormal mean 0.002; 1% macros 0.01-0.05; centres from 20 Gaussian
+clusters), 512 x 512 modes.  Seeded synthetic data (the paper's ISPD placements
+are not available).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--prec tf32|bf16x3|fp32]
+  python bench.py --impl reference ...   (the FP64 CPU oracle on the host cores)
+
+Under torchrun (N > 1) every rank evaluates its own replica of the workload
+(no collective on the data path); the time is the maximum over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "block·mode² terms/s for energy+gradient, mixed vs FP32, err vs FP64"
+WORKLOAD_INDEX = 1
+FLUSH_BYTES = 256 << 20          # > 129 MB L2
+FP32_LANES_PER_SM = 128
+SM_COUNT_GB300 = 152
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+                "sm_max_mhz": 2070.0}, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.t0 = self.t1 = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def mark(self, which):
+        setattr(self, which, time.time())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            return None
+        rows = []
+        for line in out.strip().splitlines():
+            f = [s.strip() for s in line.split(",")]
+            if len(f) < 10:
+                continue
+            try:
+                ts = time.mktime(time.strptime(f[0].split(".")[0], "%Y/%m/%d %H:%M:%S"))
+                rows.append(dict(ts=ts, sm=float(f[2]), max=float(f[3]), reasons=f[5],
+                                 hw=f[6], hwt=f[7], swt=f[8], pcap=f[9]))
+            except Exception:
+                continue
+        if not rows:
+            return None
+        inside = [r for r in rows if self.t0 - 1 <= r["ts"] <= self.t1 + 1] or rows
+        reasons = set()
+        for r in inside:
+            for key, name in (("hw", "hw_slowdown"), ("hwt", "hw_thermal_slowdown"),
+                              ("swt", "sw_thermal_slowdown"), ("pcap", "sw_power_cap")):
+                if r[key].lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(r["sm"] for r in inside),
+                "sm_max_mhz": max(r["max"] for r in inside),
+                "reasons": sorted(reasons), "samples": len(inside)}
+
+
+# ---------------------------------------------------------------------------
+# distributed plumbing (replicas)
+# ---------------------------------------------------------------------------
+def dist_info():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def dist_init(world, backend):
+    import torch.distributed as dist
+    if world > 1 and not dist.is_initialized():
+        dist.init_process_group(backend)
+    return dist
+
+
+def reduce_max(value: float, world: int, device=None) -> float:
+    """Maximum of `value` over ranks (identity for one rank)."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# ---------------------------------------------------------------------------
+# the step
+# ---------------------------------------------------------------------------
+def make_inputs(device, n=None):
+    import torch
+    from paper_2307_12041_gb300 import synth
+    p = synth.workload(WORKLOAD_INDEX, n=n)
+    t = lambda a: torch.from_numpy(a).to(device)
+    return p, (t(p.x), t(p.y), t(p.w), t(p.h), None)
+
+
+def time_steps(binding, p, dev_in, prec, steps, warmup, flush, outs, kernel_timing=False):
+    """Per-step CUDA-event times (ms) of `steps` evaluations after `warmup`; the L2
+    is flushed (FLUSH_BYTES written) before every step, outside the events.  With
+    kernel_timing, the library brackets each of its launches in the timed steps
+    with events on the launch stream; returns (step times, per-kernel times)."""
+    import torch
+    x, y, w, h, c = dev_in
+    stream = torch.cuda.current_stream()
+    run = lambda: binding.grad(x, y, w, h, c, p.W, p.H, p.Mx, p.My, prec, out=outs)
+    for _ in range(warmup):
+        flush.zero_()
+        run()
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(steps)]
+    if kernel_timing:
+        binding.timing_collect()
+        binding.timing_enable(True)
+    for a, b in evs:
+        flush.zero_()
+        a.record(stream)
+        run()
+        b.record(stream)
+    torch.cuda.synchronize()
+    ktimes = None
+    if kernel_timing:
+        binding.timing_enable(False)
+        ktimes = binding.timing_collect()
+    binding.sync_status()
+    return [a.elapsed_time(b) for a, b in evs], ktimes
+
+
+def time_e2e(binding, p, prec, steps, device):
+    """Same evaluation through host buffers: pinned H2D of x, y, w, h, pp_grad, D2H
+    of gx, gy, N, E, all inside the timed region."""
+    import torch
+    n = p.n
+    hx, hy, hw, hh = (torch.from_numpy(a).pin_memory() for a in (p.x, p.y, p.w, p.h))
+    dx, dy, dw, dh = (torch.empty(n, dtype=torch.float32, device=device) for _ in range(4))
+    outs = (torch.empty(n, dtype=torch.float32, device=device),
+            torch.empty(n, dtype=torch.float32, device=device),
+            torch.empty(n, dtype=torch.float32, device=device),
+            torch.empty(1, dtype=torch.float64, device=device))
+    hout = (torch.empty(n, dtype=torch.float32).pin_memory(),
+            torch.empty(n, dtype=torch.float32).pin_memory(),
+            torch.empty(n, dtype=torch.float32).pin_memory(),
+            torch.empty(1, dtype=torch.float64).pin_memory())
+
+    def step():
+        for d, hsrc in ((dx, hx), (dy, hy), (dw, hw), (dh, hh)):
+            d.copy_(hsrc, non_blocking=True)
+        binding.grad(dx, dy, dw, dh, None, p.W, p.H, p.Mx, p.My, prec, out=outs)
+        for hdst, d in zip(hout, outs):
+            hdst.copy_(d, non_blocking=True)
+
+    for _ in range(3):
+        step()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(steps):
+        step()
+    b.record()
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    ms = max(a.elapsed_time(b), wall * 1e3)
+    h2d = 4 * 4 * n
+    d2h = 3 * 4 * n + 8
+    return ms / steps, h2d, d2h
+
+
+def errors_vs(ref, got):
+    out = {}
+    for k in ("a", "N", "gx", "gy"):
+        r = np.asarray(ref[k], dtype=np.float64)
+        g = np.asarray(got[k], dtype=np.float64).reshape(r.shape)
+        d = g - r
+        out[k] = {"max": float(np.max(np.abs(d)) / np.max(np.abs(r))),
+                  "rms": float(np.sqrt(np.mean(d * d)) / np.sqrt(np.mean(r * r)))}
+    out["E"] = abs(got["E"] - ref["E"]) / abs(ref["E"])
+    return out
+
+
+def cpu_baseline(binding, precs, device, n_sample):
+    """The FP64 oracle as it stands on the host cores, on the first `n_sample`
+    blocks of the workload (all modes), plus the GPU's error on that sample."""
+    from oracle import series as O
+    from paper_2307_12041_gb300 import synth
+    p = synth.workload(WORKLOAD_INDEX).subset(np.arange(n_sample))
+    cores = int(os.environ.get("ORACLE_THREADS", os.cpu_count() or 1))
+    t0 = time.perf_counter()
+    ref = O.evaluate(p.W, p.H, p.x, p.y, p.w, p.h, p.c, p.Mx, p.My)
+    dt = time.perf_counter() - t0
+    errs = {}
+    for prec in precs:
+        out = binding.evaluate(p, prec=prec, device=device)
+        got = {k: out[k].double().cpu().numpy() for k in ("a", "N", "gx", "gy")}
+        got["E"] = out["E"]
+        errs[prec] = errors_vs(ref, got)
+    base = {"value": n_sample * p.Mx * p.My / dt, "unit": "terms/s", "cores": cores,
+            "kind": "oracle", "seconds": dt,
+            "sample": f"first {n_sample} of {synth.WORKLOADS[WORKLOAD_INDEX]['n']} blocks, "
+                      f"all {p.Mx}x{p.My} modes: coefficients, per-block energy, gradient (FP64 numpy)"}
+    return base, errs
+
+
+def run_ours(args):
+    import torch
+    from paper_2307_12041_gb300 import binding, synth
+
+    world, rank, local = dist_info()
+    dist_init(world, "nccl")
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    binding.lib()
+    avail = binding.available_precisions()
+    prec = args.prec or ("tf32" if "tf32" in avail else "fp32")
+    if prec not in avail:
+        raise SystemExit(f"precision {prec} not available: {avail}")
+
+    p, dev_in = make_inputs(device)
+    n = p.n
+    outs = (torch.empty(n, dtype=torch.float32, device=device),
+            torch.empty(n, dtype=torch.float32, device=device),
+            torch.empty(n, dtype=torch.float32, device=device),
+            torch.empty(1, dtype=torch.float64, device=device))
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=device)
+    terms = float(n) * p.Mx * p.My
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    barrier(world)
+    torch.cuda.synchronize()
+    clocks.mark("t0")
+    step_ms, ktimes = time_steps(binding, p, dev_in, prec, args.steps, args.warmup, flush, outs,
+                                 kernel_timing=True)
+    clocks.mark("t1")
+    torch.cuda.synchronize()
+    barrier(world)
+    clk = clocks.stop()
+
+    total_ms = reduce_max(sum(step_ms), world, device)
+    ms_per_step = total_ms / args.steps
+    value = world * terms * args.steps / (total_ms / 1e3)
+
+    launches = int(sum(v[0] for v in ktimes.values()))     # our kernels in the timed steps
+    peaks, peak_src = load_peaks()
+    dom = max(("coeff", "energy"), key=lambda k: ktimes[k][1])
+    dom_ms = ktimes[dom][1] / max(ktimes[dom][0], 1)
+    flops = (2.0 if dom == "coeff" else 4.0) * terms
+    if prec == "fp32":
+        bound = "alu"
+        peak = SM_COUNT_GB300 * FP32_LANES_PER_SM * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+        peak_note = f"FP32 FMA: {SM_COUNT_GB300} SMs x {FP32_LANES_PER_SM} lanes x 2 flop x max SM clock"
+    elif prec == "tf32":
+        bound = "tensor"
+        peak = peaks["bf16_tflops"] * 0.5
+        peak_note = f"{peak_src} bf16 burst peak x 0.5 (nominal TF32/BF16 ratio)"
+    else:
+        bound = "tensor"
+        peak = peaks["bf16_tflops"] / 3.0
+        peak_note = f"{peak_src} bf16 burst peak / 3 (three bf16 products per term)"
+    achieved = flops / (dom_ms * 1e-3) / 1e12
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "terms/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": prec,
+        "data": "synthetic",
+        "config": {"workload": synth.WORKLOADS[WORKLOAD_INDEX]["name"], "n": n, "Mx": p.Mx,
+                   "My": p.My, "sample": "rect", "precision": prec, "W": p.W, "H": p.H,
+                   "l2": "flushed: 256 MiB written before every timed step",
+                   "parallelism": f"replicas x{world}"},
+        "roofline": {"bound": bound, "kernel": dom, "achieved": achieved, "peak": peak,
+                     "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                     "peak_source": peak_note,
+                     "flops_per_launch": flops},
+        "kernels_ms_per_step": {k: v[1] / args.steps for k, v in ktimes.items()},
+        "gpu_launches": launches,
+        "clocks": clk,
+    }
+    if rank == 0:
+        # FP32 plain on the same workload (the "vs FP32" half of the metric)
+        if prec != "fp32":
+            torch.cuda.synchronize()
+            f_ms, _ = time_steps(binding, p, dev_in, "fp32", args.steps, args.warmup, flush, outs)
+            fv = terms * args.steps / (sum(f_ms) / 1e3)
+            line["fp32_plain"] = {"value": fv, "ms_per_step": sum(f_ms) / args.steps,
+                                  "speedup_of_mixed": value / world / fv}
+        e_ms, h2d, d2h = time_e2e(binding, p, prec, args.steps, device)
+        line["e2e"] = {"value": world * terms / (e_ms / 1e3), "unit": "terms/s",
+                       "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                       "ms_per_step": e_ms}
+        if world == 1 and not args.no_cpu_baseline:
+            precs = [prec] + (["fp32"] if prec != "fp32" else [])
+            base, errs = cpu_baseline(binding, precs, device, args.cpu_sample)
+            line["cpu_baseline"] = base
+            line["errors_vs_fp64_oracle"] = {"sample": base["sample"], **errs}
+        print(json.dumps(line), flush=True)
+    barrier(world)
+
+
+def run_reference(args):
+    """The FP64 oracle, unmodified, on the host cores: each step evaluates a bounded
+    sample (the first `ref_sample` blocks, all modes) of the same workload."""
+    world, rank, _ = dist_info()
+    if rank != 0:
+        return
+    from oracle import series as O
+    from paper_2307_12041_gb300 import synth
+    n_s = args.ref_sample
+    p = synth.workload(WORKLOAD_INDEX).subset(np.arange(n_s))
+    for _ in range(args.warmup):
+        O.evaluate(p.W, p.H, p.x, p.y, p.w, p.h, p.c, p.Mx, p.My)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        O.evaluate(p.W, p.H, p.x, p.y, p.w, p.h, p.c, p.Mx, p.My)
+    dt = time.perf_counter() - t0
+    terms = float(n_s) * p.Mx * p.My
+    value = terms * args.steps / dt
+    cores = int(os.environ.get("ORACLE_THREADS", os.cpu_count() or 1))
+    sample = (f"first {n_s} of {synth.WORKLOADS[WORKLOAD_INDEX]['n']} blocks, all "
+              f"{p.Mx}x{p.My} modes, per step")
+    line = {"metric": METRIC, "value": value, "unit": "terms/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "impl": "reference",
+            "config": {"workload": synth.WORKLOADS[WORKLOAD_INDEX]["name"], "n": p.n,
+                       "Mx": p.Mx, "My": p.My, "sample": "rect", "precision": "f64"},
+            "cpu_baseline": {"value": value, "unit": "terms/s", "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "terms/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--prec", choices=["fp32", "tf32", "bf16x3"], default=None)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--cpu-sample", type=int, default=200000)
+    ap.add_argument("--ref-sample", type=int, default=10000)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,140 @@
+/*
+ * pp.h -- C ABI of the GB300 library for the analytical solution of Poisson's
+ * equation on a placement die (Zhu, Huang, Chen, Chang, arXiv 2307.12041).
+ *
+ * The die is R = [0, W] x [0, H] (Sec. II-A).  Block i has centre (x_i, y_i),
+ * width w_i, height h_i and charge density c_i (unit density when c is NULL,
+ * the paper's theta_i = 1 of Eq. (global density)).  With mode counts Mx, My the
+ * library evaluates the truncated series of Sec. III (u = 0..Mx-1, p = 0..My-1):
+ *
+ *   coefficients  a_{u,p}       Eq. (a-a), (aup), (au0), (a0p)
+ *   potential     psi           Eq. (psi)
+ *   field         xi = -grad psi  Eq. (ksi)
+ *   energy        N(v) = 1/2 sum_i N_i   (Sec. II-B)
+ *   gradient      dN/d(x_i, y_i) = -(block charge) * xi   (Sec. IV, grad N = -q xi)
+ *
+ * Two readings of the per-block energy are offered (pp_sample):
+ *   PP_RECT   N_i = c_i * (integral of psi over block i).  E = 1/2 sum N_i is then
+ *             the electrostatic energy of the exact rectangle density, and the
+ *             gradient is its exact derivative (minus the block-integrated field).
+ *   PP_CENTER N_i = q_i psi(x_i, y_i), q_i = c_i w_i h_i, and the gradient is
+ *             -q_i xi(x_i, y_i): the centre substitution of Sec. III-C.
+ *
+ * Conventions shared by every call
+ *  - All array arguments are DEVICE pointers owned by the caller; the library
+ *    allocates no device memory.  Scratch space is the caller's workspace `ws`
+ *    (at least pp_workspace_size() bytes, 256-byte aligned).
+ *  - Inputs x, y, w, h (and c if not NULL) are float32 arrays of n elements.
+ *  - The coefficient matrix `a` is float32, Mx x My, row-major with u (the x
+ *    mode) as the row index: a[u * My + p].
+ *  - Calls are asynchronous on `stream` (a cudaStream_t, NULL = legacy default
+ *    stream); the outputs are valid once the stream reaches the call.  Calls
+ *    that share a workspace must be ordered on one stream.
+ *  - The return status covers argument checks and launch errors.  Errors the
+ *    GPU detects while running (a bounded wait that ran out) are recorded in a
+ *    per-device status word that pp_sync_status() reads and clears.
+ *  - n = 0 is valid: outputs are zero (a all zero, *e_total = 0).
+ *  - Limits: 1 <= Mx, My <= 4096; 0 <= n <= 2^31 - 1; W, H finite and > 0.
+ *  - pp_last_error() describes the last non-OK status of the calling thread.
+ */
+#ifndef PP_H
+#define PP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    PP_OK = 0,
+    PP_EINVAL = 1,      /* bad argument: see pp_last_error() */
+    PP_ENOMEM_WS = 2,   /* workspace missing or smaller than pp_workspace_size() */
+    PP_ECUDA = 3,       /* a CUDA runtime/driver call failed */
+    PP_ETIMEOUT = 4,    /* a device-side bounded wait ran out (pp_sync_status) */
+    PP_ENOTSUP = 5      /* precision not available on this device */
+} pp_status;
+
+/* Arithmetic of the three contractions (coefficients, X.K, X'.K):
+ *  PP_FP32    CUDA-core FP32 FMA, FP64 cross-block accumulation of the coefficients.
+ *  PP_TF32    tcgen05 tensor cores, TF32 operands, FP32 accumulation in TMEM.
+ *  PP_BF16X3  tcgen05 tensor cores, operands split into bf16 hi + lo and
+ *             multiplied as hi*hi + hi*lo + lo*hi, FP32 accumulation in TMEM.
+ * In every precision the phase u*x/W is reduced modulo 2 in 64-bit fixed point
+ * and the total energy is summed in FP64. */
+typedef enum { PP_FP32 = 0, PP_TF32 = 1, PP_BF16X3 = 2 } pp_precision;
+
+typedef enum { PP_RECT = 0, PP_CENTER = 1 } pp_sample;
+
+typedef struct {
+    double W, H;               /* die size (Sec. II-A) */
+    int64_t n;                 /* number of blocks */
+    const float *x, *y;        /* block centres, device, n each */
+    const float *w, *h;        /* block widths/heights, device, n each */
+    const float *c;            /* charge densities, device, n; NULL = 1 */
+    int32_t Mx, My;            /* modes kept: u < Mx, p < My (Sec. III-B truncation) */
+} pp_problem;
+
+/* Bytes of workspace the calls below need for this problem and precision
+ * (0 if the problem is invalid; pp_last_error() then says why). */
+size_t pp_workspace_size(const pp_problem *prob, pp_precision prec);
+
+/* Coefficient matrix of the truncated series: Eq. (a-a) a_00 = 0, Eq. (aup)
+ * for u, p >= 1, Eq. (au0) for p = 0, Eq. (a0p) for u = 0, with the block sums
+ * weighted by c_i.  Written to `a` (device, Mx*My float32, u-major). */
+pp_status pp_coeffs(const pp_problem *prob, pp_precision prec, float *a,
+                    void *ws, size_t ws_bytes, void *stream);
+
+/* Per-block energy N_i (Sec. II-B, reading per `sample`) and total energy
+ * E = 1/2 sum_i N_i.  `a` = coefficients from pp_coeffs, or NULL to compute
+ * them inside this call.  e_block (device, n float32) and e_total (device,
+ * one double, accumulated in FP64) may each be NULL; not both. */
+pp_status pp_energy(const pp_problem *prob, pp_precision prec, pp_sample sample,
+                    const float *a, float *e_block, double *e_total,
+                    void *ws, size_t ws_bytes, void *stream);
+
+/* Gradient of E = 1/2 sum_i N_i with respect to the block centres,
+ * gx[i] = dE/dx_i, gy[i] = dE/dy_i (device, n float32 each; PP_RECT: exact
+ * derivative, = -c_i * integral over block i of xi from Eq. (ksi); PP_CENTER:
+ * -q_i xi(x_i, y_i)).  Optionally also N_i and E as in pp_energy (NULL to skip).
+ * `a` = coefficients, or NULL to compute them inside this call.  With a = NULL
+ * this single call is one full energy + gradient evaluation: three
+ * contractions of N x Mx x My. */
+pp_status pp_grad(const pp_problem *prob, pp_precision prec, pp_sample sample,
+                  const float *a, float *gx, float *gy, float *e_block, double *e_total,
+                  void *ws, size_t ws_bytes, void *stream);
+
+/* Waits for `stream`, then reads and clears the current device's status word:
+ * PP_OK, or PP_ETIMEOUT if a kernel gave up a bounded wait since the last check. */
+pp_status pp_sync_status(void *stream);
+
+/* Message for the calling thread's last non-OK status ("" if none). */
+const char *pp_last_error(void);
+
+/* Library build identification string (compile flags, arch). */
+const char *pp_version(void);
+
+/* Kernel timing, a benchmarking aid with no counterpart in the paper.  While
+ * enabled, every kernel launch of the library is bracketed by two CUDA events
+ * recorded on the stream it is launched on.  pp_timing_collect() waits for
+ * those events, then writes per kernel class (pp_kernel) the number of launches
+ * and their summed device time in milliseconds since the previous collect
+ * (arrays of PP_K_COUNT entries, host memory), and resets the sums.  At most
+ * 65536 launches are timed between collects; later ones are counted in
+ * `launches` but add no time.  Timing assumes one device per process. */
+typedef enum {
+    PP_K_PREP = 0,      /* per-block phases and scale factors */
+    PP_K_COEFF = 1,     /* coefficient contraction  St = Xt^T Yt */
+    PP_K_FINISH = 2,    /* a = G o S and the energy operand */
+    PP_K_ENERGY = 3,    /* fused energy / gradient contractions and row dots */
+    PP_K_COUNT = 4
+} pp_kernel;
+void pp_timing_enable(int on);
+pp_status pp_timing_collect(int64_t *launches, double *ms);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PP_H */

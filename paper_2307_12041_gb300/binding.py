@@ -1,0 +1,249 @@
+"""Python binding of the C ABI (include/pp.h): argument marshalling only.
+
+torch provides device memory and the current stream; every arithmetic step of
+the evaluation runs in the CUDA library.  There is no fallback: if libpp.so is
+missing or a call fails, an exception is raised.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+import torch
+
+from . import build_lib
+
+PRECISIONS = {"fp32": 0, "tf32": 1, "bf16x3": 2}
+SAMPLES = {"rect": 0, "center": 1}
+STATUS = {0: "PP_OK", 1: "PP_EINVAL", 2: "PP_ENOMEM_WS", 3: "PP_ECUDA", 4: "PP_ETIMEOUT",
+          5: "PP_ENOTSUP"}
+# Normalised max-error bounds used by the parity tests (max |err| / max |ref|).
+TOLERANCE = {"fp32": 2e-6, "tf32": 5e-3, "bf16x3": 1e-4}
+
+Precision = PRECISIONS
+Sample = SAMPLES
+
+
+class PPError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS.get(status, status)}: {message}")
+        self.status = status
+
+
+class Problem(ctypes.Structure):
+    _fields_ = [("W", ctypes.c_double), ("H", ctypes.c_double), ("n", ctypes.c_int64),
+                ("x", ctypes.c_void_p), ("y", ctypes.c_void_p), ("w", ctypes.c_void_p),
+                ("h", ctypes.c_void_p), ("c", ctypes.c_void_p),
+                ("Mx", ctypes.c_int32), ("My", ctypes.c_int32)]
+
+
+_LIB = None
+EXPORTS = ("pp_workspace_size", "pp_coeffs", "pp_energy", "pp_grad", "pp_sync_status",
+           "pp_last_error", "pp_version", "pp_timing_enable", "pp_timing_collect")
+
+
+def lib_path() -> str:
+    return build_lib.LIB
+
+
+def lib() -> ctypes.CDLL:
+    """Load libpp.so (built in-tree by __graft_entry__.build())."""
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(build_lib.LIB):
+            raise RuntimeError(f"{build_lib.LIB} is not built; run __graft_entry__.build()")
+        L = ctypes.CDLL(build_lib.LIB)
+        P = ctypes.POINTER(Problem)
+        vp, sz, i = ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int
+        L.pp_workspace_size.argtypes = [P, i]
+        L.pp_workspace_size.restype = sz
+        L.pp_coeffs.argtypes = [P, i, vp, vp, sz, vp]
+        L.pp_coeffs.restype = i
+        L.pp_energy.argtypes = [P, i, i, vp, vp, vp, vp, sz, vp]
+        L.pp_energy.restype = i
+        L.pp_grad.argtypes = [P, i, i, vp, vp, vp, vp, vp, vp, sz, vp]
+        L.pp_grad.restype = i
+        L.pp_sync_status.argtypes = [vp]
+        L.pp_sync_status.restype = i
+        L.pp_last_error.argtypes = []
+        L.pp_last_error.restype = ctypes.c_char_p
+        L.pp_version.argtypes = []
+        L.pp_version.restype = ctypes.c_char_p
+        L.pp_timing_enable.argtypes = [i]
+        L.pp_timing_enable.restype = None
+        L.pp_timing_collect.argtypes = [ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double)]
+        L.pp_timing_collect.restype = i
+        _LIB = L
+    return _LIB
+
+
+KERNELS = ("prep", "coeff", "finish", "energy")
+
+
+def timing_enable(on: bool = True):
+    lib().pp_timing_enable(1 if on else 0)
+
+
+def timing_collect():
+    """{kernel: (launches, summed device ms)} since the previous collect."""
+    n = (ctypes.c_int64 * 4)()
+    ms = (ctypes.c_double * 4)()
+    _check(lib().pp_timing_collect(n, ms))
+    return {k: (int(n[i]), float(ms[i])) for i, k in enumerate(KERNELS)}
+
+
+def version() -> str:
+    return lib().pp_version().decode()
+
+
+def available_precisions():
+    v = version()
+    return ("fp32", "tf32", "bf16x3") if "tcgen05" in v else ("fp32",)
+
+
+def _check(st: int):
+    if st != 0:
+        raise PPError(st, lib().pp_last_error().decode())
+
+
+def _ptr(t: Optional[torch.Tensor]) -> Optional[int]:
+    return None if t is None else t.data_ptr()
+
+
+def _stream_handle(device) -> int:
+    return torch.cuda.current_stream(device).cuda_stream
+
+
+def make_problem(x, y, w, h, c, W, H, Mx, My) -> Problem:
+    n = x.numel()
+    for name, t in (("x", x), ("y", y), ("w", w), ("h", h), ("c", c)):
+        if t is None:
+            continue
+        if t.dtype != torch.float32 or not t.is_contiguous() or t.numel() != n:
+            raise ValueError(f"{name} must be a contiguous float32 tensor of {n} elements")
+        if t.device != x.device or t.device.type != "cuda":
+            raise ValueError(f"{name} must be a CUDA tensor on {x.device}")
+    return Problem(float(W), float(H), n, _ptr(x) if n else None, _ptr(y) if n else None,
+                   _ptr(w) if n else None, _ptr(h) if n else None,
+                   _ptr(c) if (c is not None and n) else None, int(Mx), int(My))
+
+
+_WS = {}
+
+
+def workspace(prob: Problem, prec: str, device) -> torch.Tensor:
+    """A cached device workspace of at least pp_workspace_size() bytes."""
+    need = lib().pp_workspace_size(ctypes.byref(prob), PRECISIONS[prec])
+    if need == 0:
+        _check(1)
+    key = (torch.device(device).index, torch.cuda.current_stream(device).cuda_stream)
+    buf = _WS.get(key)
+    if buf is None or buf.numel() < need:
+        buf = torch.empty(need, dtype=torch.uint8, device=device)
+        _WS[key] = buf
+    return buf
+
+
+def coeffs(x, y, w, h, c, W, H, Mx, My, prec="fp32", out=None):
+    """pp_coeffs: the Mx x My coefficient matrix a (float32, u-major)."""
+    prob = make_problem(x, y, w, h, c, W, H, Mx, My)
+    dev = x.device
+    a = out if out is not None else torch.empty((Mx, My), dtype=torch.float32, device=dev)
+    ws = workspace(prob, prec, dev)
+    _check(lib().pp_coeffs(ctypes.byref(prob), PRECISIONS[prec], a.data_ptr(), ws.data_ptr(),
+                           ws.numel(), _stream_handle(dev)))
+    return a
+
+
+def energy(x, y, w, h, c, W, H, Mx, My, prec="fp32", sample="rect", a=None,
+           want_block=True):
+    """pp_energy: (N_i per block or None, E as a 1-element float64 tensor)."""
+    prob = make_problem(x, y, w, h, c, W, H, Mx, My)
+    dev = x.device
+    n = x.numel()
+    eb = torch.empty(n, dtype=torch.float32, device=dev) if want_block else None
+    et = torch.empty(1, dtype=torch.float64, device=dev)
+    ws = workspace(prob, prec, dev)
+    _check(lib().pp_energy(ctypes.byref(prob), PRECISIONS[prec], SAMPLES[sample], _ptr(a),
+                           _ptr(eb) if n else None, et.data_ptr(), ws.data_ptr(), ws.numel(),
+                           _stream_handle(dev)))
+    return eb, et
+
+
+def grad(x, y, w, h, c, W, H, Mx, My, prec="fp32", sample="rect", a=None, want_energy=True,
+         out=None):
+    """pp_grad: (gx, gy, N_i or None, E or None)."""
+    prob = make_problem(x, y, w, h, c, W, H, Mx, My)
+    dev = x.device
+    n = x.numel()
+    if out is None:
+        gx = torch.empty(n, dtype=torch.float32, device=dev)
+        gy = torch.empty(n, dtype=torch.float32, device=dev)
+        eb = torch.empty(n, dtype=torch.float32, device=dev) if want_energy else None
+        et = torch.empty(1, dtype=torch.float64, device=dev) if want_energy else None
+    else:
+        gx, gy, eb, et = out
+    ws = workspace(prob, prec, dev)
+    _check(lib().pp_grad(ctypes.byref(prob), PRECISIONS[prec], SAMPLES[sample], _ptr(a),
+                         _ptr(gx) if n else None, _ptr(gy) if n else None,
+                         _ptr(eb) if (eb is not None and n) else None, _ptr(et),
+                         ws.data_ptr(), ws.numel(), _stream_handle(dev)))
+    return gx, gy, eb, et
+
+
+def sync_status(device=None):
+    """pp_sync_status on the current stream: raises PPError if a kernel timed out."""
+    dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+    _check(lib().pp_sync_status(_stream_handle(dev)))
+
+
+def to_device(p, device):
+    """Upload a synth.Placement's arrays to `device`."""
+    t = lambda a: None if a is None else torch.from_numpy(a).to(device)
+    return t(p.x), t(p.y), t(p.w), t(p.h), t(p.c)
+
+
+def evaluate(p, prec="fp32", device="cuda", sample="rect"):
+    """Coefficients (pp_coeffs) and a full energy + gradient evaluation (pp_grad with
+    a = NULL) of a synth.Placement; results as torch tensors plus E as a float."""
+    x, y, w, h, c = to_device(p, device)
+    a = coeffs(x, y, w, h, c, p.W, p.H, p.Mx, p.My, prec)
+    gx, gy, eb, et = grad(x, y, w, h, c, p.W, p.H, p.Mx, p.My, prec, sample)
+    sync_status(device)
+    return dict(a=a, N=eb, gx=gx, gy=gy, E=float(et.item()))
+
+
+class PoissonEnergy(torch.autograd.Function):
+    """E = 1/2 sum_i N_i as a differentiable function of the block centres.
+
+    forward:  pp_energy (coefficients computed inside the call, not kept)
+    backward: pp_grad with a = NULL: the coefficients are recomputed rather than
+              stored, and the adjoint is grad_out * (dE/dx, dE/dy).  Blocks whose
+              `movable` entry is False receive zero gradient.
+    """
+
+    @staticmethod
+    def forward(ctx, x, y, w, h, c, W, H, Mx, My, prec="fp32", sample="rect", movable=None):
+        _, et = energy(x, y, w, h, c, W, H, Mx, My, prec, sample, want_block=False)
+        ctx.save_for_backward(x, y, w, h, c if c is not None else torch.empty(0, device=x.device),
+                              movable if movable is not None else torch.empty(0, device=x.device))
+        ctx.args = (W, H, Mx, My, prec, sample, c is not None, movable is not None)
+        return et[0]
+
+    @staticmethod
+    def backward(ctx, g):
+        x, y, w, h, c, mov = ctx.saved_tensors
+        W, H, Mx, My, prec, sample, has_c, has_mov = ctx.args
+        gx, gy, _, _ = grad(x.detach(), y.detach(), w, h, c if has_c else None, W, H, Mx, My,
+                            prec, sample, want_energy=False)
+        scale = g.to(torch.float32)
+        gx = gx * scale
+        gy = gy * scale
+        if has_mov:
+            m = mov.to(torch.float32)
+            gx = gx * m
+            gy = gy * m
+        return (gx if ctx.needs_input_grad[0] else None,
+                gy if ctx.needs_input_grad[1] else None,
+                None, None, None, None, None, None, None, None, None, None)

@@ -1,0 +1,392 @@
+// C ABI entry points (include/pp.h): argument checks, workspace layout and the
+// launch sequence of one evaluation.
+//
+//   pp_coeffs : prep -> coefficient contraction -> finish(a)
+//   pp_energy : prep -> [coefficients -> finish(K)] or finish(K from a) -> energy
+//   pp_grad   : same as pp_energy, the energy kernel also writing dE/dx, dE/dy
+#include <atomic>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/pp.h"
+#include "pp_device.cuh"
+#include "pp_internal.h"
+
+namespace pp {
+
+__device__ unsigned g_status;    // bit 0: a bounded wait ran out
+
+namespace {
+
+thread_local std::string t_err;
+
+pp_status fail(pp_status st, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    t_err = buf;
+    return st;
+}
+
+pp_status cuda_fail(cudaError_t e, const char *what) {
+    return fail(PP_ECUDA, "%s: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
+}
+
+constexpr int kMaxDev = 64;
+std::mutex g_mu;
+int g_sm[kMaxDev];
+unsigned *g_status_ptr[kMaxDev];
+int g_cc_major[kMaxDev];
+
+// Per-device constants, looked up once with that device current.
+pp_status device_info(int *dev, int *sm, unsigned **status, int *cc_major) {
+    cudaError_t e = cudaGetDevice(dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    if (*dev < 0 || *dev >= kMaxDev) return fail(PP_EINVAL, "device index %d out of range", *dev);
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!g_status_ptr[*dev]) {
+        int v = 0;
+        e = cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, *dev);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceGetAttribute");
+        g_sm[*dev] = v;
+        e = cudaDeviceGetAttribute(&v, cudaDevAttrComputeCapabilityMajor, *dev);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceGetAttribute");
+        g_cc_major[*dev] = v;
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_status);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(status)");
+        g_status_ptr[*dev] = (unsigned *)p;
+    }
+    *sm = g_sm[*dev];
+    *status = g_status_ptr[*dev];
+    *cc_major = g_cc_major[*dev];
+    return PP_OK;
+}
+
+struct Layout {
+    size_t xrec, yrec, S64, K, total;
+    int Kld;
+};
+
+size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+Layout layout(const pp_problem *p, pp_precision prec) {
+    Layout L{};
+    const size_t n = (size_t)p->n;
+    size_t off = 0;
+    L.xrec = off;
+    off = align256(off + n * sizeof(AxisRec));
+    L.yrec = off;
+    off = align256(off + n * sizeof(AxisRec));
+    L.S64 = off;
+    off = align256(off + (size_t)p->Mx * p->My * sizeof(double));
+    L.K = off;
+    size_t kbytes = 0;
+    switch (prec) {
+        default:
+        case PP_FP32: {
+            const int Mxp = round_up(p->Mx, kSimtKU);
+            L.Kld = round_up(p->My, kSimtKV);
+            kbytes = (size_t)Mxp * L.Kld * sizeof(float);
+        } break;
+    }
+    off = align256(off + kbytes);
+    L.total = off;
+    return L;
+}
+
+pp_status check_dev_ptr(const void *ptr, int dev, const char *name) {
+    cudaPointerAttributes at;
+    cudaError_t e = cudaPointerGetAttributes(&at, ptr);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(PP_EINVAL, "%s: not a CUDA pointer (%s)", name, cudaGetErrorName(e));
+    }
+    if (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged)
+        return fail(PP_EINVAL, "%s: must be device memory", name);
+    if (at.device != dev)
+        return fail(PP_EINVAL, "%s: lives on device %d, current device is %d", name, at.device, dev);
+    return PP_OK;
+}
+
+// Shape checks only (no pointers): die, counts, precision.
+pp_status check_shape(const pp_problem *p, pp_precision prec) {
+    if (!p) return fail(PP_EINVAL, "problem is NULL");
+    if (!std::isfinite(p->W) || !std::isfinite(p->H) || p->W <= 0 || p->H <= 0)
+        return fail(PP_EINVAL, "die size W=%g H=%g must be finite and > 0", p->W, p->H);
+    if (p->n < 0 || p->n > 2147483647LL)
+        return fail(PP_EINVAL, "n=%lld out of range [0, 2^31-1]", (long long)p->n);
+    if (p->Mx < 1 || p->My < 1 || p->Mx > 4096 || p->My > 4096)
+        return fail(PP_EINVAL, "mode counts Mx=%d My=%d must be in [1, 4096]", p->Mx, p->My);
+    if (prec != PP_FP32 && prec != PP_TF32 && prec != PP_BF16X3)
+        return fail(PP_EINVAL, "unknown precision %d", (int)prec);
+    return PP_OK;
+}
+
+pp_status check_problem(const pp_problem *p, pp_precision prec) {
+    pp_status st = check_shape(p, prec);
+    if (st != PP_OK) return st;
+    if (p->n > 0 && (!p->x || !p->y || !p->w || !p->h))
+        return fail(PP_EINVAL, "x, y, w, h must be non-NULL when n > 0");
+    return PP_OK;
+}
+
+struct Ctx {
+    Launch L;
+    Layout lay;
+    int dev;
+    int cc_major;
+};
+
+pp_status setup(const pp_problem *p, pp_precision prec, void *ws, size_t ws_bytes, void *stream,
+                Ctx *ctx) {
+    pp_status st = check_problem(p, prec);
+    if (st != PP_OK) return st;
+    if (prec != PP_FP32) return fail(PP_ENOTSUP, "precision %d is not available in this build", (int)prec);
+    int sm = 0;
+    unsigned *status = nullptr;
+    st = device_info(&ctx->dev, &sm, &status, &ctx->cc_major);
+    if (st != PP_OK) return st;
+    ctx->lay = layout(p, prec);
+    if (!ws || ws_bytes < ctx->lay.total)
+        return fail(PP_ENOMEM_WS, "workspace of %zu bytes needed, %zu given%s", ctx->lay.total,
+                    ws ? ws_bytes : (size_t)0, ws ? "" : " (NULL)");
+    if (((uintptr_t)ws & 255) != 0) return fail(PP_EINVAL, "workspace must be 256-byte aligned");
+    if ((st = check_dev_ptr(ws, ctx->dev, "ws")) != PP_OK) return st;
+    if (p->n > 0) {
+        const void *ptrs[5] = {p->x, p->y, p->w, p->h, p->c};
+        const char *names[5] = {"x", "y", "w", "h", "c"};
+        for (int i = 0; i < 5; ++i) {
+            if (!ptrs[i]) continue;
+            if (((uintptr_t)ptrs[i] & 3) != 0) return fail(PP_EINVAL, "%s is not 4-byte aligned", names[i]);
+            if ((st = check_dev_ptr(ptrs[i], ctx->dev, names[i])) != PP_OK) return st;
+        }
+    }
+    Launch &L = ctx->L;
+    char *base = (char *)ws;
+    L.W = p->W;
+    L.H = p->H;
+    L.n = (int)p->n;
+    L.Mx = p->Mx;
+    L.My = p->My;
+    L.x = p->x;
+    L.y = p->y;
+    L.w = p->w;
+    L.h = p->h;
+    L.c = p->c;
+    L.xrec = (AxisRec *)(base + ctx->lay.xrec);
+    L.yrec = (AxisRec *)(base + ctx->lay.yrec);
+    L.S64 = (double *)(base + ctx->lay.S64);
+    L.K = base + ctx->lay.K;
+    L.Kld = ctx->lay.Kld;
+    L.status = status;
+    L.sm_count = sm;
+    L.stream = (cudaStream_t)stream;
+    return PP_OK;
+}
+
+pp_status out_ptr(const void *ptr, int dev, const char *name, bool required) {
+    if (!ptr) return required ? fail(PP_EINVAL, "%s must be non-NULL", name) : PP_OK;
+    if (((uintptr_t)ptr & 3) != 0) return fail(PP_EINVAL, "%s is not 4-byte aligned", name);
+    return check_dev_ptr(ptr, dev, name);
+}
+
+#define PP_TRY(expr, what)                                  \
+    do {                                                    \
+        cudaError_t _e = (expr);                            \
+        if (_e != cudaSuccess) return cuda_fail(_e, what);  \
+    } while (0)
+
+// ---- optional per-launch event timing (pp_timing_enable / pp_timing_collect)
+struct TimedLaunch {
+    cudaEvent_t a, b;
+    int kind;
+};
+constexpr size_t kMaxTimed = 65536;
+std::mutex g_tmu;
+std::atomic<bool> g_timing{false};
+std::vector<TimedLaunch> g_tpool;
+size_t g_tused = 0;
+int64_t g_tcount[PP_K_COUNT];
+
+long timed_begin(int kind, cudaStream_t s) {
+    if (!g_timing.load(std::memory_order_relaxed)) return -1;
+    std::lock_guard<std::mutex> lk(g_tmu);
+    g_tcount[kind]++;
+    if (g_tused >= kMaxTimed) return -1;
+    if (g_tused == g_tpool.size()) {
+        TimedLaunch t{};
+        if (cudaEventCreate(&t.a) != cudaSuccess || cudaEventCreate(&t.b) != cudaSuccess) {
+            cudaGetLastError();
+            return -1;
+        }
+        g_tpool.push_back(t);
+    }
+    TimedLaunch &t = g_tpool[g_tused];
+    t.kind = kind;
+    if (cudaEventRecord(t.a, s) != cudaSuccess) {
+        cudaGetLastError();
+        return -1;
+    }
+    return (long)g_tused++;
+}
+
+void timed_end(long idx, cudaStream_t s) {
+    if (idx < 0) return;
+    std::lock_guard<std::mutex> lk(g_tmu);
+    cudaEventRecord(g_tpool[(size_t)idx].b, s);
+}
+
+#define PP_LAUNCH(kind, stream, expr, what)                 \
+    do {                                                    \
+        long _t = timed_begin((kind), (stream));            \
+        cudaError_t _e = (expr);                            \
+        timed_end(_t, (stream));                            \
+        if (_e != cudaSuccess) return cuda_fail(_e, what);  \
+    } while (0)
+
+// Coefficients into the workspace (S64 and the energy operand K).
+pp_status run_coefficients(Ctx &c, pp_precision prec, float *a_out) {
+    PP_LAUNCH(PP_K_COEFF, c.L.stream, launch_coeff_simt(c.L), "coefficient kernel launch");
+    PP_LAUNCH(PP_K_FINISH, c.L.stream, launch_finish_simt(c.L, nullptr, a_out), "finish kernel launch");
+    (void)prec;
+    return PP_OK;
+}
+
+pp_status energy_common(const pp_problem *p, pp_precision prec, pp_sample sample, const float *a,
+                        float *gx, float *gy, float *e_block, double *e_total, void *ws,
+                        size_t ws_bytes, void *stream, bool want_grad) {
+    Ctx c;
+    pp_status st = setup(p, prec, ws, ws_bytes, stream, &c);
+    if (st != PP_OK) return st;
+    if (sample != PP_RECT && sample != PP_CENTER) return fail(PP_EINVAL, "unknown sample mode %d", (int)sample);
+    const bool has_blocks = p->n > 0;   // per-block arrays may be NULL when n = 0
+    if (want_grad) {
+        if ((st = out_ptr(gx, c.dev, "gx", has_blocks)) != PP_OK) return st;
+        if ((st = out_ptr(gy, c.dev, "gy", has_blocks)) != PP_OK) return st;
+    } else if (!e_block && !e_total && has_blocks) {
+        return fail(PP_EINVAL, "e_block and e_total are both NULL");
+    }
+    if ((st = out_ptr(e_block, c.dev, "e_block", false)) != PP_OK) return st;
+    if (e_total) {
+        if (((uintptr_t)e_total & 7) != 0) return fail(PP_EINVAL, "e_total is not 8-byte aligned");
+        if ((st = check_dev_ptr(e_total, c.dev, "e_total")) != PP_OK) return st;
+    }
+    if (a && (st = out_ptr(a, c.dev, "a", false)) != PP_OK) return st;
+    if (p->n == 0) {
+        if (e_total) PP_TRY(cudaMemsetAsync(e_total, 0, sizeof(double), c.L.stream), "memset e_total");
+        return PP_OK;
+    }
+    PP_LAUNCH(PP_K_PREP, c.L.stream, launch_prep(c.L, a == nullptr, e_total), "prep kernel launch");
+    if (a) {
+        PP_LAUNCH(PP_K_FINISH, c.L.stream, launch_finish_simt(c.L, a, nullptr), "finish kernel launch");
+    } else {
+        if ((st = run_coefficients(c, prec, nullptr)) != PP_OK) return st;
+    }
+    PP_LAUNCH(PP_K_ENERGY, c.L.stream,
+              launch_energy_simt(c.L, (int)sample, e_block, e_total, want_grad ? gx : nullptr,
+                                 want_grad ? gy : nullptr),
+              "energy kernel launch");
+    return PP_OK;
+}
+
+}  // namespace
+}  // namespace pp
+
+using namespace pp;
+
+extern "C" {
+
+size_t pp_workspace_size(const pp_problem *prob, pp_precision prec) {
+    if (check_shape(prob, prec) != PP_OK) return 0;
+    return layout(prob, prec).total;
+}
+
+pp_status pp_coeffs(const pp_problem *prob, pp_precision prec, float *a, void *ws, size_t ws_bytes,
+                    void *stream) {
+    Ctx c;
+    pp_status st = setup(prob, prec, ws, ws_bytes, stream, &c);
+    if (st != PP_OK) return st;
+    if ((st = out_ptr(a, c.dev, "a", true)) != PP_OK) return st;
+    if (prob->n == 0) {
+        PP_TRY(cudaMemsetAsync(a, 0, (size_t)prob->Mx * prob->My * sizeof(float), c.L.stream), "memset a");
+        return PP_OK;
+    }
+    PP_LAUNCH(PP_K_PREP, c.L.stream, launch_prep(c.L, true, nullptr), "prep kernel launch");
+    return run_coefficients(c, prec, a);
+}
+
+pp_status pp_energy(const pp_problem *prob, pp_precision prec, pp_sample sample, const float *a,
+                    float *e_block, double *e_total, void *ws, size_t ws_bytes, void *stream) {
+    return energy_common(prob, prec, sample, a, nullptr, nullptr, e_block, e_total, ws, ws_bytes,
+                         stream, false);
+}
+
+pp_status pp_grad(const pp_problem *prob, pp_precision prec, pp_sample sample, const float *a,
+                  float *gx, float *gy, float *e_block, double *e_total, void *ws, size_t ws_bytes,
+                  void *stream) {
+    return energy_common(prob, prec, sample, a, gx, gy, e_block, e_total, ws, ws_bytes, stream, true);
+}
+
+pp_status pp_sync_status(void *stream) {
+    int dev, sm, ccm;
+    unsigned *status;
+    pp_status st = device_info(&dev, &sm, &status, &ccm);
+    if (st != PP_OK) return st;
+    cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    unsigned v = 0;
+    e = cudaMemcpyFromSymbol(&v, g_status, sizeof v);
+    if (e != cudaSuccess) return cuda_fail(e, "read status word");
+    if (v) {
+        const unsigned zero = 0;
+        e = cudaMemcpyToSymbol(g_status, &zero, sizeof zero);
+        if (e != cudaSuccess) return cuda_fail(e, "clear status word");
+        return fail(PP_ETIMEOUT, "a kernel gave up a bounded wait (status 0x%x)", v);
+    }
+    return PP_OK;
+}
+
+const char *pp_last_error(void) { return t_err.c_str(); }
+
+void pp_timing_enable(int on) { g_timing.store(on != 0); }
+
+pp_status pp_timing_collect(int64_t *launches, double *ms) {
+    std::lock_guard<std::mutex> lk(g_tmu);
+    double acc[PP_K_COUNT] = {0, 0, 0, 0};
+    for (size_t i = 0; i < g_tused; ++i) {
+        TimedLaunch &t = g_tpool[i];
+        cudaError_t e = cudaEventSynchronize(t.b);
+        float v = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&v, t.a, t.b);
+        if (e != cudaSuccess) {
+            g_tused = 0;
+            return cuda_fail(e, "timing event");
+        }
+        acc[t.kind] += v;
+    }
+    for (int k = 0; k < PP_K_COUNT; ++k) {
+        if (launches) launches[k] = g_tcount[k];
+        if (ms) ms[k] = acc[k];
+        g_tcount[k] = 0;
+    }
+    g_tused = 0;
+    return PP_OK;
+}
+
+const char *pp_version(void) {
+    return "pp 0.1 (sm_103a; FP32 CUDA-core path"
+#ifdef PP_HAVE_TCGEN05
+           ", tcgen05 TF32/BF16x3 paths"
+#endif
+           ")";
+}
+
+}  // extern "C"

@@ -1,0 +1,67 @@
+// Device-side building blocks shared by every kernel of the library.
+//
+// Notation (arXiv 2307.12041, Sec. III): die [0,W] x [0,H]; mode u along x,
+// p (called v here) along y; k_u = u pi / W, l_v = v pi / H.
+//
+// The rectangle integrals of Eq. (aup) factor as
+//   X_iu = int theta_i(x) cos(k_u x) dx = f_u * Xt_iu,  f_u = 2W / (pi max(u,1)),
+//   Xt_iu = c_i cos(pi u s_i) sin(pi u t_i)   (u >= 1),   Xt_i0 = c_i pi t_i,
+// with s_i = x_i / W and t_i = w_i / (2W) (sin a - sin b = 2 cos((a+b)/2) sin((a-b)/2)).
+// The kernels only ever build the scaled basis Xt (values of magnitude <= |c|),
+// and fold f_u, g_v and the Green's weights into the coefficient operand.
+//
+// Phases.  pi u s is reduced modulo 2 pi exactly: s is held as a 64-bit fixed
+// point number s_fix = (s mod 2) * 2^62, so u * s_fix (mod 2^63) is the phase in
+// units of 2^-62 half-turns with no rounding at all.  Only the final reduced
+// phase in [-1, 1) half-turns is rounded to FP32 before sincospif.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace pp {
+
+// Per-block, per-axis record written by the preparation kernel (48 bytes).
+struct __align__(16) AxisRec {
+    unsigned long long s;   // (centre / L) mod 2, fixed point 2^-62 half-turns
+    unsigned long long t;   // (size / (2L)) mod 2, same units
+    float2 es;              // (cos, sin)(pi s): one mode step of the centre phase
+    float2 et;              // (cos, sin)(pi t): one mode step of the half-size phase
+    float v0;               // scaled rectangle basis at mode 0: c pi t (x), pi t (y)
+    float q;                // x axis: centre-sample charge c w h;  y axis: 1
+    float c;                // x axis: charge density c;            y axis: 1
+    float inv_l;            // pi / L (for the derivative factors -u pi / L)
+};
+static_assert(sizeof(AxisRec) == 48, "AxisRec layout");
+
+// e^{i pi m s} for an integer mode m and a fixed-point phase coefficient s.
+// The reduced phase is split into its top 24 bits (exact in FP32, fed to
+// sincospif) and a residual below 2^-23 half-turns, applied as a first-order
+// rotation (the dropped second-order term is below 1e-13).
+__device__ __forceinline__ float2 phase_cs(unsigned long long m, unsigned long long s) {
+    unsigned long long p = m * s;                 // m s mod 2^64, units 2^-62
+    long long q = (long long)(p << 1);            // (m s mod 2) -> [-1, 1), units 2^-63
+    int hi = (int)(q >> 40);                      // signed top 24 bits
+    long long lo = q - ((long long)hi << 40);     // [0, 2^40)
+    float th = (float)hi * 0x1p-23f;              // exact
+    float d = (float)(int)(lo >> 16) * (3.14159265358979f * 0x1p-47f);   // pi * residual
+    float sn, cs;
+    sincospif(th, &sn, &cs);
+    return make_float2(fmaf(-sn, d, cs), fmaf(cs, d, sn));
+}
+
+// z * e (complex), one angle-addition step.
+__device__ __forceinline__ float2 rot(float2 z, float2 e) {
+    return make_float2(fmaf(z.x, e.x, -z.y * e.y), fmaf(z.y, e.x, z.x * e.y));
+}
+
+__device__ __forceinline__ unsigned long long to_fixed_halfturns(double s) {
+    double r = s - 2.0 * floor(0.5 * s);          // [0, 2)
+    long long f = __double2ll_rn(r * 0x1p62);     // [0, 2^63]
+    return (unsigned long long)f & 0x7FFFFFFFFFFFFFFFull;
+}
+
+// Bounded spin on an mbarrier phase; returns false if it ran out.
+constexpr unsigned kSpinLimit = 1u << 26;
+
+}  // namespace pp

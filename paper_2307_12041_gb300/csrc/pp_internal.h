@@ -1,0 +1,39 @@
+// Internal launch interface between the C ABI (pp_api.cu) and the kernels.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace pp {
+
+struct AxisRec;
+
+// Everything a kernel launch needs about one evaluation.
+struct Launch {
+    double W, H;
+    int n;
+    int Mx, My;
+    const float *x, *y, *w, *h, *c;
+    AxisRec *xrec, *yrec;       // workspace: per-block records
+    double *S64;                // workspace: Mx*My FP64 sums of the scaled basis
+    void *K;                    // workspace: energy operand (layout per precision)
+    int Kld;                    // leading dimension / padded size for K (per precision)
+    unsigned *status;           // device status word
+    int sm_count;
+    cudaStream_t stream;
+};
+
+// Padded sizes of the FP32 energy operand (u rows, v columns).
+constexpr int kSimtKU = 32;     // u chunk of the FP32 energy kernel
+constexpr int kSimtKV = 128;    // v tile of the FP32 energy kernel
+inline int round_up(int a, int b) { return (a + b - 1) / b * b; }
+
+// pp_simt.cu
+cudaError_t launch_prep(const Launch &L, bool zero_S, double *e_total);
+cudaError_t launch_coeff_simt(const Launch &L);
+cudaError_t launch_finish_simt(const Launch &L, const float *a_in, float *a_out);
+cudaError_t launch_energy_simt(const Launch &L, int sample, float *e_block, double *e_total,
+                               float *gx, float *gy);
+
+}  // namespace pp

@@ -1,0 +1,471 @@
+// FP32 CUDA-core path (PP_FP32) and the precision-independent kernels:
+//   prep_kernel          per-block fixed-point phases and scale factors
+//   coeff_simt_kernel    St = Xt^T Yt over a slice of blocks (Eq. aup/au0/a0p sums)
+//   finish_simt_kernel   a = G o S (Eq. a-a..a-d) and the energy operand K
+//   energy_simt_kernel   N_i, dE/dx_i, dE/dy_i as row dots of (Xt K) with Yt, Yh
+//
+// Scaled quantities (f_u = 2W/(pi max(u,1)), g_v = 2H/(pi max(v,1))):
+//   X = f Xt, Y = g Yt                      rectangle integrals (Eq. aup factors)
+//   S = X^T Y = f St g,  a = G o S,  G_uv = e_u e_v / (W H (k_u^2 + l_v^2)), G_00 = 0
+//   K = f a g  (the operand of both energy contractions)
+//   N_i  = sum_uv Xt_iu K_uv Yt_iv
+//   gx_i = sum_uv Xh_iu K_uv Yt_iv,  Xh_iu = -(u pi / W) c sin(pi u s) sin(pi u t)
+//   gy_i = sum_uv Xt_iu K_uv Yh_iv,  Yh_iv = -(v pi / H) sin(pi v s) sin(pi v t)
+#include <cmath>
+#include <cstdio>
+
+#include "pp_device.cuh"
+#include "pp_internal.h"
+
+namespace pp {
+
+// ---------------------------------------------------------------------------
+// Preparation: one record per block and axis; zero the FP64 sums and E.
+// ---------------------------------------------------------------------------
+__global__ void prep_kernel(const float *__restrict__ x, const float *__restrict__ y,
+                            const float *__restrict__ w, const float *__restrict__ h,
+                            const float *__restrict__ c, int n, double W, double H,
+                            AxisRec *__restrict__ xr, AxisRec *__restrict__ yr,
+                            double *__restrict__ S64, size_t nS, double *e_total) {
+    const size_t tid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    const double invW = 1.0 / W, invH = 1.0 / H;
+    const double PI = 3.141592653589793;
+    for (size_t i = tid; i < (size_t)n; i += stride) {
+        const double xi = x[i], yi = y[i], wi = w[i], hi = h[i];
+        const double ci = c ? (double)c[i] : 1.0;
+        AxisRec rx, ry;
+        rx.s = to_fixed_halfturns(xi * invW);
+        rx.t = to_fixed_halfturns(0.5 * wi * invW);
+        rx.es = phase_cs(1, rx.s);
+        rx.et = phase_cs(1, rx.t);
+        rx.v0 = (float)(ci * PI * 0.5 * wi * invW);
+        rx.q = (float)(ci * wi * hi);
+        rx.c = (float)ci;
+        rx.inv_l = (float)(PI * invW);
+        ry.s = to_fixed_halfturns(yi * invH);
+        ry.t = to_fixed_halfturns(0.5 * hi * invH);
+        ry.es = phase_cs(1, ry.s);
+        ry.et = phase_cs(1, ry.t);
+        ry.v0 = (float)(PI * 0.5 * hi * invH);
+        ry.q = 1.0f;
+        ry.c = 1.0f;
+        ry.inv_l = (float)(PI * invH);
+        xr[i] = rx;
+        yr[i] = ry;
+    }
+    for (size_t j = tid; j < nS; j += stride) S64[j] = 0.0;
+    if (tid == 0 && e_total) *e_total = 0.0;
+}
+
+cudaError_t launch_prep(const Launch &L, bool zero_S, double *e_total) {
+    size_t nS = zero_S ? (size_t)L.Mx * L.My : 0;
+    size_t work = (size_t)L.n > nS ? (size_t)L.n : nS;
+    int blocks = (int)((work + 255) / 256);
+    if (blocks < 1) blocks = 1;
+    if (blocks > 8 * L.sm_count) blocks = 8 * L.sm_count;
+    prep_kernel<<<blocks, 256, 0, L.stream>>>(L.x, L.y, L.w, L.h, L.c, L.n, L.W, L.H, L.xrec,
+                                              L.yrec, L.S64, nS, e_total);
+    return cudaGetLastError();
+}
+
+// Eight consecutive modes m0..m0+7 of the scaled rectangle basis of one block:
+// out[j] = c cos(pi m s) sin(pi m t), m = m0 + j (value v0 at m = 0).
+__device__ __forceinline__ void rect_run8(const AxisRec &r, int m0, float out[8]) {
+    float2 zs = phase_cs((unsigned long long)m0, r.s);
+    float2 zt = phase_cs((unsigned long long)m0, r.t);
+    zt.x *= r.c;
+    zt.y *= r.c;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        out[j] = zs.x * zt.y;
+        zs = rot(zs, r.es);
+        zt = rot(zt, r.et);
+    }
+    if (m0 == 0) out[0] = r.v0;
+}
+
+// ---------------------------------------------------------------------------
+// Coefficient contraction, FP32: CTA tile 128 (u) x 128 (v), a slice of blocks.
+// ---------------------------------------------------------------------------
+constexpr int CT = 128;   // tile edge
+constexpr int CKC = 16;   // blocks per shared-memory chunk
+
+__global__ void __launch_bounds__(256, 1)
+coeff_simt_kernel(const AxisRec *__restrict__ xr, const AxisRec *__restrict__ yr, int n, int Mx,
+                  int My, int slice, double *__restrict__ S64) {
+    __shared__ __align__(16) float Xs[2][CKC][CT];
+    __shared__ __align__(16) float Ys[2][CKC][CT];
+    const int tiles_v = (My + CT - 1) / CT;
+    const int tu = blockIdx.x / tiles_v, tv = blockIdx.x % tiles_v;
+    const int u_base = tu * CT, v_base = tv * CT;
+    const int b0 = blockIdx.y * slice;
+    const int b1 = min(n, b0 + slice);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    // 16 x 16 thread grid; a warp covers 4 (u) x 8 (v) threads so each 16-byte
+    // shared load is one wavefront.
+    const int ty = (warp >> 1) * 4 + (lane >> 3);
+    const int tx = (warp & 1) * 8 + (lane & 7);
+    // generator mapping: chunk row gk, modes gm..gm+7
+    const int gk = tid >> 4, gm = (tid & 15) * 8;
+
+    float acc[8][8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+
+    const int nchunks = (b1 - b0 + CKC - 1) / CKC;
+    for (int ch = 0; ch < nchunks; ++ch) {
+        const int buf = ch & 1;
+        const int blk = b0 + ch * CKC + gk;
+        float vx[8], vy[8];
+        if (blk < b1) {
+            const AxisRec rx = xr[blk];
+            const AxisRec ry = yr[blk];
+            rect_run8(rx, u_base + gm, vx);
+            rect_run8(ry, v_base + gm, vy);
+        } else {
+#pragma unroll
+            for (int j = 0; j < 8; ++j) vx[j] = vy[j] = 0.f;
+        }
+        *reinterpret_cast<float4 *>(&Xs[buf][gk][gm]) = make_float4(vx[0], vx[1], vx[2], vx[3]);
+        *reinterpret_cast<float4 *>(&Xs[buf][gk][gm + 4]) = make_float4(vx[4], vx[5], vx[6], vx[7]);
+        *reinterpret_cast<float4 *>(&Ys[buf][gk][gm]) = make_float4(vy[0], vy[1], vy[2], vy[3]);
+        *reinterpret_cast<float4 *>(&Ys[buf][gk][gm + 4]) = make_float4(vy[4], vy[5], vy[6], vy[7]);
+        __syncthreads();
+#pragma unroll 4
+        for (int k = 0; k < CKC; ++k) {
+            const float4 a0 = *reinterpret_cast<const float4 *>(&Xs[buf][k][ty * 4]);
+            const float4 a1 = *reinterpret_cast<const float4 *>(&Xs[buf][k][64 + ty * 4]);
+            const float4 c0 = *reinterpret_cast<const float4 *>(&Ys[buf][k][tx * 4]);
+            const float4 c1 = *reinterpret_cast<const float4 *>(&Ys[buf][k][64 + tx * 4]);
+            const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+            const float bv[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+#pragma unroll
+                for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int u = u_base + (i < 4 ? ty * 4 + i : 64 + ty * 4 + i - 4);
+        if (u >= Mx) continue;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int v = v_base + (j < 4 ? tx * 4 + j : 64 + tx * 4 + j - 4);
+            if (v < My) atomicAdd(&S64[(size_t)u * My + v], (double)acc[i][j]);
+        }
+    }
+}
+
+cudaError_t launch_coeff_simt(const Launch &L) {
+    if (L.n == 0) return cudaSuccess;
+    const int tiles = ((L.Mx + CT - 1) / CT) * ((L.My + CT - 1) / CT);
+    // Slices of at most 2048 blocks bound the FP32 accumulation length; the
+    // slices are combined in FP64.
+    int slice = 2048;
+    int slices = (L.n + slice - 1) / slice;
+    dim3 grid(tiles, slices);
+    coeff_simt_kernel<<<grid, 256, 0, L.stream>>>(L.xrec, L.yrec, L.n, L.Mx, L.My, slice, L.S64);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Finish: a = G o (f St g) and the FP32 energy operand K = f a g, zero padded to
+// (round_up(Mx, 32), Kld = round_up(My, 128)).
+// ---------------------------------------------------------------------------
+__global__ void finish_simt_kernel(const double *__restrict__ S64, const float *__restrict__ a_in,
+                                   float *__restrict__ a_out, float *__restrict__ K, int Mx, int My,
+                                   int Mxp, int Kld, double W, double H) {
+    const double PI = 3.141592653589793;
+    const size_t total = (size_t)Mxp * Kld;
+    for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (size_t)gridDim.x * blockDim.x) {
+        const int u = (int)(idx / Kld), v = (int)(idx % Kld);
+        float kv = 0.f;
+        if (u < Mx && v < My) {
+            const double f = 2.0 * W / (PI * (u > 0 ? u : 1));
+            const double g = 2.0 * H / (PI * (v > 0 ? v : 1));
+            double av;
+            if (a_in) {
+                av = (double)a_in[(size_t)u * My + v];
+            } else {
+                const double ku = u * PI / W, lv = v * PI / H;
+                const double eps = (u ? 2.0 : 1.0) * (v ? 2.0 : 1.0);
+                const double G = (u == 0 && v == 0) ? 0.0 : eps / (W * H * (ku * ku + lv * lv));
+                av = G * f * g * S64[(size_t)u * My + v];
+                if (a_out) a_out[(size_t)u * My + v] = (float)av;
+            }
+            kv = (float)(f * av * g);
+        }
+        if (K) K[idx] = kv;
+    }
+}
+
+cudaError_t launch_finish_simt(const Launch &L, const float *a_in, float *a_out) {
+    const int Mxp = round_up(L.Mx, kSimtKU);
+    const size_t total = (size_t)Mxp * L.Kld;
+    int blocks = (int)((total + 255) / 256);
+    if (blocks > 8 * L.sm_count) blocks = 8 * L.sm_count;
+    finish_simt_kernel<<<blocks, 256, 0, L.stream>>>(L.S64, a_in, a_out, (float *)L.K, L.Mx, L.My,
+                                                     Mxp, L.Kld, L.W, L.H);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Energy and gradient, FP32: CTA = 64 blocks; loops over v tiles of 128 and u
+// chunks of 32.  T = Xt K and T' = Xh K accumulate in registers (4 blocks x 8 v
+// per thread); the row dots with Yt and Yh run at the end of each v tile.
+// ---------------------------------------------------------------------------
+constexpr int EB = 64;             // blocks per CTA
+constexpr int EU = kSimtKU;        // u chunk
+constexpr int EV = kSimtKV;        // v tile
+constexpr int XLD = EB + 4;        // padded row of the basis tiles
+
+template <int SAMPLE>
+__device__ __forceinline__ void xbasis_run8(const AxisRec &r, int m0, float xt[8], float xh[8]) {
+    // SAMPLE 0 (rectangle): Xt = c cos(pi u s) sin(pi u t), Xh = -(u pi/W) c sin sin
+    // SAMPLE 1 (centre):    Xt = q cos(pi u s) / f_u,     Xh = -q (u pi/W) sin(pi u s) / f_u
+    float2 zs = phase_cs((unsigned long long)m0, r.s);
+    if (SAMPLE == 0) {
+        float2 zt = phase_cs((unsigned long long)m0, r.t);
+        zt.x *= r.c;
+        zt.y *= r.c;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const float ku = (float)(m0 + j) * r.inv_l;
+            xt[j] = zs.x * zt.y;
+            xh[j] = -ku * zs.y * zt.y;
+            zs = rot(zs, r.es);
+            zt = rot(zt, r.et);
+        }
+        if (m0 == 0) xt[0] = r.v0;
+    } else {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int m = m0 + j;
+            const float ku = (float)m * r.inv_l;
+            const float inv_f = 0.5f * (float)(m > 0 ? m : 1) * r.inv_l;   // 1 / f_u
+            xt[j] = r.q * zs.x * inv_f;
+            xh[j] = -r.q * ku * zs.y * inv_f;
+            zs = rot(zs, r.es);
+        }
+    }
+}
+
+template <int SAMPLE>
+__device__ __forceinline__ void ybasis_run4(const AxisRec &r, int m0, float yt[4], float yh[4]) {
+    // SAMPLE 0: Yt = cos(pi v s) sin(pi v t) (v0 at v = 0), Yh = -(v pi/H) sin sin
+    // SAMPLE 1: Yt = cos(pi v s) / g_v,                   Yh = -(v pi/H) sin(pi v s) / g_v
+    float2 zs = phase_cs((unsigned long long)m0, r.s);
+    if (SAMPLE == 0) {
+        float2 zt = phase_cs((unsigned long long)m0, r.t);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const float lv = (float)(m0 + j) * r.inv_l;
+            yt[j] = zs.x * zt.y;
+            yh[j] = -lv * zs.y * zt.y;
+            zs = rot(zs, r.es);
+            zt = rot(zt, r.et);
+        }
+        if (m0 == 0) yt[0] = r.v0;
+    } else {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int m = m0 + j;
+            const float lv = (float)m * r.inv_l;
+            const float inv_g = 0.5f * (float)(m > 0 ? m : 1) * r.inv_l;
+            yt[j] = zs.x * inv_g;
+            yh[j] = -lv * zs.y * inv_g;
+            zs = rot(zs, r.es);
+        }
+    }
+}
+
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::); }
+
+struct EnergySmem {
+    float Xs[2][EU][XLD];
+    float Xh[2][EU][XLD];
+    float Ks[2][EU][EV];
+    double red[8];
+};
+
+template <int SAMPLE>
+__global__ void __launch_bounds__(256, 1)
+energy_simt_kernel(const AxisRec *__restrict__ xr, const AxisRec *__restrict__ yr, int n, int Mx,
+                   int My, const float *__restrict__ K, int Kld, float *__restrict__ e_block,
+                   double *__restrict__ e_total, float *__restrict__ gx, float *__restrict__ gy) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    EnergySmem &sm = *reinterpret_cast<EnergySmem *>(smem_raw);
+    auto &Xs = sm.Xs;
+    auto &Xh = sm.Xh;
+    auto &Ks = sm.Ks;
+    auto &red = sm.red;
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int blk0 = blockIdx.x * EB;
+    // compute mapping: bt = group of 4 blocks, vt = group of 8 v (two runs of 4)
+    const int bt = warp * 2 + (lane >> 4);
+    const int vt = lane & 15;
+    // generator mapping: one block (column), 8 u's (run)
+    const int g_run = warp >> 1;                 // u offset g_run*8 in the chunk
+    const int g_blk = (warp & 1) * 32 + lane;    // block within the CTA
+
+    const int nuc = (Mx + EU - 1) / EU;
+    const int nvt = (My + EV - 1) / EV;
+    const int total = nuc * nvt;
+
+    float eN[4] = {0.f, 0.f, 0.f, 0.f}, eX[4] = {0.f, 0.f, 0.f, 0.f}, eY[4] = {0.f, 0.f, 0.f, 0.f};
+    float T[4][8], Tp[4][8];
+
+    const bool g_valid = blk0 + g_blk < n;
+    AxisRec grec;
+    if (g_valid) grec = xr[blk0 + g_blk];
+
+    auto load_K = [&](int it, int buf) {
+        const int vtile = it / nuc, uc = it % nuc;
+        const float *src = K + (size_t)(uc * EU) * Kld + vtile * EV;
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int e = (tid + r * 256) * 4;      // float index within the 32 x 128 tile
+            const int row = e / EV, col = e % EV;
+            cp_async16(&Ks[buf][row][col], src + (size_t)row * Kld + col);
+        }
+        cp_async_commit();
+    };
+
+    load_K(0, 0);
+    for (int it = 0; it < total; ++it) {
+        const int buf = it & 1;
+        const int vtile = it / nuc, uc = it % nuc;
+        if (uc == 0) {
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 8; ++j) T[i][j] = Tp[i][j] = 0.f;
+        }
+        // basis chunk
+        {
+            float xt[8], xh[8];
+            if (g_valid) {
+                xbasis_run8<SAMPLE>(grec, uc * EU + g_run * 8, xt, xh);
+            } else {
+#pragma unroll
+                for (int j = 0; j < 8; ++j) xt[j] = xh[j] = 0.f;
+            }
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                Xs[buf][g_run * 8 + j][g_blk] = xt[j];
+                Xh[buf][g_run * 8 + j][g_blk] = xh[j];
+            }
+        }
+        cp_async_wait_all();
+        __syncthreads();
+        if (it + 1 < total) load_K(it + 1, buf ^ 1);
+#pragma unroll 4
+        for (int k = 0; k < EU; ++k) {
+            const float4 a = *reinterpret_cast<const float4 *>(&Xs[buf][k][bt * 4]);
+            const float4 b = *reinterpret_cast<const float4 *>(&Xh[buf][k][bt * 4]);
+            const float4 k0 = *reinterpret_cast<const float4 *>(&Ks[buf][k][vt * 4]);
+            const float4 k1 = *reinterpret_cast<const float4 *>(&Ks[buf][k][64 + vt * 4]);
+            const float av[4] = {a.x, a.y, a.z, a.w};
+            const float bv[4] = {b.x, b.y, b.z, b.w};
+            const float kv[8] = {k0.x, k0.y, k0.z, k0.w, k1.x, k1.y, k1.z, k1.w};
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    T[i][j] = fmaf(av[i], kv[j], T[i][j]);
+                    Tp[i][j] = fmaf(bv[i], kv[j], Tp[i][j]);
+                }
+        }
+        if (uc == nuc - 1) {
+            // row dots for this v tile
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int b = blk0 + bt * 4 + i;
+                if (b >= n) continue;
+                const AxisRec ry = yr[b];
+#pragma unroll
+                for (int half = 0; half < 2; ++half) {
+                    const int v0 = vtile * EV + half * 64 + vt * 4;
+                    float yt[4], yh[4];
+                    ybasis_run4<SAMPLE>(ry, v0, yt, yh);
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        if (v0 + j < My) {
+                            const float t = T[i][half * 4 + j], tp = Tp[i][half * 4 + j];
+                            eN[i] = fmaf(t, yt[j], eN[i]);
+                            eY[i] = fmaf(t, yh[j], eY[i]);
+                            eX[i] = fmaf(tp, yt[j], eX[i]);
+                        }
+                    }
+                }
+            }
+        }
+    }
+    // reduce over the 16 v groups (lanes differing in the low 4 bits)
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+#pragma unroll
+        for (int off = 8; off >= 1; off >>= 1) {
+            eN[i] += __shfl_xor_sync(0xffffffffu, eN[i], off);
+            eX[i] += __shfl_xor_sync(0xffffffffu, eX[i], off);
+            eY[i] += __shfl_xor_sync(0xffffffffu, eY[i], off);
+        }
+    }
+    double esum = 0.0;
+    if (vt == 0) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int b = blk0 + bt * 4 + i;
+            if (b < n) {
+                if (e_block) e_block[b] = eN[i];
+                if (gx) gx[b] = eX[i];
+                if (gy) gy[b] = eY[i];
+                esum += (double)eN[i];
+            }
+        }
+    }
+    if (e_total) {
+        esum += __shfl_xor_sync(0xffffffffu, esum, 16);
+        if (lane == 0) red[warp] = esum;
+        __syncthreads();
+        if (tid == 0) {
+            double s = 0.0;
+            for (int k = 0; k < 8; ++k) s += red[k];
+            atomicAdd(e_total, 0.5 * s);
+        }
+    }
+}
+
+cudaError_t launch_energy_simt(const Launch &L, int sample, float *e_block, double *e_total,
+                               float *gx, float *gy) {
+    if (L.n == 0) return cudaSuccess;
+    const int grid = (L.n + EB - 1) / EB;
+    const float *K = (const float *)L.K;
+    const int smem = (int)sizeof(EnergySmem);
+    cudaError_t err;
+    if (sample == 0) {
+        err = cudaFuncSetAttribute(energy_simt_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (err != cudaSuccess) return err;
+        energy_simt_kernel<0><<<grid, 256, smem, L.stream>>>(L.xrec, L.yrec, L.n, L.Mx, L.My, K, L.Kld,
+                                                             e_block, e_total, gx, gy);
+    } else {
+        err = cudaFuncSetAttribute(energy_simt_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (err != cudaSuccess) return err;
+        energy_simt_kernel<1><<<grid, 256, smem, L.stream>>>(L.xrec, L.yrec, L.n, L.Mx, L.My, K, L.Kld,
+                                                             e_block, e_total, gx, gy);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace pp

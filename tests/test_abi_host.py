@@ -1,0 +1,79 @@
+"""Host-side checks of the C ABI: the library builds, loads, exports every symbol
+that include/pp.h declares, sizes its workspace, and rejects bad arguments
+before touching the GPU.  No kernel is launched here."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_2307_12041_gb300 import binding, build_lib
+    build_lib.build()
+    return binding.lib()
+
+
+def declared_symbols():
+    names = set()
+    for f in os.listdir(os.path.join(ROOT, "include")):
+        if f.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", f)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names |= set(re.findall(r"\b(pp_\w+)\s*\(", src))
+    return sorted(names)
+
+
+def test_header_declares_the_boundary():
+    names = declared_symbols()
+    for must in ("pp_coeffs", "pp_energy", "pp_grad", "pp_workspace_size", "pp_last_error",
+                 "pp_sync_status"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(L):
+    for name in declared_symbols():
+        assert hasattr(L, name), name
+
+
+def _prob(**kw):
+    from paper_2307_12041_gb300.binding import Problem
+    d = dict(W=1.0, H=1.0, n=10, x=None, y=None, w=None, h=None, c=None, Mx=16, My=16)
+    d.update(kw)
+    return Problem(d["W"], d["H"], d["n"], d["x"], d["y"], d["w"], d["h"], d["c"], d["Mx"], d["My"])
+
+
+def test_workspace_size_scales_and_rejects_invalid(L):
+    ws = lambda p, prec=0: L.pp_workspace_size(ctypes.byref(p), prec)
+    a = ws(_prob(n=1000))
+    b = ws(_prob(n=2000))
+    assert a > 0 and b > a
+    assert ws(_prob(n=0)) > 0
+    assert ws(_prob(Mx=64, My=64)) > ws(_prob(Mx=16, My=16))
+    for bad in (dict(W=0.0), dict(H=-1.0), dict(W=float("nan")), dict(W=float("inf")),
+                dict(n=-1), dict(Mx=0), dict(My=4097), dict(n=2 ** 31)):
+        assert ws(_prob(**bad)) == 0, bad
+        assert L.pp_last_error().decode() != ""
+    assert L.pp_workspace_size(ctypes.byref(_prob()), 7) == 0
+    assert L.pp_workspace_size(None, 0) == 0
+
+
+def test_calls_reject_bad_problems_before_any_launch(L):
+    vp = ctypes.c_void_p
+    for bad in (dict(W=0.0), dict(n=-5), dict(Mx=5000), dict(x=None, n=3)):
+        p = _prob(**bad)
+        assert L.pp_coeffs(ctypes.byref(p), 0, vp(16), vp(256), 1 << 20, None) == 1
+        assert L.pp_energy(ctypes.byref(p), 0, 0, None, vp(16), None, vp(256), 1 << 20, None) == 1
+        assert L.pp_grad(ctypes.byref(p), 0, 0, None, vp(16), vp(16), None, None, vp(256),
+                         1 << 20, None) == 1
+    assert L.pp_coeffs(None, 0, None, None, 0, None) == 1
+    assert "NULL" in L.pp_last_error().decode()
+    assert L.pp_coeffs(ctypes.byref(_prob()), 9, vp(16), vp(256), 1 << 20, None) == 1
+
+
+def test_version_string(L):
+    v = L.pp_version().decode()
+    assert "sm_103a" in v

@@ -1,0 +1,169 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Error measure per output vector (coefficients a, per-block energy N, gradient
+gx, gy): max |gpu - oracle| / max |oracle|, bounded by binding.TOLERANCE[prec];
+the total energy E is compared relatively.  Inputs are seeded and synthetic.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import series as O
+from paper_2307_12041_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def nerr(got, ref):
+    got = np.asarray(got, dtype=np.float64).reshape(ref.shape)
+    scale = np.max(np.abs(ref))
+    return float(np.max(np.abs(got - ref)) / scale) if scale > 0 else float(np.max(np.abs(got)))
+
+
+def check(out, ref, tol, keys=("a", "N", "gx", "gy"), label=""):
+    errs = {}
+    for k in keys:
+        errs[k] = nerr(out[k].double().cpu().numpy(), ref[k])
+    errs["E"] = abs(out["E"] - ref["E"]) / max(abs(ref["E"]), 1e-300)
+    bad = {k: v for k, v in errs.items() if not v <= tol}
+    assert not bad, f"{label} errors above {tol:.1e}: {bad} (all: {errs})"
+    return errs
+
+
+def placement(n, Mx, My, seed, W=1.0, H=1.0, charge=False, kind="uniform"):
+    if kind == "uniform":
+        return synth.uniform_blocks(n, Mx, My, seed, W, H, charge=charge)
+    return synth.cell_mix(n, Mx, My, seed, W, H)
+
+
+SHAPES = [
+    # n, Mx, My, W, H, charge, kind
+    (2000, 64, 64, 1.0, 1.0, False, "uniform"),     # the small workload
+    (1, 1, 1, 1.0, 1.0, False, "uniform"),
+    (1, 7, 5, 2.0, 0.5, True, "uniform"),
+    (37, 5, 130, 1.0, 1.0, True, "uniform"),
+    (300, 129, 33, 1.7, 0.9, True, "uniform"),
+    (4099, 200, 257, 1.0, 1.0, False, "mix"),
+]
+
+
+@pytest.mark.parametrize("shape", SHAPES, ids=lambda s: f"n{s[0]}_{s[1]}x{s[2]}")
+def test_parity_with_oracle(pp, shape):
+    n, Mx, My, W, H, charge, kind = shape
+    p = placement(n, Mx, My, seed=100 + n, W=W, H=H, charge=charge, kind=kind)
+    ref = O.evaluate(p.W, p.H, p.x, p.y, p.w, p.h, p.c, Mx, My)
+    for prec in pp.binding.available_precisions():
+        out = pp.binding.evaluate(p, prec=prec)
+        check(out, ref, pp.binding.TOLERANCE[prec], label=f"{prec} {shape}")
+
+
+@pytest.mark.parametrize("prec", ["fp32", "tf32", "bf16x3"])
+def test_center_sampling_parity(pp, prec):
+    if prec not in pp.binding.available_precisions():
+        pytest.skip("precision not built")
+    p = placement(1500, 48, 72, seed=7, W=1.3, H=0.8, charge=True)
+    ref = O.evaluate(p.W, p.H, p.x, p.y, p.w, p.h, p.c, p.Mx, p.My, sample="center")
+    out = pp.binding.evaluate(p, prec=prec, sample="center")
+    check(out, ref, pp.binding.TOLERANCE[prec], label=f"center {prec}")
+
+
+def test_zero_blocks(pp):
+    dev = torch.device("cuda")
+    e = torch.empty(0, dtype=torch.float32, device=dev)
+    for prec in pp.binding.available_precisions():
+        a = pp.binding.coeffs(e, e, e, e, None, 1.0, 1.0, 8, 9, prec)
+        assert a.shape == (8, 9) and float(a.abs().max()) == 0.0
+        gx, gy, eb, et = pp.binding.grad(e, e, e, e, None, 1.0, 1.0, 8, 9, prec)
+        assert gx.numel() == 0 and float(et.item()) == 0.0
+
+
+def test_given_coefficients_match_internal(pp):
+    p = placement(3000, 96, 80, seed=3, charge=True)
+    dev = torch.device("cuda")
+    x, y, w, h, c = pp.binding.to_device(p, dev)
+    for prec in pp.binding.available_precisions():
+        a = pp.binding.coeffs(x, y, w, h, c, p.W, p.H, p.Mx, p.My, prec)
+        g1 = pp.binding.grad(x, y, w, h, c, p.W, p.H, p.Mx, p.My, prec)
+        g2 = pp.binding.grad(x, y, w, h, c, p.W, p.H, p.Mx, p.My, prec, a=a)
+        e2 = pp.binding.energy(x, y, w, h, c, p.W, p.H, p.Mx, p.My, prec, a=a)
+        tol = pp.binding.TOLERANCE[prec]
+        for t1, t2 in ((g1[0], g2[0]), (g1[1], g2[1]), (g1[2], g2[2]), (g1[2], e2[0])):
+            assert float((t1 - t2).abs().max()) <= tol * float(t1.abs().max())
+        assert abs(float(g1[3]) - float(e2[1])) <= tol * abs(float(g1[3]))
+
+
+def test_block_linearity_and_permutation(pp):
+    """Coefficients are a sum over blocks: a(A u B) = a(A) + a(B) (the chunked
+    accumulation a multi-GPU split would all-reduce), and block order is irrelevant."""
+    p = placement(5000, 128, 128, seed=9)
+    dev = torch.device("cuda")
+    x, y, w, h, c = pp.binding.to_device(p, dev)
+    for prec in pp.binding.available_precisions():
+        tol = pp.binding.TOLERANCE[prec]
+        a = pp.binding.coeffs(x, y, w, h, c, 1.0, 1.0, 128, 128, prec)
+        k = 1937
+        a1 = pp.binding.coeffs(x[:k], y[:k], w[:k], h[:k], None, 1.0, 1.0, 128, 128, prec)
+        a2 = pp.binding.coeffs(x[k:], y[k:], w[k:], h[k:], None, 1.0, 1.0, 128, 128, prec)
+        assert float((a - a1 - a2).abs().max()) <= tol * float(a.abs().max())
+        perm = torch.randperm(p.n, generator=torch.Generator().manual_seed(1)).to(dev)
+        ap = pp.binding.coeffs(x[perm], y[perm], w[perm], h[perm], None, 1.0, 1.0, 128, 128, prec)
+        assert float((a - ap).abs().max()) <= tol * float(a.abs().max())
+
+
+def test_max_mode_counts(pp):
+    p = placement(64, 4096, 4096, seed=12, charge=True)
+    ref = O.evaluate(p.W, p.H, p.x, p.y, p.w, p.h, p.c, p.Mx, p.My)
+    for prec in pp.binding.available_precisions():
+        out = pp.binding.evaluate(p, prec=prec)
+        check(out, ref, pp.binding.TOLERANCE[prec], label=f"4096^2 {prec}")
+
+
+def test_invalid_pointers_are_rejected(pp):
+    dev = torch.device("cuda")
+    x = torch.rand(10, device=dev)
+    host = torch.rand(10)
+    with pytest.raises(ValueError):
+        pp.binding.coeffs(x, host, x, x, None, 1.0, 1.0, 4, 4)
+    ctypes = __import__("ctypes")
+    prob = pp.binding.make_problem(x, x, x, x, None, 1.0, 1.0, 4, 4)
+    prob.y = host.data_ptr()                     # a host address: must be refused, not launched
+    a = torch.empty(16, device=dev)
+    ws = pp.binding.workspace(prob, "fp32", dev)
+    st = pp.binding.lib().pp_coeffs(ctypes.byref(prob), 0, a.data_ptr(), ws.data_ptr(),
+                                    ws.numel(), None)
+    assert st == 1
+    st = pp.binding.lib().pp_coeffs(ctypes.byref(prob), 0, a.data_ptr(), ws.data_ptr(), 16, None)
+    assert st in (1, 2)
+
+
+# ---------------------------------------------------------------------------
+# Full-size throughput workload (200k blocks, 512 x 512 modes): coefficients in
+# full, energies and gradients on a seeded sample of blocks.
+# ---------------------------------------------------------------------------
+
+@pytest.fixture(scope="module")
+def big():
+    p = synth.workload(1)
+    a = O.coefficients(p.W, p.H, p.x, p.y, p.w, p.h, p.c, p.Mx, p.My)
+    idx = np.sort(np.random.default_rng(5).choice(p.n, 2000, replace=False))
+    N, gx, gy = O.energy_grad(p.W, p.H, p.x, p.y, p.w, p.h, p.c, a, idx=idx)
+    return p, a, idx, dict(N=N, gx=gx, gy=gy)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "tf32", "bf16x3"])
+def test_full_size_workload_sampled(pp, big, prec):
+    if prec not in pp.binding.available_precisions():
+        pytest.skip("precision not built")
+    p, a_ref, idx, ref = big
+    out = pp.binding.evaluate(p, prec=prec)
+    tol = pp.binding.TOLERANCE[prec]
+    ea = nerr(out["a"].double().cpu().numpy(), a_ref)
+    assert ea <= tol, (prec, "a", ea)
+    ti = torch.from_numpy(idx).cuda()
+    for k in ("N", "gx", "gy"):
+        e = nerr(out[k][ti].double().cpu().numpy(), ref[k])
+        assert e <= tol, (prec, k, e)
+    # E from the GPU's per-block energies equals the GPU's FP64 total
+    assert abs(out["E"] - 0.5 * float(out["N"].double().sum())) <= 1e-6 * abs(out["E"])
