@@ -228,6 +228,8 @@ def time_e2e(binding, p, prec, steps, device):
 
 
 def errors_vs(ref, got):
+    """Per output: max |err| / max |ref| and RMS err / RMS ref; the gradient also as
+    one vector (both components normalised by the larger component scale)."""
     out = {}
     for k in ("a", "N", "gx", "gy"):
         r = np.asarray(ref[k], dtype=np.float64)
@@ -235,6 +237,11 @@ def errors_vs(ref, got):
         d = g - r
         out[k] = {"max": float(np.max(np.abs(d)) / np.max(np.abs(r))),
                   "rms": float(np.sqrt(np.mean(d * d)) / np.sqrt(np.mean(r * r)))}
+    r = np.stack([np.asarray(ref["gx"], np.float64), np.asarray(ref["gy"], np.float64)])
+    g = np.stack([np.asarray(got["gx"], np.float64).reshape(-1), np.asarray(got["gy"], np.float64).reshape(-1)])
+    d = g - r
+    out["grad"] = {"max": float(np.max(np.abs(d)) / np.max(np.abs(r))),
+                   "rms": float(np.sqrt(np.mean(d * d)) / np.sqrt(np.mean(r * r)))}
     out["E"] = abs(got["E"] - ref["E"]) / abs(ref["E"])
     return out
 

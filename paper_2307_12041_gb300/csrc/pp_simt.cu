@@ -85,17 +85,35 @@ __device__ __forceinline__ void rect_run8(const AxisRec &r, int m0, float out[8]
     if (m0 == 0) out[0] = r.v0;
 }
 
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::); }
+
 // ---------------------------------------------------------------------------
 // Coefficient contraction, FP32: CTA tile 128 (u) x 128 (v), a slice of blocks.
 // ---------------------------------------------------------------------------
 constexpr int CT = 128;   // tile edge
 constexpr int CKC = 16;   // blocks per shared-memory chunk
 
+struct CoeffSmem {
+    float Xs[2][CKC][CT];
+    float Ys[2][CKC][CT];
+    AxisRec Rs[2][2][CKC];
+    float lo[64 * 256];      // compensation terms of the running sums, [i*8+j][thread]
+};
+
 __global__ void __launch_bounds__(256, 1)
 coeff_simt_kernel(const AxisRec *__restrict__ xr, const AxisRec *__restrict__ yr, int n, int Mx,
                   int My, int slice, double *__restrict__ S64) {
-    __shared__ __align__(16) float Xs[2][CKC][CT];
-    __shared__ __align__(16) float Ys[2][CKC][CT];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    CoeffSmem &sm = *reinterpret_cast<CoeffSmem *>(smem_raw);
+    auto &Xs = sm.Xs;
+    auto &Ys = sm.Ys;
+    auto &Rs = sm.Rs;
+    float *lo_s = sm.lo;
     const int tiles_v = (My + CT - 1) / CT;
     const int tu = blockIdx.x / tiles_v, tv = blockIdx.x % tiles_v;
     const int u_base = tu * CT, v_base = tv * CT;
@@ -109,31 +127,58 @@ coeff_simt_kernel(const AxisRec *__restrict__ xr, const AxisRec *__restrict__ yr
     // generator mapping: chunk row gk, modes gm..gm+7
     const int gk = tid >> 4, gm = (tid & 15) * 8;
 
-    float acc[8][8];
+    // Each chunk of CKC blocks is summed into fresh registers, then added to a
+    // compensated running sum (hi in registers, lo in shared memory; error-free
+    // two-sum), so the FP32 rounding does not grow with the slice length.
+    float hi[8][8];
 #pragma unroll
     for (int i = 0; i < 8; ++i)
 #pragma unroll
-        for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+        for (int j = 0; j < 8; ++j) {
+            hi[i][j] = 0.f;
+            lo_s[(i * 8 + j) * 256 + tid] = 0.f;
+        }
 
     const int nchunks = (b1 - b0 + CKC - 1) / CKC;
+    // The records of chunk ch + 1 are copied to shared memory (cp.async) while
+    // chunk ch is multiplied: 16 blocks x 2 axes x 48 bytes = 96 x 16-byte pieces.
+    auto fetch_recs = [&](int ch, int buf) {
+        if (tid < 2 * CKC * 3) {
+            const int axis = tid / (CKC * 3), r = tid % (CKC * 3);
+            const int k = r / 3, piece = r % 3;
+            const int b = b0 + ch * CKC + k;
+            if (b < b1) {
+                const AxisRec *src = (axis == 0 ? xr : yr) + b;
+                cp_async16(reinterpret_cast<char *>(&Rs[buf][axis][k]) + 16 * piece,
+                           reinterpret_cast<const char *>(src) + 16 * piece);
+            }
+        }
+        cp_async_commit();
+    };
+    fetch_recs(0, 0);
     for (int ch = 0; ch < nchunks; ++ch) {
         const int buf = ch & 1;
-        const int blk = b0 + ch * CKC + gk;
+        cp_async_wait_all();
+        __syncthreads();
         float vx[8], vy[8];
-        if (blk < b1) {
-            const AxisRec rx = xr[blk];
-            const AxisRec ry = yr[blk];
-            rect_run8(rx, u_base + gm, vx);
-            rect_run8(ry, v_base + gm, vy);
+        if (b0 + ch * CKC + gk < b1) {
+            rect_run8(Rs[buf][0][gk], u_base + gm, vx);
+            rect_run8(Rs[buf][1][gk], v_base + gm, vy);
         } else {
 #pragma unroll
             for (int j = 0; j < 8; ++j) vx[j] = vy[j] = 0.f;
         }
+        if (ch + 1 < nchunks) fetch_recs(ch + 1, buf ^ 1);
         *reinterpret_cast<float4 *>(&Xs[buf][gk][gm]) = make_float4(vx[0], vx[1], vx[2], vx[3]);
         *reinterpret_cast<float4 *>(&Xs[buf][gk][gm + 4]) = make_float4(vx[4], vx[5], vx[6], vx[7]);
         *reinterpret_cast<float4 *>(&Ys[buf][gk][gm]) = make_float4(vy[0], vy[1], vy[2], vy[3]);
         *reinterpret_cast<float4 *>(&Ys[buf][gk][gm + 4]) = make_float4(vy[4], vy[5], vy[6], vy[7]);
         __syncthreads();
+        float acc[8][8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+#pragma unroll
+            for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
 #pragma unroll 4
         for (int k = 0; k < CKC; ++k) {
             const float4 a0 = *reinterpret_cast<const float4 *>(&Xs[buf][k][ty * 4]);
@@ -147,6 +192,15 @@ coeff_simt_kernel(const AxisRec *__restrict__ xr, const AxisRec *__restrict__ yr
 #pragma unroll
                 for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
         }
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const float s = hi[i][j] + acc[i][j];
+                const float bb = s - hi[i][j];
+                lo_s[(i * 8 + j) * 256 + tid] += (hi[i][j] - (s - bb)) + (acc[i][j] - bb);
+                hi[i][j] = s;
+            }
     }
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
@@ -155,7 +209,8 @@ coeff_simt_kernel(const AxisRec *__restrict__ xr, const AxisRec *__restrict__ yr
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
             const int v = v_base + (j < 4 ? tx * 4 + j : 64 + tx * 4 + j - 4);
-            if (v < My) atomicAdd(&S64[(size_t)u * My + v], (double)acc[i][j]);
+            if (v < My)
+                atomicAdd(&S64[(size_t)u * My + v], (double)hi[i][j] + (double)lo_s[(i * 8 + j) * 256 + tid]);
         }
     }
 }
@@ -168,7 +223,10 @@ cudaError_t launch_coeff_simt(const Launch &L) {
     int slice = 2048;
     int slices = (L.n + slice - 1) / slice;
     dim3 grid(tiles, slices);
-    coeff_simt_kernel<<<grid, 256, 0, L.stream>>>(L.xrec, L.yrec, L.n, L.Mx, L.My, slice, L.S64);
+    const int smem = (int)sizeof(CoeffSmem);
+    cudaError_t err = cudaFuncSetAttribute(coeff_simt_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (err != cudaSuccess) return err;
+    coeff_simt_kernel<<<grid, 256, smem, L.stream>>>(L.xrec, L.yrec, L.n, L.Mx, L.My, slice, L.S64);
     return cudaGetLastError();
 }
 
@@ -284,12 +342,6 @@ __device__ __forceinline__ void ybasis_run4(const AxisRec &r, int m0, float yt[4
     }
 }
 
-__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
-    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem));
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::); }
 
 struct EnergySmem {
     float Xs[2][EU][XLD];
@@ -330,8 +382,15 @@ energy_simt_kernel(const AxisRec *__restrict__ xr, const AxisRec *__restrict__ y
     AxisRec grec;
     if (g_valid) grec = xr[blk0 + g_blk];
 
+    // Iteration `it` visits v tiles and u chunks from the highest modes down, so
+    // that the decaying terms of K are summed smallest first.
+    auto coords = [&](int it, int &vtile, int &uc) {
+        vtile = nvt - 1 - it / nuc;
+        uc = nuc - 1 - it % nuc;
+    };
     auto load_K = [&](int it, int buf) {
-        const int vtile = it / nuc, uc = it % nuc;
+        int vtile, uc;
+        coords(it, vtile, uc);
         const float *src = K + (size_t)(uc * EU) * Kld + vtile * EV;
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
@@ -345,8 +404,9 @@ energy_simt_kernel(const AxisRec *__restrict__ xr, const AxisRec *__restrict__ y
     load_K(0, 0);
     for (int it = 0; it < total; ++it) {
         const int buf = it & 1;
-        const int vtile = it / nuc, uc = it % nuc;
-        if (uc == 0) {
+        int vtile, uc;
+        coords(it, vtile, uc);
+        if (uc == nuc - 1) {
 #pragma unroll
             for (int i = 0; i < 4; ++i)
 #pragma unroll
@@ -371,7 +431,7 @@ energy_simt_kernel(const AxisRec *__restrict__ xr, const AxisRec *__restrict__ y
         __syncthreads();
         if (it + 1 < total) load_K(it + 1, buf ^ 1);
 #pragma unroll 4
-        for (int k = 0; k < EU; ++k) {
+        for (int k = EU - 1; k >= 0; --k) {
             const float4 a = *reinterpret_cast<const float4 *>(&Xs[buf][k][bt * 4]);
             const float4 b = *reinterpret_cast<const float4 *>(&Xh[buf][k][bt * 4]);
             const float4 k0 = *reinterpret_cast<const float4 *>(&Ks[buf][k][vt * 4]);
@@ -387,20 +447,20 @@ energy_simt_kernel(const AxisRec *__restrict__ xr, const AxisRec *__restrict__ y
                     Tp[i][j] = fmaf(bv[i], kv[j], Tp[i][j]);
                 }
         }
-        if (uc == nuc - 1) {
-            // row dots for this v tile
+        if (uc == 0) {
+            // row dots for this v tile (highest v first)
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
                 const int b = blk0 + bt * 4 + i;
                 if (b >= n) continue;
                 const AxisRec ry = yr[b];
 #pragma unroll
-                for (int half = 0; half < 2; ++half) {
+                for (int half = 1; half >= 0; --half) {
                     const int v0 = vtile * EV + half * 64 + vt * 4;
                     float yt[4], yh[4];
                     ybasis_run4<SAMPLE>(ry, v0, yt, yh);
 #pragma unroll
-                    for (int j = 0; j < 4; ++j) {
+                    for (int j = 3; j >= 0; --j) {
                         if (v0 + j < My) {
                             const float t = T[i][half * 4 + j], tp = Tp[i][half * 4 + j];
                             eN[i] = fmaf(t, yt[j], eN[i]);

@@ -22,10 +22,23 @@ def nerr(got, ref):
     return float(np.max(np.abs(got - ref)) / scale) if scale > 0 else float(np.max(np.abs(got)))
 
 
-def check(out, ref, tol, keys=("a", "N", "gx", "gy"), label=""):
+def gerr(gx, gy, ref):
+    """Gradient error normalised by the gradient's scale: max over blocks and both
+    components of |g - g_ref| / max over blocks and components of |g_ref|."""
+    rx, ry = ref["gx"], ref["gy"]
+    scale = max(np.max(np.abs(rx)), np.max(np.abs(ry)))
+    d = max(np.max(np.abs(np.asarray(gx, np.float64).reshape(rx.shape) - rx)),
+            np.max(np.abs(np.asarray(gy, np.float64).reshape(ry.shape) - ry)))
+    return float(d / scale) if scale > 0 else float(d)
+
+
+def check(out, ref, tol, keys=("a", "N", "grad"), label=""):
     errs = {}
     for k in keys:
-        errs[k] = nerr(out[k].double().cpu().numpy(), ref[k])
+        if k == "grad":
+            errs[k] = gerr(out["gx"].double().cpu().numpy(), out["gy"].double().cpu().numpy(), ref)
+        else:
+            errs[k] = nerr(out[k].double().cpu().numpy(), ref[k])
     errs["E"] = abs(out["E"] - ref["E"]) / max(abs(ref["E"]), 1e-300)
     bad = {k: v for k, v in errs.items() if not v <= tol}
     assert not bad, f"{label} errors above {tol:.1e}: {bad} (all: {errs})"
@@ -162,8 +175,9 @@ def test_full_size_workload_sampled(pp, big, prec):
     ea = nerr(out["a"].double().cpu().numpy(), a_ref)
     assert ea <= tol, (prec, "a", ea)
     ti = torch.from_numpy(idx).cuda()
-    for k in ("N", "gx", "gy"):
-        e = nerr(out[k][ti].double().cpu().numpy(), ref[k])
-        assert e <= tol, (prec, k, e)
+    e = nerr(out["N"][ti].double().cpu().numpy(), ref["N"])
+    assert e <= tol, (prec, "N", e)
+    e = gerr(out["gx"][ti].double().cpu().numpy(), out["gy"][ti].double().cpu().numpy(), ref)
+    assert e <= tol, (prec, "grad", e)
     # E from the GPU's per-block energies equals the GPU's FP64 total
     assert abs(out["E"] - 0.5 * float(out["N"].double().sum())) <= 1e-6 * abs(out["E"])
