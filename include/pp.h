@@ -105,6 +105,32 @@ pp_status pp_grad(const pp_problem *prob, pp_precision prec, pp_sample sample,
                   const float *a, float *gx, float *gy, float *e_block, double *e_total,
                   void *ws, size_t ws_bytes, void *stream);
 
+/* Allocation-free energy + gradient.  The paper has no counterpart: this entry
+ * point exists for callers that cannot allocate device memory where they
+ * evaluate the energy (a host that fixes its device budget at start-up, a
+ * plugin whose host tool owns every allocation, code inside a region where an
+ * allocator call would break the caller's own memory bookkeeping).  It computes
+ * the same outputs as pp_grad(prob, PP_FP32, sample, NULL, ...) -- one full
+ * evaluation with the coefficients computed inside the call -- but takes no
+ * workspace: its scratch is a static device array of PP_STATIC_SCRATCH_BYTES
+ * that every GPU loading this library reserves until the process exits.
+ * The caller passes the inputs and outputs as for pp_grad (gx, gy required when
+ * n > 0; e_block, e_total optional).
+ *  - Limits: n <= PP_STATIC_MAX_BLOCKS, Mx, My <= PP_STATIC_MAX_MODES; larger
+ *    problems are rejected with PP_EINVAL (use pp_grad with a workspace).
+ *  - It allocates nothing: no cudaMalloc/cudaFree or allocating library call.
+ *  - The first call on a device looks up the array's device address (set-up,
+ *    once per device, with that device current); make that first call before
+ *    any stream capture.
+ *  - All calls share the one array and it keeps the previous call's contents;
+ *    what must start at zero is cleared on `stream` by each call.  Calls whose
+ *    kernels overlap on the GPU (unordered streams) race on the array. */
+#define PP_STATIC_MAX_BLOCKS 32768
+#define PP_STATIC_MAX_MODES 256
+#define PP_STATIC_SCRATCH_BYTES 3932160
+pp_status pp_grad_noalloc(const pp_problem *prob, pp_sample sample, float *gx, float *gy,
+                          float *e_block, double *e_total, void *stream);
+
 /* Waits for `stream`, then reads and clears the current device's status word:
  * PP_OK, or PP_ETIMEOUT if a kernel gave up a bounded wait since the last check. */
 pp_status pp_sync_status(void *stream);

@@ -40,7 +40,8 @@ class Problem(ctypes.Structure):
 
 _LIB = None
 EXPORTS = ("pp_workspace_size", "pp_coeffs", "pp_energy", "pp_grad", "pp_sync_status",
-           "pp_last_error", "pp_version", "pp_timing_enable", "pp_timing_collect")
+           "pp_last_error", "pp_version", "pp_timing_enable", "pp_timing_collect",
+           "pp_grad_noalloc")
 
 
 def lib_path() -> str:
@@ -70,6 +71,8 @@ def lib() -> ctypes.CDLL:
         L.pp_last_error.restype = ctypes.c_char_p
         L.pp_version.argtypes = []
         L.pp_version.restype = ctypes.c_char_p
+        L.pp_grad_noalloc.argtypes = [P, i, vp, vp, vp, vp, vp]
+        L.pp_grad_noalloc.restype = i
         L.pp_timing_enable.argtypes = [i]
         L.pp_timing_enable.restype = None
         L.pp_timing_collect.argtypes = [ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double)]
@@ -189,6 +192,24 @@ def grad(x, y, w, h, c, W, H, Mx, My, prec="fp32", sample="rect", a=None, want_e
                          _ptr(gx) if n else None, _ptr(gy) if n else None,
                          _ptr(eb) if (eb is not None and n) else None, _ptr(et),
                          ws.data_ptr(), ws.numel(), _stream_handle(dev)))
+    return gx, gy, eb, et
+
+
+def grad_noalloc(x, y, w, h, c, W, H, Mx, My, sample="rect", out=None):
+    """pp_grad_noalloc: the FP32 evaluation with the library's static scratch instead
+    of a workspace (for callers that cannot allocate).  Returns (gx, gy, N_i, E)."""
+    prob = make_problem(x, y, w, h, c, W, H, Mx, My)
+    dev = x.device
+    n = x.numel()
+    if out is None:
+        out = (torch.empty(n, dtype=torch.float32, device=dev),
+               torch.empty(n, dtype=torch.float32, device=dev),
+               torch.empty(n, dtype=torch.float32, device=dev),
+               torch.empty(1, dtype=torch.float64, device=dev))
+    gx, gy, eb, et = out
+    _check(lib().pp_grad_noalloc(ctypes.byref(prob), SAMPLES[sample], _ptr(gx) if n else None,
+                                 _ptr(gy) if n else None, _ptr(eb) if (eb is not None and n) else None,
+                                 _ptr(et), _stream_handle(dev)))
     return gx, gy, eb, et
 
 

@@ -298,6 +298,9 @@ pp_status energy_common(const pp_problem *p, pp_precision prec, pp_sample sample
 }
 
 }  // namespace
+
+void set_last_error(const char *msg) { t_err = msg ? msg : ""; }
+
 }  // namespace pp
 
 using namespace pp;

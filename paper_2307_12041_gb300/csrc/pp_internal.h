@@ -29,6 +29,9 @@ constexpr int kSimtKU = 32;     // u chunk of the FP32 energy kernel
 constexpr int kSimtKV = 128;    // v tile of the FP32 energy kernel
 inline int round_up(int a, int b) { return (a + b - 1) / b * b; }
 
+// pp_api.cu: message returned by pp_last_error() for the calling thread
+void set_last_error(const char *msg);
+
 // pp_simt.cu
 cudaError_t launch_prep(const Launch &L, bool zero_S, double *e_total);
 cudaError_t launch_coeff_simt(const Launch &L);
