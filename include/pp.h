@@ -127,7 +127,7 @@ pp_status pp_grad(const pp_problem *prob, pp_precision prec, pp_sample sample,
  *    kernels overlap on the GPU (unordered streams) race on the array. */
 #define PP_STATIC_MAX_BLOCKS 32768
 #define PP_STATIC_MAX_MODES 256
-#define PP_STATIC_SCRATCH_BYTES 3932160
+#define PP_STATIC_SCRATCH_BYTES 4980736
 pp_status pp_grad_noalloc(const pp_problem *prob, pp_sample sample, float *gx, float *gy,
                           float *e_block, double *e_total, void *stream);
 

@@ -71,12 +71,17 @@ pp_status device_info(int *dev, int *sm, unsigned **status, int *cc_major) {
 }
 
 struct Layout {
-    size_t xrec, yrec, S64, K, total;
+    size_t xrec, yrec, S64, K, Klo, part, total;
     int Kld;
+    TcPlan plan;
 };
 
 size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 
+// Workspace regions (byte offsets, each 256-byte aligned):
+//   PP_FP32:          x/y records, S64 [Mx*My] FP64, K FP32 [round_up(Mx,32)][round_up(My,128)]
+//   PP_TF32/BF16X3:   x/y records, partial tiles [slices][Mxc][Myc] FP32,
+//                     K in the TMA-tiled operand layout (TF32, or bf16 hi + lo)
 Layout layout(const pp_problem *p, pp_precision prec) {
     Layout L{};
     const size_t n = (size_t)p->n;
@@ -85,19 +90,26 @@ Layout layout(const pp_problem *p, pp_precision prec) {
     off = align256(off + n * sizeof(AxisRec));
     L.yrec = off;
     off = align256(off + n * sizeof(AxisRec));
-    L.S64 = off;
-    off = align256(off + (size_t)p->Mx * p->My * sizeof(double));
-    L.K = off;
-    size_t kbytes = 0;
-    switch (prec) {
-        default:
-        case PP_FP32: {
-            const int Mxp = round_up(p->Mx, kSimtKU);
-            L.Kld = round_up(p->My, kSimtKV);
-            kbytes = (size_t)Mxp * L.Kld * sizeof(float);
-        } break;
+    if (prec == PP_FP32) {
+        L.S64 = off;
+        off = align256(off + (size_t)p->Mx * p->My * sizeof(double));
+        L.K = off;
+        const int Mxp = round_up(p->Mx, kSimtKU);
+        L.Kld = round_up(p->My, kSimtKV);
+        off = align256(off + (size_t)Mxp * L.Kld * sizeof(float));
+        L.Klo = L.part = 0;
+    } else {
+        L.plan = tc_plan((int)p->n, p->Mx, p->My);
+        L.part = off;
+        off = align256(off + (size_t)L.plan.slices * L.plan.Mxc * L.plan.Myc * sizeof(float));
+        const size_t kel = (size_t)L.plan.Mxe * L.plan.Mye;
+        L.K = off;
+        off = align256(off + kel * (prec == PP_TF32 ? 4 : 2));
+        L.Klo = off;
+        if (prec == PP_BF16X3) off = align256(off + kel * 2);
+        L.S64 = 0;
+        L.Kld = L.plan.Mye;
     }
-    off = align256(off + kbytes);
     L.total = off;
     return L;
 }
@@ -143,17 +155,22 @@ struct Ctx {
     Layout lay;
     int dev;
     int cc_major;
+    pp_precision prec;
+    char *base;
 };
 
 pp_status setup(const pp_problem *p, pp_precision prec, void *ws, size_t ws_bytes, void *stream,
                 Ctx *ctx) {
     pp_status st = check_problem(p, prec);
     if (st != PP_OK) return st;
-    if (prec != PP_FP32) return fail(PP_ENOTSUP, "precision %d is not available in this build", (int)prec);
     int sm = 0;
     unsigned *status = nullptr;
     st = device_info(&ctx->dev, &sm, &status, &ctx->cc_major);
     if (st != PP_OK) return st;
+    if (prec != PP_FP32 && ctx->cc_major != 10)
+        return fail(PP_ENOTSUP, "tensor-core precisions need a compute capability 10.x GPU (this is %d.x)",
+                    ctx->cc_major);
+    ctx->prec = prec;
     ctx->lay = layout(p, prec);
     if (!ws || ws_bytes < ctx->lay.total)
         return fail(PP_ENOMEM_WS, "workspace of %zu bytes needed, %zu given%s", ctx->lay.total,
@@ -171,6 +188,7 @@ pp_status setup(const pp_problem *p, pp_precision prec, void *ws, size_t ws_byte
     }
     Launch &L = ctx->L;
     char *base = (char *)ws;
+    ctx->base = base;
     L.W = p->W;
     L.H = p->H;
     L.n = (int)p->n;
@@ -183,7 +201,7 @@ pp_status setup(const pp_problem *p, pp_precision prec, void *ws, size_t ws_byte
     L.c = p->c;
     L.xrec = (AxisRec *)(base + ctx->lay.xrec);
     L.yrec = (AxisRec *)(base + ctx->lay.yrec);
-    L.S64 = (double *)(base + ctx->lay.S64);
+    L.S64 = prec == PP_FP32 ? (double *)(base + ctx->lay.S64) : nullptr;
     L.K = base + ctx->lay.K;
     L.Kld = ctx->lay.Kld;
     L.status = status;
@@ -252,11 +270,47 @@ void timed_end(long idx, cudaStream_t s) {
         if (_e != cudaSuccess) return cuda_fail(_e, what);  \
     } while (0)
 
-// Coefficients into the workspace (S64 and the energy operand K).
-pp_status run_coefficients(Ctx &c, pp_precision prec, float *a_out) {
-    PP_LAUNCH(PP_K_COEFF, c.L.stream, launch_coeff_simt(c.L), "coefficient kernel launch");
-    PP_LAUNCH(PP_K_FINISH, c.L.stream, launch_finish_simt(c.L, nullptr, a_out), "finish kernel launch");
-    (void)prec;
+// Coefficients into the workspace (FP32: S64 and K; tensor cores: partial tiles
+// and the tiled K operand), optionally also to a_out.
+pp_status run_coefficients(Ctx &c, float *a_out) {
+    if (c.prec == PP_FP32) {
+        PP_LAUNCH(PP_K_COEFF, c.L.stream, launch_coeff_simt(c.L), "coefficient kernel launch");
+        PP_LAUNCH(PP_K_FINISH, c.L.stream, launch_finish_simt(c.L, nullptr, a_out), "finish kernel launch");
+    } else {
+        float *part = (float *)(c.base + c.lay.part);
+        void *Khi = c.base + c.lay.K, *Klo = c.base + c.lay.Klo;
+        PP_LAUNCH(PP_K_COEFF, c.L.stream, launch_coeff_tc(c.L, (int)c.prec, c.lay.plan, part),
+                  "coefficient kernel launch");
+        PP_LAUNCH(PP_K_FINISH, c.L.stream,
+                  launch_finish_tc(c.L, (int)c.prec, c.lay.plan, part, nullptr, a_out, Khi, Klo),
+                  "finish kernel launch");
+    }
+    return PP_OK;
+}
+
+// Energy operand K from caller-provided coefficients.
+pp_status operand_from_a(Ctx &c, const float *a) {
+    if (c.prec == PP_FP32) {
+        PP_LAUNCH(PP_K_FINISH, c.L.stream, launch_finish_simt(c.L, a, nullptr), "finish kernel launch");
+    } else {
+        PP_LAUNCH(PP_K_FINISH, c.L.stream,
+                  launch_finish_tc(c.L, (int)c.prec, c.lay.plan, nullptr, a, nullptr, c.base + c.lay.K,
+                                   c.base + c.lay.Klo),
+                  "finish kernel launch");
+    }
+    return PP_OK;
+}
+
+pp_status run_energy(Ctx &c, pp_sample sample, float *e_block, double *e_total, float *gx, float *gy) {
+    if (c.prec == PP_FP32) {
+        PP_LAUNCH(PP_K_ENERGY, c.L.stream, launch_energy_simt(c.L, (int)sample, e_block, e_total, gx, gy),
+                  "energy kernel launch");
+    } else {
+        PP_LAUNCH(PP_K_ENERGY, c.L.stream,
+                  launch_energy_tc(c.L, (int)c.prec, (int)sample, c.lay.plan, c.base + c.lay.K,
+                                   c.base + c.lay.Klo, e_block, e_total, gx, gy),
+                  "energy kernel launch");
+    }
     return PP_OK;
 }
 
@@ -284,16 +338,12 @@ pp_status energy_common(const pp_problem *p, pp_precision prec, pp_sample sample
         if (e_total) PP_TRY(cudaMemsetAsync(e_total, 0, sizeof(double), c.L.stream), "memset e_total");
         return PP_OK;
     }
-    PP_LAUNCH(PP_K_PREP, c.L.stream, launch_prep(c.L, a == nullptr, e_total), "prep kernel launch");
-    if (a) {
-        PP_LAUNCH(PP_K_FINISH, c.L.stream, launch_finish_simt(c.L, a, nullptr), "finish kernel launch");
-    } else {
-        if ((st = run_coefficients(c, prec, nullptr)) != PP_OK) return st;
-    }
-    PP_LAUNCH(PP_K_ENERGY, c.L.stream,
-              launch_energy_simt(c.L, (int)sample, e_block, e_total, want_grad ? gx : nullptr,
-                                 want_grad ? gy : nullptr),
-              "energy kernel launch");
+    const bool zero_S = a == nullptr && prec == PP_FP32;
+    PP_LAUNCH(PP_K_PREP, c.L.stream, launch_prep(c.L, zero_S, e_total), "prep kernel launch");
+    st = a ? operand_from_a(c, a) : run_coefficients(c, nullptr);
+    if (st != PP_OK) return st;
+    st = run_energy(c, sample, e_block, e_total, want_grad ? gx : nullptr, want_grad ? gy : nullptr);
+    if (st != PP_OK) return st;
     return PP_OK;
 }
 
@@ -322,8 +372,8 @@ pp_status pp_coeffs(const pp_problem *prob, pp_precision prec, float *a, void *w
         PP_TRY(cudaMemsetAsync(a, 0, (size_t)prob->Mx * prob->My * sizeof(float), c.L.stream), "memset a");
         return PP_OK;
     }
-    PP_LAUNCH(PP_K_PREP, c.L.stream, launch_prep(c.L, true, nullptr), "prep kernel launch");
-    return run_coefficients(c, prec, a);
+    PP_LAUNCH(PP_K_PREP, c.L.stream, launch_prep(c.L, prec == PP_FP32, nullptr), "prep kernel launch");
+    return run_coefficients(c, a);
 }
 
 pp_status pp_energy(const pp_problem *prob, pp_precision prec, pp_sample sample, const float *a,
@@ -385,11 +435,7 @@ pp_status pp_timing_collect(int64_t *launches, double *ms) {
 }
 
 const char *pp_version(void) {
-    return "pp 0.1 (sm_103a; FP32 CUDA-core path"
-#ifdef PP_HAVE_TCGEN05
-           ", tcgen05 TF32/BF16x3 paths"
-#endif
-           ")";
+    return "pp 0.2 (sm_103a; FP32 CUDA-core path, tcgen05 TF32/BF16x3 paths)";
 }
 
 }  // extern "C"

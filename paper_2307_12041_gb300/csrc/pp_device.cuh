@@ -21,7 +21,7 @@
 
 namespace pp {
 
-// Per-block, per-axis record written by the preparation kernel (48 bytes).
+// Per-block, per-axis record written by the preparation kernel (64 bytes).
 struct __align__(16) AxisRec {
     unsigned long long s;   // (centre / L) mod 2, fixed point 2^-62 half-turns
     unsigned long long t;   // (size / (2L)) mod 2, same units
@@ -31,8 +31,10 @@ struct __align__(16) AxisRec {
     float q;                // x axis: centre-sample charge c w h;  y axis: 1
     float c;                // x axis: charge density c;            y axis: 1
     float inv_l;            // pi / L (for the derivative factors -u pi / L)
+    float2 es8;             // (cos, sin)(8 pi s): an 8-mode step
+    float2 et8;             // (cos, sin)(8 pi t)
 };
-static_assert(sizeof(AxisRec) == 48, "AxisRec layout");
+static_assert(sizeof(AxisRec) == 64, "AxisRec layout");
 
 // e^{i pi m s} for an integer mode m and a fixed-point phase coefficient s.
 // The reduced phase is split into its top 24 bits (exact in FP32, fed to

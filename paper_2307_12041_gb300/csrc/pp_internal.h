@@ -29,6 +29,21 @@ constexpr int kSimtKU = 32;     // u chunk of the FP32 energy kernel
 constexpr int kSimtKV = 128;    // v tile of the FP32 energy kernel
 inline int round_up(int a, int b) { return (a + b - 1) / b * b; }
 
+// Tensor-core path (pp_tc.cu).  Coefficient tiles are 256 x 256 (padded extents
+// Mxc, Myc); the energy operand is padded to (Mxe = 32k, Mye = 256k).  Blocks are
+// cut into `slices` of slice_len for the persistent coefficient kernel; the plan
+// depends only on the problem (kPlanSMs sets the target of two units per SM).
+constexpr int kPlanSMs = 152;
+struct TcPlan {
+    int Mxc, Myc, Mxe, Mye, tiles, slices, slice_len;
+};
+TcPlan tc_plan(int n, int Mx, int My);
+cudaError_t launch_coeff_tc(const Launch &L, int prec, const TcPlan &P, float *part);
+cudaError_t launch_finish_tc(const Launch &L, int prec, const TcPlan &P, const float *part,
+                             const float *a_in, float *a_out, void *Khi, void *Klo);
+cudaError_t launch_energy_tc(const Launch &L, int prec, int sample, const TcPlan &P, void *Khi,
+                             void *Klo, float *e_block, double *e_total, float *gx, float *gy);
+
 // pp_api.cu: message returned by pp_last_error() for the calling thread
 void set_last_error(const char *msg);
 

@@ -43,6 +43,8 @@ __global__ void prep_kernel(const float *__restrict__ x, const float *__restrict
         rx.q = (float)(ci * wi * hi);
         rx.c = (float)ci;
         rx.inv_l = (float)(PI * invW);
+        rx.es8 = phase_cs(8, rx.s);
+        rx.et8 = phase_cs(8, rx.t);
         ry.s = to_fixed_halfturns(yi * invH);
         ry.t = to_fixed_halfturns(0.5 * hi * invH);
         ry.es = phase_cs(1, ry.s);
@@ -51,6 +53,8 @@ __global__ void prep_kernel(const float *__restrict__ x, const float *__restrict
         ry.q = 1.0f;
         ry.c = 1.0f;
         ry.inv_l = (float)(PI * invH);
+        ry.es8 = phase_cs(8, ry.s);
+        ry.et8 = phase_cs(8, ry.t);
         xr[i] = rx;
         yr[i] = ry;
     }
@@ -141,11 +145,11 @@ coeff_simt_kernel(const AxisRec *__restrict__ xr, const AxisRec *__restrict__ yr
 
     const int nchunks = (b1 - b0 + CKC - 1) / CKC;
     // The records of chunk ch + 1 are copied to shared memory (cp.async) while
-    // chunk ch is multiplied: 16 blocks x 2 axes x 48 bytes = 96 x 16-byte pieces.
+    // chunk ch is multiplied: 16 blocks x 2 axes x 64 bytes = 128 x 16-byte pieces.
     auto fetch_recs = [&](int ch, int buf) {
-        if (tid < 2 * CKC * 3) {
-            const int axis = tid / (CKC * 3), r = tid % (CKC * 3);
-            const int k = r / 3, piece = r % 3;
+        if (tid < 2 * CKC * 4) {
+            const int axis = tid / (CKC * 4), r = tid % (CKC * 4);
+            const int k = r / 4, piece = r % 4;
             const int b = b0 + ch * CKC + k;
             if (b < b1) {
                 const AxisRec *src = (axis == 0 ? xr : yr) + b;

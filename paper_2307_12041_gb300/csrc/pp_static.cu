@@ -11,7 +11,7 @@
 // here.
 //
 // The array below is reserved on every GPU that loads the library, from load
-// until process exit (PP_STATIC_SCRATCH_BYTES, about 3.8 MB).  All calls share
+// until process exit (PP_STATIC_SCRATCH_BYTES, about 5 MB).  All calls share
 // it: the contents of the previous call remain, so every part that must start
 // at zero (the FP64 sums and *e_total) is cleared on the stream by the first
 // kernel of each call, and two calls whose kernels overlap on the GPU (for

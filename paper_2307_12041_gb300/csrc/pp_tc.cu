@@ -1,0 +1,874 @@
+// Tensor-core path (PP_TF32, PP_BF16X3) for sm_103a: tcgen05 MMAs, TMEM
+// accumulators, TMA-staged coefficient tiles, basis tiles generated in shared
+// memory by dedicated warps.
+//
+//   tc_coeff_kernel   St = Xt^T Yt (contraction over blocks).  CTA tile 256 (u) x
+//                     256 (v) as two M=128, N=256 accumulators that share the Yt
+//                     operand; persistent over (tile, block slice) units; each
+//                     unit's FP32 sum is written as a partial, the slices are
+//                     summed in FP64 by the finish kernel.
+//   tc_finish_kernel  a = G o (f St g) and K = f a g in the operand precision,
+//                     laid out so that one 3-D TMA box is one pipeline stage.
+//   tc_energy_kernel  T = Xt K and T' = Xh K for 128 blocks per CTA (two
+//                     accumulators sharing the TMA-staged K tile), then row dots
+//                     with Yt and Yh in the epilogue warps.
+//
+// Operand layouts (no swizzle, core matrix = 8 rows x 16 bytes, LBO = K-direction
+// core stride, SBO = M/N-direction core stride):
+//   TF32  operands are K-major (MN-major TF32 is not used).
+//   BF16  coefficient operands are MN-major (modes contiguous), energy operands
+//         K-major.
+// BF16x3 splits every operand into hi = bf16(x), lo = bf16(x - hi) and sums the
+// three products hi*hi + hi*lo + lo*hi in the FP32 accumulator.
+//
+// Every wait is bounded: on a timeout the kernel raises bit 0 of the device
+// status word, stops issuing work, waits (bounded) for its own MMAs to drain,
+// frees its TMEM and returns.
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include <cmath>
+#include <cstdio>
+
+#include "pp_device.cuh"
+#include "pp_internal.h"
+#include "pp_tc.cuh"
+
+namespace pp {
+
+using namespace tc;
+
+namespace {
+
+constexpr uint64_t kWaitLimit = 4000000000ull;   // ns an mbarrier wait may take before giving up
+
+__device__ __forceinline__ void raise_timeout(unsigned *status, volatile int *abort_flag) {
+    *abort_flag = 1;
+    if (status) atomicOr(status, 1u);
+}
+
+// Split x into bf16 hi (nearest) and lo = bf16(x - hi).
+__device__ __forceinline__ void split_bf16(float x, __nv_bfloat16 &hi, __nv_bfloat16 &lo) {
+    hi = __float2bfloat16_rn(x);
+    lo = __float2bfloat16_rn(x - __bfloat162float(hi));
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(__nv_bfloat16 a, __nv_bfloat16 b) {
+    return (uint32_t)__bfloat16_as_ushort(a) | ((uint32_t)__bfloat16_as_ushort(b) << 16);
+}
+
+// ===========================================================================
+// Coefficient contraction
+// ===========================================================================
+constexpr int C_TILE = 256;                 // u and v edge of a CTA tile
+constexpr int C_KB = 32;                    // blocks per pipeline stage
+constexpr int C_STAGES = 3;
+constexpr int C_STAGE_BYTES = 65536;        // A 32 KB + B 32 KB (both precisions)
+constexpr int C_GEN_WARPS = 8;
+constexpr int C_EPI_WARPS = 4;
+constexpr int C_THREADS = 32 * (1 + C_EPI_WARPS + C_GEN_WARPS);
+
+struct CoeffBars {
+    uint64_t full[C_STAGES];
+    uint64_t empty[C_STAGES];
+    uint64_t acc_full;
+    uint64_t acc_empty;
+    uint64_t drain;
+    uint32_t tmem_slot;
+    int abort_flag;
+};
+constexpr int C_SMEM = C_STAGES * C_STAGE_BYTES + 1024 + (int)sizeof(CoeffBars);
+
+struct CoeffArgs {
+    const AxisRec *xr, *yr;
+    int n, tiles_v, slices, slice_len, units;
+    int Mxc, Myc;         // padded (multiple of 256) extents of the partial tiles
+    float *part;          // [slices][Mxc][Myc]
+    unsigned *status;
+};
+
+// TF32 generator: K-major rows of 4 consecutive blocks.  Thread (k4, r, half)
+// writes operand rows R = half*128 + r + 8j (j = 0..15), blocks 4k4..4k4+3.
+__device__ __forceinline__ void gen_coeff_tf32(unsigned char *op, const AxisRec *recs, int blk0,
+                                               int blk_end, int mode_base, int g) {
+    const int half = (g >> 6) & 1, k4 = (g & 63) >> 3, r = g & 7;
+    const int m0 = mode_base + half * 128 + r;
+    float2 zs[4], zt[4], es[4], et[4];
+    float v0[4];
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+        const int blk = blk0 + 4 * k4 + b;
+        if (blk < blk_end) {
+            const AxisRec &R = recs[blk];
+            zs[b] = phase_cs((unsigned long long)m0, R.s);
+            zt[b] = phase_cs((unsigned long long)m0, R.t);
+            zt[b].x *= R.c;
+            zt[b].y *= R.c;
+            es[b] = R.es8;
+            et[b] = R.et8;
+            v0[b] = R.v0;
+        } else {
+            zs[b] = make_float2(0.f, 0.f);
+            zt[b] = make_float2(0.f, 0.f);
+            es[b] = et[b] = make_float2(1.f, 0.f);
+            v0[b] = 0.f;
+        }
+    }
+    unsigned char *base = op + (half * 16) * 1024 + k4 * 128 + r * 16;
+#pragma unroll 4
+    for (int j = 0; j < 16; ++j) {
+        float v[4];
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            v[b] = to_tf32(zs[b].x * zt[b].y);
+            zs[b] = rot(zs[b], es[b]);
+            zt[b] = rot(zt[b], et[b]);
+        }
+        if (m0 == 0 && j == 0) {
+#pragma unroll
+            for (int b = 0; b < 4; ++b) v[b] = to_tf32(v0[b]);
+        }
+        *reinterpret_cast<float4 *>(base + j * 1024) = make_float4(v[0], v[1], v[2], v[3]);
+    }
+}
+
+// BF16 generator: MN-major rows of 8 consecutive modes of one block.  Thread
+// (block k, lane group lg) writes mode groups lg + 4q (q = 0..7), 8 modes each,
+// hi and lo parts.  Element (mode R, block k) at (R/8)*128 + (k/8)*4096 + (k%8)*16.
+__device__ __forceinline__ void gen_coeff_bf16(unsigned char *op_hi, unsigned char *op_lo,
+                                               const AxisRec *recs, int blk0, int blk_end,
+                                               int mode_base, int g) {
+    const int lane = g & 31, wq = (g >> 5) & 3;
+    const int k = (lane & 7) + 8 * wq;
+    const int lg = lane >> 3;
+    const int blk = blk0 + k;
+    float2 zs, zt, es, et, es32, et32;
+    float v0;
+    if (blk < blk_end) {
+        const AxisRec &R = recs[blk];
+        const int m0 = mode_base + 8 * lg;
+        zs = phase_cs((unsigned long long)m0, R.s);
+        zt = phase_cs((unsigned long long)m0, R.t);
+        zt.x *= R.c;
+        zt.y *= R.c;
+        es = R.es;
+        et = R.et;
+        const float2 s16 = rot(R.es8, R.es8), t16 = rot(R.et8, R.et8);
+        es32 = rot(s16, s16);
+        et32 = rot(t16, t16);
+        v0 = R.v0;
+    } else {
+        zs = zt = make_float2(0.f, 0.f);
+        es = et = es32 = et32 = make_float2(1.f, 0.f);
+        v0 = 0.f;
+    }
+    const size_t koff = (size_t)(k >> 3) * 4096 + (k & 7) * 16;
+#pragma unroll 2
+    for (int q = 0; q < 8; ++q) {
+        const int grp = lg + 4 * q;
+        float2 a = zs, b = zt;
+        uint32_t hi[4], lo[4];
+#pragma unroll
+        for (int j = 0; j < 8; j += 2) {
+            float v[2];
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                v[e] = a.x * b.y;
+                a = rot(a, es);
+                b = rot(b, et);
+            }
+            if (mode_base + 8 * grp + j == 0) v[0] = v0;
+            __nv_bfloat16 h0, l0, h1, l1;
+            split_bf16(v[0], h0, l0);
+            split_bf16(v[1], h1, l1);
+            hi[j >> 1] = pack_bf16(h0, h1);
+            lo[j >> 1] = pack_bf16(l0, l1);
+        }
+        const size_t off = (size_t)grp * 128 + koff;
+        *reinterpret_cast<uint4 *>(op_hi + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+        *reinterpret_cast<uint4 *>(op_lo + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+        zs = rot(zs, es32);
+        zt = rot(zt, et32);
+    }
+}
+
+template <int PREC>
+__global__ void __launch_bounds__(C_THREADS, 1) tc_coeff_kernel(const CoeffArgs args) {
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char *smem = reinterpret_cast<unsigned char *>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    CoeffBars &bars = *reinterpret_cast<CoeffBars *>(smem + C_STAGES * C_STAGE_BYTES);
+    volatile int *abort_flag = &bars.abort_flag;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < C_STAGES; ++s) {
+            mbar_init(&bars.full[s], C_GEN_WARPS * 32);
+            mbar_init(&bars.empty[s], 1);
+        }
+        mbar_init(&bars.acc_full, 1);
+        mbar_init(&bars.acc_empty, C_EPI_WARPS * 32);
+        mbar_init(&bars.drain, 1);
+        bars.abort_flag = 0;
+        mbar_fence_init();
+    }
+    if (warp == 0) {
+        tmem_alloc(&bars.tmem_slot, 512);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = bars.tmem_slot;
+
+    const int tiles_v = args.tiles_v;
+    if (warp == 0) {
+        // ---------------- MMA issuer ----------------
+        if (lane == 0) {
+            constexpr bool BF = PREC == 2;
+            const uint32_t idesc = instr_desc(BF ? kFmtBF16 : kFmtTF32, 128, 256, BF, BF);
+            uint32_t it = 0, uc = 0;
+            for (int unit = blockIdx.x; unit < args.units && !*abort_flag; unit += gridDim.x, ++uc) {
+                const int slice = unit % args.slices;
+                const int b0 = slice * args.slice_len;
+                const int b1 = min(args.n, b0 + args.slice_len);
+                const int nst = (b1 - b0 + C_KB - 1) / C_KB;
+                if (uc > 0 && !mbar_wait(&bars.acc_empty, (uc - 1) & 1, kWaitLimit, abort_flag)) {
+                    raise_timeout(args.status, abort_flag);
+                    break;
+                }
+                tc_fence_after();
+                for (int st = 0; st < nst; ++st, ++it) {
+                    const int s = it % C_STAGES;
+                    if (!mbar_wait(&bars.full[s], (it / C_STAGES) & 1, kWaitLimit, abort_flag)) {
+                        raise_timeout(args.status, abort_flag);
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t sb = smem_u32(smem + s * C_STAGE_BYTES);
+                    if (!BF) {
+                        // A: 256 rows x 32 blocks tf32, cores (row/8, blk/4): LBO 128, SBO 1024
+                        const uint32_t A = sb, B = sb + 32768;
+#pragma unroll
+                        for (int kk = 0; kk < 4; ++kk) {
+                            const uint64_t bd = smem_desc(B + kk * 256, 128, 1024);
+#pragma unroll
+                            for (int acc = 0; acc < 2; ++acc) {
+                                const uint64_t ad = smem_desc(A + acc * 16384 + kk * 256, 128, 1024);
+                                mma_tf32(tmem + acc * 256, ad, bd, idesc, st > 0 || kk > 0);
+                            }
+                        }
+                    } else {
+                        // MN-major bf16: element (mode R, blk k) at (R/8)*128 + (k/8)*4096
+                        // + (k%8)*16: SBO (mode groups) 128, LBO (block groups) 4096
+                        const uint32_t Ah = sb, Al = sb + 16384, Bh = sb + 32768, Bl = sb + 49152;
+#pragma unroll
+                        for (int kk = 0; kk < 2; ++kk) {
+                            const uint32_t ko = kk * 8192;
+                            const uint64_t bh = smem_desc(Bh + ko, 4096, 128);
+                            const uint64_t bl = smem_desc(Bl + ko, 4096, 128);
+#pragma unroll
+                            for (int acc = 0; acc < 2; ++acc) {
+                                const uint32_t mo = acc * 2048;
+                                const uint64_t ah = smem_desc(Ah + mo + ko, 4096, 128);
+                                const uint64_t al = smem_desc(Al + mo + ko, 4096, 128);
+                                const bool accum = st > 0 || kk > 0;
+                                mma_bf16(tmem + acc * 256, al, bh, idesc, accum);
+                                mma_bf16(tmem + acc * 256, ah, bl, idesc, true);
+                                mma_bf16(tmem + acc * 256, ah, bh, idesc, true);
+                            }
+                        }
+                    }
+                    mma_commit(&bars.empty[s]);
+                }
+                if (*abort_flag) break;
+                mma_commit(&bars.acc_full);
+            }
+            // all MMAs issued by this thread complete before the TMEM is freed
+            mma_commit(&bars.drain);
+            if (!mbar_wait(&bars.drain, 0, kWaitLimit, nullptr)) raise_timeout(args.status, abort_flag);
+        }
+        __syncwarp();
+    } else if (warp <= C_EPI_WARPS) {
+        // ---------------- epilogue: TMEM -> FP32 partial tile ----------------
+        const int quarter = warp & 3;
+        const int row = quarter * 32 + lane;
+        uint32_t uc = 0;
+        for (int unit = blockIdx.x; unit < args.units; unit += gridDim.x, ++uc) {
+            if (*abort_flag) break;
+            const int tile = unit / args.slices, slice = unit % args.slices;
+            const int tu = tile / tiles_v, tv = tile % tiles_v;
+            if (!mbar_wait(&bars.acc_full, uc & 1, kWaitLimit, abort_flag)) {
+                raise_timeout(args.status, abort_flag);
+                break;
+            }
+            tc_fence_after();
+#pragma unroll 1
+            for (int acc = 0; acc < 2; ++acc) {
+                const int u = tu * C_TILE + acc * 128 + row;
+                float *dst = args.part + ((size_t)slice * args.Mxc + u) * args.Myc + tv * C_TILE;
+#pragma unroll 1
+                for (int c = 0; c < 256; c += 16) {
+                    float v[16];
+                    tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + acc * 256 + c, v);
+                    tmem_ld_wait();
+#pragma unroll
+                    for (int j = 0; j < 16; j += 4)
+                        *reinterpret_cast<float4 *>(dst + c + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+                }
+            }
+            tc_fence_before();
+            mbar_arrive(&bars.acc_empty);
+        }
+    } else {
+        // ---------------- basis generators ----------------
+        const int g = threadIdx.x - 32 * (1 + C_EPI_WARPS);    // 0..255
+        const int which = g >> 7;                              // 0: Xt (A), 1: Yt (B)
+        const int gg = g & 127;
+        uint32_t it = 0;
+        for (int unit = blockIdx.x; unit < args.units; unit += gridDim.x) {
+            const int tile = unit / args.slices, slice = unit % args.slices;
+            const int tu = tile / tiles_v, tv = tile % tiles_v;
+            const int b0 = slice * args.slice_len;
+            const int b1 = min(args.n, b0 + args.slice_len);
+            const int nst = (b1 - b0 + C_KB - 1) / C_KB;
+            for (int st = 0; st < nst; ++st, ++it) {
+                if (*abort_flag) break;
+                const int s = it % C_STAGES;
+                if (it >= C_STAGES &&
+                    !mbar_wait(&bars.empty[s], ((it / C_STAGES) - 1) & 1, kWaitLimit, abort_flag)) {
+                    raise_timeout(args.status, abort_flag);
+                    break;
+                }
+                unsigned char *sb = smem + s * C_STAGE_BYTES;
+                const int blk0 = b0 + st * C_KB;
+                if (PREC == 1) {
+                    gen_coeff_tf32(sb + which * 32768, which ? args.yr : args.xr, blk0, b1,
+                                   (which ? tv : tu) * C_TILE, gg);
+                } else {
+                    gen_coeff_bf16(sb + which * 32768, sb + which * 32768 + 16384,
+                                   which ? args.yr : args.xr, blk0, b1, (which ? tv : tu) * C_TILE, gg);
+                }
+                fence_proxy_async_smem();
+                mbar_arrive(&bars.full[s]);
+            }
+            if (*abort_flag) break;
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        tmem_dealloc(tmem, 512);
+    }
+}
+
+// ===========================================================================
+// Finish: FP64 sum of the slice partials -> a, K in the energy operand layout
+// ===========================================================================
+template <int PREC>
+__global__ void tc_finish_kernel(const float *__restrict__ part, int slices, int Mxc, int Myc,
+                                 const float *__restrict__ a_in, float *__restrict__ a_out,
+                                 void *__restrict__ Kop, void *__restrict__ Klo, int Mx, int My,
+                                 int Mxe, int Mye, double W, double H) {
+    const double PI = 3.141592653589793;
+    const size_t total = (size_t)Mxe * Mye;
+    for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (size_t)gridDim.x * blockDim.x) {
+        const int u = (int)(idx / Mye), v = (int)(idx % Mye);
+        double kv = 0.0;
+        if (u < Mx && v < My) {
+            const double f = 2.0 * W / (PI * (u > 0 ? u : 1));
+            const double g = 2.0 * H / (PI * (v > 0 ? v : 1));
+            double av;
+            if (a_in) {
+                av = (double)a_in[(size_t)u * My + v];
+            } else {
+                double S = 0.0;
+                for (int s = 0; s < slices; ++s) S += (double)part[((size_t)s * Mxc + u) * Myc + v];
+                const double ku = u * PI / W, lv = v * PI / H;
+                const double eps = (u ? 2.0 : 1.0) * (v ? 2.0 : 1.0);
+                const double G = (u == 0 && v == 0) ? 0.0 : eps / (W * H * (ku * ku + lv * lv));
+                av = G * f * g * S;
+                if (a_out) a_out[(size_t)u * My + v] = (float)av;
+            }
+            kv = f * av * g;
+        }
+        const int vb = v >> 8, vi = v & 255;
+        if (PREC == 1) {
+            const size_t off = (((size_t)vb * (Mxe / 4) + (u >> 2)) * 256 + vi) * 4 + (u & 3);
+            reinterpret_cast<float *>(Kop)[off] = to_tf32((float)kv);
+        } else {
+            const size_t off = (((size_t)vb * (Mxe / 8) + (u >> 3)) * 256 + vi) * 8 + (u & 7);
+            const float k32 = (float)kv;
+            __nv_bfloat16 hi = __float2bfloat16_rn(k32);
+            // lo from the FP64 value: K = hi + lo to ~2^-17 relative
+            __nv_bfloat16 lo = __float2bfloat16_rn((float)(kv - (double)__bfloat162float(hi)));
+            reinterpret_cast<__nv_bfloat16 *>(Kop)[off] = hi;
+            reinterpret_cast<__nv_bfloat16 *>(Klo)[off] = lo;
+        }
+    }
+}
+
+// ===========================================================================
+// Energy and gradient
+// ===========================================================================
+constexpr int E_ROWS = 128;                 // blocks per CTA
+constexpr int E_VC = 256;                   // v columns per accumulator pass
+constexpr int E_KS = 32;                    // u per pipeline stage
+constexpr int E_STAGES = 3;
+constexpr int E_STAGE_BYTES = 65536;        // A (Xt, Xh) 32 KB + B (K) 32 KB
+constexpr int E_GEN_WARPS = 8;
+constexpr int E_EPI_WARPS = 4;
+constexpr int E_THREADS = 32 * (2 + E_EPI_WARPS + E_GEN_WARPS);
+
+struct EnergyBars {
+    uint64_t full[E_STAGES];
+    uint64_t empty[E_STAGES];
+    uint64_t acc_full;
+    uint64_t acc_empty;
+    uint64_t drain;
+    uint32_t tmem_slot;
+    int abort_flag;
+    double esum[E_EPI_WARPS];
+};
+constexpr int E_SMEM = E_STAGES * E_STAGE_BYTES + 1024 + (int)sizeof(EnergyBars);
+
+struct EnergyArgs {
+    const AxisRec *xr, *yr;
+    int n, Mx, My, Mxe, Mye;
+    float *e_block, *gx, *gy;
+    double *e_total;
+    unsigned *status;
+};
+
+// Energy-operand generator (K-major, one block per thread, 16 consecutive u):
+// Xt and Xh for SAMPLE 0 (rectangle) or 1 (centre).
+template <int PREC, int SAMPLE>
+__device__ __forceinline__ void gen_energy(unsigned char *sb, const AxisRec &R, bool valid, int row,
+                                           int u0) {
+    float xt[16], xh[16];
+    if (valid) {
+        float2 zs = phase_cs((unsigned long long)u0, R.s);
+        if (SAMPLE == 0) {
+            float2 zt = phase_cs((unsigned long long)u0, R.t);
+            zt.x *= R.c;
+            zt.y *= R.c;
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const float ku = (float)(u0 + j) * R.inv_l;
+                xt[j] = zs.x * zt.y;
+                xh[j] = -ku * (zs.y * zt.y);
+                zs = rot(zs, R.es);
+                zt = rot(zt, R.et);
+            }
+            if (u0 == 0) xt[0] = R.v0;
+        } else {
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const int m = u0 + j;
+                const float ku = (float)m * R.inv_l;
+                const float inv_f = 0.5f * (float)(m > 0 ? m : 1) * R.inv_l;
+                xt[j] = R.q * zs.x * inv_f;
+                xh[j] = -R.q * ku * zs.y * inv_f;
+                zs = rot(zs, R.es);
+            }
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) xt[j] = xh[j] = 0.f;
+    }
+    const int half = (u0 / 16) & 1;   // which 16 of the stage's 32 u
+    if (PREC == 1) {
+        // [128 rows x 32 u] tf32 K-major: core (row/8, u/4) at (row/8)*1024 + (u/4)*128
+        unsigned char *A = sb, *Ah = sb + 16384;
+        const size_t rbase = (size_t)(row >> 3) * 1024 + (row & 7) * 16;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const size_t off = rbase + (size_t)(half * 4 + c) * 128;
+            *reinterpret_cast<float4 *>(A + off) = make_float4(to_tf32(xt[4 * c]), to_tf32(xt[4 * c + 1]),
+                                                               to_tf32(xt[4 * c + 2]), to_tf32(xt[4 * c + 3]));
+            *reinterpret_cast<float4 *>(Ah + off) = make_float4(to_tf32(xh[4 * c]), to_tf32(xh[4 * c + 1]),
+                                                                to_tf32(xh[4 * c + 2]), to_tf32(xh[4 * c + 3]));
+        }
+    } else {
+        // [128 rows x 32 u] bf16 K-major: core (row/8, u/8) at (row/8)*512 + (u/8)*128;
+        // regions: Xt hi, Xt lo, Xh hi, Xh lo (8 KB each)
+        const size_t rbase = (size_t)(row >> 3) * 512 + (row & 7) * 16;
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            uint32_t th[4], tl[4], hh[4], hl[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                __nv_bfloat16 a0, a1, b0, b1, c0, c1, d0, d1;
+                split_bf16(xt[8 * c + 2 * j], a0, b0);
+                split_bf16(xt[8 * c + 2 * j + 1], a1, b1);
+                split_bf16(xh[8 * c + 2 * j], c0, d0);
+                split_bf16(xh[8 * c + 2 * j + 1], c1, d1);
+                th[j] = pack_bf16(a0, a1);
+                tl[j] = pack_bf16(b0, b1);
+                hh[j] = pack_bf16(c0, c1);
+                hl[j] = pack_bf16(d0, d1);
+            }
+            const size_t off = rbase + (size_t)(half * 2 + c) * 128;
+            *reinterpret_cast<uint4 *>(sb + off) = make_uint4(th[0], th[1], th[2], th[3]);
+            *reinterpret_cast<uint4 *>(sb + 8192 + off) = make_uint4(tl[0], tl[1], tl[2], tl[3]);
+            *reinterpret_cast<uint4 *>(sb + 16384 + off) = make_uint4(hh[0], hh[1], hh[2], hh[3]);
+            *reinterpret_cast<uint4 *>(sb + 24576 + off) = make_uint4(hl[0], hl[1], hl[2], hl[3]);
+        }
+    }
+}
+
+template <int PREC, int SAMPLE>
+__global__ void __launch_bounds__(E_THREADS, 1)
+tc_energy_kernel(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ CUtensorMap tm_lo,
+                 const EnergyArgs args) {
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char *smem = reinterpret_cast<unsigned char *>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    EnergyBars &bars = *reinterpret_cast<EnergyBars *>(smem + E_STAGES * E_STAGE_BYTES);
+    volatile int *abort_flag = &bars.abort_flag;
+    constexpr bool BF = PREC == 2;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int blk0 = blockIdx.x * E_ROWS;
+    const int nvc = args.Mye / E_VC;
+    const int nks = args.Mxe / E_KS;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < E_STAGES; ++s) {
+            mbar_init(&bars.full[s], E_GEN_WARPS * 32 + 1);
+            mbar_init(&bars.empty[s], 1);
+        }
+        mbar_init(&bars.acc_full, 1);
+        mbar_init(&bars.acc_empty, E_EPI_WARPS * 32);
+        mbar_init(&bars.drain, 1);
+        bars.abort_flag = 0;
+        mbar_fence_init();
+    }
+    if (warp == 0) {
+        tmem_alloc(&bars.tmem_slot, 512);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = bars.tmem_slot;
+
+    if (warp == 0) {
+        // ---------------- MMA issuer ----------------
+        if (lane == 0) {
+            const uint32_t idesc = instr_desc(BF ? kFmtBF16 : kFmtTF32, 128, 256, false, false);
+            int it = 0;
+            for (int vc = 0; vc < nvc && !*abort_flag; ++vc) {
+                if (vc > 0 && !mbar_wait(&bars.acc_empty, (vc - 1) & 1, kWaitLimit, abort_flag)) {
+                    raise_timeout(args.status, abort_flag);
+                    break;
+                }
+                tc_fence_after();
+                for (int ks = 0; ks < nks; ++ks, ++it) {
+                    const int s = it % E_STAGES;
+                    if (!mbar_wait(&bars.full[s], (it / E_STAGES) & 1, kWaitLimit, abort_flag)) {
+                        raise_timeout(args.status, abort_flag);
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t sb = smem_u32(smem + s * E_STAGE_BYTES);
+                    if (!BF) {
+                        const uint32_t At = sb, Ah = sb + 16384, B = sb + 32768;
+#pragma unroll
+                        for (int kk = 0; kk < 4; ++kk) {
+                            // A: LBO 128 (u cores), SBO 1024 (row groups); B: [u/4][256 v][4]
+                            const uint64_t bd = smem_desc(B + kk * 8192, 4096, 128);
+                            const bool accum = ks > 0 || kk > 0;
+                            mma_tf32(tmem, smem_desc(At + kk * 256, 128, 1024), bd, idesc, accum);
+                            mma_tf32(tmem + 256, smem_desc(Ah + kk * 256, 128, 1024), bd, idesc, accum);
+                        }
+                    } else {
+                        const uint32_t Th = sb, Tl = sb + 8192, Hh = sb + 16384, Hl = sb + 24576;
+                        const uint32_t Bh = sb + 32768, Bl = sb + 49152;
+#pragma unroll
+                        for (int kk = 0; kk < 2; ++kk) {
+                            // A: LBO 128, SBO 512; B: [u/8][256 v][8]: LBO 4096, SBO 128
+                            const uint64_t bh = smem_desc(Bh + kk * 8192, 4096, 128);
+                            const uint64_t bl = smem_desc(Bl + kk * 8192, 4096, 128);
+                            const bool accum = ks > 0 || kk > 0;
+                            const uint32_t ao = kk * 256;
+                            mma_bf16(tmem, smem_desc(Tl + ao, 128, 512), bh, idesc, accum);
+                            mma_bf16(tmem, smem_desc(Th + ao, 128, 512), bl, idesc, true);
+                            mma_bf16(tmem, smem_desc(Th + ao, 128, 512), bh, idesc, true);
+                            mma_bf16(tmem + 256, smem_desc(Hl + ao, 128, 512), bh, idesc, accum);
+                            mma_bf16(tmem + 256, smem_desc(Hh + ao, 128, 512), bl, idesc, true);
+                            mma_bf16(tmem + 256, smem_desc(Hh + ao, 128, 512), bh, idesc, true);
+                        }
+                    }
+                    mma_commit(&bars.empty[s]);
+                }
+                if (*abort_flag) break;
+                mma_commit(&bars.acc_full);
+            }
+            mma_commit(&bars.drain);
+            if (!mbar_wait(&bars.drain, 0, kWaitLimit, nullptr)) raise_timeout(args.status, abort_flag);
+        }
+        __syncwarp();
+    } else if (warp == 1) {
+        // ---------------- TMA producer: K tiles ----------------
+        if (lane == 0) {
+            constexpr int T = BF ? 8 : 4;                 // u per 16-byte core row
+            const uint32_t bytes = BF ? 2 * 16384 : 32768;
+            int it = 0;
+            for (int vc = 0; vc < nvc; ++vc) {
+                for (int ks = 0; ks < nks; ++ks, ++it) {
+                    if (*abort_flag) break;
+                    const int s = it % E_STAGES;
+                    if (it >= E_STAGES &&
+                        !mbar_wait(&bars.empty[s], ((it / E_STAGES) - 1) & 1, kWaitLimit, abort_flag)) {
+                        raise_timeout(args.status, abort_flag);
+                        break;
+                    }
+                    unsigned char *sb = smem + s * E_STAGE_BYTES + 32768;
+                    const int z = vc * (args.Mxe / T) + ks * (E_KS / T);
+                    mbar_arrive_expect_tx(&bars.full[s], bytes);
+                    tma_load_3d(sb, &tm_hi, 0, 0, z, &bars.full[s]);
+                    if (BF) tma_load_3d(sb + 16384, &tm_lo, 0, 0, z, &bars.full[s]);
+                }
+                if (*abort_flag) break;
+            }
+        }
+        __syncwarp();
+    } else if (warp < 2 + E_EPI_WARPS) {
+        // ---------------- epilogue: row dots with Yt, Yh ----------------
+        const int quarter = warp & 3;
+        const int row = quarter * 32 + lane;
+        const int b = blk0 + row;
+        const bool valid = b < args.n;
+        AxisRec Ry;
+        if (valid) Ry = args.yr[b];
+        float eN = 0.f, eX = 0.f, eY = 0.f;
+        for (int vc = 0; vc < nvc; ++vc) {
+            if (*abort_flag) break;
+            if (!mbar_wait(&bars.acc_full, vc & 1, kWaitLimit, abort_flag)) {
+                raise_timeout(args.status, abort_flag);
+                break;
+            }
+            tc_fence_after();
+#pragma unroll 1
+            for (int c = 0; c < E_VC; c += 32) {
+                float t[32], tp[32];
+                const uint32_t ta = tmem + ((uint32_t)(quarter * 32) << 16) + c;
+                tmem_ld16(ta, t);
+                tmem_ld16(ta + 16, t + 16);
+                tmem_ld16(ta + 256, tp);
+                tmem_ld16(ta + 256 + 16, tp + 16);
+                tmem_ld_wait();
+                if (!valid) continue;
+                const int v0 = vc * E_VC + c;
+                float2 zs = phase_cs((unsigned long long)v0, Ry.s);
+                float2 zt = make_float2(0.f, 0.f);
+                if (SAMPLE == 0) zt = phase_cs((unsigned long long)v0, Ry.t);
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                    const int v = v0 + j;
+                    const float lv = (float)v * Ry.inv_l;
+                    float yt, yh;
+                    if (SAMPLE == 0) {
+                        yt = (v == 0) ? Ry.v0 : zs.x * zt.y;
+                        yh = -lv * (zs.y * zt.y);
+                        zt = rot(zt, Ry.et);
+                    } else {
+                        const float inv_g = 0.5f * (float)(v > 0 ? v : 1) * Ry.inv_l;
+                        yt = zs.x * inv_g;
+                        yh = -lv * zs.y * inv_g;
+                    }
+                    zs = rot(zs, Ry.es);
+                    eN = fmaf(t[j], yt, eN);
+                    eY = fmaf(t[j], yh, eY);
+                    eX = fmaf(tp[j], yt, eX);
+                }
+            }
+            tc_fence_before();
+            mbar_arrive(&bars.acc_empty);
+        }
+        if (valid && !*abort_flag) {
+            if (args.e_block) args.e_block[b] = eN;
+            if (args.gx) args.gx[b] = eX;
+            if (args.gy) args.gy[b] = eY;
+        }
+        double es = valid ? (double)eN : 0.0;
+#pragma unroll
+        for (int off = 16; off >= 1; off >>= 1) es += __shfl_xor_sync(0xffffffffu, es, off);
+        if (lane == 0 && args.e_total && !*abort_flag) atomicAdd(args.e_total, 0.5 * es);
+    } else {
+        // ---------------- basis generators: Xt, Xh ----------------
+        const int g = threadIdx.x - 32 * (2 + E_EPI_WARPS);   // 0..255
+        const int row = g & 127, hh = g >> 7;
+        const int b = blk0 + row;
+        const bool valid = b < args.n;
+        AxisRec Rx;
+        if (valid) Rx = args.xr[b];
+        int it = 0;
+        for (int vc = 0; vc < nvc; ++vc) {
+            for (int ks = 0; ks < nks; ++ks, ++it) {
+                if (*abort_flag) break;
+                const int s = it % E_STAGES;
+                if (it >= E_STAGES &&
+                    !mbar_wait(&bars.empty[s], ((it / E_STAGES) - 1) & 1, kWaitLimit, abort_flag)) {
+                    raise_timeout(args.status, abort_flag);
+                    break;
+                }
+                gen_energy<PREC, SAMPLE>(smem + s * E_STAGE_BYTES, Rx, valid, row, ks * E_KS + hh * 16);
+                fence_proxy_async_smem();
+                mbar_arrive(&bars.full[s]);
+            }
+            if (*abort_flag) break;
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        tmem_dealloc(tmem, 512);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                  const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                  const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+    static EncodeTiledFn fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (EncodeTiledFn)p;
+        else
+            cudaGetLastError();
+    }
+    return fn;
+}
+
+// 3-D map over the tiled energy operand: (u within a core row, v within a 256
+// block, (v block, u core group)), one box = one pipeline stage (32 u x 256 v).
+cudaError_t make_kmap(CUtensorMap *map, void *base, bool bf16, int Mxe, int Mye) {
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return cudaErrorNotSupported;
+    const int T = bf16 ? 8 : 4;
+    cuuint64_t dims[3] = {(cuuint64_t)T, 256, (cuuint64_t)(Mye / 256) * (Mxe / T)};
+    cuuint64_t strides[2] = {16, 4096};
+    cuuint32_t box[3] = {(cuuint32_t)T, 256, (cuuint32_t)(E_KS / T)};
+    cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = fn(map, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base,
+                    dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+}  // namespace
+
+TcPlan tc_plan(int n, int Mx, int My) {
+    TcPlan p{};
+    p.Mxc = round_up(Mx, C_TILE);
+    p.Myc = round_up(My, C_TILE);
+    p.Mxe = round_up(Mx, E_KS);
+    p.Mye = round_up(My, E_VC);
+    const int tiles = (p.Mxc / C_TILE) * (p.Myc / C_TILE);
+    int slices = (2 * kPlanSMs + tiles - 1) / tiles;
+    const int max_slices = (n + 511) / 512;
+    if (slices > max_slices) slices = max_slices;
+    if (slices < 1) slices = 1;
+    p.slice_len = round_up((n + slices - 1) / slices > 0 ? (n + slices - 1) / slices : 1, C_KB);
+    p.slices = (n + p.slice_len - 1) / p.slice_len;
+    if (p.slices < 1) p.slices = 1;
+    p.tiles = tiles;
+    return p;
+}
+
+cudaError_t launch_coeff_tc(const Launch &L, int prec, const TcPlan &P, float *part) {
+    if (L.n == 0) return cudaSuccess;
+    CoeffArgs a{};
+    a.xr = L.xrec;
+    a.yr = L.yrec;
+    a.n = L.n;
+    a.tiles_v = P.Myc / C_TILE;
+    a.slices = P.slices;
+    a.slice_len = P.slice_len;
+    a.units = P.tiles * P.slices;
+    a.Mxc = P.Mxc;
+    a.Myc = P.Myc;
+    a.part = part;
+    a.status = L.status;
+    const int grid = a.units < L.sm_count ? a.units : L.sm_count;
+    cudaError_t e;
+    if (prec == 1) {
+        e = cudaFuncSetAttribute(tc_coeff_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, C_SMEM);
+        if (e != cudaSuccess) return e;
+        tc_coeff_kernel<1><<<grid, C_THREADS, C_SMEM, L.stream>>>(a);
+    } else {
+        e = cudaFuncSetAttribute(tc_coeff_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, C_SMEM);
+        if (e != cudaSuccess) return e;
+        tc_coeff_kernel<2><<<grid, C_THREADS, C_SMEM, L.stream>>>(a);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finish_tc(const Launch &L, int prec, const TcPlan &P, const float *part,
+                             const float *a_in, float *a_out, void *Khi, void *Klo) {
+    const size_t total = (size_t)P.Mxe * P.Mye;
+    int blocks = (int)((total + 255) / 256);
+    if (blocks > 8 * L.sm_count) blocks = 8 * L.sm_count;
+    if (blocks < 1) blocks = 1;
+    if (prec == 1)
+        tc_finish_kernel<1><<<blocks, 256, 0, L.stream>>>(part, P.slices, P.Mxc, P.Myc, a_in, a_out, Khi,
+                                                          Klo, L.Mx, L.My, P.Mxe, P.Mye, L.W, L.H);
+    else
+        tc_finish_kernel<2><<<blocks, 256, 0, L.stream>>>(part, P.slices, P.Mxc, P.Myc, a_in, a_out, Khi,
+                                                          Klo, L.Mx, L.My, P.Mxe, P.Mye, L.W, L.H);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_energy_tc(const Launch &L, int prec, int sample, const TcPlan &P, void *Khi,
+                             void *Klo, float *e_block, double *e_total, float *gx, float *gy) {
+    if (L.n == 0) return cudaSuccess;
+    CUtensorMap mh, ml;
+    const bool bf = prec == 2;
+    cudaError_t e = make_kmap(&mh, Khi, bf, P.Mxe, P.Mye);
+    if (e != cudaSuccess) return e;
+    e = make_kmap(&ml, bf ? Klo : Khi, bf, P.Mxe, P.Mye);
+    if (e != cudaSuccess) return e;
+    EnergyArgs a{};
+    a.xr = L.xrec;
+    a.yr = L.yrec;
+    a.n = L.n;
+    a.Mx = L.Mx;
+    a.My = L.My;
+    a.Mxe = P.Mxe;
+    a.Mye = P.Mye;
+    a.e_block = e_block;
+    a.gx = gx;
+    a.gy = gy;
+    a.e_total = e_total;
+    a.status = L.status;
+    const int grid = (L.n + E_ROWS - 1) / E_ROWS;
+#define PP_ELAUNCH(PR, SA)                                                                           \
+    do {                                                                                             \
+        e = cudaFuncSetAttribute(tc_energy_kernel<PR, SA>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                 E_SMEM);                                                            \
+        if (e != cudaSuccess) return e;                                                              \
+        tc_energy_kernel<PR, SA><<<grid, E_THREADS, E_SMEM, L.stream>>>(mh, ml, a);                  \
+    } while (0)
+    if (prec == 1 && sample == 0) PP_ELAUNCH(1, 0);
+    else if (prec == 1) PP_ELAUNCH(1, 1);
+    else if (sample == 0) PP_ELAUNCH(2, 0);
+    else PP_ELAUNCH(2, 1);
+#undef PP_ELAUNCH
+    return cudaGetLastError();
+}
+
+}  // namespace pp

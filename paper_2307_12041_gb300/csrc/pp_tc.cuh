@@ -45,15 +45,22 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
-// Bounded wait: returns false (and stops waiting) if the phase has not
-// completed after `limit` polls, or if *abort became non-zero.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint32_t limit,
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// Bounded wait: returns false (and stops waiting) once `limit_ns` nanoseconds have
+// passed without the phase completing, or as soon as *abort became non-zero.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint64_t limit_ns,
                                           volatile int *abort) {
-    for (uint32_t i = 0; i < limit; ++i) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = globaltimer_ns();
+    for (uint32_t i = 1;; ++i) {
         if (mbar_try_wait(bar, parity)) return true;
         if (abort && *abort) return false;
+        if ((i & 63) == 0 && globaltimer_ns() - t0 > limit_ns) return false;
     }
-    return false;
 }
 
 // ---- fences ---------------------------------------------------------------
