@@ -13,7 +13,7 @@
 #include <string>
 #include <vector>
 
-#include "../../include/pp.h"
+#include "pp.h"
 #include "pp_device.cuh"
 #include "pp_internal.h"
 

@@ -20,7 +20,7 @@
 #include <cstdint>
 #include <mutex>
 
-#include "../../include/pp.h"
+#include "pp.h"
 #include "pp_device.cuh"
 #include "pp_internal.h"
 

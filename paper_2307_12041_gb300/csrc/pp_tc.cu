@@ -66,18 +66,21 @@ constexpr int C_STAGES = 3;
 constexpr int C_STAGE_BYTES = 65536;        // A 32 KB + B 32 KB (both precisions)
 constexpr int C_GEN_WARPS = 8;
 constexpr int C_EPI_WARPS = 4;
-constexpr int C_THREADS = 32 * (1 + C_EPI_WARPS + C_GEN_WARPS);
+constexpr int C_LOADER_WARP = 1 + C_EPI_WARPS + C_GEN_WARPS;     // copies per-block records
+constexpr int C_THREADS = 32 * (C_LOADER_WARP + 1);
+constexpr int C_REC_BYTES = 2 * C_KB * (int)sizeof(AxisRec);    // x and y records of a stage
 
 struct CoeffBars {
     uint64_t full[C_STAGES];
     uint64_t empty[C_STAGES];
+    uint64_t recs_full[C_STAGES];
     uint64_t acc_full;
     uint64_t acc_empty;
     uint64_t drain;
     uint32_t tmem_slot;
     int abort_flag;
 };
-constexpr int C_SMEM = C_STAGES * C_STAGE_BYTES + 1024 + (int)sizeof(CoeffBars);
+constexpr int C_SMEM = C_STAGES * (C_STAGE_BYTES + C_REC_BYTES) + 1024 + (int)sizeof(CoeffBars);
 
 struct CoeffArgs {
     const AxisRec *xr, *yr;
@@ -88,18 +91,19 @@ struct CoeffArgs {
 };
 
 // TF32 generator: K-major rows of 4 consecutive blocks.  Thread (k4, r, half)
-// writes operand rows R = half*128 + r + 8j (j = 0..15), blocks 4k4..4k4+3.
-__device__ __forceinline__ void gen_coeff_tf32(unsigned char *op, const AxisRec *recs, int blk0,
-                                               int blk_end, int mode_base, int g) {
+// writes operand rows R = half*128 + r + 8j (j = 0..15), blocks 4k4..4k4+3 of the
+// stage (records in shared memory, `nvalid` of them valid).
+__device__ __forceinline__ void gen_coeff_tf32(unsigned char *op, const AxisRec *recs, int nvalid,
+                                               int mode_base, int g) {
     const int half = (g >> 6) & 1, k4 = (g & 63) >> 3, r = g & 7;
     const int m0 = mode_base + half * 128 + r;
     float2 zs[4], zt[4], es[4], et[4];
     float v0[4];
 #pragma unroll
     for (int b = 0; b < 4; ++b) {
-        const int blk = blk0 + 4 * k4 + b;
-        if (blk < blk_end) {
-            const AxisRec &R = recs[blk];
+        const int k = 4 * k4 + b;
+        if (k < nvalid) {
+            const AxisRec &R = recs[k];
             zs[b] = phase_cs((unsigned long long)m0, R.s);
             zt[b] = phase_cs((unsigned long long)m0, R.t);
             zt[b].x *= R.c;
@@ -136,16 +140,14 @@ __device__ __forceinline__ void gen_coeff_tf32(unsigned char *op, const AxisRec 
 // (block k, lane group lg) writes mode groups lg + 4q (q = 0..7), 8 modes each,
 // hi and lo parts.  Element (mode R, block k) at (R/8)*128 + (k/8)*4096 + (k%8)*16.
 __device__ __forceinline__ void gen_coeff_bf16(unsigned char *op_hi, unsigned char *op_lo,
-                                               const AxisRec *recs, int blk0, int blk_end,
-                                               int mode_base, int g) {
+                                               const AxisRec *recs, int nvalid, int mode_base, int g) {
     const int lane = g & 31, wq = (g >> 5) & 3;
     const int k = (lane & 7) + 8 * wq;
     const int lg = lane >> 3;
-    const int blk = blk0 + k;
     float2 zs, zt, es, et, es32, et32;
     float v0;
-    if (blk < blk_end) {
-        const AxisRec &R = recs[blk];
+    if (k < nvalid) {
+        const AxisRec &R = recs[k];
         const int m0 = mode_base + 8 * lg;
         zs = phase_cs((unsigned long long)m0, R.s);
         zt = phase_cs((unsigned long long)m0, R.t);
@@ -197,7 +199,8 @@ __global__ void __launch_bounds__(C_THREADS, 1) tc_coeff_kernel(const CoeffArgs 
     extern __shared__ unsigned char smem_raw[];
     unsigned char *smem = reinterpret_cast<unsigned char *>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-    CoeffBars &bars = *reinterpret_cast<CoeffBars *>(smem + C_STAGES * C_STAGE_BYTES);
+    unsigned char *recs_base = smem + C_STAGES * C_STAGE_BYTES;
+    CoeffBars &bars = *reinterpret_cast<CoeffBars *>(recs_base + C_STAGES * C_REC_BYTES);
     volatile int *abort_flag = &bars.abort_flag;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -205,6 +208,7 @@ __global__ void __launch_bounds__(C_THREADS, 1) tc_coeff_kernel(const CoeffArgs 
         for (int s = 0; s < C_STAGES; ++s) {
             mbar_init(&bars.full[s], C_GEN_WARPS * 32);
             mbar_init(&bars.empty[s], 1);
+            mbar_init(&bars.recs_full[s], 1);
         }
         mbar_init(&bars.acc_full, 1);
         mbar_init(&bars.acc_empty, C_EPI_WARPS * 32);
@@ -320,7 +324,7 @@ __global__ void __launch_bounds__(C_THREADS, 1) tc_coeff_kernel(const CoeffArgs 
             tc_fence_before();
             mbar_arrive(&bars.acc_empty);
         }
-    } else {
+    } else if (warp < C_LOADER_WARP) {
         // ---------------- basis generators ----------------
         const int g = threadIdx.x - 32 * (1 + C_EPI_WARPS);    // 0..255
         const int which = g >> 7;                              // 0: Xt (A), 1: Yt (B)
@@ -335,25 +339,55 @@ __global__ void __launch_bounds__(C_THREADS, 1) tc_coeff_kernel(const CoeffArgs 
             for (int st = 0; st < nst; ++st, ++it) {
                 if (*abort_flag) break;
                 const int s = it % C_STAGES;
-                if (it >= C_STAGES &&
-                    !mbar_wait(&bars.empty[s], ((it / C_STAGES) - 1) & 1, kWaitLimit, abort_flag)) {
+                if (!mbar_wait(&bars.recs_full[s], (it / C_STAGES) & 1, kWaitLimit, abort_flag) ||
+                    (it >= C_STAGES &&
+                     !mbar_wait(&bars.empty[s], ((it / C_STAGES) - 1) & 1, kWaitLimit, abort_flag))) {
                     raise_timeout(args.status, abort_flag);
                     break;
                 }
                 unsigned char *sb = smem + s * C_STAGE_BYTES;
-                const int blk0 = b0 + st * C_KB;
-                if (PREC == 1) {
-                    gen_coeff_tf32(sb + which * 32768, which ? args.yr : args.xr, blk0, b1,
-                                   (which ? tv : tu) * C_TILE, gg);
-                } else {
-                    gen_coeff_bf16(sb + which * 32768, sb + which * 32768 + 16384,
-                                   which ? args.yr : args.xr, blk0, b1, (which ? tv : tu) * C_TILE, gg);
-                }
+                const AxisRec *recs =
+                    reinterpret_cast<const AxisRec *>(recs_base + s * C_REC_BYTES) + which * C_KB;
+                const int nvalid = min(C_KB, b1 - (b0 + st * C_KB));
+                const int mode_base = (which ? tv : tu) * C_TILE;
+                if (PREC == 1)
+                    gen_coeff_tf32(sb + which * 32768, recs, nvalid, mode_base, gg);
+                else
+                    gen_coeff_bf16(sb + which * 32768, sb + which * 32768 + 16384, recs, nvalid, mode_base, gg);
                 fence_proxy_async_smem();
                 mbar_arrive(&bars.full[s]);
             }
             if (*abort_flag) break;
         }
+    } else {
+        // ---------------- record loader: x and y records of each stage ----------------
+        if (lane == 0) {
+            uint32_t it = 0;
+            for (int unit = blockIdx.x; unit < args.units; unit += gridDim.x) {
+                const int slice = unit % args.slices;
+                const int b0 = slice * args.slice_len;
+                const int b1 = min(args.n, b0 + args.slice_len);
+                const int nst = (b1 - b0 + C_KB - 1) / C_KB;
+                for (int st = 0; st < nst; ++st, ++it) {
+                    if (*abort_flag) break;
+                    const int s = it % C_STAGES;
+                    // the generators have finished with this buffer's previous stage
+                    if (it >= C_STAGES &&
+                        !mbar_wait(&bars.full[s], ((it / C_STAGES) - 1) & 1, kWaitLimit, abort_flag)) {
+                        raise_timeout(args.status, abort_flag);
+                        break;
+                    }
+                    const int blk0 = b0 + st * C_KB;
+                    const uint32_t bytes = (uint32_t)min(C_KB, b1 - blk0) * (uint32_t)sizeof(AxisRec);
+                    unsigned char *dst = recs_base + s * C_REC_BYTES;
+                    mbar_arrive_expect_tx(&bars.recs_full[s], 2 * bytes);
+                    bulk_load(dst, args.xr + blk0, bytes, &bars.recs_full[s]);
+                    bulk_load(dst + C_KB * sizeof(AxisRec), args.yr + blk0, bytes, &bars.recs_full[s]);
+                }
+                if (*abort_flag) break;
+            }
+        }
+        __syncwarp();
     }
     tc_fence_before();
     __syncthreads();
@@ -370,40 +404,44 @@ template <int PREC>
 __global__ void tc_finish_kernel(const float *__restrict__ part, int slices, int Mxc, int Myc,
                                  const float *__restrict__ a_in, float *__restrict__ a_out,
                                  void *__restrict__ Kop, void *__restrict__ Klo, int Mx, int My,
-                                 int Mxe, int Mye, double W, double H) {
-    const double PI = 3.141592653589793;
+                                 int Mxe, int Mye, float piW, float piH, float invWH) {
+    // FP32 throughout (FP64 is a narrow pipe on this GPU): the slice partials are
+    // summed with Kahan compensation; the operand is TF32 or bf16 anyway.
     const size_t total = (size_t)Mxe * Mye;
     for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
          idx += (size_t)gridDim.x * blockDim.x) {
         const int u = (int)(idx / Mye), v = (int)(idx % Mye);
-        double kv = 0.0;
+        float kv = 0.f;
         if (u < Mx && v < My) {
-            const double f = 2.0 * W / (PI * (u > 0 ? u : 1));
-            const double g = 2.0 * H / (PI * (v > 0 ? v : 1));
-            double av;
+            const float f = 2.0f / (piW * (float)(u > 0 ? u : 1));     // 2W / (pi max(u,1))
+            const float g = 2.0f / (piH * (float)(v > 0 ? v : 1));
+            float av;
             if (a_in) {
-                av = (double)a_in[(size_t)u * My + v];
+                av = a_in[(size_t)u * My + v];
             } else {
-                double S = 0.0;
-                for (int s = 0; s < slices; ++s) S += (double)part[((size_t)s * Mxc + u) * Myc + v];
-                const double ku = u * PI / W, lv = v * PI / H;
-                const double eps = (u ? 2.0 : 1.0) * (v ? 2.0 : 1.0);
-                const double G = (u == 0 && v == 0) ? 0.0 : eps / (W * H * (ku * ku + lv * lv));
+                float S = 0.f, comp = 0.f;
+                for (int s = 0; s < slices; ++s) {
+                    const float y = part[((size_t)s * Mxc + u) * Myc + v] - comp;
+                    const float t = S + y;
+                    comp = (t - S) - y;
+                    S = t;
+                }
+                const float ku = (float)u * piW, lv = (float)v * piH;
+                const float eps = (u ? 2.f : 1.f) * (v ? 2.f : 1.f);
+                const float G = (u == 0 && v == 0) ? 0.f : eps * invWH / (ku * ku + lv * lv);
                 av = G * f * g * S;
-                if (a_out) a_out[(size_t)u * My + v] = (float)av;
+                if (a_out) a_out[(size_t)u * My + v] = av;
             }
             kv = f * av * g;
         }
         const int vb = v >> 8, vi = v & 255;
         if (PREC == 1) {
             const size_t off = (((size_t)vb * (Mxe / 4) + (u >> 2)) * 256 + vi) * 4 + (u & 3);
-            reinterpret_cast<float *>(Kop)[off] = to_tf32((float)kv);
+            reinterpret_cast<float *>(Kop)[off] = to_tf32(kv);
         } else {
             const size_t off = (((size_t)vb * (Mxe / 8) + (u >> 3)) * 256 + vi) * 8 + (u & 7);
-            const float k32 = (float)kv;
-            __nv_bfloat16 hi = __float2bfloat16_rn(k32);
-            // lo from the FP64 value: K = hi + lo to ~2^-17 relative
-            __nv_bfloat16 lo = __float2bfloat16_rn((float)(kv - (double)__bfloat162float(hi)));
+            __nv_bfloat16 hi, lo;
+            split_bf16(kv, hi, lo);
             reinterpret_cast<__nv_bfloat16 *>(Kop)[off] = hi;
             reinterpret_cast<__nv_bfloat16 *>(Klo)[off] = lo;
         }
@@ -418,8 +456,8 @@ constexpr int E_VC = 256;                   // v columns per accumulator pass
 constexpr int E_KS = 32;                    // u per pipeline stage
 constexpr int E_STAGES = 3;
 constexpr int E_STAGE_BYTES = 65536;        // A (Xt, Xh) 32 KB + B (K) 32 KB
-constexpr int E_GEN_WARPS = 8;
-constexpr int E_EPI_WARPS = 4;
+constexpr int E_GEN_WARPS = 8;              // two groups of 4 warps, alternate stages
+constexpr int E_EPI_WARPS = 8;              // two per TMEM lane quarter, 128 columns each
 constexpr int E_THREADS = 32 * (2 + E_EPI_WARPS + E_GEN_WARPS);
 
 struct EnergyBars {
@@ -430,7 +468,6 @@ struct EnergyBars {
     uint64_t drain;
     uint32_t tmem_slot;
     int abort_flag;
-    double esum[E_EPI_WARPS];
 };
 constexpr int E_SMEM = E_STAGES * E_STAGE_BYTES + 1024 + (int)sizeof(EnergyBars);
 
@@ -442,79 +479,97 @@ struct EnergyArgs {
     unsigned *status;
 };
 
-// Energy-operand generator (K-major, one block per thread, 16 consecutive u):
-// Xt and Xh for SAMPLE 0 (rectangle) or 1 (centre).
+// Reinsch's form of the sine recurrence: with lam = 4 sin^2(theta/2) the pair
+// (y_k = A sin(k theta + phi), d_k = y_k - y_{k-1}) advances as
+//   d_{k+1} = d_k - lam y_k,   y_{k+1} = y_k + d_{k+1},
+// two operations per step and well conditioned for small theta (theta <= pi/2
+// here: theta = pi w / (2L) with w <= L).
+struct SinRec {
+    float y, d, lam;
+    __device__ __forceinline__ void init(float2 anchor, float2 step, float amp) {
+        // anchor = e^{i k0 theta}, step = e^{i theta}: y = sin(k0 theta), y_prev = sin((k0-1) theta)
+        const float prev = anchor.y * step.x - anchor.x * step.y;
+        y = amp * anchor.y;
+        d = amp * (anchor.y - prev);
+        lam = 2.f * step.y * step.y / (1.f + step.x);     // 2 - 2 cos(theta), no cancellation
+    }
+    __device__ __forceinline__ void next() {
+        d = fmaf(-lam, y, d);
+        y += d;
+    }
+};
+
+// Energy-operand generator: one block, the stage's 32 consecutive u, written as
+// K-major 16-byte rows (4 tf32 or 8 bf16 u each).  SAMPLE 0 (rectangle):
+//   Xt = c cos(pi u s) sin(pi u t)  (c pi t at u = 0),  Xh = -(u pi/W) c sin(pi u s) sin(pi u t);
+// SAMPLE 1 (centre): Xt = q cos(pi u s)/f_u, Xh = -q (u pi/W) sin(pi u s)/f_u.
 template <int PREC, int SAMPLE>
 __device__ __forceinline__ void gen_energy(unsigned char *sb, const AxisRec &R, bool valid, int row,
                                            int u0) {
-    float xt[16], xh[16];
+    float2 zs = make_float2(0.f, 0.f);
+    SinRec st;
+    st.y = st.d = st.lam = 0.f;
+    float ku = (float)u0 * R.inv_l;                  // u pi / W, advanced by pi / W
     if (valid) {
-        float2 zs = phase_cs((unsigned long long)u0, R.s);
-        if (SAMPLE == 0) {
-            float2 zt = phase_cs((unsigned long long)u0, R.t);
-            zt.x *= R.c;
-            zt.y *= R.c;
-#pragma unroll
-            for (int j = 0; j < 16; ++j) {
-                const float ku = (float)(u0 + j) * R.inv_l;
-                xt[j] = zs.x * zt.y;
-                xh[j] = -ku * (zs.y * zt.y);
-                zs = rot(zs, R.es);
-                zt = rot(zt, R.et);
-            }
-            if (u0 == 0) xt[0] = R.v0;
-        } else {
-#pragma unroll
-            for (int j = 0; j < 16; ++j) {
-                const int m = u0 + j;
-                const float ku = (float)m * R.inv_l;
-                const float inv_f = 0.5f * (float)(m > 0 ? m : 1) * R.inv_l;
-                xt[j] = R.q * zs.x * inv_f;
-                xh[j] = -R.q * ku * zs.y * inv_f;
-                zs = rot(zs, R.es);
-            }
-        }
-    } else {
-#pragma unroll
-        for (int j = 0; j < 16; ++j) xt[j] = xh[j] = 0.f;
+        zs = phase_cs((unsigned long long)u0, R.s);
+        if (SAMPLE == 0) st.init(phase_cs((unsigned long long)u0, R.t), R.et, R.c);
     }
-    const int half = (u0 / 16) & 1;   // which 16 of the stage's 32 u
+    auto value = [&](float &xt, float &xh, int u) {
+        if (SAMPLE == 0) {
+            xt = zs.x * st.y;
+            xh = -ku * (zs.y * st.y);
+            st.next();
+        } else {
+            const float inv_f = 0.5f * (float)(u > 0 ? u : 1) * R.inv_l;   // 1 / f_u
+            xt = R.q * zs.x * inv_f;
+            xh = -R.q * ku * zs.y * inv_f;
+        }
+        zs = rot(zs, R.es);
+        ku += R.inv_l;
+    };
     if (PREC == 1) {
         // [128 rows x 32 u] tf32 K-major: core (row/8, u/4) at (row/8)*1024 + (u/4)*128
-        unsigned char *A = sb, *Ah = sb + 16384;
-        const size_t rbase = (size_t)(row >> 3) * 1024 + (row & 7) * 16;
+        unsigned char *A = sb + (size_t)(row >> 3) * 1024 + (row & 7) * 16;
+#pragma unroll 2
+        for (int c = 0; c < 8; ++c) {
+            float t[4], h[4];
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            const size_t off = rbase + (size_t)(half * 4 + c) * 128;
-            *reinterpret_cast<float4 *>(A + off) = make_float4(to_tf32(xt[4 * c]), to_tf32(xt[4 * c + 1]),
-                                                               to_tf32(xt[4 * c + 2]), to_tf32(xt[4 * c + 3]));
-            *reinterpret_cast<float4 *>(Ah + off) = make_float4(to_tf32(xh[4 * c]), to_tf32(xh[4 * c + 1]),
-                                                                to_tf32(xh[4 * c + 2]), to_tf32(xh[4 * c + 3]));
+            for (int j = 0; j < 4; ++j) value(t[j], h[j], u0 + 4 * c + j);
+            if (SAMPLE == 0 && u0 + 4 * c == 0 && valid) t[0] = R.v0;
+            if (!valid) t[0] = t[1] = t[2] = t[3] = h[0] = h[1] = h[2] = h[3] = 0.f;
+            *reinterpret_cast<float4 *>(A + c * 128) =
+                make_float4(to_tf32(t[0]), to_tf32(t[1]), to_tf32(t[2]), to_tf32(t[3]));
+            *reinterpret_cast<float4 *>(A + 16384 + c * 128) =
+                make_float4(to_tf32(h[0]), to_tf32(h[1]), to_tf32(h[2]), to_tf32(h[3]));
         }
     } else {
         // [128 rows x 32 u] bf16 K-major: core (row/8, u/8) at (row/8)*512 + (u/8)*128;
-        // regions: Xt hi, Xt lo, Xh hi, Xh lo (8 KB each)
-        const size_t rbase = (size_t)(row >> 3) * 512 + (row & 7) * 16;
-#pragma unroll
-        for (int c = 0; c < 2; ++c) {
+        // regions Xt hi, Xt lo, Xh hi, Xh lo (8 KB each)
+        unsigned char *A = sb + (size_t)(row >> 3) * 512 + (row & 7) * 16;
+#pragma unroll 1
+        for (int c = 0; c < 4; ++c) {
             uint32_t th[4], tl[4], hh[4], hl[4];
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
+                float t0, h0, t1, h1;
+                value(t0, h0, u0 + 8 * c + 2 * j);
+                value(t1, h1, u0 + 8 * c + 2 * j + 1);
+                if (SAMPLE == 0 && j == 0 && u0 + 8 * c == 0 && valid) t0 = R.v0;
+                if (!valid) t0 = t1 = h0 = h1 = 0.f;
                 __nv_bfloat16 a0, a1, b0, b1, c0, c1, d0, d1;
-                split_bf16(xt[8 * c + 2 * j], a0, b0);
-                split_bf16(xt[8 * c + 2 * j + 1], a1, b1);
-                split_bf16(xh[8 * c + 2 * j], c0, d0);
-                split_bf16(xh[8 * c + 2 * j + 1], c1, d1);
+                split_bf16(t0, a0, b0);
+                split_bf16(t1, a1, b1);
+                split_bf16(h0, c0, d0);
+                split_bf16(h1, c1, d1);
                 th[j] = pack_bf16(a0, a1);
                 tl[j] = pack_bf16(b0, b1);
                 hh[j] = pack_bf16(c0, c1);
                 hl[j] = pack_bf16(d0, d1);
             }
-            const size_t off = rbase + (size_t)(half * 2 + c) * 128;
-            *reinterpret_cast<uint4 *>(sb + off) = make_uint4(th[0], th[1], th[2], th[3]);
-            *reinterpret_cast<uint4 *>(sb + 8192 + off) = make_uint4(tl[0], tl[1], tl[2], tl[3]);
-            *reinterpret_cast<uint4 *>(sb + 16384 + off) = make_uint4(hh[0], hh[1], hh[2], hh[3]);
-            *reinterpret_cast<uint4 *>(sb + 24576 + off) = make_uint4(hl[0], hl[1], hl[2], hl[3]);
+            *reinterpret_cast<uint4 *>(A + c * 128) = make_uint4(th[0], th[1], th[2], th[3]);
+            *reinterpret_cast<uint4 *>(A + 8192 + c * 128) = make_uint4(tl[0], tl[1], tl[2], tl[3]);
+            *reinterpret_cast<uint4 *>(A + 16384 + c * 128) = make_uint4(hh[0], hh[1], hh[2], hh[3]);
+            *reinterpret_cast<uint4 *>(A + 24576 + c * 128) = make_uint4(hl[0], hl[1], hl[2], hl[3]);
         }
     }
 }
@@ -537,7 +592,8 @@ tc_energy_kernel(const __grid_constant__ CUtensorMap tm_hi, const __grid_constan
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < E_STAGES; ++s) {
-            mbar_init(&bars.full[s], E_GEN_WARPS * 32 + 1);
+            // one generator group (128 threads) + the TMA producer per stage
+            mbar_init(&bars.full[s], (E_GEN_WARPS / 2) * 32 + 1);
             mbar_init(&bars.empty[s], 1);
         }
         mbar_init(&bars.acc_full, 1);
@@ -639,6 +695,7 @@ tc_energy_kernel(const __grid_constant__ CUtensorMap tm_hi, const __grid_constan
     } else if (warp < 2 + E_EPI_WARPS) {
         // ---------------- epilogue: row dots with Yt, Yh ----------------
         const int quarter = warp & 3;
+        const int chalf = (warp - 2) >> 2;              // columns [128*chalf, 128*chalf + 128)
         const int row = quarter * 32 + lane;
         const int b = blk0 + row;
         const bool valid = b < args.n;
@@ -653,7 +710,7 @@ tc_energy_kernel(const __grid_constant__ CUtensorMap tm_hi, const __grid_constan
             }
             tc_fence_after();
 #pragma unroll 1
-            for (int c = 0; c < E_VC; c += 32) {
+            for (int c = chalf * 128; c < chalf * 128 + 128; c += 32) {
                 float t[32], tp[32];
                 const uint32_t ta = tmem + ((uint32_t)(quarter * 32) << 16) + c;
                 tmem_ld16(ta, t);
@@ -664,63 +721,91 @@ tc_energy_kernel(const __grid_constant__ CUtensorMap tm_hi, const __grid_constan
                 if (!valid) continue;
                 const int v0 = vc * E_VC + c;
                 float2 zs = phase_cs((unsigned long long)v0, Ry.s);
-                float2 zt = make_float2(0.f, 0.f);
-                if (SAMPLE == 0) zt = phase_cs((unsigned long long)v0, Ry.t);
+                float lv = (float)v0 * Ry.inv_l;
+                if (SAMPLE == 0) {
+                    SinRec st;
+                    st.init(phase_cs((unsigned long long)v0, Ry.t), Ry.et, 1.f);
 #pragma unroll
-                for (int j = 0; j < 32; ++j) {
-                    const int v = v0 + j;
-                    const float lv = (float)v * Ry.inv_l;
-                    float yt, yh;
-                    if (SAMPLE == 0) {
-                        yt = (v == 0) ? Ry.v0 : zs.x * zt.y;
-                        yh = -lv * (zs.y * zt.y);
-                        zt = rot(zt, Ry.et);
-                    } else {
-                        const float inv_g = 0.5f * (float)(v > 0 ? v : 1) * Ry.inv_l;
-                        yt = zs.x * inv_g;
-                        yh = -lv * zs.y * inv_g;
+                    for (int j = 0; j < 32; ++j) {
+                        const float yt = zs.x * st.y;
+                        const float yh = -lv * (zs.y * st.y);
+                        eN = fmaf(t[j], yt, eN);
+                        eY = fmaf(t[j], yh, eY);
+                        eX = fmaf(tp[j], yt, eX);
+                        zs = rot(zs, Ry.es);
+                        st.next();
+                        lv += Ry.inv_l;
                     }
-                    zs = rot(zs, Ry.es);
-                    eN = fmaf(t[j], yt, eN);
-                    eY = fmaf(t[j], yh, eY);
-                    eX = fmaf(tp[j], yt, eX);
+                    if (v0 == 0) {      // v = 0 column: Yt = pi t (not the sine limit 0)
+                        eN = fmaf(t[0], Ry.v0, eN);
+                        eX = fmaf(tp[0], Ry.v0, eX);
+                    }
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) {
+                        const int v = v0 + j;
+                        const float inv_g = 0.5f * (float)(v > 0 ? v : 1) * Ry.inv_l;
+                        const float yt = zs.x * inv_g;
+                        const float yh = -lv * zs.y * inv_g;
+                        eN = fmaf(t[j], yt, eN);
+                        eY = fmaf(t[j], yh, eY);
+                        eX = fmaf(tp[j], yt, eX);
+                        zs = rot(zs, Ry.es);
+                        lv += Ry.inv_l;
+                    }
                 }
             }
             tc_fence_before();
             mbar_arrive(&bars.acc_empty);
         }
-        if (valid && !*abort_flag) {
-            if (args.e_block) args.e_block[b] = eN;
-            if (args.gx) args.gx[b] = eX;
-            if (args.gy) args.gy[b] = eY;
+        // the two column halves of a row meet through shared memory
+        float *red = reinterpret_cast<float *>(smem);   // stage 0 buffer, free once all MMAs are done
+        __syncwarp();
+        const bool ok = !*abort_flag;
+        // wait until every epilogue warp is past its last TMEM read (named barrier 1)
+        asm volatile("bar.sync 1, %0;" ::"r"(E_EPI_WARPS * 32));
+        if (chalf == 1) {
+            red[row * 3 + 0] = eN;
+            red[row * 3 + 1] = eX;
+            red[row * 3 + 2] = eY;
         }
-        double es = valid ? (double)eN : 0.0;
+        asm volatile("bar.sync 1, %0;" ::"r"(E_EPI_WARPS * 32));
+        if (chalf == 0) {
+            eN += red[row * 3 + 0];
+            eX += red[row * 3 + 1];
+            eY += red[row * 3 + 2];
+            if (valid && ok) {
+                if (args.e_block) args.e_block[b] = eN;
+                if (args.gx) args.gx[b] = eX;
+                if (args.gy) args.gy[b] = eY;
+            }
+            double es = valid ? (double)eN : 0.0;
 #pragma unroll
-        for (int off = 16; off >= 1; off >>= 1) es += __shfl_xor_sync(0xffffffffu, es, off);
-        if (lane == 0 && args.e_total && !*abort_flag) atomicAdd(args.e_total, 0.5 * es);
+            for (int off = 16; off >= 1; off >>= 1) es += __shfl_xor_sync(0xffffffffu, es, off);
+            if (lane == 0 && args.e_total && ok) atomicAdd(args.e_total, 0.5 * es);
+        }
     } else {
         // ---------------- basis generators: Xt, Xh ----------------
+        // group 0 (warps 0-3 of the generators) fills even stages, group 1 odd ones
         const int g = threadIdx.x - 32 * (2 + E_EPI_WARPS);   // 0..255
-        const int row = g & 127, hh = g >> 7;
+        const int row = g & 127, grp = g >> 7;
         const int b = blk0 + row;
         const bool valid = b < args.n;
         AxisRec Rx;
         if (valid) Rx = args.xr[b];
-        int it = 0;
-        for (int vc = 0; vc < nvc; ++vc) {
-            for (int ks = 0; ks < nks; ++ks, ++it) {
-                if (*abort_flag) break;
-                const int s = it % E_STAGES;
-                if (it >= E_STAGES &&
-                    !mbar_wait(&bars.empty[s], ((it / E_STAGES) - 1) & 1, kWaitLimit, abort_flag)) {
-                    raise_timeout(args.status, abort_flag);
-                    break;
-                }
-                gen_energy<PREC, SAMPLE>(smem + s * E_STAGE_BYTES, Rx, valid, row, ks * E_KS + hh * 16);
-                fence_proxy_async_smem();
-                mbar_arrive(&bars.full[s]);
-            }
+        const int total = nvc * nks;
+        for (int it = grp; it < total; it += 2) {
             if (*abort_flag) break;
+            const int s = it % E_STAGES;
+            if (it >= E_STAGES &&
+                !mbar_wait(&bars.empty[s], ((it / E_STAGES) - 1) & 1, kWaitLimit, abort_flag)) {
+                raise_timeout(args.status, abort_flag);
+                break;
+            }
+            const int ks = it % nks;
+            gen_energy<PREC, SAMPLE>(smem + s * E_STAGE_BYTES, Rx, valid, row, ks * E_KS);
+            fence_proxy_async_smem();
+            mbar_arrive(&bars.full[s]);
         }
     }
     tc_fence_before();
@@ -824,12 +909,14 @@ cudaError_t launch_finish_tc(const Launch &L, int prec, const TcPlan &P, const f
     int blocks = (int)((total + 255) / 256);
     if (blocks > 8 * L.sm_count) blocks = 8 * L.sm_count;
     if (blocks < 1) blocks = 1;
+    const double PI = 3.141592653589793;
+    const float piW = (float)(PI / L.W), piH = (float)(PI / L.H), invWH = (float)(1.0 / (L.W * L.H));
     if (prec == 1)
         tc_finish_kernel<1><<<blocks, 256, 0, L.stream>>>(part, P.slices, P.Mxc, P.Myc, a_in, a_out, Khi,
-                                                          Klo, L.Mx, L.My, P.Mxe, P.Mye, L.W, L.H);
+                                                          Klo, L.Mx, L.My, P.Mxe, P.Mye, piW, piH, invWH);
     else
         tc_finish_kernel<2><<<blocks, 256, 0, L.stream>>>(part, P.slices, P.Mxc, P.Myc, a_in, a_out, Khi,
-                                                          Klo, L.Mx, L.My, P.Mxe, P.Mye, L.W, L.H);
+                                                          Klo, L.Mx, L.My, P.Mxe, P.Mye, piW, piH, invWH);
     return cudaGetLastError();
 }
 
