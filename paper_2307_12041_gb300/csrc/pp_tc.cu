@@ -459,6 +459,10 @@ constexpr int E_STAGE_BYTES = 65536;        // A (Xt, Xh) 32 KB + B (K) 32 KB
 constexpr int E_GEN_WARPS = 8;              // two groups of 4 warps, alternate stages
 constexpr int E_EPI_WARPS = 8;              // two per TMEM lane quarter, 128 columns each
 constexpr int E_THREADS = 32 * (2 + E_EPI_WARPS + E_GEN_WARPS);
+#ifndef PP_ENERGY_CLUSTER
+#define PP_ENERGY_CLUSTER 1
+#endif
+constexpr int kEnergyCluster = PP_ENERGY_CLUSTER;     // CTAs sharing each K tile
 
 struct EnergyBars {
     uint64_t full[E_STAGES];
@@ -574,7 +578,10 @@ __device__ __forceinline__ void gen_energy(unsigned char *sb, const AxisRec &R, 
     }
 }
 
-template <int PREC, int SAMPLE>
+// CL = CTAs per cluster sharing each K tile: CTA rank 0 multicasts the tile to all
+// of them, and every CTA's MMA completion is signalled to all of them, so a
+// stage buffer is refilled only once every CTA of the cluster has consumed it.
+template <int PREC, int SAMPLE, int CL>
 __global__ void __launch_bounds__(E_THREADS, 1)
 tc_energy_kernel(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ CUtensorMap tm_lo,
                  const EnergyArgs args) {
@@ -590,11 +597,13 @@ tc_energy_kernel(const __grid_constant__ CUtensorMap tm_hi, const __grid_constan
     const int nvc = args.Mye / E_VC;
     const int nks = args.Mxe / E_KS;
 
+    constexpr uint16_t cl_mask = (uint16_t)((1u << CL) - 1u);
+    const uint32_t cl_rank = CL > 1 ? cluster_ctarank() : 0u;
     if (threadIdx.x == 0) {
         for (int s = 0; s < E_STAGES; ++s) {
             // one generator group (128 threads) + the TMA producer per stage
             mbar_init(&bars.full[s], (E_GEN_WARPS / 2) * 32 + 1);
-            mbar_init(&bars.empty[s], 1);
+            mbar_init(&bars.empty[s], CL);        // one MMA completion per cluster CTA
         }
         mbar_init(&bars.acc_full, 1);
         mbar_init(&bars.acc_empty, E_EPI_WARPS * 32);
@@ -607,7 +616,8 @@ tc_energy_kernel(const __grid_constant__ CUtensorMap tm_hi, const __grid_constan
         tmem_relinquish();
     }
     tc_fence_before();
-    __syncthreads();
+    if (CL > 1) cluster_sync();      // barriers of every CTA initialised before remote use
+    else __syncthreads();
     tc_fence_after();
     const uint32_t tmem = bars.tmem_slot;
 
@@ -658,7 +668,8 @@ tc_energy_kernel(const __grid_constant__ CUtensorMap tm_hi, const __grid_constan
                             mma_bf16(tmem + 256, smem_desc(Hh + ao, 128, 512), bh, idesc, true);
                         }
                     }
-                    mma_commit(&bars.empty[s]);
+                    if (CL > 1) mma_commit_multicast(&bars.empty[s], cl_mask);
+                    else mma_commit(&bars.empty[s]);
                 }
                 if (*abort_flag) break;
                 mma_commit(&bars.acc_full);
@@ -683,10 +694,16 @@ tc_energy_kernel(const __grid_constant__ CUtensorMap tm_hi, const __grid_constan
                         break;
                     }
                     unsigned char *sb = smem + s * E_STAGE_BYTES + 32768;
-                    const int z = vc * (args.Mxe / T) + ks * (E_KS / T);
+                    // stage start in 1 KB rows: ((vc*(Mxe/T) + ks*(32/T)) * 4 KB) / 1 KB
+                    const int row = 4 * (vc * (args.Mxe / T) + ks * (E_KS / T));
                     mbar_arrive_expect_tx(&bars.full[s], bytes);
-                    tma_load_3d(sb, &tm_hi, 0, 0, z, &bars.full[s]);
-                    if (BF) tma_load_3d(sb + 16384, &tm_lo, 0, 0, z, &bars.full[s]);
+                    if (CL == 1) {
+                        tma_load_2d(sb, &tm_hi, 0, row, &bars.full[s]);
+                        if (BF) tma_load_2d(sb + 16384, &tm_lo, 0, row, &bars.full[s]);
+                    } else if (cl_rank == 0) {
+                        tma_load_2d_multicast(sb, &tm_hi, 0, row, &bars.full[s], cl_mask);
+                        if (BF) tma_load_2d_multicast(sb + 16384, &tm_lo, 0, row, &bars.full[s], cl_mask);
+                    }
                 }
                 if (*abort_flag) break;
             }
@@ -704,11 +721,22 @@ tc_energy_kernel(const __grid_constant__ CUtensorMap tm_hi, const __grid_constan
         float eN = 0.f, eX = 0.f, eY = 0.f;
         for (int vc = 0; vc < nvc; ++vc) {
             if (*abort_flag) break;
+            // phase anchors for this thread's 128 columns, ahead of the wait
+            const int vb = vc * E_VC + chalf * 128;
+            float2 zs = make_float2(1.f, 0.f), zt = make_float2(0.f, 0.f);
+            if (valid) {
+                zs = phase_cs((unsigned long long)vb, Ry.s);
+                if (SAMPLE == 0) zt = phase_cs((unsigned long long)vb, Ry.t);
+            }
+            SinRec st;
+            st.init(zt, Ry.et, 1.f);
+            float lv = (float)vb * Ry.inv_l;
             if (!mbar_wait(&bars.acc_full, vc & 1, kWaitLimit, abort_flag)) {
                 raise_timeout(args.status, abort_flag);
                 break;
             }
             tc_fence_after();
+            float aN = 0.f, aX = 0.f, aY = 0.f;      // second accumulator set (odd columns)
 #pragma unroll 1
             for (int c = chalf * 128; c < chalf * 128 + 128; c += 32) {
                 float t[32], tp[32];
@@ -719,31 +747,33 @@ tc_energy_kernel(const __grid_constant__ CUtensorMap tm_hi, const __grid_constan
                 tmem_ld16(ta + 256 + 16, tp + 16);
                 tmem_ld_wait();
                 if (!valid) continue;
-                const int v0 = vc * E_VC + c;
-                float2 zs = phase_cs((unsigned long long)v0, Ry.s);
-                float lv = (float)v0 * Ry.inv_l;
                 if (SAMPLE == 0) {
-                    SinRec st;
-                    st.init(phase_cs((unsigned long long)v0, Ry.t), Ry.et, 1.f);
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) {
-                        const float yt = zs.x * st.y;
-                        const float yh = -lv * (zs.y * st.y);
+                    for (int j = 0; j < 32; j += 2) {
+                        float yt = zs.x * st.y, p = zs.y * st.y;
                         eN = fmaf(t[j], yt, eN);
-                        eY = fmaf(t[j], yh, eY);
                         eX = fmaf(tp[j], yt, eX);
+                        eY = fmaf(-t[j] * lv, p, eY);
+                        zs = rot(zs, Ry.es);
+                        st.next();
+                        lv += Ry.inv_l;
+                        yt = zs.x * st.y;
+                        p = zs.y * st.y;
+                        aN = fmaf(t[j + 1], yt, aN);
+                        aX = fmaf(tp[j + 1], yt, aX);
+                        aY = fmaf(-t[j + 1] * lv, p, aY);
                         zs = rot(zs, Ry.es);
                         st.next();
                         lv += Ry.inv_l;
                     }
-                    if (v0 == 0) {      // v = 0 column: Yt = pi t (not the sine limit 0)
+                    if (c == 0 && vc == 0) {      // v = 0 column: Yt = pi t (not the sine limit 0)
                         eN = fmaf(t[0], Ry.v0, eN);
                         eX = fmaf(tp[0], Ry.v0, eX);
                     }
                 } else {
 #pragma unroll
                     for (int j = 0; j < 32; ++j) {
-                        const int v = v0 + j;
+                        const int v = vc * E_VC + c + j;
                         const float inv_g = 0.5f * (float)(v > 0 ? v : 1) * Ry.inv_l;
                         const float yt = zs.x * inv_g;
                         const float yh = -lv * zs.y * inv_g;
@@ -757,6 +787,9 @@ tc_energy_kernel(const __grid_constant__ CUtensorMap tm_hi, const __grid_constan
             }
             tc_fence_before();
             mbar_arrive(&bars.acc_empty);
+            eN += aN;
+            eX += aX;
+            eY += aY;
         }
         // the two column halves of a row meet through shared memory
         float *red = reinterpret_cast<float *>(smem);   // stage 0 buffer, free once all MMAs are done
@@ -809,7 +842,8 @@ tc_energy_kernel(const __grid_constant__ CUtensorMap tm_hi, const __grid_constan
         }
     }
     tc_fence_before();
-    __syncthreads();
+    if (CL > 1) cluster_sync();      // no CTA leaves while a peer may still signal or fill it
+    else __syncthreads();
     if (warp == 0) {
         tc_fence_after();
         tmem_dealloc(tmem, 512);
@@ -839,18 +873,20 @@ EncodeTiledFn encode_fn() {
     return fn;
 }
 
-// 3-D map over the tiled energy operand: (u within a core row, v within a 256
-// block, (v block, u core group)), one box = one pipeline stage (32 u x 256 v).
+// 2-D map over the tiled energy operand viewed as rows of 1 KB (256 x 32-bit
+// words).  The finish kernel lays K out so that one pipeline stage (32 u x 256 v,
+// in the K-major core-matrix order the MMA reads) is one contiguous run of
+// 32 KB (TF32) or 16 KB (each bf16 half), so a stage is one box of 32 or 16 rows.
 cudaError_t make_kmap(CUtensorMap *map, void *base, bool bf16, int Mxe, int Mye) {
     EncodeTiledFn fn = encode_fn();
     if (!fn) return cudaErrorNotSupported;
-    const int T = bf16 ? 8 : 4;
-    cuuint64_t dims[3] = {(cuuint64_t)T, 256, (cuuint64_t)(Mye / 256) * (Mxe / T)};
-    cuuint64_t strides[2] = {16, 4096};
-    cuuint32_t box[3] = {(cuuint32_t)T, 256, (cuuint32_t)(E_KS / T)};
-    cuuint32_t estr[3] = {1, 1, 1};
-    CUresult r = fn(map, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base,
-                    dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+    const size_t bytes = (size_t)Mxe * Mye * (bf16 ? 2 : 4);
+    cuuint64_t dims[2] = {256, (cuuint64_t)(bytes / 1024)};
+    cuuint64_t strides[1] = {1024};
+    cuuint32_t box[2] = {256, (cuuint32_t)(bf16 ? 16 : 32)};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_UINT32, 2, base, dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
@@ -942,13 +978,27 @@ cudaError_t launch_energy_tc(const Launch &L, int prec, int sample, const TcPlan
     a.gy = gy;
     a.e_total = e_total;
     a.status = L.status;
-    const int grid = (L.n + E_ROWS - 1) / E_ROWS;
-#define PP_ELAUNCH(PR, SA)                                                                           \
-    do {                                                                                             \
-        e = cudaFuncSetAttribute(tc_energy_kernel<PR, SA>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                                 E_SMEM);                                                            \
-        if (e != cudaSuccess) return e;                                                              \
-        tc_energy_kernel<PR, SA><<<grid, E_THREADS, E_SMEM, L.stream>>>(mh, ml, a);                  \
+    const int ctas = (L.n + E_ROWS - 1) / E_ROWS;
+    const int grid = (ctas + kEnergyCluster - 1) / kEnergyCluster * kEnergyCluster;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(E_THREADS);
+    cfg.dynamicSmemBytes = E_SMEM;
+    cfg.stream = L.stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = kEnergyCluster;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+#define PP_ELAUNCH(PR, SA)                                                                         \
+    do {                                                                                           \
+        auto kfn = tc_energy_kernel<PR, SA, kEnergyCluster>;                                       \
+        e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, E_SMEM);       \
+        if (e != cudaSuccess) return e;                                                            \
+        e = cudaLaunchKernelEx(&cfg, kfn, mh, ml, a);                                              \
+        if (e != cudaSuccess) return e;                                                            \
     } while (0)
     if (prec == 1 && sample == 0) PP_ELAUNCH(1, 0);
     else if (prec == 1) PP_ELAUNCH(1, 1);
