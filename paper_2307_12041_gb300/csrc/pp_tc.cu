@@ -31,12 +31,15 @@
 #include <cstdio>
 
 #include "pp_device.cuh"
+#include "pp_gen.cuh"
 #include "pp_internal.h"
 #include "pp_tc.cuh"
 
 namespace pp {
 
 using namespace tc;
+using gen::c2;
+using gen::f2;
 
 namespace {
 
@@ -90,115 +93,146 @@ struct CoeffArgs {
     unsigned *status;
 };
 
-// TF32 generator: K-major rows of 4 consecutive blocks.  Thread (k4, r, half)
-// writes operand rows R = half*128 + r + 8j (j = 0..15), blocks 4k4..4k4+3 of the
-// stage (records in shared memory, `nvalid` of them valid).
+// TF32 generator: K-major rows of 4 consecutive blocks.  Thread gg (0..127) owns
+// the block pair 4*k4 + 2*pp + {0, 1} of the stage and the mode residue r; it
+// writes operand rows R = r + 8j (j = 0..31) as 8-byte halves of the 16-byte core
+// rows, with the two blocks' rotations advanced together in packed registers.
 __device__ __forceinline__ void gen_coeff_tf32(unsigned char *op, const AxisRec *recs, int nvalid,
-                                               int mode_base, int g) {
-    const int half = (g >> 6) & 1, k4 = (g & 63) >> 3, r = g & 7;
-    const int m0 = mode_base + half * 128 + r;
-    float2 zs[4], zt[4], es[4], et[4];
-    float v0[4];
+                                               int mode_base, int gg) {
+    const int lane = gg & 31, w = gg >> 5;
+    const int r = lane & 7, pp = (lane >> 3) & 1, k4 = 2 * w + (lane >> 4);
+    const int b0 = 4 * k4 + 2 * pp;
+    const unsigned long long m0 = (unsigned long long)(mode_base + r);
+    float2 zs[2], zt[2], es[2], et[2];
+    float v0[2];
 #pragma unroll
-    for (int b = 0; b < 4; ++b) {
-        const int k = 4 * k4 + b;
+    for (int b = 0; b < 2; ++b) {
+        const int k = b0 + b;
         if (k < nvalid) {
             const AxisRec &R = recs[k];
-            zs[b] = phase_cs((unsigned long long)m0, R.s);
-            zt[b] = phase_cs((unsigned long long)m0, R.t);
+            zs[b] = gen::phase_poly(m0, R.s);
+            zt[b] = gen::phase_poly(m0, R.t);
             zt[b].x *= R.c;
             zt[b].y *= R.c;
             es[b] = R.es8;
             et[b] = R.et8;
             v0[b] = R.v0;
         } else {
-            zs[b] = make_float2(0.f, 0.f);
-            zt[b] = make_float2(0.f, 0.f);
+            zs[b] = zt[b] = make_float2(0.f, 0.f);
             es[b] = et[b] = make_float2(1.f, 0.f);
             v0[b] = 0.f;
         }
     }
-    unsigned char *base = op + (half * 16) * 1024 + k4 * 128 + r * 16;
-#pragma unroll 4
-    for (int j = 0; j < 16; ++j) {
-        float v[4];
-#pragma unroll
-        for (int b = 0; b < 4; ++b) {
-            v[b] = to_tf32(zs[b].x * zt[b].y);
-            zs[b] = rot(zs[b], es[b]);
-            zt[b] = rot(zt[b], et[b]);
+    // two sub-chains: even j (Z0, T0) and odd j (Z1, T1), each stepping 16 modes
+    const gen::rot2_step E8 = gen::make_step(es[0], es[1]), F8 = gen::make_step(et[0], et[1]);
+    c2 Z0 = gen::make_c2(zs[0], zs[1]), T0 = gen::make_c2(zt[0], zt[1]);
+    c2 Z1 = gen::rot2(Z0, E8), T1 = gen::rot2(T0, F8);
+    const gen::rot2_step ES = gen::make_step(rot(es[0], es[0]), rot(es[1], es[1]));
+    const gen::rot2_step ET = gen::make_step(rot(et[0], et[0]), rot(et[1], et[1]));
+    unsigned char *base = op + k4 * 128 + r * 16 + pp * 8;
+#pragma unroll 2
+    for (int jj = 0; jj < 32; jj += 2) {
+        float a0, b0, a1, b1;
+        gen::upk(gen::mul2(Z0.re, T0.im), a0, b0);
+        gen::upk(gen::mul2(Z1.re, T1.im), a1, b1);
+        if (m0 == 0 && jj == 0) {
+            a0 = v0[0];
+            b0 = v0[1];
         }
-        if (m0 == 0 && j == 0) {
-#pragma unroll
-            for (int b = 0; b < 4; ++b) v[b] = to_tf32(v0[b]);
-        }
-        *reinterpret_cast<float4 *>(base + j * 1024) = make_float4(v[0], v[1], v[2], v[3]);
+        *reinterpret_cast<float2 *>(base + jj * 1024) = make_float2(to_tf32(a0), to_tf32(b0));
+        *reinterpret_cast<float2 *>(base + (jj + 1) * 1024) = make_float2(to_tf32(a1), to_tf32(b1));
+        Z0 = gen::rot2(Z0, ES);
+        T0 = gen::rot2(T0, ET);
+        Z1 = gen::rot2(Z1, ES);
+        T1 = gen::rot2(T1, ET);
     }
+}
+
+__device__ __forceinline__ uint32_t cvt_bf16x2(float lo_half, float hi_half) {
+    uint32_t d;
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi_half), "f"(lo_half));
+    return d;
+}
+// (a, b) -> packed bf16 hi parts and packed bf16 lo = bf16(x - hi) parts (a in the low half)
+__device__ __forceinline__ void split2(float a, float b, uint32_t &hi, uint32_t &lo) {
+    hi = cvt_bf16x2(a, b);
+    const float ha = __uint_as_float(hi << 16), hb = __uint_as_float(hi & 0xFFFF0000u);
+    lo = cvt_bf16x2(a - ha, b - hb);
 }
 
 // BF16 generator: MN-major rows of 8 consecutive modes of one block.  Thread
 // (block k, lane group lg) writes mode groups lg + 4q (q = 0..7), 8 modes each,
-// hi and lo parts.  Element (mode R, block k) at (R/8)*128 + (k/8)*4096 + (k%8)*16.
+// hi and lo parts; even and odd modes advance as two packed chains.  Element
+// (mode R, block k) at (R/8)*128 + (k/8)*4096 + (k%8)*16.
 __device__ __forceinline__ void gen_coeff_bf16(unsigned char *op_hi, unsigned char *op_lo,
                                                const AxisRec *recs, int nvalid, int mode_base, int g) {
     const int lane = g & 31, wq = (g >> 5) & 3;
     const int k = (lane & 7) + 8 * wq;
     const int lg = lane >> 3;
-    float2 zs, zt, es, et, es32, et32;
-    float v0;
+    float2 za = make_float2(0.f, 0.f), ta = za, es = make_float2(1.f, 0.f), et = es, es8 = es, et8 = es;
+    float v0 = 0.f;
     if (k < nvalid) {
         const AxisRec &R = recs[k];
-        const int m0 = mode_base + 8 * lg;
-        zs = phase_cs((unsigned long long)m0, R.s);
-        zt = phase_cs((unsigned long long)m0, R.t);
-        zt.x *= R.c;
-        zt.y *= R.c;
+        const unsigned long long m0 = (unsigned long long)(mode_base + 8 * lg);
+        za = gen::phase_poly(m0, R.s);
+        ta = gen::phase_poly(m0, R.t);
+        ta.x *= R.c;
+        ta.y *= R.c;
         es = R.es;
         et = R.et;
-        const float2 s16 = rot(R.es8, R.es8), t16 = rot(R.et8, R.et8);
-        es32 = rot(s16, s16);
-        et32 = rot(t16, t16);
+        es8 = R.es8;
+        et8 = R.et8;
         v0 = R.v0;
-    } else {
-        zs = zt = make_float2(0.f, 0.f);
-        es = et = es32 = et32 = make_float2(1.f, 0.f);
-        v0 = 0.f;
     }
+    // group-start chains (modes m, m+1), the 2-mode step, and the 32-mode jump
+    c2 GS = gen::make_c2(za, rot(za, es)), GT = gen::make_c2(ta, rot(ta, et));
+    const float2 es2 = rot(es, es), et2 = rot(et, et);
+    const float2 s16 = rot(es8, es8), t16 = rot(et8, et8);
+    const gen::rot2_step S2 = gen::make_step(es2, es2), T2 = gen::make_step(et2, et2);
+    const gen::rot2_step S32 = gen::make_step(rot(s16, s16), rot(s16, s16));
+    const gen::rot2_step T32 = gen::make_step(rot(t16, t16), rot(t16, t16));
     const size_t koff = (size_t)(k >> 3) * 4096 + (k & 7) * 16;
-#pragma unroll 2
-    for (int q = 0; q < 8; ++q) {
-        const int grp = lg + 4 * q;
-        float2 a = zs, b = zt;
-        uint32_t hi[4], lo[4];
+    // groups q and q + 4 (128 modes apart) advance together: two independent chains
+    const float2 s64 = rot(rot(s16, s16), rot(s16, s16)), t64 = rot(rot(t16, t16), rot(t16, t16));
+    const gen::rot2_step S128 = gen::make_step(rot(s64, s64), rot(s64, s64));
+    const gen::rot2_step T128 = gen::make_step(rot(t64, t64), rot(t64, t64));
+    c2 HS = gen::rot2(GS, S128), HT = gen::rot2(GT, T128);
+#pragma unroll 1
+    for (int q = 0; q < 4; ++q) {
+        const int grp0 = lg + 4 * q, grp1 = grp0 + 16;
+        c2 z0 = GS, t0 = GT, z1 = HS, t1 = HT;
+        uint32_t hi0[4], lo0[4], hi1[4], lo1[4];
 #pragma unroll
-        for (int j = 0; j < 8; j += 2) {
-            float v[2];
-#pragma unroll
-            for (int e = 0; e < 2; ++e) {
-                v[e] = a.x * b.y;
-                a = rot(a, es);
-                b = rot(b, et);
-            }
-            if (mode_base + 8 * grp + j == 0) v[0] = v0;
-            __nv_bfloat16 h0, l0, h1, l1;
-            split_bf16(v[0], h0, l0);
-            split_bf16(v[1], h1, l1);
-            hi[j >> 1] = pack_bf16(h0, h1);
-            lo[j >> 1] = pack_bf16(l0, l1);
+        for (int jj = 0; jj < 4; ++jj) {
+            float a, b, c, d;
+            gen::upk(gen::mul2(z0.re, t0.im), a, b);
+            gen::upk(gen::mul2(z1.re, t1.im), c, d);
+            if (jj == 0 && mode_base + 8 * grp0 == 0) a = v0;
+            split2(a, b, hi0[jj], lo0[jj]);
+            split2(c, d, hi1[jj], lo1[jj]);
+            z0 = gen::rot2(z0, S2);
+            t0 = gen::rot2(t0, T2);
+            z1 = gen::rot2(z1, S2);
+            t1 = gen::rot2(t1, T2);
         }
-        const size_t off = (size_t)grp * 128 + koff;
-        *reinterpret_cast<uint4 *>(op_hi + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
-        *reinterpret_cast<uint4 *>(op_lo + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
-        zs = rot(zs, es32);
-        zt = rot(zt, et32);
+        const size_t off0 = (size_t)grp0 * 128 + koff, off1 = (size_t)grp1 * 128 + koff;
+        *reinterpret_cast<uint4 *>(op_hi + off0) = make_uint4(hi0[0], hi0[1], hi0[2], hi0[3]);
+        *reinterpret_cast<uint4 *>(op_lo + off0) = make_uint4(lo0[0], lo0[1], lo0[2], lo0[3]);
+        *reinterpret_cast<uint4 *>(op_hi + off1) = make_uint4(hi1[0], hi1[1], hi1[2], hi1[3]);
+        *reinterpret_cast<uint4 *>(op_lo + off1) = make_uint4(lo1[0], lo1[1], lo1[2], lo1[3]);
+        GS = gen::rot2(GS, S32);
+        GT = gen::rot2(GT, T32);
+        HS = gen::rot2(HS, S32);
+        HT = gen::rot2(HT, T32);
     }
 }
 
 template <int PREC>
 __global__ void __launch_bounds__(C_THREADS, 1) tc_coeff_kernel(const CoeffArgs args) {
     extern __shared__ unsigned char smem_raw[];
-    unsigned char *smem = reinterpret_cast<unsigned char *>(
-        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    // 1 KB-aligned base by pointer arithmetic on the __shared__ array, so that the
+    // compiler keeps every access in the shared address space (LDS/STS)
+    unsigned char *smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
     unsigned char *recs_base = smem + C_STAGES * C_STAGE_BYTES;
     CoeffBars &bars = *reinterpret_cast<CoeffBars *>(recs_base + C_STAGES * C_REC_BYTES);
     volatile int *abort_flag = &bars.abort_flag;
@@ -483,111 +517,144 @@ struct EnergyArgs {
     unsigned *status;
 };
 
-// Reinsch's form of the sine recurrence: with lam = 4 sin^2(theta/2) the pair
-// (y_k = A sin(k theta + phi), d_k = y_k - y_{k-1}) advances as
-//   d_{k+1} = d_k - lam y_k,   y_{k+1} = y_k + d_{k+1},
-// two operations per step and well conditioned for small theta (theta <= pi/2
-// here: theta = pi w / (2L) with w <= L).
-struct SinRec {
-    float y, d, lam;
-    __device__ __forceinline__ void init(float2 anchor, float2 step, float amp) {
-        // anchor = e^{i k0 theta}, step = e^{i theta}: y = sin(k0 theta), y_prev = sin((k0-1) theta)
-        const float prev = anchor.y * step.x - anchor.x * step.y;
-        y = amp * anchor.y;
-        d = amp * (anchor.y - prev);
-        lam = 2.f * step.y * step.y / (1.f + step.x);     // 2 - 2 cos(theta), no cancellation
+// Energy-operand generator: one block, the stage's 32 consecutive u, written as
+// K-major 16-byte rows (4 tf32 or 8 bf16 u each) as they are produced.
+// SAMPLE 0 (rectangle): Xt = c cos(pi u s) sin(pi u t)  (c pi t at u = 0),
+//                       Xh = -(u pi/W) c sin(pi u s) sin(pi u t);
+// SAMPLE 1 (centre):    Xt = q cos(pi u s)/f_u,  Xh = -q (u pi/W) sin(pi u s)/f_u.
+// Rectangle mode advances (u, u+1) as two packed chains with a 2-mode step.
+template <int SAMPLE>
+struct EnergyChain {
+    // SAMPLE 0 state
+    c2 Z, T;
+    gen::rot2_step S2, T2;
+    f2 nku, dku;
+    // SAMPLE 1 state
+    float2 zs, es;
+    float ku, inv_l, q;
+    int u;
+    bool valid;
+    __device__ __forceinline__ void init(const AxisRec &R, bool v, int u0) {
+        valid = v;
+        u = u0;
+        if (!v) return;
+        if (SAMPLE == 0) {
+            const float2 za = gen::phase_poly((unsigned long long)u0, R.s);
+            float2 ta = gen::phase_poly((unsigned long long)u0, R.t);
+            ta.x *= R.c;
+            ta.y *= R.c;
+            Z = gen::make_c2(za, rot(za, R.es));
+            T = gen::make_c2(ta, rot(ta, R.et));
+            const float2 es2 = rot(R.es, R.es), et2 = rot(R.et, R.et);
+            S2 = gen::make_step(es2, es2);
+            T2 = gen::make_step(et2, et2);
+            nku = gen::pk(-(float)u0 * R.inv_l, -(float)(u0 + 1) * R.inv_l);
+            dku = gen::pk(-2.f * R.inv_l, -2.f * R.inv_l);
+        } else {
+            zs = gen::phase_poly((unsigned long long)u0, R.s);
+            es = R.es;
+            ku = (float)u0 * R.inv_l;
+            inv_l = R.inv_l;
+            q = R.q;
+        }
     }
-    __device__ __forceinline__ void next() {
-        d = fmaf(-lam, y, d);
-        y += d;
+    // the next two u: Xt, Xh
+    __device__ __forceinline__ void next2(float &t0, float &t1, float &h0, float &h1) {
+        if (!valid) {
+            t0 = t1 = h0 = h1 = 0.f;
+            return;
+        }
+        if (SAMPLE == 0) {
+            gen::upk(gen::mul2(Z.re, T.im), t0, t1);
+            gen::upk(gen::mul2(nku, gen::mul2(Z.im, T.im)), h0, h1);
+            nku = gen::add2(nku, dku);
+            Z = gen::rot2(Z, S2);
+            T = gen::rot2(T, T2);
+        } else {
+            float tt[2], hh[2];
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                const int m = u + e;
+                const float inv_f = 0.5f * (float)(m > 0 ? m : 1) * inv_l;   // 1 / f_u
+                tt[e] = q * zs.x * inv_f;
+                hh[e] = -q * ku * zs.y * inv_f;
+                zs = rot(zs, es);
+                ku += inv_l;
+            }
+            t0 = tt[0];
+            t1 = tt[1];
+            h0 = hh[0];
+            h1 = hh[1];
+        }
+        u += 2;
     }
 };
 
-// Energy-operand generator: one block, the stage's 32 consecutive u, written as
-// K-major 16-byte rows (4 tf32 or 8 bf16 u each).  SAMPLE 0 (rectangle):
-//   Xt = c cos(pi u s) sin(pi u t)  (c pi t at u = 0),  Xh = -(u pi/W) c sin(pi u s) sin(pi u t);
-// SAMPLE 1 (centre): Xt = q cos(pi u s)/f_u, Xh = -q (u pi/W) sin(pi u s)/f_u.
 template <int PREC, int SAMPLE>
 __device__ __forceinline__ void gen_energy(unsigned char *sb, const AxisRec &R, bool valid, int row,
                                            int u0) {
-    float2 zs = make_float2(0.f, 0.f);
-    SinRec st;
-    st.y = st.d = st.lam = 0.f;
-    float ku = (float)u0 * R.inv_l;                  // u pi / W, advanced by pi / W
-    if (valid) {
-        zs = phase_cs((unsigned long long)u0, R.s);
-        if (SAMPLE == 0) st.init(phase_cs((unsigned long long)u0, R.t), R.et, R.c);
-    }
-    auto value = [&](float &xt, float &xh, int u) {
-        if (SAMPLE == 0) {
-            xt = zs.x * st.y;
-            xh = -ku * (zs.y * st.y);
-            st.next();
-        } else {
-            const float inv_f = 0.5f * (float)(u > 0 ? u : 1) * R.inv_l;   // 1 / f_u
-            xt = R.q * zs.x * inv_f;
-            xh = -R.q * ku * zs.y * inv_f;
-        }
-        zs = rot(zs, R.es);
-        ku += R.inv_l;
-    };
+    // two independent chains: u0..u0+15 (a) and u0+16..u0+31 (b)
+    EnergyChain<SAMPLE> a, b;
+    a.init(R, valid, u0);
+    b.init(R, valid, u0 + 16);
     if (PREC == 1) {
         // [128 rows x 32 u] tf32 K-major: core (row/8, u/4) at (row/8)*1024 + (u/4)*128
         unsigned char *A = sb + (size_t)(row >> 3) * 1024 + (row & 7) * 16;
-#pragma unroll 2
-        for (int c = 0; c < 8; ++c) {
-            float t[4], h[4];
-#pragma unroll
-            for (int j = 0; j < 4; ++j) value(t[j], h[j], u0 + 4 * c + j);
-            if (SAMPLE == 0 && u0 + 4 * c == 0 && valid) t[0] = R.v0;
-            if (!valid) t[0] = t[1] = t[2] = t[3] = h[0] = h[1] = h[2] = h[3] = 0.f;
+#pragma unroll 1
+        for (int c = 0; c < 4; ++c) {
+            float t[4], h[4], tb[4], hb[4];
+            a.next2(t[0], t[1], h[0], h[1]);
+            b.next2(tb[0], tb[1], hb[0], hb[1]);
+            a.next2(t[2], t[3], h[2], h[3]);
+            b.next2(tb[2], tb[3], hb[2], hb[3]);
+            if (SAMPLE == 0 && c == 0 && u0 == 0 && valid) t[0] = R.v0;
             *reinterpret_cast<float4 *>(A + c * 128) =
                 make_float4(to_tf32(t[0]), to_tf32(t[1]), to_tf32(t[2]), to_tf32(t[3]));
             *reinterpret_cast<float4 *>(A + 16384 + c * 128) =
                 make_float4(to_tf32(h[0]), to_tf32(h[1]), to_tf32(h[2]), to_tf32(h[3]));
+            *reinterpret_cast<float4 *>(A + (c + 4) * 128) =
+                make_float4(to_tf32(tb[0]), to_tf32(tb[1]), to_tf32(tb[2]), to_tf32(tb[3]));
+            *reinterpret_cast<float4 *>(A + 16384 + (c + 4) * 128) =
+                make_float4(to_tf32(hb[0]), to_tf32(hb[1]), to_tf32(hb[2]), to_tf32(hb[3]));
         }
     } else {
         // [128 rows x 32 u] bf16 K-major: core (row/8, u/8) at (row/8)*512 + (u/8)*128;
         // regions Xt hi, Xt lo, Xh hi, Xh lo (8 KB each)
         unsigned char *A = sb + (size_t)(row >> 3) * 512 + (row & 7) * 16;
 #pragma unroll 1
-        for (int c = 0; c < 4; ++c) {
-            uint32_t th[4], tl[4], hh[4], hl[4];
+        for (int c = 0; c < 2; ++c) {
+            uint32_t th[4], tl[4], hh[4], hl[4], th2[4], tl2[4], hh2[4], hl2[4];
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
-                float t0, h0, t1, h1;
-                value(t0, h0, u0 + 8 * c + 2 * j);
-                value(t1, h1, u0 + 8 * c + 2 * j + 1);
-                if (SAMPLE == 0 && j == 0 && u0 + 8 * c == 0 && valid) t0 = R.v0;
-                if (!valid) t0 = t1 = h0 = h1 = 0.f;
-                __nv_bfloat16 a0, a1, b0, b1, c0, c1, d0, d1;
-                split_bf16(t0, a0, b0);
-                split_bf16(t1, a1, b1);
-                split_bf16(h0, c0, d0);
-                split_bf16(h1, c1, d1);
-                th[j] = pack_bf16(a0, a1);
-                tl[j] = pack_bf16(b0, b1);
-                hh[j] = pack_bf16(c0, c1);
-                hl[j] = pack_bf16(d0, d1);
+                float t0, t1, h0, h1, q0, q1, g0, g1;
+                a.next2(t0, t1, h0, h1);
+                b.next2(q0, q1, g0, g1);
+                if (SAMPLE == 0 && c == 0 && j == 0 && u0 == 0 && valid) t0 = R.v0;
+                split2(t0, t1, th[j], tl[j]);
+                split2(h0, h1, hh[j], hl[j]);
+                split2(q0, q1, th2[j], tl2[j]);
+                split2(g0, g1, hh2[j], hl2[j]);
             }
             *reinterpret_cast<uint4 *>(A + c * 128) = make_uint4(th[0], th[1], th[2], th[3]);
             *reinterpret_cast<uint4 *>(A + 8192 + c * 128) = make_uint4(tl[0], tl[1], tl[2], tl[3]);
             *reinterpret_cast<uint4 *>(A + 16384 + c * 128) = make_uint4(hh[0], hh[1], hh[2], hh[3]);
             *reinterpret_cast<uint4 *>(A + 24576 + c * 128) = make_uint4(hl[0], hl[1], hl[2], hl[3]);
+            *reinterpret_cast<uint4 *>(A + (c + 2) * 128) = make_uint4(th2[0], th2[1], th2[2], th2[3]);
+            *reinterpret_cast<uint4 *>(A + 8192 + (c + 2) * 128) = make_uint4(tl2[0], tl2[1], tl2[2], tl2[3]);
+            *reinterpret_cast<uint4 *>(A + 16384 + (c + 2) * 128) = make_uint4(hh2[0], hh2[1], hh2[2], hh2[3]);
+            *reinterpret_cast<uint4 *>(A + 24576 + (c + 2) * 128) = make_uint4(hl2[0], hl2[1], hl2[2], hl2[3]);
         }
     }
 }
 
-// CL = CTAs per cluster sharing each K tile: CTA rank 0 multicasts the tile to all
-// of them, and every CTA's MMA completion is signalled to all of them, so a
-// stage buffer is refilled only once every CTA of the cluster has consumed it.
 template <int PREC, int SAMPLE, int CL>
 __global__ void __launch_bounds__(E_THREADS, 1)
 tc_energy_kernel(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ CUtensorMap tm_lo,
                  const EnergyArgs args) {
     extern __shared__ unsigned char smem_raw[];
-    unsigned char *smem = reinterpret_cast<unsigned char *>(
-        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    // 1 KB-aligned base by pointer arithmetic on the __shared__ array, so that the
+    // compiler keeps every access in the shared address space (LDS/STS)
+    unsigned char *smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
     EnergyBars &bars = *reinterpret_cast<EnergyBars *>(smem + E_STAGES * E_STAGE_BYTES);
     volatile int *abort_flag = &bars.abort_flag;
     constexpr bool BF = PREC == 2;
@@ -721,69 +788,75 @@ tc_energy_kernel(const __grid_constant__ CUtensorMap tm_hi, const __grid_constan
         float eN = 0.f, eX = 0.f, eY = 0.f;
         for (int vc = 0; vc < nvc; ++vc) {
             if (*abort_flag) break;
-            // phase anchors for this thread's 128 columns, ahead of the wait
+            // phase anchors for this thread's 128 columns, ahead of the wait;
+            // columns (v, v+1) advance as two packed chains with a 2-mode step
             const int vb = vc * E_VC + chalf * 128;
-            float2 zs = make_float2(1.f, 0.f), zt = make_float2(0.f, 0.f);
+            float2 za = make_float2(1.f, 0.f), ta = make_float2(0.f, 0.f);
             if (valid) {
-                zs = phase_cs((unsigned long long)vb, Ry.s);
-                if (SAMPLE == 0) zt = phase_cs((unsigned long long)vb, Ry.t);
+                za = gen::phase_poly((unsigned long long)vb, Ry.s);
+                if (SAMPLE == 0) ta = gen::phase_poly((unsigned long long)vb, Ry.t);
             }
-            SinRec st;
-            st.init(zt, Ry.et, 1.f);
+            c2 Z = gen::make_c2(za, rot(za, Ry.es)), Tt = gen::make_c2(ta, rot(ta, Ry.et));
+            const float2 es2 = rot(Ry.es, Ry.es), et2 = rot(Ry.et, Ry.et);
+            const gen::rot2_step S2 = gen::make_step(es2, es2), T2 = gen::make_step(et2, et2);
+            f2 nlv = gen::pk(-(float)vb * Ry.inv_l, -(float)(vb + 1) * Ry.inv_l);
+            const f2 dlv = gen::pk(-2.f * Ry.inv_l, -2.f * Ry.inv_l);
+            f2 EN = gen::pk(0.f, 0.f), EX = EN, EY = EN;
+            float2 zs = za;
             float lv = (float)vb * Ry.inv_l;
             if (!mbar_wait(&bars.acc_full, vc & 1, kWaitLimit, abort_flag)) {
                 raise_timeout(args.status, abort_flag);
                 break;
             }
             tc_fence_after();
-            float aN = 0.f, aX = 0.f, aY = 0.f;      // second accumulator set (odd columns)
+            float aN = 0.f, aX = 0.f, aY = 0.f;
 #pragma unroll 1
-            for (int c = chalf * 128; c < chalf * 128 + 128; c += 32) {
-                float t[32], tp[32];
-                const uint32_t ta = tmem + ((uint32_t)(quarter * 32) << 16) + c;
-                tmem_ld16(ta, t);
-                tmem_ld16(ta + 16, t + 16);
-                tmem_ld16(ta + 256, tp);
-                tmem_ld16(ta + 256 + 16, tp + 16);
+            for (int c = chalf * 128; c < chalf * 128 + 128; c += 16) {
+                float t[16], tp[16];
+                const uint32_t ta_ = tmem + ((uint32_t)(quarter * 32) << 16) + c;
+                tmem_ld16(ta_, t);
+                tmem_ld16(ta_ + 256, tp);
                 tmem_ld_wait();
                 if (!valid) continue;
                 if (SAMPLE == 0) {
 #pragma unroll
-                    for (int j = 0; j < 32; j += 2) {
-                        float yt = zs.x * st.y, p = zs.y * st.y;
-                        eN = fmaf(t[j], yt, eN);
-                        eX = fmaf(tp[j], yt, eX);
-                        eY = fmaf(-t[j] * lv, p, eY);
-                        zs = rot(zs, Ry.es);
-                        st.next();
-                        lv += Ry.inv_l;
-                        yt = zs.x * st.y;
-                        p = zs.y * st.y;
-                        aN = fmaf(t[j + 1], yt, aN);
-                        aX = fmaf(tp[j + 1], yt, aX);
-                        aY = fmaf(-t[j + 1] * lv, p, aY);
-                        zs = rot(zs, Ry.es);
-                        st.next();
-                        lv += Ry.inv_l;
+                    for (int j = 0; j < 16; j += 2) {
+                        const f2 tt = gen::pk(t[j], t[j + 1]), ttp = gen::pk(tp[j], tp[j + 1]);
+                        const f2 yt = gen::mul2(Z.re, Tt.im), pr = gen::mul2(Z.im, Tt.im);
+                        EN = gen::fma2(tt, yt, EN);
+                        EX = gen::fma2(ttp, yt, EX);
+                        EY = gen::fma2(gen::mul2(tt, nlv), pr, EY);
+                        nlv = gen::add2(nlv, dlv);
+                        Z = gen::rot2(Z, S2);
+                        Tt = gen::rot2(Tt, T2);
                     }
                     if (c == 0 && vc == 0) {      // v = 0 column: Yt = pi t (not the sine limit 0)
-                        eN = fmaf(t[0], Ry.v0, eN);
-                        eX = fmaf(tp[0], Ry.v0, eX);
+                        aN = fmaf(t[0], Ry.v0, aN);
+                        aX = fmaf(tp[0], Ry.v0, aX);
                     }
                 } else {
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) {
+                    for (int j = 0; j < 16; ++j) {
                         const int v = vc * E_VC + c + j;
                         const float inv_g = 0.5f * (float)(v > 0 ? v : 1) * Ry.inv_l;
                         const float yt = zs.x * inv_g;
                         const float yh = -lv * zs.y * inv_g;
-                        eN = fmaf(t[j], yt, eN);
-                        eY = fmaf(t[j], yh, eY);
-                        eX = fmaf(tp[j], yt, eX);
+                        aN = fmaf(t[j], yt, aN);
+                        aY = fmaf(t[j], yh, aY);
+                        aX = fmaf(tp[j], yt, aX);
                         zs = rot(zs, Ry.es);
                         lv += Ry.inv_l;
                     }
                 }
+            }
+            {
+                float x0, x1;
+                gen::upk(EN, x0, x1);
+                aN += x0 + x1;
+                gen::upk(EX, x0, x1);
+                aX += x0 + x1;
+                gen::upk(EY, x0, x1);
+                aY += x0 + x1;
             }
             tc_fence_before();
             mbar_arrive(&bars.acc_empty);
