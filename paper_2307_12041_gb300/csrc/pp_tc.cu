@@ -4,9 +4,14 @@
 //
 //   tc_coeff_kernel   St = Xt^T Yt (contraction over blocks).  CTA tile 256 (u) x
 //                     256 (v) as two M=128, N=256 accumulators that share the Yt
-//                     operand; persistent over (tile, block slice) units; each
-//                     unit's FP32 sum is written as a partial, the slices are
-//                     summed in FP64 by the finish kernel.
+//                     operand; persistent over (tile, block slice) units.  A
+//                     slice is contracted in chains of at most C_CHAIN blocks:
+//                     the tensor cores' FP32 accumulation rounds toward zero,
+//                     a bias that grows with the number of MMAs accumulated into
+//                     one TMEM value, so each chain starts a fresh accumulator
+//                     and the epilogue adds it (round to nearest) into the
+//                     unit's FP32 partial; the slices are summed with Kahan
+//                     compensation by the finish kernel.
 //   tc_finish_kernel  a = G o (f St g) and K = f a g in the operand precision,
 //                     laid out so that one 3-D TMA box is one pipeline stage.
 //   tc_energy_kernel  T = Xt K and T' = Xh K for 128 blocks per CTA (two
@@ -66,6 +71,7 @@ __device__ __forceinline__ uint32_t pack_bf16(__nv_bfloat16 a, __nv_bfloat16 b) 
 constexpr int C_TILE = 256;                 // u and v edge of a CTA tile
 constexpr int C_KB = 32;                    // blocks per pipeline stage
 constexpr int C_STAGES = 3;
+constexpr int C_CHAIN = 2048;               // most blocks accumulated in one TMEM chain
 constexpr int C_STAGE_BYTES = 65536;        // A 32 KB + B 32 KB (both precisions)
 constexpr int C_GEN_WARPS = 8;
 constexpr int C_EPI_WARPS = 4;
@@ -227,6 +233,19 @@ __device__ __forceinline__ void gen_coeff_bf16(unsigned char *op_hi, unsigned ch
     }
 }
 
+__device__ __forceinline__ void red_add4(float *p, float a, float b, float c, float d) {
+    asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(a), "f"(b), "f"(c), "f"(d)
+                 : "memory");
+}
+
+// Stages per accumulation chain for a unit of nst stages: the fewest chains of at
+// most C_CHAIN blocks, of equal length (the last one possibly shorter).
+__device__ __forceinline__ int chain_stages(int nst) {
+    constexpr int cmax = C_CHAIN / C_KB;
+    const int nch = (nst + cmax - 1) / cmax;
+    return nch > 0 ? (nst + nch - 1) / nch : 1;
+}
+
 template <int PREC>
 __global__ void __launch_bounds__(C_THREADS, 1) tc_coeff_kernel(const CoeffArgs args) {
     extern __shared__ unsigned char smem_raw[];
@@ -265,19 +284,24 @@ __global__ void __launch_bounds__(C_THREADS, 1) tc_coeff_kernel(const CoeffArgs 
         if (lane == 0) {
             constexpr bool BF = PREC == 2;
             const uint32_t idesc = instr_desc(BF ? kFmtBF16 : kFmtTF32, 128, 256, BF, BF);
-            uint32_t it = 0, uc = 0;
-            for (int unit = blockIdx.x; unit < args.units && !*abort_flag; unit += gridDim.x, ++uc) {
+            uint32_t it = 0, dc = 0;     // stages issued, chains committed
+            for (int unit = blockIdx.x; unit < args.units && !*abort_flag; unit += gridDim.x) {
                 const int slice = unit % args.slices;
                 const int b0 = slice * args.slice_len;
                 const int b1 = min(args.n, b0 + args.slice_len);
                 const int nst = (b1 - b0 + C_KB - 1) / C_KB;
-                if (uc > 0 && !mbar_wait(&bars.acc_empty, (uc - 1) & 1, kWaitLimit, abort_flag)) {
-                    raise_timeout(args.status, abort_flag);
-                    break;
-                }
-                tc_fence_after();
+                const int cst = chain_stages(nst);
                 for (int st = 0; st < nst; ++st, ++it) {
                     const int s = it % C_STAGES;
+                    const int sc = st % cst;    // stage within the chain
+                    if (sc == 0) {
+                        // the epilogue has read the previous chain out of TMEM
+                        if (dc > 0 && !mbar_wait(&bars.acc_empty, (dc - 1) & 1, kWaitLimit, abort_flag)) {
+                            raise_timeout(args.status, abort_flag);
+                            break;
+                        }
+                        tc_fence_after();
+                    }
                     if (!mbar_wait(&bars.full[s], (it / C_STAGES) & 1, kWaitLimit, abort_flag)) {
                         raise_timeout(args.status, abort_flag);
                         break;
@@ -293,7 +317,7 @@ __global__ void __launch_bounds__(C_THREADS, 1) tc_coeff_kernel(const CoeffArgs 
 #pragma unroll
                             for (int acc = 0; acc < 2; ++acc) {
                                 const uint64_t ad = smem_desc(A + acc * 16384 + kk * 256, 128, 1024);
-                                mma_tf32(tmem + acc * 256, ad, bd, idesc, st > 0 || kk > 0);
+                                mma_tf32(tmem + acc * 256, ad, bd, idesc, sc > 0 || kk > 0);
                             }
                         }
                     } else {
@@ -310,7 +334,7 @@ __global__ void __launch_bounds__(C_THREADS, 1) tc_coeff_kernel(const CoeffArgs 
                                 const uint32_t mo = acc * 2048;
                                 const uint64_t ah = smem_desc(Ah + mo + ko, 4096, 128);
                                 const uint64_t al = smem_desc(Al + mo + ko, 4096, 128);
-                                const bool accum = st > 0 || kk > 0;
+                                const bool accum = sc > 0 || kk > 0;
                                 mma_bf16(tmem + acc * 256, al, bh, idesc, accum);
                                 mma_bf16(tmem + acc * 256, ah, bl, idesc, true);
                                 mma_bf16(tmem + acc * 256, ah, bh, idesc, true);
@@ -318,9 +342,11 @@ __global__ void __launch_bounds__(C_THREADS, 1) tc_coeff_kernel(const CoeffArgs 
                         }
                     }
                     mma_commit(&bars.empty[s]);
+                    if (sc == cst - 1 || st == nst - 1) {
+                        mma_commit(&bars.acc_full);
+                        ++dc;
+                    }
                 }
-                if (*abort_flag) break;
-                mma_commit(&bars.acc_full);
             }
             // all MMAs issued by this thread complete before the TMEM is freed
             mma_commit(&bars.drain);
@@ -331,32 +357,43 @@ __global__ void __launch_bounds__(C_THREADS, 1) tc_coeff_kernel(const CoeffArgs 
         // ---------------- epilogue: TMEM -> FP32 partial tile ----------------
         const int quarter = warp & 3;
         const int row = quarter * 32 + lane;
-        uint32_t uc = 0;
-        for (int unit = blockIdx.x; unit < args.units; unit += gridDim.x, ++uc) {
+        uint32_t dc = 0;
+        for (int unit = blockIdx.x; unit < args.units; unit += gridDim.x) {
             if (*abort_flag) break;
             const int tile = unit / args.slices, slice = unit % args.slices;
             const int tu = tile / tiles_v, tv = tile % tiles_v;
-            if (!mbar_wait(&bars.acc_full, uc & 1, kWaitLimit, abort_flag)) {
-                raise_timeout(args.status, abort_flag);
-                break;
-            }
-            tc_fence_after();
+            const int b0 = slice * args.slice_len;
+            const int nst = (min(args.n, b0 + args.slice_len) - b0 + C_KB - 1) / C_KB;
+            const int nch = (nst + chain_stages(nst) - 1) / chain_stages(nst);
 #pragma unroll 1
-            for (int acc = 0; acc < 2; ++acc) {
-                const int u = tu * C_TILE + acc * 128 + row;
-                float *dst = args.part + ((size_t)slice * args.Mxc + u) * args.Myc + tv * C_TILE;
-#pragma unroll 1
-                for (int c = 0; c < 256; c += 16) {
-                    float v[16];
-                    tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + acc * 256 + c, v);
-                    tmem_ld_wait();
-#pragma unroll
-                    for (int j = 0; j < 16; j += 4)
-                        *reinterpret_cast<float4 *>(dst + c + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+            for (int ch = 0; ch < nch; ++ch, ++dc) {
+                if (!mbar_wait(&bars.acc_full, dc & 1, kWaitLimit, abort_flag)) {
+                    raise_timeout(args.status, abort_flag);
+                    break;
                 }
+                tc_fence_after();
+#pragma unroll 1
+                for (int acc = 0; acc < 2; ++acc) {
+                    const int u = tu * C_TILE + acc * 128 + row;
+                    float *dst = args.part + ((size_t)slice * args.Mxc + u) * args.Myc + tv * C_TILE;
+#pragma unroll 1
+                    for (int c = 0; c < 256; c += 16) {
+                        float v[16];
+                        tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + acc * 256 + c, v);
+                        tmem_ld_wait();
+#pragma unroll
+                        for (int j = 0; j < 16; j += 4) {
+                            if (ch == 0)
+                                *reinterpret_cast<float4 *>(dst + c + j) =
+                                    make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+                            else    // added in L2 (round to nearest) after this thread's earlier store
+                                red_add4(dst + c + j, v[j], v[j + 1], v[j + 2], v[j + 3]);
+                        }
+                    }
+                }
+                tc_fence_before();
+                mbar_arrive(&bars.acc_empty);
             }
-            tc_fence_before();
-            mbar_arrive(&bars.acc_empty);
         }
     } else if (warp < C_LOADER_WARP) {
         // ---------------- basis generators ----------------

@@ -181,3 +181,29 @@ def test_full_size_workload_sampled(pp, big, prec):
     assert e <= tol, (prec, "grad", e)
     # E from the GPU's per-block energies equals the GPU's FP64 total
     assert abs(out["E"] - 0.5 * float(out["N"].double().sum())) <= 1e-6 * abs(out["E"])
+
+
+# ---------------------------------------------------------------------------
+# 1,000,000 blocks, 1024 x 1024 modes (the BF16x3 workload): coefficients in full
+# and 2,000 sampled blocks' energies and gradients.
+# ---------------------------------------------------------------------------
+
+@pytest.fixture(scope="module")
+def million():
+    p = synth.workload(2)
+    a = O.coefficients(p.W, p.H, p.x, p.y, p.w, p.h, p.c, p.Mx, p.My)
+    idx = np.sort(np.random.default_rng(6).choice(p.n, 2000, replace=False))
+    N, gx, gy = O.energy_grad(p.W, p.H, p.x, p.y, p.w, p.h, p.c, a, idx=idx)
+    return p, a, idx, dict(N=N, gx=gx, gy=gy)
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("prec", ["bf16x3", "fp32", "tf32"])
+def test_million_block_workload_sampled(pp, million, prec):
+    p, a_ref, idx, ref = million
+    out = pp.binding.evaluate(p, prec=prec)
+    tol = pp.binding.TOLERANCE[prec]
+    assert nerr(out["a"].double().cpu().numpy(), a_ref) <= tol
+    ti = torch.from_numpy(idx).cuda()
+    assert nerr(out["N"][ti].double().cpu().numpy(), ref["N"]) <= tol
+    assert gerr(out["gx"][ti].double().cpu().numpy(), out["gy"][ti].double().cpu().numpy(), ref) <= tol
