@@ -40,6 +40,35 @@ FP32_LANES_PER_SM = 128
 SM_COUNT_GB300 = 152
 
 
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the
+# tensor-core kernels on this workload, from one `ncu --set full` capture each
+# (profiles/tc_coeff_tf32_cellmix-200k-512x512.md and
+# profiles/tc_energy_tf32_cellmix-200k-512x512.md), valid only while the kernel
+# sources hash to the digest they were captured with.
+NCU_TRAFFIC = {
+    "digest": "026e66b896527a20",
+    ("tf32", "coeff"): 28.136192e6 + 29.166592e6,
+    ("tf32", "energy"): 26.677248e6 + 0.0,
+}
+
+
+def kernel_source_digest() -> str:
+    import hashlib
+    import glob
+    h = hashlib.sha256()
+    for f in sorted(glob.glob(os.path.join(ROOT, "paper_2307_12041_gb300", "csrc", "*"))):
+        h.update(os.path.basename(f).encode())
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(prec: str, kernel: str):
+    if kernel_source_digest() != NCU_TRAFFIC["digest"]:
+        return None
+    return NCU_TRAFFIC.get((prec, kernel))
+
+
 def load_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -338,7 +367,8 @@ def run_ours(args):
                    "l2": "flushed: 256 MiB written before every timed step",
                    "parallelism": f"replicas x{world}"},
         "roofline": {"bound": bound, "kernel": dom, "achieved": achieved, "peak": peak,
-                     "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                     "unit": "TFLOP/s", "frac": achieved / peak,
+                     "traffic": ncu_traffic(prec, dom),
                      "peak_source": peak_note,
                      "flops_per_launch": flops},
         "kernels_ms_per_step": {k: v[1] / args.steps for k, v in ktimes.items()},
