@@ -166,6 +166,14 @@ def reduce_max(value: float, world: int, device=None) -> float:
     return float(t.item())
 
 
+def whole_job_throughput(units_per_rank: float, steps: int, rank_ms: float, world: int,
+                         device=None):
+    """(units/s over all ranks, slowest rank's ms): every rank processes
+    `units_per_rank` per step; the job takes as long as its slowest rank."""
+    total_ms = reduce_max(rank_ms, world, device)
+    return world * units_per_rank * steps / (total_ms / 1e3), total_ms
+
+
 def barrier(world):
     if world > 1:
         import torch.distributed as dist
@@ -334,9 +342,8 @@ def run_ours(args):
     barrier(world)
     clk = clocks.stop()
 
-    total_ms = reduce_max(sum(step_ms), world, device)
+    value, total_ms = whole_job_throughput(terms, args.steps, sum(step_ms), world, device)
     ms_per_step = total_ms / args.steps
-    value = world * terms * args.steps / (total_ms / 1e3)
 
     launches = int(sum(v[0] for v in ktimes.values()))     # our kernels in the timed steps
     peaks, peak_src = load_peaks()

@@ -135,6 +135,16 @@ pp_status pp_grad_noalloc(const pp_problem *prob, pp_sample sample, float *gx, f
  * PP_OK, or PP_ETIMEOUT if a kernel gave up a bounded wait since the last check. */
 pp_status pp_sync_status(void *stream);
 
+/* Failure-path check (no counterpart in the paper).  Launches, on `stream`, one
+ * kernel whose thread waits on a shared-memory mbarrier that nothing completes,
+ * through the same time-bounded wait the tensor-core kernels use between their
+ * pipeline stages.  After `limit_ns` nanoseconds (clamped to [1e3, 5e9]) the wait
+ * gives up and the kernel records the timeout in the device status word and
+ * returns, as a stalled pipeline would; the next pp_sync_status() reports
+ * PP_ETIMEOUT and the context stays usable.  Returns PP_ENOTSUP below compute
+ * capability 9.0, PP_ECUDA if the launch fails. */
+pp_status pp_check_wait_timeout(uint64_t limit_ns, void *stream);
+
 /* Message for the calling thread's last non-OK status ("" if none). */
 const char *pp_last_error(void);
 

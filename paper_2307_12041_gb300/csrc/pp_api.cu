@@ -407,6 +407,19 @@ pp_status pp_sync_status(void *stream) {
     return PP_OK;
 }
 
+pp_status pp_check_wait_timeout(uint64_t limit_ns, void *stream) {
+    int dev, sm, ccm;
+    unsigned *status;
+    pp_status st = device_info(&dev, &sm, &status, &ccm);
+    if (st != PP_OK) return st;
+    if (ccm < 9) return fail(PP_ENOTSUP, "mbarrier waits need compute capability 9.0 or newer");
+    if (limit_ns < 1000) limit_ns = 1000;
+    if (limit_ns > 5000000000ull) limit_ns = 5000000000ull;
+    cudaError_t e = launch_wait_probe(limit_ns, status, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "wait probe launch");
+    return PP_OK;
+}
+
 const char *pp_last_error(void) { return t_err.c_str(); }
 
 void pp_timing_enable(int on) { g_timing.store(on != 0); }

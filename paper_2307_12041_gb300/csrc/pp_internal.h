@@ -46,6 +46,8 @@ cudaError_t launch_energy_tc(const Launch &L, int prec, int sample, const TcPlan
 
 // pp_api.cu: message returned by pp_last_error() for the calling thread
 void set_last_error(const char *msg);
+// one CTA whose thread waits (bounded) on an mbarrier nothing completes
+cudaError_t launch_wait_probe(uint64_t limit_ns, unsigned *status, cudaStream_t stream);
 
 // pp_simt.cu
 cudaError_t launch_prep(const Launch &L, bool zero_S, double *e_total);

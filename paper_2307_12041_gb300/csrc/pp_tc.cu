@@ -1003,6 +1003,24 @@ cudaError_t make_kmap(CUtensorMap *map, void *base, bool bf16, int Mxe, int Mye)
 
 }  // namespace
 
+namespace {
+__global__ void wait_probe_kernel(uint64_t limit_ns, unsigned *status) {
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+    // phase 0 never completes: nothing arrives on the barrier
+    if (threadIdx.x == 0 && !mbar_wait(&bar, 0, limit_ns, nullptr)) atomicOr(status, 1u);
+}
+}  // namespace
+
+cudaError_t launch_wait_probe(uint64_t limit_ns, unsigned *status, cudaStream_t stream) {
+    wait_probe_kernel<<<1, 32, 0, stream>>>(limit_ns, status);
+    return cudaGetLastError();
+}
+
 TcPlan tc_plan(int n, int Mx, int My) {
     TcPlan p{};
     p.Mxc = round_up(Mx, C_TILE);
