@@ -135,6 +135,19 @@ pp_status pp_grad_noalloc(const pp_problem *prob, pp_sample sample, float *gx, f
  * PP_OK, or PP_ETIMEOUT if a kernel gave up a bounded wait since the last check. */
 pp_status pp_sync_status(void *stream);
 
+/* Phase step of the basis generators (the cos/sin factors of Eq. aup), exposed
+ * for testing.  For i < count: s = x[i] / L reduced to [0, 2) and held as 64-bit
+ * fixed point (2^-62 half-turn units), exactly as the per-block records hold it;
+ * then out[2i], out[2i+1] = cos, sin of pi * (m[i] * s mod 2), evaluated by
+ * `evaluator` 0 (the records' and CUDA-core kernels' evaluator: sincospif of the
+ * top 24 phase bits plus a first-order residual rotation) or 1 (the tensor-core
+ * generators' anchor: quarter-turn reduction and Taylor polynomials).
+ * x (float32), m (int32, >= 0) and out (float32, 2 * count) are device arrays.
+ * PP_EINVAL for L not finite and > 0, count < 0, NULL or host pointers, or an
+ * unknown evaluator; asynchronous on `stream`. */
+pp_status pp_phase_eval(const float *x, double L, const int32_t *m, int64_t count, int evaluator,
+                        float *out, void *stream);
+
 /* Failure-path check (no counterpart in the paper).  Launches, on `stream`, one
  * kernel whose thread waits on a shared-memory mbarrier that nothing completes,
  * through the same time-bounded wait the tensor-core kernels use between their

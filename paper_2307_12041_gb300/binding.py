@@ -67,6 +67,8 @@ def lib() -> ctypes.CDLL:
         L.pp_grad.restype = i
         L.pp_sync_status.argtypes = [vp]
         L.pp_sync_status.restype = i
+        L.pp_phase_eval.argtypes = [vp, ctypes.c_double, vp, ctypes.c_int64, i, vp, vp]
+        L.pp_phase_eval.restype = i
         L.pp_check_wait_timeout.argtypes = [ctypes.c_uint64, vp]
         L.pp_check_wait_timeout.restype = i
         L.pp_last_error.argtypes = []
@@ -219,6 +221,19 @@ def sync_status(device=None):
     """pp_sync_status on the current stream: raises PPError if a kernel timed out."""
     dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
     _check(lib().pp_sync_status(_stream_handle(dev)))
+
+
+def phase_eval(x, L: float, m, evaluator: int = 0):
+    """pp_phase_eval: (cos, sin)(pi * (m * x / L mod 2)) per element, shape (count, 2);
+    x float32 and m int32 device tensors of equal length."""
+    x = x.contiguous()
+    m = m.contiguous()
+    if x.dtype != torch.float32 or m.dtype != torch.int32 or x.numel() != m.numel():
+        raise ValueError("x must be float32 and m int32, of equal length")
+    out = torch.empty((x.numel(), 2), dtype=torch.float32, device=x.device)
+    _check(lib().pp_phase_eval(_ptr(x), float(L), _ptr(m), x.numel(), int(evaluator), _ptr(out),
+                               _stream_handle(x.device)))
+    return out
 
 
 def check_wait_timeout(limit_ns: int, device=None):

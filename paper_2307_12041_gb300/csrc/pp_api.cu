@@ -407,6 +407,24 @@ pp_status pp_sync_status(void *stream) {
     return PP_OK;
 }
 
+pp_status pp_phase_eval(const float *x, double L, const int32_t *m, int64_t count, int evaluator,
+                        float *out, void *stream) {
+    int dev, sm, ccm;
+    unsigned *status;
+    pp_status st = device_info(&dev, &sm, &status, &ccm);
+    if (st != PP_OK) return st;
+    if (!(std::isfinite(L) && L > 0.0)) return fail(PP_EINVAL, "L must be finite and > 0");
+    if (count < 0) return fail(PP_EINVAL, "count must be >= 0");
+    if (evaluator != 0 && evaluator != 1) return fail(PP_EINVAL, "evaluator must be 0 or 1");
+    if (count == 0) return PP_OK;
+    if ((st = check_dev_ptr(x, dev, "x")) != PP_OK) return st;
+    if ((st = check_dev_ptr(m, dev, "m")) != PP_OK) return st;
+    if ((st = check_dev_ptr(out, dev, "out")) != PP_OK) return st;
+    cudaError_t e = launch_phase_eval(x, 1.0 / L, m, count, evaluator, out, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "phase evaluation launch");
+    return PP_OK;
+}
+
 pp_status pp_check_wait_timeout(uint64_t limit_ns, void *stream) {
     int dev, sm, ccm;
     unsigned *status;

@@ -63,7 +63,5 @@ __device__ __forceinline__ unsigned long long to_fixed_halfturns(double s) {
     return (unsigned long long)f & 0x7FFFFFFFFFFFFFFFull;
 }
 
-// Bounded spin on an mbarrier phase; returns false if it ran out.
-constexpr unsigned kSpinLimit = 1u << 26;
 
 }  // namespace pp

@@ -46,6 +46,8 @@ cudaError_t launch_energy_tc(const Launch &L, int prec, int sample, const TcPlan
 
 // pp_api.cu: message returned by pp_last_error() for the calling thread
 void set_last_error(const char *msg);
+cudaError_t launch_phase_eval(const float *x, double invL, const int32_t *m, int64_t count,
+                              int evaluator, float *out, cudaStream_t stream);
 // one CTA whose thread waits (bounded) on an mbarrier nothing completes
 cudaError_t launch_wait_probe(uint64_t limit_ns, unsigned *status, cudaStream_t stream);
 

@@ -1016,6 +1016,28 @@ __global__ void wait_probe_kernel(uint64_t limit_ns, unsigned *status) {
 }
 }  // namespace
 
+namespace {
+__global__ void phase_eval_kernel(const float *__restrict__ x, double invL, const int32_t *__restrict__ m,
+                                  int64_t count, int evaluator, float2 *__restrict__ out) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const unsigned long long s = to_fixed_halfturns((double)x[i] * invL);
+        const unsigned long long mm = (unsigned long long)m[i];
+        out[i] = evaluator == 0 ? phase_cs(mm, s) : gen::phase_poly(mm, s);
+    }
+}
+}  // namespace
+
+cudaError_t launch_phase_eval(const float *x, double invL, const int32_t *m, int64_t count,
+                              int evaluator, float *out, cudaStream_t stream) {
+    if (count == 0) return cudaSuccess;
+    const int64_t want = (count + 255) / 256;
+    const int grid = (int)(want < 4096 ? want : 4096);
+    phase_eval_kernel<<<grid, 256, 0, stream>>>(x, invL, m, count, evaluator,
+                                                reinterpret_cast<float2 *>(out));
+    return cudaGetLastError();
+}
+
 cudaError_t launch_wait_probe(uint64_t limit_ns, unsigned *status, cudaStream_t stream) {
     wait_probe_kernel<<<1, 32, 0, stream>>>(limit_ns, status);
     return cudaGetLastError();
