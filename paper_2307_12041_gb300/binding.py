@@ -41,7 +41,7 @@ class Problem(ctypes.Structure):
 _LIB = None
 EXPORTS = ("pp_workspace_size", "pp_coeffs", "pp_energy", "pp_grad", "pp_sync_status",
            "pp_last_error", "pp_version", "pp_timing_enable", "pp_timing_collect",
-           "pp_grad_noalloc")
+           "pp_grad_noalloc", "pp_phase_eval", "pp_check_wait_timeout")
 
 
 def lib_path() -> str:

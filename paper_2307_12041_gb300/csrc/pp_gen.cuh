@@ -5,36 +5,25 @@
 
 #include <cstdint>
 
+#include <cuda_runtime.h>
+
 namespace pp {
 namespace gen {
 
 // ---- packed FP32 pairs ------------------------------------------------------
+// Built on the float2 builtins (__ffma2_rn and friends), which the compiler
+// keeps as single packed instructions on register pairs.
 struct f2 {
-    unsigned long long v;
+    float2 v;
 };
-__device__ __forceinline__ f2 pk(float a, float b) {
-    f2 r;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(r.v) : "f"(a), "f"(b));
-    return r;
-}
+__device__ __forceinline__ f2 pk(float a, float b) { return f2{make_float2(a, b)}; }
 __device__ __forceinline__ void upk(f2 a, float &x, float &y) {
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(x), "=f"(y) : "l"(a.v));
+    x = a.v.x;
+    y = a.v.y;
 }
-__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) {
-    f2 d;
-    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d.v) : "l"(a.v), "l"(b.v), "l"(c.v));
-    return d;
-}
-__device__ __forceinline__ f2 mul2(f2 a, f2 b) {
-    f2 d;
-    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d.v) : "l"(a.v), "l"(b.v));
-    return d;
-}
-__device__ __forceinline__ f2 add2(f2 a, f2 b) {
-    f2 d;
-    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d.v) : "l"(a.v), "l"(b.v));
-    return d;
-}
+__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) { return f2{__ffma2_rn(a.v, b.v, c.v)}; }
+__device__ __forceinline__ f2 mul2(f2 a, f2 b) { return f2{__fmul2_rn(a.v, b.v)}; }
+__device__ __forceinline__ f2 add2(f2 a, f2 b) { return f2{__fadd2_rn(a.v, b.v)}; }
 
 // Two complex numbers held as packed real parts and packed imaginary parts.
 struct c2 {

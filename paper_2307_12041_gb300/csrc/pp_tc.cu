@@ -73,7 +73,8 @@ constexpr int C_KB = 32;                    // blocks per pipeline stage
 constexpr int C_STAGES = 3;
 constexpr int C_CHAIN = 2048;               // most blocks accumulated in one TMEM chain
 constexpr int C_STAGE_BYTES = 65536;        // A 32 KB + B 32 KB (both precisions)
-constexpr int C_GEN_WARPS = 8;
+constexpr int C_GEN_GROUPS = 2;            // generator groups filling alternate stages
+constexpr int C_GEN_WARPS = 8 * C_GEN_GROUPS;
 constexpr int C_EPI_WARPS = 4;
 constexpr int C_LOADER_WARP = 1 + C_EPI_WARPS + C_GEN_WARPS;     // copies per-block records
 constexpr int C_THREADS = 32 * (C_LOADER_WARP + 1);
@@ -259,7 +260,7 @@ __global__ void __launch_bounds__(C_THREADS, 1) tc_coeff_kernel(const CoeffArgs 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
         for (int s = 0; s < C_STAGES; ++s) {
-            mbar_init(&bars.full[s], C_GEN_WARPS * 32);
+            mbar_init(&bars.full[s], (C_GEN_WARPS / C_GEN_GROUPS) * 32);   // one group per stage
             mbar_init(&bars.empty[s], 1);
             mbar_init(&bars.recs_full[s], 1);
         }
@@ -397,8 +398,11 @@ __global__ void __launch_bounds__(C_THREADS, 1) tc_coeff_kernel(const CoeffArgs 
         }
     } else if (warp < C_LOADER_WARP) {
         // ---------------- basis generators ----------------
-        const int g = threadIdx.x - 32 * (1 + C_EPI_WARPS);    // 0..255
-        const int which = g >> 7;                              // 0: Xt (A), 1: Yt (B)
+        // group gr fills the stages it with it % C_GEN_GROUPS == gr, so two stages are
+        // generated at once and each group's latency is hidden behind the other's
+        const int g = threadIdx.x - 32 * (1 + C_EPI_WARPS);    // 0..511
+        const int gr = g >> 8;
+        const int which = (g >> 7) & 1;                        // 0: Xt (A), 1: Yt (B)
         const int gg = g & 127;
         uint32_t it = 0;
         for (int unit = blockIdx.x; unit < args.units; unit += gridDim.x) {
@@ -409,6 +413,7 @@ __global__ void __launch_bounds__(C_THREADS, 1) tc_coeff_kernel(const CoeffArgs 
             const int nst = (b1 - b0 + C_KB - 1) / C_KB;
             for (int st = 0; st < nst; ++st, ++it) {
                 if (*abort_flag) break;
+                if ((int)(it % C_GEN_GROUPS) != gr) continue;
                 const int s = it % C_STAGES;
                 if (!mbar_wait(&bars.recs_full[s], (it / C_STAGES) & 1, kWaitLimit, abort_flag) ||
                     (it >= C_STAGES &&

@@ -211,10 +211,14 @@ __device__ __forceinline__ void tma_load_3d(void *dst_smem, const void *tmap, in
 }
 
 // Round an FP32 value to TF32 (nearest, ties away), kept in an FP32 container.
+// FP32 -> TF32 (10-bit mantissa), round to nearest with ties away from zero, for
+// finite inputs whose rounding does not overflow: adding half a TF32 unit to the
+// sign-magnitude bit pattern rounds the magnitude, the mask clears the 13 dropped
+// bits.  Same result as cvt.rna.tf32.f32 on that range, at two integer
+// operations instead of that conversion's longer sequence; every operand here
+// is finite and bounded.
 __device__ __forceinline__ float to_tf32(float x) {
-    uint32_t r;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-    return __uint_as_float(r);
+    return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
 }
 
 }  // namespace tc
