@@ -34,7 +34,7 @@
  *    GPU detects while running (a bounded wait that ran out) are recorded in a
  *    per-device status word that pp_sync_status() reads and clears.
  *  - n = 0 is valid: outputs are zero (a all zero, *e_total = 0).
- *  - Limits: 1 <= Mx, My <= 4096; 0 <= n <= 2^31 - 1; W, H finite and > 0.
+ *  - Limits: 1 <= Mx, My <= 4096; 0 <= n <= 2^31 - 1; 1e-300 <= W, H <= 1e300.
  *  - pp_last_error() describes the last non-OK status of the calling thread.
  */
 #ifndef PP_H
@@ -136,14 +136,15 @@ pp_status pp_grad_noalloc(const pp_problem *prob, pp_sample sample, float *gx, f
 pp_status pp_sync_status(void *stream);
 
 /* Phase step of the basis generators (the cos/sin factors of Eq. aup), exposed
- * for testing.  For i < count: s = x[i] / L reduced to [0, 2) and held as 64-bit
- * fixed point (2^-62 half-turn units), exactly as the per-block records hold it;
+ * for testing.  For i < count: s = x[i] * (1/L) (the float32 x times the double
+ * 1/L, exact product) reduced to [0, 2) and rounded to 64-bit fixed point
+ * (2^-62 half-turn units), exactly as the per-block records hold it;
  * then out[2i], out[2i+1] = cos, sin of pi * (m[i] * s mod 2), evaluated by
  * `evaluator` 0 (the records' and CUDA-core kernels' evaluator: sincospif of the
  * top 24 phase bits plus a first-order residual rotation) or 1 (the tensor-core
  * generators' anchor: quarter-turn reduction and Taylor polynomials).
  * x (float32), m (int32, >= 0) and out (float32, 2 * count) are device arrays.
- * PP_EINVAL for L not finite and > 0, count < 0, NULL or host pointers, or an
+ * PP_EINVAL for L outside [1e-300, 1e300], count < 0, NULL or host pointers, or an
  * unknown evaluator; asynchronous on `stream`. */
 pp_status pp_phase_eval(const float *x, double L, const int32_t *m, int64_t count, int evaluator,
                         float *out, void *stream);

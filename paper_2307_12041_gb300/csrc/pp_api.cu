@@ -131,8 +131,9 @@ pp_status check_dev_ptr(const void *ptr, int dev, const char *name) {
 // Shape checks only (no pointers): die, counts, precision.
 pp_status check_shape(const pp_problem *p, pp_precision prec) {
     if (!p) return fail(PP_EINVAL, "problem is NULL");
-    if (!std::isfinite(p->W) || !std::isfinite(p->H) || p->W <= 0 || p->H <= 0)
-        return fail(PP_EINVAL, "die size W=%g H=%g must be finite and > 0", p->W, p->H);
+    if (!std::isfinite(p->W) || !std::isfinite(p->H) || !(p->W >= 1e-300 && p->W <= 1e300) ||
+        !(p->H >= 1e-300 && p->H <= 1e300))
+        return fail(PP_EINVAL, "die size W=%g H=%g must be finite and in [1e-300, 1e300]", p->W, p->H);
     if (p->n < 0 || p->n > 2147483647LL)
         return fail(PP_EINVAL, "n=%lld out of range [0, 2^31-1]", (long long)p->n);
     if (p->Mx < 1 || p->My < 1 || p->Mx > 4096 || p->My > 4096)
@@ -413,7 +414,8 @@ pp_status pp_phase_eval(const float *x, double L, const int32_t *m, int64_t coun
     unsigned *status;
     pp_status st = device_info(&dev, &sm, &status, &ccm);
     if (st != PP_OK) return st;
-    if (!(std::isfinite(L) && L > 0.0)) return fail(PP_EINVAL, "L must be finite and > 0");
+    if (!(std::isfinite(L) && L >= 1e-300 && L <= 1e300))
+        return fail(PP_EINVAL, "L must be finite and in [1e-300, 1e300]");
     if (count < 0) return fail(PP_EINVAL, "count must be >= 0");
     if (evaluator != 0 && evaluator != 1) return fail(PP_EINVAL, "evaluator must be 0 or 1");
     if (count == 0) return PP_OK;

@@ -57,10 +57,39 @@ __device__ __forceinline__ float2 rot(float2 z, float2 e) {
     return make_float2(fmaf(z.x, e.x, -z.y * e.y), fmaf(z.y, e.x, z.x * e.y));
 }
 
-__device__ __forceinline__ unsigned long long to_fixed_halfturns(double s) {
-    double r = s - 2.0 * floor(0.5 * s);          // [0, 2)
-    long long f = __double2ll_rn(r * 0x1p62);     // [0, 2^63]
-    return (unsigned long long)f & 0x7FFFFFFFFFFFFFFFull;
+// (x * k) mod 2 in units of 2^-62 half-turns, for a float32 x and a positive
+// normal double k, from the exact 77-bit product of the two significands
+// (integer arithmetic only: FP64 is a narrow pipe on this GPU), rounded to the
+// nearest unit (ties away from zero), then reduced mod 2.  Used for s = x / L and
+// t = w / (2L) with k = 1/L, 1/(2L).
+__device__ __forceinline__ unsigned long long fixed_halfturns(float x, double k) {
+    const unsigned xb = __float_as_uint(x);
+    const int xe = (int)((xb >> 23) & 0xFFu);
+    if ((xb & 0x7FFFFFFFu) == 0u || xe == 0xFF) return 0ull;      // zero (or not finite)
+    const unsigned long long mx = (unsigned long long)((xb & 0x7FFFFFu) | (xe ? 0x800000u : 0u));
+    const unsigned long long kb = (unsigned long long)__double_as_longlong(k);
+    const unsigned long long mk = (kb & 0xFFFFFFFFFFFFFull) | 0x10000000000000ull;
+    // value * 2^62 = mx * mk * 2^sh
+    const int sh = (xe ? xe : 1) - 150 + ((int)((kb >> 52) & 0x7FF) - 1075) + 62;
+    const unsigned long long lo = mx * mk, hi = __umul64hi(mx, mk);   // mx * mk < 2^77
+    constexpr unsigned long long M63 = 0x7FFFFFFFFFFFFFFFull;
+    unsigned long long q;
+    if (sh >= 0) {
+        q = sh >= 63 ? 0ull : (lo << sh);
+    } else {
+        const int r = -sh;
+        if (r >= 78) {
+            q = 0ull;
+        } else if (r < 64) {
+            q = (lo >> r) | (r ? (hi << (64 - r)) : 0ull);
+            q += (lo >> (r - 1)) & 1ull;                                // r >= 1 here
+        } else {
+            q = hi >> (r - 64);
+            q += (r == 64 ? (lo >> 63) : (hi >> (r - 65))) & 1ull;
+        }
+    }
+    q &= M63;
+    return (xb >> 31) ? ((0ull - q) & M63) : q;
 }
 
 

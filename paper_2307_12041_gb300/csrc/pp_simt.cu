@@ -24,39 +24,40 @@ namespace pp {
 // ---------------------------------------------------------------------------
 __global__ void prep_kernel(const float *__restrict__ x, const float *__restrict__ y,
                             const float *__restrict__ w, const float *__restrict__ h,
-                            const float *__restrict__ c, int n, double W, double H,
-                            AxisRec *__restrict__ xr, AxisRec *__restrict__ yr,
+                            const float *__restrict__ c, int n, double invW, double invH,
+                            float piW, float piH, AxisRec *__restrict__ xr, AxisRec *__restrict__ yr,
                             double *__restrict__ S64, size_t nS, double *e_total) {
+    // FP32 and integer arithmetic only (FP64 is a narrow pipe on this GPU)
     const size_t tid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     const size_t stride = (size_t)gridDim.x * blockDim.x;
-    const double invW = 1.0 / W, invH = 1.0 / H;
-    const double PI = 3.141592653589793;
-    for (size_t i = tid; i < (size_t)n; i += stride) {
-        const double xi = x[i], yi = y[i], wi = w[i], hi = h[i];
-        const double ci = c ? (double)c[i] : 1.0;
-        AxisRec rx, ry;
-        rx.s = to_fixed_halfturns(xi * invW);
-        rx.t = to_fixed_halfturns(0.5 * wi * invW);
-        rx.es = phase_cs(1, rx.s);
-        rx.et = phase_cs(1, rx.t);
-        rx.v0 = (float)(ci * PI * 0.5 * wi * invW);
-        rx.q = (float)(ci * wi * hi);
-        rx.c = (float)ci;
-        rx.inv_l = (float)(PI * invW);
-        rx.es8 = phase_cs(8, rx.s);
-        rx.et8 = phase_cs(8, rx.t);
-        ry.s = to_fixed_halfturns(yi * invH);
-        ry.t = to_fixed_halfturns(0.5 * hi * invH);
-        ry.es = phase_cs(1, ry.s);
-        ry.et = phase_cs(1, ry.t);
-        ry.v0 = (float)(PI * 0.5 * hi * invH);
-        ry.q = 1.0f;
-        ry.c = 1.0f;
-        ry.inv_l = (float)(PI * invH);
-        ry.es8 = phase_cs(8, ry.s);
-        ry.et8 = phase_cs(8, ry.t);
-        xr[i] = rx;
-        yr[i] = ry;
+    const double halfW = 0.5 * invW, halfH = 0.5 * invH;       // exact: powers of two
+    // work item i < n: the x record of block i; n <= i < 2n: the y record of block i - n
+    for (size_t i = tid; i < 2 * (size_t)n; i += stride) {
+        const bool ax = i < (size_t)n;
+        const size_t b = ax ? i : i - n;
+        const float pos = ax ? x[b] : y[b], len = ax ? w[b] : h[b];
+        const double k = ax ? invW : invH, kh = ax ? halfW : halfH;
+        const float pil = ax ? piW : piH;
+        AxisRec r;
+        r.s = fixed_halfturns(pos, k);
+        r.t = fixed_halfturns(len, kh);
+        r.es = phase_cs(1, r.s);
+        r.et = phase_cs(1, r.t);
+        r.inv_l = pil;
+        r.es8 = phase_cs(8, r.s);
+        r.et8 = phase_cs(8, r.t);
+        if (ax) {
+            const float ci = c ? c[b] : 1.0f;
+            r.v0 = ci * (0.5f * pil * len);                           // c pi t
+            r.q = ci * len * h[b];
+            r.c = ci;
+            xr[b] = r;
+        } else {
+            r.v0 = 0.5f * pil * len;
+            r.q = 1.0f;
+            r.c = 1.0f;
+            yr[b] = r;
+        }
     }
     for (size_t j = tid; j < nS; j += stride) S64[j] = 0.0;
     if (tid == 0 && e_total) *e_total = 0.0;
@@ -64,12 +65,14 @@ __global__ void prep_kernel(const float *__restrict__ x, const float *__restrict
 
 cudaError_t launch_prep(const Launch &L, bool zero_S, double *e_total) {
     size_t nS = zero_S ? (size_t)L.Mx * L.My : 0;
-    size_t work = (size_t)L.n > nS ? (size_t)L.n : nS;
+    size_t work = 2 * (size_t)L.n > nS ? 2 * (size_t)L.n : nS;
     int blocks = (int)((work + 255) / 256);
     if (blocks < 1) blocks = 1;
-    if (blocks > 8 * L.sm_count) blocks = 8 * L.sm_count;
-    prep_kernel<<<blocks, 256, 0, L.stream>>>(L.x, L.y, L.w, L.h, L.c, L.n, L.W, L.H, L.xrec,
-                                              L.yrec, L.S64, nS, e_total);
+    if (blocks > 32 * L.sm_count) blocks = 32 * L.sm_count;
+    const double PI = 3.141592653589793;
+    prep_kernel<<<blocks, 256, 0, L.stream>>>(L.x, L.y, L.w, L.h, L.c, L.n, 1.0 / L.W, 1.0 / L.H,
+                                              (float)(PI / L.W), (float)(PI / L.H), L.xrec, L.yrec,
+                                              L.S64, nS, e_total);
     return cudaGetLastError();
 }
 

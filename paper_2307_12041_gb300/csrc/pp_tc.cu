@@ -14,9 +14,10 @@
 //                     compensation by the finish kernel.
 //   tc_finish_kernel  a = G o (f St g) and K = f a g in the operand precision,
 //                     laid out so that one 3-D TMA box is one pipeline stage.
-//   tc_energy_kernel  T = Xt K and T' = Xh K for 128 blocks per CTA (two
+//   tc_energy_kernel  T = Xt K and T' = Xh K for row tiles of 128 blocks (two
 //                     accumulators sharing the TMA-staged K tile), then row dots
-//                     with Yt and Yh in the epilogue warps.
+//                     with Yt and Yh in the epilogue warps; persistent, one CTA
+//                     per SM looping over row tiles.
 //
 // Operand layouts (no swizzle, core matrix = 8 rows x 16 bytes, LBO = K-direction
 // core stride, SBO = M/N-direction core stride):
@@ -33,6 +34,7 @@
 #include <cuda_bf16.h>
 
 #include <cmath>
+#include <type_traits>
 #include <cstdio>
 
 #include "pp_device.cuh"
@@ -61,9 +63,6 @@ __device__ __forceinline__ void split_bf16(float x, __nv_bfloat16 &hi, __nv_bflo
     lo = __float2bfloat16_rn(x - __bfloat162float(hi));
 }
 
-__device__ __forceinline__ uint32_t pack_bf16(__nv_bfloat16 a, __nv_bfloat16 b) {
-    return (uint32_t)__bfloat16_as_ushort(a) | ((uint32_t)__bfloat16_as_ushort(b) << 16);
-}
 
 // ===========================================================================
 // Coefficient contraction
@@ -535,10 +534,8 @@ constexpr int E_STAGE_BYTES = 65536;        // A (Xt, Xh) 32 KB + B (K) 32 KB
 constexpr int E_GEN_WARPS = 8;              // two groups of 4 warps, alternate stages
 constexpr int E_EPI_WARPS = 8;              // two per TMEM lane quarter, 128 columns each
 constexpr int E_THREADS = 32 * (2 + E_EPI_WARPS + E_GEN_WARPS);
-#ifndef PP_ENERGY_CLUSTER
-#define PP_ENERGY_CLUSTER 1
-#endif
-constexpr int kEnergyCluster = PP_ENERGY_CLUSTER;     // CTAs sharing each K tile
+constexpr int E_DRAIN_THREADS = 32 * E_EPI_WARPS;
+constexpr int E_DRAIN_COLS = E_VC / 2;
 
 struct EnergyBars {
     uint64_t full[E_STAGES];
@@ -548,12 +545,13 @@ struct EnergyBars {
     uint64_t drain;
     uint32_t tmem_slot;
     int abort_flag;
+    float red[2][E_ROWS][3];    // per tile parity: column half 1 of each row, for half 0
 };
 constexpr int E_SMEM = E_STAGES * E_STAGE_BYTES + 1024 + (int)sizeof(EnergyBars);
 
 struct EnergyArgs {
     const AxisRec *xr, *yr;
-    int n, Mx, My, Mxe, Mye;
+    int n, tiles, Mx, My, Mxe, Mye;      // tiles: row tiles of E_ROWS blocks
     float *e_block, *gx, *gy;
     double *e_total;
     unsigned *status;
@@ -689,7 +687,184 @@ __device__ __forceinline__ void gen_energy(unsigned char *sb, const AxisRec &R, 
     }
 }
 
-template <int PREC, int SAMPLE, int CL>
+// The y-axis fields one epilogue row needs.
+struct YRec {
+    unsigned long long s, t;
+    float2 es, et;
+    float inv_l, v0;
+};
+__device__ __forceinline__ YRec load_yrec(const AxisRec *yr, int b) {
+    const AxisRec &R = yr[b];
+    YRec y;
+    y.s = R.s;
+    y.t = R.t;
+    y.es = R.es;
+    y.et = R.et;
+    y.inv_l = R.inv_l;
+    y.v0 = R.v0;
+    return y;
+}
+
+// Row dots of one thread's 8 columns (rectangle sampling): Yt and Yh advance as
+// packed chains over column pairs.
+struct EpiRect {
+    c2 Z, T;
+    gen::rot2_step S2, T2;
+    f2 nlv, dlv, EN, EX, EY;
+    __device__ __forceinline__ void init(const YRec &Ry, int vb) {
+        const float2 za = gen::phase_poly((unsigned long long)vb, Ry.s);
+        const float2 ta = gen::phase_poly((unsigned long long)vb, Ry.t);
+        Z = gen::make_c2(za, rot(za, Ry.es));
+        T = gen::make_c2(ta, rot(ta, Ry.et));
+        const float2 es2 = rot(Ry.es, Ry.es), et2 = rot(Ry.et, Ry.et);
+        S2 = gen::make_step(es2, es2);
+        T2 = gen::make_step(et2, et2);
+        nlv = gen::pk(-(float)vb * Ry.inv_l, -(float)(vb + 1) * Ry.inv_l);
+        dlv = gen::pk(-2.f * Ry.inv_l, -2.f * Ry.inv_l);
+        EN = EX = EY = gen::pk(0.f, 0.f);
+    }
+    __device__ __forceinline__ void cols8(const float t[8], const float tp[8]) {
+#pragma unroll
+        for (int j = 0; j < 8; j += 2) {
+            const f2 tt = gen::pk(t[j], t[j + 1]), ttp = gen::pk(tp[j], tp[j + 1]);
+            const f2 yt = gen::mul2(Z.re, T.im), pr = gen::mul2(Z.im, T.im);
+            EN = gen::fma2(tt, yt, EN);
+            EX = gen::fma2(ttp, yt, EX);
+            EY = gen::fma2(gen::mul2(tt, nlv), pr, EY);
+            nlv = gen::add2(nlv, dlv);
+            Z = gen::rot2(Z, S2);
+            T = gen::rot2(T, T2);
+        }
+    }
+    __device__ __forceinline__ void sums(float &aN, float &aX, float &aY) const {
+        float x0, x1;
+        gen::upk(EN, x0, x1);
+        aN = x0 + x1;
+        gen::upk(EX, x0, x1);
+        aX = x0 + x1;
+        gen::upk(EY, x0, x1);
+        aY = x0 + x1;
+    }
+};
+// Centre sampling: Yt = cos(pi v s') / g_v, Yh = -l_v sin(pi v s') / g_v, one chain.
+struct EpiCenter {
+    float2 zs, es;
+    float lv, inv_l;
+    int v;
+    float aN, aX, aY;
+    __device__ __forceinline__ void init(const YRec &Ry, int vb) {
+        zs = gen::phase_poly((unsigned long long)vb, Ry.s);
+        es = Ry.es;
+        inv_l = Ry.inv_l;
+        lv = (float)vb * Ry.inv_l;
+        v = vb;
+        aN = aX = aY = 0.f;
+    }
+    __device__ __forceinline__ void cols8(const float t[8], const float tp[8]) {
+#pragma unroll
+        for (int j = 0; j < 8; ++j, ++v) {
+            const float inv_g = 0.5f * (float)(v > 0 ? v : 1) * inv_l;
+            const float yt = zs.x * inv_g;
+            const float yh = -lv * zs.y * inv_g;
+            aN = fmaf(t[j], yt, aN);
+            aY = fmaf(t[j], yh, aY);
+            aX = fmaf(tp[j], yt, aX);
+            zs = rot(zs, es);
+            lv += inv_l;
+        }
+    }
+    __device__ __forceinline__ void sums(float &a, float &b, float &c) const {
+        a = aN;
+        b = aX;
+        c = aY;
+    }
+};
+
+// One thread's share of accumulator pass pc: TMEM lane row (trow), columns
+// [cb, cb + E_DRAIN_COLS) of the pass, global column base vb; adds its row dots
+// to (eN, eX, eY) and releases its part of TMEM.
+template <int SAMPLE>
+__device__ __forceinline__ void drain_pass(EnergyBars &bars, volatile int *abort_flag, unsigned *status,
+                                           uint32_t trow, int cb, int vb, int pc, bool valid,
+                                           const YRec &Ry, float &eN, float &eX, float &eY) {
+    if (*abort_flag) return;
+    typename std::conditional<SAMPLE == 0, EpiRect, EpiCenter>::type ep;
+    if (valid) ep.init(Ry, vb);          // phase anchors ahead of the wait
+    if (!mbar_wait(&bars.acc_full, pc & 1, kWaitLimit, abort_flag)) {
+        raise_timeout(status, abort_flag);
+        return;
+    }
+    tc_fence_after();
+    // 8-column chunks, the TMEM loads of the next chunk in flight while the
+    // current one is used
+    float tA[8], pA[8], tB[8], pB[8];
+    tmem_ld8(trow + cb, tA);
+    tmem_ld8(trow + cb + 256, pA);
+    tmem_ld_wait_regs(tA, pA);
+    // v = 0 column (rectangle sampling): Yt = pi t there, not the sine limit 0 the
+    // chain gives; Yh = 0
+    const float fixN = (SAMPLE == 0 && vb == 0) ? tA[0] * Ry.v0 : 0.f;
+    const float fixX = (SAMPLE == 0 && vb == 0) ? pA[0] * Ry.v0 : 0.f;
+#pragma unroll 1
+    for (int c = 0; c < E_DRAIN_COLS; c += 16) {
+        tmem_ld8(trow + cb + c + 8, tB);
+        tmem_ld8(trow + cb + c + 8 + 256, pB);
+        if (valid) ep.cols8(tA, pA);
+        tmem_ld_wait_regs(tB, pB);
+        if (c + 16 < E_DRAIN_COLS) {
+            tmem_ld8(trow + cb + c + 16, tA);
+            tmem_ld8(trow + cb + c + 16 + 256, pA);
+        }
+        if (valid) ep.cols8(tB, pB);
+        tmem_ld_wait_regs(tA, pA);
+    }
+    tc_fence_before();
+    mbar_arrive(&bars.acc_empty);
+    if (valid) {
+        float aN, aX, aY;
+        ep.sums(aN, aX, aY);
+        eN += fixN + aN;
+        eX += fixX + aX;
+        eY += aY;
+    }
+}
+
+// End of a row tile for one epilogue thread: column half 1 puts its sums in
+// shared memory (double-buffered by tile parity, so that a one-pass tile cannot
+// overwrite them before they are read); half 0 waits for them (named barrier 1,
+// all epilogue threads) and writes the block's outputs and its share of E.
+__device__ __forceinline__ void finish_tile(EnergyBars &bars, volatile int *abort_flag, const EnergyArgs &args,
+                                            int tile, int row, int cq, float eN, float eX, float eY) {
+    if (cq != 0) {
+        float *r = bars.red[tile & 1][row];
+        r[0] = eN;
+        r[1] = eX;
+        r[2] = eY;
+        asm volatile("bar.arrive 1, %0;" ::"r"(E_DRAIN_THREADS) : "memory");
+        return;
+    }
+    asm volatile("bar.sync 1, %0;" ::"r"(E_DRAIN_THREADS) : "memory");
+    const int b = tile * E_ROWS + row;
+    const bool valid = b < args.n;
+    eN += bars.red[tile & 1][row][0];
+    eX += bars.red[tile & 1][row][1];
+    eY += bars.red[tile & 1][row][2];
+    const bool ok = !*abort_flag;
+    if (valid && ok) {
+        if (args.e_block) args.e_block[b] = eN;
+        if (args.gx) args.gx[b] = eX;
+        if (args.gy) args.gy[b] = eY;
+    }
+    double es = valid ? (double)eN : 0.0;
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) es += __shfl_xor_sync(0xffffffffu, es, off);
+    if ((threadIdx.x & 31) == 0 && args.e_total && ok) atomicAdd(args.e_total, 0.5 * es);
+}
+
+// Persistent over row tiles (tile = blockIdx.x + k * gridDim.x): the generators
+// and the TMA warp fill the next tile's stages while the epilogue drains the
+// previous one, and TMEM is allocated once.
+template <int PREC, int SAMPLE>
 __global__ void __launch_bounds__(E_THREADS, 1)
 tc_energy_kernel(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ CUtensorMap tm_lo,
                  const EnergyArgs args) {
@@ -702,20 +877,17 @@ tc_energy_kernel(const __grid_constant__ CUtensorMap tm_hi, const __grid_constan
     constexpr bool BF = PREC == 2;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int blk0 = blockIdx.x * E_ROWS;
     const int nvc = args.Mye / E_VC;
     const int nks = args.Mxe / E_KS;
 
-    constexpr uint16_t cl_mask = (uint16_t)((1u << CL) - 1u);
-    const uint32_t cl_rank = CL > 1 ? cluster_ctarank() : 0u;
     if (threadIdx.x == 0) {
         for (int s = 0; s < E_STAGES; ++s) {
             // one generator group (128 threads) + the TMA producer per stage
             mbar_init(&bars.full[s], (E_GEN_WARPS / 2) * 32 + 1);
-            mbar_init(&bars.empty[s], CL);        // one MMA completion per cluster CTA
+            mbar_init(&bars.empty[s], 1);
         }
         mbar_init(&bars.acc_full, 1);
-        mbar_init(&bars.acc_empty, E_EPI_WARPS * 32);
+        mbar_init(&bars.acc_empty, E_DRAIN_THREADS);
         mbar_init(&bars.drain, 1);
         bars.abort_flag = 0;
         mbar_fence_init();
@@ -725,8 +897,7 @@ tc_energy_kernel(const __grid_constant__ CUtensorMap tm_hi, const __grid_constan
         tmem_relinquish();
     }
     tc_fence_before();
-    if (CL > 1) cluster_sync();      // barriers of every CTA initialised before remote use
-    else __syncthreads();
+    __syncthreads();
     tc_fence_after();
     const uint32_t tmem = bars.tmem_slot;
 
@@ -734,231 +905,140 @@ tc_energy_kernel(const __grid_constant__ CUtensorMap tm_hi, const __grid_constan
         // ---------------- MMA issuer ----------------
         if (lane == 0) {
             const uint32_t idesc = instr_desc(BF ? kFmtBF16 : kFmtTF32, 128, 256, false, false);
-            int it = 0;
-            for (int vc = 0; vc < nvc && !*abort_flag; ++vc) {
-                if (vc > 0 && !mbar_wait(&bars.acc_empty, (vc - 1) & 1, kWaitLimit, abort_flag)) {
-                    raise_timeout(args.status, abort_flag);
-                    break;
-                }
-                tc_fence_after();
-                for (int ks = 0; ks < nks; ++ks, ++it) {
-                    const int s = it % E_STAGES;
-                    if (!mbar_wait(&bars.full[s], (it / E_STAGES) & 1, kWaitLimit, abort_flag)) {
+            int it = 0, pc = 0;       // stages consumed, accumulator passes
+            for (int tile = blockIdx.x; tile < args.tiles && !*abort_flag; tile += gridDim.x) {
+                for (int vc = 0; vc < nvc && !*abort_flag; ++vc, ++pc) {
+                    if (pc > 0 && !mbar_wait(&bars.acc_empty, (pc - 1) & 1, kWaitLimit, abort_flag)) {
                         raise_timeout(args.status, abort_flag);
                         break;
                     }
                     tc_fence_after();
-                    const uint32_t sb = smem_u32(smem + s * E_STAGE_BYTES);
-                    if (!BF) {
-                        const uint32_t At = sb, Ah = sb + 16384, B = sb + 32768;
-#pragma unroll
-                        for (int kk = 0; kk < 4; ++kk) {
-                            // A: LBO 128 (u cores), SBO 1024 (row groups); B: [u/4][256 v][4]
-                            const uint64_t bd = smem_desc(B + kk * 8192, 4096, 128);
-                            const bool accum = ks > 0 || kk > 0;
-                            mma_tf32(tmem, smem_desc(At + kk * 256, 128, 1024), bd, idesc, accum);
-                            mma_tf32(tmem + 256, smem_desc(Ah + kk * 256, 128, 1024), bd, idesc, accum);
+                    for (int ks = 0; ks < nks; ++ks, ++it) {
+                        const int s = it % E_STAGES;
+                        if (!mbar_wait(&bars.full[s], (it / E_STAGES) & 1, kWaitLimit, abort_flag)) {
+                            raise_timeout(args.status, abort_flag);
+                            break;
                         }
-                    } else {
-                        const uint32_t Th = sb, Tl = sb + 8192, Hh = sb + 16384, Hl = sb + 24576;
-                        const uint32_t Bh = sb + 32768, Bl = sb + 49152;
+                        tc_fence_after();
+                        const uint32_t sb = smem_u32(smem + s * E_STAGE_BYTES);
+                        if (!BF) {
+                            const uint32_t At = sb, Ah = sb + 16384, B = sb + 32768;
 #pragma unroll
-                        for (int kk = 0; kk < 2; ++kk) {
-                            // A: LBO 128, SBO 512; B: [u/8][256 v][8]: LBO 4096, SBO 128
-                            const uint64_t bh = smem_desc(Bh + kk * 8192, 4096, 128);
-                            const uint64_t bl = smem_desc(Bl + kk * 8192, 4096, 128);
-                            const bool accum = ks > 0 || kk > 0;
-                            const uint32_t ao = kk * 256;
-                            mma_bf16(tmem, smem_desc(Tl + ao, 128, 512), bh, idesc, accum);
-                            mma_bf16(tmem, smem_desc(Th + ao, 128, 512), bl, idesc, true);
-                            mma_bf16(tmem, smem_desc(Th + ao, 128, 512), bh, idesc, true);
-                            mma_bf16(tmem + 256, smem_desc(Hl + ao, 128, 512), bh, idesc, accum);
-                            mma_bf16(tmem + 256, smem_desc(Hh + ao, 128, 512), bl, idesc, true);
-                            mma_bf16(tmem + 256, smem_desc(Hh + ao, 128, 512), bh, idesc, true);
+                            for (int kk = 0; kk < 4; ++kk) {
+                                // A: LBO 128 (u cores), SBO 1024 (row groups); B: [u/4][256 v][4]
+                                const uint64_t bd = smem_desc(B + kk * 8192, 4096, 128);
+                                const bool accum = ks > 0 || kk > 0;
+                                mma_tf32(tmem, smem_desc(At + kk * 256, 128, 1024), bd, idesc, accum);
+                                mma_tf32(tmem + 256, smem_desc(Ah + kk * 256, 128, 1024), bd, idesc, accum);
+                            }
+                        } else {
+                            const uint32_t Th = sb, Tl = sb + 8192, Hh = sb + 16384, Hl = sb + 24576;
+                            const uint32_t Bh = sb + 32768, Bl = sb + 49152;
+#pragma unroll
+                            for (int kk = 0; kk < 2; ++kk) {
+                                // A: LBO 128, SBO 512; B: [u/8][256 v][8]: LBO 4096, SBO 128
+                                const uint64_t bh = smem_desc(Bh + kk * 8192, 4096, 128);
+                                const uint64_t bl = smem_desc(Bl + kk * 8192, 4096, 128);
+                                const bool accum = ks > 0 || kk > 0;
+                                const uint32_t ao = kk * 256;
+                                mma_bf16(tmem, smem_desc(Tl + ao, 128, 512), bh, idesc, accum);
+                                mma_bf16(tmem, smem_desc(Th + ao, 128, 512), bl, idesc, true);
+                                mma_bf16(tmem, smem_desc(Th + ao, 128, 512), bh, idesc, true);
+                                mma_bf16(tmem + 256, smem_desc(Hl + ao, 128, 512), bh, idesc, accum);
+                                mma_bf16(tmem + 256, smem_desc(Hh + ao, 128, 512), bl, idesc, true);
+                                mma_bf16(tmem + 256, smem_desc(Hh + ao, 128, 512), bh, idesc, true);
+                            }
                         }
+                        mma_commit(&bars.empty[s]);
                     }
-                    if (CL > 1) mma_commit_multicast(&bars.empty[s], cl_mask);
-                    else mma_commit(&bars.empty[s]);
+                    if (*abort_flag) break;
+                    mma_commit(&bars.acc_full);
                 }
-                if (*abort_flag) break;
-                mma_commit(&bars.acc_full);
             }
+            // all MMAs issued by this thread complete before the TMEM is freed
             mma_commit(&bars.drain);
             if (!mbar_wait(&bars.drain, 0, kWaitLimit, nullptr)) raise_timeout(args.status, abort_flag);
         }
         __syncwarp();
     } else if (warp == 1) {
-        // ---------------- TMA producer: K tiles ----------------
+        // ---------------- TMA producer: K tiles (the same sequence for every row tile) ----------------
         if (lane == 0) {
             constexpr int T = BF ? 8 : 4;                 // u per 16-byte core row
             const uint32_t bytes = BF ? 2 * 16384 : 32768;
             int it = 0;
-            for (int vc = 0; vc < nvc; ++vc) {
-                for (int ks = 0; ks < nks; ++ks, ++it) {
-                    if (*abort_flag) break;
-                    const int s = it % E_STAGES;
-                    if (it >= E_STAGES &&
-                        !mbar_wait(&bars.empty[s], ((it / E_STAGES) - 1) & 1, kWaitLimit, abort_flag)) {
-                        raise_timeout(args.status, abort_flag);
-                        break;
-                    }
-                    unsigned char *sb = smem + s * E_STAGE_BYTES + 32768;
-                    // stage start in 1 KB rows: ((vc*(Mxe/T) + ks*(32/T)) * 4 KB) / 1 KB
-                    const int row = 4 * (vc * (args.Mxe / T) + ks * (E_KS / T));
-                    mbar_arrive_expect_tx(&bars.full[s], bytes);
-                    if (CL == 1) {
+            for (int tile = blockIdx.x; tile < args.tiles && !*abort_flag; tile += gridDim.x) {
+                for (int vc = 0; vc < nvc && !*abort_flag; ++vc) {
+                    for (int ks = 0; ks < nks; ++ks, ++it) {
+                        if (*abort_flag) break;
+                        const int s = it % E_STAGES;
+                        if (it >= E_STAGES &&
+                            !mbar_wait(&bars.empty[s], ((it / E_STAGES) - 1) & 1, kWaitLimit, abort_flag)) {
+                            raise_timeout(args.status, abort_flag);
+                            break;
+                        }
+                        unsigned char *sb = smem + s * E_STAGE_BYTES + 32768;
+                        // stage start in 1 KB rows: ((vc*(Mxe/T) + ks*(32/T)) * 4 KB) / 1 KB
+                        const int row = 4 * (vc * (args.Mxe / T) + ks * (E_KS / T));
+                        mbar_arrive_expect_tx(&bars.full[s], bytes);
                         tma_load_2d(sb, &tm_hi, 0, row, &bars.full[s]);
                         if (BF) tma_load_2d(sb + 16384, &tm_lo, 0, row, &bars.full[s]);
-                    } else if (cl_rank == 0) {
-                        tma_load_2d_multicast(sb, &tm_hi, 0, row, &bars.full[s], cl_mask);
-                        if (BF) tma_load_2d_multicast(sb + 16384, &tm_lo, 0, row, &bars.full[s], cl_mask);
                     }
                 }
-                if (*abort_flag) break;
             }
         }
         __syncwarp();
     } else if (warp < 2 + E_EPI_WARPS) {
         // ---------------- epilogue: row dots with Yt, Yh ----------------
-        const int quarter = warp & 3;
-        const int chalf = (warp - 2) >> 2;              // columns [128*chalf, 128*chalf + 128)
-        const int row = quarter * 32 + lane;
-        const int b = blk0 + row;
-        const bool valid = b < args.n;
-        AxisRec Ry;
-        if (valid) Ry = args.yr[b];
-        float eN = 0.f, eX = 0.f, eY = 0.f;
-        for (int vc = 0; vc < nvc; ++vc) {
-            if (*abort_flag) break;
-            // phase anchors for this thread's 128 columns, ahead of the wait;
-            // columns (v, v+1) advance as two packed chains with a 2-mode step
-            const int vb = vc * E_VC + chalf * 128;
-            float2 za = make_float2(1.f, 0.f), ta = make_float2(0.f, 0.f);
-            if (valid) {
-                za = gen::phase_poly((unsigned long long)vb, Ry.s);
-                if (SAMPLE == 0) ta = gen::phase_poly((unsigned long long)vb, Ry.t);
-            }
-            c2 Z = gen::make_c2(za, rot(za, Ry.es)), Tt = gen::make_c2(ta, rot(ta, Ry.et));
-            const float2 es2 = rot(Ry.es, Ry.es), et2 = rot(Ry.et, Ry.et);
-            const gen::rot2_step S2 = gen::make_step(es2, es2), T2 = gen::make_step(et2, et2);
-            f2 nlv = gen::pk(-(float)vb * Ry.inv_l, -(float)(vb + 1) * Ry.inv_l);
-            const f2 dlv = gen::pk(-2.f * Ry.inv_l, -2.f * Ry.inv_l);
-            f2 EN = gen::pk(0.f, 0.f), EX = EN, EY = EN;
-            float2 zs = za;
-            float lv = (float)vb * Ry.inv_l;
-            if (!mbar_wait(&bars.acc_full, vc & 1, kWaitLimit, abort_flag)) {
-                raise_timeout(args.status, abort_flag);
-                break;
-            }
-            tc_fence_after();
-            float aN = 0.f, aX = 0.f, aY = 0.f;
-#pragma unroll 1
-            for (int c = chalf * 128; c < chalf * 128 + 128; c += 16) {
-                float t[16], tp[16];
-                const uint32_t ta_ = tmem + ((uint32_t)(quarter * 32) << 16) + c;
-                tmem_ld16(ta_, t);
-                tmem_ld16(ta_ + 256, tp);
-                tmem_ld_wait();
-                if (!valid) continue;
-                if (SAMPLE == 0) {
-#pragma unroll
-                    for (int j = 0; j < 16; j += 2) {
-                        const f2 tt = gen::pk(t[j], t[j + 1]), ttp = gen::pk(tp[j], tp[j + 1]);
-                        const f2 yt = gen::mul2(Z.re, Tt.im), pr = gen::mul2(Z.im, Tt.im);
-                        EN = gen::fma2(tt, yt, EN);
-                        EX = gen::fma2(ttp, yt, EX);
-                        EY = gen::fma2(gen::mul2(tt, nlv), pr, EY);
-                        nlv = gen::add2(nlv, dlv);
-                        Z = gen::rot2(Z, S2);
-                        Tt = gen::rot2(Tt, T2);
-                    }
-                    if (c == 0 && vc == 0) {      // v = 0 column: Yt = pi t (not the sine limit 0)
-                        aN = fmaf(t[0], Ry.v0, aN);
-                        aX = fmaf(tp[0], Ry.v0, aX);
-                    }
-                } else {
-#pragma unroll
-                    for (int j = 0; j < 16; ++j) {
-                        const int v = vc * E_VC + c + j;
-                        const float inv_g = 0.5f * (float)(v > 0 ? v : 1) * Ry.inv_l;
-                        const float yt = zs.x * inv_g;
-                        const float yh = -lv * zs.y * inv_g;
-                        aN = fmaf(t[j], yt, aN);
-                        aY = fmaf(t[j], yh, aY);
-                        aX = fmaf(tp[j], yt, aX);
-                        zs = rot(zs, Ry.es);
-                        lv += Ry.inv_l;
-                    }
-                }
-            }
-            {
-                float x0, x1;
-                gen::upk(EN, x0, x1);
-                aN += x0 + x1;
-                gen::upk(EX, x0, x1);
-                aX += x0 + x1;
-                gen::upk(EY, x0, x1);
-                aY += x0 + x1;
-            }
-            tc_fence_before();
-            mbar_arrive(&bars.acc_empty);
-            eN += aN;
-            eX += aX;
-            eY += aY;
-        }
-        // the two column halves of a row meet through shared memory
-        float *red = reinterpret_cast<float *>(smem);   // stage 0 buffer, free once all MMAs are done
-        __syncwarp();
-        const bool ok = !*abort_flag;
-        // wait until every epilogue warp is past its last TMEM read (named barrier 1)
-        asm volatile("bar.sync 1, %0;" ::"r"(E_EPI_WARPS * 32));
-        if (chalf == 1) {
-            red[row * 3 + 0] = eN;
-            red[row * 3 + 1] = eX;
-            red[row * 3 + 2] = eY;
-        }
-        asm volatile("bar.sync 1, %0;" ::"r"(E_EPI_WARPS * 32));
-        if (chalf == 0) {
-            eN += red[row * 3 + 0];
-            eX += red[row * 3 + 1];
-            eY += red[row * 3 + 2];
-            if (valid && ok) {
-                if (args.e_block) args.e_block[b] = eN;
-                if (args.gx) args.gx[b] = eX;
-                if (args.gy) args.gy[b] = eY;
-            }
-            double es = valid ? (double)eN : 0.0;
-#pragma unroll
-            for (int off = 16; off >= 1; off >>= 1) es += __shfl_xor_sync(0xffffffffu, es, off);
-            if (lane == 0 && args.e_total && ok) atomicAdd(args.e_total, 0.5 * es);
+        // A warp reads TMEM lanes 32 * (warp % 4) .. + 31: its rows; two warps per
+        // lane quarter take 128 columns each.  Every epilogue thread runs the same
+        // tile sequence and meets named barrier 1 once per tile, also after an
+        // abort (the work is then skipped).
+        const int row = (warp & 3) * 32 + lane;
+        const int cq = (warp - 2) >> 2;
+        const uint32_t trow = tmem + ((uint32_t)((warp & 3) * 32) << 16);
+        int pc = 0;
+        for (int tile = blockIdx.x; tile < args.tiles; tile += gridDim.x) {
+            const int b = tile * E_ROWS + row;
+            const bool valid = b < args.n;
+            YRec Ry{};
+            if (valid) Ry = load_yrec(args.yr, b);
+            float eN = 0.f, eX = 0.f, eY = 0.f;
+            for (int vc = 0; vc < nvc; ++vc, ++pc)
+                drain_pass<SAMPLE>(bars, abort_flag, args.status, trow, cq * E_DRAIN_COLS,
+                                   vc * E_VC + cq * E_DRAIN_COLS, pc, valid, Ry, eN, eX, eY);
+            finish_tile(bars, abort_flag, args, tile, row, cq, eN, eX, eY);
         }
     } else {
         // ---------------- basis generators: Xt, Xh ----------------
-        // group 0 (warps 0-3 of the generators) fills even stages, group 1 odd ones
+        // group grp fills the stages j = grp, grp + 2, ... of each tile (j counted
+        // within the tile), so every stage is filled by exactly one group
         const int g = threadIdx.x - 32 * (2 + E_EPI_WARPS);   // 0..255
         const int row = g & 127, grp = g >> 7;
-        const int b = blk0 + row;
-        const bool valid = b < args.n;
-        AxisRec Rx;
-        if (valid) Rx = args.xr[b];
         const int total = nvc * nks;
-        for (int it = grp; it < total; it += 2) {
-            if (*abort_flag) break;
-            const int s = it % E_STAGES;
-            if (it >= E_STAGES &&
-                !mbar_wait(&bars.empty[s], ((it / E_STAGES) - 1) & 1, kWaitLimit, abort_flag)) {
-                raise_timeout(args.status, abort_flag);
-                break;
+        int base = 0;                                        // first stage of this tile
+        for (int tile = blockIdx.x; tile < args.tiles && !*abort_flag; tile += gridDim.x, base += total) {
+            const int b = tile * E_ROWS + row;
+            const bool valid = b < args.n;
+            AxisRec Rx;
+            if (valid) Rx = args.xr[b];
+            for (int j = grp; j < total; j += 2) {
+                if (*abort_flag) break;
+                const int it = base + j;
+                const int s = it % E_STAGES;
+                if (it >= E_STAGES &&
+                    !mbar_wait(&bars.empty[s], ((it / E_STAGES) - 1) & 1, kWaitLimit, abort_flag)) {
+                    raise_timeout(args.status, abort_flag);
+                    break;
+                }
+                const int ks = j % nks;
+                gen_energy<PREC, SAMPLE>(smem + s * E_STAGE_BYTES, Rx, valid, row, ks * E_KS);
+                fence_proxy_async_smem();
+                mbar_arrive(&bars.full[s]);
             }
-            const int ks = it % nks;
-            gen_energy<PREC, SAMPLE>(smem + s * E_STAGE_BYTES, Rx, valid, row, ks * E_KS);
-            fence_proxy_async_smem();
-            mbar_arrive(&bars.full[s]);
         }
     }
     tc_fence_before();
-    if (CL > 1) cluster_sync();      // no CTA leaves while a peer may still signal or fill it
-    else __syncthreads();
+    __syncthreads();
     if (warp == 0) {
         tc_fence_after();
         tmem_dealloc(tmem, 512);
@@ -1026,7 +1106,7 @@ __global__ void phase_eval_kernel(const float *__restrict__ x, double invL, cons
                                   int64_t count, int evaluator, float2 *__restrict__ out) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
          i += (int64_t)gridDim.x * blockDim.x) {
-        const unsigned long long s = to_fixed_halfturns((double)x[i] * invL);
+        const unsigned long long s = fixed_halfturns(x[i], invL);
         const unsigned long long mm = (unsigned long long)m[i];
         out[i] = evaluator == 0 ? phase_cs(mm, s) : gen::phase_poly(mm, s);
     }
@@ -1133,27 +1213,14 @@ cudaError_t launch_energy_tc(const Launch &L, int prec, int sample, const TcPlan
     a.gy = gy;
     a.e_total = e_total;
     a.status = L.status;
-    const int ctas = (L.n + E_ROWS - 1) / E_ROWS;
-    const int grid = (ctas + kEnergyCluster - 1) / kEnergyCluster * kEnergyCluster;
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(grid);
-    cfg.blockDim = dim3(E_THREADS);
-    cfg.dynamicSmemBytes = E_SMEM;
-    cfg.stream = L.stream;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = kEnergyCluster;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
+    a.tiles = (L.n + E_ROWS - 1) / E_ROWS;
+    const int grid = a.tiles < L.sm_count ? a.tiles : L.sm_count;     // persistent
 #define PP_ELAUNCH(PR, SA)                                                                         \
     do {                                                                                           \
-        auto kfn = tc_energy_kernel<PR, SA, kEnergyCluster>;                                       \
+        auto kfn = tc_energy_kernel<PR, SA>;                                                       \
         e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, E_SMEM);       \
         if (e != cudaSuccess) return e;                                                            \
-        e = cudaLaunchKernelEx(&cfg, kfn, mh, ml, a);                                              \
-        if (e != cudaSuccess) return e;                                                            \
+        kfn<<<grid, E_THREADS, E_SMEM, L.stream>>>(mh, ml, a);                                     \
     } while (0)
     if (prec == 1 && sample == 0) PP_ELAUNCH(1, 0);
     else if (prec == 1) PP_ELAUNCH(1, 1);

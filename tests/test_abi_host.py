@@ -53,7 +53,7 @@ def test_workspace_size_scales_and_rejects_invalid(L):
     assert a > 0 and b > a
     assert ws(_prob(n=0)) > 0
     assert ws(_prob(Mx=64, My=64)) > ws(_prob(Mx=16, My=16))
-    for bad in (dict(W=0.0), dict(H=-1.0), dict(W=float("nan")), dict(W=float("inf")),
+    for bad in (dict(W=0.0), dict(H=-1.0), dict(W=float("nan")), dict(W=float("inf")), dict(W=1e-310),
                 dict(n=-1), dict(Mx=0), dict(My=4097), dict(n=2 ** 31)):
         assert ws(_prob(**bad)) == 0, bad
         assert L.pp_last_error().decode() != ""

@@ -1,6 +1,7 @@
 """Phase step of the basis generators (the cos/sin factors of Eq. aup) against
-exact arithmetic: s = x/L is formed in double as the records form it, reduced
-modulo 2 and rounded to 2^-62 half-turns with Python integers, m*s mod 2 is taken
+exact arithmetic: s = x * (1/L) is formed exactly from the float32 x and the
+double 1/L as the records form it, reduced modulo 2 and rounded to 2^-62
+half-turns with Python integers, m*s mod 2 is taken
 exactly, and cos/sin of pi times that phase come from FP64 numpy.  Both device
 evaluators (the sincospif-based one of the records and CUDA-core kernels, and the
 Taylor-polynomial anchor of the tensor-core generators) must agree to a few FP32
@@ -17,13 +18,14 @@ pytestmark = pytest.mark.gpu
 
 
 def exact_phase(x32, L, m):
-    """(cos, sin)(pi * (m * s mod 2)) with s = fl64(fl64(x) * fl64(1/L)) rounded to 2^-62."""
+    """(cos, sin)(pi * (m * s mod 2)) with s = x * fl64(1/L) (exact product of the
+    float32 x and the double 1/L) reduced mod 2 and rounded to 2^-62 half-turns."""
     out = np.empty((len(x32), 2))
-    invL = 1.0 / L
+    invL = Fraction(1.0 / L)
     for i, (xv, mv) in enumerate(zip(x32, m)):
-        s = float(np.float64(xv) * invL)                 # the double the records start from
-        r = Fraction(s) % 2
-        f = round(r * 2 ** 62) & (2 ** 63 - 1)           # fixed point, 2^-62 half-turn units
+        v = Fraction(float(xv)) * invL * 2 ** 62          # exact, in 2^-62 half-turn units
+        f = math.floor(abs(v) + Fraction(1, 2))           # nearest, ties away from zero
+        f = (-f if v < 0 else f) % 2 ** 63                # reduced mod 2 half-turns
         p = (int(mv) * f) % 2 ** 63                      # m s mod 2, exact
         th = math.pi * (p / 2 ** 62)
         out[i] = (math.cos(th), math.sin(th))
