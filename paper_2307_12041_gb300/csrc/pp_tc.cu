@@ -1135,10 +1135,22 @@ TcPlan tc_plan(int n, int Mx, int My) {
     p.Mxe = round_up(Mx, E_KS);
     p.Mye = round_up(My, E_VC);
     const int tiles = (p.Mxc / C_TILE) * (p.Myc / C_TILE);
-    int slices = (2 * kPlanSMs + tiles - 1) / tiles;
-    const int max_slices = (n + 511) / 512;
-    if (slices > max_slices) slices = max_slices;
-    if (slices < 1) slices = 1;
+    // Slice count s: the kernel takes ceil(tiles * s / SMs) unit times of n / s
+    // blocks each, so pick the s that minimises ceil(tiles * s / SMs) / s (the
+    // smallest such s: fewest partial tiles to sum), with slices of >= 512 blocks.
+    int max_slices = (n + 511) / 512;
+    if (max_slices > 4 * kPlanSMs) max_slices = 4 * kPlanSMs;
+    if (max_slices < 1) max_slices = 1;
+    int slices = 1;
+    double best = 1e300;
+    for (int sc = 1; sc <= max_slices; ++sc) {
+        const double waves = (double)(((long long)tiles * sc + kPlanSMs - 1) / kPlanSMs);
+        const double t = waves / sc;
+        if (t < best * (1.0 - 1e-9)) {
+            best = t;
+            slices = sc;
+        }
+    }
     p.slice_len = round_up((n + slices - 1) / slices > 0 ? (n + slices - 1) / slices : 1, C_KB);
     p.slices = (n + p.slice_len - 1) / p.slice_len;
     if (p.slices < 1) p.slices = 1;
