@@ -141,17 +141,16 @@ __device__ __forceinline__ void gen_coeff_tf32(unsigned char *op, const AxisRec 
         float a0, b0, a1, b1;
         gen::upk(gen::mul2(Z0.re, T0.im), a0, b0);
         gen::upk(gen::mul2(Z1.re, T1.im), a1, b1);
-        if (m0 == 0 && jj == 0) {
-            a0 = v0[0];
-            b0 = v0[1];
-        }
-        *reinterpret_cast<float2 *>(base + jj * 1024) = make_float2(to_tf32(a0), to_tf32(b0));
-        *reinterpret_cast<float2 *>(base + (jj + 1) * 1024) = make_float2(to_tf32(a1), to_tf32(b1));
+        *reinterpret_cast<float2 *>(base + jj * 1024) = make_float2(to_tf32_mma(a0), to_tf32_mma(b0));
+        *reinterpret_cast<float2 *>(base + (jj + 1) * 1024) = make_float2(to_tf32_mma(a1), to_tf32_mma(b1));
         Z0 = gen::rot2(Z0, ES);
         T0 = gen::rot2(T0, ET);
         Z1 = gen::rot2(Z1, ES);
         T1 = gen::rot2(T1, ET);
     }
+    // mode 0 (the u = 0 / v = 0 column): v0 = c pi t, not the sine limit the chain
+    // gives; this thread stored that slot first, so its own later store wins
+    if (m0 == 0) *reinterpret_cast<float2 *>(base) = make_float2(to_tf32_mma(v0[0]), to_tf32_mma(v0[1]));
 }
 
 __device__ __forceinline__ uint32_t cvt_bf16x2(float lo_half, float hi_half) {
@@ -649,13 +648,13 @@ __device__ __forceinline__ void gen_energy(unsigned char *sb, const AxisRec &R, 
             b.next2(tb[2], tb[3], hb[2], hb[3]);
             if (SAMPLE == 0 && c == 0 && u0 == 0 && valid) t[0] = R.v0;
             *reinterpret_cast<float4 *>(A + c * 128) =
-                make_float4(to_tf32(t[0]), to_tf32(t[1]), to_tf32(t[2]), to_tf32(t[3]));
+                make_float4(to_tf32_mma(t[0]), to_tf32_mma(t[1]), to_tf32_mma(t[2]), to_tf32_mma(t[3]));
             *reinterpret_cast<float4 *>(A + 16384 + c * 128) =
-                make_float4(to_tf32(h[0]), to_tf32(h[1]), to_tf32(h[2]), to_tf32(h[3]));
+                make_float4(to_tf32_mma(h[0]), to_tf32_mma(h[1]), to_tf32_mma(h[2]), to_tf32_mma(h[3]));
             *reinterpret_cast<float4 *>(A + (c + 4) * 128) =
-                make_float4(to_tf32(tb[0]), to_tf32(tb[1]), to_tf32(tb[2]), to_tf32(tb[3]));
+                make_float4(to_tf32_mma(tb[0]), to_tf32_mma(tb[1]), to_tf32_mma(tb[2]), to_tf32_mma(tb[3]));
             *reinterpret_cast<float4 *>(A + 16384 + (c + 4) * 128) =
-                make_float4(to_tf32(hb[0]), to_tf32(hb[1]), to_tf32(hb[2]), to_tf32(hb[3]));
+                make_float4(to_tf32_mma(hb[0]), to_tf32_mma(hb[1]), to_tf32_mma(hb[2]), to_tf32_mma(hb[3]));
         }
     } else {
         // [128 rows x 32 u] bf16 K-major: core (row/8, u/8) at (row/8)*512 + (u/8)*128;

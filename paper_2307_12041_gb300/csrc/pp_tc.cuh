@@ -206,6 +206,14 @@ __device__ __forceinline__ void bulk_load(void *dst_smem, const void *src, uint3
 __device__ __forceinline__ float to_tf32(float x) {
     return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
 }
+// Round-to-nearest for an operand that only a kind::tf32 MMA reads: the tensor
+// core uses the top 19 bits of each 32-bit operand and ignores the 13 below
+// (measured on sm_103a: raw FP32 operands give exactly the product of the
+// truncated values), so adding half a TF32 unit is enough; the stored word is
+// not a clean TF32 value and must not be read any other way.
+__device__ __forceinline__ float to_tf32_mma(float x) {
+    return __uint_as_float(__float_as_uint(x) + 0x1000u);
+}
 
 }  // namespace tc
 }  // namespace pp
