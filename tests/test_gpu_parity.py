@@ -207,3 +207,30 @@ def test_million_block_workload_sampled(pp, million, prec):
     ti = torch.from_numpy(idx).cuda()
     assert nerr(out["N"][ti].double().cpu().numpy(), ref["N"]) <= tol
     assert gerr(out["gx"][ti].double().cpu().numpy(), out["gy"][ti].double().cpu().numpy(), ref) <= tol
+
+
+def grid_aligned(n_side=24, W=1.0, H=1.0, seed=5):
+    """Blocks whose centres sit on 1/16 and 1/32 fractions of the die and whose
+    sizes are 1/8, 1/16, 1/32 of it: the phase steps 16 pi s, 16 pi t of the
+    generators' recurrences land exactly on 0, pi/2, pi, 3 pi/2 (the boundaries
+    between their two forms), next to random blocks."""
+    g = np.random.default_rng(seed)
+    k = np.arange(1, 32)
+    xs = np.concatenate([k / 32.0, g.uniform(0.05, 0.95, n_side)]) * W
+    ys = np.concatenate([k[::-1] / 32.0, g.uniform(0.05, 0.95, n_side)]) * H
+    sizes = np.array([1 / 8, 1 / 16, 1 / 32, 1 / 64])
+    w = sizes[np.arange(len(xs)) % 4] * W
+    h = sizes[(np.arange(len(xs)) + 1) % 4] * H
+    xs = np.clip(xs, w / 2, W - w / 2)
+    ys = np.clip(ys, h / 2, H - h / 2)
+    f32 = lambda a: np.asarray(a, np.float32)
+    return synth.Placement(W=W, H=H, x=f32(xs), y=f32(ys), w=f32(w), h=f32(h), c=None,
+                           Mx=300, My=280, name="grid-aligned")
+
+
+def test_grid_aligned_phase_steps(pp):
+    p = grid_aligned()
+    ref = O.evaluate(p.W, p.H, p.x, p.y, p.w, p.h, p.c, p.Mx, p.My)
+    for prec in pp.binding.available_precisions():
+        out = pp.binding.evaluate(p, prec=prec)
+        check(out, ref, pp.binding.TOLERANCE[prec], label=f"{prec} grid-aligned")
