@@ -33,6 +33,10 @@
  *  - The return status covers argument checks and launch errors.  Errors the
  *    GPU detects while running (a bounded wait that ran out) are recorded in a
  *    per-device status word that pp_sync_status() reads and clears.
+ *  - e_total in the rectangle reading is E = 1/2 sum_i N_i.  On the tensor-core
+ *    paths with a == NULL it is evaluated as the equal sum 1/2 sum_uv a_uv S_uv
+ *    from the FP32 coefficients (their accuracy, not that of the TF32 / bf16 K
+ *    operand shared by all blocks); with a given it is the sum of the N_i.
  *  - n = 0 is valid: outputs are zero (a all zero, *e_total = 0).
  *  - Limits: 1 <= Mx, My <= 4096; 0 <= n <= 2^31 - 1; 1e-300 <= W, H <= 1e300.
  *  - pp_last_error() describes the last non-OK status of the calling thread.
@@ -148,6 +152,32 @@ pp_status pp_sync_status(void *stream);
  * unknown evaluator; asynchronous on `stream`. */
 pp_status pp_phase_eval(const float *x, double L, const int32_t *m, int64_t count, int evaluator,
                         float *out, void *stream);
+
+/* Total energy from coefficients: *e_total = 1/2 sum_{(u,v) != (0,0)} a_uv^2 / G_uv
+ * with G_uv = e_u e_v / (W H (k_u^2 + l_v^2)) (FP64 sum), i.e. 1/2 sum_uv a_uv S_uv
+ * (Eq. a-a..a-d: S = a / G) = 1/2 sum_i N_i in the rectangle reading, for the
+ * placement whose coefficients a are (for instance a = sum of pp_coeffs over
+ * chunks of its blocks).  a: device float32 Mx x My, u-major; e_total: device
+ * double.  PP_EINVAL for bad sizes or pointers.  Asynchronous on `stream`. */
+pp_status pp_energy_from_coeffs(const float *a, int32_t Mx, int32_t My, double W, double H,
+                                double *e_total, void *stream);
+
+/* One position update of the descent loop (a driver around the evaluation; the
+ * placer of Sec. IV, whose step rule the paper does not give, is out of scope).
+ * For every block i with movable == NULL or movable[i] != 0:
+ *   x_i <- clamp(x_i - lr * gx_i + sigma * n0_i, w_i / 2, W - w_i / 2)
+ *   y_i <- clamp(y_i - lr * gy_i + sigma * n1_i, h_i / 2, H - h_i / 2)
+ * where (n0_i, n1_i) are standard normals by Box-Muller from the Philox4x32-10
+ * output (Salmon et al., SC 2011) for counter (i, step, 0, 0) and key (seed mod
+ * 2^32, seed >> 32): u0 = (out0 + 1/2) 2^-32, u1 = (out1 + 1/2) 2^-32,
+ * r = sqrt(-2 ln u0), n0 = r cos(2 pi u1), n1 = r sin(2 pi u1).
+ * x, y (updated in place), w, h, gx, gy: float32 device arrays of n; movable:
+ * uint8 device array of n or NULL.  PP_EINVAL for a die size outside
+ * [1e-300, 1e300], n < 0, lr or sigma not finite, or a missing / host pointer
+ * when n > 0.  Asynchronous on `stream`. */
+pp_status pp_descent_step(double W, double H, int64_t n, float *x, float *y, const float *w,
+                          const float *h, const float *gx, const float *gy, const uint8_t *movable,
+                          float lr, float sigma, uint64_t seed, uint64_t step, void *stream);
 
 /* Failure-path check (no counterpart in the paper).  Launches, on `stream`, one
  * kernel whose thread waits on a shared-memory mbarrier that nothing completes,

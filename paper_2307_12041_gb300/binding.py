@@ -41,7 +41,8 @@ class Problem(ctypes.Structure):
 _LIB = None
 EXPORTS = ("pp_workspace_size", "pp_coeffs", "pp_energy", "pp_grad", "pp_sync_status",
            "pp_last_error", "pp_version", "pp_timing_enable", "pp_timing_collect",
-           "pp_grad_noalloc", "pp_phase_eval", "pp_check_wait_timeout")
+           "pp_grad_noalloc", "pp_phase_eval", "pp_energy_from_coeffs", "pp_descent_step",
+           "pp_check_wait_timeout")
 
 
 def lib_path() -> str:
@@ -69,6 +70,13 @@ def lib() -> ctypes.CDLL:
         L.pp_sync_status.restype = i
         L.pp_phase_eval.argtypes = [vp, ctypes.c_double, vp, ctypes.c_int64, i, vp, vp]
         L.pp_phase_eval.restype = i
+        L.pp_energy_from_coeffs.argtypes = [vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
+                                            ctypes.c_double, vp, vp]
+        L.pp_energy_from_coeffs.restype = i
+        L.pp_descent_step.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_int64, vp, vp, vp,
+                                      vp, vp, vp, vp, ctypes.c_float, ctypes.c_float,
+                                      ctypes.c_uint64, ctypes.c_uint64, vp]
+        L.pp_descent_step.restype = i
         L.pp_check_wait_timeout.argtypes = [ctypes.c_uint64, vp]
         L.pp_check_wait_timeout.restype = i
         L.pp_last_error.argtypes = []
@@ -234,6 +242,29 @@ def phase_eval(x, L: float, m, evaluator: int = 0):
     _check(lib().pp_phase_eval(_ptr(x), float(L), _ptr(m), x.numel(), int(evaluator), _ptr(out),
                                _stream_handle(x.device)))
     return out
+
+
+def energy_from_coeffs(a, W, H):
+    """pp_energy_from_coeffs: E = 1/2 sum a^2 / G (FP64) of an Mx x My float32 device tensor."""
+    a = a.contiguous()
+    if a.dtype != torch.float32 or a.dim() != 2:
+        raise ValueError("a must be a 2-D float32 tensor")
+    e = torch.empty(1, dtype=torch.float64, device=a.device)
+    _check(lib().pp_energy_from_coeffs(_ptr(a), a.shape[0], a.shape[1], float(W), float(H), _ptr(e),
+                                       _stream_handle(a.device)))
+    return e
+
+
+def descent_step(x, y, w, h, gx, gy, W, H, lr, sigma, seed, step, movable=None):
+    """pp_descent_step: in-place position update of float32 device tensors x, y
+    (movable: optional bool/uint8 device mask)."""
+    for t in (x, y, w, h, gx, gy):
+        if t.dtype != torch.float32 or not t.is_contiguous():
+            raise ValueError("descent_step takes contiguous float32 tensors")
+    mv = None if movable is None else movable.to(torch.uint8).contiguous()
+    _check(lib().pp_descent_step(float(W), float(H), x.numel(), _ptr(x), _ptr(y), _ptr(w), _ptr(h),
+                                 _ptr(gx), _ptr(gy), _ptr(mv), float(lr), float(sigma),
+                                 int(seed) & (2 ** 64 - 1), int(step), _stream_handle(x.device)))
 
 
 def check_wait_timeout(limit_ns: int, device=None):

@@ -273,7 +273,7 @@ void timed_end(long idx, cudaStream_t s) {
 
 // Coefficients into the workspace (FP32: S64 and K; tensor cores: partial tiles
 // and the tiled K operand), optionally also to a_out.
-pp_status run_coefficients(Ctx &c, float *a_out) {
+pp_status run_coefficients(Ctx &c, float *a_out, double *e_total = nullptr) {
     if (c.prec == PP_FP32) {
         PP_LAUNCH(PP_K_COEFF, c.L.stream, launch_coeff_simt(c.L), "coefficient kernel launch");
         PP_LAUNCH(PP_K_FINISH, c.L.stream, launch_finish_simt(c.L, nullptr, a_out), "finish kernel launch");
@@ -283,7 +283,7 @@ pp_status run_coefficients(Ctx &c, float *a_out) {
         PP_LAUNCH(PP_K_COEFF, c.L.stream, launch_coeff_tc(c.L, (int)c.prec, c.lay.plan, part),
                   "coefficient kernel launch");
         PP_LAUNCH(PP_K_FINISH, c.L.stream,
-                  launch_finish_tc(c.L, (int)c.prec, c.lay.plan, part, nullptr, a_out, Khi, Klo),
+                  launch_finish_tc(c.L, (int)c.prec, c.lay.plan, part, nullptr, a_out, Khi, Klo, e_total),
                   "finish kernel launch");
     }
     return PP_OK;
@@ -296,7 +296,7 @@ pp_status operand_from_a(Ctx &c, const float *a) {
     } else {
         PP_LAUNCH(PP_K_FINISH, c.L.stream,
                   launch_finish_tc(c.L, (int)c.prec, c.lay.plan, nullptr, a, nullptr, c.base + c.lay.K,
-                                   c.base + c.lay.Klo),
+                                   c.base + c.lay.Klo, nullptr),
                   "finish kernel launch");
     }
     return PP_OK;
@@ -341,9 +341,14 @@ pp_status energy_common(const pp_problem *p, pp_precision prec, pp_sample sample
     }
     const bool zero_S = a == nullptr && prec == PP_FP32;
     PP_LAUNCH(PP_K_PREP, c.L.stream, launch_prep(c.L, zero_S, e_total), "prep kernel launch");
-    st = a ? operand_from_a(c, a) : run_coefficients(c, nullptr);
+    // Tensor-core path, rectangle sampling, coefficients of these blocks: E comes from
+    // the FP32 coefficients (1/2 sum a S, FP64) in the finish kernel instead of the
+    // per-block sums, whose K operand is rounded to TF32 or bf16 pairs.
+    const bool e_from_a = prec != PP_FP32 && sample == PP_RECT && a == nullptr;
+    st = a ? operand_from_a(c, a) : run_coefficients(c, nullptr, e_from_a ? e_total : nullptr);
     if (st != PP_OK) return st;
-    st = run_energy(c, sample, e_block, e_total, want_grad ? gx : nullptr, want_grad ? gy : nullptr);
+    st = run_energy(c, sample, e_block, e_from_a ? nullptr : e_total, want_grad ? gx : nullptr,
+                    want_grad ? gy : nullptr);
     if (st != PP_OK) return st;
     return PP_OK;
 }
@@ -424,6 +429,47 @@ pp_status pp_phase_eval(const float *x, double L, const int32_t *m, int64_t coun
     if ((st = check_dev_ptr(out, dev, "out")) != PP_OK) return st;
     cudaError_t e = launch_phase_eval(x, 1.0 / L, m, count, evaluator, out, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "phase evaluation launch");
+    return PP_OK;
+}
+
+pp_status pp_energy_from_coeffs(const float *a, int32_t Mx, int32_t My, double W, double H, double *e_total,
+                                void *stream) {
+    int dev, sm, ccm;
+    unsigned *status;
+    pp_status st = device_info(&dev, &sm, &status, &ccm);
+    if (st != PP_OK) return st;
+    if (!(std::isfinite(W) && std::isfinite(H) && W >= 1e-300 && W <= 1e300 && H >= 1e-300 && H <= 1e300))
+        return fail(PP_EINVAL, "die size W=%g H=%g must be finite and in [1e-300, 1e300]", W, H);
+    if (Mx < 1 || My < 1 || Mx > 4096 || My > 4096) return fail(PP_EINVAL, "Mx=%d My=%d out of range", Mx, My);
+    if ((st = check_dev_ptr(a, dev, "a")) != PP_OK) return st;
+    if (((uintptr_t)e_total & 7) != 0) return fail(PP_EINVAL, "e_total is not 8-byte aligned");
+    if ((st = check_dev_ptr(e_total, dev, "e_total")) != PP_OK) return st;
+    PP_TRY(cudaMemsetAsync(e_total, 0, sizeof(double), (cudaStream_t)stream), "memset e_total");
+    cudaError_t e = launch_energy_from_coeffs(a, Mx, My, W, H, e_total, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "energy-from-coefficients launch");
+    return PP_OK;
+}
+
+pp_status pp_descent_step(double W, double H, int64_t n, float *x, float *y, const float *w,
+                          const float *h, const float *gx, const float *gy, const uint8_t *movable,
+                          float lr, float sigma, uint64_t seed, uint64_t step, void *stream) {
+    int dev, sm, ccm;
+    unsigned *status;
+    pp_status st = device_info(&dev, &sm, &status, &ccm);
+    if (st != PP_OK) return st;
+    if (!(std::isfinite(W) && std::isfinite(H) && W >= 1e-300 && W <= 1e300 && H >= 1e-300 && H <= 1e300))
+        return fail(PP_EINVAL, "die size W=%g H=%g must be finite and in [1e-300, 1e300]", W, H);
+    if (n < 0 || n > INT64_C(0x7FFFFFFF)) return fail(PP_EINVAL, "n=%lld out of range", (long long)n);
+    if (!std::isfinite(lr) || !std::isfinite(sigma)) return fail(PP_EINVAL, "lr and sigma must be finite");
+    if (n == 0) return PP_OK;
+    const void *ptrs[6] = {x, y, w, h, gx, gy};
+    const char *names[6] = {"x", "y", "w", "h", "gx", "gy"};
+    for (int i = 0; i < 6; ++i)
+        if ((st = check_dev_ptr(ptrs[i], dev, names[i])) != PP_OK) return st;
+    if (movable && (st = check_dev_ptr(movable, dev, "movable")) != PP_OK) return st;
+    cudaError_t e = launch_descent_step((float)W, (float)H, n, x, y, w, h, gx, gy, movable, lr, sigma,
+                                        seed, step, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "descent step launch");
     return PP_OK;
 }
 

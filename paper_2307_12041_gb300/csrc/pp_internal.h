@@ -40,12 +40,19 @@ struct TcPlan {
 TcPlan tc_plan(int n, int Mx, int My);
 cudaError_t launch_coeff_tc(const Launch &L, int prec, const TcPlan &P, float *part);
 cudaError_t launch_finish_tc(const Launch &L, int prec, const TcPlan &P, const float *part,
-                             const float *a_in, float *a_out, void *Khi, void *Klo);
+                             const float *a_in, float *a_out, void *Khi, void *Klo, double *e_total);
 cudaError_t launch_energy_tc(const Launch &L, int prec, int sample, const TcPlan &P, void *Khi,
                              void *Klo, float *e_block, double *e_total, float *gx, float *gy);
 
 // pp_api.cu: message returned by pp_last_error() for the calling thread
 void set_last_error(const char *msg);
+// E = 1/2 sum_uv a_uv^2 / G_uv (FP64) from coefficients a (Mx x My, u-major), added to *e_total
+cudaError_t launch_energy_from_coeffs(const float *a, int Mx, int My, double W, double H, double *e_total,
+                                      cudaStream_t stream);
+cudaError_t launch_descent_step(float W, float H, int64_t n, float *x, float *y, const float *w,
+                                const float *h, const float *gx, const float *gy,
+                                const uint8_t *movable, float lr, float sigma, uint64_t seed,
+                                uint64_t step, cudaStream_t stream);
 cudaError_t launch_phase_eval(const float *x, double invL, const int32_t *m, int64_t count,
                               int evaluator, float *out, cudaStream_t stream);
 // one CTA whose thread waits (bounded) on an mbarrier nothing completes

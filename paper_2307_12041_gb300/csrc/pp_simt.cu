@@ -76,6 +76,58 @@ cudaError_t launch_prep(const Launch &L, bool zero_S, double *e_total) {
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Descent step: x <- clamp(x - lr gx + sigma n0, w/2, W - w/2), likewise y, with
+// Box-Muller normals from Philox4x32-10 (Salmon et al., SC 2011) keyed by the seed
+// and counted by (block, step).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const unsigned lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+        const unsigned lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+        k.x += 0x9E3779B9u;
+        k.y += 0xBB67AE85u;
+    }
+    return c;
+}
+
+__global__ void descent_step_kernel(float W, float H, int64_t n, float *__restrict__ x,
+                                    float *__restrict__ y, const float *__restrict__ w,
+                                    const float *__restrict__ h, const float *__restrict__ gx,
+                                    const float *__restrict__ gy, const uint8_t *__restrict__ movable,
+                                    float lr, float sigma, uint2 key, unsigned step) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        if (movable && !movable[i]) continue;
+        const uint4 o = philox4x32_10(make_uint4((unsigned)i, step, 0u, 0u), key);
+        const float u0 = ((float)o.x + 0.5f) * 0x1p-32f;          // (0, 1]
+        const float u1 = ((float)o.y + 0.5f) * 0x1p-32f;
+        const float r = sqrtf(-2.f * logf(u0));
+        float sn, cs;
+        sincospif(2.f * u1, &sn, &cs);
+        const float wi = w[i], hi = h[i];
+        const float xi = x[i] - lr * gx[i] + sigma * (r * cs);
+        const float yi = y[i] - lr * gy[i] + sigma * (r * sn);
+        x[i] = fminf(fmaxf(xi, 0.5f * wi), W - 0.5f * wi);
+        y[i] = fminf(fmaxf(yi, 0.5f * hi), H - 0.5f * hi);
+    }
+}
+
+cudaError_t launch_descent_step(float W, float H, int64_t n, float *x, float *y, const float *w,
+                                const float *h, const float *gx, const float *gy,
+                                const uint8_t *movable, float lr, float sigma, uint64_t seed,
+                                uint64_t step, cudaStream_t stream) {
+    if (n == 0) return cudaSuccess;
+    const int64_t want = (n + 255) / 256;
+    const int grid = (int)(want < 65535 ? want : 65535);
+    descent_step_kernel<<<grid, 256, 0, stream>>>(W, H, n, x, y, w, h, gx, gy, movable, lr, sigma,
+                                                  make_uint2((unsigned)seed, (unsigned)(seed >> 32)),
+                                                  (unsigned)step);
+    return cudaGetLastError();
+}
+
 // Eight consecutive modes m0..m0+7 of the scaled rectangle basis of one block:
 // out[j] = c cos(pi m s) sin(pi m t), m = m0 + j (value v0 at m = 0).
 __device__ __forceinline__ void rect_run8(const AxisRec &r, int m0, float out[8]) {

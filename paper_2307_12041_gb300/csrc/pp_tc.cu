@@ -454,9 +454,12 @@ __global__ void __launch_bounds__(C_THREADS, 1) tc_coeff_kernel(const CoeffArgs 
                 if (*abort_flag) break;
                 if ((int)(it % C_GEN_GROUPS) != gr) continue;
                 const int s = it % C_STAGES;
-                if (!mbar_wait(&bars.recs_full[s], (it / C_STAGES) & 1, kWaitLimit, abort_flag) ||
-                    (it >= C_STAGES &&
-                     !mbar_wait(&bars.empty[s], ((it / C_STAGES) - 1) & 1, kWaitLimit, abort_flag))) {
+                // empty first: the MMAs have consumed stage it - 3, so the other group
+                // has filled it and its records phase is complete; only then is the
+                // parity wait on recs_full unambiguous (it cannot be two phases behind)
+                if ((it >= C_STAGES &&
+                     !mbar_wait(&bars.empty[s], ((it / C_STAGES) - 1) & 1, kWaitLimit, abort_flag)) ||
+                    !mbar_wait(&bars.recs_full[s], (it / C_STAGES) & 1, kWaitLimit, abort_flag)) {
                     raise_timeout(args.status, abort_flag);
                     break;
                 }
@@ -515,13 +518,34 @@ __global__ void __launch_bounds__(C_THREADS, 1) tc_coeff_kernel(const CoeffArgs 
 // ===========================================================================
 // Finish: FP64 sum of the slice partials -> a, K in the energy operand layout
 // ===========================================================================
+// Sum of one double per thread over the CTA, added to *dst (one atomic per CTA).
+__device__ __forceinline__ void cta_add_double(double v, double *dst) {
+    __shared__ double part_sums[32];
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    if ((threadIdx.x & 31) == 0) part_sums[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += part_sums[w];
+        atomicAdd(dst, t);
+    }
+}
+
+// e_total (optional, with a computed here from the partials): E = 1/2 sum_uv a_uv S_uv,
+// which equals 1/2 sum_i N_i of the blocks the partials came from, in FP64 from the
+// FP32 coefficients.  The per-block sums of the energy kernel use K rounded to the
+// operand precision; K is shared by all blocks, so its rounding shifts every N_i
+// alike and their total by up to about one TF32 unit; this sum does not.
 template <int PREC>
 __global__ void tc_finish_kernel(const float *__restrict__ part, int slices, int Mxc, int Myc,
                                  const float *__restrict__ a_in, float *__restrict__ a_out,
                                  void *__restrict__ Kop, void *__restrict__ Klo, int Mx, int My,
-                                 int Mxe, int Mye, float piW, float piH, float invWH) {
+                                 int Mxe, int Mye, float piW, float piH, float invWH,
+                                 double *__restrict__ e_total) {
     // FP32 throughout (FP64 is a narrow pipe on this GPU): the slice partials are
     // summed with Kahan compensation; the operand is TF32 or bf16 anyway.
+    double e_acc = 0.0;
     const size_t total = (size_t)Mxe * Mye;
     for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
          idx += (size_t)gridDim.x * blockDim.x) {
@@ -546,6 +570,7 @@ __global__ void tc_finish_kernel(const float *__restrict__ part, int slices, int
                 const float G = (u == 0 && v == 0) ? 0.f : eps * invWH / (ku * ku + lv * lv);
                 av = G * f * g * S;
                 if (a_out) a_out[(size_t)u * My + v] = av;
+                e_acc += 0.5 * (double)av * ((double)f * (double)g * (double)S);
             }
             kv = f * av * g;
         }
@@ -561,6 +586,7 @@ __global__ void tc_finish_kernel(const float *__restrict__ part, int slices, int
             reinterpret_cast<__nv_bfloat16 *>(Klo)[off] = lo;
         }
     }
+    if (e_total) cta_add_double(e_acc, e_total);
 }
 
 // ===========================================================================
@@ -871,8 +897,8 @@ __device__ __forceinline__ void drain_pass(EnergyBars &bars, volatile int *abort
 
 // End of a row tile for one epilogue thread: column half 1 puts its sums in
 // shared memory (double-buffered by tile parity, so that a one-pass tile cannot
-// overwrite them before they are read); half 0 waits for them (named barrier 1,
-// all epilogue threads) and writes the block's outputs and its share of E.
+// overwrite them before they are read); after named barrier 1 (all epilogue
+// threads) half 0 adds them and writes the block's outputs and its share of E.
 __device__ __forceinline__ void finish_tile(EnergyBars &bars, volatile int *abort_flag, const EnergyArgs &args,
                                             int tile, int row, int cq, float eN, float eX, float eY) {
     if (cq != 0) {
@@ -880,10 +906,11 @@ __device__ __forceinline__ void finish_tile(EnergyBars &bars, volatile int *abor
         r[0] = eN;
         r[1] = eX;
         r[2] = eY;
-        asm volatile("bar.arrive 1, %0;" ::"r"(E_DRAIN_THREADS) : "memory");
-        return;
     }
+    // both halves wait (no half can run ahead into the next tile's arrival and
+    // complete a barrier phase that belongs to this tile)
     asm volatile("bar.sync 1, %0;" ::"r"(E_DRAIN_THREADS) : "memory");
+    if (cq != 0) return;
     const int b = tile * E_ROWS + row;
     const bool valid = b < args.n;
     eN += bars.red[tile & 1][row][0];
@@ -1226,8 +1253,34 @@ cudaError_t launch_coeff_tc(const Launch &L, int prec, const TcPlan &P, float *p
     return cudaGetLastError();
 }
 
+__global__ void energy_from_coeffs_kernel(const float *__restrict__ a, int Mx, int My, double piW,
+                                          double piH, double invWH, double *__restrict__ e_total) {
+    double e = 0.0;
+    const size_t total = (size_t)Mx * My;
+    for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (size_t)gridDim.x * blockDim.x) {
+        const int u = (int)(idx / My), v = (int)(idx % My);
+        if (u == 0 && v == 0) continue;
+        const double ku = u * piW, lv = v * piH;
+        const double inv_G = (ku * ku + lv * lv) / ((u ? 2.0 : 1.0) * (v ? 2.0 : 1.0) * invWH);
+        const double av = a[idx];
+        e += 0.5 * av * av * inv_G;
+    }
+    cta_add_double(e, e_total);
+}
+
+cudaError_t launch_energy_from_coeffs(const float *a, int Mx, int My, double W, double H, double *e_total,
+                                      cudaStream_t stream) {
+    const size_t total = (size_t)Mx * My;
+    int blocks = (int)((total + 255) / 256);
+    if (blocks > 1024) blocks = 1024;
+    const double PI = 3.141592653589793;
+    energy_from_coeffs_kernel<<<blocks, 256, 0, stream>>>(a, Mx, My, PI / W, PI / H, 1.0 / (W * H), e_total);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_finish_tc(const Launch &L, int prec, const TcPlan &P, const float *part,
-                             const float *a_in, float *a_out, void *Khi, void *Klo) {
+                             const float *a_in, float *a_out, void *Khi, void *Klo, double *e_total) {
     const size_t total = (size_t)P.Mxe * P.Mye;
     int blocks = (int)((total + 255) / 256);
     if (blocks > 8 * L.sm_count) blocks = 8 * L.sm_count;
@@ -1236,10 +1289,12 @@ cudaError_t launch_finish_tc(const Launch &L, int prec, const TcPlan &P, const f
     const float piW = (float)(PI / L.W), piH = (float)(PI / L.H), invWH = (float)(1.0 / (L.W * L.H));
     if (prec == 1)
         tc_finish_kernel<1><<<blocks, 256, 0, L.stream>>>(part, P.slices, P.Mxc, P.Myc, a_in, a_out, Khi,
-                                                          Klo, L.Mx, L.My, P.Mxe, P.Mye, piW, piH, invWH);
+                                                          Klo, L.Mx, L.My, P.Mxe, P.Mye, piW, piH, invWH,
+                                                          a_in ? nullptr : e_total);
     else
         tc_finish_kernel<2><<<blocks, 256, 0, L.stream>>>(part, P.slices, P.Mxc, P.Myc, a_in, a_out, Khi,
-                                                          Klo, L.Mx, L.My, P.Mxe, P.Mye, piW, piH, invWH);
+                                                          Klo, L.Mx, L.My, P.Mxe, P.Mye, piW, piH, invWH,
+                                                          a_in ? nullptr : e_total);
     return cudaGetLastError();
 }
 

@@ -2,15 +2,15 @@
 Sec. IV, whose Nesterov parameters the paper does not restate).
 
 Each step evaluates E and its gradient through the C ABI, then moves the
-movable blocks:  x <- clamp(x - lr * dE/dx + j, w/2, W - w/2)  (same for y), with
-a seed-fixed jitter j ~ N(0, (jitter * W)^2) per block and step drawn on the host
-(PCG64 keyed by (seed, step)) and uploaded.
+movable blocks with pp_descent_step:  x <- clamp(x - lr * dE/dx + j, w/2, W - w/2)
+(same for y), with a seed-fixed jitter j ~ N(0, (jitter * W)^2) per block and step
+drawn on the device (Philox4x32-10 counted by (block, step), Box-Muller).
 
 Chunked evaluation.  The coefficients are a sum over blocks (Eq. aup sums over
 i), so with the blocks cut into chunks, a = sum_c a(chunk c) (pp_coeffs per chunk)
-and each chunk's energies and gradients follow from pp_grad with that total a.
-This bounds the workspace by the chunk size for placements too large for one
-call.
+and each chunk's gradients follow from pp_grad with that total a; the total
+energy is 1/2 sum_uv a_uv S_uv of the total a (pp_energy_from_coeffs).  This
+bounds the workspace by the chunk size for placements too large for one call.
 """
 from __future__ import annotations
 
@@ -46,14 +46,13 @@ def evaluate_chunked(x, y, w, h, c, W, H, Mx, My, prec="tf32", chunk: Optional[i
         a = ac if a is None else a + ac
     gx = torch.empty_like(x)
     gy = torch.empty_like(y)
-    E = torch.zeros(1, dtype=torch.float64, device=x.device)
     for s, e in zip(cuts[:-1], cuts[1:]):
-        gxc, gyc, _, ec = binding.grad(x[s:e], y[s:e], w[s:e], h[s:e], sl(c, s, e), W, H, Mx, My,
-                                       prec, a=a)
+        gxc, gyc, _, _ = binding.grad(x[s:e], y[s:e], w[s:e], h[s:e], sl(c, s, e), W, H, Mx, My,
+                                      prec, a=a, want_energy=False)
         gx[s:e] = gxc
         gy[s:e] = gyc
-        E += ec
-    return gx, gy, E
+    # E = 1/2 sum_uv a_uv S_uv from the summed coefficients (the whole placement's)
+    return gx, gy, binding.energy_from_coeffs(a, W, H)
 
 
 def descend(p: synth.Placement, steps: int, lr: float = 1e-4, jitter: float = 1e-6,
@@ -66,8 +65,6 @@ def descend(p: synth.Placement, steps: int, lr: float = 1e-4, jitter: float = 1e
     x = x.clone()
     y = y.clone()
     mov = None if p.movable is None else torch.from_numpy(p.movable).to(dev)
-    lo_x, hi_x = 0.5 * w, p.W - 0.5 * w
-    lo_y, hi_y = 0.5 * h, p.H - 0.5 * h
     res = DescentResult()
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)
@@ -77,14 +74,7 @@ def descend(p: synth.Placement, steps: int, lr: float = 1e-4, jitter: float = 1e
         res.energy.append(E)
         if callback is not None:
             callback(k, x, y, gx, gy, E)
-        j = torch.from_numpy(synth.descent_jitter(p.n, k, seed, jitter * p.W)).to(dev)
-        dx = -lr * gx + j[0]
-        dy = -lr * gy + j[1]
-        if mov is not None:
-            dx = torch.where(mov, dx, torch.zeros_like(dx))
-            dy = torch.where(mov, dy, torch.zeros_like(dy))
-        x = torch.minimum(torch.maximum(x + dx, lo_x), hi_x)
-        y = torch.minimum(torch.maximum(y + dy, lo_y), hi_y)
+        binding.descent_step(x, y, w, h, gx, gy, p.W, p.H, lr, jitter * p.W, seed, k, movable=mov)
     t1.record()
     torch.cuda.synchronize()
     binding.sync_status(dev)
@@ -92,3 +82,68 @@ def descend(p: synth.Placement, steps: int, lr: float = 1e-4, jitter: float = 1e
     res.x, res.y = x, y
     res.ms_per_step = t0.elapsed_time(t1) / max(steps, 1)
     return res
+
+
+def _main(argv=None) -> int:
+    """Run the descent loop on a synthetic workload and print one JSON line:
+    time per step, block-mode^2 terms/s, the energy trace, and the same first
+    evaluation in FP32 plain for comparison (time and relative gradient gap)."""
+    import argparse
+    import json
+    ap = argparse.ArgumentParser(prog="python -m paper_2307_12041_gb300.descent")
+    ap.add_argument("--workload", type=int, default=4, help="synth.WORKLOADS index")
+    ap.add_argument("--n", type=int, default=None, help="first n blocks only")
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--lr", type=float, default=1e-4)
+    ap.add_argument("--jitter", type=float, default=1e-6)
+    ap.add_argument("--prec", default="tf32")
+    ap.add_argument("--chunk", type=int, default=None)
+    ap.add_argument("--fp32-steps", type=int, default=2, help="FP32-plain evaluations to time")
+    ap.add_argument("--check-every", type=int, default=0,
+                    help="also evaluate E in FP32 plain at the current positions every K steps")
+    a = ap.parse_args(argv)
+    p = synth.workload(a.workload, n=a.n)
+    dev = torch.device("cuda")
+    terms = float(p.n) * p.Mx * p.My
+    descend(p, 2, a.lr, a.jitter, prec=a.prec, chunk=a.chunk)          # warm-up (workspaces, modules)
+    checks = []
+    if a.check_every:
+        # a separate run (checks would perturb the timing): E in both precisions
+        def cb(k, xk, yk, gxk, gyk, Ek):
+            if k % a.check_every == 0:
+                wk, hk, ck = binding.to_device(p, dev)[2:]
+                Ep = evaluate_chunked(xk, yk, wk, hk, ck, p.W, p.H, p.Mx, p.My, "fp32", a.chunk)[2]
+                checks.append((k, float(Ek.item()), float(Ep.item())))
+        descend(p, a.steps, a.lr, a.jitter, prec=a.prec, chunk=a.chunk, callback=cb)
+    res = descend(p, a.steps, a.lr, a.jitter, prec=a.prec, chunk=a.chunk)
+    x, y, w, h, c = binding.to_device(p, dev)
+    x, y = res.x, res.y                                 # compare at the final positions
+    g_mixed = evaluate_chunked(x, y, w, h, c, p.W, p.H, p.Mx, p.My, a.prec, a.chunk)
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record()
+    for _ in range(a.fp32_steps):
+        g_plain = evaluate_chunked(x, y, w, h, c, p.W, p.H, p.Mx, p.My, "fp32", a.chunk)
+    t1.record()
+    torch.cuda.synchronize()
+    binding.sync_status(dev)
+    fp32_ms = t0.elapsed_time(t1) / max(a.fp32_steps, 1)
+    scale = float(torch.maximum(g_plain[0].abs().max(), g_plain[1].abs().max()))
+    gap = max(float((g_mixed[0] - g_plain[0]).abs().max()), float((g_mixed[1] - g_plain[1]).abs().max()))
+    e = res.energy
+    print(json.dumps({
+        "workload": synth.WORKLOADS[a.workload]["name"], "n": p.n, "Mx": p.Mx, "My": p.My,
+        "precision": a.prec, "steps": a.steps, "lr": a.lr, "jitter": a.jitter, "chunk": a.chunk,
+        "ms_per_step": res.ms_per_step, "terms_per_s": terms / (res.ms_per_step / 1e3),
+        "energy_first": e[0], "energy_last": e[-1],
+        "energy_trace": [e[i] for i in range(0, len(e), max(1, len(e) // 10))] + [e[-1]],
+        "fp32_plain_ms_per_eval": fp32_ms, "speedup_vs_fp32_plain": fp32_ms / res.ms_per_step,
+        "grad_gap_vs_fp32_plain": gap / scale if scale > 0 else gap,
+        "E_gap_vs_fp32_plain": abs(float(g_mixed[2]) - float(g_plain[2])) / abs(float(g_plain[2])),
+        "E_checks": checks,
+    }), flush=True)
+    return 0
+
+
+if __name__ == "__main__":
+    raise SystemExit(_main())

@@ -159,9 +159,3 @@ def workload(index: int, n: int | None = None) -> Placement:
         p.name = spec["name"]
     return p
 
-
-def descent_jitter(n: int, step: int, seed: int, scale: float) -> np.ndarray:
-    """Seed-fixed per-step jitter for the descent loop: N(0, scale^2) per block,
-    from PCG64 keyed by (seed, step)."""
-    g = np.random.Generator(np.random.PCG64(np.random.SeedSequence([seed, step])))
-    return g.normal(0.0, scale, (2, n)).astype(np.float32)

@@ -162,7 +162,14 @@ def big():
     a = O.coefficients(p.W, p.H, p.x, p.y, p.w, p.h, p.c, p.Mx, p.My)
     idx = np.sort(np.random.default_rng(5).choice(p.n, 2000, replace=False))
     N, gx, gy = O.energy_grad(p.W, p.H, p.x, p.y, p.w, p.h, p.c, a, idx=idx)
-    return p, a, idx, dict(N=N, gx=gx, gy=gy)
+    E = 0.5 * float(np.sum(O.energy_grad(p.W, p.H, p.x, p.y, p.w, p.h, p.c, a)[0]))
+    return p, a, idx, dict(N=N, gx=gx, gy=gy, E=E)
+
+
+# Bound on the relative error of the total energy: E = 1/2 sum a S is quadratic in
+# the coefficients, so about twice their normalised error (FP32: the per-block
+# FP64 sum; TF32, BF16x3: from the FP32 coefficients of the tensor-core contraction).
+E_TOL = {"fp32": 1e-6, "tf32": 2e-4, "bf16x3": 2e-5}
 
 
 @pytest.mark.parametrize("prec", ["fp32", "tf32", "bf16x3"])
@@ -179,8 +186,19 @@ def test_full_size_workload_sampled(pp, big, prec):
     assert e <= tol, (prec, "N", e)
     e = gerr(out["gx"][ti].double().cpu().numpy(), out["gy"][ti].double().cpu().numpy(), ref)
     assert e <= tol, (prec, "grad", e)
-    # E from the GPU's per-block energies equals the GPU's FP64 total
-    assert abs(out["E"] - 0.5 * float(out["N"].double().sum())) <= 1e-6 * abs(out["E"])
+    e = abs(out["E"] - ref["E"]) / abs(ref["E"])
+    assert e <= E_TOL[prec], (prec, "E", e)
+    if prec == "fp32":
+        # E from the GPU's per-block energies equals the GPU's FP64 total
+        assert abs(out["E"] - 0.5 * float(out["N"].double().sum())) <= 1e-6 * abs(out["E"])
+
+
+def test_energy_from_coefficients(pp, big):
+    """pp_energy_from_coeffs on the oracle's coefficients reproduces the oracle's
+    1/2 sum_i N_i (the identity 1/2 sum_i N_i = 1/2 sum_uv a_uv S_uv, S = a / G)."""
+    p, a_ref, _, ref = big
+    E = float(pp.binding.energy_from_coeffs(torch.from_numpy(a_ref.astype(np.float32)).cuda(), p.W, p.H).item())
+    assert abs(E - ref["E"]) <= 1e-6 * abs(ref["E"])
 
 
 # ---------------------------------------------------------------------------
