@@ -545,7 +545,7 @@ __global__ void tc_finish_kernel(const float *__restrict__ part, int slices, int
                                  double *__restrict__ e_total) {
     // FP32 throughout (FP64 is a narrow pipe on this GPU): the slice partials are
     // summed with Kahan compensation; the operand is TF32 or bf16 anyway.
-    double e_acc = 0.0;
+    float e_acc = 0.f;                 // this thread's few terms; summed across the CTA in FP64
     const size_t total = (size_t)Mxe * Mye;
     for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
          idx += (size_t)gridDim.x * blockDim.x) {
@@ -570,7 +570,7 @@ __global__ void tc_finish_kernel(const float *__restrict__ part, int slices, int
                 const float G = (u == 0 && v == 0) ? 0.f : eps * invWH / (ku * ku + lv * lv);
                 av = G * f * g * S;
                 if (a_out) a_out[(size_t)u * My + v] = av;
-                e_acc += 0.5 * (double)av * ((double)f * (double)g * (double)S);
+                e_acc = fmaf(0.5f * av, f * g * S, e_acc);
             }
             kv = f * av * g;
         }
@@ -586,7 +586,7 @@ __global__ void tc_finish_kernel(const float *__restrict__ part, int slices, int
             reinterpret_cast<__nv_bfloat16 *>(Klo)[off] = lo;
         }
     }
-    if (e_total) cta_add_double(e_acc, e_total);
+    if (e_total) cta_add_double((double)e_acc, e_total);
 }
 
 // ===========================================================================
