@@ -183,23 +183,38 @@ def barrier(world):
 # ---------------------------------------------------------------------------
 # the step
 # ---------------------------------------------------------------------------
-def make_inputs(device, n=None):
+def make_inputs(device, n=None, workload=WORKLOAD_INDEX):
     import torch
     from paper_2307_12041_gb300 import synth
-    p = synth.workload(WORKLOAD_INDEX, n=n)
+    p = synth.workload(workload, n=n)
     t = lambda a: torch.from_numpy(a).to(device)
     return p, (t(p.x), t(p.y), t(p.w), t(p.h), None)
 
 
-def time_steps(binding, p, dev_in, prec, steps, warmup, flush, outs, kernel_timing=False):
+def time_steps(binding, p, dev_in, prec, steps, warmup, flush, outs, kernel_timing=False,
+               mode="grad"):
     """Per-step CUDA-event times (ms) of `steps` evaluations after `warmup`; the L2
     is flushed (FLUSH_BYTES written) before every step, outside the events.  With
     kernel_timing, the library brackets each of its launches in the timed steps
-    with events on the launch stream; returns (step times, per-kernel times)."""
+    with events on the launch stream; returns (step times, per-kernel times).
+    mode "grad": one pp_grad call (a computed inside); "autograd": the autograd
+    function's forward (pp_energy) and backward (pp_grad, a recomputed), fixed
+    blocks masked."""
     import torch
     x, y, w, h, c = dev_in
     stream = torch.cuda.current_stream()
-    run = lambda: binding.grad(x, y, w, h, c, p.W, p.H, p.Mx, p.My, prec, out=outs)
+    if mode == "autograd":
+        mov = None if p.movable is None else torch.from_numpy(p.movable).to(x.device)
+        xg = x.detach().clone().requires_grad_(True)
+        yg = y.detach().clone().requires_grad_(True)
+
+        def run():
+            xg.grad = None
+            yg.grad = None
+            E = binding.PoissonEnergy.apply(xg, yg, w, h, c, p.W, p.H, p.Mx, p.My, prec, "rect", mov)
+            E.backward()
+    else:
+        run = lambda: binding.grad(x, y, w, h, c, p.W, p.H, p.Mx, p.My, prec, out=outs)
     for _ in range(warmup):
         flush.zero_()
         run()
@@ -283,12 +298,14 @@ def errors_vs(ref, got):
     return out
 
 
-def cpu_baseline(binding, precs, device, n_sample):
+def cpu_baseline(binding, precs, device, n_sample, workload=WORKLOAD_INDEX):
     """The FP64 oracle as it stands on the host cores, on the first `n_sample`
     blocks of the workload (all modes), plus the GPU's error on that sample."""
     from oracle import series as O
     from paper_2307_12041_gb300 import synth
-    p = synth.workload(WORKLOAD_INDEX).subset(np.arange(n_sample))
+    full_n = synth.WORKLOADS[workload]["n"]
+    n_sample = min(n_sample, full_n)
+    p = synth.workload(workload).subset(np.arange(n_sample))
     cores = int(os.environ.get("ORACLE_THREADS", os.cpu_count() or 1))
     t0 = time.perf_counter()
     ref = O.evaluate(p.W, p.H, p.x, p.y, p.w, p.h, p.c, p.Mx, p.My)
@@ -301,7 +318,7 @@ def cpu_baseline(binding, precs, device, n_sample):
         errs[prec] = errors_vs(ref, got)
     base = {"value": n_sample * p.Mx * p.My / dt, "unit": "terms/s", "cores": cores,
             "kind": "oracle", "seconds": dt,
-            "sample": f"first {n_sample} of {synth.WORKLOADS[WORKLOAD_INDEX]['n']} blocks, "
+            "sample": f"first {n_sample} of {full_n} blocks, "
                       f"all {p.Mx}x{p.My} modes: coefficients, per-block energy, gradient (FP64 numpy)"}
     return base, errs
 
@@ -320,7 +337,7 @@ def run_ours(args):
     if prec not in avail:
         raise SystemExit(f"precision {prec} not available: {avail}")
 
-    p, dev_in = make_inputs(device)
+    p, dev_in = make_inputs(device, workload=args.workload)
     n = p.n
     outs = (torch.empty(n, dtype=torch.float32, device=device),
             torch.empty(n, dtype=torch.float32, device=device),
@@ -336,7 +353,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     clocks.mark("t0")
     step_ms, ktimes = time_steps(binding, p, dev_in, prec, args.steps, args.warmup, flush, outs,
-                                 kernel_timing=True)
+                                 kernel_timing=True, mode=args.mode)
     clocks.mark("t1")
     torch.cuda.synchronize()
     barrier(world)
@@ -369,7 +386,7 @@ def run_ours(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": prec,
         "data": "synthetic",
-        "config": {"workload": synth.WORKLOADS[WORKLOAD_INDEX]["name"], "n": n, "Mx": p.Mx,
+        "config": {"workload": synth.WORKLOADS[args.workload]["name"], "mode": args.mode, "n": n, "Mx": p.Mx,
                    "My": p.My, "sample": "rect", "precision": prec, "W": p.W, "H": p.H,
                    "l2": "flushed: 256 MiB written before every timed step",
                    "parallelism": f"replicas x{world}"},
@@ -386,7 +403,8 @@ def run_ours(args):
         # FP32 plain on the same workload (the "vs FP32" half of the metric)
         if prec != "fp32":
             torch.cuda.synchronize()
-            f_ms, _ = time_steps(binding, p, dev_in, "fp32", args.steps, args.warmup, flush, outs)
+            f_ms, _ = time_steps(binding, p, dev_in, "fp32", args.steps, args.warmup, flush, outs,
+                                 mode=args.mode)
             fv = terms * args.steps / (sum(f_ms) / 1e3)
             line["fp32_plain"] = {"value": fv, "ms_per_step": sum(f_ms) / args.steps,
                                   "speedup_of_mixed": value / world / fv}
@@ -396,7 +414,7 @@ def run_ours(args):
                        "ms_per_step": e_ms}
         if world == 1 and not args.no_cpu_baseline:
             precs = [prec] + (["fp32"] if prec != "fp32" else [])
-            base, errs = cpu_baseline(binding, precs, device, args.cpu_sample)
+            base, errs = cpu_baseline(binding, precs, device, args.cpu_sample, args.workload)
             line["cpu_baseline"] = base
             line["errors_vs_fp64_oracle"] = {"sample": base["sample"], **errs}
         print(json.dumps(line), flush=True)
@@ -412,7 +430,9 @@ def run_reference(args):
     from oracle import series as O
     from paper_2307_12041_gb300 import synth
     n_s = args.ref_sample
-    p = synth.workload(WORKLOAD_INDEX).subset(np.arange(n_s))
+    full_n = synth.WORKLOADS[args.workload]["n"]
+    n_s = min(n_s, full_n)
+    p = synth.workload(args.workload).subset(np.arange(n_s))
     for _ in range(args.warmup):
         O.evaluate(p.W, p.H, p.x, p.y, p.w, p.h, p.c, p.Mx, p.My)
     t0 = time.perf_counter()
@@ -422,13 +442,13 @@ def run_reference(args):
     terms = float(n_s) * p.Mx * p.My
     value = terms * args.steps / dt
     cores = int(os.environ.get("ORACLE_THREADS", os.cpu_count() or 1))
-    sample = (f"first {n_s} of {synth.WORKLOADS[WORKLOAD_INDEX]['n']} blocks, all "
+    sample = (f"first {n_s} of {full_n} blocks, all "
               f"{p.Mx}x{p.My} modes, per step")
     line = {"metric": METRIC, "value": value, "unit": "terms/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "impl": "reference",
-            "config": {"workload": synth.WORKLOADS[WORKLOAD_INDEX]["name"], "n": p.n,
+            "config": {"workload": synth.WORKLOADS[args.workload]["name"], "n": p.n,
                        "Mx": p.Mx, "My": p.My, "sample": "rect", "precision": "f64"},
             "cpu_baseline": {"value": value, "unit": "terms/s", "cores": cores, "kind": "oracle",
                              "sample": sample},
@@ -447,6 +467,10 @@ def main(argv=None):
     ap.add_argument("--cpu-sample", type=int, default=200000)
     ap.add_argument("--ref-sample", type=int, default=10000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", type=int, default=WORKLOAD_INDEX,
+                    help="synth.WORKLOADS index (default: the metric's 200k x 512^2 workload)")
+    ap.add_argument("--mode", choices=["grad", "autograd"], default="grad",
+                    help="grad: one pp_grad per step; autograd: energy forward + adjoint backward")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
