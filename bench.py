@@ -199,20 +199,26 @@ def time_steps(binding, p, dev_in, prec, steps, warmup, flush, outs, kernel_timi
     with events on the launch stream; returns (step times, per-kernel times).
     mode "grad": one pp_grad call (a computed inside); "autograd": the autograd
     function's forward (pp_energy) and backward (pp_grad, a recomputed), fixed
-    blocks masked."""
+    blocks masked; "block-adjoint": per-block energies forward and the backward for
+    a random upstream gradient (two coefficient and two energy contractions)."""
     import torch
     x, y, w, h, c = dev_in
     stream = torch.cuda.current_stream()
-    if mode == "autograd":
+    if mode in ("autograd", "block-adjoint"):
         mov = None if p.movable is None else torch.from_numpy(p.movable).to(x.device)
         xg = x.detach().clone().requires_grad_(True)
         yg = y.detach().clone().requires_grad_(True)
+        gw = torch.randn(p.n, generator=torch.Generator().manual_seed(5), dtype=torch.float32).to(x.device)
 
         def run():
             xg.grad = None
             yg.grad = None
-            E = binding.PoissonEnergy.apply(xg, yg, w, h, c, p.W, p.H, p.Mx, p.My, prec, "rect", mov)
-            E.backward()
+            if mode == "autograd":
+                E = binding.PoissonEnergy.apply(xg, yg, w, h, c, p.W, p.H, p.Mx, p.My, prec, "rect", mov)
+                E.backward()
+            else:       # per-block energies, backward for an arbitrary upstream gradient
+                N = binding.PoissonBlockEnergies.apply(xg, yg, w, h, c, p.W, p.H, p.Mx, p.My, prec, mov)
+                N.backward(gw)
     else:
         run = lambda: binding.grad(x, y, w, h, c, p.W, p.H, p.Mx, p.My, prec, out=outs)
     for _ in range(warmup):
@@ -469,8 +475,9 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", type=int, default=WORKLOAD_INDEX,
                     help="synth.WORKLOADS index (default: the metric's 200k x 512^2 workload)")
-    ap.add_argument("--mode", choices=["grad", "autograd"], default="grad",
-                    help="grad: one pp_grad per step; autograd: energy forward + adjoint backward")
+    ap.add_argument("--mode", choices=["grad", "autograd", "block-adjoint"], default="grad",
+                    help="grad: one pp_grad per step; autograd: energy forward + adjoint backward; "
+                         "block-adjoint: per-block energies forward + vector-output adjoint")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")

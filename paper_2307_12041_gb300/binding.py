@@ -323,3 +323,47 @@ class PoissonEnergy(torch.autograd.Function):
         return (gx if ctx.needs_input_grad[0] else None,
                 gy if ctx.needs_input_grad[1] else None,
                 None, None, None, None, None, None, None, None, None, None)
+
+
+class PoissonBlockEnergies(torch.autograd.Function):
+    """The per-block energies N_i (rectangle reading) as a differentiable function of
+    the block centres, for any upstream gradient g.
+
+    With L = sum_i g_i N_i, N_i = sum_uv X_iu a_uv Y_iv and a = G o S(x, y):
+      dL/dx_j = g_j h_j + h^b_j,
+    where h_j = sum_uv X'_ju a_uv Y_jv is the gradient pp_grad returns with the
+    placement's own coefficients a, and h^b_j the same with b = G o sum_i g_i X_i Y_i^T,
+    i.e. the coefficients of the same blocks with charges c_i g_i (pp_coeffs).  For
+    g = 1/2 everywhere b = a/2 and dL/dx = h = dE/dx.  The backward recomputes a and
+    computes b: two coefficient and two energy contractions.  Blocks whose `movable`
+    entry is False receive zero gradient.
+    """
+
+    @staticmethod
+    def forward(ctx, x, y, w, h, c, W, H, Mx, My, prec="fp32", movable=None):
+        eb, _ = energy(x, y, w, h, c, W, H, Mx, My, prec, "rect")
+        ctx.save_for_backward(x, y, w, h, c if c is not None else torch.empty(0, device=x.device),
+                              movable if movable is not None else torch.empty(0, device=x.device))
+        ctx.args = (W, H, Mx, My, prec, c is not None, movable is not None)
+        return eb
+
+    @staticmethod
+    def backward(ctx, g):
+        x, y, w, h, c, mov = ctx.saved_tensors
+        W, H, Mx, My, prec, has_c, has_mov = ctx.args
+        x, y = x.detach(), y.detach()
+        cc = c if has_c else None
+        g = g.to(torch.float32).contiguous()
+        gxa, gya, _, _ = grad(x, y, w, h, cc, W, H, Mx, My, prec, want_energy=False)
+        cg = (g * c if has_c else g).contiguous()
+        b = coeffs(x, y, w, h, cg, W, H, Mx, My, prec)
+        gxb, gyb, _, _ = grad(x, y, w, h, cc, W, H, Mx, My, prec, a=b, want_energy=False)
+        gx = g * gxa + gxb
+        gy = g * gya + gyb
+        if has_mov:
+            m = mov.to(torch.float32)
+            gx = gx * m
+            gy = gy * m
+        return (gx if ctx.needs_input_grad[0] else None,
+                gy if ctx.needs_input_grad[1] else None,
+                None, None, None, None, None, None, None, None, None)

@@ -119,3 +119,58 @@ def test_autograd_finite_differences_full_size(pp, cells_fixed_macros, prec):
     got = np.array([gxh[j] if ax == 0 else gyh[j] for j, ax in coords])
     err = np.max(np.abs(got - fd)) / np.max(np.abs(fd))
     assert err <= pp.binding.TOLERANCE[prec], (prec, err)
+
+
+def oracle_L(p, gw, x, y):
+    """L = sum_i g_i N_i (rectangle reading) in FP64 at positions (x, y)."""
+    a = O.coefficients(p.W, p.H, x, y, p.w, p.h, p.c, p.Mx, p.My)
+    N = O.energy_grad(p.W, p.H, x, y, p.w, p.h, p.c, a)[0]
+    return float(np.dot(gw, N))
+
+
+@pytest.mark.parametrize("prec", ["fp32", "tf32", "bf16x3"])
+def test_block_energies_adjoint_matches_fd(pp, prec):
+    """Vector-output adjoint: d(sum_i g_i N_i)/d(x, y) for a random g against central
+    differences of the FP64 oracle's sum_i g_i N_i on 30 sampled coordinates."""
+    p = synth.uniform_blocks(400, 40, 48, seed=77, charge=True)
+    gw = np.random.default_rng(3).normal(size=p.n)
+    dev = torch.device("cuda")
+    x, y, w, h, c = pp.binding.to_device(p, dev)
+    x = x.clone().requires_grad_(True)
+    y = y.clone().requires_grad_(True)
+    N = pp.binding.PoissonBlockEnergies.apply(x, y, w, h, c, p.W, p.H, p.Mx, p.My, prec)
+    (N * torch.from_numpy(gw).to(dev, torch.float32)).sum().backward()
+    gx, gy = x.grad.double().cpu().numpy(), y.grad.double().cpu().numpy()
+    g = np.random.default_rng(4)
+    coords = list(zip(g.choice(p.n, 30, replace=False).tolist(), g.integers(0, 2, 30).tolist()))
+    px, py = p.x.astype(np.float64), p.y.astype(np.float64)
+    d = 1e-6
+    fd, got = [], []
+    for j, ax in coords:
+        xp, yp, xm, ym = px.copy(), py.copy(), px.copy(), py.copy()
+        if ax == 0:
+            xp[j] += d
+            xm[j] -= d
+        else:
+            yp[j] += d
+            ym[j] -= d
+        fd.append((oracle_L(p, gw, xp, yp) - oracle_L(p, gw, xm, ym)) / (2 * d))
+        got.append(gx[j] if ax == 0 else gy[j])
+    fd, got = np.array(fd), np.array(got)
+    err = np.max(np.abs(got - fd)) / np.max(np.abs(fd))
+    assert err <= 2 * pp.binding.TOLERANCE[prec] + 1e-6, (prec, err)
+
+
+def test_block_energies_scalar_case_is_energy_gradient(pp):
+    """g = 1/2 for every block: d(1/2 sum N_i)/dx = dE/dx, the gradient pp_grad returns."""
+    p = synth.uniform_blocks(1000, 64, 48, seed=8)
+    dev = torch.device("cuda")
+    x, y, w, h, c = pp.binding.to_device(p, dev)
+    x = x.clone().requires_grad_(True)
+    y = y.clone().requires_grad_(True)
+    N = pp.binding.PoissonBlockEnergies.apply(x, y, w, h, c, p.W, p.H, p.Mx, p.My, "fp32")
+    (0.5 * N).sum().backward()
+    rgx, rgy, _, _ = pp.binding.grad(x.detach(), y.detach(), w, h, c, p.W, p.H, p.Mx, p.My, "fp32")
+    scale = float(torch.maximum(rgx.abs().max(), rgy.abs().max()))
+    assert float((x.grad - rgx).abs().max()) <= 2e-6 * scale
+    assert float((y.grad - rgy).abs().max()) <= 2e-6 * scale
