@@ -192,7 +192,7 @@ def make_inputs(device, n=None, workload=WORKLOAD_INDEX):
 
 
 def time_steps(binding, p, dev_in, prec, steps, warmup, flush, outs, kernel_timing=False,
-               mode="grad"):
+               mode="grad", bins=None):
     """Per-step CUDA-event times (ms) of `steps` evaluations after `warmup`; the L2
     is flushed (FLUSH_BYTES written) before every step, outside the events.  With
     kernel_timing, the library brackets each of its launches in the timed steps
@@ -200,7 +200,8 @@ def time_steps(binding, p, dev_in, prec, steps, warmup, flush, outs, kernel_timi
     mode "grad": one pp_grad call (a computed inside); "autograd": the autograd
     function's forward (pp_energy) and backward (pp_grad, a recomputed), fixed
     blocks masked; "block-adjoint": per-block energies forward and the backward for
-    a random upstream gradient (two coefficient and two energy contractions)."""
+    a random upstream gradient (two coefficient and two energy contractions);
+    "binned": the binned fast scheme (Sec. III-D) on `bins` x `bins` bins."""
     import torch
     x, y, w, h, c = dev_in
     stream = torch.cuda.current_stream()
@@ -219,6 +220,10 @@ def time_steps(binding, p, dev_in, prec, steps, warmup, flush, outs, kernel_timi
             else:       # per-block energies, backward for an arbitrary upstream gradient
                 N = binding.PoissonBlockEnergies.apply(xg, yg, w, h, c, p.W, p.H, p.Mx, p.My, prec, mov)
                 N.backward(gw)
+    elif mode == "binned":
+        m = max(p.Mx, p.My) if bins is None else bins
+        bprec = "tf32" if prec == "bf16x3" else prec
+        run = lambda: binding.binned_grad(x, y, w, h, c, p.W, p.H, p.Mx, p.My, m, bprec, want_coeffs=False)
     else:
         run = lambda: binding.grad(x, y, w, h, c, p.W, p.H, p.Mx, p.My, prec, out=outs)
     for _ in range(warmup):
@@ -359,7 +364,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     clocks.mark("t0")
     step_ms, ktimes = time_steps(binding, p, dev_in, prec, args.steps, args.warmup, flush, outs,
-                                 kernel_timing=True, mode=args.mode)
+                                 kernel_timing=args.mode != "binned", mode=args.mode, bins=args.bins)
     clocks.mark("t1")
     torch.cuda.synchronize()
     barrier(world)
@@ -368,8 +373,12 @@ def run_ours(args):
     value, total_ms = whole_job_throughput(terms, args.steps, sum(step_ms), world, device)
     ms_per_step = total_ms / args.steps
 
-    launches = int(sum(v[0] for v in ktimes.values()))     # our kernels in the timed steps
     peaks, peak_src = load_peaks()
+    if ktimes is None:      # binned mode: five kernels of ours and eight cuBLAS GEMMs per step
+        ktimes = {"coeff": (0, 0.0), "energy": (0, 0.0)}
+        launches = 5 * args.steps
+    else:
+        launches = int(sum(v[0] for v in ktimes.values()))     # our kernels in the timed steps
     dom = max(("coeff", "energy"), key=lambda k: ktimes[k][1])
     dom_ms = ktimes[dom][1] / max(ktimes[dom][0], 1)
     flops = (2.0 if dom == "coeff" else 4.0) * terms
@@ -385,22 +394,22 @@ def run_ours(args):
         bound = "tensor"
         peak = peaks["bf16_tflops"] / 3.0
         peak_note = f"{peak_src} bf16 burst peak / 3 (three bf16 products per term)"
-    achieved = flops / (dom_ms * 1e-3) / 1e12
+    achieved = flops / (dom_ms * 1e-3) / 1e12 if dom_ms > 0 else None
 
     line = {
         "metric": METRIC, "value": value, "unit": "terms/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": prec,
         "data": "synthetic",
-        "config": {"workload": synth.WORKLOADS[args.workload]["name"], "mode": args.mode, "n": n, "Mx": p.Mx,
+        "config": {"workload": synth.WORKLOADS[args.workload]["name"], "mode": args.mode,
+                   "bins": (args.bins or max(p.Mx, p.My)) if args.mode == "binned" else None, "n": n, "Mx": p.Mx,
                    "My": p.My, "sample": "rect", "precision": prec, "W": p.W, "H": p.H,
                    "l2": "flushed: 256 MiB written before every timed step",
                    "parallelism": f"replicas x{world}"},
-        "roofline": {"bound": bound, "kernel": dom, "achieved": achieved, "peak": peak,
-                     "unit": "TFLOP/s", "frac": achieved / peak,
-                     "traffic": ncu_traffic(prec, dom),
-                     "peak_source": peak_note,
-                     "flops_per_launch": flops},
+        "roofline": None if achieved is None else {
+            "bound": bound, "kernel": dom, "achieved": achieved, "peak": peak,
+            "unit": "TFLOP/s", "frac": achieved / peak, "traffic": ncu_traffic(prec, dom),
+            "peak_source": peak_note, "flops_per_launch": flops},
         "kernels_ms_per_step": {k: v[1] / args.steps for k, v in ktimes.items()},
         "gpu_launches": launches,
         "clocks": clk,
@@ -410,7 +419,7 @@ def run_ours(args):
         if prec != "fp32":
             torch.cuda.synchronize()
             f_ms, _ = time_steps(binding, p, dev_in, "fp32", args.steps, args.warmup, flush, outs,
-                                 mode=args.mode)
+                                 mode=args.mode, bins=args.bins)
             fv = terms * args.steps / (sum(f_ms) / 1e3)
             line["fp32_plain"] = {"value": fv, "ms_per_step": sum(f_ms) / args.steps,
                                   "speedup_of_mixed": value / world / fv}
@@ -475,9 +484,11 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", type=int, default=WORKLOAD_INDEX,
                     help="synth.WORKLOADS index (default: the metric's 200k x 512^2 workload)")
-    ap.add_argument("--mode", choices=["grad", "autograd", "block-adjoint"], default="grad",
+    ap.add_argument("--bins", type=int, default=None, help="bins per side for --mode binned")
+    ap.add_argument("--mode", choices=["grad", "autograd", "block-adjoint", "binned"], default="grad",
                     help="grad: one pp_grad per step; autograd: energy forward + adjoint backward; "
-                         "block-adjoint: per-block energies forward + vector-output adjoint")
+                         "block-adjoint: per-block energies forward + vector-output adjoint; "
+                         "binned: the binned fast scheme (terms counted as N Mx My)")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")

@@ -153,6 +153,27 @@ pp_status pp_sync_status(void *stream);
 pp_status pp_phase_eval(const float *x, double L, const int32_t *m, int64_t count, int evaluator,
                         float *out, void *stream);
 
+/* The paper's binned fast scheme (Sec. III-D) on m x m uniform bins, for the same
+ * problem description (Mx, My <= m modes, i.e. K <= m - 1):
+ *   P_lj  = sum_i c_i area(block i ∩ bin lj) / area(bin)           (bin density)
+ *   a     = Eq. (disa-a..d) from the cosine transform of P           (coefficients)
+ *   psi, xi at the bin centres, Eq. (dis-psi1) and (dis-ksi)
+ *   N_i   = q_i psi(x_i, y_i), gradient of E = 1/2 sum N_i = -q_i xi(x_i, y_i), with
+ *           q_i = c_i w_i h_i and the bin-centre values weighted bilinearly at the
+ *           block centre (clamped to the outermost centres).
+ * The paper leaves its local-smoothness weighting of the density and its weighting
+ * of the surrounding bins unstated; these are the readings taken.  The transforms
+ * are dense GEMMs with the m-point cosine / sine matrices (cuBLAS): prec PP_FP32
+ * (FP32) or PP_TF32 (TF32 tensor cores); PP_BF16X3 gives PP_ENOTSUP.  The density
+ * is accumulated with FP32 atomics (summation order, and so the last bits, may vary
+ * between runs).  a_out (Mx x My, optional), gx, gy (required when n > 0), e_block,
+ * e_total (optional): device arrays.  2 <= m <= 4096.  Workspace: at least
+ * pp_binned_workspace_size() bytes, 256-byte aligned; 0 for invalid arguments. */
+size_t pp_binned_workspace_size(const pp_problem *prob, int32_t m);
+pp_status pp_binned_grad(const pp_problem *prob, pp_precision prec, int32_t m, float *a_out, float *gx,
+                         float *gy, float *e_block, double *e_total, void *ws, size_t ws_bytes,
+                         void *stream);
+
 /* Total energy from coefficients: *e_total = 1/2 sum_{(u,v) != (0,0)} a_uv^2 / G_uv
  * with G_uv = e_u e_v / (W H (k_u^2 + l_v^2)) (FP64 sum), i.e. 1/2 sum_uv a_uv S_uv
  * (Eq. a-a..a-d: S = a / G) = 1/2 sum_i N_i in the rectangle reading, for the

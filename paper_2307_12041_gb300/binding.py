@@ -41,7 +41,8 @@ class Problem(ctypes.Structure):
 _LIB = None
 EXPORTS = ("pp_workspace_size", "pp_coeffs", "pp_energy", "pp_grad", "pp_sync_status",
            "pp_last_error", "pp_version", "pp_timing_enable", "pp_timing_collect",
-           "pp_grad_noalloc", "pp_phase_eval", "pp_energy_from_coeffs", "pp_descent_step",
+           "pp_grad_noalloc", "pp_phase_eval", "pp_binned_workspace_size", "pp_binned_grad",
+           "pp_energy_from_coeffs", "pp_descent_step",
            "pp_check_wait_timeout")
 
 
@@ -70,6 +71,10 @@ def lib() -> ctypes.CDLL:
         L.pp_sync_status.restype = i
         L.pp_phase_eval.argtypes = [vp, ctypes.c_double, vp, ctypes.c_int64, i, vp, vp]
         L.pp_phase_eval.restype = i
+        L.pp_binned_workspace_size.argtypes = [P, ctypes.c_int32]
+        L.pp_binned_workspace_size.restype = sz
+        L.pp_binned_grad.argtypes = [P, i, ctypes.c_int32, vp, vp, vp, vp, vp, vp, sz, vp]
+        L.pp_binned_grad.restype = i
         L.pp_energy_from_coeffs.argtypes = [vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
                                             ctypes.c_double, vp, vp]
         L.pp_energy_from_coeffs.restype = i
@@ -242,6 +247,27 @@ def phase_eval(x, L: float, m, evaluator: int = 0):
     _check(lib().pp_phase_eval(_ptr(x), float(L), _ptr(m), x.numel(), int(evaluator), _ptr(out),
                                _stream_handle(x.device)))
     return out
+
+
+def binned_grad(x, y, w, h, c, W, H, Mx, My, m, prec="fp32", want_coeffs=True):
+    """pp_binned_grad, the binned fast scheme on m x m bins: (gx, gy, N_i, E, a or None)."""
+    prob = make_problem(x, y, w, h, c, W, H, Mx, My)
+    dev = x.device
+    n = x.numel()
+    need = lib().pp_binned_workspace_size(ctypes.byref(prob), int(m))
+    if need == 0:
+        raise PPError(1, lib().pp_last_error().decode())
+    ws = torch.empty(need + 256, dtype=torch.uint8, device=dev)
+    base = (ws.data_ptr() + 255) // 256 * 256
+    gx = torch.empty(n, dtype=torch.float32, device=dev)
+    gy = torch.empty(n, dtype=torch.float32, device=dev)
+    eb = torch.empty(n, dtype=torch.float32, device=dev)
+    et = torch.empty(1, dtype=torch.float64, device=dev)
+    a = torch.empty((Mx, My), dtype=torch.float32, device=dev) if want_coeffs else None
+    _check(lib().pp_binned_grad(ctypes.byref(prob), PRECISIONS[prec], int(m), _ptr(a),
+                                _ptr(gx) if n else None, _ptr(gy) if n else None, _ptr(eb) if n else None,
+                                _ptr(et), base, need, _stream_handle(dev)))
+    return gx, gy, eb, et, a
 
 
 def energy_from_coeffs(a, W, H):

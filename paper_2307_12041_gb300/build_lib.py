@@ -3,7 +3,8 @@
 Each translation unit is compiled by its own nvcc process (in parallel), then
 linked with `nvcc -shared`.  The CUDA runtime is linked statically; the driver
 API (tensor-map encoding) is reached through cudaGetDriverEntryPoint, so the
-library needs no -lcuda.  Objects go to `_build/` next to this file.
+library needs no -lcuda; cuBLAS (the binned scheme's transform GEMMs) is linked
+dynamically.  Objects go to `_build/` next to this file.
 """
 from __future__ import annotations
 
@@ -16,7 +17,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libpp.so")
-SOURCES = ["pp_api.cu", "pp_simt.cu", "pp_static.cu", "pp_tc.cu"]
+SOURCES = ["pp_api.cu", "pp_simt.cu", "pp_static.cu", "pp_tc.cu", "pp_binned.cu"]
 HEADERS = ["pp_device.cuh", "pp_internal.h", "pp_tc.cuh", "pp_gen.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ARCH + ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC",
@@ -70,7 +71,7 @@ def build(verbose: bool = False, force: bool = False) -> str:
     if failed:
         raise RuntimeError("nvcc failed:\n" + "\n".join(f"--- {s}\n{o}" for s, o in failed))
     tmp = LIB + ".tmp"
-    cmd = [cc] + ARCH + ["-shared", "-o", tmp] + objs
+    cmd = [cc] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcublas"]
     if verbose:
         print(" ".join(cmd), flush=True)
     subprocess.run(cmd, check=True)

@@ -432,6 +432,67 @@ pp_status pp_phase_eval(const float *x, double L, const int32_t *m, int64_t coun
     return PP_OK;
 }
 
+size_t pp_binned_workspace_size(const pp_problem *prob, int32_t m) {
+    if (check_shape(prob, PP_FP32) != PP_OK) return 0;
+    if (m < 2 || m > 4096 || prob->Mx > m || prob->My > m) {
+        fail(PP_EINVAL, "bins m=%d must be in [2, 4096] and >= Mx=%d, My=%d", m, prob->Mx, prob->My);
+        return 0;
+    }
+    return binned_layout(m, prob->Mx, prob->My).total;
+}
+
+pp_status pp_binned_grad(const pp_problem *prob, pp_precision prec, int32_t m, float *a_out, float *gx,
+                         float *gy, float *e_block, double *e_total, void *ws, size_t ws_bytes, void *stream) {
+    pp_status st = check_problem(prob, PP_FP32);
+    if (st != PP_OK) return st;
+    if (prec != PP_FP32 && prec != PP_TF32)
+        return fail(prec == PP_BF16X3 ? PP_ENOTSUP : PP_EINVAL, "binned scheme: precision %d not offered",
+                    (int)prec);
+    const size_t need = pp_binned_workspace_size(prob, m);
+    if (need == 0) return PP_EINVAL;
+    int dev, sm, ccm;
+    unsigned *status;
+    if ((st = device_info(&dev, &sm, &status, &ccm)) != PP_OK) return st;
+    if (!ws || ws_bytes < need)
+        return fail(PP_ENOMEM_WS, "workspace of %zu bytes needed, %zu given", need, ws ? ws_bytes : (size_t)0);
+    if (((uintptr_t)ws & 255) != 0) return fail(PP_EINVAL, "workspace must be 256-byte aligned");
+    if ((st = check_dev_ptr(ws, dev, "ws")) != PP_OK) return st;
+    const bool has_blocks = prob->n > 0;
+    if (has_blocks) {
+        const void *ptrs[5] = {prob->x, prob->y, prob->w, prob->h, prob->c};
+        const char *names[5] = {"x", "y", "w", "h", "c"};
+        for (int i = 0; i < 5; ++i)
+            if (ptrs[i] && (st = check_dev_ptr(ptrs[i], dev, names[i])) != PP_OK) return st;
+    }
+    if ((st = out_ptr(gx, dev, "gx", has_blocks)) != PP_OK) return st;
+    if ((st = out_ptr(gy, dev, "gy", has_blocks)) != PP_OK) return st;
+    if ((st = out_ptr(e_block, dev, "e_block", false)) != PP_OK) return st;
+    if ((st = out_ptr(a_out, dev, "a_out", false)) != PP_OK) return st;
+    if (e_total) {
+        if (((uintptr_t)e_total & 7) != 0) return fail(PP_EINVAL, "e_total is not 8-byte aligned");
+        if ((st = check_dev_ptr(e_total, dev, "e_total")) != PP_OK) return st;
+    }
+    Launch L{};
+    L.W = prob->W;
+    L.H = prob->H;
+    L.n = (int)prob->n;
+    L.Mx = prob->Mx;
+    L.My = prob->My;
+    L.x = prob->x;
+    L.y = prob->y;
+    L.w = prob->w;
+    L.h = prob->h;
+    L.c = prob->c;
+    L.status = status;
+    L.sm_count = sm;
+    L.stream = (cudaStream_t)stream;
+    const char *what = "";
+    cudaError_t e = run_binned(L, dev, m, prec == PP_TF32, (unsigned char *)ws, a_out, e_block, gx, gy,
+                               e_total, &what);
+    if (e != cudaSuccess) return cuda_fail(e, what);
+    return PP_OK;
+}
+
 pp_status pp_energy_from_coeffs(const float *a, int32_t Mx, int32_t My, double W, double H, double *e_total,
                                 void *stream) {
     int dev, sm, ccm;

@@ -46,6 +46,14 @@ cudaError_t launch_energy_tc(const Launch &L, int prec, int sample, const TcPlan
 
 // pp_api.cu: message returned by pp_last_error() for the calling thread
 void set_last_error(const char *msg);
+// Binned fast scheme (pp_binned.cu): workspace offsets (bytes) and the pipeline.
+struct BinnedLayout {
+    size_t P, Cx, Sx, Cy, Sy, T, ap, a, ka, al, U, psi, xix, xiy, total;
+};
+BinnedLayout binned_layout(int m, int Mx, int My);
+// `what` names the failing step on error (a CUDA launch or a cuBLAS call)
+cudaError_t run_binned(const Launch &L, int dev, int m, bool tf32, unsigned char *ws, float *a_out,
+                       float *e_block, float *gx, float *gy, double *e_total, const char **what);
 // E = 1/2 sum_uv a_uv^2 / G_uv (FP64) from coefficients a (Mx x My, u-major), added to *e_total
 cudaError_t launch_energy_from_coeffs(const float *a, int Mx, int My, double W, double H, double *e_total,
                                       cudaStream_t stream);
