@@ -71,7 +71,8 @@ pp_status device_info(int *dev, int *sm, unsigned **status, int *cc_major) {
 }
 
 struct Layout {
-    size_t xrec, yrec, S64, K, Klo, part, total;
+    size_t xrec, yrec, S64, K, Klo, part, esplit, esplit_cnt, total;
+    int esplit_n;
     int Kld;
     TcPlan plan;
 };
@@ -81,7 +82,8 @@ size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 // Workspace regions (byte offsets, each 256-byte aligned):
 //   PP_FP32:          x/y records, S64 [Mx*My] FP64, K FP32 [round_up(Mx,32)][round_up(My,128)]
 //   PP_TF32/BF16X3:   x/y records, partial tiles [slices][Mxc][Myc] FP32,
-//                     K in the TMA-tiled operand layout (TF32, or bf16 hi + lo)
+//                     K in the TMA-tiled operand layout (TF32, or bf16 hi + lo),
+//                     energy split-tile scratch and counters
 Layout layout(const pp_problem *p, pp_precision prec) {
     Layout L{};
     const size_t n = (size_t)p->n;
@@ -107,6 +109,11 @@ Layout layout(const pp_problem *p, pp_precision prec) {
         off = align256(off + kel * (prec == PP_TF32 ? 4 : 2));
         L.Klo = off;
         if (prec == PP_BF16X3) off = align256(off + kel * 2);
+        L.esplit_n = energy_boundaries((int)p->n);
+        L.esplit = off;
+        off = align256(off + (size_t)L.esplit_n * 2 * kEnergyRows * 3 * sizeof(float));
+        L.esplit_cnt = off;
+        off = align256(off + (size_t)L.esplit_n * sizeof(unsigned));
         L.S64 = 0;
         L.Kld = L.plan.Mye;
     }
@@ -205,6 +212,9 @@ pp_status setup(const pp_problem *p, pp_precision prec, void *ws, size_t ws_byte
     L.S64 = prec == PP_FP32 ? (double *)(base + ctx->lay.S64) : nullptr;
     L.K = base + ctx->lay.K;
     L.Kld = ctx->lay.Kld;
+    L.esplit = prec == PP_FP32 ? nullptr : (float *)(base + ctx->lay.esplit);
+    L.esplit_cnt = prec == PP_FP32 ? nullptr : (unsigned *)(base + ctx->lay.esplit_cnt);
+    L.esplit_n = prec == PP_FP32 ? 0 : ctx->lay.esplit_n;
     L.status = status;
     L.sm_count = sm;
     L.stream = (cudaStream_t)stream;

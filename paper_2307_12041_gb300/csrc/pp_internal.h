@@ -20,6 +20,9 @@ struct Launch {
     void *K;                    // workspace: energy operand (layout per precision)
     int Kld;                    // leading dimension / padded size for K (per precision)
     unsigned *status;           // device status word
+    float *esplit;              // tensor-core energy: split-tile scratch (see tc_energy_kernel)
+    unsigned *esplit_cnt;       //   and its boundary counters (esplit_n of them)
+    int esplit_n;
     int sm_count;
     cudaStream_t stream;
 };
@@ -34,6 +37,15 @@ inline int round_up(int a, int b) { return (a + b - 1) / b * b; }
 // cut into `slices` of slice_len for the persistent coefficient kernel; the plan
 // depends only on the problem (kPlanSMs sets the target of two units per SM).
 constexpr int kPlanSMs = 152;
+// Energy kernel: row tiles of kEnergyRows blocks, at most kEnergyGridMax persistent
+// CTAs; a tile cut between two CTAs meets in a scratch of kEnergyRows x 3 floats per
+// side and boundary, with one counter per boundary.
+constexpr int kEnergyRows = 128;
+constexpr int kEnergyGridMax = 256;
+inline int energy_boundaries(int n) {
+    const int tiles = (n + kEnergyRows - 1) / kEnergyRows;
+    return (tiles < kEnergyGridMax ? tiles : kEnergyGridMax) + 1;
+}
 struct TcPlan {
     int Mxc, Myc, Mxe, Mye, tiles, slices, slice_len;
 };

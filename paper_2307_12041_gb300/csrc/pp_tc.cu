@@ -542,7 +542,11 @@ __global__ void tc_finish_kernel(const float *__restrict__ part, int slices, int
                                  const float *__restrict__ a_in, float *__restrict__ a_out,
                                  void *__restrict__ Kop, void *__restrict__ Klo, int Mx, int My,
                                  int Mxe, int Mye, float piW, float piH, float invWH,
-                                 double *__restrict__ e_total) {
+                                 double *__restrict__ e_total, unsigned *__restrict__ split_cnt,
+                                 int nsplit) {
+    // the energy kernel that follows finds its split-tile counters at zero
+    if (blockIdx.x == 0)
+        for (int i = threadIdx.x; i < nsplit; i += blockDim.x) split_cnt[i] = 0u;
     // FP32 throughout (FP64 is a narrow pipe on this GPU): the slice partials are
     // summed with Kahan compensation; the operand is TF32 or bf16 anyway.
     float e_acc = 0.f;                 // this thread's few terms; summed across the CTA in FP64
@@ -592,7 +596,7 @@ __global__ void tc_finish_kernel(const float *__restrict__ part, int slices, int
 // ===========================================================================
 // Energy and gradient
 // ===========================================================================
-constexpr int E_ROWS = 128;                 // blocks per CTA
+constexpr int E_ROWS = kEnergyRows;         // blocks per row tile
 constexpr int E_VC = 256;                   // v columns per accumulator pass
 constexpr int E_KS = 32;                    // u per pipeline stage
 constexpr int E_STAGES = 3;
@@ -611,13 +615,21 @@ struct EnergyBars {
     uint64_t drain;
     uint32_t tmem_slot;
     int abort_flag;
-    float red[2][E_ROWS][3];    // per tile parity: column half 1 of each row, for half 0
+    float red[2][E_ROWS][3];    // per segment parity: column half 1 of each row, for half 0
+    unsigned split_old;         // boundary counter value seen by this CTA
 };
 constexpr int E_SMEM = E_STAGES * E_STAGE_BYTES + 1024 + (int)sizeof(EnergyBars);
 
+// Row tiles of E_ROWS blocks, each a sequence of nvc accumulator passes: the
+// tiles * nvc (tile, pass) units are cut into gridDim.x equal ranges, one per CTA,
+// so a tile may be split between two neighbouring CTAs (never three: a range has
+// at least nvc units).  The two parts of a split tile meet in `split`: the CTA that
+// arrives second at the boundary counter adds head + tail and writes the outputs.
 struct EnergyArgs {
     const AxisRec *xr, *yr;
     int n, tiles, Mx, My, Mxe, Mye;      // tiles: row tiles of E_ROWS blocks
+    float *split;                        // [gridDim.x + 1][2][E_ROWS][3]
+    unsigned *split_cnt;                 // [gridDim.x + 1], zero at launch (finish kernel)
     float *e_block, *gx, *gy;
     double *e_total;
     unsigned *status;
@@ -895,42 +907,75 @@ __device__ __forceinline__ void drain_pass(EnergyBars &bars, volatile int *abort
     }
 }
 
-// End of a row tile for one epilogue thread: column half 1 puts its sums in
-// shared memory (double-buffered by tile parity, so that a one-pass tile cannot
-// overwrite them before they are read); after named barrier 1 (all epilogue
-// threads) half 0 adds them and writes the block's outputs and its share of E.
-__device__ __forceinline__ void finish_tile(EnergyBars &bars, volatile int *abort_flag, const EnergyArgs &args,
-                                            int tile, int row, int cq, float eN, float eX, float eY) {
+// End of a tile segment (the passes [v0, v1] of row tile `tile`) for one epilogue
+// thread: column half 1 puts its sums in shared memory (double-buffered by segment
+// parity, so that a one-pass segment cannot overwrite them before they are read);
+// after named barrier 1 (all epilogue threads) half 0 adds them.  A whole tile's
+// outputs are written directly; a split tile's part goes to the boundary scratch
+// and the second part to arrive writes head + tail (named barrier 2: half 0).
+// E gets each part's share directly (it is a sum over blocks).
+__device__ __forceinline__ void finish_segment(EnergyBars &bars, volatile int *abort_flag, const EnergyArgs &args,
+                                               int seg, int tile, int v0, int v1, int nvc, int row, int cq,
+                                               float eN, float eX, float eY) {
     if (cq != 0) {
-        float *r = bars.red[tile & 1][row];
+        float *r = bars.red[seg & 1][row];
         r[0] = eN;
         r[1] = eX;
         r[2] = eY;
     }
-    // both halves wait (no half can run ahead into the next tile's arrival and
-    // complete a barrier phase that belongs to this tile)
+    // both halves wait (no half can run ahead into the next segment's arrival and
+    // complete a barrier phase that belongs to this one)
     asm volatile("bar.sync 1, %0;" ::"r"(E_DRAIN_THREADS) : "memory");
     if (cq != 0) return;
     const int b = tile * E_ROWS + row;
     const bool valid = b < args.n;
-    eN += bars.red[tile & 1][row][0];
-    eX += bars.red[tile & 1][row][1];
-    eY += bars.red[tile & 1][row][2];
+    eN += bars.red[seg & 1][row][0];
+    eX += bars.red[seg & 1][row][1];
+    eY += bars.red[seg & 1][row][2];
     const bool ok = !*abort_flag;
-    if (valid && ok) {
-        if (args.e_block) args.e_block[b] = eN;
-        if (args.gx) args.gx[b] = eX;
-        if (args.gy) args.gy[b] = eY;
-    }
     double es = valid ? (double)eN : 0.0;
 #pragma unroll
     for (int off = 16; off >= 1; off >>= 1) es += __shfl_xor_sync(0xffffffffu, es, off);
     if ((threadIdx.x & 31) == 0 && args.e_total && ok) atomicAdd(args.e_total, 0.5 * es);
+    if (v0 == 0 && v1 == nvc - 1) {
+        if (valid && ok) {
+            if (args.e_block) args.e_block[b] = eN;
+            if (args.gx) args.gx[b] = eX;
+            if (args.gy) args.gy[b] = eY;
+        }
+        return;
+    }
+    // split tile: head part (v0 == 0) ends this CTA's range, tail part starts it
+    const int side = v0 == 0 ? 0 : 1;
+    const int bd = side == 0 ? blockIdx.x + 1 : blockIdx.x;           // boundary index
+    float *mine = args.split + (((size_t)bd * 2 + side) * E_ROWS + row) * 3;
+    const float *other = args.split + (((size_t)bd * 2 + (1 - side)) * E_ROWS + row) * 3;
+    mine[0] = eN;
+    mine[1] = eX;
+    mine[2] = eY;
+    __threadfence();
+    asm volatile("bar.sync 2, %0;" ::"r"(E_ROWS) : "memory");
+    if (row == 0) bars.split_old = atomicAdd(&args.split_cnt[bd], 1u);
+    asm volatile("bar.sync 2, %0;" ::"r"(E_ROWS) : "memory");
+    if (bars.split_old == 1u) {              // the other part is in: head + tail, fixed order
+        __threadfence();
+        const float o0 = __ldcg(other), o1 = __ldcg(other + 1), o2 = __ldcg(other + 2);
+        const float hN = side == 0 ? eN : o0, tN = side == 0 ? o0 : eN;
+        const float hX = side == 0 ? eX : o1, tX = side == 0 ? o1 : eX;
+        const float hY = side == 0 ? eY : o2, tY = side == 0 ? o2 : eY;
+        if (valid && ok) {
+            if (args.e_block) args.e_block[b] = hN + tN;
+            if (args.gx) args.gx[b] = hX + tX;
+            if (args.gy) args.gy[b] = hY + tY;
+        }
+    }
+    // keep bars.split_old until every half-0 thread has read it
+    asm volatile("bar.sync 2, %0;" ::"r"(E_ROWS) : "memory");
 }
 
-// Persistent over row tiles (tile = blockIdx.x + k * gridDim.x): the generators
-// and the TMA warp fill the next tile's stages while the epilogue drains the
-// previous one, and TMEM is allocated once.
+// Persistent: each CTA runs its range of (tile, pass) units; the generators and the
+// TMA warp fill the next pass's stages while the epilogue drains the previous
+// one, and TMEM is allocated once.
 template <int PREC, int SAMPLE>
 __global__ void __launch_bounds__(E_THREADS, 1)
 tc_energy_kernel(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ CUtensorMap tm_lo,
@@ -946,6 +991,8 @@ tc_energy_kernel(const __grid_constant__ CUtensorMap tm_hi, const __grid_constan
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nvc = args.Mye / E_VC;
     const int nks = args.Mxe / E_KS;
+    const long long U = (long long)args.tiles * nvc;              // (tile, pass) units
+    const int ub = (int)(U * blockIdx.x / gridDim.x), ue = (int)(U * (blockIdx.x + 1) / gridDim.x);
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < E_STAGES; ++s) {
@@ -973,8 +1020,8 @@ tc_energy_kernel(const __grid_constant__ CUtensorMap tm_hi, const __grid_constan
         if (lane == 0) {
             const uint32_t idesc = instr_desc(BF ? kFmtBF16 : kFmtTF32, 128, 256, false, false);
             int it = 0, pc = 0;       // stages consumed, accumulator passes
-            for (int tile = blockIdx.x; tile < args.tiles && !*abort_flag; tile += gridDim.x) {
-                for (int vc = 0; vc < nvc && !*abort_flag; ++vc, ++pc) {
+            for (int un = ub; un < ue && !*abort_flag; ++un, ++pc) {
+                {
                     if (pc > 0 && !mbar_wait(&bars.acc_empty, (pc - 1) & 1, kWaitLimit, abort_flag)) {
                         raise_timeout(args.status, abort_flag);
                         break;
@@ -1033,8 +1080,9 @@ tc_energy_kernel(const __grid_constant__ CUtensorMap tm_hi, const __grid_constan
             constexpr int T = BF ? 8 : 4;                 // u per 16-byte core row
             const uint32_t bytes = BF ? 2 * 16384 : 32768;
             int it = 0;
-            for (int tile = blockIdx.x; tile < args.tiles && !*abort_flag; tile += gridDim.x) {
-                for (int vc = 0; vc < nvc && !*abort_flag; ++vc) {
+            for (int un = ub; un < ue && !*abort_flag; ++un) {
+                const int vc = un % nvc;
+                {
                     for (int ks = 0; ks < nks; ++ks, ++it) {
                         if (*abort_flag) break;
                         const int s = it % E_STAGES;
@@ -1063,41 +1111,49 @@ tc_energy_kernel(const __grid_constant__ CUtensorMap tm_hi, const __grid_constan
         const int row = (warp & 3) * 32 + lane;
         const int cq = (warp - 2) >> 2;
         const uint32_t trow = tmem + ((uint32_t)((warp & 3) * 32) << 16);
-        int pc = 0;
-        for (int tile = blockIdx.x; tile < args.tiles; tile += gridDim.x) {
-            const int b = tile * E_ROWS + row;
-            const bool valid = b < args.n;
-            YRec Ry{};
-            if (valid) Ry = load_yrec(args.yr, b);
-            float eN = 0.f, eX = 0.f, eY = 0.f;
-            for (int vc = 0; vc < nvc; ++vc, ++pc)
-                drain_pass<SAMPLE>(bars, abort_flag, args.status, trow, cq * E_DRAIN_COLS,
-                                   vc * E_VC + cq * E_DRAIN_COLS, pc, valid, Ry, eN, eX, eY);
-            finish_tile(bars, abort_flag, args, tile, row, cq, eN, eX, eY);
+        int pc = 0, seg = 0, v0 = 0;
+        bool valid = false;
+        YRec Ry{};
+        float eN = 0.f, eX = 0.f, eY = 0.f;
+        for (int un = ub; un < ue; ++un, ++pc) {
+            const int tile = un / nvc, vc = un % nvc;
+            if (un == ub || vc == 0) {           // a new tile segment
+                const int b = tile * E_ROWS + row;
+                valid = b < args.n;
+                if (valid) Ry = load_yrec(args.yr, b);
+                eN = eX = eY = 0.f;
+                v0 = vc;
+            }
+            drain_pass<SAMPLE>(bars, abort_flag, args.status, trow, cq * E_DRAIN_COLS,
+                               vc * E_VC + cq * E_DRAIN_COLS, pc, valid, Ry, eN, eX, eY);
+            if (vc == nvc - 1 || un == ue - 1)
+                finish_segment(bars, abort_flag, args, seg++, tile, v0, vc, nvc, row, cq, eN, eX, eY);
         }
     } else {
         // ---------------- basis generators: Xt, Xh ----------------
-        // group grp fills the stages j = grp, grp + 2, ... of each tile (j counted
-        // within the tile), so every stage is filled by exactly one group
+        // group grp fills the CTA's stages it = grp, grp + 2, ..., so every stage is
+        // filled by exactly one group
         const int g = threadIdx.x - 32 * (2 + E_EPI_WARPS);   // 0..255
         const int row = g & 127, grp = g >> 7;
-        const int total = nvc * nks;
-        int base = 0;                                        // first stage of this tile
-        for (int tile = blockIdx.x; tile < args.tiles && !*abort_flag; tile += gridDim.x, base += total) {
-            const int b = tile * E_ROWS + row;
-            const bool valid = b < args.n;
-            AxisRec Rx;
-            if (valid) Rx = args.xr[b];
-            for (int j = grp; j < total; j += 2) {
+        bool valid = false;
+        AxisRec Rx;
+        for (int un = ub; un < ue && !*abort_flag; ++un) {
+            const int tile = un / nvc, vc = un % nvc;
+            if (un == ub || vc == 0) {
+                const int b = tile * E_ROWS + row;
+                valid = b < args.n;
+                if (valid) Rx = args.xr[b];
+            }
+            const int base = (un - ub) * nks;
+            for (int ks = (base + grp) & 1; ks < nks; ks += 2) {
                 if (*abort_flag) break;
-                const int it = base + j;
+                const int it = base + ks;
                 const int s = it % E_STAGES;
                 if (it >= E_STAGES &&
                     !mbar_wait(&bars.empty[s], ((it / E_STAGES) - 1) & 1, kWaitLimit, abort_flag)) {
                     raise_timeout(args.status, abort_flag);
                     break;
                 }
-                const int ks = j % nks;
                 gen_energy<PREC, SAMPLE>(smem + s * E_STAGE_BYTES, Rx, valid, row, ks * E_KS);
                 fence_proxy_async_smem();
                 mbar_arrive(&bars.full[s]);
@@ -1290,11 +1346,13 @@ cudaError_t launch_finish_tc(const Launch &L, int prec, const TcPlan &P, const f
     if (prec == 1)
         tc_finish_kernel<1><<<blocks, 256, 0, L.stream>>>(part, P.slices, P.Mxc, P.Myc, a_in, a_out, Khi,
                                                           Klo, L.Mx, L.My, P.Mxe, P.Mye, piW, piH, invWH,
-                                                          a_in ? nullptr : e_total);
+                                                          a_in ? nullptr : e_total, L.esplit_cnt,
+                                                          L.esplit_n);
     else
         tc_finish_kernel<2><<<blocks, 256, 0, L.stream>>>(part, P.slices, P.Mxc, P.Myc, a_in, a_out, Khi,
                                                           Klo, L.Mx, L.My, P.Mxe, P.Mye, piW, piH, invWH,
-                                                          a_in ? nullptr : e_total);
+                                                          a_in ? nullptr : e_total, L.esplit_cnt,
+                                                          L.esplit_n);
     return cudaGetLastError();
 }
 
@@ -1321,7 +1379,11 @@ cudaError_t launch_energy_tc(const Launch &L, int prec, int sample, const TcPlan
     a.e_total = e_total;
     a.status = L.status;
     a.tiles = (L.n + E_ROWS - 1) / E_ROWS;
-    const int grid = a.tiles < L.sm_count ? a.tiles : L.sm_count;     // persistent
+    a.split = L.esplit;
+    a.split_cnt = L.esplit_cnt;
+    int grid = a.tiles < L.sm_count ? a.tiles : L.sm_count;           // persistent
+    if (grid > kEnergyGridMax) grid = kEnergyGridMax;
+    if (grid + 1 > L.esplit_n || !L.esplit || !L.esplit_cnt) return cudaErrorInvalidValue;
 #define PP_ELAUNCH(PR, SA)                                                                         \
     do {                                                                                           \
         auto kfn = tc_energy_kernel<PR, SA>;                                                       \
