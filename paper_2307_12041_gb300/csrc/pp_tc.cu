@@ -5,13 +5,13 @@
 //   tc_coeff_kernel   St = Xt^T Yt (contraction over blocks).  CTA tile 256 (u) x
 //                     256 (v) as two M=128, N=256 accumulators that share the Yt
 //                     operand; persistent over (tile, block slice) units.  A
-//                     slice is contracted in chains of at most C_CHAIN blocks:
-//                     the tensor cores' FP32 accumulation rounds toward zero,
-//                     a bias that grows with the number of MMAs accumulated into
-//                     one TMEM value, so each chain starts a fresh accumulator
-//                     and the epilogue adds it (round to nearest) into the
-//                     unit's FP32 partial; the slices are summed with Kahan
-//                     compensation by the finish kernel.
+//                     slice is contracted in chains of at most c_chain<PREC>()
+//                     blocks: the tensor cores' FP32 accumulation rounds toward
+//                     zero, a bias that grows with the number of MMAs
+//                     accumulated into one TMEM value, so each chain starts a
+//                     fresh accumulator and the epilogue adds it (round to
+//                     nearest) into the unit's FP32 partial; the slices are
+//                     summed with Kahan compensation by the finish kernel.
 //   tc_finish_kernel  a = G o (f St g) and K = f a g in the operand precision,
 //                     laid out so that one 3-D TMA box is one pipeline stage.
 //   tc_energy_kernel  T = Xt K and T' = Xh K for row tiles of 128 blocks (two
@@ -70,11 +70,10 @@ __device__ __forceinline__ void split_bf16(float x, __nv_bfloat16 &hi, __nv_bflo
 constexpr int C_TILE = 256;                 // u and v edge of a CTA tile
 constexpr int C_KB = 32;                    // blocks per pipeline stage
 constexpr int C_STAGES = 3;
-constexpr int C_CHAIN = 2048;               // most blocks accumulated in one TMEM chain
 constexpr int C_STAGE_BYTES = 65536;        // A 32 KB + B 32 KB (both precisions)
 constexpr int C_GEN_GROUPS = 2;            // generator groups filling alternate stages
 constexpr int C_GEN_WARPS = 8 * C_GEN_GROUPS;
-constexpr int C_EPI_WARPS = 4;
+constexpr int C_EPI_WARPS = 8;             // two per TMEM lane quarter: one per accumulator
 constexpr int C_LOADER_WARP = 1 + C_EPI_WARPS + C_GEN_WARPS;     // copies per-block records
 constexpr int C_THREADS = 32 * (C_LOADER_WARP + 1);
 constexpr int C_REC_BYTES = 2 * C_KB * (int)sizeof(AxisRec);    // x and y records of a stage
@@ -273,15 +272,23 @@ __device__ __forceinline__ void gen_coeff_bf16(unsigned char *op_hi, unsigned ch
     }
 }
 
-__device__ __forceinline__ void red_add4(float *p, float a, float b, float c, float d) {
-    asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(a), "f"(b), "f"(c), "f"(d)
-                 : "memory");
+__device__ __forceinline__ void red_add2(float *p, float a, float b) {
+    asm volatile("red.global.add.v2.f32 [%0], {%1, %2};" ::"l"(p), "f"(a), "f"(b) : "memory");
 }
 
+// Most blocks accumulated in one TMEM chain.  Each MMA step may truncate the FP32
+// accumulator by up to one unit in the last place, in a consistent direction:
+// 8192 TF32 blocks are 1024 steps of K = 8, a relative bias below 1.3e-4, small
+// beside the 2^-11 rounding of TF32 operands; BF16x3 (operands good to about
+// 2^-16, three MMAs per K = 16 step) keeps chains of 2048 blocks, 384 steps.
+template <int PREC>
+__host__ __device__ constexpr int c_chain() { return PREC == 1 ? 8192 : 2048; }
+
 // Stages per accumulation chain for a unit of nst stages: the fewest chains of at
-// most C_CHAIN blocks, of equal length (the last one possibly shorter).
+// most c_chain<PREC>() blocks, of equal length (the last one possibly shorter).
+template <int PREC>
 __device__ __forceinline__ int chain_stages(int nst) {
-    constexpr int cmax = C_CHAIN / C_KB;
+    constexpr int cmax = c_chain<PREC>() / C_KB;
     const int nch = (nst + cmax - 1) / cmax;
     return nch > 0 ? (nst + nch - 1) / nch : 1;
 }
@@ -330,7 +337,7 @@ __global__ void __launch_bounds__(C_THREADS, 1) tc_coeff_kernel(const CoeffArgs 
                 const int b0 = slice * args.slice_len;
                 const int b1 = min(args.n, b0 + args.slice_len);
                 const int nst = (b1 - b0 + C_KB - 1) / C_KB;
-                const int cst = chain_stages(nst);
+                const int cst = chain_stages<PREC>(nst);
                 for (int st = 0; st < nst; ++st, ++it) {
                     const int s = it % C_STAGES;
                     const int sc = st % cst;    // stage within the chain
@@ -395,8 +402,12 @@ __global__ void __launch_bounds__(C_THREADS, 1) tc_coeff_kernel(const CoeffArgs 
         __syncwarp();
     } else if (warp <= C_EPI_WARPS) {
         // ---------------- epilogue: TMEM -> FP32 partial tile ----------------
-        const int quarter = warp & 3;
-        const int row = quarter * 32 + lane;
+        // Warp w reads TMEM lanes 32 (w % 4) .. + 31 of accumulator (w - 1) / 4, 16
+        // lanes x 64 columns per load (16x256b shape: thread t holds rows t/4 and
+        // t/4 + 8, columns 8j + 2 (t % 4) + {0, 1}), so that the four threads of a
+        // row write one full 32-byte sector per store.
+        const int quarter = warp & 3, acc = (warp - 1) >> 2;
+        const int rsub = lane >> 2, csub = 2 * (lane & 3);
         uint32_t dc = 0;
         for (int unit = blockIdx.x; unit < args.units; unit += gridDim.x) {
             if (*abort_flag) break;
@@ -404,7 +415,7 @@ __global__ void __launch_bounds__(C_THREADS, 1) tc_coeff_kernel(const CoeffArgs 
             const int tu = tile / tiles_v, tv = tile % tiles_v;
             const int b0 = slice * args.slice_len;
             const int nst = (min(args.n, b0 + args.slice_len) - b0 + C_KB - 1) / C_KB;
-            const int nch = (nst + chain_stages(nst) - 1) / chain_stages(nst);
+            const int nch = (nst + chain_stages<PREC>(nst) - 1) / chain_stages<PREC>(nst);
 #pragma unroll 1
             for (int ch = 0; ch < nch; ++ch, ++dc) {
                 if (!mbar_wait(&bars.acc_full, dc & 1, kWaitLimit, abort_flag)) {
@@ -413,21 +424,26 @@ __global__ void __launch_bounds__(C_THREADS, 1) tc_coeff_kernel(const CoeffArgs 
                 }
                 tc_fence_after();
 #pragma unroll 1
-                for (int acc = 0; acc < 2; ++acc) {
-                    const int u = tu * C_TILE + acc * 128 + row;
-                    float *dst = args.part + ((size_t)slice * args.Mxc + u) * args.Myc + tv * C_TILE;
+                for (int half = 0; half < 2; ++half) {
+                    const int r0 = quarter * 32 + half * 16;          // first TMEM lane of the load
+                    const int u = tu * C_TILE + acc * 128 + r0 + rsub;
+                    float *dst0 = args.part + ((size_t)slice * args.Mxc + u) * args.Myc + tv * C_TILE + csub;
+                    float *dst1 = dst0 + (size_t)8 * args.Myc;          // row + 8
 #pragma unroll 1
-                    for (int c = 0; c < 256; c += 16) {
-                        float v[16];
-                        tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + acc * 256 + c, v);
-                        tmem_ld_wait();
+                    for (int c = 0; c < 256; c += 64) {
+                        float v[32];
+                        tmem_ld_16x256b_x8(tmem + ((uint32_t)r0 << 16) + acc * 256 + c, v);
+                        tmem_ld_wait_regs32(v);
 #pragma unroll
-                        for (int j = 0; j < 16; j += 4) {
-                            if (ch == 0)
-                                *reinterpret_cast<float4 *>(dst + c + j) =
-                                    make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
-                            else    // added in L2 (round to nearest) after this thread's earlier store
-                                red_add4(dst + c + j, v[j], v[j + 1], v[j + 2], v[j + 3]);
+                        for (int j = 0; j < 8; ++j) {
+                            float *p0 = dst0 + c + 8 * j, *p1 = dst1 + c + 8 * j;
+                            if (ch == 0) {
+                                *reinterpret_cast<float2 *>(p0) = make_float2(v[4 * j], v[4 * j + 1]);
+                                *reinterpret_cast<float2 *>(p1) = make_float2(v[4 * j + 2], v[4 * j + 3]);
+                            } else {    // added in L2 (round to nearest) after this thread's earlier store
+                                red_add2(p0, v[4 * j], v[4 * j + 1]);
+                                red_add2(p1, v[4 * j + 2], v[4 * j + 3]);
+                            }
                         }
                     }
                 }
