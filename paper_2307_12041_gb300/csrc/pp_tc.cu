@@ -98,42 +98,34 @@ struct CoeffArgs {
     unsigned *status;
 };
 
-// Reinsch's form of the three-term recurrence for a sampled sinusoid
-// y_k = f(a + k th), f = cos or sin, with the half step h = e^{i th / 2}:
-//   case A (cos th >= 0): lambda = 4 sin^2(th/2), sigma = 1, d_0 = y_0 - y_{-1};
-//   case B (cos th <  0): z_k = (-1)^k y_k is the sequence of step th - pi,
-//                         lambda = 4 cos^2(th/2), sigma = -1, d_0 = z_0 - z_{-1};
-//   d_{k+1} = d_k - lambda z_k,   z_{k+1} = z_k + d_{k+1},   y_k = sigma^k z_k.
-// Its rounding errors grow linearly in k in both cases (the plain recurrence
-// y_{k+1} = 2 cos(th) y_k - y_{k-1} amplifies them by 1 / sin th).  A = e^{i a}.
-__device__ __forceinline__ void reinsch_setup(float2 A, float2 h, bool cosine, float scale, float &z0,
-                                              float &d0, float &lam, float &sig) {
-    const float2 Ah = make_float2(fmaf(A.x, h.x, A.y * h.y), fmaf(A.y, h.x, -A.x * h.y));   // A conj(h)
-    const bool caseA = fabsf(h.x) >= fabsf(h.y);
-    lam = caseA ? 4.f * h.y * h.y : 4.f * h.x * h.x;
-    sig = caseA ? 1.f : -1.f;
-    z0 = scale * (cosine ? A.x : A.y);
-    // cos: y_0 -/+ y_{-1} = -2 sin(a - th/2) sin(th/2) | 2 cos(a - th/2) cos(th/2)
-    // sin: y_0 -/+ y_{-1} =  2 cos(a - th/2) sin(th/2) | 2 sin(a - th/2) cos(th/2)
-    if (cosine) d0 = scale * (caseA ? -2.f * Ah.y * h.y : 2.f * Ah.x * h.x);
-    else d0 = scale * (caseA ? 2.f * Ah.x * h.y : 2.f * Ah.y * h.x);
-}
-
-// TF32 generator: K-major rows of 4 consecutive blocks.  Thread gg (0..127) owns
-// the block pair 4*k4 + 2*pp + {0, 1} of the stage and the mode residue r; it
-// writes operand rows R = r + 8j (j = 0..31) as 8-byte halves of the 16-byte core
-// rows.  Modes r + 16k (even j) and r + 8 + 16k (odd j) are two sub-chains of
-// step 16; along each, cos(pi u s) and c sin(pi u t) follow Reinsch recurrences
-// (step th = 16 pi s, half step e^{i 8 pi s} from the record), the two blocks'
-// recurrences advanced together in packed registers.
+// TF32 generator.  A sampled sinusoid y_j = f(a + j th) (f = cos or sin) obeys
+// y_{j+1} = 2 cos(th) y_j - y_{j-1}.  With the signs sigma_j = +,+,-,-,+,+,...
+// (period 4, so that sigma_{j+1} sigma_{j-1} = -1) the scaled values s_j =
+// sigma_j y_j obey s_{j+1} = c_j s_j + s_{j-1}, c_j = +2 cos(th) for even j and
+// -2 cos(th) for odd j: one FMA per step and no negation.  The cosine chain of the
+// centre phase and the sine chain of the half-size phase carry the same signs, so
+// their product s^Z_j s^T_j is the basis value itself.
+//
+// Rounding: an error d entering at step i reaches step j multiplied by
+// sin((j - i) th) / sin th, at most j - i in magnitude, so after J steps the
+// accumulated error is below J^2 / 2 units of FP32 rounding: 512 units (3e-5
+// relative) for the 32-step chains here, far below the 2^-11 rounding of the TF32
+// operand they feed.
+//
+// Layout: K-major rows of 4 consecutive blocks.  Thread gg (0..127) owns the block
+// pair 4*k4 + 2*pp + {0, 1} of the stage and the mode residue r; it writes the
+// operand rows R = r + 8j (modes mode_base + r + 8j, j = 0..31) as 8-byte halves of
+// the 16-byte core rows, the two blocks' chains advanced together in packed
+// registers (step th = 8 pi s for the centre, 8 pi t for the half size; e^{i th}
+// from the record).
 __device__ __forceinline__ void gen_coeff_tf32(unsigned char *op, const AxisRec *recs, int nvalid,
                                                int mode_base, int gg) {
     const int lane = gg & 31, w = gg >> 5;
     const int r = lane & 7, pp = (lane >> 3) & 1, k4 = 2 * w + (lane >> 4);
     const int b0 = 4 * k4 + 2 * pp;
     const unsigned long long m0 = (unsigned long long)(mode_base + r);
-    // per block: [sub-chain E, O] x [Z (cos), T (c sin)] initial z, d; lambdas; sign
-    float zZ[2][2], dZ[2][2], zT[2][2], dT[2][2], lZ[2], lT[2], sg[2], v0[2];
+    // per block: s_0, s_{-1} of both chains, 2 cos(th) of both chains
+    float z0[2], zm[2], t0[2], tm[2], cz[2], ct[2], v0[2];
 #pragma unroll
     for (int b = 0; b < 2; ++b) {
         const int k = b0 + b;
@@ -141,52 +133,42 @@ __device__ __forceinline__ void gen_coeff_tf32(unsigned char *op, const AxisRec 
             const AxisRec &R = recs[k];
             const float2 AZ = gen::phase_poly(m0, R.s), AT = gen::phase_poly(m0, R.t);
             const float2 hZ = R.es8, hT = R.et8;
-            float sZ, sT;
-            reinsch_setup(AZ, hZ, true, 1.f, zZ[b][0], dZ[b][0], lZ[b], sZ);
-            reinsch_setup(AT, hT, false, R.c, zT[b][0], dT[b][0], lT[b], sT);
-            reinsch_setup(rot(AZ, hZ), hZ, true, 1.f, zZ[b][1], dZ[b][1], lZ[b], sZ);
-            reinsch_setup(rot(AT, hT), hT, false, R.c, zT[b][1], dT[b][1], lT[b], sT);
-            sg[b] = sZ * sT;
+            z0[b] = AZ.x;                                          // cos(pi m0 s)
+            zm[b] = -fmaf(AZ.x, hZ.x, AZ.y * hZ.y);                // -cos(pi (m0 - 8) s)
+            t0[b] = R.c * AT.y;                                    // c sin(pi m0 t)
+            tm[b] = -R.c * fmaf(AT.y, hT.x, -AT.x * hT.y);         // -c sin(pi (m0 - 8) t)
+            cz[b] = 2.f * hZ.x;
+            ct[b] = 2.f * hT.x;
             v0[b] = R.v0;
         } else {
-            zZ[b][0] = zZ[b][1] = dZ[b][0] = dZ[b][1] = 0.f;
-            zT[b][0] = zT[b][1] = dT[b][0] = dT[b][1] = 0.f;
-            lZ[b] = lT[b] = 0.f;
-            sg[b] = 1.f;
-            v0[b] = 0.f;
+            z0[b] = zm[b] = t0[b] = tm[b] = cz[b] = ct[b] = v0[b] = 0.f;
         }
     }
-    f2 ZE = gen::pk(zZ[0][0], zZ[1][0]), DZE = gen::pk(dZ[0][0], dZ[1][0]);
-    f2 TE = gen::pk(zT[0][0], zT[1][0]), DTE = gen::pk(dT[0][0], dT[1][0]);
-    f2 ZO = gen::pk(zZ[0][1], zZ[1][1]), DZO = gen::pk(dZ[0][1], dZ[1][1]);
-    f2 TO = gen::pk(zT[0][1], zT[1][1]), DTO = gen::pk(dT[0][1], dT[1][1]);
-    const f2 NLZ = gen::pk(-lZ[0], -lZ[1]), NLT = gen::pk(-lT[0], -lT[1]), SG = gen::pk(sg[0], sg[1]);
+    f2 Z = gen::pk(z0[0], z0[1]), Zp = gen::pk(zm[0], zm[1]);
+    f2 T = gen::pk(t0[0], t0[1]), Tp = gen::pk(tm[0], tm[1]);
+    const f2 CZ = gen::pk(cz[0], cz[1]), NCZ = gen::pk(-cz[0], -cz[1]);
+    const f2 CT = gen::pk(ct[0], ct[1]), NCT = gen::pk(-ct[0], -ct[1]);
     unsigned char *base = op + k4 * 128 + r * 16 + pp * 8;
-    auto advance = [&]() {
-        DZE = gen::fma2(NLZ, ZE, DZE);
-        ZE = gen::add2(ZE, DZE);
-        DTE = gen::fma2(NLT, TE, DTE);
-        TE = gen::add2(TE, DTE);
-        DZO = gen::fma2(NLZ, ZO, DZO);
-        ZO = gen::add2(ZO, DZO);
-        DTO = gen::fma2(NLT, TO, DTO);
-        TO = gen::add2(TO, DTO);
+    auto put = [&](int j) {
+        float a, b;
+        gen::upk(gen::mul2(Z, T), a, b);
+        *reinterpret_cast<float2 *>(base + j * 1024) = make_float2(to_tf32_mma(a), to_tf32_mma(b));
     };
-#pragma unroll 2
-    for (int k = 0; k < 16; k += 2) {
-        float a0, b0_, a1, b1;
-        // even k: sigma^k = 1
-        gen::upk(gen::mul2(ZE, TE), a0, b0_);
-        gen::upk(gen::mul2(ZO, TO), a1, b1);
-        *reinterpret_cast<float2 *>(base + (2 * k) * 1024) = make_float2(to_tf32_mma(a0), to_tf32_mma(b0_));
-        *reinterpret_cast<float2 *>(base + (2 * k + 1) * 1024) = make_float2(to_tf32_mma(a1), to_tf32_mma(b1));
-        advance();
-        // odd k: sigma^k = sigma
-        gen::upk(gen::mul2(gen::mul2(ZE, TE), SG), a0, b0_);
-        gen::upk(gen::mul2(gen::mul2(ZO, TO), SG), a1, b1);
-        *reinterpret_cast<float2 *>(base + (2 * k + 2) * 1024) = make_float2(to_tf32_mma(a0), to_tf32_mma(b0_));
-        *reinterpret_cast<float2 *>(base + (2 * k + 3) * 1024) = make_float2(to_tf32_mma(a1), to_tf32_mma(b1));
-        advance();
+#pragma unroll 4
+    for (int j = 0; j < 32; j += 2) {
+        put(j);
+        f2 nz = gen::fma2(CZ, Z, Zp), nt = gen::fma2(CT, T, Tp);     // even j: c_j = +2 cos th
+        Zp = Z;
+        Z = nz;
+        Tp = T;
+        T = nt;
+        put(j + 1);
+        nz = gen::fma2(NCZ, Z, Zp);                                   // odd j: c_j = -2 cos th
+        nt = gen::fma2(NCT, T, Tp);
+        Zp = Z;
+        Z = nz;
+        Tp = T;
+        T = nt;
     }
     // mode 0 (the u = 0 / v = 0 column): v0 = c pi t, not the sine limit the chain
     // gives; this thread stored that slot first, so its own later store wins
