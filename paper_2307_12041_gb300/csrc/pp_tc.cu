@@ -706,9 +706,82 @@ struct EnergyChain {
     }
 };
 
+// TF32, rectangle sampling: the stage's modes u0 .. u0 + 31 as two chains, u0 + j
+// (lane a) and u0 + 16 + j (lane b) for j = 0..15, advanced together in packed
+// registers.  cos(pi u s), sin(pi u s) and c sin(pi u t) follow the signed
+// three-term recurrence of the TF32 coefficient generator (one FMA per step,
+// signs +,+,-,- shared by the three chains, so that the products are the basis
+// values); 16 steps keep the rounding below 128 FP32 units (8e-6), far under the
+// TF32 operand rounding.
+__device__ __forceinline__ void gen_energy_tf32_rect(unsigned char *sb, const AxisRec &R, bool valid, int row,
+                                                     int u0) {
+    f2 C, S, T, Cp, Sp, Tp, KZ, KT, nku, dku;
+    float v0 = 0.f;
+    if (valid) {
+        const float2 za = gen::phase_poly((unsigned long long)u0, R.s);
+        const float2 ta = gen::phase_poly((unsigned long long)u0, R.t);
+        const float2 zb = rot(za, rot(R.es8, R.es8));      // u0 + 16: times e^{i 16 pi s}
+        const float2 tb = rot(ta, rot(R.et8, R.et8));
+        const float2 es = R.es, et = R.et;
+        C = gen::pk(za.x, zb.x);
+        S = gen::pk(za.y, zb.y);
+        T = gen::pk(R.c * ta.y, R.c * tb.y);
+        // s_{-1} = -y_{-1}, the chains' values at u - 1 (rotation by conj(e^{i pi s}))
+        Cp = gen::pk(-fmaf(za.x, es.x, za.y * es.y), -fmaf(zb.x, es.x, zb.y * es.y));
+        Sp = gen::pk(-fmaf(za.y, es.x, -za.x * es.y), -fmaf(zb.y, es.x, -zb.x * es.y));
+        Tp = gen::pk(-R.c * fmaf(ta.y, et.x, -ta.x * et.y), -R.c * fmaf(tb.y, et.x, -tb.x * et.y));
+        KZ = gen::pk(2.f * es.x, 2.f * es.x);
+        KT = gen::pk(2.f * et.x, 2.f * et.x);
+        nku = gen::pk(-(float)u0 * R.inv_l, -(float)(u0 + 16) * R.inv_l);
+        dku = gen::pk(-R.inv_l, -R.inv_l);
+        v0 = R.v0;
+    } else {
+        C = S = T = Cp = Sp = Tp = KZ = KT = nku = dku = gen::pk(0.f, 0.f);
+    }
+    const f2 NKZ = gen::pk(-KZ.v.x, -KZ.v.y), NKT = gen::pk(-KT.v.x, -KT.v.y);
+    // [128 rows x 32 u] tf32 K-major: core (row/8, u/4) at (row/8)*1024 + (u/4)*128
+    unsigned char *A = sb + (size_t)(row >> 3) * 1024 + (row & 7) * 16;
+    auto step = [&](const f2 &kz, const f2 &kt) {
+        const f2 nc = gen::fma2(kz, C, Cp), ns = gen::fma2(kz, S, Sp), nt = gen::fma2(kt, T, Tp);
+        Cp = C;
+        C = nc;
+        Sp = S;
+        S = ns;
+        Tp = T;
+        T = nt;
+        nku = gen::add2(nku, dku);
+    };
+#pragma unroll 1
+    for (int c = 0; c < 4; ++c) {
+        float ta[4], tb[4], ha[4], hb[4];
+#pragma unroll
+        for (int jj = 0; jj < 4; jj += 2) {
+            gen::upk(gen::mul2(C, T), ta[jj], tb[jj]);
+            gen::upk(gen::mul2(gen::mul2(S, T), nku), ha[jj], hb[jj]);
+            step(KZ, KT);                                   // even j: +2 cos
+            gen::upk(gen::mul2(C, T), ta[jj + 1], tb[jj + 1]);
+            gen::upk(gen::mul2(gen::mul2(S, T), nku), ha[jj + 1], hb[jj + 1]);
+            step(NKZ, NKT);                                 // odd j: -2 cos
+        }
+        if (c == 0 && u0 == 0 && valid) ta[0] = v0;        // u = 0: c pi t, not the sine limit
+        *reinterpret_cast<float4 *>(A + c * 128) =
+            make_float4(to_tf32_mma(ta[0]), to_tf32_mma(ta[1]), to_tf32_mma(ta[2]), to_tf32_mma(ta[3]));
+        *reinterpret_cast<float4 *>(A + 16384 + c * 128) =
+            make_float4(to_tf32_mma(ha[0]), to_tf32_mma(ha[1]), to_tf32_mma(ha[2]), to_tf32_mma(ha[3]));
+        *reinterpret_cast<float4 *>(A + (c + 4) * 128) =
+            make_float4(to_tf32_mma(tb[0]), to_tf32_mma(tb[1]), to_tf32_mma(tb[2]), to_tf32_mma(tb[3]));
+        *reinterpret_cast<float4 *>(A + 16384 + (c + 4) * 128) =
+            make_float4(to_tf32_mma(hb[0]), to_tf32_mma(hb[1]), to_tf32_mma(hb[2]), to_tf32_mma(hb[3]));
+    }
+}
+
 template <int PREC, int SAMPLE>
 __device__ __forceinline__ void gen_energy(unsigned char *sb, const AxisRec &R, bool valid, int row,
                                            int u0) {
+    if (PREC == 1 && SAMPLE == 0) {
+        gen_energy_tf32_rect(sb, R, valid, row, u0);
+        return;
+    }
     // two independent chains: u0..u0+15 (a) and u0+16..u0+31 (b)
     EnergyChain<SAMPLE> a, b;
     a.init(R, valid, u0);
