@@ -895,6 +895,71 @@ struct EpiRect {
         aY = x0 + x1;
     }
 };
+// Row dots for TF32 operands (rectangle sampling): cos(pi v s), sin(pi v s) and
+// sin(pi v t) over column pairs (v, v + 1) as signed three-term recurrences with a
+// 2-mode step (one FMA per step, signs +,+,-,- shared by the three chains), anchored
+// again from the phase every 64 columns, so that no chain runs more than 32 steps
+// (rounding below 512 FP32 units).
+struct EpiRect3 {
+    f2 C, S, T, Cp, Sp, Tp, K, KT, nlv, dlv, EN, EX, EY;
+    int col;
+    __device__ __forceinline__ void anchor(const YRec &Ry, int v) {
+        const float2 z = gen::phase_poly((unsigned long long)v, Ry.s);
+        const float2 t = gen::phase_poly((unsigned long long)v, Ry.t);
+        const float2 z1 = rot(z, Ry.es), t1 = rot(t, Ry.et);
+        const float2 e2s = rot(Ry.es, Ry.es), e2t = rot(Ry.et, Ry.et);
+        const float2 ce2s = make_float2(e2s.x, -e2s.y), ce2t = make_float2(e2t.x, -e2t.y);
+        const float2 zp = rot(z, ce2s), zp1 = rot(z1, ce2s), tp = rot(t, ce2t), tp1 = rot(t1, ce2t);
+        C = gen::pk(z.x, z1.x);
+        S = gen::pk(z.y, z1.y);
+        T = gen::pk(t.y, t1.y);
+        Cp = gen::pk(-zp.x, -zp1.x);                        // s_{-1} = -y_{-1}
+        Sp = gen::pk(-zp.y, -zp1.y);
+        Tp = gen::pk(-tp.y, -tp1.y);
+        K = gen::pk(2.f * e2s.x, 2.f * e2s.x);
+        KT = gen::pk(2.f * e2t.x, 2.f * e2t.x);
+        nlv = gen::pk(-(float)v * Ry.inv_l, -(float)(v + 1) * Ry.inv_l);
+    }
+    __device__ __forceinline__ void init(const YRec &Ry, int vb) {
+        anchor(Ry, vb);
+        dlv = gen::pk(-2.f * Ry.inv_l, -2.f * Ry.inv_l);
+        EN = EX = EY = gen::pk(0.f, 0.f);
+        col = 0;
+    }
+    __device__ __forceinline__ void cols8(const float t[8], const float tp[8], const YRec &Ry, int vb) {
+        if (col > 0 && (col & 63) == 0) anchor(Ry, vb + col);
+#pragma unroll
+        for (int j = 0; j < 8; j += 2) {
+            const f2 tt = gen::pk(t[j], t[j + 1]), ttp = gen::pk(tp[j], tp[j + 1]);
+            const f2 yt = gen::mul2(C, T), pr = gen::mul2(S, T);
+            EN = gen::fma2(tt, yt, EN);
+            EX = gen::fma2(ttp, yt, EX);
+            EY = gen::fma2(gen::mul2(tt, nlv), pr, EY);
+            nlv = gen::add2(nlv, dlv);
+            // step j / 2 of the chain: +2 cos for even, -2 cos for odd
+            const f2 k = (j & 2) ? gen::pk(-K.v.x, -K.v.y) : K;
+            const f2 kt = (j & 2) ? gen::pk(-KT.v.x, -KT.v.y) : KT;
+            const f2 nc = gen::fma2(k, C, Cp), ns = gen::fma2(k, S, Sp), nt = gen::fma2(kt, T, Tp);
+            Cp = C;
+            C = nc;
+            Sp = S;
+            S = ns;
+            Tp = T;
+            T = nt;
+        }
+        col += 8;
+    }
+    __device__ __forceinline__ void sums(float &aN, float &aX, float &aY) const {
+        float x0, x1;
+        gen::upk(EN, x0, x1);
+        aN = x0 + x1;
+        gen::upk(EX, x0, x1);
+        aX = x0 + x1;
+        gen::upk(EY, x0, x1);
+        aY = x0 + x1;
+    }
+};
+
 // Centre sampling: Yt = cos(pi v s') / g_v, Yh = -l_v sin(pi v s') / g_v, one chain.
 struct EpiCenter {
     float2 zs, es;
@@ -929,15 +994,25 @@ struct EpiCenter {
     }
 };
 
+__device__ __forceinline__ void epi_cols8(EpiRect3 &ep, const float t[8], const float tp[8], const YRec &Ry,
+                                          int vb) {
+    ep.cols8(t, tp, Ry, vb);
+}
+template <class E>
+__device__ __forceinline__ void epi_cols8(E &ep, const float t[8], const float tp[8], const YRec &, int) {
+    ep.cols8(t, tp);
+}
+
 // One thread's share of accumulator pass pc: TMEM lane row (trow), columns
 // [cb, cb + E_DRAIN_COLS) of the pass, global column base vb; adds its row dots
 // to (eN, eX, eY) and releases its part of TMEM.
-template <int SAMPLE>
+template <int PREC, int SAMPLE>
 __device__ __forceinline__ void drain_pass(EnergyBars &bars, volatile int *abort_flag, unsigned *status,
                                            uint32_t trow, int cb, int vb, int pc, bool valid,
                                            const YRec &Ry, float &eN, float &eX, float &eY) {
     if (*abort_flag) return;
-    typename std::conditional<SAMPLE == 0, EpiRect, EpiCenter>::type ep;
+    constexpr bool R3 = PREC == 1 && SAMPLE == 0;
+    typename std::conditional<R3, EpiRect3, typename std::conditional<SAMPLE == 0, EpiRect, EpiCenter>::type>::type ep;
     if (valid) ep.init(Ry, vb);          // phase anchors ahead of the wait
     if (!mbar_wait(&bars.acc_full, pc & 1, kWaitLimit, abort_flag)) {
         raise_timeout(status, abort_flag);
@@ -958,13 +1033,13 @@ __device__ __forceinline__ void drain_pass(EnergyBars &bars, volatile int *abort
     for (int c = 0; c < E_DRAIN_COLS; c += 16) {
         tmem_ld8(trow + cb + c + 8, tB);
         tmem_ld8(trow + cb + c + 8 + 256, pB);
-        if (valid) ep.cols8(tA, pA);
+        if (valid) epi_cols8(ep, tA, pA, Ry, vb);
         tmem_ld_wait_regs(tB, pB);
         if (c + 16 < E_DRAIN_COLS) {
             tmem_ld8(trow + cb + c + 16, tA);
             tmem_ld8(trow + cb + c + 16 + 256, pA);
         }
-        if (valid) ep.cols8(tB, pB);
+        if (valid) epi_cols8(ep, tB, pB, Ry, vb);
         tmem_ld_wait_regs(tA, pA);
     }
     tc_fence_before();
@@ -1195,7 +1270,7 @@ tc_energy_kernel(const __grid_constant__ CUtensorMap tm_hi, const __grid_constan
                 eN = eX = eY = 0.f;
                 v0 = vc;
             }
-            drain_pass<SAMPLE>(bars, abort_flag, args.status, trow, cq * E_DRAIN_COLS,
+            drain_pass<PREC, SAMPLE>(bars, abort_flag, args.status, trow, cq * E_DRAIN_COLS,
                                vc * E_VC + cq * E_DRAIN_COLS, pc, valid, Ry, eN, eX, eY);
             if (vc == nvc - 1 || un == ue - 1)
                 finish_segment(bars, abort_flag, args, seg++, tile, v0, vc, nvc, row, cq, eN, eX, eY);
