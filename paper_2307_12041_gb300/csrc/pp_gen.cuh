@@ -82,5 +82,16 @@ __device__ __forceinline__ float2 phase_poly(unsigned long long m, unsigned long
     return make_float2((k == 1u || k == 2u) ? -c_ : c_, (k >= 2u) ? -s_ : s_);
 }
 
+// e^{i pi m s} from the hardware sine and cosine (__sincosf: absolute error at most
+// 2^-21.4 for arguments in [-pi, pi]); the reduced phase keeps 31 bits.  For the
+// TF32 operands only, whose own rounding (2^-11 relative) is far larger.
+__device__ __forceinline__ float2 phase_sfu(unsigned long long m, unsigned long long s) {
+    const long long q = (long long)((m * s) << 1);      // (m s mod 2) in [-1, 1) half-turns, 2^-63 units
+    const float y = (float)(int)(q >> 32) * (3.14159265358979f * 0x1p-31f);   // radians in [-pi, pi)
+    float sn, cs;
+    __sincosf(y, &sn, &cs);
+    return make_float2(cs, sn);
+}
+
 }  // namespace gen
 }  // namespace pp

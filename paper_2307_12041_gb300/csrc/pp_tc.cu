@@ -109,8 +109,9 @@ struct CoeffArgs {
 // Rounding: an error d entering at step i reaches step j multiplied by
 // sin((j - i) th) / sin th, at most j - i in magnitude, so after J steps the
 // accumulated error is below J^2 / 2 units of FP32 rounding: 512 units (3e-5
-// relative) for the 32-step chains here, far below the 2^-11 rounding of the TF32
-// operand they feed.
+// relative) for the 32-step chains here; the anchors come from the hardware sine
+// and cosine (error 4e-7, at most 32 times that at the chain's end).  Both are far
+// below the 2^-11 rounding of the TF32 operand they feed.
 //
 // Layout: K-major rows of 4 consecutive blocks.  Thread gg (0..127) owns the block
 // pair 4*k4 + 2*pp + {0, 1} of the stage and the mode residue r; it writes the
@@ -131,7 +132,7 @@ __device__ __forceinline__ void gen_coeff_tf32(unsigned char *op, const AxisRec 
         const int k = b0 + b;
         if (k < nvalid) {
             const AxisRec &R = recs[k];
-            const float2 AZ = gen::phase_poly(m0, R.s), AT = gen::phase_poly(m0, R.t);
+            const float2 AZ = gen::phase_sfu(m0, R.s), AT = gen::phase_sfu(m0, R.t);
             const float2 hZ = R.es8, hT = R.et8;
             z0[b] = AZ.x;                                          // cos(pi m0 s)
             zm[b] = -fmaf(AZ.x, hZ.x, AZ.y * hZ.y);                // -cos(pi (m0 - 8) s)
@@ -711,15 +712,16 @@ struct EnergyChain {
 // registers.  cos(pi u s), sin(pi u s) and c sin(pi u t) follow the signed
 // three-term recurrence of the TF32 coefficient generator (one FMA per step,
 // signs +,+,-,- shared by the three chains, so that the products are the basis
-// values); 16 steps keep the rounding below 128 FP32 units (8e-6), far under the
-// TF32 operand rounding.
+// values); 16 steps keep the rounding below 128 FP32 units (8e-6) and the
+// hardware sine and cosine anchors (error 4e-7) below 16 times theirs, far under
+// the TF32 operand rounding.
 __device__ __forceinline__ void gen_energy_tf32_rect(unsigned char *sb, const AxisRec &R, bool valid, int row,
                                                      int u0) {
     f2 C, S, T, Cp, Sp, Tp, KZ, KT, nku, dku;
     float v0 = 0.f;
     if (valid) {
-        const float2 za = gen::phase_poly((unsigned long long)u0, R.s);
-        const float2 ta = gen::phase_poly((unsigned long long)u0, R.t);
+        const float2 za = gen::phase_sfu((unsigned long long)u0, R.s);
+        const float2 ta = gen::phase_sfu((unsigned long long)u0, R.t);
         const float2 zb = rot(za, rot(R.es8, R.es8));      // u0 + 16: times e^{i 16 pi s}
         const float2 tb = rot(ta, rot(R.et8, R.et8));
         const float2 es = R.es, et = R.et;
@@ -898,14 +900,19 @@ struct EpiRect {
 // Row dots for TF32 operands (rectangle sampling): cos(pi v s), sin(pi v s) and
 // sin(pi v t) over column pairs (v, v + 1) as signed three-term recurrences with a
 // 2-mode step (one FMA per step, signs +,+,-,- shared by the three chains), anchored
-// again from the phase every 64 columns, so that no chain runs more than 32 steps
-// (rounding below 512 FP32 units).
+// again from the phase (hardware sine and cosine) every 64 columns, so that no
+// chain runs more than 32 steps (rounding below 512 FP32 units).  The derivative
+// dot sum_k n_k a_k, with a_k = T'_k sin(pi v s) sin(pi v t) and the linear weight
+// n_k = n_0 + k d (n = -l_v), is summed as n_0 A + d (K A - B) with A = sum a_k and
+// B = sum of the partial sums of A (sum_k k a_k = K A - B): two operations a step
+// instead of three.
 struct EpiRect3 {
-    f2 C, S, T, Cp, Sp, Tp, K, KT, nlv, dlv, EN, EX, EY;
+    f2 C, S, T, Cp, Sp, Tp, K, KT, n0, EN, EX, EA, EB;
+    float dl;
     int col;
     __device__ __forceinline__ void anchor(const YRec &Ry, int v) {
-        const float2 z = gen::phase_poly((unsigned long long)v, Ry.s);
-        const float2 t = gen::phase_poly((unsigned long long)v, Ry.t);
+        const float2 z = gen::phase_sfu((unsigned long long)v, Ry.s);
+        const float2 t = gen::phase_sfu((unsigned long long)v, Ry.t);
         const float2 z1 = rot(z, Ry.es), t1 = rot(t, Ry.et);
         const float2 e2s = rot(Ry.es, Ry.es), e2t = rot(Ry.et, Ry.et);
         const float2 ce2s = make_float2(e2s.x, -e2s.y), ce2t = make_float2(e2t.x, -e2t.y);
@@ -918,12 +925,12 @@ struct EpiRect3 {
         Tp = gen::pk(-tp.y, -tp1.y);
         K = gen::pk(2.f * e2s.x, 2.f * e2s.x);
         KT = gen::pk(2.f * e2t.x, 2.f * e2t.x);
-        nlv = gen::pk(-(float)v * Ry.inv_l, -(float)(v + 1) * Ry.inv_l);
     }
     __device__ __forceinline__ void init(const YRec &Ry, int vb) {
         anchor(Ry, vb);
-        dlv = gen::pk(-2.f * Ry.inv_l, -2.f * Ry.inv_l);
-        EN = EX = EY = gen::pk(0.f, 0.f);
+        n0 = gen::pk(-(float)vb * Ry.inv_l, -(float)(vb + 1) * Ry.inv_l);
+        dl = -2.f * Ry.inv_l;
+        EN = EX = EA = EB = gen::pk(0.f, 0.f);
         col = 0;
     }
     __device__ __forceinline__ void cols8(const float t[8], const float tp[8], const YRec &Ry, int vb) {
@@ -934,8 +941,8 @@ struct EpiRect3 {
             const f2 yt = gen::mul2(C, T), pr = gen::mul2(S, T);
             EN = gen::fma2(tt, yt, EN);
             EX = gen::fma2(ttp, yt, EX);
-            EY = gen::fma2(gen::mul2(tt, nlv), pr, EY);
-            nlv = gen::add2(nlv, dlv);
+            EA = gen::fma2(tt, pr, EA);
+            EB = gen::add2(EB, EA);
             // step j / 2 of the chain: +2 cos for even, -2 cos for odd
             const f2 k = (j & 2) ? gen::pk(-K.v.x, -K.v.y) : K;
             const f2 kt = (j & 2) ? gen::pk(-KT.v.x, -KT.v.y) : KT;
@@ -955,7 +962,9 @@ struct EpiRect3 {
         aN = x0 + x1;
         gen::upk(EX, x0, x1);
         aX = x0 + x1;
-        gen::upk(EY, x0, x1);
+        const float steps = (float)(col >> 1);
+        const f2 kab = gen::fma2(gen::pk(steps, steps), EA, gen::pk(-EB.v.x, -EB.v.y));   // K A - B
+        gen::upk(gen::fma2(n0, EA, gen::mul2(gen::pk(dl, dl), kab)), x0, x1);
         aY = x0 + x1;
     }
 };
