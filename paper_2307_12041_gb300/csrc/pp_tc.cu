@@ -1028,28 +1028,25 @@ __device__ __forceinline__ void drain_pass(EnergyBars &bars, volatile int *abort
         return;
     }
     tc_fence_after();
-    // 8-column chunks, the TMEM loads of the next chunk in flight while the
-    // current one is used
-    float tA[8], pA[8], tB[8], pB[8];
-    tmem_ld8(trow + cb, tA);
-    tmem_ld8(trow + cb + 256, pA);
-    tmem_ld_wait_regs(tA, pA);
-    // v = 0 column (rectangle sampling): Yt = pi t there, not the sine limit 0 the
-    // chain gives; Yh = 0
-    const float fixN = (SAMPLE == 0 && vb == 0) ? tA[0] * Ry.v0 : 0.f;
-    const float fixX = (SAMPLE == 0 && vb == 0) ? pA[0] * Ry.v0 : 0.f;
+    // 16-column chunks (T and T' of each): one load round per chunk, whose
+    // latency is paid once per 16 columns
+    float tA[16], pA[16];
+    float fixN = 0.f, fixX = 0.f;
 #pragma unroll 1
     for (int c = 0; c < E_DRAIN_COLS; c += 16) {
-        tmem_ld8(trow + cb + c + 8, tB);
-        tmem_ld8(trow + cb + c + 8 + 256, pB);
-        if (valid) epi_cols8(ep, tA, pA, Ry, vb);
-        tmem_ld_wait_regs(tB, pB);
-        if (c + 16 < E_DRAIN_COLS) {
-            tmem_ld8(trow + cb + c + 16, tA);
-            tmem_ld8(trow + cb + c + 16 + 256, pA);
+        tmem_ld16(trow + cb + c, tA);
+        tmem_ld16(trow + cb + c + 256, pA);
+        tmem_ld_wait_regs16(tA, pA);
+        // v = 0 column (rectangle sampling): Yt = pi t there, not the sine limit 0 the
+        // chain gives; Yh = 0
+        if (SAMPLE == 0 && c == 0 && vb == 0) {
+            fixN = tA[0] * Ry.v0;
+            fixX = pA[0] * Ry.v0;
         }
-        if (valid) epi_cols8(ep, tB, pB, Ry, vb);
-        tmem_ld_wait_regs(tA, pA);
+        if (valid) {
+            epi_cols8(ep, tA, pA, Ry, vb);
+            epi_cols8(ep, tA + 8, pA + 8, Ry, vb);
+        }
     }
     tc_fence_before();
     mbar_arrive(&bars.acc_empty);
