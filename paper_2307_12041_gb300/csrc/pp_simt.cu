@@ -31,33 +31,33 @@ __global__ void prep_kernel(const float *__restrict__ x, const float *__restrict
     const size_t tid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     const size_t stride = (size_t)gridDim.x * blockDim.x;
     const double halfW = 0.5 * invW, halfH = 0.5 * invH;       // exact: powers of two
-    // work item i < n: the x record of block i; n <= i < 2n: the y record of block i - n
-    for (size_t i = tid; i < 2 * (size_t)n; i += stride) {
-        const bool ax = i < (size_t)n;
-        const size_t b = ax ? i : i - n;
-        const float pos = ax ? x[b] : y[b], len = ax ? w[b] : h[b];
-        const double k = ax ? invW : invH, kh = ax ? halfW : halfH;
-        const float pil = ax ? piW : piH;
-        AxisRec r;
-        r.s = fixed_halfturns(pos, k);
-        r.t = fixed_halfturns(len, kh);
-        r.es = phase_cs(1, r.s);
-        r.et = phase_cs(1, r.t);
-        r.inv_l = pil;
-        r.es8 = phase_cs(8, r.s);
-        r.et8 = phase_cs(8, r.t);
-        if (ax) {
-            const float ci = c ? c[b] : 1.0f;
-            r.v0 = ci * (0.5f * pil * len);                           // c pi t
-            r.q = ci * len * h[b];
-            r.c = ci;
-            xr[b] = r;
-        } else {
-            r.v0 = 0.5f * pil * len;
-            r.q = 1.0f;
-            r.c = 1.0f;
-            yr[b] = r;
-        }
+    // one thread per block: its x and y records (independent work, issued together)
+    for (size_t b = tid; b < (size_t)n; b += stride) {
+        const float px = x[b], py = y[b], lw = w[b], lh = h[b];
+        const float ci = c ? c[b] : 1.0f;
+        AxisRec rx, ry;
+        rx.s = fixed_halfturns(px, invW);
+        ry.s = fixed_halfturns(py, invH);
+        rx.t = fixed_halfturns(lw, halfW);
+        ry.t = fixed_halfturns(lh, halfH);
+        rx.es = phase_cs(1, rx.s);
+        ry.es = phase_cs(1, ry.s);
+        rx.et = phase_cs(1, rx.t);
+        ry.et = phase_cs(1, ry.t);
+        rx.es8 = phase_cs(8, rx.s);
+        ry.es8 = phase_cs(8, ry.s);
+        rx.et8 = phase_cs(8, rx.t);
+        ry.et8 = phase_cs(8, ry.t);
+        rx.inv_l = piW;
+        ry.inv_l = piH;
+        rx.v0 = ci * (0.5f * piW * lw);                               // c pi t
+        rx.q = ci * lw * lh;
+        rx.c = ci;
+        ry.v0 = 0.5f * piH * lh;
+        ry.q = 1.0f;
+        ry.c = 1.0f;
+        xr[b] = rx;
+        yr[b] = ry;
     }
     for (size_t j = tid; j < nS; j += stride) S64[j] = 0.0;
     if (tid == 0 && e_total) *e_total = 0.0;
@@ -65,7 +65,7 @@ __global__ void prep_kernel(const float *__restrict__ x, const float *__restrict
 
 cudaError_t launch_prep(const Launch &L, bool zero_S, double *e_total) {
     size_t nS = zero_S ? (size_t)L.Mx * L.My : 0;
-    size_t work = 2 * (size_t)L.n > nS ? 2 * (size_t)L.n : nS;
+    size_t work = (size_t)L.n > nS ? (size_t)L.n : nS;
     int blocks = (int)((work + 255) / 256);
     if (blocks < 1) blocks = 1;
     if (blocks > 32 * L.sm_count) blocks = 32 * L.sm_count;

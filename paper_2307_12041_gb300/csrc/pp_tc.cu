@@ -561,9 +561,25 @@ __global__ void tc_finish_kernel(const float *__restrict__ part, int slices, int
             if (a_in) {
                 av = a_in[(size_t)u * My + v];
             } else {
+                // slices in order (Kahan), their loads issued eight at a time
                 float S = 0.f, comp = 0.f;
-                for (int s = 0; s < slices; ++s) {
-                    const float y = part[((size_t)s * Mxc + u) * Myc + v] - comp;
+                const size_t sstride = (size_t)Mxc * Myc;
+                const float *src = part + (size_t)u * Myc + v;
+                int s = 0;
+                for (; s + 8 <= slices; s += 8) {
+                    float pv[8];
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) pv[q] = __ldcg(src + (size_t)(s + q) * sstride);
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) {
+                        const float y = pv[q] - comp;
+                        const float t = S + y;
+                        comp = (t - S) - y;
+                        S = t;
+                    }
+                }
+                for (; s < slices; ++s) {
+                    const float y = __ldcg(src + (size_t)s * sstride) - comp;
                     const float t = S + y;
                     comp = (t - S) - y;
                     S = t;
