@@ -145,8 +145,9 @@ pp_status pp_sync_status(void *stream);
  * (2^-62 half-turn units), exactly as the per-block records hold it;
  * then out[2i], out[2i+1] = cos, sin of pi * (m[i] * s mod 2), evaluated by
  * `evaluator` 0 (the records' and CUDA-core kernels' evaluator: sincospif of the
- * top 24 phase bits plus a first-order residual rotation) or 1 (the tensor-core
- * generators' anchor: quarter-turn reduction and Taylor polynomials).
+ * top 24 phase bits plus a first-order residual rotation), 1 (the BF16x3
+ * generators' anchor: quarter-turn reduction and Taylor polynomials) or 2 (the
+ * TF32 generators' anchor: the hardware sine and cosine of the reduced phase).
  * x (float32), m (int32, >= 0) and out (float32, 2 * count) are device arrays.
  * PP_EINVAL for L outside [1e-300, 1e300], count < 0, NULL or host pointers, or an
  * unknown evaluator; asynchronous on `stream`. */

@@ -432,7 +432,7 @@ pp_status pp_phase_eval(const float *x, double L, const int32_t *m, int64_t coun
     if (!(std::isfinite(L) && L >= 1e-300 && L <= 1e300))
         return fail(PP_EINVAL, "L must be finite and in [1e-300, 1e300]");
     if (count < 0) return fail(PP_EINVAL, "count must be >= 0");
-    if (evaluator != 0 && evaluator != 1) return fail(PP_EINVAL, "evaluator must be 0 or 1");
+    if (evaluator < 0 || evaluator > 2) return fail(PP_EINVAL, "evaluator must be 0, 1 or 2");
     if (count == 0) return PP_OK;
     if ((st = check_dev_ptr(x, dev, "x")) != PP_OK) return st;
     if ((st = check_dev_ptr(m, dev, "m")) != PP_OK) return st;

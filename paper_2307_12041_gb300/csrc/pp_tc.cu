@@ -190,7 +190,9 @@ __device__ __forceinline__ void split2(float a, float b, uint32_t &hi, uint32_t 
 
 // BF16 generator: MN-major rows of 8 consecutive modes of one block.  Thread
 // (block k, lane group lg) writes mode groups lg + 4q (q = 0..7), 8 modes each,
-// hi and lo parts; even and odd modes advance as two packed chains.  Element
+// hi and lo parts; even and odd modes advance as two packed chains, the group
+// anchors by complex rotation (32 modes), the modes within a group by the signed
+// three-term recurrence.  Element
 // (mode R, block k) at (R/8)*128 + (k/8)*4096 + (k%8)*16.
 __device__ __forceinline__ void gen_coeff_bf16(unsigned char *op_hi, unsigned char *op_lo,
                                                const AxisRec *recs, int nvalid, int mode_base, int g) {
@@ -216,7 +218,6 @@ __device__ __forceinline__ void gen_coeff_bf16(unsigned char *op_hi, unsigned ch
     c2 GS = gen::make_c2(za, rot(za, es)), GT = gen::make_c2(ta, rot(ta, et));
     const float2 es2 = rot(es, es), et2 = rot(et, et);
     const float2 s16 = rot(es8, es8), t16 = rot(et8, et8);
-    const gen::rot2_step S2 = gen::make_step(es2, es2), T2 = gen::make_step(et2, et2);
     const gen::rot2_step S32 = gen::make_step(rot(s16, s16), rot(s16, s16));
     const gen::rot2_step T32 = gen::make_step(rot(t16, t16), rot(t16, t16));
     const size_t koff = (size_t)(k >> 3) * 4096 + (k & 7) * 16;
@@ -225,23 +226,48 @@ __device__ __forceinline__ void gen_coeff_bf16(unsigned char *op_hi, unsigned ch
     const gen::rot2_step S128 = gen::make_step(rot(s64, s64), rot(s64, s64));
     const gen::rot2_step T128 = gen::make_step(rot(t64, t64), rot(t64, t64));
     c2 HS = gen::rot2(GS, S128), HT = gen::rot2(GT, T128);
+    // within a group, (m, m+1) advance by the signed three-term recurrence of the
+    // TF32 generators (4 steps: rounding below 8 FP32 units), started from the
+    // group's complex anchor and its value two modes back (times conj(e^{2 i pi s}))
+    const f2 KZ = gen::pk(2.f * es2.x, 2.f * es2.x), NKZ = gen::pk(-2.f * es2.x, -2.f * es2.x);
+    const f2 KT = gen::pk(2.f * et2.x, 2.f * et2.x), NKT = gen::pk(-2.f * et2.x, -2.f * et2.x);
+    const f2 E2X = gen::pk(es2.x, es2.x), E2Y = gen::pk(es2.y, es2.y);
+    const f2 F2X = gen::pk(et2.x, et2.x), NF2Y = gen::pk(-et2.y, -et2.y);
+    auto start = [&](const c2 &z, const c2 &t, f2 &Z, f2 &Zp, f2 &T, f2 &Tp) {
+        Z = z.re;
+        T = t.im;
+        // s_{-1} = -y_{-1}: -Re(z conj(e2)) = -(z.re e2.x + z.im e2.y), -Im(t conj(e2))
+        const f2 zr = gen::fma2(z.re, E2X, gen::mul2(z.im, E2Y));
+        const f2 ti = gen::fma2(t.im, F2X, gen::mul2(t.re, NF2Y));
+        Zp = gen::pk(-zr.v.x, -zr.v.y);
+        Tp = gen::pk(-ti.v.x, -ti.v.y);
+    };
 #pragma unroll 1
     for (int q = 0; q < 4; ++q) {
         const int grp0 = lg + 4 * q, grp1 = grp0 + 16;
-        c2 z0 = GS, t0 = GT, z1 = HS, t1 = HT;
+        f2 Z0, Zp0, T0, Tp0, Z1, Zp1, T1, Tp1;
+        start(GS, GT, Z0, Zp0, T0, Tp0);
+        start(HS, HT, Z1, Zp1, T1, Tp1);
         uint32_t hi0[4], lo0[4], hi1[4], lo1[4];
 #pragma unroll
         for (int jj = 0; jj < 4; ++jj) {
             float a, b, c, d;
-            gen::upk(gen::mul2(z0.re, t0.im), a, b);
-            gen::upk(gen::mul2(z1.re, t1.im), c, d);
+            gen::upk(gen::mul2(Z0, T0), a, b);
+            gen::upk(gen::mul2(Z1, T1), c, d);
             if (jj == 0 && mode_base + 8 * grp0 == 0) a = v0;
             split2(a, b, hi0[jj], lo0[jj]);
             split2(c, d, hi1[jj], lo1[jj]);
-            z0 = gen::rot2(z0, S2);
-            t0 = gen::rot2(t0, T2);
-            z1 = gen::rot2(z1, S2);
-            t1 = gen::rot2(t1, T2);
+            const f2 kz = (jj & 1) ? NKZ : KZ, kt = (jj & 1) ? NKT : KT;
+            const f2 nz0 = gen::fma2(kz, Z0, Zp0), nt0 = gen::fma2(kt, T0, Tp0);
+            const f2 nz1 = gen::fma2(kz, Z1, Zp1), nt1 = gen::fma2(kt, T1, Tp1);
+            Zp0 = Z0;
+            Z0 = nz0;
+            Tp0 = T0;
+            T0 = nt0;
+            Zp1 = Z1;
+            Z1 = nz1;
+            Tp1 = T1;
+            T1 = nt1;
         }
         const size_t off0 = (size_t)grp0 * 128 + koff, off1 = (size_t)grp1 * 128 + koff;
         *reinterpret_cast<uint4 *>(op_hi + off0) = make_uint4(hi0[0], hi0[1], hi0[2], hi0[3]);
@@ -1399,7 +1425,7 @@ __global__ void phase_eval_kernel(const float *__restrict__ x, double invL, cons
          i += (int64_t)gridDim.x * blockDim.x) {
         const unsigned long long s = fixed_halfturns(x[i], invL);
         const unsigned long long mm = (unsigned long long)m[i];
-        out[i] = evaluator == 0 ? phase_cs(mm, s) : gen::phase_poly(mm, s);
+        out[i] = evaluator == 0 ? phase_cs(mm, s) : evaluator == 1 ? gen::phase_poly(mm, s) : gen::phase_sfu(mm, s);
     }
 }
 }  // namespace

@@ -4,9 +4,13 @@ double 1/L as the records form it, reduced modulo 2 and rounded to 2^-62
 half-turns with Python integers, m*s mod 2 is taken
 exactly, and cos/sin of pi times that phase come from FP64 numpy.  Both device
 evaluators (the sincospif-based one of the records and CUDA-core kernels, and the
-Taylor-polynomial anchor of the tensor-core generators) must agree to a few FP32
-units at every mode up to 65535, including phases that need exact reduction
-(m * s far beyond FP32's reach)."""
+Taylor-polynomial anchor of the BF16x3 generators) must agree to a few FP32 units
+at every mode up to 65535, including phases that need exact reduction (m * s far
+beyond FP32's reach).  The TF32 generators' anchor (the hardware sine and cosine
+of the exactly reduced phase) must stay within its documented bound: absolute
+error at most 2^-21.41 (3.6e-7) for arguments in [-pi, pi], plus the rounding of
+the 31-bit phase to FP32 (2^-24 of pi, 1.9e-7) and of the product by pi (1e-7):
+1e-6 in all."""
 import math
 from fractions import Fraction
 
@@ -41,17 +45,20 @@ def cases(seed, n, L):
     return x, m
 
 
+TOL = {0: 3e-7, 1: 3e-7, 2: 1e-6}
+
+
 @pytest.mark.parametrize("L", [1.0, 0.7, 123.25])
-@pytest.mark.parametrize("evaluator", [0, 1])
+@pytest.mark.parametrize("evaluator", [0, 1, 2])
 def test_phase_evaluators_match_exact_reduction(pp, L, evaluator):
     x, m = cases(int(L * 100) + evaluator, 4000, L)
     got = pp.binding.phase_eval(torch.from_numpy(x).cuda(), L, torch.from_numpy(m).cuda(),
                                 evaluator).double().cpu().numpy()
     ref = exact_phase(x, L, m)
     err = np.abs(got - ref).max()
-    assert err <= 3e-7, (evaluator, err)
-    # unit modulus to FP32 rounding
-    assert np.abs(np.hypot(got[:, 0], got[:, 1]) - 1).max() <= 3e-7
+    assert err <= TOL[evaluator], (evaluator, err)
+    # unit modulus to FP32 rounding (to the hardware functions' error for evaluator 2)
+    assert np.abs(np.hypot(got[:, 0], got[:, 1]) - 1).max() <= TOL[evaluator]
 
 
 def test_phase_eval_rejects_bad_arguments(pp):
@@ -60,4 +67,4 @@ def test_phase_eval_rejects_bad_arguments(pp):
     with pytest.raises(pp.binding.PPError):
         pp.binding.phase_eval(x, 0.0, m)
     with pytest.raises(pp.binding.PPError):
-        pp.binding.phase_eval(x, 1.0, m, evaluator=2)
+        pp.binding.phase_eval(x, 1.0, m, evaluator=3)
