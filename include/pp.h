@@ -201,6 +201,76 @@ pp_status pp_descent_step(double W, double H, int64_t n, float *x, float *y, con
                           const float *h, const float *gx, const float *gy, const uint8_t *movable,
                           float lr, float sigma, uint64_t seed, uint64_t step, void *stream);
 
+/* ---- placement loop (Sec. IV: min f = W_LSE + lambda N, one Nesterov step per
+ * iteration, a penalty update and an overflow stop, "as in ePlace"; the host
+ * orchestrates, these entry points do the per-iteration work on the device) ---- */
+
+/* A netlist in both orientations (device int32 arrays): net e's pins are the cells
+ * net_pin[net_ptr[e] .. net_ptr[e+1]); cell i's nets are cell_net[cell_ptr[i] ..
+ * cell_ptr[i+1]).  Pins sit at the cell centres.  The kernels index with these
+ * arrays unchecked: every pin must lie in [0, n_cells), every net in [0, n_nets),
+ * and the pointer arrays must be non-decreasing from 0 (the Python binding checks
+ * this when it builds the netlist). */
+typedef struct {
+    int32_t n_cells, n_nets;
+    const int32_t *net_ptr, *net_pin;
+    const int32_t *cell_ptr, *cell_net;
+} pp_netlist;
+
+/* Bytes of workspace pp_wirelength needs: 32 per net (per-net maxima, minima and
+ * the reciprocals of the shifted exponential sums), rounded up to 256. */
+size_t pp_wirelength_workspace_size(int32_t n_nets);
+
+/* Log-sum-exp wirelength (Sec. IV's W_LSE, the smooth HPWL model of ePlace):
+ *   W = sum_e sum_{axis} gamma [ln sum_{i in e} e^{x_i/gamma} + ln sum_{i in e} e^{-x_i/gamma}]
+ * over nets of two or more pins, each sum shifted by the net's max (min) so that no
+ * exponential overflows; gx, gy (float32, n_cells) receive dW/dx, dW/dy, gathered
+ * per cell from its nets (no atomics); out (device, 2 doubles) receives
+ * {W, HPWL}.  x, y: float32 device arrays of n_cells.  PP_EINVAL for gamma not
+ * finite or <= 0, a NULL or host pointer; PP_ENOMEM_WS for a short workspace
+ * (256-byte aligned device memory).  Asynchronous on `stream`. */
+pp_status pp_wirelength(const pp_netlist *netlist, const float *x, const float *y, float gamma, float *gx,
+                        float *gy, double *out, void *ws, size_t ws_bytes, void *stream);
+
+/* Objective gradient with ePlace's diagonal preconditioner:
+ *   g_i = (gw_i + lambda gn_i) / max(1, deg_i + lambda q_i)
+ * with deg_i = cell_ptr[i+1] - cell_ptr[i] (0 if cell_ptr is NULL) and q_i the
+ * block's charge (c w h); g_i = 0 where movable[i] == 0.  float32 device arrays of
+ * n; movable uint8 or NULL.  PP_EINVAL for lambda not finite or < 0 or a bad
+ * pointer.  Asynchronous on `stream`. */
+pp_status pp_place_combine(int64_t n, const float *gwx, const float *gwy, const float *gnx, const float *gny,
+                           const int32_t *cell_ptr, const float *q, const uint8_t *movable, float lambda,
+                           float *gx, float *gy, void *stream);
+
+/* norms[0] = sum_i |v_i - vp_i|^2, norms[1] = sum_i |g_i - gp_i|^2 (both axes, FP64),
+ * the quantities of the Nesterov step length.  norms: device, 2 doubles (zeroed
+ * here).  Asynchronous on `stream`. */
+pp_status pp_step_norms(int64_t n, const float *vx, const float *vy, const float *vpx, const float *vpy,
+                        const float *gx, const float *gy, const float *gpx, const float *gpy, double *norms,
+                        void *stream);
+
+/* One Nesterov step of every movable block (in place):
+ *   alpha = sqrt(norms[0] / norms[1]) when norms != NULL and both are > 0, else alpha0;
+ *   vp <- v, gp <- g;
+ *   u' = clamp(v - alpha g), v' = clamp(u' + coef (u' - u)),  u <- u', v <- v',
+ * clamp keeping the block inside the die (x in [w/2, W - w/2], likewise y), and
+ * coef = (a_k - 1) / a_{k+1} with a_{k+1} = (1 + sqrt(4 a_k^2 + 1)) / 2 from the
+ * caller.  Blocks with movable[i] == 0 keep u and v.  All arrays float32 device of
+ * n; movable uint8 or NULL; norms device (2 doubles) or NULL.  PP_EINVAL for a bad
+ * die size, alpha0 < 0, non-finite scalars or a bad pointer.  Asynchronous. */
+pp_status pp_nesterov_step(int64_t n, double W, double H, float *ux, float *uy, float *vx, float *vy, float *vpx,
+                           float *vpy, const float *gx, const float *gy, float *gpx, float *gpy, const float *w,
+                           const float *h, const uint8_t *movable, const double *norms, float alpha0,
+                           float coef, void *stream);
+
+/* Density overflow on an m x m grid: bins (device float32, m*m, written here)
+ * receives P_b = sum_i c_i area(block i ∩ b) / area(b) (exact overlap areas, block
+ * edges in 2^-40-bin fixed point; c = NULL means 1), and *out (device double)
+ * = sum_b max(P_b - target, 0), the excess in bin areas; the overflow ratio is
+ * *out * area(bin) / (movable area).  PP_EINVAL for m outside [1, 8192], a bad die
+ * size, target < 0 or a bad pointer.  Asynchronous on `stream`. */
+pp_status pp_overflow(const pp_problem *prob, int32_t m, float target, float *bins, double *out, void *stream);
+
 /* Failure-path check (no counterpart in the paper).  Launches, on `stream`, one
  * kernel whose thread waits on a shared-memory mbarrier that nothing completes,
  * through the same time-bounded wait the tensor-core kernels use between their

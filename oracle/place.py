@@ -96,8 +96,8 @@ def nesterov_step(u, v, g, w, L, alpha, a, movable=None):
     un = np.clip(v - alpha * g, lo, hi)
     an = nesterov_next_a(a)
     vn = np.clip(un + (a - 1.0) / an * (un - u), lo, hi)
-    if movable is not None:                 # fixed blocks stay where they are
+    if movable is not None:                 # fixed blocks keep both solutions: they do not move
         mov = np.asarray(movable, bool)
-        un = np.where(mov, un, v)
+        un = np.where(mov, un, u)
         vn = np.where(mov, vn, v)
     return un, vn

@@ -10,6 +10,7 @@ import ctypes
 import os
 from typing import Optional
 
+import numpy as np
 import torch
 
 from . import build_lib
@@ -38,11 +39,19 @@ class Problem(ctypes.Structure):
                 ("Mx", ctypes.c_int32), ("My", ctypes.c_int32)]
 
 
+class Netlist(ctypes.Structure):
+    _fields_ = [("n_cells", ctypes.c_int32), ("n_nets", ctypes.c_int32),
+                ("net_ptr", ctypes.c_void_p), ("net_pin", ctypes.c_void_p),
+                ("cell_ptr", ctypes.c_void_p), ("cell_net", ctypes.c_void_p)]
+
+
 _LIB = None
 EXPORTS = ("pp_workspace_size", "pp_coeffs", "pp_energy", "pp_grad", "pp_sync_status",
            "pp_last_error", "pp_version", "pp_timing_enable", "pp_timing_collect",
            "pp_grad_noalloc", "pp_phase_eval", "pp_binned_workspace_size", "pp_binned_grad",
            "pp_energy_from_coeffs", "pp_descent_step",
+           "pp_wirelength_workspace_size", "pp_wirelength", "pp_place_combine", "pp_step_norms",
+           "pp_nesterov_step", "pp_overflow",
            "pp_check_wait_timeout")
 
 
@@ -82,6 +91,21 @@ def lib() -> ctypes.CDLL:
                                       vp, vp, vp, vp, ctypes.c_float, ctypes.c_float,
                                       ctypes.c_uint64, ctypes.c_uint64, vp]
         L.pp_descent_step.restype = i
+        NL = ctypes.POINTER(Netlist)
+        f32, i64 = ctypes.c_float, ctypes.c_int64
+        L.pp_wirelength_workspace_size.argtypes = [ctypes.c_int32]
+        L.pp_wirelength_workspace_size.restype = sz
+        L.pp_wirelength.argtypes = [NL, vp, vp, f32, vp, vp, vp, vp, sz, vp]
+        L.pp_wirelength.restype = i
+        L.pp_place_combine.argtypes = [i64, vp, vp, vp, vp, vp, vp, vp, f32, vp, vp, vp]
+        L.pp_place_combine.restype = i
+        L.pp_step_norms.argtypes = [i64] + [vp] * 9 + [vp]
+        L.pp_step_norms.restype = i
+        L.pp_nesterov_step.argtypes = ([i64, ctypes.c_double, ctypes.c_double] + [vp] * 14 +
+                                       [f32, f32, vp])
+        L.pp_nesterov_step.restype = i
+        L.pp_overflow.argtypes = [P, ctypes.c_int32, f32, vp, vp, vp]
+        L.pp_overflow.restype = i
         L.pp_check_wait_timeout.argtypes = [ctypes.c_uint64, vp]
         L.pp_check_wait_timeout.restype = i
         L.pp_last_error.argtypes = []
@@ -393,3 +417,86 @@ class PoissonBlockEnergies(torch.autograd.Function):
         return (gx if ctx.needs_input_grad[0] else None,
                 gy if ctx.needs_input_grad[1] else None,
                 None, None, None, None, None, None, None, None, None)
+
+
+# ---- placement loop (Sec. IV) ---------------------------------------------------
+
+class DeviceNetlist:
+    """A netlist in both orientations on the device (int32 CSR arrays) and its
+    C-ABI view; built from host arrays (net_ptr, net_pin) once per netlist."""
+
+    def __init__(self, n_cells: int, net_ptr, net_pin, device="cuda"):
+        net_ptr = np.asarray(net_ptr, dtype=np.int64)
+        net_pin = np.asarray(net_pin, dtype=np.int64)
+        n_nets = len(net_ptr) - 1
+        # the kernels index with these arrays: check them here, once
+        if n_nets < 0 or net_ptr[0] != 0 or np.any(np.diff(net_ptr) < 0) or net_ptr[-1] != len(net_pin):
+            raise ValueError("net_ptr must start at 0, not decrease and end at len(net_pin)")
+        if len(net_pin) and (net_pin.min() < 0 or net_pin.max() >= n_cells):
+            raise ValueError("net_pin entries must lie in [0, n_cells)")
+        if n_cells > 2**31 - 1 or len(net_pin) > 2**31 - 1:
+            raise ValueError("netlist too large for int32 indices")
+        # the transpose: cell -> its nets, nets in increasing order per cell
+        net_of_pin = np.repeat(np.arange(n_nets, dtype=np.int64), np.diff(net_ptr))
+        order = np.lexsort((net_of_pin, net_pin))
+        cell_ptr = np.zeros(n_cells + 1, dtype=np.int64)
+        np.add.at(cell_ptr, net_pin + 1, 1)
+        cell_ptr = np.cumsum(cell_ptr)
+        dev = torch.device(device)
+        t = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.int32)).to(dev)
+        self.n_cells, self.n_nets = int(n_cells), int(n_nets)
+        self.net_ptr, self.net_pin = t(net_ptr), t(net_pin)
+        self.cell_ptr, self.cell_net = t(cell_ptr), t(net_of_pin[order])
+        self.c = Netlist(self.n_cells, self.n_nets, _ptr(self.net_ptr), _ptr(self.net_pin),
+                         _ptr(self.cell_ptr), _ptr(self.cell_net))
+        self.ws = torch.empty(lib().pp_wirelength_workspace_size(self.n_nets), dtype=torch.uint8,
+                              device=dev)
+
+    def degree(self) -> torch.Tensor:
+        return (self.cell_ptr[1:] - self.cell_ptr[:-1]).float()
+
+
+def wirelength(nl: DeviceNetlist, x, y, gamma: float, out=None):
+    """pp_wirelength: (gx, gy, out) with out = device double [W_LSE, HPWL]."""
+    gx = torch.empty_like(x)
+    gy = torch.empty_like(y)
+    if out is None:
+        out = torch.empty(2, dtype=torch.float64, device=x.device)
+    _check(lib().pp_wirelength(ctypes.byref(nl.c), _ptr(x), _ptr(y), float(gamma), _ptr(gx), _ptr(gy),
+                               _ptr(out), _ptr(nl.ws), nl.ws.numel(), _stream_handle(x.device)))
+    return gx, gy, out
+
+
+def place_combine(gwx, gwy, gnx, gny, cell_ptr, q, movable, lam: float):
+    gx = torch.empty_like(gwx)
+    gy = torch.empty_like(gwy)
+    _check(lib().pp_place_combine(gwx.numel(), _ptr(gwx), _ptr(gwy), _ptr(gnx), _ptr(gny), _ptr(cell_ptr),
+                                  _ptr(q), _ptr(movable), float(lam), _ptr(gx), _ptr(gy),
+                                  _stream_handle(gwx.device)))
+    return gx, gy
+
+
+def step_norms(vx, vy, vpx, vpy, gx, gy, gpx, gpy, norms):
+    _check(lib().pp_step_norms(vx.numel(), _ptr(vx), _ptr(vy), _ptr(vpx), _ptr(vpy), _ptr(gx), _ptr(gy),
+                               _ptr(gpx), _ptr(gpy), _ptr(norms), _stream_handle(vx.device)))
+    return norms
+
+
+def nesterov_step(W, H, ux, uy, vx, vy, vpx, vpy, gx, gy, gpx, gpy, w, h, movable, norms, alpha0, coef):
+    """pp_nesterov_step, in place on u, v, vp, gp."""
+    _check(lib().pp_nesterov_step(ux.numel(), float(W), float(H), _ptr(ux), _ptr(uy), _ptr(vx), _ptr(vy),
+                                  _ptr(vpx), _ptr(vpy), _ptr(gx), _ptr(gy), _ptr(gpx), _ptr(gpy), _ptr(w),
+                                  _ptr(h), _ptr(movable), _ptr(norms), float(alpha0), float(coef),
+                                  _stream_handle(ux.device)))
+
+
+def overflow(x, y, w, h, W, H, m: int, target: float = 1.0, bins=None, out=None):
+    """pp_overflow: (excess in bin areas as a device double, bin density m x m)."""
+    if bins is None:
+        bins = torch.empty((m, m), dtype=torch.float32, device=x.device)
+    if out is None:
+        out = torch.empty(1, dtype=torch.float64, device=x.device)
+    prob = make_problem(x, y, w, h, None, W, H, 1, 1)
+    _check(lib().pp_overflow(ctypes.byref(prob), int(m), float(target), _ptr(bins), _ptr(out),
+                             _stream_handle(x.device)))
+    return out, bins

@@ -544,6 +544,158 @@ pp_status pp_descent_step(double W, double H, int64_t n, float *x, float *y, con
     return PP_OK;
 }
 
+// ---- placement loop (Sec. IV) -------------------------------------------------
+namespace {
+pp_status check_netlist(const pp_netlist *nl, int dev) {
+    if (!nl) return fail(PP_EINVAL, "netlist is NULL");
+    if (nl->n_cells < 0 || nl->n_nets < 0) return fail(PP_EINVAL, "negative netlist sizes");
+    pp_status st;
+    if (nl->n_nets > 0) {
+        if ((st = check_dev_ptr(nl->net_ptr, dev, "net_ptr")) != PP_OK) return st;
+        if ((st = check_dev_ptr(nl->net_pin, dev, "net_pin")) != PP_OK) return st;
+    }
+    if (nl->n_cells > 0) {
+        if ((st = check_dev_ptr(nl->cell_ptr, dev, "cell_ptr")) != PP_OK) return st;
+        if ((st = check_dev_ptr(nl->cell_net, dev, "cell_net")) != PP_OK) return st;
+    }
+    return PP_OK;
+}
+pp_status check_arrays(int dev, int count, const void *const *ptrs, const char *const *names) {
+    pp_status st;
+    for (int i = 0; i < count; ++i)
+        if ((st = check_dev_ptr(ptrs[i], dev, names[i])) != PP_OK) return st;
+    return PP_OK;
+}
+}  // namespace
+
+size_t pp_wirelength_workspace_size(int32_t n_nets) {
+    return n_nets <= 0 ? 256 : ((size_t)n_nets * 32 + 255) & ~(size_t)255;
+}
+
+pp_status pp_wirelength(const pp_netlist *nl, const float *x, const float *y, float gamma, float *gx, float *gy,
+                        double *out, void *ws, size_t ws_bytes, void *stream) {
+    int dev, sm, ccm;
+    unsigned *status;
+    pp_status st = device_info(&dev, &sm, &status, &ccm);
+    if (st != PP_OK) return st;
+    if ((st = check_netlist(nl, dev)) != PP_OK) return st;
+    if (!(std::isfinite(gamma) && gamma > 0.f)) return fail(PP_EINVAL, "gamma must be finite and > 0");
+    const size_t need = pp_wirelength_workspace_size(nl->n_nets);
+    if (!ws || ws_bytes < need)
+        return fail(PP_ENOMEM_WS, "workspace of %zu bytes needed, %zu given", need, ws ? ws_bytes : (size_t)0);
+    if (((uintptr_t)ws & 255) != 0) return fail(PP_EINVAL, "workspace must be 256-byte aligned");
+    if ((st = check_dev_ptr(ws, dev, "ws")) != PP_OK) return st;
+    if ((st = check_dev_ptr(out, dev, "out")) != PP_OK) return st;
+    if (((uintptr_t)out & 7) != 0) return fail(PP_EINVAL, "out is not 8-byte aligned");
+    if (nl->n_cells > 0) {
+        const void *ptrs[4] = {x, y, gx, gy};
+        const char *names[4] = {"x", "y", "gx", "gy"};
+        if ((st = check_arrays(dev, 4, ptrs, names)) != PP_OK) return st;
+    }
+    cudaError_t e = launch_wirelength(nl->n_nets, nl->n_cells, nl->net_ptr, nl->net_pin, nl->cell_ptr,
+                                      nl->cell_net, x, y, gamma, (float *)ws, gx, gy, out, sm,
+                                      (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "wirelength launch");
+    return PP_OK;
+}
+
+pp_status pp_place_combine(int64_t n, const float *gwx, const float *gwy, const float *gnx, const float *gny,
+                           const int32_t *cell_ptr, const float *q, const uint8_t *movable, float lambda,
+                           float *gx, float *gy, void *stream) {
+    int dev, sm, ccm;
+    unsigned *status;
+    pp_status st = device_info(&dev, &sm, &status, &ccm);
+    if (st != PP_OK) return st;
+    if (n < 0 || n > INT64_C(0x7FFFFFFF)) return fail(PP_EINVAL, "n=%lld out of range", (long long)n);
+    if (!(std::isfinite(lambda) && lambda >= 0.f)) return fail(PP_EINVAL, "lambda must be finite and >= 0");
+    if (n == 0) return PP_OK;
+    const void *ptrs[7] = {gwx, gwy, gnx, gny, q, gx, gy};
+    const char *names[7] = {"gwx", "gwy", "gnx", "gny", "q", "gx", "gy"};
+    if ((st = check_arrays(dev, 7, ptrs, names)) != PP_OK) return st;
+    if (cell_ptr && (st = check_dev_ptr(cell_ptr, dev, "cell_ptr")) != PP_OK) return st;
+    if (movable && (st = check_dev_ptr(movable, dev, "movable")) != PP_OK) return st;
+    cudaError_t e = launch_combine(n, gwx, gwy, gnx, gny, cell_ptr, q, movable, lambda, gx, gy,
+                                   (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "combine launch");
+    return PP_OK;
+}
+
+pp_status pp_step_norms(int64_t n, const float *vx, const float *vy, const float *vpx, const float *vpy,
+                        const float *gx, const float *gy, const float *gpx, const float *gpy, double *norms,
+                        void *stream) {
+    int dev, sm, ccm;
+    unsigned *status;
+    pp_status st = device_info(&dev, &sm, &status, &ccm);
+    if (st != PP_OK) return st;
+    if (n < 0 || n > INT64_C(0x7FFFFFFF)) return fail(PP_EINVAL, "n=%lld out of range", (long long)n);
+    if ((st = check_dev_ptr(norms, dev, "norms")) != PP_OK) return st;
+    if (((uintptr_t)norms & 7) != 0) return fail(PP_EINVAL, "norms is not 8-byte aligned");
+    if (n > 0) {
+        const void *ptrs[8] = {vx, vy, vpx, vpy, gx, gy, gpx, gpy};
+        const char *names[8] = {"vx", "vy", "vpx", "vpy", "gx", "gy", "gpx", "gpy"};
+        if ((st = check_arrays(dev, 8, ptrs, names)) != PP_OK) return st;
+    }
+    cudaError_t e = launch_step_norms(n, vx, vy, vpx, vpy, gx, gy, gpx, gpy, norms, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "step norms launch");
+    return PP_OK;
+}
+
+pp_status pp_nesterov_step(int64_t n, double W, double H, float *ux, float *uy, float *vx, float *vy, float *vpx,
+                           float *vpy, const float *gx, const float *gy, float *gpx, float *gpy, const float *w,
+                           const float *h, const uint8_t *movable, const double *norms, float alpha0,
+                           float coef, void *stream) {
+    int dev, sm, ccm;
+    unsigned *status;
+    pp_status st = device_info(&dev, &sm, &status, &ccm);
+    if (st != PP_OK) return st;
+    if (!(std::isfinite(W) && std::isfinite(H) && W >= 1e-300 && W <= 1e300 && H >= 1e-300 && H <= 1e300))
+        return fail(PP_EINVAL, "die size W=%g H=%g must be finite and in [1e-300, 1e300]", W, H);
+    if (n < 0 || n > INT64_C(0x7FFFFFFF)) return fail(PP_EINVAL, "n=%lld out of range", (long long)n);
+    if (!(std::isfinite(alpha0) && alpha0 >= 0.f && std::isfinite(coef)))
+        return fail(PP_EINVAL, "alpha0 must be finite and >= 0, coef finite");
+    if (n == 0) return PP_OK;
+    const void *ptrs[12] = {ux, uy, vx, vy, vpx, vpy, gx, gy, gpx, gpy, w, h};
+    const char *names[12] = {"ux", "uy", "vx", "vy", "vpx", "vpy", "gx", "gy", "gpx", "gpy", "w", "h"};
+    if ((st = check_arrays(dev, 12, ptrs, names)) != PP_OK) return st;
+    if (movable && (st = check_dev_ptr(movable, dev, "movable")) != PP_OK) return st;
+    if (norms && (st = check_dev_ptr(norms, dev, "norms")) != PP_OK) return st;
+    cudaError_t e = launch_nesterov(n, ux, uy, vx, vy, vpx, vpy, gx, gy, gpx, gpy, w, h, (float)W, (float)H,
+                                    movable, norms, alpha0, coef, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "Nesterov step launch");
+    return PP_OK;
+}
+
+pp_status pp_overflow(const pp_problem *prob, int32_t m, float target, float *bins, double *out, void *stream) {
+    int dev, sm, ccm;
+    unsigned *status;
+    pp_status st = device_info(&dev, &sm, &status, &ccm);
+    if (st != PP_OK) return st;
+    if (!prob) return fail(PP_EINVAL, "problem is NULL");
+    if (!(std::isfinite(prob->W) && std::isfinite(prob->H) && prob->W >= 1e-300 && prob->W <= 1e300 &&
+          prob->H >= 1e-300 && prob->H <= 1e300))
+        return fail(PP_EINVAL, "die size must be finite and in [1e-300, 1e300]");
+    if (prob->n < 0 || prob->n > INT64_C(0x7FFFFFFF)) return fail(PP_EINVAL, "n out of range");
+    if (m < 1 || m > 8192) return fail(PP_EINVAL, "bins m=%d must be in [1, 8192]", m);
+    if (!(std::isfinite(target) && target >= 0.f)) return fail(PP_EINVAL, "target must be finite and >= 0");
+    if ((st = check_dev_ptr(bins, dev, "bins")) != PP_OK) return st;
+    if ((st = check_dev_ptr(out, dev, "out")) != PP_OK) return st;
+    if (((uintptr_t)out & 7) != 0) return fail(PP_EINVAL, "out is not 8-byte aligned");
+    if (prob->n > 0) {
+        const void *ptrs[4] = {prob->x, prob->y, prob->w, prob->h};
+        const char *names[4] = {"x", "y", "w", "h"};
+        if ((st = check_arrays(dev, 4, ptrs, names)) != PP_OK) return st;
+        if (prob->c && (st = check_dev_ptr(prob->c, dev, "c")) != PP_OK) return st;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaMemsetAsync(bins, 0, (size_t)m * m * sizeof(float), s);
+    if (e == cudaSuccess)
+        e = launch_bin_density(prob->x, prob->y, prob->w, prob->h, prob->c, (int)prob->n, m, prob->W, prob->H,
+                               bins, sm, s);
+    if (e == cudaSuccess) e = launch_overflow(m, bins, target, out, s);
+    if (e != cudaSuccess) return cuda_fail(e, "overflow launch");
+    return PP_OK;
+}
+
 pp_status pp_check_wait_timeout(uint64_t limit_ns, void *stream) {
     int dev, sm, ccm;
     unsigned *status;

@@ -180,6 +180,13 @@ BinnedLayout binned_layout(int m, int Mx, int My) {
     return L;
 }
 
+cudaError_t launch_bin_density(const float *x, const float *y, const float *w, const float *h, const float *c,
+                               int n, int m, double W, double H, float *P, int sm_count, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    bin_density_kernel<<<8 * sm_count, 256, 0, st>>>(x, y, w, h, c, n, m, m / W, m / H, P);
+    return cudaGetLastError();
+}
+
 cudaError_t run_binned(const Launch &Lc, int dev, int m, bool tf32, unsigned char *ws, float *a_out, float *e_block,
                        float *gx, float *gy, double *e_total, const char **what) {
     const int Mx = Lc.Mx, My = Lc.My, n = Lc.n;

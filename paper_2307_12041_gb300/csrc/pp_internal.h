@@ -66,6 +66,9 @@ BinnedLayout binned_layout(int m, int Mx, int My);
 // `what` names the failing step on error (a CUDA launch or a cuBLAS call)
 cudaError_t run_binned(const Launch &L, int dev, int m, bool tf32, unsigned char *ws, float *a_out,
                        float *e_block, float *gx, float *gy, double *e_total, const char **what);
+// P[l m + j] += sum_i c_i area(block i ∩ bin lj) / area(bin) on an m x m grid (P zeroed by the caller)
+cudaError_t launch_bin_density(const float *x, const float *y, const float *w, const float *h, const float *c,
+                               int n, int m, double W, double H, float *P, int sm_count, cudaStream_t st);
 // E = 1/2 sum_uv a_uv^2 / G_uv (FP64) from coefficients a (Mx x My, u-major), added to *e_total
 cudaError_t launch_energy_from_coeffs(const float *a, int Mx, int My, double W, double H, double *e_total,
                                       cudaStream_t stream);
@@ -77,6 +80,24 @@ cudaError_t launch_phase_eval(const float *x, double invL, const int32_t *m, int
                               int evaluator, float *out, cudaStream_t stream);
 // one CTA whose thread waits (bounded) on an mbarrier nothing completes
 cudaError_t launch_wait_probe(uint64_t limit_ns, unsigned *status, cudaStream_t stream);
+
+// pp_place.cu: the placement loop's kernels (log-sum-exp wirelength, gradient
+// combination, Nesterov step, overflow)
+cudaError_t launch_wirelength(int n_nets, int n_cells, const int32_t *net_ptr, const int32_t *net_pin,
+                              const int32_t *cell_ptr, const int32_t *cell_net, const float *x,
+                              const float *y, float gamma, float *stats, float *gx, float *gy,
+                              double *out, int sm_count, cudaStream_t st);
+cudaError_t launch_combine(int64_t n, const float *gwx, const float *gwy, const float *gnx, const float *gny,
+                           const int32_t *cell_ptr, const float *q, const uint8_t *movable, float lambda,
+                           float *gx, float *gy, cudaStream_t st);
+cudaError_t launch_nesterov(int64_t n, float *ux, float *uy, float *vx, float *vy, float *vpx, float *vpy,
+                            const float *gx, const float *gy, float *gpx, float *gpy, const float *w,
+                            const float *h, float W, float H, const uint8_t *movable, const double *norms,
+                            float alpha0, float coef, cudaStream_t st);
+cudaError_t launch_step_norms(int64_t n, const float *vx, const float *vy, const float *vpx, const float *vpy,
+                              const float *gx, const float *gy, const float *gpx, const float *gpy,
+                              double *norms, cudaStream_t st);
+cudaError_t launch_overflow(int m, const float *P, float target, double *out, cudaStream_t st);
 
 // pp_simt.cu
 cudaError_t launch_prep(const Launch &L, bool zero_S, double *e_total);

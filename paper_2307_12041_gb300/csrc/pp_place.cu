@@ -1,0 +1,227 @@
+// Kernels of the placement loop around the density energy (Sec. IV: minimise
+// f = W_LSE + lambda N with one Nesterov step per iteration, a penalty update and an
+// overflow stop, "as in ePlace").
+//
+//   lse_net_kernel      per net and axis: max, min and the shifted sums
+//                       sum exp((x - max) / gamma), sum exp((min - x) / gamma); the net's
+//                       W_LSE and HPWL into a per-CTA sum
+//   lse_cell_kernel     per cell: dW/dx = sum over its nets of softmax(x / gamma) -
+//                       softmax(-x / gamma) at the cell (a gather over the cell's nets,
+//                       no atomics: the result does not depend on thread timing)
+//   combine_kernel      g = (dW + lambda dN) / max(1, |nets of i| + lambda q_i)
+//                       (ePlace's diagonal preconditioner; fixed blocks get 0)
+//   step_norms_kernel   |v - v_prev|^2 and |g - g_prev|^2 (for the step length)
+//   nesterov_kernel     u' = clamp(v - alpha g), v' = clamp(u' + coef (u' - u)),
+//                       alpha = |v - v_prev| / |g - g_prev| read on the device
+//   overflow_kernel     sum_b max(P_b - rho_t, 0) of a bin density P
+#include <cmath>
+#include <cstdint>
+
+#include "pp_internal.h"
+
+namespace pp {
+namespace {
+
+// Sum of one double per thread over the CTA, added to *dst (one atomic per CTA).
+__device__ __forceinline__ void block_add(double v, double *dst) {
+    __shared__ double part[32];
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += part[w];
+        atomicAdd(dst, t);
+    }
+    __syncthreads();
+}
+
+// stats[e] = {max x, min x, 1 / sum exp((x - max)/g), 1 / sum exp((min - x)/g), same for y}
+__global__ void lse_net_kernel(int n_nets, const int32_t *__restrict__ net_ptr,
+                               const int32_t *__restrict__ net_pin, const float *__restrict__ x,
+                               const float *__restrict__ y, float gamma, float inv_gamma,
+                               float4 *__restrict__ stats, double *__restrict__ out) {
+    double wl = 0.0, hp = 0.0;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n_nets; e += gridDim.x * blockDim.x) {
+        const int p0 = net_ptr[e], p1 = net_ptr[e + 1];
+        float hx = -INFINITY, lx = INFINITY, hy = -INFINITY, ly = INFINITY;
+        for (int p = p0; p < p1; ++p) {
+            const int i = net_pin[p];
+            const float xi = x[i], yi = y[i];
+            hx = fmaxf(hx, xi);
+            lx = fminf(lx, xi);
+            hy = fmaxf(hy, yi);
+            ly = fminf(ly, yi);
+        }
+        float spx = 0.f, snx = 0.f, spy = 0.f, sny = 0.f;
+        for (int p = p0; p < p1; ++p) {
+            const int i = net_pin[p];
+            const float xi = x[i], yi = y[i];
+            spx += expf((xi - hx) * inv_gamma);
+            snx += expf((lx - xi) * inv_gamma);
+            spy += expf((yi - hy) * inv_gamma);
+            sny += expf((ly - yi) * inv_gamma);
+        }
+        if (p1 - p0 >= 2) {
+            stats[2 * e] = make_float4(hx, lx, 1.f / spx, 1.f / snx);
+            stats[2 * e + 1] = make_float4(hy, ly, 1.f / spy, 1.f / sny);
+            hp += (double)(hx - lx) + (double)(hy - ly);
+            wl += (double)(hx - lx) + (double)(hy - ly) +
+                  (double)gamma * ((double)logf(spx) + logf(snx) + logf(spy) + logf(sny));
+        } else {       // a net of fewer than two pins adds nothing: both exponentials
+                       // of its gradient terms are exp(-inf) = 0 (no inf * 0)
+            stats[2 * e] = make_float4(INFINITY, -INFINITY, 0.f, 0.f);
+            stats[2 * e + 1] = make_float4(INFINITY, -INFINITY, 0.f, 0.f);
+        }
+    }
+    block_add(wl, out);
+    block_add(hp, out + 1);
+}
+
+__global__ void lse_cell_kernel(int n_cells, const int32_t *__restrict__ cell_ptr,
+                                const int32_t *__restrict__ cell_net, const float *__restrict__ x,
+                                const float *__restrict__ y, float inv_gamma, const float4 *__restrict__ stats,
+                                float *__restrict__ gx, float *__restrict__ gy) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_cells; i += gridDim.x * blockDim.x) {
+        const float xi = x[i], yi = y[i];
+        float ax = 0.f, ay = 0.f;
+        for (int k = cell_ptr[i]; k < cell_ptr[i + 1]; ++k) {
+            const int e = cell_net[k];
+            const float4 sx = stats[2 * e], sy = stats[2 * e + 1];
+            ax += expf((xi - sx.x) * inv_gamma) * sx.z - expf((sx.y - xi) * inv_gamma) * sx.w;
+            ay += expf((yi - sy.x) * inv_gamma) * sy.z - expf((sy.y - yi) * inv_gamma) * sy.w;
+        }
+        gx[i] = ax;
+        gy[i] = ay;
+    }
+}
+
+__global__ void combine_kernel(int64_t n, const float *__restrict__ gwx, const float *__restrict__ gwy,
+                               const float *__restrict__ gnx, const float *__restrict__ gny,
+                               const int32_t *__restrict__ cell_ptr, const float *__restrict__ q,
+                               const uint8_t *__restrict__ movable, float lambda, float *__restrict__ gx,
+                               float *__restrict__ gy) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        if (movable && !movable[i]) {
+            gx[i] = gy[i] = 0.f;
+            continue;
+        }
+        const float deg = cell_ptr ? (float)(cell_ptr[i + 1] - cell_ptr[i]) : 0.f;
+        const float inv = 1.f / fmaxf(1.f, deg + lambda * q[i]);
+        gx[i] = (gwx[i] + lambda * gnx[i]) * inv;
+        gy[i] = (gwy[i] + lambda * gny[i]) * inv;
+    }
+}
+
+__global__ void step_norms_kernel(int64_t n, const float *__restrict__ vx, const float *__restrict__ vy,
+                                  const float *__restrict__ vpx, const float *__restrict__ vpy,
+                                  const float *__restrict__ gx, const float *__restrict__ gy,
+                                  const float *__restrict__ gpx, const float *__restrict__ gpy,
+                                  double *__restrict__ norms) {
+    double dv = 0.0, dg = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float a = vx[i] - vpx[i], b = vy[i] - vpy[i], c = gx[i] - gpx[i], d = gy[i] - gpy[i];
+        dv += (double)a * a + (double)b * b;
+        dg += (double)c * c + (double)d * d;
+    }
+    block_add(dv, norms);
+    block_add(dg, norms + 1);
+}
+
+__global__ void nesterov_kernel(int64_t n, float *__restrict__ ux, float *__restrict__ uy, float *__restrict__ vx,
+                                float *__restrict__ vy, float *__restrict__ vpx, float *__restrict__ vpy,
+                                const float *__restrict__ gx, const float *__restrict__ gy,
+                                float *__restrict__ gpx, float *__restrict__ gpy, const float *__restrict__ w,
+                                const float *__restrict__ h, float W, float H,
+                                const uint8_t *__restrict__ movable, const double *__restrict__ norms,
+                                float alpha0, float coef) {
+    // step length: |v - v_prev| / |g - g_prev| from the previous iteration, else alpha0
+    float alpha = alpha0;
+    if (norms && norms[1] > 0.0 && norms[0] > 0.0) alpha = (float)sqrt(norms[0] / norms[1]);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float vxi = vx[i], vyi = vy[i], gxi = gx[i], gyi = gy[i];
+        vpx[i] = vxi;
+        vpy[i] = vyi;
+        gpx[i] = gxi;
+        gpy[i] = gyi;
+        if (movable && !movable[i]) continue;
+        const float lx = 0.5f * w[i], hx = W - 0.5f * w[i], ly = 0.5f * h[i], hy = H - 0.5f * h[i];
+        const float nux = fminf(fmaxf(vxi - alpha * gxi, lx), hx);
+        const float nuy = fminf(fmaxf(vyi - alpha * gyi, ly), hy);
+        const float nvx = fminf(fmaxf(nux + coef * (nux - ux[i]), lx), hx);
+        const float nvy = fminf(fmaxf(nuy + coef * (nuy - uy[i]), ly), hy);
+        ux[i] = nux;
+        uy[i] = nuy;
+        vx[i] = nvx;
+        vy[i] = nvy;
+    }
+}
+
+__global__ void overflow_kernel(int64_t cells, const float *__restrict__ P, float target, double *__restrict__ out) {
+    double s = 0.0;
+    for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < cells; b += (int64_t)gridDim.x * blockDim.x)
+        s += (double)fmaxf(P[b] - target, 0.f);
+    block_add(s, out);
+}
+
+int grid_for(int64_t n, int cap) {
+    int64_t b = (n + 255) / 256;
+    if (b < 1) b = 1;
+    return (int)(b < cap ? b : cap);
+}
+
+}  // namespace
+
+cudaError_t launch_wirelength(int n_nets, int n_cells, const int32_t *net_ptr, const int32_t *net_pin,
+                              const int32_t *cell_ptr, const int32_t *cell_net, const float *x,
+                              const float *y, float gamma, float *stats, float *gx, float *gy,
+                              double *out, int sm_count, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(out, 0, 2 * sizeof(double), st);
+    if (e != cudaSuccess) return e;
+    if (n_nets > 0)
+        lse_net_kernel<<<grid_for(n_nets, 16 * sm_count), 256, 0, st>>>(
+            n_nets, net_ptr, net_pin, x, y, gamma, 1.f / gamma, reinterpret_cast<float4 *>(stats), out);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (n_cells > 0)
+        lse_cell_kernel<<<grid_for(n_cells, 16 * sm_count), 256, 0, st>>>(
+            n_cells, cell_ptr, cell_net, x, y, 1.f / gamma, reinterpret_cast<const float4 *>(stats), gx, gy);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_combine(int64_t n, const float *gwx, const float *gwy, const float *gnx, const float *gny,
+                           const int32_t *cell_ptr, const float *q, const uint8_t *movable, float lambda,
+                           float *gx, float *gy, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    combine_kernel<<<grid_for(n, 4096), 256, 0, st>>>(n, gwx, gwy, gnx, gny, cell_ptr, q, movable, lambda, gx, gy);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_step_norms(int64_t n, const float *vx, const float *vy, const float *vpx, const float *vpy,
+                              const float *gx, const float *gy, const float *gpx, const float *gpy,
+                              double *norms, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(norms, 0, 2 * sizeof(double), st);
+    if (e != cudaSuccess || n <= 0) return e;
+    step_norms_kernel<<<grid_for(n, 1024), 256, 0, st>>>(n, vx, vy, vpx, vpy, gx, gy, gpx, gpy, norms);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_nesterov(int64_t n, float *ux, float *uy, float *vx, float *vy, float *vpx, float *vpy,
+                            const float *gx, const float *gy, float *gpx, float *gpy, const float *w,
+                            const float *h, float W, float H, const uint8_t *movable, const double *norms,
+                            float alpha0, float coef, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    nesterov_kernel<<<grid_for(n, 4096), 256, 0, st>>>(n, ux, uy, vx, vy, vpx, vpy, gx, gy, gpx, gpy, w, h, W, H,
+                                                       movable, norms, alpha0, coef);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_overflow(int m, const float *P, float target, double *out, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(out, 0, sizeof(double), st);
+    if (e != cudaSuccess) return e;
+    const int64_t cells = (int64_t)m * m;
+    overflow_kernel<<<grid_for(cells, 1024), 256, 0, st>>>(cells, P, target, out);
+    return cudaGetLastError();
+}
+
+}  // namespace pp

@@ -159,3 +159,70 @@ def workload(index: int, n: int | None = None) -> Placement:
         p.name = spec["name"]
     return p
 
+
+
+# ---- placement-loop inputs (Sec. IV) --------------------------------------------
+# The ISPD netlists are not available; the stand-in is a netlist with the usual
+# character: about one net per cell, mostly two- and three-pin nets with a tail up
+# to 16 pins, and locality (a net's pins lie close together in a hidden target
+# layout), on standard cells of one row height at a set utilisation, started from
+# a dense cluster at the die centre so that the loop has to spread them.
+
+NET_DEGREES = np.array([2, 3, 4, 5, 6, 8, 12, 16])
+NET_DEGREE_P = np.array([0.55, 0.18, 0.1, 0.06, 0.04, 0.03, 0.02, 0.02])
+
+
+def placement_cells(n: int, M: int, seed: int, util: float = 0.7, W: float = 1.0, H: float = 1.0,
+                    start_sigma: float = 0.05) -> Placement:
+    """n standard cells (h one row, w lognormal with sigma 0.5) scaled so that their
+    total area is util * W * H; centres normal around the die centre (std
+    start_sigma of the die), clamped.  M modes per axis."""
+    r_w, r_x, r_y = _streams(seed, 3)
+    row = 0.001 * H
+    w = lognormal_with_mean(r_w, 0.002 * W, 0.5, n)
+    h = np.full(n, row)
+    w *= util * W * H / float(np.sum(w * h))
+    w = np.minimum(w, W)
+    x = _clamp_centres(0.5 * W + r_x.normal(0.0, start_sigma, n) * W, w, W)
+    y = _clamp_centres(0.5 * H + r_y.normal(0.0, start_sigma, n) * H, h, H)
+    return Placement(W, H, x.astype(np.float32), y.astype(np.float32), w.astype(np.float32),
+                     h.astype(np.float32), None, M, M, name=f"place-{n}-{M}x{M}",
+                     meta={"util": util, "start_sigma": start_sigma})
+
+
+def netlist(n_cells: int, seed: int, nets_per_cell: float = 1.0, window: int = 64):
+    """(net_ptr, net_pin) int64: net degrees from NET_DEGREES / NET_DEGREE_P; a net's
+    pins are distinct cells within `window` positions of a random start in a hidden
+    order (the cells sorted along a space-filling curve of a random target layout),
+    so that nets are local.  Every cell gets at least one net (two-pin nets to a
+    neighbour in the order are added for cells left out)."""
+    r_ord, r_deg, r_start, r_pick = _streams(seed, 4)
+    # hidden target layout: random points in a 1024 x 1024 grid, ordered by a Morton curve
+    g = r_ord.integers(0, 1024, (n_cells, 2))
+    def spread(v):
+        v = v.astype(np.int64)
+        out = np.zeros_like(v)
+        for b in range(10):
+            out |= ((v >> b) & 1) << (2 * b)
+        return out
+    order = np.argsort(spread(g[:, 0]) | (spread(g[:, 1]) << 1), kind="stable")
+    n_nets = max(1, int(round(nets_per_cell * n_cells)))
+    deg = r_deg.choice(NET_DEGREES, n_nets, p=NET_DEGREE_P)
+    deg = np.minimum(deg, max(2, n_cells))
+    start = r_start.integers(0, max(1, n_cells - window), n_nets)
+    pins = []
+    for d, s0 in zip(deg, start):
+        span = min(window, n_cells)
+        pick = r_pick.choice(span, d, replace=False)
+        pins.append(order[np.minimum(s0 + pick, n_cells - 1)])
+    used = np.zeros(n_cells, bool)
+    for pp in pins:
+        used[pp] = True
+    rank = np.empty(n_cells, np.int64)
+    rank[order] = np.arange(n_cells)
+    for c in np.flatnonzero(~used):                 # a two-pin net to the next cell in the order
+        k = rank[c]
+        other = order[k + 1] if k + 1 < n_cells else order[k - 1]
+        pins.append(np.array([c, other]))
+    ptr = np.concatenate([[0], np.cumsum([len(pp) for pp in pins])]).astype(np.int64)
+    return ptr, np.concatenate(pins).astype(np.int64)

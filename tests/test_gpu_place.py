@@ -1,0 +1,163 @@
+"""The placement loop's kernels (Sec. IV) through the C ABI against the FP64
+oracle (oracle/place.py): log-sum-exp wirelength and its gradient, the overflow
+ratio, the preconditioned combination, the step norms and the Nesterov step; then
+the whole loop on a scaled-down synthetic netlist, checked against the oracle's
+wirelength and density gradients at the GPU's own positions at checkpoints."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import place as OP
+from oracle import series as OS
+from paper_2307_12041_gb300 import place, synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def small_netlist():
+    n = 20_000
+    p = synth.placement_cells(n, 128, 11, start_sigma=0.2)
+    ptr, pins = synth.netlist(n, 12)
+    return p, ptr, pins
+
+
+@pytest.mark.parametrize("gamma", [0.02, 1e-3])
+def test_wirelength_matches_oracle(pp, small_netlist, gamma):
+    p, ptr, pins = small_netlist
+    nl = pp.binding.DeviceNetlist(p.n, ptr, pins)
+    x, y = torch.from_numpy(p.x).cuda(), torch.from_numpy(p.y).cuda()
+    gx, gy, out = pp.binding.wirelength(nl, x, y, gamma)
+    W, hp, rgx, rgy = OP.lse_wirelength(p.x, p.y, ptr, pins, gamma)
+    o = out.cpu().numpy()
+    assert abs(o[0] - W) <= 2e-6 * W, (o[0], W)
+    assert abs(o[1] - hp) <= 1e-6 * hp, (o[1], hp)
+    g = np.concatenate([gx.double().cpu().numpy(), gy.double().cpu().numpy()])
+    r = np.concatenate([rgx, rgy])
+    assert np.abs(g - r).max() <= 2e-5 * np.abs(r).max(), np.abs(g - r).max()
+
+
+def test_wirelength_edge_cases(pp):
+    # one-pin and empty nets add nothing; a two-pin net gives +-tanh(d / 2 gamma)
+    ptr = np.array([0, 1, 1, 3])
+    pins = np.array([0, 1, 2])
+    nl = pp.binding.DeviceNetlist(3, ptr, pins)
+    x = torch.tensor([0.5, 0.2, 0.6], device="cuda")
+    y = torch.tensor([0.5, 0.3, 0.3], device="cuda")
+    gamma = 0.05
+    gx, gy, out = pp.binding.wirelength(nl, x, y, gamma)
+    d = 0.4
+    t = math.tanh(d / (2 * gamma))
+    assert abs(float(gx[0])) == 0.0 and abs(float(gx[2]) - t) <= 1e-6 and abs(float(gx[1]) + t) <= 1e-6
+    assert abs(float(gy[1])) <= 1e-7 and abs(float(gy[2])) <= 1e-7
+    W = d + 2 * gamma * math.log1p(math.exp(-d / gamma)) + 2 * gamma * math.log(2.0)
+    o = out.cpu().numpy()
+    assert abs(o[0] - W) <= 1e-6 and abs(o[1] - d) <= 1e-6
+
+
+def test_overflow_matches_oracle(pp):
+    g = np.random.default_rng(21)
+    n, m = 3000, 64
+    w = np.where(g.random(n) < 0.05, g.uniform(0.02, 0.08, n), g.uniform(0.001, 0.01, n)).astype(np.float32)
+    h = np.where(g.random(n) < 0.05, g.uniform(0.02, 0.08, n), np.full(n, 0.004)).astype(np.float32)
+    x = (w / 2 + g.random(n) * (1 - w)).astype(np.float32)
+    y = (0.5 + g.normal(0, 0.1, n)).clip(h / 2, 1 - h / 2).astype(np.float32)
+    t = lambda a: torch.from_numpy(a).cuda()
+    for target in (1.0, 0.7):
+        out, bins = pp.binding.overflow(t(x), t(y), t(w), t(h), 1.0, 1.0, m, target)
+        tau = float(out.item()) * (1.0 / m) ** 2 / float(np.sum(w.astype(np.float64) * h))
+        ref, D = OP.overflow(x, y, w, h, None, 1.0, 1.0, m, target)
+        assert abs(tau - ref) <= 2e-5 * max(ref, 1e-3), (target, tau, ref)
+        assert np.abs(bins.double().cpu().numpy() * (1.0 / m) ** 2 - D).max() <= 1e-5 * D.max()
+
+
+def test_combine_norms_and_nesterov_match_oracle(pp):
+    g = np.random.default_rng(5)
+    n = 50_000
+    f32 = lambda a: torch.from_numpy(np.asarray(a, np.float32)).cuda()
+    gwx, gwy, gnx, gny = (g.normal(size=n) for _ in range(4))
+    q = g.uniform(1e-6, 5e-6, n)
+    deg = g.integers(0, 6, n)
+    cell_ptr = np.concatenate([[0], np.cumsum(deg)]).astype(np.int32)
+    mov = (g.random(n) < 0.95).astype(np.uint8)
+    lam = 3.0e5
+    gx, gy = pp.binding.place_combine(f32(gwx), f32(gwy), f32(gnx), f32(gny),
+                                      torch.from_numpy(cell_ptr).cuda(), f32(q),
+                                      torch.from_numpy(mov).cuda(), lam)
+    pre = np.maximum(1.0, deg + lam * q)
+    rx = np.where(mov > 0, (gwx + lam * gnx) / pre, 0.0)
+    assert np.abs(gx.double().cpu().numpy() - rx).max() <= 1e-5 * np.abs(rx).max()
+    # norms and one Nesterov step from identical inputs
+    w = g.uniform(0.001, 0.01, n)
+    h = np.full(n, 0.001)
+    ux, vx, vpx = (g.uniform(0.1, 0.9, n) for _ in range(3))
+    uy, vy, vpy = (g.uniform(0.1, 0.9, n) for _ in range(3))
+    gpx, gpy = g.normal(size=n), g.normal(size=n)
+    T = {k: f32(v) for k, v in dict(ux=ux, uy=uy, vx=vx, vy=vy, vpx=vpx, vpy=vpy, gpx=gpx, gpy=gpy,
+                                      w=w, h=h).items()}
+    norms = torch.zeros(2, dtype=torch.float64, device="cuda")
+    pp.binding.step_norms(T["vx"], T["vy"], T["vpx"], T["vpy"], gx, gy, T["gpx"], T["gpy"], norms)
+    gxh, gyh = gx.double().cpu().numpy(), gy.double().cpu().numpy()
+    f = lambda a: np.asarray(a, np.float32).astype(np.float64)
+    dv = np.sum((f(vx) - f(vpx)) ** 2 + (f(vy) - f(vpy)) ** 2)
+    dg = np.sum((gxh - f(gpx)) ** 2 + (gyh - f(gpy)) ** 2)
+    nrm = norms.cpu().numpy()
+    assert abs(nrm[0] - dv) <= 1e-6 * dv and abs(nrm[1] - dg) <= 1e-6 * dg
+    a_k = 2.7
+    coef = (a_k - 1.0) / OP.nesterov_next_a(a_k)
+    pp.binding.nesterov_step(1.0, 1.0, T["ux"], T["uy"], T["vx"], T["vy"], T["vpx"], T["vpy"], gx, gy,
+                             T["gpx"], T["gpy"], T["w"], T["h"], torch.from_numpy(mov).cuda(), norms, 0.0, coef)
+    alpha = math.sqrt(dv / dg)
+    rux, rvx = OP.nesterov_step(f(ux), f(vx), gxh, f(w), 1.0, alpha, a_k, movable=mov)
+    assert np.abs(T["ux"].double().cpu().numpy() - rux).max() <= 2e-6
+    assert np.abs(T["vx"].double().cpu().numpy() - rvx).max() <= 2e-6
+    assert np.array_equal(T["vpx"].cpu().numpy(), np.asarray(vx, np.float32))   # v saved as v_prev
+    assert np.array_equal(T["gpx"].cpu().numpy(), gx.cpu().numpy())            # g saved as g_prev
+
+
+def test_place_loop_spreads_and_gradients_match_oracle(pp):
+    """150 iterations on 8,000 cells (70% utilisation, started in a cluster) and
+    64 x 64 modes: the overflow falls, and at iterations 0 and 60 the GPU's
+    wirelength and density gradients at the GPU's positions match the oracle."""
+    n, M = 8000, 64
+    p = synth.placement_cells(n, M, 31)
+    ptr, pins = synth.netlist(n, 32)
+    checks = {}
+
+    def cb(k, rec, xe, ye, ux, uy):
+        if k in (0, 60):
+            checks[k] = (xe.cpu().numpy(), ye.cpu().numpy(), rec)
+
+    r = place.place(p, ptr, pins, iters=150, prec="fp32", tau_stop=0.0, callback=cb)
+    taus = [t["tau"] for t in r.trace]
+    assert taus[-1] < 0.8 * taus[0], (taus[0], taus[-1])
+    assert all(np.isfinite([t["hpwl"] for t in r.trace]))
+    sub = np.random.default_rng(3).choice(n, 300, replace=False)
+    for k, (vx, vy, rec) in checks.items():
+        # wirelength at the GPU's positions, with the gamma of that iteration
+        gx, gy, out = pp.binding.wirelength(pp.binding.DeviceNetlist(n, ptr, pins), torch.from_numpy(vx).cuda(),
+                                            torch.from_numpy(vy).cuda(), rec["gamma"])
+        W, hp, rgx, _ = OP.lse_wirelength(vx, vy, ptr, pins, rec["gamma"])
+        assert abs(rec["W_lse"] - W) <= 2e-6 * W and abs(rec["hpwl"] - hp) <= 1e-6 * hp
+        assert np.abs(gx.double().cpu().numpy() - rgx).max() <= 2e-5 * np.abs(rgx).max()
+        # density: energy and gradient of the exact series at the same positions
+        ref = OS.evaluate(p.W, p.H, vx, vy, p.w, p.h, None, M, M, idx=sub)
+        assert abs(rec["E"] - ref["E"]) <= 1e-5 * abs(ref["E"]), (k, rec["E"], ref["E"])
+
+
+def test_place_entry_points_reject_bad_arguments(pp):
+    nl = pp.binding.DeviceNetlist(2, np.array([0, 2]), np.array([0, 1]))
+    x = torch.zeros(2, device="cuda")
+    with pytest.raises(pp.binding.PPError):
+        pp.binding.wirelength(nl, x, x.clone(), 0.0)
+    with pytest.raises(pp.binding.PPError):
+        pp.binding.wirelength(nl, x, x.clone(), float("nan"))
+    w = torch.full((2,), 0.1, device="cuda")
+    with pytest.raises(pp.binding.PPError):
+        pp.binding.overflow(x, x.clone(), w, w.clone(), 1.0, 1.0, 0)
+    with pytest.raises(pp.binding.PPError):
+        pp.binding.overflow(x, x.clone(), w, w.clone(), 1.0, 1.0, 16, target=-1.0)
+    with pytest.raises(pp.binding.PPError):
+        pp.binding.place_combine(x, x, x, x, None, w, None, -1.0)
