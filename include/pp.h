@@ -185,7 +185,7 @@ pp_status pp_energy_from_coeffs(const float *a, int32_t Mx, int32_t My, double W
                                 double *e_total, void *stream);
 
 /* One position update of the descent loop (a driver around the evaluation; the
- * placer of Sec. IV, whose step rule the paper does not give, is out of scope).
+ * Nesterov loop of Sec. IV is pp_nesterov_step and its companions below).
  * For every block i with movable == NULL or movable[i] != 0:
  *   x_i <- clamp(x_i - lr * gx_i + sigma * n0_i, w_i / 2, W - w_i / 2)
  *   y_i <- clamp(y_i - lr * gy_i + sigma * n1_i, h_i / 2, H - h_i / 2)
