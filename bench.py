@@ -186,10 +186,12 @@ def barrier(world):
 # ---------------------------------------------------------------------------
 # the step
 # ---------------------------------------------------------------------------
-def make_inputs(device, n=None, workload=WORKLOAD_INDEX):
+def make_inputs(device, n=None, workload=WORKLOAD_INDEX, mode="grad"):
     import torch
     from paper_2307_12041_gb300 import synth
     p = synth.workload(workload, n=n)
+    if mode == "place":         # the loop's inputs: cells at 70% utilisation, started in a cluster
+        p = synth.placement_cells(p.n, p.Mx, synth.BASE_SEED + 10 + workload)
     t = lambda a: torch.from_numpy(a).to(device)
     return p, (t(p.x), t(p.y), t(p.w), t(p.h), None)
 
@@ -204,7 +206,8 @@ def time_steps(binding, p, dev_in, prec, steps, warmup, flush, outs, kernel_timi
     function's forward (pp_energy) and backward (pp_grad, a recomputed), fixed
     blocks masked; "block-adjoint": per-block energies forward and the backward for
     a random upstream gradient (two coefficient and two energy contractions);
-    "binned": the binned fast scheme (Sec. III-D) on `bins` x `bins` bins."""
+    "binned": the binned fast scheme (Sec. III-D) on `bins` x `bins` bins; "place": one
+    iteration of the Sec. IV placement loop per step."""
     import torch
     x, y, w, h, c = dev_in
     stream = torch.cuda.current_stream()
@@ -223,6 +226,11 @@ def time_steps(binding, p, dev_in, prec, steps, warmup, flush, outs, kernel_timi
             else:       # per-block energies, backward for an arbitrary upstream gradient
                 N = binding.PoissonBlockEnergies.apply(xg, yg, w, h, c, p.W, p.H, p.Mx, p.My, prec, mov)
                 N.backward(gw)
+    elif mode == "place":        # one iteration of the Sec. IV loop per step (the loop's state carries over)
+        from paper_2307_12041_gb300 import place as placemod, synth
+        ptr, pins = synth.netlist(p.n, synth.BASE_SEED + 11)
+        placer = placemod.Placer(p, ptr, pins, prec)
+        run = placer.step
     elif mode == "binned":
         m = max(p.Mx, p.My) if bins is None else bins
         bprec = "tf32" if prec == "bf16x3" else prec
@@ -351,7 +359,7 @@ def run_ours(args):
     if prec not in avail:
         raise SystemExit(f"precision {prec} not available: {avail}")
 
-    p, dev_in = make_inputs(device, workload=args.workload)
+    p, dev_in = make_inputs(device, workload=args.workload, mode=args.mode)
     n = p.n
     outs = (torch.empty(n, dtype=torch.float32, device=device),
             torch.empty(n, dtype=torch.float32, device=device),
@@ -404,7 +412,8 @@ def run_ours(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": prec,
         "data": "synthetic",
-        "config": {"workload": synth.WORKLOADS[args.workload]["name"], "mode": args.mode,
+        "config": {"workload": p.name if args.mode == "place" else synth.WORKLOADS[args.workload]["name"],
+                   "mode": args.mode,
                    "bins": (args.bins or max(p.Mx, p.My)) if args.mode == "binned" else None, "n": n, "Mx": p.Mx,
                    "My": p.My, "sample": "rect", "precision": prec, "W": p.W, "H": p.H,
                    "l2": "flushed: 256 MiB written before every timed step",
@@ -488,10 +497,12 @@ def main(argv=None):
     ap.add_argument("--workload", type=int, default=WORKLOAD_INDEX,
                     help="synth.WORKLOADS index (default: the metric's 200k x 512^2 workload)")
     ap.add_argument("--bins", type=int, default=None, help="bins per side for --mode binned")
-    ap.add_argument("--mode", choices=["grad", "autograd", "block-adjoint", "binned"], default="grad",
+    ap.add_argument("--mode", choices=["grad", "autograd", "block-adjoint", "binned", "place"], default="grad",
                     help="grad: one pp_grad per step; autograd: energy forward + adjoint backward; "
                          "block-adjoint: per-block energies forward + vector-output adjoint; "
-                         "binned: the binned fast scheme (terms counted as N Mx My)")
+                         "binned: the binned fast scheme (terms counted as N Mx My); "
+                         "place: one iteration of the Sec. IV placement loop (density, LSE "
+                         "wirelength, Nesterov step, overflow) on a synthetic netlist")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")

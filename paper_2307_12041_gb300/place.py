@@ -49,73 +49,91 @@ def gamma_of(tau: float, bin_w: float) -> float:
     return 8.0 * bin_w * 10.0 ** ((20.0 / 9.0) * (tau - 0.1) - 1.0)
 
 
+class Placer:
+    """The loop's state on the device (major and reference solutions u, v, the
+    previous v and gradient, the netlist, the bins) and its scalars (lambda,
+    gamma, a_k); step() runs one iteration and returns its record."""
+
+    def __init__(self, p: synth.Placement, net_ptr, net_pin, prec: str = "tf32", target: float = 1.0,
+                 d_hpwl_frac: float = 3.5e-3, device="cuda"):
+        dev = torch.device(device)
+        self.p, self.prec, self.target, self.d_hpwl_frac = p, prec, target, d_hpwl_frac
+        self.nl = binding.DeviceNetlist(p.n, net_ptr, net_pin, dev)
+        x, y, self.w, self.h, self.c = binding.to_device(p, dev)
+        self.M = p.Mx
+        self.bin_w = p.W / self.M
+        self.ux, self.uy = x.clone(), y.clone()
+        self.vx, self.vy = x.clone(), y.clone()
+        self.vpx, self.vpy = x.clone(), y.clone()
+        self.gpx, self.gpy = torch.zeros_like(x), torch.zeros_like(y)
+        self.q = self.w * self.h if self.c is None else self.c * self.w * self.h
+        self.mov = None if p.movable is None else torch.from_numpy(p.movable.astype("uint8")).to(dev)
+        self.area_mov = float(self.q.sum() if self.mov is None else self.q[self.mov.bool()].sum())
+        self.bin_area = (p.W / self.M) * (p.H / self.M)
+        self.norms = torch.zeros(2, dtype=torch.float64, device=dev)
+        self.bins = torch.empty((self.M, self.M), dtype=torch.float32, device=dev)
+        ovf, _ = binding.overflow(self.ux, self.uy, self.w, self.h, p.W, p.H, self.M, target, bins=self.bins)
+        self.tau = float(ovf.item()) * self.bin_area / self.area_mov
+        self.gamma = gamma_of(self.tau, self.bin_w)
+        self.lam, self.a_k, self.hp_prev, self.d_ref, self.k = None, 1.0, None, None, 0
+
+    def step(self) -> dict:
+        p, M, k = self.p, self.M, self.k
+        gnx, gny, _, E = binding.grad(self.vx, self.vy, self.w, self.h, self.c, p.W, p.H, M, M, self.prec)
+        gwx, gwy, wl = binding.wirelength(self.nl, self.vx, self.vy, self.gamma)
+        if self.lam is None:                  # lambda_0: ratio of the L1 gradient norms
+            self.lam = float((gwx.abs().sum() + gwy.abs().sum()) / (gnx.abs().sum() + gny.abs().sum()))
+        gx, gy = binding.place_combine(gwx, gwy, gnx, gny, self.nl.cell_ptr, self.q, self.mov, self.lam)
+        if k > 0:
+            binding.step_norms(self.vx, self.vy, self.vpx, self.vpy, gx, gy, self.gpx, self.gpy, self.norms)
+            alpha0 = 0.0
+        else:                                 # first step: the largest gradient moves one bin
+            gmax = float(torch.maximum(gx.abs().max(), gy.abs().max()))
+            alpha0 = self.bin_w / gmax if gmax > 0 else 0.0
+        a_next = (1.0 + math.sqrt(4.0 * self.a_k * self.a_k + 1.0)) / 2.0
+        binding.nesterov_step(p.W, p.H, self.ux, self.uy, self.vx, self.vy, self.vpx, self.vpy, gx, gy,
+                              self.gpx, self.gpy, self.w, self.h, self.mov, self.norms if k > 0 else None,
+                              alpha0, (self.a_k - 1.0) / a_next)
+        self.a_k = a_next
+        ovf, _ = binding.overflow(self.ux, self.uy, self.w, self.h, p.W, p.H, M, self.target, bins=self.bins)
+        s = torch.cat([ovf, wl, E.reshape(1)]).cpu()        # the one read-back of the iteration
+        self.tau = float(s[0]) * self.bin_area / self.area_mov
+        rec = {"k": k, "tau": self.tau, "W_lse": float(s[1]), "hpwl": float(s[2]), "E": float(s[3]),
+               "lambda": self.lam, "gamma": self.gamma}
+        # penalty and smoothing updates for the next iteration
+        if self.hp_prev is None:
+            self.d_ref = self.d_hpwl_frac * rec["hpwl"]
+        else:
+            mu = 1.1 ** (1.0 - (rec["hpwl"] - self.hp_prev) / self.d_ref)
+            self.lam *= min(1.1, max(0.75, mu))
+        self.hp_prev = rec["hpwl"]
+        self.gamma = gamma_of(self.tau, self.bin_w)
+        self.k += 1
+        return rec
+
+
 def place(p: synth.Placement, net_ptr, net_pin, iters: int = 200, prec: str = "tf32",
           tau_stop: float = 0.1, target: float = 1.0, d_hpwl_frac: float = 3.5e-3,
           device="cuda", callback: Optional[Callable] = None) -> PlaceResult:
     """Run up to `iters` iterations; callback(k, rec, x_eval, y_eval, ux, uy) after
     each, with the positions at which W_LSE and E of `rec` were evaluated."""
-    dev = torch.device(device)
-    nl = binding.DeviceNetlist(p.n, net_ptr, net_pin, dev)
-    x, y, w, h, c = binding.to_device(p, dev)
-    M = p.Mx
-    bin_w = p.W / M
-    ux, uy = x.clone(), y.clone()
-    vx, vy = x.clone(), y.clone()
-    vpx, vpy = vx.clone(), vy.clone()
-    gpx, gpy = torch.zeros_like(vx), torch.zeros_like(vy)
-    q = w * h if c is None else c * w * h
-    mov = None if p.movable is None else torch.from_numpy(p.movable.astype("uint8")).to(dev)
-    area_mov = float(q.sum() if mov is None else q[mov.bool()].sum())
-    bin_area = (p.W / M) * (p.H / M)
-    norms = torch.zeros(2, dtype=torch.float64, device=dev)
-    bins = torch.empty((M, M), dtype=torch.float32, device=dev)
-    # starting overflow -> gamma
-    ovf, _ = binding.overflow(ux, uy, w, h, p.W, p.H, M, target, bins=bins)
-    tau = float(ovf.item()) * bin_area / area_mov
-    gamma = gamma_of(tau, bin_w)
+    pl = Placer(p, net_ptr, net_pin, prec, target, d_hpwl_frac, device)
     res = PlaceResult()
-    lam, a_k, hp_prev, d_ref = None, 1.0, None, None
+    dev = torch.device(device)
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
-    for k in range(iters):
-        gnx, gny, _, E = binding.grad(vx, vy, w, h, c, p.W, p.H, M, M, prec)
-        gwx, gwy, wl = binding.wirelength(nl, vx, vy, gamma)
-        if lam is None:                       # lambda_0: ratio of the L1 gradient norms
-            lam = float((gwx.abs().sum() + gwy.abs().sum()) / (gnx.abs().sum() + gny.abs().sum()))
-        gx, gy = binding.place_combine(gwx, gwy, gnx, gny, nl.cell_ptr, q, mov, lam)
-        if k > 0:
-            binding.step_norms(vx, vy, vpx, vpy, gx, gy, gpx, gpy, norms)
-            alpha0 = 0.0
-        else:                                 # first step: the largest gradient moves one bin
-            gmax = float(torch.maximum(gx.abs().max(), gy.abs().max()))
-            alpha0 = bin_w / gmax if gmax > 0 else 0.0
-        a_next = (1.0 + math.sqrt(4.0 * a_k * a_k + 1.0)) / 2.0
-        binding.nesterov_step(p.W, p.H, ux, uy, vx, vy, vpx, vpy, gx, gy, gpx, gpy, w, h, mov,
-                              norms if k > 0 else None, alpha0, (a_k - 1.0) / a_next)
-        a_k = a_next
-        ovf, _ = binding.overflow(ux, uy, w, h, p.W, p.H, M, target, bins=bins)
-        s = torch.cat([ovf, wl, E.reshape(1)]).cpu()        # the one read-back of the iteration
-        tau = float(s[0]) * bin_area / area_mov
-        rec = {"k": k, "tau": tau, "W_lse": float(s[1]), "hpwl": float(s[2]), "E": float(s[3]),
-               "lambda": lam, "gamma": gamma}
+    for _ in range(iters):
+        rec = pl.step()
         res.trace.append(rec)
         if callback is not None:          # vpx, vpy: the positions this iteration evaluated
-            callback(k, rec, vpx, vpy, ux, uy)
-        # penalty and smoothing updates
-        if hp_prev is None:
-            d_ref = d_hpwl_frac * rec["hpwl"]
-        else:
-            mu = 1.1 ** (1.0 - (rec["hpwl"] - hp_prev) / d_ref)
-            lam *= min(1.1, max(0.75, mu))
-        hp_prev = rec["hpwl"]
-        gamma = gamma_of(tau, bin_w)
-        res.iterations = k + 1
-        if tau < tau_stop:
+            callback(rec["k"], rec, pl.vpx, pl.vpy, pl.ux, pl.uy)
+        res.iterations = rec["k"] + 1
+        if rec["tau"] < tau_stop:
             break
     torch.cuda.synchronize(dev)
     binding.sync_status(dev)
     res.ms_per_iter = (time.perf_counter() - t0) * 1e3 / max(res.iterations, 1)
-    res.x, res.y = ux, uy
+    res.x, res.y = pl.ux, pl.uy
     return res
 
 
