@@ -252,3 +252,43 @@ def test_grid_aligned_phase_steps(pp):
     for prec in pp.binding.available_precisions():
         out = pp.binding.evaluate(p, prec=prec)
         check(out, ref, pp.binding.TOLERANCE[prec], label=f"{prec} grid-aligned")
+
+
+def split_tile_rows(n, My, sms, rows=128, vc=256, grid_max=256):
+    """Blocks of the energy kernel's row tiles that are cut between two CTAs: the
+    (tile, pass) units are divided into equal ranges, one per CTA (grid = the
+    smaller of the tile count, the SM count and grid_max)."""
+    tiles = (n + rows - 1) // rows
+    nvc = (My + vc - 1) // vc
+    grid = min(tiles, sms, grid_max)
+    U = tiles * nvc
+    cut = set()
+    for b in range(1, grid):
+        ub = U * b // grid
+        if ub % nvc:
+            cut.add(ub // nvc)
+    return sorted(cut), [t * rows + r for t in sorted(cut) for r in range(rows) if t * rows + r < n]
+
+
+@pytest.mark.parametrize("prec", ["tf32", "bf16x3"])
+def test_split_energy_tiles_and_determinism(pp, prec):
+    """The rows of tiles cut between two CTAs of the energy kernel (their two parts
+    meet through the workspace) against the FP64 oracle, and two identical calls give
+    bitwise identical coefficients, per-block energies and gradients."""
+    n, M = 40_000, 512                       # 313 tiles of 128 rows, two 256-column passes each
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    tiles, rows = split_tile_rows(n, M, sms)
+    assert len(tiles) > 10
+    p = synth.cell_mix(n, M, M, 97)
+    sub = np.array(rows[::7] + [rows[-1]])
+    ref = O.evaluate(p.W, p.H, p.x, p.y, p.w, p.h, p.c, M, M, idx=sub)
+    out1 = pp.binding.evaluate(p, prec=prec)
+    out2 = pp.binding.evaluate(p, prec=prec)
+    tol = pp.binding.TOLERANCE[prec]
+    N = out1["N"].double().cpu().numpy()[sub]
+    gx = out1["gx"].double().cpu().numpy()[sub]
+    gy = out1["gy"].double().cpu().numpy()[sub]
+    assert nerr(N, ref["N"]) <= tol
+    assert gerr(gx, gy, ref) <= tol
+    for k in ("a", "N", "gx", "gy"):
+        assert torch.equal(out1[k], out2[k]), k
