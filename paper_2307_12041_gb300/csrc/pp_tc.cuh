@@ -197,28 +197,6 @@ __device__ __forceinline__ void tmem_ld_wait_regs16(float a[16], float b[16]) {
                  : "memory");
 }
 
-// 32 lanes x 8 columns of 32 bits (one register per column)
-__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float v[8]) {
-    uint32_t r[8];
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
-                   "=r"(r[6]), "=r"(r[7])
-                 : "r"(taddr));
-#pragma unroll
-    for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
-}
-
-// Wait for this thread's outstanding TMEM loads; the registers of a and b are
-// operands of the wait, so no use of them is scheduled before it.
-__device__ __forceinline__ void tmem_ld_wait_regs(float a[8], float b[8]) {
-    asm volatile("tcgen05.wait::ld.sync.aligned;"
-                 : "+f"(a[0]), "+f"(a[1]), "+f"(a[2]), "+f"(a[3]), "+f"(a[4]), "+f"(a[5]), "+f"(a[6]),
-                   "+f"(a[7]), "+f"(b[0]), "+f"(b[1]), "+f"(b[2]), "+f"(b[3]), "+f"(b[4]), "+f"(b[5]),
-                   "+f"(b[6]), "+f"(b[7])
-                 :
-                 : "memory");
-}
-
 // ---- TMA ----------------------------------------------------------------------
 __device__ __forceinline__ void tma_load_2d(void *dst_smem, const void *tmap, int c0, int c1,
                                             uint64_t *bar) {
