@@ -260,69 +260,48 @@ def time_steps(binding, p, dev_in, prec, steps, warmup, flush, outs, kernel_timi
     return [a.elapsed_time(b) for a, b in evs], ktimes
 
 
-def time_e2e(binding, p, prec, steps, device):
+def time_e2e(binding, p, prec, steps, device, flush):
     """Same evaluation through host buffers: every step copies its x, y, w, h in
     from pinned host memory, runs pp_grad, and copies its gx, gy, N, E out, all
-    inside the timed region.  Device buffers are double-buffered and the copies
-    run on a second stream ordered by events, so that step k + 1's inputs travel
-    while step k computes (each buffer is reused only after the work that last
-    read or wrote it is done)."""
+    inside the step's CUDA events (one stream, so copies and compute are serial);
+    the L2 is flushed before every step, outside the events, as in the device-side
+    timing."""
     import torch
     n = p.n
     hin = [torch.from_numpy(a).pin_memory() for a in (p.x, p.y, p.w, p.h)]
-    din = [[torch.empty(n, dtype=torch.float32, device=device) for _ in range(4)] for _ in range(2)]
-    dout = [(torch.empty(n, dtype=torch.float32, device=device),
-             torch.empty(n, dtype=torch.float32, device=device),
-             torch.empty(n, dtype=torch.float32, device=device),
-             torch.empty(1, dtype=torch.float64, device=device)) for _ in range(2)]
-    hout = [(torch.empty(n, dtype=torch.float32).pin_memory(),
-             torch.empty(n, dtype=torch.float32).pin_memory(),
-             torch.empty(n, dtype=torch.float32).pin_memory(),
-             torch.empty(1, dtype=torch.float64).pin_memory()) for _ in range(2)]
-    comp = torch.cuda.current_stream(device)
-    copy = torch.cuda.Stream(device)
-    ev = lambda: torch.cuda.Event()
-    inputs_in, computed, results_out = [ev(), ev()], [ev(), ev()], [ev(), ev()]
-    used = [False, False]
+    din = [torch.empty(n, dtype=torch.float32, device=device) for _ in range(4)]
+    dout = (torch.empty(n, dtype=torch.float32, device=device),
+            torch.empty(n, dtype=torch.float32, device=device),
+            torch.empty(n, dtype=torch.float32, device=device),
+            torch.empty(1, dtype=torch.float64, device=device))
+    hout = (torch.empty(n, dtype=torch.float32).pin_memory(),
+            torch.empty(n, dtype=torch.float32).pin_memory(),
+            torch.empty(n, dtype=torch.float32).pin_memory(),
+            torch.empty(1, dtype=torch.float64).pin_memory())
+    stream = torch.cuda.current_stream(device)
 
-    def step(i):
-        b = i & 1
-        with torch.cuda.stream(copy):
-            if used[b]:
-                copy.wait_event(computed[b])          # the compute that read din[b] is done
-            for d, hsrc in zip(din[b], hin):
-                d.copy_(hsrc, non_blocking=True)
-            inputs_in[b].record(copy)
-        comp.wait_event(inputs_in[b])
-        if used[b]:
-            comp.wait_event(results_out[b])           # dout[b] has been copied out
-        dx, dy, dw, dh = din[b]
-        binding.grad(dx, dy, dw, dh, None, p.W, p.H, p.Mx, p.My, prec, out=dout[b])
-        computed[b].record(comp)
-        with torch.cuda.stream(copy):
-            copy.wait_event(computed[b])
-            for hdst, d in zip(hout[b], dout[b]):
-                hdst.copy_(d, non_blocking=True)
-            results_out[b].record(copy)
-        used[b] = True
+    def step():
+        for d, hsrc in zip(din, hin):
+            d.copy_(hsrc, non_blocking=True)
+        binding.grad(din[0], din[1], din[2], din[3], None, p.W, p.H, p.Mx, p.My, prec, out=dout)
+        for hdst, d in zip(hout, dout):
+            hdst.copy_(d, non_blocking=True)
 
-    for i in range(3):
-        step(i)
+    for _ in range(3):
+        step()
     torch.cuda.synchronize(device)
-    t0 = time.perf_counter()
-    a = torch.cuda.Event(enable_timing=True)
-    z = torch.cuda.Event(enable_timing=True)
-    a.record(comp)
-    for i in range(steps):
-        step(i)
-    comp.wait_stream(copy)                            # the last results are out
-    z.record(comp)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(steps)]
+    for a, b in evs:
+        flush.zero_()
+        a.record(stream)
+        step()
+        b.record(stream)
     torch.cuda.synchronize(device)
-    wall = time.perf_counter() - t0
-    ms = max(a.elapsed_time(z), wall * 1e3)
+    ms = sum(a.elapsed_time(b) for a, b in evs) / steps
     h2d = 4 * 4 * n
     d2h = 3 * 4 * n + 8
-    return ms / steps, h2d, d2h
+    return ms, h2d, d2h
 
 
 def errors_vs(ref, got):
@@ -459,7 +438,7 @@ def run_ours(args):
             fv = terms * args.steps / (sum(f_ms) / 1e3)
             line["fp32_plain"] = {"value": fv, "ms_per_step": sum(f_ms) / args.steps,
                                   "speedup_of_mixed": value / world / fv}
-        e_ms, h2d, d2h = time_e2e(binding, p, prec, args.steps, device)
+        e_ms, h2d, d2h = time_e2e(binding, p, prec, args.steps, device, flush)
         line["e2e"] = {"value": world * terms / (e_ms / 1e3), "unit": "terms/s",
                        "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                        "ms_per_step": e_ms}
