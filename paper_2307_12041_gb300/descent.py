@@ -1,5 +1,6 @@
-"""Gradient-descent driver over block positions (a stand-in for the placer loop of
-Sec. IV, whose Nesterov parameters the paper does not restate).
+"""Gradient-descent driver over block positions: a plain, fixed-step loop around the
+density evaluation alone (the Sec. IV loop with wirelength, Nesterov steps and the
+penalty schedule is `place.py`).
 
 Each step evaluates E and its gradient through the C ABI, then moves the
 movable blocks with pp_descent_step:  x <- clamp(x - lr * dE/dx + j, w/2, W - w/2)
