@@ -5,7 +5,9 @@ paper takes the optimiser and its parameters from ePlace without restating them;
 the readings used here (each a parameter of `place`):
 
 * density N: the exact series of this library (`pp_grad`, rectangle reading, any
-  precision), E = 1/2 sum_i N_i and its gradient;
+  precision), E = 1/2 sum_i N_i and its gradient; or, as in the paper's own placer,
+  the binned fast scheme of Sec. III-D on M x M bins (`pp_binned_grad`, centre
+  reading, FP32 or TF32 transforms);
 * wirelength: log-sum-exp with smoothing gamma = 8 w_b 10^{(20/9)(tau - 0.1) - 1}
   (w_b the bin width, tau the current overflow: gamma shrinks as the placement
   spreads);
@@ -55,9 +57,12 @@ class Placer:
     gamma, a_k); step() runs one iteration and returns its record."""
 
     def __init__(self, p: synth.Placement, net_ptr, net_pin, prec: str = "tf32", target: float = 1.0,
-                 d_hpwl_frac: float = 3.5e-3, device="cuda"):
+                 d_hpwl_frac: float = 3.5e-3, device="cuda", density: str = "exact"):
+        if density not in ("exact", "binned"):
+            raise ValueError("density must be 'exact' or 'binned'")
         dev = torch.device(device)
         self.p, self.prec, self.target, self.d_hpwl_frac = p, prec, target, d_hpwl_frac
+        self.density = density
         self.nl = binding.DeviceNetlist(p.n, net_ptr, net_pin, dev)
         x, y, self.w, self.h, self.c = binding.to_device(p, dev)
         self.M = p.Mx
@@ -79,7 +84,12 @@ class Placer:
 
     def step(self) -> dict:
         p, M, k = self.p, self.M, self.k
-        gnx, gny, _, E = binding.grad(self.vx, self.vy, self.w, self.h, self.c, p.W, p.H, M, M, self.prec)
+        if self.density == "exact":
+            gnx, gny, _, E = binding.grad(self.vx, self.vy, self.w, self.h, self.c, p.W, p.H, M, M, self.prec)
+        else:                                 # binned scheme: bins = modes per axis (K = m - 1)
+            bprec = "fp32" if self.prec == "fp32" else "tf32"
+            gnx, gny, _, E, _ = binding.binned_grad(self.vx, self.vy, self.w, self.h, self.c, p.W, p.H, M, M, M,
+                                                    bprec, want_coeffs=False)
         gwx, gwy, wl = binding.wirelength(self.nl, self.vx, self.vy, self.gamma)
         if self.lam is None:                  # lambda_0: ratio of the L1 gradient norms
             self.lam = float((gwx.abs().sum() + gwy.abs().sum()) / (gnx.abs().sum() + gny.abs().sum()))
@@ -114,10 +124,10 @@ class Placer:
 
 def place(p: synth.Placement, net_ptr, net_pin, iters: int = 200, prec: str = "tf32",
           tau_stop: float = 0.1, target: float = 1.0, d_hpwl_frac: float = 3.5e-3,
-          device="cuda", callback: Optional[Callable] = None) -> PlaceResult:
+          device="cuda", callback: Optional[Callable] = None, density: str = "exact") -> PlaceResult:
     """Run up to `iters` iterations; callback(k, rec, x_eval, y_eval, ux, uy) after
     each, with the positions at which W_LSE and E of `rec` were evaluated."""
-    pl = Placer(p, net_ptr, net_pin, prec, target, d_hpwl_frac, device)
+    pl = Placer(p, net_ptr, net_pin, prec, target, d_hpwl_frac, device, density)
     res = PlaceResult()
     dev = torch.device(device)
     torch.cuda.synchronize(dev)
@@ -149,16 +159,17 @@ def _main(argv=None) -> int:
     ap.add_argument("--iters", type=int, default=300)
     ap.add_argument("--prec", default="tf32")
     ap.add_argument("--seed", type=int, default=synth.BASE_SEED + 10)
+    ap.add_argument("--density", choices=["exact", "binned"], default="exact")
     a = ap.parse_args(argv)
     p = synth.placement_cells(a.n, a.modes, a.seed)
     ptr, pins = synth.netlist(a.n, a.seed + 1)
-    place(p, ptr, pins, iters=3, prec=a.prec)                       # warm-up
-    r = place(p, ptr, pins, iters=a.iters, prec=a.prec)
+    place(p, ptr, pins, iters=3, prec=a.prec, density=a.density)      # warm-up
+    r = place(p, ptr, pins, iters=a.iters, prec=a.prec, density=a.density)
     t = r.trace
     pick = [t[i] for i in range(0, len(t), max(1, len(t) // 10))] + [t[-1]]
     print(json.dumps({
         "workload": p.name, "n": p.n, "nets": len(ptr) - 1, "pins": int(len(pins)), "modes": a.modes,
-        "precision": a.prec, "iterations": r.iterations, "ms_per_iter": r.ms_per_iter,
+        "precision": a.prec, "density": a.density, "iterations": r.iterations, "ms_per_iter": r.ms_per_iter,
         "density_terms_per_s": p.n * a.modes * a.modes / (r.ms_per_iter / 1e3),
         "tau_first": t[0]["tau"], "tau_last": t[-1]["tau"], "hpwl_first": t[0]["hpwl"],
         "hpwl_last": t[-1]["hpwl"],

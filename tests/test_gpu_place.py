@@ -9,6 +9,7 @@ import numpy as np
 import pytest
 import torch
 
+from oracle import binned as OB
 from oracle import place as OP
 from oracle import series as OS
 from paper_2307_12041_gb300 import place, synth
@@ -145,6 +146,26 @@ def test_place_loop_spreads_and_gradients_match_oracle(pp):
         # density: energy and gradient of the exact series at the same positions
         ref = OS.evaluate(p.W, p.H, vx, vy, p.w, p.h, None, M, M, idx=sub)
         assert abs(rec["E"] - ref["E"]) <= 1e-5 * abs(ref["E"]), (k, rec["E"], ref["E"])
+
+
+def test_place_loop_with_binned_density(pp):
+    """The same loop with the paper's binned scheme (Sec. III-D) as the density term:
+    the overflow falls, and at iteration 0 E matches the binned oracle at the GPU's
+    positions."""
+    n, M = 8000, 64
+    p = synth.placement_cells(n, M, 41)
+    ptr, pins = synth.netlist(n, 42)
+    first = {}
+
+    def cb(k, rec, xe, ye, ux, uy):
+        if k == 0:
+            first["x"], first["y"], first["E"] = xe.cpu().numpy(), ye.cpu().numpy(), rec["E"]
+
+    r = place.place(p, ptr, pins, iters=150, prec="fp32", tau_stop=0.0, callback=cb, density="binned")
+    taus = [t["tau"] for t in r.trace]
+    assert taus[-1] < 0.8 * taus[0], (taus[0], taus[-1])
+    ref = OB.evaluate(p.W, p.H, first["x"], first["y"], p.w, p.h, None, M, M, M)
+    assert abs(first["E"] - ref["E"]) <= 1e-4 * abs(ref["E"]), (first["E"], ref["E"])
 
 
 def test_place_entry_points_reject_bad_arguments(pp):
