@@ -19,8 +19,11 @@ the readings used here (each a parameter of `place`):
 * step length |v_k - v_{k-1}| / |g_k - g_{k-1}| (first step: the largest gradient
   moves one bin width), Nesterov momentum from a_{k+1} = (1 + sqrt(4 a_k^2 + 1)) / 2;
 * overflow on the M x M bins of the mode grid at target density 1, stop below
-  tau_stop = 0.1; no filler cells (the density term spreads the cells over the
-  whole die).
+  tau_stop = 0.1;
+* filler cells (optional, `fillers=True`): movable cells without nets, of the mean
+  movable cell's size, as many as bring the total block area to target * W * H,
+  started uniformly over the die; they take part in the density term only (not in
+  the wirelength, nor in the overflow, which measures the given blocks).
 
 Every per-iteration step runs in the library's kernels through the C ABI; the host
 keeps the scalars (lambda, gamma, a_k) and reads one small vector back per
@@ -57,12 +60,16 @@ class Placer:
     gamma, a_k); step() runs one iteration and returns its record."""
 
     def __init__(self, p: synth.Placement, net_ptr, net_pin, prec: str = "tf32", target: float = 1.0,
-                 d_hpwl_frac: float = 3.5e-3, device="cuda", density: str = "exact"):
+                 d_hpwl_frac: float = 3.5e-3, device="cuda", density: str = "exact", fillers: bool = False,
+                 filler_seed: int = synth.BASE_SEED + 99):
         if density not in ("exact", "binned"):
             raise ValueError("density must be 'exact' or 'binned'")
         dev = torch.device(device)
-        self.p, self.prec, self.target, self.d_hpwl_frac = p, prec, target, d_hpwl_frac
         self.density = density
+        self.n_real = p.n
+        if fillers:
+            p = with_fillers(p, target, filler_seed)
+        self.p, self.prec, self.target, self.d_hpwl_frac = p, prec, target, d_hpwl_frac
         self.nl = binding.DeviceNetlist(p.n, net_ptr, net_pin, dev)
         x, y, self.w, self.h, self.c = binding.to_device(p, dev)
         self.M = p.Mx
@@ -73,14 +80,22 @@ class Placer:
         self.gpx, self.gpy = torch.zeros_like(x), torch.zeros_like(y)
         self.q = self.w * self.h if self.c is None else self.c * self.w * self.h
         self.mov = None if p.movable is None else torch.from_numpy(p.movable.astype("uint8")).to(dev)
-        self.area_mov = float(self.q.sum() if self.mov is None else self.q[self.mov.bool()].sum())
+        nr = self.n_real                      # overflow and its area: the given blocks only
+        q_real = self.q[:nr]
+        self.area_mov = float(q_real.sum() if self.mov is None else q_real[self.mov[:nr].bool()].sum())
         self.bin_area = (p.W / self.M) * (p.H / self.M)
         self.norms = torch.zeros(2, dtype=torch.float64, device=dev)
         self.bins = torch.empty((self.M, self.M), dtype=torch.float32, device=dev)
-        ovf, _ = binding.overflow(self.ux, self.uy, self.w, self.h, p.W, p.H, self.M, target, bins=self.bins)
+        ovf = self.overflow_now()
         self.tau = float(ovf.item()) * self.bin_area / self.area_mov
         self.gamma = gamma_of(self.tau, self.bin_w)
         self.lam, self.a_k, self.hp_prev, self.d_ref, self.k = None, 1.0, None, None, 0
+
+    def overflow_now(self):
+        nr = self.n_real
+        ovf, _ = binding.overflow(self.ux[:nr], self.uy[:nr], self.w[:nr], self.h[:nr], self.p.W, self.p.H,
+                                  self.M, self.target, bins=self.bins)
+        return ovf
 
     def step(self) -> dict:
         p, M, k = self.p, self.M, self.k
@@ -105,7 +120,7 @@ class Placer:
                               self.gpx, self.gpy, self.w, self.h, self.mov, self.norms if k > 0 else None,
                               alpha0, (self.a_k - 1.0) / a_next)
         self.a_k = a_next
-        ovf, _ = binding.overflow(self.ux, self.uy, self.w, self.h, p.W, p.H, M, self.target, bins=self.bins)
+        ovf = self.overflow_now()
         s = torch.cat([ovf, wl, E.reshape(1)]).cpu()        # the one read-back of the iteration
         self.tau = float(s[0]) * self.bin_area / self.area_mov
         rec = {"k": k, "tau": self.tau, "W_lse": float(s[1]), "hpwl": float(s[2]), "E": float(s[3]),
@@ -122,12 +137,34 @@ class Placer:
         return rec
 
 
+def with_fillers(p: synth.Placement, target: float, seed: int) -> synth.Placement:
+    """p followed by filler cells (see the module notes): movable, no charge factor."""
+    import numpy as np
+    area = float(np.sum(p.w.astype(np.float64) * p.h))
+    free = target * p.W * p.H - area
+    mov = np.ones(p.n, bool) if p.movable is None else p.movable
+    fw, fh = float(np.mean(p.w[mov])), float(np.mean(p.h[mov]))
+    k = int(free // (fw * fh)) if free > 0 else 0
+    if k == 0:
+        return p
+    g = np.random.default_rng(seed)
+    fx = (0.5 * fw + g.random(k) * (p.W - fw)).astype(np.float32)
+    fy = (0.5 * fh + g.random(k) * (p.H - fh)).astype(np.float32)
+    cat = lambda a, b: np.concatenate([a, b]).astype(np.float32)
+    c = None if p.c is None else cat(p.c, np.ones(k))
+    return synth.Placement(p.W, p.H, cat(p.x, fx), cat(p.y, fy), cat(p.w, np.full(k, fw)),
+                           cat(p.h, np.full(k, fh)), c, p.Mx, p.My,
+                           movable=np.concatenate([mov, np.ones(k, bool)]), name=p.name + "+fillers",
+                           meta=dict(p.meta, fillers=k))
+
+
 def place(p: synth.Placement, net_ptr, net_pin, iters: int = 200, prec: str = "tf32",
           tau_stop: float = 0.1, target: float = 1.0, d_hpwl_frac: float = 3.5e-3,
-          device="cuda", callback: Optional[Callable] = None, density: str = "exact") -> PlaceResult:
+          device="cuda", callback: Optional[Callable] = None, density: str = "exact",
+          fillers: bool = False) -> PlaceResult:
     """Run up to `iters` iterations; callback(k, rec, x_eval, y_eval, ux, uy) after
     each, with the positions at which W_LSE and E of `rec` were evaluated."""
-    pl = Placer(p, net_ptr, net_pin, prec, target, d_hpwl_frac, device, density)
+    pl = Placer(p, net_ptr, net_pin, prec, target, d_hpwl_frac, device, density, fillers)
     res = PlaceResult()
     dev = torch.device(device)
     torch.cuda.synchronize(dev)
@@ -143,7 +180,7 @@ def place(p: synth.Placement, net_ptr, net_pin, iters: int = 200, prec: str = "t
     torch.cuda.synchronize(dev)
     binding.sync_status(dev)
     res.ms_per_iter = (time.perf_counter() - t0) * 1e3 / max(res.iterations, 1)
-    res.x, res.y = pl.ux, pl.uy
+    res.x, res.y = pl.ux[:pl.n_real], pl.uy[:pl.n_real]
     return res
 
 
@@ -160,16 +197,18 @@ def _main(argv=None) -> int:
     ap.add_argument("--prec", default="tf32")
     ap.add_argument("--seed", type=int, default=synth.BASE_SEED + 10)
     ap.add_argument("--density", choices=["exact", "binned"], default="exact")
+    ap.add_argument("--fillers", action="store_true")
     a = ap.parse_args(argv)
     p = synth.placement_cells(a.n, a.modes, a.seed)
     ptr, pins = synth.netlist(a.n, a.seed + 1)
-    place(p, ptr, pins, iters=3, prec=a.prec, density=a.density)      # warm-up
-    r = place(p, ptr, pins, iters=a.iters, prec=a.prec, density=a.density)
+    place(p, ptr, pins, iters=3, prec=a.prec, density=a.density, fillers=a.fillers)      # warm-up
+    r = place(p, ptr, pins, iters=a.iters, prec=a.prec, density=a.density, fillers=a.fillers)
     t = r.trace
     pick = [t[i] for i in range(0, len(t), max(1, len(t) // 10))] + [t[-1]]
     print(json.dumps({
         "workload": p.name, "n": p.n, "nets": len(ptr) - 1, "pins": int(len(pins)), "modes": a.modes,
-        "precision": a.prec, "density": a.density, "iterations": r.iterations, "ms_per_iter": r.ms_per_iter,
+        "precision": a.prec, "density": a.density, "fillers": a.fillers, "iterations": r.iterations,
+        "ms_per_iter": r.ms_per_iter,
         "density_terms_per_s": p.n * a.modes * a.modes / (r.ms_per_iter / 1e3),
         "tau_first": t[0]["tau"], "tau_last": t[-1]["tau"], "hpwl_first": t[0]["hpwl"],
         "hpwl_last": t[-1]["hpwl"],

@@ -168,6 +168,18 @@ def test_place_loop_with_binned_density(pp):
     assert abs(first["E"] - ref["E"]) <= 1e-4 * abs(ref["E"]), (first["E"], ref["E"])
 
 
+def test_place_loop_with_fillers(pp):
+    """Filler cells bring the total area to the target density; the given blocks'
+    overflow still falls."""
+    n, M = 8000, 64
+    p = synth.placement_cells(n, M, 51)
+    ptr, pins = synth.netlist(n, 52)
+    r = place.place(p, ptr, pins, iters=150, prec="fp32", tau_stop=0.0, fillers=True)
+    taus = [t["tau"] for t in r.trace]
+    assert taus[-1] < 0.8 * taus[0], (taus[0], taus[-1])
+    assert r.x.numel() == n and np.all(np.isfinite([t["hpwl"] for t in r.trace]))
+
+
 def test_place_entry_points_reject_bad_arguments(pp):
     nl = pp.binding.DeviceNetlist(2, np.array([0, 2]), np.array([0, 1]))
     x = torch.zeros(2, device="cuda")

@@ -101,3 +101,18 @@ def test_nesterov_sequence_and_clamp():
     a2 = P.nesterov_next_a(a1)
     assert np.allclose(un2[:2], un[:2]) and np.allclose(vn2[:2], un[:2])   # zero gradient: no move
     assert un2[2] == vn[2]                                                 # fixed
+
+
+def test_fillers_fill_to_target_density():
+    """place.with_fillers (host-side input preparation): the added cells bring the
+    total area to within one filler of target * W * H, are movable and lie inside
+    the die."""
+    from paper_2307_12041_gb300 import place, synth
+    p = synth.placement_cells(5000, 64, 3)
+    q = place.with_fillers(p, 1.0, 7)
+    k = q.n - p.n
+    assert k > 0 and q.movable[p.n:].all()
+    fa = float(q.w[-1]) * float(q.h[-1])
+    total = float(np.sum(q.w.astype(np.float64) * q.h))
+    assert 1.0 - fa <= total <= 1.0 + 1e-6
+    assert np.all(q.x - q.w / 2 >= 0) and np.all(q.x + q.w / 2 <= 1 + 1e-6)
