@@ -292,3 +292,37 @@ def test_split_energy_tiles_and_determinism(pp, prec):
     assert gerr(gx, gy, ref) <= tol
     for k in ("a", "N", "gx", "gy"):
         assert torch.equal(out1[k], out2[k]), k
+
+
+@pytest.mark.parametrize("prec", ["fp32", "tf32", "bf16x3"])
+def test_grad_replays_from_a_cuda_graph(pp, prec):
+    """pp_grad captured into a CUDA graph (fixed input, output and workspace buffers)
+    and replayed after the inputs change gives the results of a direct call."""
+    p = synth.cell_mix(5000, 96, 80, 17)
+    q = synth.cell_mix(5000, 96, 80, 18)
+    dev = torch.device("cuda")
+    x, y, w, h, c = pp.binding.to_device(p, dev)
+    n = p.n
+    outs = (torch.empty(n, device=dev), torch.empty(n, device=dev), torch.empty(n, device=dev),
+            torch.empty(1, dtype=torch.float64, device=dev))
+    pp.binding.grad(x, y, w, h, c, p.W, p.H, p.Mx, p.My, prec, out=outs)    # workspace, attributes
+    torch.cuda.synchronize()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(g, stream=s):
+            pp.binding.grad(x, y, w, h, c, p.W, p.H, p.Mx, p.My, prec, out=outs)
+    torch.cuda.synchronize()
+    for src in (q, p):                   # new inputs in the captured buffers, then the old ones
+        x.copy_(torch.from_numpy(src.x))
+        y.copy_(torch.from_numpy(src.y))
+        w.copy_(torch.from_numpy(src.w))
+        h.copy_(torch.from_numpy(src.h))
+        g.replay()
+        torch.cuda.synchronize()
+        ref = pp.binding.grad(x, y, w, h, c, p.W, p.H, p.Mx, p.My, prec)
+        for a, b in zip(outs[:3], ref[:3]):
+            assert torch.equal(a, b)
+        assert abs(float(outs[3]) - float(ref[3])) <= 1e-12 * abs(float(ref[3]))
+    pp.binding.sync_status()
