@@ -287,14 +287,18 @@ const char *pp_last_error(void);
 /* Library build identification string (compile flags, arch). */
 const char *pp_version(void);
 
-/* Kernel timing, a benchmarking aid with no counterpart in the paper.  While
- * enabled, every kernel launch of the library is bracketed by two CUDA events
- * recorded on the stream it is launched on.  pp_timing_collect() waits for
- * those events, then writes per kernel class (pp_kernel) the number of launches
- * and their summed device time in milliseconds since the previous collect
- * (arrays of PP_K_COUNT entries, host memory), and resets the sums.  At most
- * 65536 launches are timed between collects; later ones are counted in
- * `launches` but add no time.  Timing assumes one device per process. */
+/* Kernel counting and timing, a benchmarking aid with no counterpart in the
+ * paper.  Every kernel launch of the evaluation entry points is counted per
+ * kernel class (pp_kernel).  While timing is enabled, each launch is also
+ * bracketed by two CUDA events recorded on the stream it is launched on (the
+ * events cost device time between launches and keep a kernel from starting
+ * before the previous one has ended, so time whole steps with timing off).
+ * pp_timing_collect() waits for those events, then writes per kernel class the
+ * number of launches and their summed device time in milliseconds (0 for
+ * launches made with timing off) since the previous collect (arrays of
+ * PP_K_COUNT entries, host memory), and resets both.  At most 65536 launches are
+ * timed between collects; later ones are counted in `launches` but add no time.
+ * Timing assumes one device per process. */
 typedef enum {
     PP_K_PREP = 0,      /* per-block phases and scale factors */
     PP_K_COEFF = 1,     /* coefficient contraction  St = Xt^T Yt */

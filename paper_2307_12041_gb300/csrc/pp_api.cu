@@ -243,12 +243,12 @@ std::mutex g_tmu;
 std::atomic<bool> g_timing{false};
 std::vector<TimedLaunch> g_tpool;
 size_t g_tused = 0;
-int64_t g_tcount[PP_K_COUNT];
+std::atomic<int64_t> g_tcount[PP_K_COUNT];
 
 long timed_begin(int kind, cudaStream_t s) {
+    g_tcount[kind].fetch_add(1, std::memory_order_relaxed);       // every launch is counted
     if (!g_timing.load(std::memory_order_relaxed)) return -1;
     std::lock_guard<std::mutex> lk(g_tmu);
-    g_tcount[kind]++;
     if (g_tused >= kMaxTimed) return -1;
     if (g_tused == g_tpool.size()) {
         TimedLaunch t{};
@@ -728,9 +728,9 @@ pp_status pp_timing_collect(int64_t *launches, double *ms) {
         acc[t.kind] += v;
     }
     for (int k = 0; k < PP_K_COUNT; ++k) {
-        if (launches) launches[k] = g_tcount[k];
+        const int64_t cnt = g_tcount[k].exchange(0, std::memory_order_relaxed);
+        if (launches) launches[k] = cnt;
         if (ms) ms[k] = acc[k];
-        g_tcount[k] = 0;
     }
     g_tused = 0;
     return PP_OK;

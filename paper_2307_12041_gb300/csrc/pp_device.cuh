@@ -92,5 +92,30 @@ __device__ __forceinline__ unsigned long long fixed_halfturns(float x, double k)
     return (xb >> 31) ? ((0ull - q) & M63) : q;
 }
 
+// Programmatic dependent launch.  A kernel launched by launch_dependent() may be
+// scheduled while the kernel before it in the stream is still running; pdl_wait()
+// blocks until that kernel has completed and its writes are visible (a no-op for a
+// plain launch).  Every such kernel calls pdl_wait() before its first global load or
+// store and before it allocates tensor memory, so that while it waits it holds
+// nothing an earlier kernel still needs.  pdl_trigger() lets the next dependent
+// kernel be scheduled once every CTA of this grid has issued it or exited.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <typename... Params, typename... Args>
+cudaError_t launch_dependent(void (*kernel)(Params...), dim3 grid, dim3 block, size_t smem,
+                             cudaStream_t stream, Args &&...args) {
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<Args &&>(args)...);
+}
 
 }  // namespace pp

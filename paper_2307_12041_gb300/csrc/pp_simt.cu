@@ -28,6 +28,7 @@ __global__ void prep_kernel(const float *__restrict__ x, const float *__restrict
                             float piW, float piH, AxisRec *__restrict__ xr, AxisRec *__restrict__ yr,
                             double *__restrict__ S64, size_t nS, double *e_total) {
     // FP32 and integer arithmetic only (FP64 is a narrow pipe on this GPU)
+    pdl_trigger();            // a dependent coefficient or finish kernel may be scheduled now
     const size_t tid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     const size_t stride = (size_t)gridDim.x * blockDim.x;
     const double halfW = 0.5 * invW, halfH = 0.5 * invH;       // exact: powers of two

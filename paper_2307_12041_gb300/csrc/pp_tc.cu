@@ -325,6 +325,7 @@ __global__ void __launch_bounds__(C_THREADS, 1) tc_coeff_kernel(const CoeffArgs 
         bars.abort_flag = 0;
         mbar_fence_init();
     }
+    pdl_wait();                        // the block records come from the preparation kernel
     if (warp == 0) {
         tmem_alloc(&bars.tmem_slot, 512);
         tmem_relinquish();
@@ -332,6 +333,7 @@ __global__ void __launch_bounds__(C_THREADS, 1) tc_coeff_kernel(const CoeffArgs 
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
+    pdl_trigger();                     // the finish kernel may be scheduled (it waits for this one)
     const uint32_t tmem = bars.tmem_slot;
 
     const int tiles_v = args.tiles_v;
@@ -569,6 +571,8 @@ __global__ void tc_finish_kernel(const float *__restrict__ part, int slices, int
                                  int Mxe, int Mye, float piW, float piH, float invWH,
                                  double *__restrict__ e_total, unsigned *__restrict__ split_cnt,
                                  int nsplit) {
+    pdl_wait();                        // the slice partials come from the coefficient kernel
+    pdl_trigger();                     // the energy kernel may be scheduled (it waits for this one)
     // the energy kernel that follows finds its split-tile counters at zero
     if (blockIdx.x == 0)
         for (int i = threadIdx.x; i < nsplit; i += blockDim.x) split_cnt[i] = 0u;
@@ -1200,6 +1204,7 @@ tc_energy_kernel(const __grid_constant__ CUtensorMap tm_hi, const __grid_constan
         bars.abort_flag = 0;
         mbar_fence_init();
     }
+    pdl_wait();                        // K and the split counters come from the finish kernel
     if (warp == 0) {
         tmem_alloc(&bars.tmem_slot, 512);
         tmem_relinquish();
@@ -1494,11 +1499,13 @@ cudaError_t launch_coeff_tc(const Launch &L, int prec, const TcPlan &P, float *p
     if (prec == 1) {
         e = cudaFuncSetAttribute(tc_coeff_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, C_SMEM);
         if (e != cudaSuccess) return e;
-        tc_coeff_kernel<1><<<grid, C_THREADS, C_SMEM, L.stream>>>(a);
+        e = launch_dependent(tc_coeff_kernel<1>, dim3(grid), dim3(C_THREADS), C_SMEM, L.stream, a);
+        if (e != cudaSuccess) return e;
     } else {
         e = cudaFuncSetAttribute(tc_coeff_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, C_SMEM);
         if (e != cudaSuccess) return e;
-        tc_coeff_kernel<2><<<grid, C_THREADS, C_SMEM, L.stream>>>(a);
+        e = launch_dependent(tc_coeff_kernel<2>, dim3(grid), dim3(C_THREADS), C_SMEM, L.stream, a);
+        if (e != cudaSuccess) return e;
     }
     return cudaGetLastError();
 }
@@ -1537,17 +1544,10 @@ cudaError_t launch_finish_tc(const Launch &L, int prec, const TcPlan &P, const f
     if (blocks < 1) blocks = 1;
     const double PI = 3.141592653589793;
     const float piW = (float)(PI / L.W), piH = (float)(PI / L.H), invWH = (float)(1.0 / (L.W * L.H));
-    if (prec == 1)
-        tc_finish_kernel<1><<<blocks, 256, 0, L.stream>>>(part, P.slices, P.Mxc, P.Myc, a_in, a_out, Khi,
-                                                          Klo, L.Mx, L.My, P.Mxe, P.Mye, piW, piH, invWH,
-                                                          a_in ? nullptr : e_total, L.esplit_cnt,
-                                                          L.esplit_n);
-    else
-        tc_finish_kernel<2><<<blocks, 256, 0, L.stream>>>(part, P.slices, P.Mxc, P.Myc, a_in, a_out, Khi,
-                                                          Klo, L.Mx, L.My, P.Mxe, P.Mye, piW, piH, invWH,
-                                                          a_in ? nullptr : e_total, L.esplit_cnt,
-                                                          L.esplit_n);
-    return cudaGetLastError();
+    auto kfn = prec == 1 ? tc_finish_kernel<1> : tc_finish_kernel<2>;
+    return launch_dependent(kfn, dim3(blocks), dim3(256), 0, L.stream, part, P.slices, P.Mxc, P.Myc, a_in,
+                            a_out, Khi, Klo, L.Mx, L.My, P.Mxe, P.Mye, piW, piH, invWH,
+                            a_in ? nullptr : e_total, L.esplit_cnt, L.esplit_n);
 }
 
 cudaError_t launch_energy_tc(const Launch &L, int prec, int sample, const TcPlan &P, void *Khi,
@@ -1583,7 +1583,8 @@ cudaError_t launch_energy_tc(const Launch &L, int prec, int sample, const TcPlan
         auto kfn = tc_energy_kernel<PR, SA>;                                                       \
         e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, E_SMEM);       \
         if (e != cudaSuccess) return e;                                                            \
-        kfn<<<grid, E_THREADS, E_SMEM, L.stream>>>(mh, ml, a);                                     \
+        e = launch_dependent(kfn, dim3(grid), dim3(E_THREADS), E_SMEM, L.stream, mh, ml, a);       \
+        if (e != cudaSuccess) return e;                                                            \
     } while (0)
     if (prec == 1 && sample == 0) PP_ELAUNCH(1, 0);
     else if (prec == 1) PP_ELAUNCH(1, 1);

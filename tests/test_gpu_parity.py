@@ -326,3 +326,30 @@ def test_grad_replays_from_a_cuda_graph(pp, prec):
             assert torch.equal(a, b)
         assert abs(float(outs[3]) - float(ref[3])) <= 1e-12 * abs(float(ref[3]))
     pp.binding.sync_status()
+
+
+@pytest.mark.parametrize("prec", ["fp32", "tf32"])
+def test_launch_counts_and_kernel_timing(pp, prec):
+    """Every launch is counted whether or not timing is on; with timing on each
+    kernel class also reports device time, and the results do not change."""
+    p = synth.cell_mix(3000, 64, 64, 23)
+    x, y, w, h, c = pp.binding.to_device(p, torch.device("cuda"))
+    b = pp.binding
+    ref = b.grad(x, y, w, h, c, p.W, p.H, p.Mx, p.My, prec)
+    b.timing_collect()
+    for _ in range(3):
+        b.grad(x, y, w, h, c, p.W, p.H, p.Mx, p.My, prec)
+    torch.cuda.synchronize()
+    counts = b.timing_collect()
+    assert {k: v[0] for k, v in counts.items()} == {"prep": 3, "coeff": 3, "finish": 3, "energy": 3}
+    assert all(v[1] == 0.0 for v in counts.values())
+    b.timing_enable(True)
+    try:
+        got = b.grad(x, y, w, h, c, p.W, p.H, p.Mx, p.My, prec)
+        torch.cuda.synchronize()
+    finally:
+        b.timing_enable(False)
+    timed = b.timing_collect()
+    assert all(v[0] == 1 and v[1] > 0.0 for v in timed.values())
+    for g, r in zip(got[:3], ref[:3]):
+        assert torch.equal(g, r)
