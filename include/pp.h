@@ -271,6 +271,51 @@ pp_status pp_nesterov_step(int64_t n, double W, double H, float *ux, float *uy, 
  * size, target < 0 or a bad pointer.  Asynchronous on `stream`. */
 pp_status pp_overflow(const pp_problem *prob, int32_t m, float target, float *bins, double *out, void *stream);
 
+/* One iteration of the loop after the first, in one call: the work of the calls
+ * below, made one after the other on `stream` (the same kernels in the same
+ * order), with their scratch carved from one workspace.
+ *   1. gn, E      density gradient and energy at v: the exact series on M x M modes
+ *                 (pp_grad, PP_RECT) or the binned scheme of Sec. III-D on M x M
+ *                 bins (pp_binned_grad; prec PP_FP32 or PP_TF32);
+ *   2. gw, W, HPWL  pp_wirelength at v with smoothing gamma;
+ *   3. g          pp_place_combine(gw, gn, lambda) with the netlist's cell degrees;
+ *   4. norms      pp_step_norms(v, vp, g, gp);
+ *   5.            pp_nesterov_step(alpha from the norms, else alpha0; coef), in place
+ *                 on u, v, vp, gp;
+ *   6.            pp_overflow of the new u over the first n_overflow blocks on M x M
+ *                 bins with unit charge.
+ * stats (device, 4 doubles) = {overflow excess (as pp_overflow's out), W_LSE, HPWL, E}.
+ * The netlist's cells are the n blocks (fillers are cells without nets); every
+ * block array is float32 device memory of n_cells, movable uint8 or NULL, c NULL
+ * for unit charge.  ws: at least pp_place_workspace_size(args) bytes of 256-byte
+ * aligned device memory.  Errors are those of the calls above, plus PP_EINVAL
+ * for a NULL args or netlist, an unknown density or n_overflow outside [0, n].
+ * Sizes and scalars are checked before any step is issued; each step checks its
+ * own device pointers before its launches, so a bad pointer can stop the call
+ * after earlier steps were issued (u and v change only in step 5). */
+typedef enum { PP_DENSITY_EXACT = 0, PP_DENSITY_BINNED = 1 } pp_density;
+
+typedef struct {
+    const pp_netlist *netlist;
+    double W, H;                        /* die */
+    int32_t M;                          /* modes per axis (exact), bins per axis (binned, overflow) */
+    int32_t density;                    /* pp_density */
+    int32_t prec;                       /* pp_precision of the density term */
+    int32_t reserved;                   /* 0 */
+    int64_t n_overflow;                 /* blocks counted in the overflow: the first n_overflow */
+    const float *w, *h, *c, *q;         /* sizes, charge density (or NULL), c w h */
+    const uint8_t *movable;             /* or NULL: all movable */
+    float *ux, *uy, *vx, *vy;           /* Nesterov solutions u and v (in place) */
+    float *vpx, *vpy, *gpx, *gpy;       /* previous v and g (in place) */
+    float lambda, gamma, alpha0, coef, target;
+    double *stats;
+} pp_place_iteration_args;
+
+/* Workspace bytes of pp_place_iteration (0 for invalid sizes; pp_last_error()
+ * says why).  Reads only the sizes in args and its netlist. */
+size_t pp_place_workspace_size(const pp_place_iteration_args *args);
+pp_status pp_place_iteration(const pp_place_iteration_args *args, void *ws, size_t ws_bytes, void *stream);
+
 /* Failure-path check (no counterpart in the paper).  Launches, on `stream`, one
  * kernel whose thread waits on a shared-memory mbarrier that nothing completes,
  * through the same time-bounded wait the tensor-core kernels use between their

@@ -45,13 +45,24 @@ class Netlist(ctypes.Structure):
                 ("cell_ptr", ctypes.c_void_p), ("cell_net", ctypes.c_void_p)]
 
 
+class PlaceIterationArgs(ctypes.Structure):
+    """pp_place_iteration_args (one placement-loop iteration in one call)."""
+    _fields_ = [("netlist", ctypes.POINTER(Netlist)), ("W", ctypes.c_double), ("H", ctypes.c_double),
+                ("M", ctypes.c_int32), ("density", ctypes.c_int32), ("prec", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("n_overflow", ctypes.c_int64)] + \
+              [(k, ctypes.c_void_p) for k in ("w", "h", "c", "q", "movable", "ux", "uy", "vx", "vy",
+                                              "vpx", "vpy", "gpx", "gpy")] + \
+              [(k, ctypes.c_float) for k in ("lam", "gamma", "alpha0", "coef", "target")] + \
+              [("stats", ctypes.c_void_p)]
+
+
 _LIB = None
 EXPORTS = ("pp_workspace_size", "pp_coeffs", "pp_energy", "pp_grad", "pp_sync_status",
            "pp_last_error", "pp_version", "pp_timing_enable", "pp_timing_collect",
            "pp_grad_noalloc", "pp_phase_eval", "pp_binned_workspace_size", "pp_binned_grad",
            "pp_energy_from_coeffs", "pp_descent_step",
            "pp_wirelength_workspace_size", "pp_wirelength", "pp_place_combine", "pp_step_norms",
-           "pp_nesterov_step", "pp_overflow",
+           "pp_nesterov_step", "pp_overflow", "pp_place_workspace_size", "pp_place_iteration",
            "pp_check_wait_timeout")
 
 
@@ -106,6 +117,11 @@ def lib() -> ctypes.CDLL:
         L.pp_nesterov_step.restype = i
         L.pp_overflow.argtypes = [P, ctypes.c_int32, f32, vp, vp, vp]
         L.pp_overflow.restype = i
+        PA = ctypes.POINTER(PlaceIterationArgs)
+        L.pp_place_workspace_size.argtypes = [PA]
+        L.pp_place_workspace_size.restype = sz
+        L.pp_place_iteration.argtypes = [PA, vp, sz, vp]
+        L.pp_place_iteration.restype = i
         L.pp_check_wait_timeout.argtypes = [ctypes.c_uint64, vp]
         L.pp_check_wait_timeout.restype = i
         L.pp_last_error.argtypes = []
@@ -488,6 +504,37 @@ def nesterov_step(W, H, ux, uy, vx, vy, vpx, vpy, gx, gy, gpx, gpy, w, h, movabl
                                   _ptr(vpx), _ptr(vpy), _ptr(gx), _ptr(gy), _ptr(gpx), _ptr(gpy), _ptr(w),
                                   _ptr(h), _ptr(movable), _ptr(norms), float(alpha0), float(coef),
                                   _stream_handle(ux.device)))
+
+
+DENSITIES = {"exact": 0, "binned": 1}
+
+
+class PlaceIteration:
+    """pp_place_iteration bound to one placement state: the C-ABI argument block,
+    its workspace and the 4-double stats buffer {overflow excess, W_LSE, HPWL, E}.
+    The tensors are referenced, not copied: the call updates u, v, vp, gp in place."""
+
+    def __init__(self, nl: DeviceNetlist, W, H, M: int, density: str, prec: str, n_overflow: int,
+                 w, h, c, q, movable, ux, uy, vx, vy, vpx, vpy, gpx, gpy, target: float = 1.0):
+        self.nl = nl
+        self.keep = (w, h, c, q, movable, ux, uy, vx, vy, vpx, vpy, gpx, gpy)
+        dev = ux.device
+        self.stats = torch.zeros(4, dtype=torch.float64, device=dev)
+        self.a = PlaceIterationArgs(ctypes.pointer(nl.c), float(W), float(H), int(M), DENSITIES[density],
+                                    PRECISIONS[prec], 0, int(n_overflow),
+                                    *[_ptr(t) for t in self.keep], 0.0, 1.0, 0.0, 0.0, float(target),
+                                    _ptr(self.stats))
+        nbytes = lib().pp_place_workspace_size(ctypes.byref(self.a))
+        if nbytes == 0:
+            raise PPError(1, lib().pp_last_error().decode())
+        self.ws = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+
+    def __call__(self, lam: float, gamma: float, coef: float, alpha0: float = 0.0):
+        a = self.a
+        a.lam, a.gamma, a.coef, a.alpha0 = float(lam), float(gamma), float(coef), float(alpha0)
+        _check(lib().pp_place_iteration(ctypes.byref(a), _ptr(self.ws), self.ws.numel(),
+                                        _stream_handle(self.ws.device)))
+        return self.stats
 
 
 def overflow(x, y, w, h, W, H, m: int, target: float = 1.0, bins=None, out=None):

@@ -635,7 +635,7 @@ pp_status pp_step_norms(int64_t n, const float *vx, const float *vy, const float
         const char *names[8] = {"vx", "vy", "vpx", "vpy", "gx", "gy", "gpx", "gpy"};
         if ((st = check_arrays(dev, 8, ptrs, names)) != PP_OK) return st;
     }
-    cudaError_t e = launch_step_norms(n, vx, vy, vpx, vpy, gx, gy, gpx, gpy, norms, (cudaStream_t)stream);
+    cudaError_t e = launch_step_norms(n, vx, vy, vpx, vpy, gx, gy, gpx, gpy, norms, sm, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "step norms launch");
     return PP_OK;
 }
@@ -691,9 +691,97 @@ pp_status pp_overflow(const pp_problem *prob, int32_t m, float target, float *bi
     if (e == cudaSuccess)
         e = launch_bin_density(prob->x, prob->y, prob->w, prob->h, prob->c, (int)prob->n, m, prob->W, prob->H,
                                bins, sm, s);
-    if (e == cudaSuccess) e = launch_overflow(m, bins, target, out, s);
+    if (e == cudaSuccess) e = launch_overflow(m, bins, target, out, sm, s);
     if (e != cudaSuccess) return cuda_fail(e, "overflow launch");
     return PP_OK;
+}
+
+namespace {
+// Scratch of one placement iteration: the density and wirelength workspaces, six
+// float arrays of n (gn, gw, g per axis), the two norms and the M x M bins.
+struct PlaceLayout {
+    size_t dens, dens_bytes, wl, wl_bytes, vec, vec_bytes, norms, bins, total;
+};
+
+size_t round256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+pp_status place_layout(const pp_place_iteration_args *a, PlaceLayout *L) {
+    if (!a) return fail(PP_EINVAL, "args is NULL");
+    if (!a->netlist) return fail(PP_EINVAL, "netlist is NULL");
+    if (a->density != PP_DENSITY_EXACT && a->density != PP_DENSITY_BINNED)
+        return fail(PP_EINVAL, "unknown density %d", (int)a->density);
+    const int64_t n = a->netlist->n_cells;
+    if (n < 0 || a->netlist->n_nets < 0) return fail(PP_EINVAL, "negative netlist sizes");
+    if (a->n_overflow < 0 || a->n_overflow > n)
+        return fail(PP_EINVAL, "n_overflow=%lld outside [0, %lld]", (long long)a->n_overflow, (long long)n);
+    pp_problem prob{a->W, a->H, n, a->vx, a->vy, a->w, a->h, a->c, a->M, a->M};
+    L->dens_bytes = a->density == PP_DENSITY_EXACT ? pp_workspace_size(&prob, (pp_precision)a->prec)
+                                                   : pp_binned_workspace_size(&prob, a->M);
+    if (L->dens_bytes == 0) return PP_EINVAL;           // the size function said why
+    L->wl_bytes = pp_wirelength_workspace_size(a->netlist->n_nets);
+    L->vec_bytes = round256((size_t)n * sizeof(float));
+    L->dens = 0;
+    L->wl = round256(L->dens_bytes);
+    L->vec = L->wl + round256(L->wl_bytes);
+    L->norms = L->vec + 6 * L->vec_bytes;
+    L->bins = L->norms + 256;
+    L->total = L->bins + round256((size_t)a->M * (size_t)a->M * sizeof(float));
+    return PP_OK;
+}
+}  // namespace
+
+size_t pp_place_workspace_size(const pp_place_iteration_args *a) {
+    PlaceLayout L;
+    return place_layout(a, &L) == PP_OK ? L.total : 0;
+}
+
+pp_status pp_place_iteration(const pp_place_iteration_args *a, void *ws, size_t ws_bytes, void *stream) {
+    PlaceLayout L;
+    pp_status st = place_layout(a, &L);
+    if (st != PP_OK) return st;
+    if (!ws || ws_bytes < L.total)
+        return fail(PP_ENOMEM_WS, "workspace of %zu bytes needed, %zu given", L.total, ws ? ws_bytes : (size_t)0);
+    if (((uintptr_t)ws & 255) != 0) return fail(PP_EINVAL, "workspace must be 256-byte aligned");
+    if (!a->stats || ((uintptr_t)a->stats & 7) != 0) return fail(PP_EINVAL, "stats must be 8-byte aligned device memory");
+    // the scalars are checked here, before any step is issued (each step checks its
+    // own device pointers before its launches)
+    if (!(std::isfinite(a->gamma) && a->gamma > 0.f)) return fail(PP_EINVAL, "gamma must be finite and > 0");
+    if (!(std::isfinite(a->lambda) && a->lambda >= 0.f)) return fail(PP_EINVAL, "lambda must be finite and >= 0");
+    if (!(std::isfinite(a->alpha0) && a->alpha0 >= 0.f && std::isfinite(a->coef)))
+        return fail(PP_EINVAL, "alpha0 must be finite and >= 0, coef finite");
+    if (!(std::isfinite(a->target) && a->target >= 0.f)) return fail(PP_EINVAL, "target must be finite and >= 0");
+    if (a->M < 1 || a->M > 8192) return fail(PP_EINVAL, "M=%d must be in [1, 8192]", (int)a->M);
+    const pp_netlist *nl = a->netlist;
+    const int64_t n = nl->n_cells;
+    unsigned char *base = (unsigned char *)ws;
+    float *vec[6];
+    for (int k = 0; k < 6; ++k) vec[k] = (float *)(base + L.vec + k * L.vec_bytes);
+    float *gnx = vec[0], *gny = vec[1], *gwx = vec[2], *gwy = vec[3], *gx = vec[4], *gy = vec[5];
+    double *norms = (double *)(base + L.norms);
+    float *bins = (float *)(base + L.bins);
+    double *stats = a->stats;
+
+    pp_problem prob{a->W, a->H, n, a->vx, a->vy, a->w, a->h, a->c, a->M, a->M};
+    if (a->density == PP_DENSITY_EXACT)
+        st = pp_grad(&prob, (pp_precision)a->prec, PP_RECT, nullptr, gnx, gny, nullptr, stats + 3, base + L.dens,
+                     L.dens_bytes, stream);
+    else
+        st = pp_binned_grad(&prob, (pp_precision)a->prec, a->M, nullptr, gnx, gny, nullptr, stats + 3,
+                            base + L.dens, L.dens_bytes, stream);
+    if (st != PP_OK) return st;
+    if ((st = pp_wirelength(nl, a->vx, a->vy, a->gamma, gwx, gwy, stats + 1, base + L.wl, L.wl_bytes, stream)) !=
+        PP_OK)
+        return st;
+    if ((st = pp_place_combine(n, gwx, gwy, gnx, gny, nl->cell_ptr, a->q, a->movable, a->lambda, gx, gy,
+                               stream)) != PP_OK)
+        return st;
+    if ((st = pp_step_norms(n, a->vx, a->vy, a->vpx, a->vpy, gx, gy, a->gpx, a->gpy, norms, stream)) != PP_OK)
+        return st;
+    if ((st = pp_nesterov_step(n, a->W, a->H, a->ux, a->uy, a->vx, a->vy, a->vpx, a->vpy, gx, gy, a->gpx, a->gpy,
+                               a->w, a->h, a->movable, norms, a->alpha0, a->coef, stream)) != PP_OK)
+        return st;
+    pp_problem over{a->W, a->H, a->n_overflow, a->ux, a->uy, a->w, a->h, nullptr, 1, 1};
+    return pp_overflow(&over, a->M, a->target, bins, stats, stream);
 }
 
 pp_status pp_check_wait_timeout(uint64_t limit_ns, void *stream) {

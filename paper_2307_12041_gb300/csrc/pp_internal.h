@@ -96,8 +96,8 @@ cudaError_t launch_nesterov(int64_t n, float *ux, float *uy, float *vx, float *v
                             float alpha0, float coef, cudaStream_t st);
 cudaError_t launch_step_norms(int64_t n, const float *vx, const float *vy, const float *vpx, const float *vpy,
                               const float *gx, const float *gy, const float *gpx, const float *gpy,
-                              double *norms, cudaStream_t st);
-cudaError_t launch_overflow(int m, const float *P, float target, double *out, cudaStream_t st);
+                              double *norms, int sm_count, cudaStream_t st);
+cudaError_t launch_overflow(int m, const float *P, float target, double *out, int sm_count, cudaStream_t st);
 
 // pp_simt.cu
 cudaError_t launch_prep(const Launch &L, bool zero_S, double *e_total);

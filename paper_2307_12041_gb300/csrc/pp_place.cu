@@ -137,8 +137,15 @@ __global__ void nesterov_kernel(int64_t n, float *__restrict__ ux, float *__rest
                                 const uint8_t *__restrict__ movable, const double *__restrict__ norms,
                                 float alpha0, float coef) {
     // step length: |v - v_prev| / |g - g_prev| from the previous iteration, else alpha0
-    float alpha = alpha0;
-    if (norms && norms[1] > 0.0 && norms[0] > 0.0) alpha = (float)sqrt(norms[0] / norms[1]);
+    // (once per CTA: FP64 division and square root are slow on this GPU)
+    __shared__ float s_alpha;
+    if (threadIdx.x == 0) {
+        float al = alpha0;
+        if (norms && norms[1] > 0.0 && norms[0] > 0.0) al = (float)sqrt(norms[0] / norms[1]);
+        s_alpha = al;
+    }
+    __syncthreads();
+    const float alpha = s_alpha;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const float vxi = vx[i], vyi = vy[i], gxi = gx[i], gyi = gy[i];
         vpx[i] = vxi;
@@ -199,10 +206,11 @@ cudaError_t launch_combine(int64_t n, const float *gwx, const float *gwy, const 
 
 cudaError_t launch_step_norms(int64_t n, const float *vx, const float *vy, const float *vpx, const float *vpy,
                               const float *gx, const float *gy, const float *gpx, const float *gpy,
-                              double *norms, cudaStream_t st) {
+                              double *norms, int sm_count, cudaStream_t st) {
     cudaError_t e = cudaMemsetAsync(norms, 0, 2 * sizeof(double), st);
     if (e != cudaSuccess || n <= 0) return e;
-    step_norms_kernel<<<grid_for(n, 1024), 256, 0, st>>>(n, vx, vy, vpx, vpy, gx, gy, gpx, gpy, norms);
+    // two CTAs per SM, grid-stride: few same-address FP64 atomics at the end
+    step_norms_kernel<<<grid_for(n, 2 * sm_count), 256, 0, st>>>(n, vx, vy, vpx, vpy, gx, gy, gpx, gpy, norms);
     return cudaGetLastError();
 }
 
@@ -216,11 +224,11 @@ cudaError_t launch_nesterov(int64_t n, float *ux, float *uy, float *vx, float *v
     return cudaGetLastError();
 }
 
-cudaError_t launch_overflow(int m, const float *P, float target, double *out, cudaStream_t st) {
+cudaError_t launch_overflow(int m, const float *P, float target, double *out, int sm_count, cudaStream_t st) {
     cudaError_t e = cudaMemsetAsync(out, 0, sizeof(double), st);
     if (e != cudaSuccess) return e;
     const int64_t cells = (int64_t)m * m;
-    overflow_kernel<<<grid_for(cells, 1024), 256, 0, st>>>(cells, P, target, out);
+    overflow_kernel<<<grid_for(cells, 2 * sm_count), 256, 0, st>>>(cells, P, target, out);
     return cudaGetLastError();
 }
 

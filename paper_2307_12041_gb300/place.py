@@ -57,11 +57,14 @@ def gamma_of(tau: float, bin_w: float) -> float:
 class Placer:
     """The loop's state on the device (major and reference solutions u, v, the
     previous v and gradient, the netlist, the bins) and its scalars (lambda,
-    gamma, a_k); step() runs one iteration and returns its record."""
+    gamma, a_k); step() runs one iteration and returns its record.  After the
+    first iteration (whose lambda_0 and step length need host reductions) each
+    step is one library call, pp_place_iteration, and one 32-byte read-back;
+    fused=False issues the same kernels through the separate entry points."""
 
     def __init__(self, p: synth.Placement, net_ptr, net_pin, prec: str = "tf32", target: float = 1.0,
                  d_hpwl_frac: float = 3.5e-3, device="cuda", density: str = "exact", fillers: bool = False,
-                 filler_seed: int = synth.BASE_SEED + 99):
+                 filler_seed: int = synth.BASE_SEED + 99, fused: bool = True):
         if density not in ("exact", "binned"):
             raise ValueError("density must be 'exact' or 'binned'")
         dev = torch.device(device)
@@ -90,6 +93,7 @@ class Placer:
         self.tau = float(ovf.item()) * self.bin_area / self.area_mov
         self.gamma = gamma_of(self.tau, self.bin_w)
         self.lam, self.a_k, self.hp_prev, self.d_ref, self.k = None, 1.0, None, None, 0
+        self.fused, self._it = fused, None
 
     def overflow_now(self):
         nr = self.n_real
@@ -97,31 +101,47 @@ class Placer:
                                   self.M, self.target, bins=self.bins)
         return ovf
 
+    def _fused(self) -> binding.PlaceIteration:
+        if self._it is None:
+            p = self.p
+            dprec = self.prec if self.density == "exact" else ("fp32" if self.prec == "fp32" else "tf32")
+            self._it = binding.PlaceIteration(self.nl, p.W, p.H, self.M, self.density, dprec, self.n_real,
+                                              self.w, self.h, self.c, self.q, self.mov, self.ux, self.uy,
+                                              self.vx, self.vy, self.vpx, self.vpy, self.gpx, self.gpy,
+                                              self.target)
+        return self._it
+
     def step(self) -> dict:
         p, M, k = self.p, self.M, self.k
-        if self.density == "exact":
-            gnx, gny, _, E = binding.grad(self.vx, self.vy, self.w, self.h, self.c, p.W, p.H, M, M, self.prec)
-        else:                                 # binned scheme: bins = modes per axis (K = m - 1)
-            bprec = "fp32" if self.prec == "fp32" else "tf32"
-            gnx, gny, _, E, _ = binding.binned_grad(self.vx, self.vy, self.w, self.h, self.c, p.W, p.H, M, M, M,
-                                                    bprec, want_coeffs=False)
-        gwx, gwy, wl = binding.wirelength(self.nl, self.vx, self.vy, self.gamma)
-        if self.lam is None:                  # lambda_0: ratio of the L1 gradient norms
-            self.lam = float((gwx.abs().sum() + gwy.abs().sum()) / (gnx.abs().sum() + gny.abs().sum()))
-        gx, gy = binding.place_combine(gwx, gwy, gnx, gny, self.nl.cell_ptr, self.q, self.mov, self.lam)
-        if k > 0:
-            binding.step_norms(self.vx, self.vy, self.vpx, self.vpy, gx, gy, self.gpx, self.gpy, self.norms)
-            alpha0 = 0.0
-        else:                                 # first step: the largest gradient moves one bin
-            gmax = float(torch.maximum(gx.abs().max(), gy.abs().max()))
-            alpha0 = self.bin_w / gmax if gmax > 0 else 0.0
         a_next = (1.0 + math.sqrt(4.0 * self.a_k * self.a_k + 1.0)) / 2.0
-        binding.nesterov_step(p.W, p.H, self.ux, self.uy, self.vx, self.vy, self.vpx, self.vpy, gx, gy,
-                              self.gpx, self.gpy, self.w, self.h, self.mov, self.norms if k > 0 else None,
-                              alpha0, (self.a_k - 1.0) / a_next)
+        coef = (self.a_k - 1.0) / a_next
+        if k > 0 and self.fused:              # one library call for the whole iteration
+            s = self._fused()(self.lam, self.gamma, coef).cpu()     # the one read-back of the iteration
+        else:
+            if self.density == "exact":
+                gnx, gny, _, E = binding.grad(self.vx, self.vy, self.w, self.h, self.c, p.W, p.H, M, M,
+                                              self.prec)
+            else:                             # binned scheme: bins = modes per axis (K = m - 1)
+                bprec = "fp32" if self.prec == "fp32" else "tf32"
+                gnx, gny, _, E, _ = binding.binned_grad(self.vx, self.vy, self.w, self.h, self.c, p.W, p.H, M,
+                                                        M, M, bprec, want_coeffs=False)
+            gwx, gwy, wl = binding.wirelength(self.nl, self.vx, self.vy, self.gamma)
+            if self.lam is None:              # lambda_0: ratio of the L1 gradient norms
+                self.lam = float((gwx.abs().sum() + gwy.abs().sum()) / (gnx.abs().sum() + gny.abs().sum()))
+            gx, gy = binding.place_combine(gwx, gwy, gnx, gny, self.nl.cell_ptr, self.q, self.mov, self.lam)
+            if k > 0:
+                binding.step_norms(self.vx, self.vy, self.vpx, self.vpy, gx, gy, self.gpx, self.gpy,
+                                   self.norms)
+                alpha0 = 0.0
+            else:                             # first step: the largest gradient moves one bin
+                gmax = float(torch.maximum(gx.abs().max(), gy.abs().max()))
+                alpha0 = self.bin_w / gmax if gmax > 0 else 0.0
+            binding.nesterov_step(p.W, p.H, self.ux, self.uy, self.vx, self.vy, self.vpx, self.vpy, gx, gy,
+                                  self.gpx, self.gpy, self.w, self.h, self.mov,
+                                  self.norms if k > 0 else None, alpha0, coef)
+            ovf = self.overflow_now()
+            s = torch.cat([ovf, wl, E.reshape(1)]).cpu()    # the one read-back of the iteration
         self.a_k = a_next
-        ovf = self.overflow_now()
-        s = torch.cat([ovf, wl, E.reshape(1)]).cpu()        # the one read-back of the iteration
         self.tau = float(s[0]) * self.bin_area / self.area_mov
         rec = {"k": k, "tau": self.tau, "W_lse": float(s[1]), "hpwl": float(s[2]), "E": float(s[3]),
                "lambda": self.lam, "gamma": self.gamma}
@@ -161,10 +181,10 @@ def with_fillers(p: synth.Placement, target: float, seed: int) -> synth.Placemen
 def place(p: synth.Placement, net_ptr, net_pin, iters: int = 200, prec: str = "tf32",
           tau_stop: float = 0.1, target: float = 1.0, d_hpwl_frac: float = 3.5e-3,
           device="cuda", callback: Optional[Callable] = None, density: str = "exact",
-          fillers: bool = False) -> PlaceResult:
+          fillers: bool = False, fused: bool = True) -> PlaceResult:
     """Run up to `iters` iterations; callback(k, rec, x_eval, y_eval, ux, uy) after
     each, with the positions at which W_LSE and E of `rec` were evaluated."""
-    pl = Placer(p, net_ptr, net_pin, prec, target, d_hpwl_frac, device, density, fillers)
+    pl = Placer(p, net_ptr, net_pin, prec, target, d_hpwl_frac, device, density, fillers, fused=fused)
     res = PlaceResult()
     dev = torch.device(device)
     torch.cuda.synchronize(dev)
@@ -198,16 +218,19 @@ def _main(argv=None) -> int:
     ap.add_argument("--seed", type=int, default=synth.BASE_SEED + 10)
     ap.add_argument("--density", choices=["exact", "binned"], default="exact")
     ap.add_argument("--fillers", action="store_true")
+    ap.add_argument("--unfused", action="store_true", help="one entry point per step of an iteration")
     a = ap.parse_args(argv)
     p = synth.placement_cells(a.n, a.modes, a.seed)
     ptr, pins = synth.netlist(a.n, a.seed + 1)
-    place(p, ptr, pins, iters=3, prec=a.prec, density=a.density, fillers=a.fillers)      # warm-up
-    r = place(p, ptr, pins, iters=a.iters, prec=a.prec, density=a.density, fillers=a.fillers)
+    kw = dict(prec=a.prec, density=a.density, fillers=a.fillers, fused=not a.unfused)
+    place(p, ptr, pins, iters=3, **kw)      # warm-up
+    r = place(p, ptr, pins, iters=a.iters, **kw)
     t = r.trace
     pick = [t[i] for i in range(0, len(t), max(1, len(t) // 10))] + [t[-1]]
     print(json.dumps({
         "workload": p.name, "n": p.n, "nets": len(ptr) - 1, "pins": int(len(pins)), "modes": a.modes,
-        "precision": a.prec, "density": a.density, "fillers": a.fillers, "iterations": r.iterations,
+        "precision": a.prec, "density": a.density, "fillers": a.fillers, "fused": not a.unfused,
+        "iterations": r.iterations,
         "ms_per_iter": r.ms_per_iter,
         "density_terms_per_s": p.n * a.modes * a.modes / (r.ms_per_iter / 1e3),
         "tau_first": t[0]["tau"], "tau_last": t[-1]["tau"], "hpwl_first": t[0]["hpwl"],

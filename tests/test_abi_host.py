@@ -77,3 +77,27 @@ def test_calls_reject_bad_problems_before_any_launch(L):
 def test_version_string(L):
     v = L.pp_version().decode()
     assert "sm_103a" in v
+
+
+def test_place_workspace_size_host_only(L):
+    """pp_place_workspace_size reads sizes only: it grows with the blocks and the
+    modes and rejects bad densities, overflow counts and mode counts."""
+    from paper_2307_12041_gb300.binding import Netlist, PlaceIterationArgs
+    nl = Netlist(1000, 300, None, None, None, None)
+
+    def size(n_cells=1000, **kw):
+        nl.n_cells = n_cells
+        d = dict(W=1.0, H=1.0, M=64, density=0, prec=0, n_overflow=min(1000, n_cells))
+        d.update(kw)
+        a = PlaceIterationArgs(ctypes.pointer(nl), d["W"], d["H"], d["M"], d["density"], d["prec"], 0,
+                               d["n_overflow"])
+        return L.pp_place_workspace_size(ctypes.byref(a))
+
+    base = size()
+    assert base > 0 and size(n_cells=2000) > base and size(M=128) > base
+    assert size(density=1) > 0 and size(prec=1) > 0
+    for bad in (dict(density=2), dict(n_overflow=1001), dict(n_overflow=-1), dict(M=0), dict(W=0.0),
+                dict(density=1, M=1)):
+        assert size(**bad) == 0, bad
+        assert L.pp_last_error().decode() != ""
+    assert L.pp_place_workspace_size(None) == 0

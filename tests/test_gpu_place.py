@@ -194,3 +194,64 @@ def test_place_entry_points_reject_bad_arguments(pp):
         pp.binding.overflow(x, x.clone(), w, w.clone(), 1.0, 1.0, 16, target=-1.0)
     with pytest.raises(pp.binding.PPError):
         pp.binding.place_combine(x, x, x, x, None, w, None, -1.0)
+
+
+STATE = ("ux", "uy", "vx", "vy", "vpx", "vpy", "gpx", "gpy")
+
+
+@pytest.mark.parametrize("density", ["exact", "binned"])
+def test_fused_iteration_matches_separate_calls(pp, density):
+    """pp_place_iteration issues the same kernels in the same order as the separate
+    entry points.  Two placers, one fused and one not, start each iteration from the
+    same state (copied over, since the FP64 sums inside the kernels are summed in
+    an order that varies from run to run); the iteration's records and new state
+    then agree to rounding."""
+    n, M = 8000, 64
+    p = synth.placement_cells(n, M, 61)
+    ptr, pins = synth.netlist(n, 62)
+    A = place.Placer(p, ptr, pins, "fp32", density=density, fused=True)
+    B = place.Placer(p, ptr, pins, "fp32", density=density, fused=False)
+    A.step(), B.step()                                   # the first iteration: the same path in both
+    for k in range(1, 7):
+        for name in STATE:
+            getattr(A, name).copy_(getattr(B, name))
+        A.lam, A.gamma, A.a_k, A.hp_prev, A.d_ref = B.lam, B.gamma, B.a_k, B.hp_prev, B.d_ref
+        ra, rb = A.step(), B.step()
+        for key in ("tau", "W_lse", "hpwl", "E", "lambda", "gamma"):
+            assert ra[key] == pytest.approx(rb[key], rel=1e-6, abs=1e-12), (k, key, ra[key], rb[key])
+        for name in ("ux", "uy", "vx", "vy"):
+            d = (getattr(A, name) - getattr(B, name)).abs().max().item()
+            assert d <= 1e-6, (k, name, d)
+        for name in ("vpx", "vpy"):                       # v of the evaluation, saved as is
+            assert torch.equal(getattr(A, name), getattr(B, name)), (k, name)
+        for name in ("gpx", "gpy"):
+            a, b = getattr(A, name), getattr(B, name)
+            d = (a - b).abs().max().item()
+            assert d <= 1e-5 * b.abs().max().item(), (k, name, d)
+    assert A._it is not None and B._it is None
+
+
+def test_fused_iteration_rejects_bad_arguments(pp):
+    n, M = 500, 32
+    p = synth.placement_cells(n, M, 71)
+    ptr, pins = synth.netlist(n, 72)
+    pl = place.Placer(p, ptr, pins, "fp32")
+    pl.step()
+    it = pl._fused()
+    it(pl.lam, pl.gamma, 0.1)
+    torch.cuda.synchronize()
+    b, a = pp.binding, it.a
+    with pytest.raises(b.PPError):                       # workspace too small
+        b._check(b.lib().pp_place_iteration(b.ctypes.byref(a), it.ws.data_ptr(), it.ws.numel() - 256, None))
+    for field, bad in (("density", 7), ("n_overflow", n + 1), ("n_overflow", -1), ("M", 0)):
+        old = getattr(a, field)
+        setattr(a, field, bad)
+        try:
+            assert b.lib().pp_place_workspace_size(b.ctypes.byref(a)) == 0, field
+            with pytest.raises(b.PPError):
+                b._check(b.lib().pp_place_iteration(b.ctypes.byref(a), it.ws.data_ptr(), it.ws.numel(), None))
+        finally:
+            setattr(a, field, old)
+    with pytest.raises(b.PPError):                       # gamma must be > 0 (pp_wirelength's check)
+        it(pl.lam, 0.0, 0.1)
+    b.sync_status()
