@@ -229,7 +229,10 @@ def time_steps(binding, p, dev_in, prec, steps, warmup, flush, outs, kernel_timi
     elif mode == "place":        # one iteration of the Sec. IV loop per step (the loop's state carries over)
         from paper_2307_12041_gb300 import place as placemod, synth
         ptr, pins = synth.netlist(p.n, synth.BASE_SEED + 11)
-        placer = placemod.Placer(p, ptr, pins, prec)
+        # the fused library call per iteration, not its CUDA-graph replay: the library
+        # counts launches as they are issued, and a replay issues none from the host
+        # (for this exact-density loop the two take the same time per iteration)
+        placer = placemod.Placer(p, ptr, pins, prec, graph=False)
         run = placer.step
     elif mode == "binned":
         m = max(p.Mx, p.My) if bins is None else bins

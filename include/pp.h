@@ -292,7 +292,10 @@ pp_status pp_overflow(const pp_problem *prob, int32_t m, float target, float *bi
  * for a NULL args or netlist, an unknown density or n_overflow outside [0, n].
  * Sizes and scalars are checked before any step is issued; each step checks its
  * own device pointers before its launches, so a bad pointer can stop the call
- * after earlier steps were issued (u and v change only in step 5). */
+ * after earlier steps were issued (u and v change only in step 5).  With
+ * `scalars` set, the work of one call depends on nothing but device memory, so
+ * the call can be captured once in a CUDA graph and replayed every iteration
+ * after the four scalars are written to the device. */
 typedef enum { PP_DENSITY_EXACT = 0, PP_DENSITY_BINNED = 1 } pp_density;
 
 typedef struct {
@@ -309,6 +312,9 @@ typedef struct {
     float *vpx, *vpy, *gpx, *gpy;       /* previous v and g (in place) */
     float lambda, gamma, alpha0, coef, target;
     double *stats;
+    const float *scalars;               /* NULL, or device float[4] {lambda, gamma, alpha0, coef}
+                                           read by the kernels as they run, in place of the
+                                           fields above (16-byte aligned; not range-checked) */
 } pp_place_iteration_args;
 
 /* Workspace bytes of pp_place_iteration (0 for invalid sizes; pp_last_error()

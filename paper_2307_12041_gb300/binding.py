@@ -7,6 +7,7 @@ missing or a call fails, an exception is raised.
 from __future__ import annotations
 
 import ctypes
+import math
 import os
 from typing import Optional
 
@@ -53,7 +54,7 @@ class PlaceIterationArgs(ctypes.Structure):
               [(k, ctypes.c_void_p) for k in ("w", "h", "c", "q", "movable", "ux", "uy", "vx", "vy",
                                               "vpx", "vpy", "gpx", "gpy")] + \
               [(k, ctypes.c_float) for k in ("lam", "gamma", "alpha0", "coef", "target")] + \
-              [("stats", ctypes.c_void_p)]
+              [("stats", ctypes.c_void_p), ("scalars", ctypes.c_void_p)]
 
 
 _LIB = None
@@ -512,10 +513,17 @@ DENSITIES = {"exact": 0, "binned": 1}
 class PlaceIteration:
     """pp_place_iteration bound to one placement state: the C-ABI argument block,
     its workspace and the 4-double stats buffer {overflow excess, W_LSE, HPWL, E}.
-    The tensors are referenced, not copied: the call updates u, v, vp, gp in place."""
+    The tensors are referenced, not copied: the call updates u, v, vp, gp in place.
+
+    graph=True: the scalars live in a device array the kernels read as they run, the
+    call is captured once in a CUDA graph, and every later call writes the four
+    scalars to the device and replays the graph (no per-call argument checks or
+    launches on the host).  The captured call keeps the workspace, state and stats
+    pointers, so none of those tensors may be reallocated."""
 
     def __init__(self, nl: DeviceNetlist, W, H, M: int, density: str, prec: str, n_overflow: int,
-                 w, h, c, q, movable, ux, uy, vx, vy, vpx, vpy, gpx, gpy, target: float = 1.0):
+                 w, h, c, q, movable, ux, uy, vx, vy, vpx, vpy, gpx, gpy, target: float = 1.0,
+                 graph: bool = False):
         self.nl = nl
         self.keep = (w, h, c, q, movable, ux, uy, vx, vy, vpx, vpy, gpx, gpy)
         dev = ux.device
@@ -523,17 +531,52 @@ class PlaceIteration:
         self.a = PlaceIterationArgs(ctypes.pointer(nl.c), float(W), float(H), int(M), DENSITIES[density],
                                     PRECISIONS[prec], 0, int(n_overflow),
                                     *[_ptr(t) for t in self.keep], 0.0, 1.0, 0.0, 0.0, float(target),
-                                    _ptr(self.stats))
+                                    _ptr(self.stats), None)
         nbytes = lib().pp_place_workspace_size(ctypes.byref(self.a))
         if nbytes == 0:
             raise PPError(1, lib().pp_last_error().decode())
         self.ws = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+        self.graph, self.graph_error, self.scal_dev = None, None, None
+        if graph:
+            self.scal_dev = torch.zeros(4, dtype=torch.float32, device=dev)
+            self.a.scalars = _ptr(self.scal_dev)
+
+    def _call(self):
+        _check(lib().pp_place_iteration(ctypes.byref(self.a), _ptr(self.ws), self.ws.numel(),
+                                        _stream_handle(self.ws.device)))
 
     def __call__(self, lam: float, gamma: float, coef: float, alpha0: float = 0.0):
         a = self.a
         a.lam, a.gamma, a.coef, a.alpha0 = float(lam), float(gamma), float(coef), float(alpha0)
-        _check(lib().pp_place_iteration(ctypes.byref(a), _ptr(self.ws), self.ws.numel(),
-                                        _stream_handle(self.ws.device)))
+        if self.scal_dev is None:
+            self._call()
+            return self.stats
+        if not (math.isfinite(lam) and lam >= 0 and math.isfinite(gamma) and gamma > 0
+                and math.isfinite(alpha0) and alpha0 >= 0 and math.isfinite(coef)):
+            raise PPError(1, "lambda, gamma, alpha0 must be finite (lambda, alpha0 >= 0, gamma > 0), coef finite")
+        dev = self.ws.device
+        if self.graph is None:          # capture once (nothing runs during the capture)
+            g = torch.cuda.CUDAGraph()
+            main = torch.cuda.current_stream(dev)
+            side = torch.cuda.Stream(device=dev)
+            side.wait_stream(main)
+            try:
+                with torch.cuda.graph(g, stream=side):
+                    self._call()
+            except Exception as e:      # keep the eager call (same kernels) and say why
+                torch.cuda.set_stream(main)
+                self.graph_error = f"{type(e).__name__}: {e}"
+                self.a.scalars = None
+                self.scal_dev = None
+                main.wait_stream(side)
+                self._call()
+                return self.stats
+            main.wait_stream(side)
+            self.graph = g
+        # a pinned staging tensor per call: the host allocator keeps it until the copy is done
+        src = torch.tensor([lam, gamma, alpha0, coef], dtype=torch.float32).pin_memory()
+        self.scal_dev.copy_(src, non_blocking=True)
+        self.graph.replay()
         return self.stats
 
 

@@ -572,14 +572,18 @@ size_t pp_wirelength_workspace_size(int32_t n_nets) {
     return n_nets <= 0 ? 256 : ((size_t)n_nets * 32 + 255) & ~(size_t)255;
 }
 
-pp_status pp_wirelength(const pp_netlist *nl, const float *x, const float *y, float gamma, float *gx, float *gy,
-                        double *out, void *ws, size_t ws_bytes, void *stream) {
+namespace {
+// The entry points of the loop with their scalars optionally on the device (`scal`,
+// {lambda, gamma, alpha0, coef}, read by the kernels when they run); a by-value
+// scalar is checked only when scal is NULL.
+pp_status wirelength_impl(const pp_netlist *nl, const float *x, const float *y, float gamma, const float *scal,
+                          float *gx, float *gy, double *out, void *ws, size_t ws_bytes, void *stream) {
     int dev, sm, ccm;
     unsigned *status;
     pp_status st = device_info(&dev, &sm, &status, &ccm);
     if (st != PP_OK) return st;
     if ((st = check_netlist(nl, dev)) != PP_OK) return st;
-    if (!(std::isfinite(gamma) && gamma > 0.f)) return fail(PP_EINVAL, "gamma must be finite and > 0");
+    if (!scal && !(std::isfinite(gamma) && gamma > 0.f)) return fail(PP_EINVAL, "gamma must be finite and > 0");
     const size_t need = pp_wirelength_workspace_size(nl->n_nets);
     if (!ws || ws_bytes < need)
         return fail(PP_ENOMEM_WS, "workspace of %zu bytes needed, %zu given", need, ws ? ws_bytes : (size_t)0);
@@ -593,32 +597,59 @@ pp_status pp_wirelength(const pp_netlist *nl, const float *x, const float *y, fl
         if ((st = check_arrays(dev, 4, ptrs, names)) != PP_OK) return st;
     }
     cudaError_t e = launch_wirelength(nl->n_nets, nl->n_cells, nl->net_ptr, nl->net_pin, nl->cell_ptr,
-                                      nl->cell_net, x, y, gamma, (float *)ws, gx, gy, out, sm,
+                                      nl->cell_net, x, y, gamma, scal, (float *)ws, gx, gy, out, sm,
                                       (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "wirelength launch");
     return PP_OK;
 }
 
-pp_status pp_place_combine(int64_t n, const float *gwx, const float *gwy, const float *gnx, const float *gny,
-                           const int32_t *cell_ptr, const float *q, const uint8_t *movable, float lambda,
-                           float *gx, float *gy, void *stream) {
+pp_status combine_impl(int64_t n, const float *gwx, const float *gwy, const float *gnx, const float *gny,
+                       const int32_t *cell_ptr, const float *q, const uint8_t *movable, float lambda,
+                       const float *scal, float *gx, float *gy, void *stream) {
     int dev, sm, ccm;
     unsigned *status;
     pp_status st = device_info(&dev, &sm, &status, &ccm);
     if (st != PP_OK) return st;
     if (n < 0 || n > INT64_C(0x7FFFFFFF)) return fail(PP_EINVAL, "n=%lld out of range", (long long)n);
-    if (!(std::isfinite(lambda) && lambda >= 0.f)) return fail(PP_EINVAL, "lambda must be finite and >= 0");
+    if (!scal && !(std::isfinite(lambda) && lambda >= 0.f))
+        return fail(PP_EINVAL, "lambda must be finite and >= 0");
     if (n == 0) return PP_OK;
     const void *ptrs[7] = {gwx, gwy, gnx, gny, q, gx, gy};
     const char *names[7] = {"gwx", "gwy", "gnx", "gny", "q", "gx", "gy"};
     if ((st = check_arrays(dev, 7, ptrs, names)) != PP_OK) return st;
     if (cell_ptr && (st = check_dev_ptr(cell_ptr, dev, "cell_ptr")) != PP_OK) return st;
     if (movable && (st = check_dev_ptr(movable, dev, "movable")) != PP_OK) return st;
-    cudaError_t e = launch_combine(n, gwx, gwy, gnx, gny, cell_ptr, q, movable, lambda, gx, gy,
+    cudaError_t e = launch_combine(n, gwx, gwy, gnx, gny, cell_ptr, q, movable, lambda, scal, gx, gy,
                                    (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "combine launch");
     return PP_OK;
 }
+
+pp_status nesterov_impl(int64_t n, double W, double H, float *ux, float *uy, float *vx, float *vy, float *vpx,
+                        float *vpy, const float *gx, const float *gy, float *gpx, float *gpy, const float *w,
+                        const float *h, const uint8_t *movable, const double *norms, float alpha0, float coef,
+                        const float *scal, void *stream) {
+    int dev, sm, ccm;
+    unsigned *status;
+    pp_status st = device_info(&dev, &sm, &status, &ccm);
+    if (st != PP_OK) return st;
+    if (!(std::isfinite(W) && std::isfinite(H) && W >= 1e-300 && W <= 1e300 && H >= 1e-300 && H <= 1e300))
+        return fail(PP_EINVAL, "die size W=%g H=%g must be finite and in [1e-300, 1e300]", W, H);
+    if (n < 0 || n > INT64_C(0x7FFFFFFF)) return fail(PP_EINVAL, "n=%lld out of range", (long long)n);
+    if (!scal && !(std::isfinite(alpha0) && alpha0 >= 0.f && std::isfinite(coef)))
+        return fail(PP_EINVAL, "alpha0 must be finite and >= 0, coef finite");
+    if (n == 0) return PP_OK;
+    const void *ptrs[12] = {ux, uy, vx, vy, vpx, vpy, gx, gy, gpx, gpy, w, h};
+    const char *names[12] = {"ux", "uy", "vx", "vy", "vpx", "vpy", "gx", "gy", "gpx", "gpy", "w", "h"};
+    if ((st = check_arrays(dev, 12, ptrs, names)) != PP_OK) return st;
+    if (movable && (st = check_dev_ptr(movable, dev, "movable")) != PP_OK) return st;
+    if (norms && (st = check_dev_ptr(norms, dev, "norms")) != PP_OK) return st;
+    cudaError_t e = launch_nesterov(n, ux, uy, vx, vy, vpx, vpy, gx, gy, gpx, gpy, w, h, (float)W, (float)H,
+                                    movable, norms, alpha0, coef, scal, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "Nesterov step launch");
+    return PP_OK;
+}
+}  // namespace
 
 pp_status pp_step_norms(int64_t n, const float *vx, const float *vy, const float *vpx, const float *vpy,
                         const float *gx, const float *gy, const float *gpx, const float *gpy, double *norms,
@@ -640,29 +671,23 @@ pp_status pp_step_norms(int64_t n, const float *vx, const float *vy, const float
     return PP_OK;
 }
 
+pp_status pp_wirelength(const pp_netlist *nl, const float *x, const float *y, float gamma, float *gx, float *gy,
+                        double *out, void *ws, size_t ws_bytes, void *stream) {
+    return wirelength_impl(nl, x, y, gamma, nullptr, gx, gy, out, ws, ws_bytes, stream);
+}
+
+pp_status pp_place_combine(int64_t n, const float *gwx, const float *gwy, const float *gnx, const float *gny,
+                           const int32_t *cell_ptr, const float *q, const uint8_t *movable, float lambda,
+                           float *gx, float *gy, void *stream) {
+    return combine_impl(n, gwx, gwy, gnx, gny, cell_ptr, q, movable, lambda, nullptr, gx, gy, stream);
+}
+
 pp_status pp_nesterov_step(int64_t n, double W, double H, float *ux, float *uy, float *vx, float *vy, float *vpx,
                            float *vpy, const float *gx, const float *gy, float *gpx, float *gpy, const float *w,
                            const float *h, const uint8_t *movable, const double *norms, float alpha0,
                            float coef, void *stream) {
-    int dev, sm, ccm;
-    unsigned *status;
-    pp_status st = device_info(&dev, &sm, &status, &ccm);
-    if (st != PP_OK) return st;
-    if (!(std::isfinite(W) && std::isfinite(H) && W >= 1e-300 && W <= 1e300 && H >= 1e-300 && H <= 1e300))
-        return fail(PP_EINVAL, "die size W=%g H=%g must be finite and in [1e-300, 1e300]", W, H);
-    if (n < 0 || n > INT64_C(0x7FFFFFFF)) return fail(PP_EINVAL, "n=%lld out of range", (long long)n);
-    if (!(std::isfinite(alpha0) && alpha0 >= 0.f && std::isfinite(coef)))
-        return fail(PP_EINVAL, "alpha0 must be finite and >= 0, coef finite");
-    if (n == 0) return PP_OK;
-    const void *ptrs[12] = {ux, uy, vx, vy, vpx, vpy, gx, gy, gpx, gpy, w, h};
-    const char *names[12] = {"ux", "uy", "vx", "vy", "vpx", "vpy", "gx", "gy", "gpx", "gpy", "w", "h"};
-    if ((st = check_arrays(dev, 12, ptrs, names)) != PP_OK) return st;
-    if (movable && (st = check_dev_ptr(movable, dev, "movable")) != PP_OK) return st;
-    if (norms && (st = check_dev_ptr(norms, dev, "norms")) != PP_OK) return st;
-    cudaError_t e = launch_nesterov(n, ux, uy, vx, vy, vpx, vpy, gx, gy, gpx, gpy, w, h, (float)W, (float)H,
-                                    movable, norms, alpha0, coef, (cudaStream_t)stream);
-    if (e != cudaSuccess) return cuda_fail(e, "Nesterov step launch");
-    return PP_OK;
+    return nesterov_impl(n, W, H, ux, uy, vx, vy, vpx, vpy, gx, gy, gpx, gpy, w, h, movable, norms, alpha0, coef,
+                         nullptr, stream);
 }
 
 pp_status pp_overflow(const pp_problem *prob, int32_t m, float target, float *bins, double *out, void *stream) {
@@ -744,11 +769,22 @@ pp_status pp_place_iteration(const pp_place_iteration_args *a, void *ws, size_t 
     if (((uintptr_t)ws & 255) != 0) return fail(PP_EINVAL, "workspace must be 256-byte aligned");
     if (!a->stats || ((uintptr_t)a->stats & 7) != 0) return fail(PP_EINVAL, "stats must be 8-byte aligned device memory");
     // the scalars are checked here, before any step is issued (each step checks its
-    // own device pointers before its launches)
-    if (!(std::isfinite(a->gamma) && a->gamma > 0.f)) return fail(PP_EINVAL, "gamma must be finite and > 0");
-    if (!(std::isfinite(a->lambda) && a->lambda >= 0.f)) return fail(PP_EINVAL, "lambda must be finite and >= 0");
-    if (!(std::isfinite(a->alpha0) && a->alpha0 >= 0.f && std::isfinite(a->coef)))
-        return fail(PP_EINVAL, "alpha0 must be finite and >= 0, coef finite");
+    // own device pointers before its launches); scalars on the device are read by the
+    // kernels as they run and cannot be checked here
+    const float *scal = a->scalars;
+    if (scal) {
+        if (((uintptr_t)scal & 15) != 0) return fail(PP_EINVAL, "scalars must be 16-byte aligned");
+        int dev, sm, ccm;
+        unsigned *status;
+        if ((st = device_info(&dev, &sm, &status, &ccm)) != PP_OK) return st;
+        if ((st = check_dev_ptr(scal, dev, "scalars")) != PP_OK) return st;
+    } else {
+        if (!(std::isfinite(a->gamma) && a->gamma > 0.f)) return fail(PP_EINVAL, "gamma must be finite and > 0");
+        if (!(std::isfinite(a->lambda) && a->lambda >= 0.f))
+            return fail(PP_EINVAL, "lambda must be finite and >= 0");
+        if (!(std::isfinite(a->alpha0) && a->alpha0 >= 0.f && std::isfinite(a->coef)))
+            return fail(PP_EINVAL, "alpha0 must be finite and >= 0, coef finite");
+    }
     if (!(std::isfinite(a->target) && a->target >= 0.f)) return fail(PP_EINVAL, "target must be finite and >= 0");
     if (a->M < 1 || a->M > 8192) return fail(PP_EINVAL, "M=%d must be in [1, 8192]", (int)a->M);
     const pp_netlist *nl = a->netlist;
@@ -769,16 +805,16 @@ pp_status pp_place_iteration(const pp_place_iteration_args *a, void *ws, size_t 
         st = pp_binned_grad(&prob, (pp_precision)a->prec, a->M, nullptr, gnx, gny, nullptr, stats + 3,
                             base + L.dens, L.dens_bytes, stream);
     if (st != PP_OK) return st;
-    if ((st = pp_wirelength(nl, a->vx, a->vy, a->gamma, gwx, gwy, stats + 1, base + L.wl, L.wl_bytes, stream)) !=
-        PP_OK)
+    if ((st = wirelength_impl(nl, a->vx, a->vy, a->gamma, scal, gwx, gwy, stats + 1, base + L.wl, L.wl_bytes,
+                              stream)) != PP_OK)
         return st;
-    if ((st = pp_place_combine(n, gwx, gwy, gnx, gny, nl->cell_ptr, a->q, a->movable, a->lambda, gx, gy,
-                               stream)) != PP_OK)
+    if ((st = combine_impl(n, gwx, gwy, gnx, gny, nl->cell_ptr, a->q, a->movable, a->lambda, scal, gx, gy,
+                           stream)) != PP_OK)
         return st;
     if ((st = pp_step_norms(n, a->vx, a->vy, a->vpx, a->vpy, gx, gy, a->gpx, a->gpy, norms, stream)) != PP_OK)
         return st;
-    if ((st = pp_nesterov_step(n, a->W, a->H, a->ux, a->uy, a->vx, a->vy, a->vpx, a->vpy, gx, gy, a->gpx, a->gpy,
-                               a->w, a->h, a->movable, norms, a->alpha0, a->coef, stream)) != PP_OK)
+    if ((st = nesterov_impl(n, a->W, a->H, a->ux, a->uy, a->vx, a->vy, a->vpx, a->vpy, gx, gy, a->gpx, a->gpy,
+                            a->w, a->h, a->movable, norms, a->alpha0, a->coef, scal, stream)) != PP_OK)
         return st;
     pp_problem over{a->W, a->H, a->n_overflow, a->ux, a->uy, a->w, a->h, nullptr, 1, 1};
     return pp_overflow(&over, a->M, a->target, bins, stats, stream);

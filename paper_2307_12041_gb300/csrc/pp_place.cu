@@ -14,6 +14,10 @@
 //   nesterov_kernel     u' = clamp(v - alpha g), v' = clamp(u' + coef (u' - u)),
 //                       alpha = |v - v_prev| / |g - g_prev| read on the device
 //   overflow_kernel     sum_b max(P_b - rho_t, 0) of a bin density P
+//
+// The loop's scalars (lambda, gamma, alpha0, coef) come either as kernel arguments or,
+// when `scal` is non-NULL, from device memory {lambda, gamma, alpha0, coef} read when
+// the kernel runs (so that one captured CUDA graph serves every iteration).
 #include <cmath>
 #include <cstdint>
 
@@ -41,7 +45,12 @@ __device__ __forceinline__ void block_add(double v, double *dst) {
 __global__ void lse_net_kernel(int n_nets, const int32_t *__restrict__ net_ptr,
                                const int32_t *__restrict__ net_pin, const float *__restrict__ x,
                                const float *__restrict__ y, float gamma, float inv_gamma,
-                               float4 *__restrict__ stats, double *__restrict__ out) {
+                               const float *__restrict__ scal, float4 *__restrict__ stats,
+                               double *__restrict__ out) {
+    if (scal) {
+        gamma = scal[1];
+        inv_gamma = 1.f / gamma;
+    }
     double wl = 0.0, hp = 0.0;
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n_nets; e += gridDim.x * blockDim.x) {
         const int p0 = net_ptr[e], p1 = net_ptr[e + 1];
@@ -81,8 +90,10 @@ __global__ void lse_net_kernel(int n_nets, const int32_t *__restrict__ net_ptr,
 
 __global__ void lse_cell_kernel(int n_cells, const int32_t *__restrict__ cell_ptr,
                                 const int32_t *__restrict__ cell_net, const float *__restrict__ x,
-                                const float *__restrict__ y, float inv_gamma, const float4 *__restrict__ stats,
-                                float *__restrict__ gx, float *__restrict__ gy) {
+                                const float *__restrict__ y, float inv_gamma, const float *__restrict__ scal,
+                                const float4 *__restrict__ stats, float *__restrict__ gx,
+                                float *__restrict__ gy) {
+    if (scal) inv_gamma = 1.f / scal[1];
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_cells; i += gridDim.x * blockDim.x) {
         const float xi = x[i], yi = y[i];
         float ax = 0.f, ay = 0.f;
@@ -100,8 +111,9 @@ __global__ void lse_cell_kernel(int n_cells, const int32_t *__restrict__ cell_pt
 __global__ void combine_kernel(int64_t n, const float *__restrict__ gwx, const float *__restrict__ gwy,
                                const float *__restrict__ gnx, const float *__restrict__ gny,
                                const int32_t *__restrict__ cell_ptr, const float *__restrict__ q,
-                               const uint8_t *__restrict__ movable, float lambda, float *__restrict__ gx,
-                               float *__restrict__ gy) {
+                               const uint8_t *__restrict__ movable, float lambda, const float *__restrict__ scal,
+                               float *__restrict__ gx, float *__restrict__ gy) {
+    if (scal) lambda = scal[0];
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         if (movable && !movable[i]) {
             gx[i] = gy[i] = 0.f;
@@ -135,7 +147,11 @@ __global__ void nesterov_kernel(int64_t n, float *__restrict__ ux, float *__rest
                                 float *__restrict__ gpx, float *__restrict__ gpy, const float *__restrict__ w,
                                 const float *__restrict__ h, float W, float H,
                                 const uint8_t *__restrict__ movable, const double *__restrict__ norms,
-                                float alpha0, float coef) {
+                                float alpha0, float coef, const float *__restrict__ scal) {
+    if (scal) {
+        alpha0 = scal[2];
+        coef = scal[3];
+    }
     // step length: |v - v_prev| / |g - g_prev| from the previous iteration, else alpha0
     // (once per CTA: FP64 division and square root are slow on this GPU)
     __shared__ float s_alpha;
@@ -182,25 +198,27 @@ int grid_for(int64_t n, int cap) {
 
 cudaError_t launch_wirelength(int n_nets, int n_cells, const int32_t *net_ptr, const int32_t *net_pin,
                               const int32_t *cell_ptr, const int32_t *cell_net, const float *x,
-                              const float *y, float gamma, float *stats, float *gx, float *gy,
-                              double *out, int sm_count, cudaStream_t st) {
+                              const float *y, float gamma, const float *scal, float *stats, float *gx,
+                              float *gy, double *out, int sm_count, cudaStream_t st) {
     cudaError_t e = cudaMemsetAsync(out, 0, 2 * sizeof(double), st);
     if (e != cudaSuccess) return e;
     if (n_nets > 0)
         lse_net_kernel<<<grid_for(n_nets, 16 * sm_count), 256, 0, st>>>(
-            n_nets, net_ptr, net_pin, x, y, gamma, 1.f / gamma, reinterpret_cast<float4 *>(stats), out);
+            n_nets, net_ptr, net_pin, x, y, gamma, 1.f / gamma, scal, reinterpret_cast<float4 *>(stats), out);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (n_cells > 0)
         lse_cell_kernel<<<grid_for(n_cells, 16 * sm_count), 256, 0, st>>>(
-            n_cells, cell_ptr, cell_net, x, y, 1.f / gamma, reinterpret_cast<const float4 *>(stats), gx, gy);
+            n_cells, cell_ptr, cell_net, x, y, 1.f / gamma, scal, reinterpret_cast<const float4 *>(stats), gx,
+            gy);
     return cudaGetLastError();
 }
 
 cudaError_t launch_combine(int64_t n, const float *gwx, const float *gwy, const float *gnx, const float *gny,
                            const int32_t *cell_ptr, const float *q, const uint8_t *movable, float lambda,
-                           float *gx, float *gy, cudaStream_t st) {
+                           const float *scal, float *gx, float *gy, cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
-    combine_kernel<<<grid_for(n, 4096), 256, 0, st>>>(n, gwx, gwy, gnx, gny, cell_ptr, q, movable, lambda, gx, gy);
+    combine_kernel<<<grid_for(n, 4096), 256, 0, st>>>(n, gwx, gwy, gnx, gny, cell_ptr, q, movable, lambda, scal, gx,
+                                                      gy);
     return cudaGetLastError();
 }
 
@@ -217,10 +235,10 @@ cudaError_t launch_step_norms(int64_t n, const float *vx, const float *vy, const
 cudaError_t launch_nesterov(int64_t n, float *ux, float *uy, float *vx, float *vy, float *vpx, float *vpy,
                             const float *gx, const float *gy, float *gpx, float *gpy, const float *w,
                             const float *h, float W, float H, const uint8_t *movable, const double *norms,
-                            float alpha0, float coef, cudaStream_t st) {
+                            float alpha0, float coef, const float *scal, cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
     nesterov_kernel<<<grid_for(n, 4096), 256, 0, st>>>(n, ux, uy, vx, vy, vpx, vpy, gx, gy, gpx, gpy, w, h, W, H,
-                                                       movable, norms, alpha0, coef);
+                                                       movable, norms, alpha0, coef, scal);
     return cudaGetLastError();
 }
 

@@ -48,6 +48,8 @@ class PlaceResult:
     y: Optional[torch.Tensor] = None
     iterations: int = 0
     ms_per_iter: float = 0.0
+    graph: bool = False                 # iterations after the first replayed a CUDA graph
+    graph_error: Optional[str] = None   # why the capture failed, if it did
 
 
 def gamma_of(tau: float, bin_w: float) -> float:
@@ -60,11 +62,13 @@ class Placer:
     gamma, a_k); step() runs one iteration and returns its record.  After the
     first iteration (whose lambda_0 and step length need host reductions) each
     step is one library call, pp_place_iteration, and one 32-byte read-back;
+    with graph=True that call is captured once in a CUDA graph and replayed with
+    the iteration's lambda, gamma and momentum written to the device.
     fused=False issues the same kernels through the separate entry points."""
 
     def __init__(self, p: synth.Placement, net_ptr, net_pin, prec: str = "tf32", target: float = 1.0,
                  d_hpwl_frac: float = 3.5e-3, device="cuda", density: str = "exact", fillers: bool = False,
-                 filler_seed: int = synth.BASE_SEED + 99, fused: bool = True):
+                 filler_seed: int = synth.BASE_SEED + 99, fused: bool = True, graph: bool = True):
         if density not in ("exact", "binned"):
             raise ValueError("density must be 'exact' or 'binned'")
         dev = torch.device(device)
@@ -93,7 +97,7 @@ class Placer:
         self.tau = float(ovf.item()) * self.bin_area / self.area_mov
         self.gamma = gamma_of(self.tau, self.bin_w)
         self.lam, self.a_k, self.hp_prev, self.d_ref, self.k = None, 1.0, None, None, 0
-        self.fused, self._it = fused, None
+        self.fused, self.use_graph, self._it = fused, graph, None
 
     def overflow_now(self):
         nr = self.n_real
@@ -108,7 +112,7 @@ class Placer:
             self._it = binding.PlaceIteration(self.nl, p.W, p.H, self.M, self.density, dprec, self.n_real,
                                               self.w, self.h, self.c, self.q, self.mov, self.ux, self.uy,
                                               self.vx, self.vy, self.vpx, self.vpy, self.gpx, self.gpy,
-                                              self.target)
+                                              self.target, graph=self.use_graph)
         return self._it
 
     def step(self) -> dict:
@@ -181,10 +185,11 @@ def with_fillers(p: synth.Placement, target: float, seed: int) -> synth.Placemen
 def place(p: synth.Placement, net_ptr, net_pin, iters: int = 200, prec: str = "tf32",
           tau_stop: float = 0.1, target: float = 1.0, d_hpwl_frac: float = 3.5e-3,
           device="cuda", callback: Optional[Callable] = None, density: str = "exact",
-          fillers: bool = False, fused: bool = True) -> PlaceResult:
+          fillers: bool = False, fused: bool = True, graph: bool = True) -> PlaceResult:
     """Run up to `iters` iterations; callback(k, rec, x_eval, y_eval, ux, uy) after
     each, with the positions at which W_LSE and E of `rec` were evaluated."""
-    pl = Placer(p, net_ptr, net_pin, prec, target, d_hpwl_frac, device, density, fillers, fused=fused)
+    pl = Placer(p, net_ptr, net_pin, prec, target, d_hpwl_frac, device, density, fillers, fused=fused,
+                graph=graph)
     res = PlaceResult()
     dev = torch.device(device)
     torch.cuda.synchronize(dev)
@@ -201,6 +206,8 @@ def place(p: synth.Placement, net_ptr, net_pin, iters: int = 200, prec: str = "t
     binding.sync_status(dev)
     res.ms_per_iter = (time.perf_counter() - t0) * 1e3 / max(res.iterations, 1)
     res.x, res.y = pl.ux[:pl.n_real], pl.uy[:pl.n_real]
+    if pl._it is not None:
+        res.graph, res.graph_error = pl._it.graph is not None, pl._it.graph_error
     return res
 
 
@@ -219,10 +226,11 @@ def _main(argv=None) -> int:
     ap.add_argument("--density", choices=["exact", "binned"], default="exact")
     ap.add_argument("--fillers", action="store_true")
     ap.add_argument("--unfused", action="store_true", help="one entry point per step of an iteration")
+    ap.add_argument("--no-graph", action="store_true", help="issue the fused call each iteration")
     a = ap.parse_args(argv)
     p = synth.placement_cells(a.n, a.modes, a.seed)
     ptr, pins = synth.netlist(a.n, a.seed + 1)
-    kw = dict(prec=a.prec, density=a.density, fillers=a.fillers, fused=not a.unfused)
+    kw = dict(prec=a.prec, density=a.density, fillers=a.fillers, fused=not a.unfused, graph=not a.no_graph)
     place(p, ptr, pins, iters=3, **kw)      # warm-up
     r = place(p, ptr, pins, iters=a.iters, **kw)
     t = r.trace
@@ -230,6 +238,7 @@ def _main(argv=None) -> int:
     print(json.dumps({
         "workload": p.name, "n": p.n, "nets": len(ptr) - 1, "pins": int(len(pins)), "modes": a.modes,
         "precision": a.prec, "density": a.density, "fillers": a.fillers, "fused": not a.unfused,
+        "graph": r.graph, "graph_error": r.graph_error,
         "iterations": r.iterations,
         "ms_per_iter": r.ms_per_iter,
         "density_terms_per_s": p.n * a.modes * a.modes / (r.ms_per_iter / 1e3),

@@ -132,6 +132,7 @@ def test_place_loop_spreads_and_gradients_match_oracle(pp):
             checks[k] = (xe.cpu().numpy(), ye.cpu().numpy(), rec)
 
     r = place.place(p, ptr, pins, iters=150, prec="fp32", tau_stop=0.0, callback=cb)
+    assert r.graph, r.graph_error                        # iterations after the first replay a graph
     taus = [t["tau"] for t in r.trace]
     assert taus[-1] < 0.8 * taus[0], (taus[0], taus[-1])
     assert all(np.isfinite([t["hpwl"] for t in r.trace]))
@@ -162,6 +163,7 @@ def test_place_loop_with_binned_density(pp):
             first["x"], first["y"], first["E"] = xe.cpu().numpy(), ye.cpu().numpy(), rec["E"]
 
     r = place.place(p, ptr, pins, iters=150, prec="fp32", tau_stop=0.0, callback=cb, density="binned")
+    assert r.graph, r.graph_error
     taus = [t["tau"] for t in r.trace]
     assert taus[-1] < 0.8 * taus[0], (taus[0], taus[-1])
     ref = OB.evaluate(p.W, p.H, first["x"], first["y"], p.w, p.h, None, M, M, M)
@@ -199,8 +201,9 @@ def test_place_entry_points_reject_bad_arguments(pp):
 STATE = ("ux", "uy", "vx", "vy", "vpx", "vpy", "gpx", "gpy")
 
 
+@pytest.mark.parametrize("graph", [False, True], ids=["call", "graph"])
 @pytest.mark.parametrize("density", ["exact", "binned"])
-def test_fused_iteration_matches_separate_calls(pp, density):
+def test_fused_iteration_matches_separate_calls(pp, density, graph):
     """pp_place_iteration issues the same kernels in the same order as the separate
     entry points.  Two placers, one fused and one not, start each iteration from the
     same state (copied over, since the FP64 sums inside the kernels are summed in
@@ -209,7 +212,7 @@ def test_fused_iteration_matches_separate_calls(pp, density):
     n, M = 8000, 64
     p = synth.placement_cells(n, M, 61)
     ptr, pins = synth.netlist(n, 62)
-    A = place.Placer(p, ptr, pins, "fp32", density=density, fused=True)
+    A = place.Placer(p, ptr, pins, "fp32", density=density, fused=True, graph=graph)
     B = place.Placer(p, ptr, pins, "fp32", density=density, fused=False)
     A.step(), B.step()                                   # the first iteration: the same path in both
     for k in range(1, 7):
@@ -229,6 +232,7 @@ def test_fused_iteration_matches_separate_calls(pp, density):
             d = (a - b).abs().max().item()
             assert d <= 1e-5 * b.abs().max().item(), (k, name, d)
     assert A._it is not None and B._it is None
+    assert (A._it.graph is not None) == graph, A._it.graph_error
 
 
 def test_fused_iteration_rejects_bad_arguments(pp):
@@ -252,6 +256,17 @@ def test_fused_iteration_rejects_bad_arguments(pp):
                 b._check(b.lib().pp_place_iteration(b.ctypes.byref(a), it.ws.data_ptr(), it.ws.numel(), None))
         finally:
             setattr(a, field, old)
-    with pytest.raises(b.PPError):                       # gamma must be > 0 (pp_wirelength's check)
+    old = a.scalars                                      # device scalars must be 16-byte aligned
+    a.scalars = it.scal_dev.data_ptr() + 4
+    try:
+        with pytest.raises(b.PPError):
+            b._check(b.lib().pp_place_iteration(b.ctypes.byref(a), it.ws.data_ptr(), it.ws.numel(), None))
+    finally:
+        a.scalars = old
+    with pytest.raises(b.PPError):                       # gamma must be > 0
         it(pl.lam, 0.0, 0.1)
+    eager = place.Placer(p, ptr, pins, "fp32", graph=False)
+    eager.step()
+    with pytest.raises(b.PPError):                       # the same check in the library call
+        eager._fused()(eager.lam, 0.0, 0.1)
     b.sync_status()
