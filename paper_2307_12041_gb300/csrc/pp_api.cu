@@ -16,6 +16,7 @@
 #include "pp.h"
 #include "pp_device.cuh"
 #include "pp_internal.h"
+#include "pp_place.h"
 
 namespace pp {
 

@@ -22,6 +22,7 @@
 #include <cstdint>
 
 #include "pp_internal.h"
+#include "pp_place.h"
 
 namespace pp {
 namespace {
