@@ -101,3 +101,38 @@ def test_place_workspace_size_host_only(L):
         assert size(**bad) == 0, bad
         assert L.pp_last_error().decode() != ""
     assert L.pp_place_workspace_size(None) == 0
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """The binding's ctypes mirrors of pp_problem, pp_netlist and
+    pp_place_iteration_args have the header's size and field offsets (a C program
+    compiled against include/pp.h prints them)."""
+    import json
+    import shutil
+    import subprocess
+    from paper_2307_12041_gb300.binding import Netlist, PlaceIterationArgs, Problem
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    mirrors = {"pp_problem": Problem, "pp_netlist": Netlist, "pp_place_iteration_args": PlaceIterationArgs}
+    # the C names of the fields the binding renames
+    c_name = {("pp_place_iteration_args", "lam"): "lambda"}
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "pp.h"', 'int main(void) {', 'printf("{");']
+    first = True
+    for sname, cls in mirrors.items():
+        for fname, _ in cls._fields_:
+            cf = c_name.get((sname, fname), fname)
+            sep = "" if first else ","
+            first = False
+            lines.append(f'printf("{sep}\\"{sname}.{fname}\\": %zu", offsetof({sname}, {cf}));')
+        lines.append(f'printf(",\\"{sname}.sizeof\\": %zu", sizeof({sname}));')
+    lines += ['printf("}\\n");', "return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = json.loads(subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout)
+    for sname, cls in mirrors.items():
+        assert got[f"{sname}.sizeof"] == ctypes.sizeof(cls), sname
+        for fname, _ in cls._fields_:
+            assert got[f"{sname}.{fname}"] == getattr(cls, fname).offset, (sname, fname)
