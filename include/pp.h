@@ -109,6 +109,44 @@ pp_status pp_grad(const pp_problem *prob, pp_precision prec, pp_sample sample,
                   const float *a, float *gx, float *gy, float *e_block, double *e_total,
                   void *ws, size_t ws_bytes, void *stream);
 
+/* Adjoint of the energies for an upstream gradient (the backward pass of
+ *   L = g_total * E + sum_i g_block_i N_i,   E = 1/2 sum_i N_i   (Sec. II-B)
+ * with respect to the block centres).  N_i = sum_uv X_iu a_uv Y_iv depends on x_j
+ * through block j's own basis and through the coefficients a (Eq. aup sums over
+ * all blocks), so with w_i = g_total / 2 + g_block_i:
+ *   dL/dx_j = w_j h_j + h^b_j,
+ * where h = the gradient pp_grad returns (coefficients a of the charges c_i) and
+ * h^b the same with the coefficients b of the charges c_i w_i (likewise for y).
+ *  - g_total: device, one double (dL/dE), or NULL = 0.  g_block: device, n float32
+ *    (dL/dN_i), or NULL = 0.  Not both NULL.
+ *  - g_block == NULL: one evaluation (three contractions), gx = g_total * dE/dx in
+ *    either reading (PP_CENTER: the centre-sample gradient of pp_grad scaled).
+ *    g_block != NULL: PP_RECT only; two evaluations (the coefficients of both
+ *    charge sets, two energy passes).
+ *  - movable: device uint8 of n, or NULL: blocks with movable[i] == 0 get 0.
+ *  - gx, gy: device float32 n (required when n > 0); e_block, e_total: optional,
+ *    N_i and E of the placement as in pp_grad.
+ *  - Workspace as pp_grad (pp_workspace_size).  PP_EINVAL as pp_grad, plus a
+ *    NULL g_total and g_block, g_block with PP_CENTER, a misaligned g_total or
+ *    host pointers.  Asynchronous on `stream`. */
+pp_status pp_grad_adjoint(const pp_problem *prob, pp_precision prec, pp_sample sample,
+                          const double *g_total, const float *g_block, const uint8_t *movable,
+                          float *gx, float *gy, float *e_block, double *e_total,
+                          void *ws, size_t ws_bytes, void *stream);
+
+/* Coefficients summed over calls in FP64: a64 += a(these blocks), Eq. (aup),
+ * (au0), (a0p) being sums over blocks (Eq. a-a..a-d).  For a placement cut into
+ * chunks of blocks (to bound the workspace) or shared out over processes (each
+ * adding its blocks, then a sum of a64 over processes), the total is a64 after
+ * every part has been added.  a64: device double Mx x My (u-major), zeroed by the
+ * caller before the first part.  a_out (optional): device float32 Mx x My
+ * receiving the rounded running sum (float)a64 after this call; with n = 0 the
+ * call adds nothing and only writes a_out.  Each part's a is formed in the
+ * precision `prec` and added in FP64.  Workspace as pp_coeffs.  Asynchronous on
+ * `stream`; calls that share a64 must be ordered. */
+pp_status pp_coeffs_accumulate(const pp_problem *prob, pp_precision prec, double *a64, float *a_out,
+                               void *ws, size_t ws_bytes, void *stream);
+
 /* Allocation-free energy + gradient.  The paper has no counterpart: this entry
  * point exists for callers that cannot allocate device memory where they
  * evaluate the energy (a host that fixes its device budget at start-up, a
@@ -117,7 +155,7 @@ pp_status pp_grad(const pp_problem *prob, pp_precision prec, pp_sample sample,
  * the same outputs as pp_grad(prob, PP_FP32, sample, NULL, ...) -- one full
  * evaluation with the coefficients computed inside the call -- but takes no
  * workspace: its scratch is a static device array of PP_STATIC_SCRATCH_BYTES
- * that every GPU loading this library reserves until the process exits.
+ * inside the library, held on each GPU that uses it until the process exits.
  * The caller passes the inputs and outputs as for pp_grad (gx, gy required when
  * n > 0; e_block, e_total optional).
  *  - Limits: n <= PP_STATIC_MAX_BLOCKS, Mx, My <= PP_STATIC_MAX_MODES; larger
@@ -125,7 +163,12 @@ pp_status pp_grad(const pp_problem *prob, pp_precision prec, pp_sample sample,
  *  - It allocates nothing: no cudaMalloc/cudaFree or allocating library call.
  *  - The first call on a device looks up the array's device address (set-up,
  *    once per device, with that device current); make that first call before
- *    any stream capture.
+ *    any stream capture.  Under the CUDA runtime's default lazy module loading
+ *    the array is reserved on a device by that first call (when the module that
+ *    holds it is loaded), not when the library is loaded: a caller that fixes
+ *    its device budget at start-up makes one call there first (n = 0 does only
+ *    the set-up and zeroes *e_total).
+ *  - The die size is checked as in pp_grad (W, H in [1e-300, 1e300]).
  *  - All calls share the one array and it keeps the previous call's contents;
  *    what must start at zero is cleared on `stream` by each call.  Calls whose
  *    kernels overlap on the GPU (unordered streams) race on the array. */

@@ -21,7 +21,7 @@ SAMPLES = {"rect": 0, "center": 1}
 STATUS = {0: "PP_OK", 1: "PP_EINVAL", 2: "PP_ENOMEM_WS", 3: "PP_ECUDA", 4: "PP_ETIMEOUT",
           5: "PP_ENOTSUP"}
 # Normalised max-error bounds used by the parity tests (max |err| / max |ref|).
-TOLERANCE = {"fp32": 1e-6, "tf32": 5e-3, "bf16x3": 1e-4}
+TOLERANCE = {"fp32": 1e-6, "tf32": 1e-3, "bf16x3": 1e-4}
 
 Precision = PRECISIONS
 Sample = SAMPLES
@@ -64,7 +64,7 @@ EXPORTS = ("pp_workspace_size", "pp_coeffs", "pp_energy", "pp_grad", "pp_sync_st
            "pp_energy_from_coeffs", "pp_descent_step",
            "pp_wirelength_workspace_size", "pp_wirelength", "pp_place_combine", "pp_step_norms",
            "pp_nesterov_step", "pp_overflow", "pp_place_workspace_size", "pp_place_iteration",
-           "pp_check_wait_timeout")
+           "pp_check_wait_timeout", "pp_grad_adjoint", "pp_coeffs_accumulate")
 
 
 def lib_path() -> str:
@@ -129,6 +129,10 @@ def lib() -> ctypes.CDLL:
         L.pp_last_error.restype = ctypes.c_char_p
         L.pp_version.argtypes = []
         L.pp_version.restype = ctypes.c_char_p
+        L.pp_grad_adjoint.argtypes = [P, i, i, vp, vp, vp, vp, vp, vp, vp, vp, sz, vp]
+        L.pp_grad_adjoint.restype = i
+        L.pp_coeffs_accumulate.argtypes = [P, i, vp, vp, vp, sz, vp]
+        L.pp_coeffs_accumulate.restype = i
         L.pp_grad_noalloc.argtypes = [P, i, vp, vp, vp, vp, vp]
         L.pp_grad_noalloc.restype = i
         L.pp_timing_enable.argtypes = [i]
@@ -253,6 +257,65 @@ def grad(x, y, w, h, c, W, H, Mx, My, prec="fp32", sample="rect", a=None, want_e
     return gx, gy, eb, et
 
 
+def _mask(movable, n, device):
+    if movable is None:
+        return None
+    m = movable if movable.dtype == torch.uint8 else movable.to(torch.uint8)
+    m = m.contiguous()
+    if m.numel() != n or m.device != torch.device(device):
+        raise ValueError(f"movable must be a bool/uint8 tensor of {n} elements on {device}")
+    return m
+
+
+def grad_adjoint(x, y, w, h, c, W, H, Mx, My, prec="fp32", sample="rect", g_total=None, g_block=None,
+                 movable=None, want_energy=False):
+    """pp_grad_adjoint: (dL/dx, dL/dy, N_i or None, E or None) for
+    L = g_total * E + sum_i g_block_i N_i; g_total a 1-element float64 device tensor
+    (or None), g_block a float32 device tensor of n (or None); blocks whose `movable`
+    entry is False get 0."""
+    prob = make_problem(x, y, w, h, c, W, H, Mx, My)
+    dev = x.device
+    n = x.numel()
+    if g_total is not None:
+        g_total = g_total.reshape(1)
+        if g_total.dtype != torch.float64:
+            g_total = g_total.to(torch.float64)
+        g_total = g_total.contiguous()
+    if g_block is not None:
+        g_block = g_block.contiguous()
+        if g_block.dtype != torch.float32 or g_block.numel() != n:
+            raise ValueError(f"g_block must be a float32 tensor of {n} elements")
+    mv = _mask(movable, n, dev)
+    gx = torch.empty(n, dtype=torch.float32, device=dev)
+    gy = torch.empty(n, dtype=torch.float32, device=dev)
+    eb = torch.empty(n, dtype=torch.float32, device=dev) if want_energy else None
+    et = torch.empty(1, dtype=torch.float64, device=dev) if want_energy else None
+    ws = workspace(prob, prec, dev)
+    _check(lib().pp_grad_adjoint(ctypes.byref(prob), PRECISIONS[prec], SAMPLES[sample], _ptr(g_total),
+                                 _ptr(g_block) if n else None, _ptr(mv) if n else None,
+                                 _ptr(gx) if n else None, _ptr(gy) if n else None,
+                                 _ptr(eb) if (eb is not None and n) else None, _ptr(et),
+                                 ws.data_ptr(), ws.numel(), _stream_handle(dev)))
+    return gx, gy, eb, et
+
+
+def coeffs_accumulate(x, y, w, h, c, W, H, Mx, My, a64, prec="fp32", a_out=None):
+    """pp_coeffs_accumulate: a64 (float64 Mx x My device tensor) += the coefficients of
+    these blocks; a_out (optional float32 Mx x My) receives the rounded running sum.
+    With zero blocks only a_out is written."""
+    prob = make_problem(x, y, w, h, c, W, H, Mx, My)
+    dev = a64.device
+    if a64.dtype != torch.float64 or not a64.is_contiguous() or a64.numel() != Mx * My:
+        raise ValueError("a64 must be a contiguous float64 tensor of Mx * My elements")
+    if a_out is not None and (a_out.dtype != torch.float32 or not a_out.is_contiguous()
+                              or a_out.numel() != Mx * My):
+        raise ValueError("a_out must be a contiguous float32 tensor of Mx * My elements")
+    ws = workspace(prob, prec, dev)
+    _check(lib().pp_coeffs_accumulate(ctypes.byref(prob), PRECISIONS[prec], _ptr(a64), _ptr(a_out),
+                                      ws.data_ptr(), ws.numel(), _stream_handle(dev)))
+    return a64
+
+
 def grad_noalloc(x, y, w, h, c, W, H, Mx, My, sample="rect", out=None):
     """pp_grad_noalloc: the FP32 evaluation with the library's static scratch instead
     of a workspace (for callers that cannot allocate).  Returns (gx, gy, N_i, E)."""
@@ -361,9 +424,9 @@ class PoissonEnergy(torch.autograd.Function):
     """E = 1/2 sum_i N_i as a differentiable function of the block centres.
 
     forward:  pp_energy (coefficients computed inside the call, not kept)
-    backward: pp_grad with a = NULL: the coefficients are recomputed rather than
-              stored, and the adjoint is grad_out * (dE/dx, dE/dy).  Blocks whose
-              `movable` entry is False receive zero gradient.
+    backward: pp_grad_adjoint with g_total = the upstream gradient: the coefficients
+              are recomputed rather than stored, and the library scales dE/dx, dE/dy
+              by it.  Blocks whose `movable` entry is False receive zero gradient.
     """
 
     @staticmethod
@@ -378,15 +441,8 @@ class PoissonEnergy(torch.autograd.Function):
     def backward(ctx, g):
         x, y, w, h, c, mov = ctx.saved_tensors
         W, H, Mx, My, prec, sample, has_c, has_mov = ctx.args
-        gx, gy, _, _ = grad(x.detach(), y.detach(), w, h, c if has_c else None, W, H, Mx, My,
-                            prec, sample, want_energy=False)
-        scale = g.to(torch.float32)
-        gx = gx * scale
-        gy = gy * scale
-        if has_mov:
-            m = mov.to(torch.float32)
-            gx = gx * m
-            gy = gy * m
+        gx, gy, _, _ = grad_adjoint(x.detach(), y.detach(), w, h, c if has_c else None, W, H, Mx, My,
+                                    prec, sample, g_total=g, movable=mov if has_mov else None)
         return (gx if ctx.needs_input_grad[0] else None,
                 gy if ctx.needs_input_grad[1] else None,
                 None, None, None, None, None, None, None, None, None, None)
@@ -400,10 +456,11 @@ class PoissonBlockEnergies(torch.autograd.Function):
       dL/dx_j = g_j h_j + h^b_j,
     where h_j = sum_uv X'_ju a_uv Y_jv is the gradient pp_grad returns with the
     placement's own coefficients a, and h^b_j the same with b = G o sum_i g_i X_i Y_i^T,
-    i.e. the coefficients of the same blocks with charges c_i g_i (pp_coeffs).  For
-    g = 1/2 everywhere b = a/2 and dL/dx = h = dE/dx.  The backward recomputes a and
-    computes b: two coefficient and two energy contractions.  Blocks whose `movable`
-    entry is False receive zero gradient.
+    i.e. the coefficients of the same blocks with charges c_i g_i.  For g = 1/2
+    everywhere b = a/2 and dL/dx = h = dE/dx.  The backward is one library call,
+    pp_grad_adjoint with g_block = g: it recomputes a, computes b and combines the
+    two energy passes on the device (two coefficient and two energy contractions).
+    Blocks whose `movable` entry is False receive zero gradient.
     """
 
     @staticmethod
@@ -418,19 +475,9 @@ class PoissonBlockEnergies(torch.autograd.Function):
     def backward(ctx, g):
         x, y, w, h, c, mov = ctx.saved_tensors
         W, H, Mx, My, prec, has_c, has_mov = ctx.args
-        x, y = x.detach(), y.detach()
-        cc = c if has_c else None
-        g = g.to(torch.float32).contiguous()
-        gxa, gya, _, _ = grad(x, y, w, h, cc, W, H, Mx, My, prec, want_energy=False)
-        cg = (g * c if has_c else g).contiguous()
-        b = coeffs(x, y, w, h, cg, W, H, Mx, My, prec)
-        gxb, gyb, _, _ = grad(x, y, w, h, cc, W, H, Mx, My, prec, a=b, want_energy=False)
-        gx = g * gxa + gxb
-        gy = g * gya + gyb
-        if has_mov:
-            m = mov.to(torch.float32)
-            gx = gx * m
-            gy = gy * m
+        gx, gy, _, _ = grad_adjoint(x.detach(), y.detach(), w, h, c if has_c else None, W, H, Mx, My,
+                                    prec, "rect", g_block=g.to(torch.float32),
+                                    movable=mov if has_mov else None)
         return (gx if ctx.needs_input_grad[0] else None,
                 gy if ctx.needs_input_grad[1] else None,
                 None, None, None, None, None, None, None, None, None)

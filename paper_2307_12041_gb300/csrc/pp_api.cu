@@ -313,15 +313,35 @@ pp_status operand_from_a(Ctx &c, const float *a) {
     return PP_OK;
 }
 
-pp_status run_energy(Ctx &c, pp_sample sample, float *e_block, double *e_total, float *gx, float *gy) {
+pp_status run_energy(Ctx &c, pp_sample sample, float *e_block, double *e_total, float *gx, float *gy,
+                     const GradOut &go = GradOut()) {
     if (c.prec == PP_FP32) {
-        PP_LAUNCH(PP_K_ENERGY, c.L.stream, launch_energy_simt(c.L, (int)sample, e_block, e_total, gx, gy),
+        PP_LAUNCH(PP_K_ENERGY, c.L.stream, launch_energy_simt(c.L, (int)sample, e_block, e_total, gx, gy, go),
                   "energy kernel launch");
     } else {
         PP_LAUNCH(PP_K_ENERGY, c.L.stream,
                   launch_energy_tc(c.L, (int)c.prec, (int)sample, c.lay.plan, c.base + c.lay.K,
-                                   c.base + c.lay.Klo, e_block, e_total, gx, gy),
+                                   c.base + c.lay.Klo, e_block, e_total, gx, gy, go),
                   "energy kernel launch");
+    }
+    return PP_OK;
+}
+
+// Coefficients of these blocks added into a64 (FP64, Mx x My); a_out (optional)
+// receives the rounded running sum.  No energy operand is formed.
+pp_status accumulate_coefficients(Ctx &c, double *a64, float *a_out) {
+    if (c.prec == PP_FP32) {
+        PP_LAUNCH(PP_K_COEFF, c.L.stream, launch_coeff_simt(c.L), "coefficient kernel launch");
+        PP_LAUNCH(PP_K_FINISH, c.L.stream, launch_finish_simt(c.L, nullptr, a_out, a64, false),
+                  "finish kernel launch");
+    } else {
+        float *part = (float *)(c.base + c.lay.part);
+        PP_LAUNCH(PP_K_COEFF, c.L.stream, launch_coeff_tc(c.L, (int)c.prec, c.lay.plan, part),
+                  "coefficient kernel launch");
+        PP_LAUNCH(PP_K_FINISH, c.L.stream,
+                  launch_finish_tc(c.L, (int)c.prec, c.lay.plan, part, nullptr, a_out, nullptr, nullptr,
+                                   nullptr, a64),
+                  "finish kernel launch");
     }
     return PP_OK;
 }
@@ -403,6 +423,81 @@ pp_status pp_grad(const pp_problem *prob, pp_precision prec, pp_sample sample, c
                   float *gx, float *gy, float *e_block, double *e_total, void *ws, size_t ws_bytes,
                   void *stream) {
     return energy_common(prob, prec, sample, a, gx, gy, e_block, e_total, ws, ws_bytes, stream, true);
+}
+
+pp_status pp_grad_adjoint(const pp_problem *prob, pp_precision prec, pp_sample sample, const double *g_total,
+                          const float *g_block, const uint8_t *movable, float *gx, float *gy, float *e_block,
+                          double *e_total, void *ws, size_t ws_bytes, void *stream) {
+    Ctx c;
+    pp_status st = setup(prob, prec, ws, ws_bytes, stream, &c);
+    if (st != PP_OK) return st;
+    if (sample != PP_RECT && sample != PP_CENTER) return fail(PP_EINVAL, "unknown sample mode %d", (int)sample);
+    if (!g_total && !g_block) return fail(PP_EINVAL, "g_total and g_block are both NULL");
+    if (g_block && sample != PP_RECT)
+        return fail(PP_EINVAL, "per-block upstream gradients (g_block) need the rectangle reading PP_RECT");
+    const bool has_blocks = prob->n > 0;
+    if ((st = out_ptr(gx, c.dev, "gx", has_blocks)) != PP_OK) return st;
+    if ((st = out_ptr(gy, c.dev, "gy", has_blocks)) != PP_OK) return st;
+    if ((st = out_ptr(e_block, c.dev, "e_block", false)) != PP_OK) return st;
+    if (e_total) {
+        if (((uintptr_t)e_total & 7) != 0) return fail(PP_EINVAL, "e_total is not 8-byte aligned");
+        if ((st = check_dev_ptr(e_total, c.dev, "e_total")) != PP_OK) return st;
+    }
+    if (g_total) {
+        if (((uintptr_t)g_total & 7) != 0) return fail(PP_EINVAL, "g_total is not 8-byte aligned");
+        if ((st = check_dev_ptr(g_total, c.dev, "g_total")) != PP_OK) return st;
+    }
+    if (has_blocks && g_block && (st = out_ptr(g_block, c.dev, "g_block", true)) != PP_OK) return st;
+    if (has_blocks && movable && (st = check_dev_ptr(movable, c.dev, "movable")) != PP_OK) return st;
+    if (!has_blocks) {
+        if (e_total) PP_TRY(cudaMemsetAsync(e_total, 0, sizeof(double), c.L.stream), "memset e_total");
+        return PP_OK;
+    }
+    // pass 1: the placement's coefficients a and h = dE/d(x, y) (the whole answer when
+    // only g_total is given: g_total * h, masked)
+    PP_LAUNCH(PP_K_PREP, c.L.stream, launch_prep(c.L, prec == PP_FP32, e_total), "prep kernel launch");
+    const bool e_from_a = prec != PP_FP32 && sample == PP_RECT;
+    if ((st = run_coefficients(c, nullptr, e_from_a ? e_total : nullptr)) != PP_OK) return st;
+    GradOut g1;
+    if (!g_block) {
+        g1.scale = g_total;
+        g1.mask = movable;
+    }
+    if ((st = run_energy(c, sample, e_block, e_from_a ? nullptr : e_total, gx, gy, g1)) != PP_OK) return st;
+    if (!g_block) return PP_OK;
+    // pass 2: coefficients b of the charges c_i w_i, w_i = g_total / 2 + g_block_i, then
+    // h^b from the records with the plain charges again, combined as w_j h_j + h^b_j
+    ChargeWeights cw;
+    cw.gw = g_block;
+    cw.gt = g_total;
+    cw.on = true;
+    PP_LAUNCH(PP_K_PREP, c.L.stream, launch_prep(c.L, prec == PP_FP32, nullptr, cw), "prep kernel launch");
+    if ((st = run_coefficients(c, nullptr)) != PP_OK) return st;
+    PP_LAUNCH(PP_K_PREP, c.L.stream, launch_prep(c.L, false, nullptr), "prep kernel launch");
+    GradOut g2;
+    g2.acc = true;
+    g2.w = g_block;
+    g2.wt = g_total;
+    g2.mask = movable;
+    return run_energy(c, sample, nullptr, nullptr, gx, gy, g2);
+}
+
+pp_status pp_coeffs_accumulate(const pp_problem *prob, pp_precision prec, double *a64, float *a_out, void *ws,
+                               size_t ws_bytes, void *stream) {
+    Ctx c;
+    pp_status st = setup(prob, prec, ws, ws_bytes, stream, &c);
+    if (st != PP_OK) return st;
+    if (!a64) return fail(PP_EINVAL, "a64 must be non-NULL");
+    if (((uintptr_t)a64 & 7) != 0) return fail(PP_EINVAL, "a64 is not 8-byte aligned");
+    if ((st = check_dev_ptr(a64, c.dev, "a64")) != PP_OK) return st;
+    if ((st = out_ptr(a_out, c.dev, "a_out", false)) != PP_OK) return st;
+    if (prob->n == 0) {
+        if (a_out)
+            PP_TRY(launch_round_coeffs(a64, a_out, (size_t)prob->Mx * prob->My, c.L.stream), "round kernel launch");
+        return PP_OK;
+    }
+    PP_LAUNCH(PP_K_PREP, c.L.stream, launch_prep(c.L, prec == PP_FP32, nullptr), "prep kernel launch");
+    return accumulate_coefficients(c, a64, a_out);
 }
 
 pp_status pp_sync_status(void *stream) {

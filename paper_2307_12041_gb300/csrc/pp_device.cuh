@@ -52,6 +52,20 @@ __device__ __forceinline__ float2 phase_cs(unsigned long long m, unsigned long l
     return make_float2(fmaf(-sn, d, cs), fmaf(cs, d, sn));
 }
 
+// The gradient value v of block b as the energy kernels write it (GradOut in
+// pp_internal.h): optionally combined with the value already in out[b] (weighted by
+// w[b]), scaled by a device scalar and masked.
+template <typename GO>
+__device__ __forceinline__ float grad_out(const GO &go, const float *out, size_t b, float v) {
+    if (go.acc) {
+        const float wb = (go.w ? go.w[b] : 0.0f) + (go.wt ? 0.5f * (float)go.wt[0] : 0.0f);
+        v = fmaf(wb, out[b], v);
+    }
+    if (go.scale) v *= (float)go.scale[0];
+    if (go.mask && go.mask[b] == 0) v = 0.0f;
+    return v;
+}
+
 // z * e (complex), one angle-addition step.
 __device__ __forceinline__ float2 rot(float2 z, float2 e) {
     return make_float2(fmaf(z.x, e.x, -z.y * e.y), fmaf(z.y, e.x, z.x * e.y));

@@ -27,6 +27,29 @@ struct Launch {
     cudaStream_t stream;
 };
 
+// What the energy kernels do with the gradient they form for block b (value v,
+// either axis) before writing it: nothing (the default), or
+//   v <- (w[b] + 0.5 wt[0]) * out[b] + v   when acc (out already holds a gradient;
+//                                          w, wt may each be NULL = 0),
+//   v <- v * scale[0]                      when scale != NULL (a device scalar),
+//   v <- 0                                 when mask != NULL and mask[b] == 0.
+// This is how the adjoint entry point combines its two energy passes.
+struct GradOut {
+    const float *w = nullptr;
+    const double *wt = nullptr;
+    const double *scale = nullptr;
+    const uint8_t *mask = nullptr;
+    bool acc = false;
+};
+
+// Per-block charge weights of the preparation kernel: the x records get charge
+// c_i * (0.5 * gt[0] + gw[i]) instead of c_i (either pointer may be NULL = 0).
+struct ChargeWeights {
+    const float *gw = nullptr;
+    const double *gt = nullptr;
+    bool on = false;
+};
+
 // Padded sizes of the FP32 energy operand (u rows, v columns).
 constexpr int kSimtKU = 32;     // u chunk of the FP32 energy kernel
 constexpr int kSimtKV = 128;    // v tile of the FP32 energy kernel
@@ -51,10 +74,14 @@ struct TcPlan {
 };
 TcPlan tc_plan(int n, int Mx, int My);
 cudaError_t launch_coeff_tc(const Launch &L, int prec, const TcPlan &P, float *part);
+// a64 (optional): FP64 running sum of coefficients, a64 += a; a_out then receives
+// the rounded running sum instead of this call's a.  Khi == NULL: no operand.
 cudaError_t launch_finish_tc(const Launch &L, int prec, const TcPlan &P, const float *part,
-                             const float *a_in, float *a_out, void *Khi, void *Klo, double *e_total);
+                             const float *a_in, float *a_out, void *Khi, void *Klo, double *e_total,
+                             double *a64 = nullptr);
 cudaError_t launch_energy_tc(const Launch &L, int prec, int sample, const TcPlan &P, void *Khi,
-                             void *Klo, float *e_block, double *e_total, float *gx, float *gy);
+                             void *Klo, float *e_block, double *e_total, float *gx, float *gy,
+                             const GradOut &go = GradOut());
 
 // pp_api.cu: message returned by pp_last_error() for the calling thread
 void set_last_error(const char *msg);
@@ -84,10 +111,15 @@ cudaError_t launch_wait_probe(uint64_t limit_ns, unsigned *status, cudaStream_t 
 // pp_place.cu: the placement loop's launchers are declared in pp_place.h
 
 // pp_simt.cu
-cudaError_t launch_prep(const Launch &L, bool zero_S, double *e_total);
+cudaError_t launch_prep(const Launch &L, bool zero_S, double *e_total,
+                        const ChargeWeights &cw = ChargeWeights());
 cudaError_t launch_coeff_simt(const Launch &L);
-cudaError_t launch_finish_simt(const Launch &L, const float *a_in, float *a_out);
+// a64 as for launch_finish_tc; with_K = false skips the energy operand
+cudaError_t launch_finish_simt(const Launch &L, const float *a_in, float *a_out, double *a64 = nullptr,
+                               bool with_K = true);
 cudaError_t launch_energy_simt(const Launch &L, int sample, float *e_block, double *e_total,
-                               float *gx, float *gy);
+                               float *gx, float *gy, const GradOut &go = GradOut());
+// a_out[i] = (float)a64[i], i < count (the rounded running sum alone)
+cudaError_t launch_round_coeffs(const double *a64, float *a_out, size_t count, cudaStream_t stream);
 
 }  // namespace pp

@@ -26,16 +26,21 @@ __global__ void prep_kernel(const float *__restrict__ x, const float *__restrict
                             const float *__restrict__ w, const float *__restrict__ h,
                             const float *__restrict__ c, int n, double invW, double invH,
                             float piW, float piH, AxisRec *__restrict__ xr, AxisRec *__restrict__ yr,
-                            double *__restrict__ S64, size_t nS, double *e_total) {
+                            double *__restrict__ S64, size_t nS, double *e_total,
+                            const float *__restrict__ gw, const double *__restrict__ gt, bool weighted) {
     // FP32 and integer arithmetic only (FP64 is a narrow pipe on this GPU)
     pdl_trigger();            // a dependent coefficient or finish kernel may be scheduled now
     const size_t tid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     const size_t stride = (size_t)gridDim.x * blockDim.x;
     const double halfW = 0.5 * invW, halfH = 0.5 * invH;       // exact: powers of two
+    // weighted: charge c_i (0.5 gt + gw_i), the charges whose coefficients b give the
+    // second term of the adjoint of sum_i gw_i N_i + gt E
+    const float ght = (weighted && gt) ? 0.5f * (float)gt[0] : 0.0f;
     // one thread per block: its x and y records (independent work, issued together)
     for (size_t b = tid; b < (size_t)n; b += stride) {
         const float px = x[b], py = y[b], lw = w[b], lh = h[b];
-        const float ci = c ? c[b] : 1.0f;
+        float ci = c ? c[b] : 1.0f;
+        if (weighted) ci *= ght + (gw ? gw[b] : 0.0f);
         AxisRec rx, ry;
         rx.s = fixed_halfturns(px, invW);
         ry.s = fixed_halfturns(py, invH);
@@ -64,7 +69,7 @@ __global__ void prep_kernel(const float *__restrict__ x, const float *__restrict
     if (tid == 0 && e_total) *e_total = 0.0;
 }
 
-cudaError_t launch_prep(const Launch &L, bool zero_S, double *e_total) {
+cudaError_t launch_prep(const Launch &L, bool zero_S, double *e_total, const ChargeWeights &cw) {
     size_t nS = zero_S ? (size_t)L.Mx * L.My : 0;
     size_t work = (size_t)L.n > nS ? (size_t)L.n : nS;
     int blocks = (int)((work + 255) / 256);
@@ -73,7 +78,20 @@ cudaError_t launch_prep(const Launch &L, bool zero_S, double *e_total) {
     const double PI = 3.141592653589793;
     prep_kernel<<<blocks, 256, 0, L.stream>>>(L.x, L.y, L.w, L.h, L.c, L.n, 1.0 / L.W, 1.0 / L.H,
                                               (float)(PI / L.W), (float)(PI / L.H), L.xrec, L.yrec,
-                                              L.S64, nS, e_total);
+                                              L.S64, nS, e_total, cw.gw, cw.gt, cw.on);
+    return cudaGetLastError();
+}
+
+__global__ void round_coeffs_kernel(const double *__restrict__ a64, float *__restrict__ a_out, size_t count) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x)
+        a_out[i] = (float)a64[i];
+}
+
+cudaError_t launch_round_coeffs(const double *a64, float *a_out, size_t count, cudaStream_t stream) {
+    if (count == 0) return cudaSuccess;
+    size_t blocks = (count + 255) / 256;
+    if (blocks > 1024) blocks = 1024;
+    round_coeffs_kernel<<<(int)blocks, 256, 0, stream>>>(a64, a_out, count);
     return cudaGetLastError();
 }
 
@@ -296,7 +314,7 @@ cudaError_t launch_coeff_simt(const Launch &L) {
 // ---------------------------------------------------------------------------
 __global__ void finish_simt_kernel(const double *__restrict__ S64, const float *__restrict__ a_in,
                                    float *__restrict__ a_out, float *__restrict__ K, int Mx, int My,
-                                   int Mxp, int Kld, double W, double H) {
+                                   int Mxp, int Kld, double W, double H, double *__restrict__ a64) {
     const double PI = 3.141592653589793;
     const size_t total = (size_t)Mxp * Kld;
     for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
@@ -314,7 +332,13 @@ __global__ void finish_simt_kernel(const double *__restrict__ S64, const float *
                 const double eps = (u ? 2.0 : 1.0) * (v ? 2.0 : 1.0);
                 const double G = (u == 0 && v == 0) ? 0.0 : eps / (W * H * (ku * ku + lv * lv));
                 av = G * f * g * S64[(size_t)u * My + v];
-                if (a_out) a_out[(size_t)u * My + v] = (float)av;
+                if (a64) {                      // running FP64 sum over calls (chunks, ranks)
+                    const double t = a64[(size_t)u * My + v] + av;
+                    a64[(size_t)u * My + v] = t;
+                    if (a_out) a_out[(size_t)u * My + v] = (float)t;
+                } else if (a_out) {
+                    a_out[(size_t)u * My + v] = (float)av;
+                }
             }
             kv = (float)(f * av * g);
         }
@@ -322,13 +346,13 @@ __global__ void finish_simt_kernel(const double *__restrict__ S64, const float *
     }
 }
 
-cudaError_t launch_finish_simt(const Launch &L, const float *a_in, float *a_out) {
+cudaError_t launch_finish_simt(const Launch &L, const float *a_in, float *a_out, double *a64, bool with_K) {
     const int Mxp = round_up(L.Mx, kSimtKU);
     const size_t total = (size_t)Mxp * L.Kld;
     int blocks = (int)((total + 255) / 256);
     if (blocks > 8 * L.sm_count) blocks = 8 * L.sm_count;
-    finish_simt_kernel<<<blocks, 256, 0, L.stream>>>(L.S64, a_in, a_out, (float *)L.K, L.Mx, L.My,
-                                                     Mxp, L.Kld, L.W, L.H);
+    finish_simt_kernel<<<blocks, 256, 0, L.stream>>>(L.S64, a_in, a_out, with_K ? (float *)L.K : nullptr,
+                                                     L.Mx, L.My, Mxp, L.Kld, L.W, L.H, a64);
     return cudaGetLastError();
 }
 
@@ -414,7 +438,8 @@ template <int SAMPLE>
 __global__ void __launch_bounds__(256, 1)
 energy_simt_kernel(const AxisRec *__restrict__ xr, const AxisRec *__restrict__ yr, int n, int Mx,
                    int My, const float *__restrict__ K, int Kld, float *__restrict__ e_block,
-                   double *__restrict__ e_total, float *__restrict__ gx, float *__restrict__ gy) {
+                   double *__restrict__ e_total, float *__restrict__ gx, float *__restrict__ gy,
+                   const GradOut go) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     EnergySmem &sm = *reinterpret_cast<EnergySmem *>(smem_raw);
     auto &Xs = sm.Xs;
@@ -549,8 +574,8 @@ energy_simt_kernel(const AxisRec *__restrict__ xr, const AxisRec *__restrict__ y
             const int b = blk0 + bt * 4 + i;
             if (b < n) {
                 if (e_block) e_block[b] = eN[i];
-                if (gx) gx[b] = eX[i];
-                if (gy) gy[b] = eY[i];
+                if (gx) gx[b] = grad_out(go, gx, b, eX[i]);
+                if (gy) gy[b] = grad_out(go, gy, b, eY[i]);
                 esum += (double)eN[i];
             }
         }
@@ -568,7 +593,7 @@ energy_simt_kernel(const AxisRec *__restrict__ xr, const AxisRec *__restrict__ y
 }
 
 cudaError_t launch_energy_simt(const Launch &L, int sample, float *e_block, double *e_total,
-                               float *gx, float *gy) {
+                               float *gx, float *gy, const GradOut &go) {
     if (L.n == 0) return cudaSuccess;
     const int grid = (L.n + EB - 1) / EB;
     const float *K = (const float *)L.K;
@@ -578,12 +603,12 @@ cudaError_t launch_energy_simt(const Launch &L, int sample, float *e_block, doub
         err = cudaFuncSetAttribute(energy_simt_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (err != cudaSuccess) return err;
         energy_simt_kernel<0><<<grid, 256, smem, L.stream>>>(L.xrec, L.yrec, L.n, L.Mx, L.My, K, L.Kld,
-                                                             e_block, e_total, gx, gy);
+                                                             e_block, e_total, gx, gy, go);
     } else {
         err = cudaFuncSetAttribute(energy_simt_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (err != cudaSuccess) return err;
         energy_simt_kernel<1><<<grid, 256, smem, L.stream>>>(L.xrec, L.yrec, L.n, L.Mx, L.My, K, L.Kld,
-                                                             e_block, e_total, gx, gy);
+                                                             e_block, e_total, gx, gy, go);
     }
     return cudaGetLastError();
 }

@@ -10,12 +10,17 @@
 // (per-block records, the FP64 coefficient sums and the energy operand) lives
 // here.
 //
-// The array below is reserved on every GPU that loads the library, from load
-// until process exit (PP_STATIC_SCRATCH_BYTES, about 5 MB).  All calls share
-// it: the contents of the previous call remain, so every part that must start
-// at zero (the FP64 sums and *e_total) is cleared on the stream by the first
-// kernel of each call, and two calls whose kernels overlap on the GPU (for
-// example on two streams without ordering between them) race on it.
+// The array below (PP_STATIC_SCRATCH_BYTES, about 5 MB) is reserved on a GPU
+// when this file's CUDA module is loaded there and stays reserved until process
+// exit.  The CUDA runtime loads modules lazily by default (CUDA_MODULE_LOADING
+// = LAZY), and nothing in this module is used before the set-up below looks up
+// the array's address, so in practice the first pp_grad_noalloc call on a
+// device is the one that reserves it: a caller that fixes its device budget at
+// start-up makes one call then (n = 0 does only the set-up).  All calls share
+// the array: the contents of the previous call remain, so every part that must
+// start at zero (the FP64 sums and *e_total) is cleared on the stream by the
+// first kernel of each call, and two calls whose kernels overlap on the GPU
+// (for example on two streams without ordering between them) race on it.
 #include <cmath>
 #include <cstdint>
 #include <mutex>
@@ -96,8 +101,11 @@ using namespace pp;
 extern "C" pp_status pp_grad_noalloc(const pp_problem *prob, pp_sample sample, float *gx, float *gy,
                                      float *e_block, double *e_total, void *stream) {
     if (!prob) return err(PP_EINVAL, "pp_grad_noalloc: problem is NULL");
-    if (!std::isfinite(prob->W) || !std::isfinite(prob->H) || prob->W <= 0 || prob->H <= 0)
-        return err(PP_EINVAL, "pp_grad_noalloc: die size must be finite and > 0");
+    // the die range of pp_grad: 1/W and 1/H must be finite normal numbers for the
+    // fixed-point phases
+    if (!std::isfinite(prob->W) || !std::isfinite(prob->H) || !(prob->W >= 1e-300 && prob->W <= 1e300) ||
+        !(prob->H >= 1e-300 && prob->H <= 1e300))
+        return err(PP_EINVAL, "pp_grad_noalloc: die size W, H must be finite and in [1e-300, 1e300]");
     if (prob->n < 0 || prob->n > PP_STATIC_MAX_BLOCKS)
         return err(PP_EINVAL, "pp_grad_noalloc: n must be in [0, PP_STATIC_MAX_BLOCKS = 32768]");
     if (prob->Mx < 1 || prob->My < 1 || prob->Mx > PP_STATIC_MAX_MODES || prob->My > PP_STATIC_MAX_MODES)

@@ -570,7 +570,7 @@ __global__ void tc_finish_kernel(const float *__restrict__ part, int slices, int
                                  void *__restrict__ Kop, void *__restrict__ Klo, int Mx, int My,
                                  int Mxe, int Mye, float piW, float piH, float invWH,
                                  double *__restrict__ e_total, unsigned *__restrict__ split_cnt,
-                                 int nsplit) {
+                                 int nsplit, double *__restrict__ a64) {
     pdl_wait();                        // the slice partials come from the coefficient kernel
     pdl_trigger();                     // the energy kernel may be scheduled (it waits for this one)
     // the energy kernel that follows finds its split-tile counters at zero
@@ -618,11 +618,18 @@ __global__ void tc_finish_kernel(const float *__restrict__ part, int slices, int
                 const float eps = (u ? 2.f : 1.f) * (v ? 2.f : 1.f);
                 const float G = (u == 0 && v == 0) ? 0.f : eps * invWH / (ku * ku + lv * lv);
                 av = G * f * g * S;
-                if (a_out) a_out[(size_t)u * My + v] = av;
+                if (a64) {                      // running FP64 sum over calls (chunks, ranks)
+                    const double t = a64[(size_t)u * My + v] + (double)av;
+                    a64[(size_t)u * My + v] = t;
+                    if (a_out) a_out[(size_t)u * My + v] = (float)t;
+                } else if (a_out) {
+                    a_out[(size_t)u * My + v] = av;
+                }
                 e_acc = fmaf(0.5f * av, f * g * S, e_acc);
             }
             kv = f * av * g;
         }
+        if (!Kop) continue;
         const int vb = v >> 8, vi = v & 255;
         if (PREC == 1) {
             const size_t off = (((size_t)vb * (Mxe / 4) + (u >> 2)) * 256 + vi) * 4 + (u & 3);
@@ -678,6 +685,7 @@ struct EnergyArgs {
     float *e_block, *gx, *gy;
     double *e_total;
     unsigned *status;
+    GradOut go;                          // what happens to gx, gy before they are written
 };
 
 // Energy-operand generator: one block, the stage's 32 consecutive u, written as
@@ -1138,8 +1146,8 @@ __device__ __forceinline__ void finish_segment(EnergyBars &bars, volatile int *a
     if (v0 == 0 && v1 == nvc - 1) {
         if (valid && ok) {
             if (args.e_block) args.e_block[b] = eN;
-            if (args.gx) args.gx[b] = eX;
-            if (args.gy) args.gy[b] = eY;
+            if (args.gx) args.gx[b] = grad_out(args.go, args.gx, b, eX);
+            if (args.gy) args.gy[b] = grad_out(args.go, args.gy, b, eY);
         }
         return;
     }
@@ -1163,8 +1171,8 @@ __device__ __forceinline__ void finish_segment(EnergyBars &bars, volatile int *a
         const float hY = side == 0 ? eY : o2, tY = side == 0 ? o2 : eY;
         if (valid && ok) {
             if (args.e_block) args.e_block[b] = hN + tN;
-            if (args.gx) args.gx[b] = hX + tX;
-            if (args.gy) args.gy[b] = hY + tY;
+            if (args.gx) args.gx[b] = grad_out(args.go, args.gx, b, hX + tX);
+            if (args.gy) args.gy[b] = grad_out(args.go, args.gy, b, hY + tY);
         }
     }
     // keep bars.split_old until every half-0 thread has read it
@@ -1537,7 +1545,8 @@ cudaError_t launch_energy_from_coeffs(const float *a, int Mx, int My, double W, 
 }
 
 cudaError_t launch_finish_tc(const Launch &L, int prec, const TcPlan &P, const float *part,
-                             const float *a_in, float *a_out, void *Khi, void *Klo, double *e_total) {
+                             const float *a_in, float *a_out, void *Khi, void *Klo, double *e_total,
+                             double *a64) {
     const size_t total = (size_t)P.Mxe * P.Mye;
     int blocks = (int)((total + 255) / 256);
     if (blocks > 8 * L.sm_count) blocks = 8 * L.sm_count;
@@ -1547,11 +1556,12 @@ cudaError_t launch_finish_tc(const Launch &L, int prec, const TcPlan &P, const f
     auto kfn = prec == 1 ? tc_finish_kernel<1> : tc_finish_kernel<2>;
     return launch_dependent(kfn, dim3(blocks), dim3(256), 0, L.stream, part, P.slices, P.Mxc, P.Myc, a_in,
                             a_out, Khi, Klo, L.Mx, L.My, P.Mxe, P.Mye, piW, piH, invWH,
-                            a_in ? nullptr : e_total, L.esplit_cnt, L.esplit_n);
+                            a_in ? nullptr : e_total, L.esplit_cnt, L.esplit_n, a_in ? nullptr : a64);
 }
 
 cudaError_t launch_energy_tc(const Launch &L, int prec, int sample, const TcPlan &P, void *Khi,
-                             void *Klo, float *e_block, double *e_total, float *gx, float *gy) {
+                             void *Klo, float *e_block, double *e_total, float *gx, float *gy,
+                             const GradOut &go) {
     if (L.n == 0) return cudaSuccess;
     CUtensorMap mh, ml;
     const bool bf = prec == 2;
@@ -1571,6 +1581,7 @@ cudaError_t launch_energy_tc(const Launch &L, int prec, int sample, const TcPlan
     a.gx = gx;
     a.gy = gy;
     a.e_total = e_total;
+    a.go = go;
     a.status = L.status;
     a.tiles = (L.n + E_ROWS - 1) / E_ROWS;
     a.split = L.esplit;

@@ -8,10 +8,11 @@ movable blocks with pp_descent_step:  x <- clamp(x - lr * dE/dx + j, w/2, W - w/
 drawn on the device (Philox4x32-10 counted by (block, step), Box-Muller).
 
 Chunked evaluation.  The coefficients are a sum over blocks (Eq. aup sums over
-i), so with the blocks cut into chunks, a = sum_c a(chunk c) (pp_coeffs per chunk)
-and each chunk's gradients follow from pp_grad with that total a; the total
-energy is 1/2 sum_uv a_uv S_uv of the total a (pp_energy_from_coeffs).  This
-bounds the workspace by the chunk size for placements too large for one call.
+i), so with the blocks cut into chunks, a = sum_c a(chunk c), summed in FP64 on
+the device by pp_coeffs_accumulate, and each chunk's gradients follow from
+pp_grad with that total a; the total energy is 1/2 sum_uv a_uv S_uv of the total
+a (pp_energy_from_coeffs).  This bounds the workspace by the chunk size for
+placements too large for one call.
 """
 from __future__ import annotations
 
@@ -41,17 +42,17 @@ def evaluate_chunked(x, y, w, h, c, W, H, Mx, My, prec="tf32", chunk: Optional[i
         return gx, gy, et
     cuts = list(range(0, n, chunk)) + [n]
     sl = lambda t, a, b: None if t is None else t[a:b]
-    a = None
-    for s, e in zip(cuts[:-1], cuts[1:]):
-        ac = binding.coeffs(x[s:e], y[s:e], w[s:e], h[s:e], sl(c, s, e), W, H, Mx, My, prec)
-        a = ac if a is None else a + ac
+    a64 = torch.zeros((Mx, My), dtype=torch.float64, device=x.device)
+    a = torch.empty((Mx, My), dtype=torch.float32, device=x.device)
+    for k, (s, e) in enumerate(zip(cuts[:-1], cuts[1:])):
+        last = k == len(cuts) - 2
+        binding.coeffs_accumulate(x[s:e], y[s:e], w[s:e], h[s:e], sl(c, s, e), W, H, Mx, My, a64, prec,
+                                  a_out=a if last else None)
     gx = torch.empty_like(x)
     gy = torch.empty_like(y)
     for s, e in zip(cuts[:-1], cuts[1:]):
-        gxc, gyc, _, _ = binding.grad(x[s:e], y[s:e], w[s:e], h[s:e], sl(c, s, e), W, H, Mx, My,
-                                      prec, a=a, want_energy=False)
-        gx[s:e] = gxc
-        gy[s:e] = gyc
+        binding.grad(x[s:e], y[s:e], w[s:e], h[s:e], sl(c, s, e), W, H, Mx, My, prec, a=a,
+                     out=(gx[s:e], gy[s:e], None, None))
     # E = 1/2 sum_uv a_uv S_uv from the summed coefficients (the whole placement's)
     return gx, gy, binding.energy_from_coeffs(a, W, H)
 

@@ -12,7 +12,9 @@ centres.
 
 Every array is float32 (the library's input type).  The die is [0, W] x [0, H].
 Centres are clamped so that each block lies inside the die, which is the
-setting of Eq. (global density): theta_i is supported inside R.
+setting of Eq. (global density): theta_i is supported inside R.  The one
+exception is `out_of_die_blocks`, which draws blocks that overhang an edge, lie
+outside the die or are wider than it, for the edge-case tests.
 """
 from __future__ import annotations
 
@@ -130,6 +132,53 @@ def cells_plus_fixed_macros(n_cells: int, n_macros: int, Mx: int, My: int, seed:
     return Placement(W, H, cat(p.x, mx), cat(p.y, my), cat(p.w, mw), cat(p.h, mh),
                      None, Mx, My, movable=mov, name=p.name,
                      meta={"cells": n_cells, "fixed_macros": n_macros})
+
+
+OUT_OF_DIE_KINDS = ("inside", "overhang", "centre-outside", "wider-than-die", "negative", "far")
+
+
+def out_of_die_blocks(n: int, Mx: int, My: int, seed: int, W: float = 1.0, H: float = 1.0,
+                      charge: bool = True) -> Placement:
+    """Blocks the workload generators never make: the die R = [0, W] x [0, H] of
+    Eq. (global density) no longer contains every block.  Per axis, each block is
+    drawn from one of OUT_OF_DIE_KINDS (cyclically, so every kind occurs on both
+    axes and in combination):
+      inside          centre uniform with the block inside, size lognormal (mean 0.05)
+      overhang        the block straddles a die edge (left/bottom or right/top)
+      centre-outside  the centre lies up to half a size beyond an edge
+      wider-than-die  size 1 to 2.5 times the die, centre uniform in the die
+      negative        centre in [-1.5 L, 0): the block mostly or wholly below 0
+      far             centre in (L, 3 L]: beyond the far edge, past 2 L
+    Charges uniform in [0.5, 1.5] (or None)."""
+    r_kx, r_ky, r_sx, r_sy, r_px, r_py, r_side, r_c = _streams(seed, 8)
+    kx = (np.arange(n) + r_kx.integers(0, len(OUT_OF_DIE_KINDS))) % len(OUT_OF_DIE_KINDS)
+    ky = (np.arange(n) // len(OUT_OF_DIE_KINDS) + r_ky.integers(0, len(OUT_OF_DIE_KINDS))) \
+        % len(OUT_OF_DIE_KINDS)
+
+    def axis(kind, r_s, r_p, L):
+        size = lognormal_with_mean(r_s, 0.05 * L, 0.5, n)
+        u = r_p.random(n)
+        side = r_side.random(n) < 0.5
+        pos = 0.5 * size + u * (L - size)                                # inside
+        edge = np.where(side, 0.0, L)
+        sgn = np.where(side, 1.0, -1.0)
+        over = edge + sgn * (u - 0.5) * size                             # straddles the edge
+        beyond = edge - sgn * u * 0.5 * size                             # centre past the edge
+        wide = r_s.uniform(1.0, 2.5, n) * L
+        pos = np.where(kind == 1, over, pos)
+        pos = np.where(kind == 2, beyond, pos)
+        size = np.where(kind == 3, wide, size)
+        pos = np.where(kind == 3, u * L, pos)
+        pos = np.where(kind == 4, -1.5 * L * u, pos)
+        pos = np.where(kind == 5, L + 2.0 * L * (1.0 - u), pos)
+        return pos, size
+
+    x, w = axis(kx, r_sx, r_px, W)
+    y, h = axis(ky, r_sy, r_py, H)
+    c = r_c.uniform(0.5, 1.5, n) if charge else None
+    return Placement(W, H, x.astype(np.float32), y.astype(np.float32), w.astype(np.float32),
+                     h.astype(np.float32), None if c is None else c.astype(np.float32), Mx, My,
+                     name="out-of-die", meta={"kinds_x": kx, "kinds_y": ky})
 
 
 # The five workloads: (n, Mx, My, recipe).  Index 0 is the small case the oracle

@@ -431,3 +431,66 @@ def test_workload_generator_is_deterministic_and_in_die():
     for P in (p, synth.workload(1, n=5000), synth.workload(3, n=3000)):
         assert np.all(P.x - P.w / 2 >= -1e-7) and np.all(P.x + P.w / 2 <= P.W + 1e-7)
         assert np.all(P.y - P.h / 2 >= -1e-7) and np.all(P.y + P.h / 2 <= P.H + 1e-7)
+
+
+# ---------------------------------------------------------------------------
+# 9. Blocks outside the die: the literal formula is the mirror fold
+# ---------------------------------------------------------------------------
+
+def _fold(lo, hi, L):
+    """Images in [0, L] of the interval [lo, hi] under the even, 2L-periodic
+    extension (t -> -t, t -> t + 2L): a list of (a, b, s) with s = +1 where the
+    piece keeps its orientation and -1 where it is mirrored."""
+    out = []
+    k = math.floor(lo / L)
+    while k * L < hi:
+        p, q = max(lo, k * L), min(hi, (k + 1) * L)
+        if q > p:
+            if k % 2 == 0:
+                out.append((p - k * L, q - k * L, 1.0))
+            else:
+                out.append(((k + 1) * L - q, (k + 1) * L - p, -1.0))
+        k += 1
+    return out
+
+
+def test_out_of_die_blocks_equal_their_mirror_folded_pieces():
+    """The paper's integrals assume every block inside R (Eq. global density).  For a
+    block that overhangs an edge, lies outside the die or is wider than it, the
+    closed forms of Eq. (aup), (au0), (a0p) applied as they stand equal the sum over
+    the block's pieces folded back into the die by mirror reflection at the walls
+    (the Neumann problem's even, 2L-periodic extension).  The pieces lie inside R,
+    so this pins the out-of-die reading on in-die evaluations: coefficients, the
+    block integral of psi (N_i) and of the field (the gradient, whose x or y part
+    flips sign on a mirrored piece)."""
+    W, H = 1.3, 0.7
+    p = synth.out_of_die_blocks(36, 23, 19, seed=77, W=W, H=H)
+    x, y, w, h, c = (np.asarray(v, np.float64) for v in (p.x, p.y, p.w, p.h, p.c))
+    Mx, My = p.Mx, p.My
+    assert not np.all((x - w / 2 >= 0) & (x + w / 2 <= W))
+    pieces = []          # (x, y, w, h, c, sx, sy, owner)
+    for i in range(len(x)):
+        for ax, bx, sx in _fold(x[i] - w[i] / 2, x[i] + w[i] / 2, W):
+            for ay, by, sy in _fold(y[i] - h[i] / 2, y[i] + h[i] / 2, H):
+                pieces.append(((ax + bx) / 2, (ay + by) / 2, bx - ax, by - ay, c[i], sx, sy, i))
+    P = np.array(pieces)
+    assert np.all(P[:, 0] - P[:, 2] / 2 >= -1e-12) and np.all(P[:, 0] + P[:, 2] / 2 <= W + 1e-12)
+    assert len(P) > 2 * len(x)
+    a = O.coefficients(W, H, x, y, w, h, c, Mx, My)
+    a_f = O.coefficients(W, H, P[:, 0], P[:, 1], P[:, 2], P[:, 3], P[:, 4], Mx, My)
+    assert np.max(np.abs(a - a_f)) <= 1e-11 * np.max(np.abs(a))
+    N, gx, gy = O.energy_grad(W, H, x, y, w, h, c, a)
+    Nf, gxf, gyf = O.energy_grad(W, H, P[:, 0], P[:, 1], P[:, 2], P[:, 3], P[:, 4], a)
+    own = P[:, 7].astype(int)
+    Ns = np.bincount(own, Nf, len(x))
+    gxs = np.bincount(own, P[:, 5] * gxf, len(x))
+    gys = np.bincount(own, P[:, 6] * gyf, len(x))
+    assert np.max(np.abs(N - Ns)) <= 1e-10 * np.max(np.abs(N))
+    g = max(np.max(np.abs(gx)), np.max(np.abs(gy)))
+    assert np.max(np.abs(gx - gxs)) <= 1e-10 * g
+    assert np.max(np.abs(gy - gys)) <= 1e-10 * g
+    # shifting a block by 2W, or mirroring it about 0, changes nothing
+    a2 = O.coefficients(W, H, np.r_[x[:5] + 2 * W, x[5:]], y, w, h, c, Mx, My)
+    am = O.coefficients(W, H, np.r_[-x[:5], x[5:]], y, w, h, c, Mx, My)
+    assert np.max(np.abs(a2 - a)) <= 1e-11 * np.max(np.abs(a))
+    assert np.max(np.abs(am - a)) <= 1e-11 * np.max(np.abs(a))
