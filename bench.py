@@ -15,8 +15,11 @@ are not available).
   python bench.py [--gpus N] [--steps K] [--warmup W] [--prec tf32|bf16x3|fp32]
   python bench.py --impl reference ...   (the FP64 CPU oracle on the host cores)
 
-Under torchrun (N > 1) every rank evaluates its own replica of the workload
-(no collective on the data path); the time is the maximum over ranks.
+Under torchrun (N > 1) the ranks share one placement of N x 200,000 blocks
+(each rank's 200,000 blocks; per-GPU work fixed, weak scaling): per step every
+rank adds its blocks' coefficients into an FP64 array, one all-reduce sums it
+over the ranks, and every rank evaluates its own blocks against the whole
+placement's coefficients; the time is the maximum over ranks.
 """
 from __future__ import annotations
 
@@ -188,12 +191,16 @@ def barrier(world):
 # ---------------------------------------------------------------------------
 # the step
 # ---------------------------------------------------------------------------
-def make_inputs(device, n=None, workload=WORKLOAD_INDEX, mode="grad"):
+def make_inputs(device, n=None, workload=WORKLOAD_INDEX, mode="grad", world=1, rank=0):
     import torch
-    from paper_2307_12041_gb300 import synth
+    from paper_2307_12041_gb300 import sharded, synth
     p = synth.workload(workload, n=n)
     if mode == "place":         # the loop's inputs: cells at 70% utilisation, started in a cluster
         p = synth.placement_cells(p.n, p.Mx, synth.BASE_SEED + 10 + workload)
+    if mode == "sharded":       # one placement of world x n blocks, this rank's contiguous share
+        whole = synth.workload(workload, n=world * p.n)
+        p = sharded.shard(whole, world, rank)
+        p.name = f"{synth.WORKLOADS[workload]['name']} x{world} blocks, sharded"
     t = lambda a: torch.from_numpy(a).to(device)
     return p, (t(p.x), t(p.y), t(p.w), t(p.h), None)
 
@@ -236,6 +243,9 @@ def time_steps(binding, p, dev_in, prec, steps, warmup, flush, outs, kernel_timi
         # (for this exact-density loop the two take the same time per iteration)
         placer = placemod.Placer(p, ptr, pins, prec, graph=False)
         run = placer.step
+    elif mode == "sharded":      # this rank's blocks of one placement: one FP64 all-reduce per step
+        from paper_2307_12041_gb300 import sharded
+        run = lambda: sharded.evaluate(x, y, w, h, c, p.W, p.H, p.Mx, p.My, prec)
     elif mode == "binned":
         m = max(p.Mx, p.My) if bins is None else bins
         bprec = "tf32" if prec == "bf16x3" else prec
@@ -263,7 +273,7 @@ def time_steps(binding, p, dev_in, prec, steps, warmup, flush, outs, kernel_timi
     return [a.elapsed_time(b) for a, b in evs], ktimes
 
 
-def time_e2e(binding, p, prec, steps, device, flush):
+def time_e2e(binding, p, prec, steps, device, flush, mode="grad", bins=None):
     """Same evaluation through host buffers: every step copies its x, y, w, h in
     from pinned host memory, runs pp_grad, and copies its gx, gy, N, E out, all
     inside the step's CUDA events (one stream, so copies and compute are serial);
@@ -286,8 +296,20 @@ def time_e2e(binding, p, prec, steps, device, flush):
     def step():
         for d, hsrc in zip(din, hin):
             d.copy_(hsrc, non_blocking=True)
-        binding.grad(din[0], din[1], din[2], din[3], None, p.W, p.H, p.Mx, p.My, prec, out=dout)
-        for hdst, d in zip(hout, dout):
+        if mode == "sharded":
+            from paper_2307_12041_gb300 import sharded
+            gx, gy, eb, et, _ = sharded.evaluate(din[0], din[1], din[2], din[3], None, p.W, p.H, p.Mx, p.My,
+                                                 prec)
+            res = (gx, gy, eb, et)
+        elif mode == "binned":
+            gx, gy, eb, et, _ = binding.binned_grad(din[0], din[1], din[2], din[3], None, p.W, p.H, p.Mx, p.My,
+                                                    bins, "tf32" if prec == "bf16x3" else prec,
+                                                    want_coeffs=False)
+            res = (gx, gy, eb, et)
+        else:
+            binding.grad(din[0], din[1], din[2], din[3], None, p.W, p.H, p.Mx, p.My, prec, out=dout)
+            res = dout
+        for hdst, d in zip(hout, res):
             hdst.copy_(d, non_blocking=True)
 
     for _ in range(3):
@@ -420,8 +442,10 @@ def run_ours(args):
     from paper_2307_12041_gb300 import binding, synth
 
     world, rank, local = dist_info()
-    dist_init(world, "nccl")
     torch.cuda.set_device(local)
+    dist_init(world, "nccl")
+    if args.mode is None:       # one placement shared out over the ranks when there are several
+        args.mode = "grad" if world == 1 else "sharded"
     device = torch.device("cuda", local)
     binding.lib()
     avail = binding.available_precisions()
@@ -430,9 +454,9 @@ def run_ours(args):
         raise SystemExit(f"precision {prec} not available: {avail}")
     # the precision the 1e-4 accuracy target binds, timed in the same run on the
     # same workload (its own line object; the headline `value` stays `prec`)
-    extra = [q for q in ("bf16x3",) if q != prec and q in avail and args.mode == "grad"]
+    extra = [q for q in ("bf16x3",) if q != prec and q in avail and args.mode in ("grad", "sharded")]
 
-    p, dev_in = make_inputs(device, workload=args.workload, mode=args.mode)
+    p, dev_in = make_inputs(device, workload=args.workload, mode=args.mode, world=world, rank=rank)
     n = p.n
     outs = (torch.empty(n, dtype=torch.float32, device=device),
             torch.empty(n, dtype=torch.float32, device=device),
@@ -470,9 +494,9 @@ def run_ours(args):
     ms_per_step = total_ms / args.steps
 
     peaks, peak_src = load_peaks()
-    if ktimes is None:      # binned mode: five kernels of ours and eight cuBLAS GEMMs per step
-        ktimes = {"coeff": (0, 0.0), "energy": (0, 0.0)}
-        launches = 5 * args.steps
+    if ktimes is None:      # binned mode: 13 kernels per step (density, 7 transforms, 3 transposes,
+        ktimes = {"coeff": (0, 0.0), "energy": (0, 0.0)}        # scale, interpolation), not counted
+        launches = 13 * args.steps                              # by the library's counters
     else:
         launches = int(sum(v[0] for v in counts.values()))     # our kernels in the timed steps
     extra_lines = {}
@@ -488,34 +512,43 @@ def run_ours(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": prec,
         "data": "synthetic",
-        "config": {"workload": p.name if args.mode == "place" else synth.WORKLOADS[args.workload]["name"],
+        "config": {"workload": p.name if args.mode in ("place", "sharded") else synth.WORKLOADS[args.workload]["name"],
                    "mode": args.mode,
                    "bins": (args.bins or max(p.Mx, p.My)) if args.mode == "binned" else None, "n": n, "Mx": p.Mx,
                    "My": p.My, "sample": "rect", "precision": prec, "W": p.W, "H": p.H,
                    "l2": "flushed: 256 MiB written before every timed step",
                    "kernel_times": "per-launch CUDA events in a second pass of the same steps",
-                   "parallelism": f"replicas x{world}"},
+                   "parallelism": (f"blocks sharded over {world} ranks (one FP64 all-reduce of the "
+                                   f"{p.Mx} x {p.My} coefficient sums per step)") if args.mode == "sharded"
+                                  else f"replicas x{world}"},
         "roofline": roofline(prec, ktimes, terms, peaks, peak_src),
         "kernels_ms_per_step": {k: v[1] / args.steps for k, v in ktimes.items()},
         "gpu_launches": launches + sum(v["gpu_launches"] for v in extra_lines.values()),
         "clocks": clk,
     }
     line.update(extra_lines)
+    # end to end through host buffers: every rank (the sharded evaluation holds a collective)
+    barrier(world)
+    e_mode = args.mode if args.mode in ("grad", "sharded", "binned") else "grad"
+    e_ms, h2d, d2h = time_e2e(binding, p, prec, args.steps, device, flush, mode=e_mode,
+                              bins=args.bins or max(p.Mx, p.My))
+    e_ms = reduce_max(e_ms, world, device)
+    line["e2e"] = {"value": world * terms / (e_ms / 1e3), "unit": "terms/s",
+                   "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                   "ms_per_step": e_ms, "mode": e_mode}
     if rank == 0:
-        # FP32 plain on the same workload (the "vs FP32" half of the metric)
+        # FP32 plain on the same workload (the "vs FP32" half of the metric); in sharded
+        # mode on rank 0's blocks alone, with no collective (the other ranks wait)
         if prec != "fp32":
             torch.cuda.synchronize()
+            f_mode = "grad" if args.mode == "sharded" else args.mode
             f_ms, _ = time_steps(binding, p, dev_in, "fp32", args.steps, args.warmup, flush, outs,
-                                 mode=args.mode, bins=args.bins)
+                                 mode=f_mode, bins=args.bins)
             fv = terms * args.steps / (sum(f_ms) / 1e3)
             line["fp32_plain"] = {"value": fv, "ms_per_step": sum(f_ms) / args.steps,
                                   "speedup_of_mixed": value / world / fv}
             for q, ql in extra_lines.items():
                 ql["speedup_over_fp32_plain"] = ql["value"] / world / fv
-        e_ms, h2d, d2h = time_e2e(binding, p, prec, args.steps, device, flush)
-        line["e2e"] = {"value": world * terms / (e_ms / 1e3), "unit": "terms/s",
-                       "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                       "ms_per_step": e_ms}
         if world == 1 and not args.no_cpu_baseline:
             precs = [prec] + extra + (["fp32"] if prec != "fp32" else [])
             base, errs = cpu_baseline(binding, precs, device, args.cpu_sample, args.workload)
@@ -579,8 +612,12 @@ def main(argv=None):
     ap.add_argument("--workload", type=int, default=WORKLOAD_INDEX,
                     help="synth.WORKLOADS index (default: the metric's 200k x 512^2 workload)")
     ap.add_argument("--bins", type=int, default=None, help="bins per side for --mode binned")
-    ap.add_argument("--mode", choices=["grad", "autograd", "block-adjoint", "binned", "place"], default="grad",
-                    help="grad: one pp_grad per step; autograd: energy forward + adjoint backward; "
+    ap.add_argument("--mode", choices=["grad", "sharded", "autograd", "block-adjoint", "binned", "place"],
+                    default=None,
+                    help="default: grad on one GPU, sharded on several; "
+                         "grad: one pp_grad per step; sharded: one placement of N x the workload's blocks "
+                         "shared out over the N ranks (pp_coeffs_accumulate, an FP64 all-reduce, pp_grad "
+                         "with the summed coefficients); autograd: energy forward + adjoint backward; "
                          "block-adjoint: per-block energies forward + vector-output adjoint; "
                          "binned: the binned fast scheme (terms counted as N Mx My); "
                          "place: one iteration of the Sec. IV placement loop (density, LSE "

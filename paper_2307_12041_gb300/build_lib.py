@@ -3,8 +3,8 @@
 Each translation unit is compiled by its own nvcc process (in parallel), then
 linked with `nvcc -shared`.  The CUDA runtime is linked statically; the driver
 API (tensor-map encoding) is reached through cudaGetDriverEntryPoint, so the
-library needs no -lcuda; cuBLAS (the binned scheme's transform GEMMs) is linked
-dynamically.  Objects go to `_build/` next to this file.
+library needs no -lcuda, and it links no other CUDA library.  Objects go to
+`_build/` next to this file.
 """
 from __future__ import annotations
 
@@ -71,7 +71,7 @@ def build(verbose: bool = False, force: bool = False) -> str:
     if failed:
         raise RuntimeError("nvcc failed:\n" + "\n".join(f"--- {s}\n{o}" for s, o in failed))
     tmp = LIB + ".tmp"
-    cmd = [cc] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcublas"]
+    cmd = [cc] + ARCH + ["-shared", "-o", tmp] + objs
     if verbose:
         print(" ".join(cmd), flush=True)
     subprocess.run(cmd, check=True)

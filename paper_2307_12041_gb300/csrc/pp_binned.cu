@@ -1,18 +1,24 @@
 // The paper's binned fast scheme (Sec. III-D) on the GPU:
 //   bin_density_kernel    P_lj = sum_i c_i area(block i ∩ bin lj) / area(bin)
-//   trig_kernel           C[u][l] = cos(u (l + 1/2) pi / m), S[u][l] = sin(...)
-//   cuBLAS GEMMs          a' = Cx P Cy^T;  psi = Cx^T a Cy;  xi_x = Sx^T (k o a) Cy;
-//                         xi_y = Cx^T (a o l) Sy   (Eq. disa, dis-psi1, dis-ksi)
-//   scale_kernel          a = (Eq. disa prefactors) o a';  k o a;  a o l
+//   transform kernels     the cosine / sine transforms of Eq. (disa), (dis-psi1) and
+//                         (dis-ksi) along one grid axis at a time, one CTA per row:
+//                           a'   = Cx P Cy^T            (DCT-II along j, then along l)
+//                           psi  = Cx^T a Cy            (DCT-III along v, then along u)
+//                           xi_x = Sx^T (k o a) Cy      (DCT-III along v, DST-III along u)
+//                           xi_y = Cx^T (a o l) Sy      (DST-III along v, DCT-III along u)
+//                         with C[u][l] = cos(pi u (2l + 1) / 2m), S likewise with sin.
+//                         For m a power of two each transform is one m-point complex
+//                         FFT in shared memory (the paper computes these transforms with
+//                         the FFT: O(m^2 log m) per 2-D transform); other m use a direct
+//                         sum over a shared-memory table of cos(pi q / 2m), q < 4m.
+//   transpose_kernel      between the two axes of a 2-D transform
+//   scale_kernel          a = (Eq. disa prefactors) o a'
 //   interp_kernel         bilinear weighting of the bin-centre values at each block
 //                         centre: N_i = q_i psi_i, grad = -q_i xi_i, E = 1/2 sum N_i
-// The transforms are dense products of an m-point cosine / sine matrix with an
-// m x m grid: plain GEMMs, issued to cuBLAS (FP32, or TF32 tensor cores).
-#include <cublas_v2.h>
+// Every transform runs in FP32.
 #include <cuda_runtime.h>
 
 #include <cmath>
-#include <mutex>
 
 #include "pp_internal.h"
 
@@ -72,23 +78,10 @@ __global__ void bin_density_kernel(const float *__restrict__ x, const float *__r
     }
 }
 
-// C, S: M x m, angle pi u (2l + 1) / (2m) reduced exactly in integers
-__global__ void trig_kernel(int M, int m, float *__restrict__ C, float *__restrict__ S) {
-    const long long total = (long long)M * m;
-    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < total;
-         k += (long long)gridDim.x * blockDim.x) {
-        const int u = (int)(k / m), l = (int)(k % m);
-        const long long q = ((long long)u * (2 * l + 1)) % (4LL * m);   // in units of pi / (2m)
-        float s, co;
-        sincospif((float)q / (float)(2 * m), &s, &co);
-        C[k] = co;
-        S[k] = s;
-    }
-}
-
-// a = prefactor o a' (Eq. disa-a..d), ka = (u pi / W) a, al = a (p pi / H); FP32
-__global__ void scale_kernel(int Mx, int My, int m, float W, float H, const float *__restrict__ ap,
-                             float *__restrict__ a, float *__restrict__ ka, float *__restrict__ al) {
+// a = prefactor o a' (Eq. disa-a..d), FP32; a' arrives transposed (apt[p][u], row
+// stride Mx), a leaves u-major (a[u][p]).
+__global__ void scale_kernel(int Mx, int My, int m, float W, float H, const float *__restrict__ apt,
+                             float *__restrict__ a) {
     const float PI = 3.14159265358979f;
     const float inv_pi3 = 1.f / (PI * PI * PI), inv_pi4 = inv_pi3 / PI;
     const long long total = (long long)Mx * My;
@@ -102,10 +95,158 @@ __global__ void scale_kernel(int Mx, int My, int m, float W, float H, const floa
         else if (p == 0 && u > 0) f = 4.f * W * W * inv_pi3 / (fu * fu * fu * (float)m) * su;
         else if (u > 0 && p > 0)
             f = 16.f * (W * W) * (H * H) * inv_pi4 / (fu * fp * (fu * fu * H * H + fp * fp * W * W)) * su * sp;
-        const float av = f * ap[k];
-        a[k] = av;
-        ka[k] = (fu * PI / W) * av;
-        al[k] = av * (fp * PI / H);
+        a[k] = f * apt[(size_t)p * Mx + u];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// One-dimensional transforms along rows, one CTA per row.
+//   DCT2:  X_u = sum_{l < kin} x_l cos(pi u (2l + 1) / 2m),          u < keep
+//   DCT3:  T_l = sum_{u < kin} s_u c_u cos(pi u (2l + 1) / 2m),      l < m
+//   DST3:  T_l = sum_{u < kin} s_u c_u sin(pi u (2l + 1) / 2m),      l < m
+// with s_u = u * in_scale when in_scale != 0, else 1 (the k_u, l_p factors of
+// Eq. dis-ksi applied on the fly).
+// FFT form (m a power of two; Makhoul's reordering): DCT2: y_k = x_2k, y_{m-1-k} =
+// x_{2k+1}, Y = DFT(y), X_u = Re(e^{-i pi u / 2m} Y_u).  DCT3: Y_u = e^{i pi u / 2m}
+// (c_u - i c_{m-u}) (c_m = 0), z = unnormalised inverse DFT(Y), then m x_2k = Re z_k,
+// m x_{2k+1} = Re z_{m-1-k} and T_l = (m x_l + c_0) / 2.  DST3: sin(pi u (2l + 1) /
+// 2m) = (-1)^l cos(pi (m - u)(2l + 1) / 2m), i.e. the DCT3 of c'_u = c_{m-u} (c'_0 =
+// 0) with alternating signs.
+// ---------------------------------------------------------------------------
+enum { T_DCT2 = 0, T_DCT3 = 1, T_DST3 = 2 };
+constexpr int T_THREADS = 256;
+
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(T_THREADS) fft_rows_kernel(const float *__restrict__ in, int in_ld, int kin,
+                                                           float in_scale, int m, int log2m, int keep,
+                                                           float *__restrict__ out, int out_ld) {
+    extern __shared__ float2 sm2[];
+    float2 *buf = sm2;                 // m values
+    float2 *tw = sm2 + m;              // m / 2 twiddles e^{-2 pi i k / m}
+    const float *row = in + (size_t)blockIdx.x * in_ld;
+    const int half = m >> 1;
+    for (int k = threadIdx.x; k < half; k += blockDim.x) {
+        float sn, cs;
+        sincospif(2.0f * (float)k / (float)m, &sn, &cs);      // exact argument: m is a power of two
+        tw[k] = make_float2(cs, -sn);
+    }
+    auto coef = [&](int u) -> float {                           // s_u c_u, 0 beyond kin
+        if (u < 0 || u >= kin) return 0.f;
+        const float v = row[u];
+        return in_scale != 0.f ? v * ((float)u * in_scale) : v;
+    };
+    const int shift = 32 - log2m;
+    for (int k = threadIdx.x; k < m; k += blockDim.x) {
+        float2 v;
+        if (MODE == T_DCT2) {
+            const int src = k < half ? 2 * k : 2 * (m - 1 - k) + 1;
+            v = make_float2(src < kin ? row[src] : 0.f, 0.f);
+        } else {
+            // DCT3 of c (MODE DCT3) or of c'_u = c_{m-u}, c'_0 = 0 (MODE DST3)
+            const float cu = MODE == T_DCT3 ? coef(k) : (k == 0 ? 0.f : coef(m - k));
+            const float cmu = k == 0 ? 0.f : (MODE == T_DCT3 ? coef(m - k) : coef(k));
+            float sn, cs;
+            sincospif((float)k / (float)(2 * m), &sn, &cs);
+            v = make_float2(cs * cu + sn * cmu, sn * cu - cs * cmu);   // e^{i theta} (cu - i cmu)
+        }
+        buf[__brev((unsigned)k) >> shift] = v;
+    }
+    __syncthreads();
+    // iterative radix-2 decimation in time; DCT2 forward, DCT3 / DST3 inverse (conjugate twiddles)
+    for (int s = 1; s <= log2m; ++s) {
+        const int hs = 1 << (s - 1), step = m >> s;
+        for (int b = threadIdx.x; b < half; b += blockDim.x) {
+            const int pos = b & (hs - 1);
+            const int i = ((b >> (s - 1)) << s) + pos, j = i + hs;
+            float2 w = tw[pos * step];
+            if (MODE != T_DCT2) w.y = -w.y;
+            const float2 t = cmul(w, buf[j]);
+            const float2 x = buf[i];
+            buf[i] = make_float2(x.x + t.x, x.y + t.y);
+            buf[j] = make_float2(x.x - t.x, x.y - t.y);
+        }
+        __syncthreads();
+    }
+    float *orow = out + (size_t)blockIdx.x * out_ld;
+    if (MODE == T_DCT2) {
+        for (int u = threadIdx.x; u < keep; u += blockDim.x) {
+            float sn, cs;
+            sincospif((float)u / (float)(2 * m), &sn, &cs);
+            orow[u] = buf[u].x * cs + buf[u].y * sn;
+        }
+    } else {
+        const float c0 = MODE == T_DCT3 ? coef(0) : 0.f;
+        for (int l = threadIdx.x; l < m; l += blockDim.x) {
+            const float mx = (l & 1) ? buf[m - 1 - (l >> 1)].x : buf[l >> 1].x;
+            const float t = 0.5f * (mx + c0);
+            orow[l] = (MODE == T_DST3 && (l & 1)) ? -t : t;
+        }
+    }
+}
+
+// The same transforms for any m: direct sums over a table cos(pi q / 2m), q < 4m
+// (sin(pi q / 2m) = cos(pi (q - m) / 2m)); the phase u (2l + 1) is kept mod 4m in
+// integers.
+template <int MODE>
+__global__ void __launch_bounds__(T_THREADS) direct_rows_kernel(const float *__restrict__ in, int in_ld, int kin,
+                                                              float in_scale, int m, int keep,
+                                                              float *__restrict__ out, int out_ld) {
+    extern __shared__ float smf[];
+    float *tab = smf;                  // 4m
+    float *x = smf + 4 * m;            // the row's inputs (kin of them)
+    const float *row = in + (size_t)blockIdx.x * in_ld;
+    const int m4 = 4 * m;
+    for (int q = threadIdx.x; q < m4; q += blockDim.x) tab[q] = cospif((float)q / (float)(2 * m));
+    for (int u = threadIdx.x; u < kin; u += blockDim.x) {
+        const float v = row[u];
+        x[u] = (MODE != T_DCT2 && in_scale != 0.f) ? v * ((float)u * in_scale) : v;
+    }
+    __syncthreads();
+    float *orow = out + (size_t)blockIdx.x * out_ld;
+    if (MODE == T_DCT2) {
+        for (int u = threadIdx.x; u < keep; u += blockDim.x) {
+            float acc = 0.f;
+            int q = u % m4;                          // u (2l + 1) at l = 0
+            const int dq = (2 * u) % m4;
+            for (int l = 0; l < kin; ++l) {
+                acc = fmaf(x[l], tab[q], acc);
+                q += dq;
+                if (q >= m4) q -= m4;
+            }
+            orow[u] = acc;
+        }
+    } else {
+        for (int l = threadIdx.x; l < m; l += blockDim.x) {
+            float acc = 0.f;
+            const int dq = 2 * l + 1;                // phase step per u
+            int q = MODE == T_DST3 ? m4 - m : 0;     // u (2l + 1) - m (sine) at u = 0, mod 4m
+            for (int u = 0; u < kin; ++u) {
+                acc = fmaf(x[u], tab[q], acc);
+                q += dq;
+                if (q >= m4) q -= m4;
+            }
+            orow[l] = acc;
+        }
+    }
+}
+
+// out[c][r] = in[r][c] for r < R, c < C (32 x 32 tiles through shared memory)
+__global__ void transpose_kernel(const float *__restrict__ in, int in_ld, int R, int C, float *__restrict__ out,
+                                 int out_ld) {
+    __shared__ float t[32][33];
+    const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+    for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+        const int r = r0 + k, c = c0 + threadIdx.x;
+        if (r < R && c < C) t[k][threadIdx.x] = in[(size_t)r * in_ld + c];
+    }
+    __syncthreads();
+    for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+        const int c = c0 + k, r = r0 + threadIdx.x;
+        if (r < R && c < C) out[(size_t)c * out_ld + r] = t[threadIdx.x][k];
     }
 }
 
@@ -121,7 +262,8 @@ __global__ void interp_kernel(const float *__restrict__ x, const float *__restri
         const float fy = fminf(fmaxf(y[i] * inv_hb - 0.5f, 0.f), (float)(m - 1));
         const int l0 = min((int)fx, m - 2), j0 = min((int)fy, m - 2);
         const float tx = fx - (float)l0, ty = fy - (float)j0;
-        const size_t k00 = (size_t)l0 * m + j0, k10 = k00 + m, k01 = k00 + 1, k11 = k10 + 1;
+        // bin-centre values are stored transposed: V[j * m + l]
+        const size_t k00 = (size_t)j0 * m + l0, k10 = k00 + 1, k01 = k00 + m, k11 = k01 + 1;
         const float w00 = (1.f - tx) * (1.f - ty), w10 = tx * (1.f - ty), w01 = (1.f - tx) * ty, w11 = tx * ty;
         auto at = [&](const float *V) { return w00 * V[k00] + w10 * V[k10] + w01 * V[k01] + w11 * V[k11]; };
         const float q = (c ? c[i] : 1.f) * w[i] * h[i];
@@ -138,19 +280,6 @@ __global__ void interp_kernel(const float *__restrict__ x, const float *__restri
     }
 }
 
-std::mutex g_cublas_mu;
-cublasHandle_t g_cublas[64];
-
-// C = op(A) op(B) on row-major matrices (C: M x N, inner K) through column-major cuBLAS:
-// C^T = op(B)^T op(A)^T, the buffers read as their transposes.
-cublasStatus_t gemm_rm(cublasHandle_t hd, bool tf32, bool ta, bool tb, int M, int N, int K, const float *A,
-                       int lda, const float *B, int ldb, float *C, int ldc) {
-    const float one = 1.f, zero = 0.f;
-    return cublasGemmEx(hd, tb ? CUBLAS_OP_T : CUBLAS_OP_N, ta ? CUBLAS_OP_T : CUBLAS_OP_N, N, M, K, &one, B,
-                        CUDA_R_32F, ldb, A, CUDA_R_32F, lda, &zero, C, CUDA_R_32F, ldc,
-                        tf32 ? CUBLAS_COMPUTE_32F_FAST_TF32 : CUBLAS_COMPUTE_32F, CUBLAS_GEMM_DEFAULT);
-}
-
 }  // namespace
 
 BinnedLayout binned_layout(int m, int Mx, int My) {
@@ -163,16 +292,14 @@ BinnedLayout binned_layout(int m, int Mx, int My) {
     };
     const size_t mm = (size_t)m * m;
     L.P = take(mm);
-    L.Cx = take((size_t)Mx * m);
-    L.Sx = take((size_t)Mx * m);
-    L.Cy = take((size_t)My * m);
-    L.Sy = take((size_t)My * m);
-    L.T = take((size_t)Mx * m);
-    L.ap = take((size_t)Mx * My);
+    L.R1 = take((size_t)m * My);
+    L.R1t = take((size_t)My * m);
+    L.R2 = take((size_t)My * Mx);
     L.a = take((size_t)Mx * My);
-    L.ka = take((size_t)Mx * My);
-    L.al = take((size_t)Mx * My);
-    L.U = take((size_t)m * My);
+    L.U = take((size_t)Mx * m);
+    L.Up = take((size_t)Mx * m);
+    L.Ut = take((size_t)m * Mx);
+    L.Upt = take((size_t)m * Mx);
     L.psi = take(mm);
     L.xix = take(mm);
     L.xiy = take(mm);
@@ -187,14 +314,59 @@ cudaError_t launch_bin_density(const float *x, const float *y, const float *w, c
     return cudaGetLastError();
 }
 
+namespace {
+
+bool pow2(int m) { return m > 0 && (m & (m - 1)) == 0; }
+
+// rows transforms of `mode` (T_DCT2 / T_DCT3 / T_DST3), FFT when m is a power of two
+cudaError_t rows(int mode, const float *in, int in_ld, int nrows, int kin, float in_scale, int m, int keep,
+                 float *out, int out_ld, cudaStream_t st) {
+    if (nrows <= 0) return cudaSuccess;
+    cudaError_t e;
+    if (pow2(m)) {
+        int lg = 0;
+        while ((1 << lg) < m) ++lg;
+        const size_t smem = (size_t)(m + m / 2) * sizeof(float2);
+        auto go = [&](auto kfn) {
+            cudaError_t r = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (r != cudaSuccess) return r;
+            kfn<<<nrows, T_THREADS, smem, st>>>(in, in_ld, kin, in_scale, m, lg, keep, out, out_ld);
+            return cudaGetLastError();
+        };
+        e = mode == T_DCT2 ? go(fft_rows_kernel<T_DCT2>)
+                           : (mode == T_DCT3 ? go(fft_rows_kernel<T_DCT3>) : go(fft_rows_kernel<T_DST3>));
+    } else {
+        const size_t smem = (size_t)(4 * m + kin) * sizeof(float);
+        auto go = [&](auto kfn) {
+            cudaError_t r = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (r != cudaSuccess) return r;
+            kfn<<<nrows, T_THREADS, smem, st>>>(in, in_ld, kin, in_scale, m, keep, out, out_ld);
+            return cudaGetLastError();
+        };
+        e = mode == T_DCT2 ? go(direct_rows_kernel<T_DCT2>)
+                           : (mode == T_DCT3 ? go(direct_rows_kernel<T_DCT3>) : go(direct_rows_kernel<T_DST3>));
+    }
+    return e;
+}
+
+cudaError_t transpose(const float *in, int in_ld, int R, int C, float *out, int out_ld, cudaStream_t st) {
+    dim3 grid((C + 31) / 32, (R + 31) / 32), block(32, 8);
+    transpose_kernel<<<grid, block, 0, st>>>(in, in_ld, R, C, out, out_ld);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
 cudaError_t run_binned(const Launch &Lc, int dev, int m, bool tf32, unsigned char *ws, float *a_out, float *e_block,
                        float *gx, float *gy, double *e_total, const char **what) {
+    (void)dev;
+    (void)tf32;                        // the transforms are FP32 FFTs (or direct sums) in either precision
     const int Mx = Lc.Mx, My = Lc.My, n = Lc.n;
     const BinnedLayout B = binned_layout(m, Mx, My);
-    float *P = (float *)(ws + B.P), *Cx = (float *)(ws + B.Cx), *Sx = (float *)(ws + B.Sx);
-    float *Cy = (float *)(ws + B.Cy), *Sy = (float *)(ws + B.Sy), *T = (float *)(ws + B.T);
-    float *ap = (float *)(ws + B.ap), *a = a_out ? a_out : (float *)(ws + B.a);
-    float *ka = (float *)(ws + B.ka), *al = (float *)(ws + B.al), *U = (float *)(ws + B.U);
+    float *P = (float *)(ws + B.P), *R1 = (float *)(ws + B.R1), *R1t = (float *)(ws + B.R1t);
+    float *R2 = (float *)(ws + B.R2), *a = a_out ? a_out : (float *)(ws + B.a);
+    float *U = (float *)(ws + B.U), *Up = (float *)(ws + B.Up), *Ut = (float *)(ws + B.Ut);
+    float *Upt = (float *)(ws + B.Upt);
     float *psi = (float *)(ws + B.psi), *xix = (float *)(ws + B.xix), *xiy = (float *)(ws + B.xiy);
     cudaStream_t st = Lc.stream;
     *what = "binned scheme launch";
@@ -206,30 +378,27 @@ cudaError_t run_binned(const Launch &Lc, int dev, int m, bool tf32, unsigned cha
         bin_density_kernel<<<grid, 256, 0, st>>>(Lc.x, Lc.y, Lc.w, Lc.h, Lc.c, n, m, m / Lc.W, m / Lc.H, P);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
-    trig_kernel<<<grid, 256, 0, st>>>(Mx, m, Cx, Sx);
-    trig_kernel<<<grid, 256, 0, st>>>(My, m, Cy, Sy);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    {
-        std::lock_guard<std::mutex> lk(g_cublas_mu);
-        *what = "cuBLAS";
-        if (!g_cublas[dev] && cublasCreate(&g_cublas[dev]) != CUBLAS_STATUS_SUCCESS) return cudaErrorUnknown;
-        cublasHandle_t hd = g_cublas[dev];
-        if (cublasSetStream(hd, st) != CUBLAS_STATUS_SUCCESS) return cudaErrorUnknown;
-        bool ok = true;
-        ok &= gemm_rm(hd, tf32, false, false, Mx, m, m, Cx, m, P, m, T, m) == CUBLAS_STATUS_SUCCESS;      // T = Cx P
-        ok &= gemm_rm(hd, tf32, false, true, Mx, My, m, T, m, Cy, m, ap, My) == CUBLAS_STATUS_SUCCESS;    // a' = T Cy^T
-        if (!ok) return cudaErrorUnknown;
-        scale_kernel<<<grid, 256, 0, st>>>(Mx, My, m, (float)Lc.W, (float)Lc.H, ap, a, ka, al);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        ok &= gemm_rm(hd, tf32, true, false, m, My, Mx, Cx, m, a, My, U, My) == CUBLAS_STATUS_SUCCESS;     // Cx^T a
-        ok &= gemm_rm(hd, tf32, false, false, m, m, My, U, My, Cy, m, psi, m) == CUBLAS_STATUS_SUCCESS;    // psi
-        ok &= gemm_rm(hd, tf32, true, false, m, My, Mx, Sx, m, ka, My, U, My) == CUBLAS_STATUS_SUCCESS;    // Sx^T (k a)
-        ok &= gemm_rm(hd, tf32, false, false, m, m, My, U, My, Cy, m, xix, m) == CUBLAS_STATUS_SUCCESS;    // xi_x
-        ok &= gemm_rm(hd, tf32, true, false, m, My, Mx, Cx, m, al, My, U, My) == CUBLAS_STATUS_SUCCESS;    // Cx^T (a l)
-        ok &= gemm_rm(hd, tf32, false, false, m, m, My, U, My, Sy, m, xiy, m) == CUBLAS_STATUS_SUCCESS;    // xi_y
-        if (!ok) return cudaErrorUnknown;
-    }
-    *what = "binned scheme launch";
+    const float kW = (float)(3.141592653589793 / Lc.W), lH = (float)(3.141592653589793 / Lc.H);
+#define PP_STEP(expr)                              \
+    do {                                           \
+        if ((e = (expr)) != cudaSuccess) return e; \
+    } while (0)
+    // a' = Cx P Cy^T: along j (rows l of P), then along l
+    PP_STEP(rows(T_DCT2, P, m, m, m, 0.f, m, My, R1, My, st));
+    PP_STEP(transpose(R1, My, m, My, R1t, m, st));
+    PP_STEP(rows(T_DCT2, R1t, m, My, m, 0.f, m, Mx, R2, Mx, st));
+    scale_kernel<<<grid, 256, 0, st>>>(Mx, My, m, (float)Lc.W, (float)Lc.H, R2, a);
+    PP_STEP(cudaGetLastError());
+    // along v (rows u of a): U = a Cy (psi, xi_x), Up = (a o l) Sy (xi_y)
+    PP_STEP(rows(T_DCT3, a, My, Mx, My, 0.f, m, m, U, m, st));
+    PP_STEP(rows(T_DST3, a, My, Mx, My, lH, m, m, Up, m, st));
+    PP_STEP(transpose(U, m, Mx, m, Ut, Mx, st));
+    PP_STEP(transpose(Up, m, Mx, m, Upt, Mx, st));
+    // along u (rows j): psi = Cx^T U, xi_x = Sx^T (k o U), xi_y = Cx^T Up; stored [j][l]
+    PP_STEP(rows(T_DCT3, Ut, Mx, m, Mx, 0.f, m, m, psi, m, st));
+    PP_STEP(rows(T_DST3, Ut, Mx, m, Mx, kW, m, m, xix, m, st));
+    PP_STEP(rows(T_DCT3, Upt, Mx, m, Mx, 0.f, m, m, xiy, m, st));
+#undef PP_STEP
     if (n > 0) {
         interp_kernel<<<grid, 256, 0, st>>>(Lc.x, Lc.y, Lc.w, Lc.h, Lc.c, n, m, (float)(m / Lc.W),
                                             (float)(m / Lc.H), psi, xix, xiy, e_block, gx, gy, e_total);

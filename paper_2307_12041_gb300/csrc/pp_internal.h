@@ -87,10 +87,10 @@ cudaError_t launch_energy_tc(const Launch &L, int prec, int sample, const TcPlan
 void set_last_error(const char *msg);
 // Binned fast scheme (pp_binned.cu): workspace offsets (bytes) and the pipeline.
 struct BinnedLayout {
-    size_t P, Cx, Sx, Cy, Sy, T, ap, a, ka, al, U, psi, xix, xiy, total;
+    size_t P, R1, R1t, R2, a, U, Up, Ut, Upt, psi, xix, xiy, total;
 };
 BinnedLayout binned_layout(int m, int Mx, int My);
-// `what` names the failing step on error (a CUDA launch or a cuBLAS call)
+// `what` names the failing step on error
 cudaError_t run_binned(const Launch &L, int dev, int m, bool tf32, unsigned char *ws, float *a_out,
                        float *e_block, float *gx, float *gy, double *e_total, const char **what);
 // P[l m + j] += sum_i c_i area(block i ∩ bin lj) / area(bin) on an m x m grid (P zeroed by the caller)

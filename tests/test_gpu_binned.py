@@ -10,8 +10,9 @@ from paper_2307_12041_gb300 import synth
 
 pytestmark = pytest.mark.gpu
 
-# FP32: density by FP32 atomics, FP32 transforms over m terms; TF32 transforms
-BINNED_TOL = {"fp32": 2e-5, "tf32": 5e-3}
+# density by FP32 atomics, FP32 transforms (FFTs for m a power of two, direct sums
+# otherwise) in both precisions
+BINNED_TOL = {"fp32": 2e-5, "tf32": 2e-5}
 
 CASES = [
     # n, Mx, My, m, W, H, charge, kind
@@ -19,6 +20,10 @@ CASES = [
     (500, 64, 64, 64, 1.3, 0.8, True, "uniform"),
     (3000, 100, 90, 128, 1.0, 1.0, False, "mix"),
     (1, 2, 2, 2, 1.0, 1.0, False, "uniform"),
+    (20000, 256, 200, 512, 1.0, 1.0, False, "mix"),          # FFT, 9 radix-2 stages
+    (700, 50, 60, 96, 1.2, 0.9, True, "uniform"),             # m not a power of two: direct sums
+    (5, 3, 3, 3, 1.0, 1.0, False, "uniform"),
+    (4000, 90, 100, 100, 1.0, 1.0, False, "mix"),
 ]
 
 
