@@ -50,6 +50,12 @@ __device__ __forceinline__ long long fixed_bins(float x, double k) {
     return (xb >> 31) ? -(long long)q : (long long)q;
 }
 
+// Blocks covering at most kSmallBins bins are binned by their own thread; larger ones
+// (macros: up to thousands of bins) by the whole warp, which takes them one at a time
+// (found by a ballot) and shares out their bins, so that one large block does not
+// hold its warp for thousands of serial additions.
+constexpr int kSmallBins = 8;
+
 __global__ void bin_density_kernel(const float *__restrict__ x, const float *__restrict__ y,
                                    const float *__restrict__ w, const float *__restrict__ h,
                                    const float *__restrict__ c, int n, int m, double inv_wb,
@@ -57,22 +63,61 @@ __global__ void bin_density_kernel(const float *__restrict__ x, const float *__r
     constexpr int F = 40;                                 // fraction bits of a bin coordinate
     constexpr long long ONE = 1ll << F;
     const float unit = 0x1p-40f;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        // block edges in bin units, exact (2^-40 bins)
-        const long long cx = fixed_bins(x[i], inv_wb), hx = fixed_bins(w[i], 0.5 * inv_wb);
-        const long long cy = fixed_bins(y[i], inv_hb), hy = fixed_bins(h[i], 0.5 * inv_hb);
-        const long long x0 = cx - hx, x1 = cx + hx, y0 = cy - hy, y1 = cy + hy;
-        const int l0 = (int)max(0ll, x0 >> F), l1 = (int)min((long long)(m - 1), (x1 - 1) >> F);
-        const int j0 = (int)max(0ll, y0 >> F), j1 = (int)min((long long)(m - 1), (y1 - 1) >> F);
-        const float ci = c ? c[i] : 1.f;
-        for (int l = l0; l <= l1; ++l) {
-            const long long ox = min(x1, (long long)(l + 1) * ONE) - max(x0, (long long)l * ONE);
-            if (ox <= 0) continue;
-            const float cox = ci * ((float)ox * unit);
-            for (int j = j0; j <= j1; ++j) {
-                const long long oy = min(y1, (long long)(j + 1) * ONE) - max(y0, (long long)j * ONE);
-                if (oy <= 0) continue;
-                atomicAdd(&P[(size_t)l * m + j], cox * ((float)oy * unit));   // area / bin area
+    const int lane = threadIdx.x & 31;
+    const long long warps = ((long long)gridDim.x * blockDim.x) >> 5;
+    const long long wid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    // overlap of block [b0, b1) with bin k, in units of 2^-40 bins
+    auto overlap = [&](long long b0, long long b1, int k) {
+        return min(b1, (long long)(k + 1) * ONE) - max(b0, (long long)k * ONE);
+    };
+    // every lane of the warp runs every iteration (the warp-wide steps need them all)
+    for (long long base = wid * 32; base < n; base += warps * 32) {
+        const long long i = base + lane;
+        long long x0 = 0, x1 = 0, y0 = 0, y1 = 0;
+        int l0 = 0, l1 = -1, j0 = 0, j1 = -1;
+        float ci = 0.f;
+        if (i < n) {
+            // block edges in bin units, exact (2^-40 bins)
+            const long long cx = fixed_bins(x[i], inv_wb), hx = fixed_bins(w[i], 0.5 * inv_wb);
+            const long long cy = fixed_bins(y[i], inv_hb), hy = fixed_bins(h[i], 0.5 * inv_hb);
+            x0 = cx - hx;
+            x1 = cx + hx;
+            y0 = cy - hy;
+            y1 = cy + hy;
+            l0 = (int)max(0ll, x0 >> F);
+            l1 = (int)min((long long)(m - 1), (x1 - 1) >> F);
+            j0 = (int)max(0ll, y0 >> F);
+            j1 = (int)min((long long)(m - 1), (y1 - 1) >> F);
+            ci = c ? c[i] : 1.f;
+        }
+        const long long nl = l1 >= l0 ? l1 - l0 + 1 : 0, nj = j1 >= j0 ? j1 - j0 + 1 : 0;
+        const bool large = nl * nj > kSmallBins;
+        if (!large) {
+            for (int l = l0; l <= l1; ++l) {
+                const long long ox = overlap(x0, x1, l);
+                if (ox <= 0) continue;
+                const float cox = ci * ((float)ox * unit);
+                for (int j = j0; j <= j1; ++j) {
+                    const long long oy = overlap(y0, y1, j);
+                    if (oy <= 0) continue;
+                    atomicAdd(&P[(size_t)l * m + j], cox * ((float)oy * unit));   // area / bin area
+                }
+            }
+        }
+        unsigned todo = __ballot_sync(0xffffffffu, large);
+        while (todo) {
+            const int src = __ffs(todo) - 1;
+            todo &= todo - 1;
+            const long long bx0 = __shfl_sync(0xffffffffu, x0, src), bx1 = __shfl_sync(0xffffffffu, x1, src);
+            const long long by0 = __shfl_sync(0xffffffffu, y0, src), by1 = __shfl_sync(0xffffffffu, y1, src);
+            const int bl0 = __shfl_sync(0xffffffffu, l0, src), bj0 = __shfl_sync(0xffffffffu, j0, src);
+            const long long bnj = __shfl_sync(0xffffffffu, nj, src), tot = bnj * __shfl_sync(0xffffffffu, nl, src);
+            const float bc = __shfl_sync(0xffffffffu, ci, src);
+            for (long long k = lane; k < tot; k += 32) {
+                const int l = bl0 + (int)(k / bnj), j = bj0 + (int)(k % bnj);
+                const long long ox = overlap(bx0, bx1, l), oy = overlap(by0, by1, j);
+                if (ox > 0 && oy > 0)
+                    atomicAdd(&P[(size_t)l * m + j], bc * ((float)ox * unit) * ((float)oy * unit));
             }
         }
     }
@@ -120,20 +165,33 @@ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
     return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
 
+// Twiddle tables of an m-point transform (m a power of two), computed once per
+// evaluation: tw[k] = e^{-2 pi i k / m} (k < m/2) and qw[u] = (cos, sin)(pi u / 2m)
+// (u < m), from exact arguments.
+__global__ void fft_tables_kernel(int m, float2 *__restrict__ tw, float2 *__restrict__ qw) {
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < m; k += gridDim.x * blockDim.x) {
+        float sn, cs;
+        if (k < m / 2) {
+            sincospif(2.0f * (float)k / (float)m, &sn, &cs);
+            tw[k] = make_float2(cs, -sn);
+        }
+        sincospif((float)k / (float)(2 * m), &sn, &cs);
+        qw[k] = make_float2(cs, sn);
+    }
+}
+
 template <int MODE>
 __global__ void __launch_bounds__(T_THREADS) fft_rows_kernel(const float *__restrict__ in, int in_ld, int kin,
                                                            float in_scale, int m, int log2m, int keep,
-                                                           float *__restrict__ out, int out_ld) {
+                                                           float *__restrict__ out, int out_ld, int ostr,
+                                                           const float2 *__restrict__ tw_g,
+                                                           const float2 *__restrict__ qw) {
     extern __shared__ float2 sm2[];
     float2 *buf = sm2;                 // m values
     float2 *tw = sm2 + m;              // m / 2 twiddles e^{-2 pi i k / m}
     const float *row = in + (size_t)blockIdx.x * in_ld;
     const int half = m >> 1;
-    for (int k = threadIdx.x; k < half; k += blockDim.x) {
-        float sn, cs;
-        sincospif(2.0f * (float)k / (float)m, &sn, &cs);      // exact argument: m is a power of two
-        tw[k] = make_float2(cs, -sn);
-    }
+    for (int k = threadIdx.x; k < half; k += blockDim.x) tw[k] = tw_g[k];
     auto coef = [&](int u) -> float {                           // s_u c_u, 0 beyond kin
         if (u < 0 || u >= kin) return 0.f;
         const float v = row[u];
@@ -149,9 +207,8 @@ __global__ void __launch_bounds__(T_THREADS) fft_rows_kernel(const float *__rest
             // DCT3 of c (MODE DCT3) or of c'_u = c_{m-u}, c'_0 = 0 (MODE DST3)
             const float cu = MODE == T_DCT3 ? coef(k) : (k == 0 ? 0.f : coef(m - k));
             const float cmu = k == 0 ? 0.f : (MODE == T_DCT3 ? coef(m - k) : coef(k));
-            float sn, cs;
-            sincospif((float)k / (float)(2 * m), &sn, &cs);
-            v = make_float2(cs * cu + sn * cmu, sn * cu - cs * cmu);   // e^{i theta} (cu - i cmu)
+            const float2 q = qw[k];                                     // (cos, sin)(pi k / 2m)
+            v = make_float2(q.x * cu + q.y * cmu, q.y * cu - q.x * cmu);   // e^{i theta} (cu - i cmu)
         }
         buf[__brev((unsigned)k) >> shift] = v;
     }
@@ -174,16 +231,15 @@ __global__ void __launch_bounds__(T_THREADS) fft_rows_kernel(const float *__rest
     float *orow = out + (size_t)blockIdx.x * out_ld;
     if (MODE == T_DCT2) {
         for (int u = threadIdx.x; u < keep; u += blockDim.x) {
-            float sn, cs;
-            sincospif((float)u / (float)(2 * m), &sn, &cs);
-            orow[u] = buf[u].x * cs + buf[u].y * sn;
+            const float2 q = qw[u];
+            orow[(size_t)u * ostr] = buf[u].x * q.x + buf[u].y * q.y;
         }
     } else {
         const float c0 = MODE == T_DCT3 ? coef(0) : 0.f;
         for (int l = threadIdx.x; l < m; l += blockDim.x) {
             const float mx = (l & 1) ? buf[m - 1 - (l >> 1)].x : buf[l >> 1].x;
             const float t = 0.5f * (mx + c0);
-            orow[l] = (MODE == T_DST3 && (l & 1)) ? -t : t;
+            orow[(size_t)l * ostr] = (MODE == T_DST3 && (l & 1)) ? -t : t;
         }
     }
 }
@@ -194,7 +250,7 @@ __global__ void __launch_bounds__(T_THREADS) fft_rows_kernel(const float *__rest
 template <int MODE>
 __global__ void __launch_bounds__(T_THREADS) direct_rows_kernel(const float *__restrict__ in, int in_ld, int kin,
                                                               float in_scale, int m, int keep,
-                                                              float *__restrict__ out, int out_ld) {
+                                                              float *__restrict__ out, int out_ld, int ostr) {
     extern __shared__ float smf[];
     float *tab = smf;                  // 4m
     float *x = smf + 4 * m;            // the row's inputs (kin of them)
@@ -217,7 +273,7 @@ __global__ void __launch_bounds__(T_THREADS) direct_rows_kernel(const float *__r
                 q += dq;
                 if (q >= m4) q -= m4;
             }
-            orow[u] = acc;
+            orow[(size_t)u * ostr] = acc;
         }
     } else {
         for (int l = threadIdx.x; l < m; l += blockDim.x) {
@@ -229,7 +285,7 @@ __global__ void __launch_bounds__(T_THREADS) direct_rows_kernel(const float *__r
                 q += dq;
                 if (q >= m4) q -= m4;
             }
-            orow[l] = acc;
+            orow[(size_t)l * ostr] = acc;
         }
     }
 }
@@ -253,8 +309,7 @@ __global__ void transpose_kernel(const float *__restrict__ in, int in_ld, int R,
 __global__ void interp_kernel(const float *__restrict__ x, const float *__restrict__ y,
                               const float *__restrict__ w, const float *__restrict__ h,
                               const float *__restrict__ c, int n, int m, float inv_wb, float inv_hb,
-                              const float *__restrict__ psi, const float *__restrict__ xix,
-                              const float *__restrict__ xiy, float *__restrict__ e_block,
+                              const float4 *__restrict__ V, float *__restrict__ e_block,
                               float *__restrict__ gx, float *__restrict__ gy, double *__restrict__ e_total) {
     double e = 0.0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
@@ -262,15 +317,18 @@ __global__ void interp_kernel(const float *__restrict__ x, const float *__restri
         const float fy = fminf(fmaxf(y[i] * inv_hb - 0.5f, 0.f), (float)(m - 1));
         const int l0 = min((int)fx, m - 2), j0 = min((int)fy, m - 2);
         const float tx = fx - (float)l0, ty = fy - (float)j0;
-        // bin-centre values are stored transposed: V[j * m + l]
+        // bin-centre values (psi, xi_x, xi_y) at (l, j) are V[j * m + l]
         const size_t k00 = (size_t)j0 * m + l0, k10 = k00 + 1, k01 = k00 + m, k11 = k01 + 1;
         const float w00 = (1.f - tx) * (1.f - ty), w10 = tx * (1.f - ty), w01 = (1.f - tx) * ty, w11 = tx * ty;
-        auto at = [&](const float *V) { return w00 * V[k00] + w10 * V[k10] + w01 * V[k01] + w11 * V[k11]; };
+        const float4 v00 = V[k00], v10 = V[k10], v01 = V[k01], v11 = V[k11];
+        const float psi = w00 * v00.x + w10 * v10.x + w01 * v01.x + w11 * v11.x;
+        const float xix = w00 * v00.y + w10 * v10.y + w01 * v01.y + w11 * v11.y;
+        const float xiy = w00 * v00.z + w10 * v10.z + w01 * v01.z + w11 * v11.z;
         const float q = (c ? c[i] : 1.f) * w[i] * h[i];
-        const float Ni = q * at(psi);
+        const float Ni = q * psi;
         if (e_block) e_block[i] = Ni;
-        if (gx) gx[i] = -q * at(xix);
-        if (gy) gy[i] = -q * at(xiy);
+        if (gx) gx[i] = -q * xix;
+        if (gy) gy[i] = -q * xiy;
         e += 0.5 * (double)Ni;
     }
     if (e_total) {
@@ -300,9 +358,8 @@ BinnedLayout binned_layout(int m, int Mx, int My) {
     L.Up = take((size_t)Mx * m);
     L.Ut = take((size_t)m * Mx);
     L.Upt = take((size_t)m * Mx);
-    L.psi = take(mm);
-    L.xix = take(mm);
-    L.xiy = take(mm);
+    L.V = take(4 * mm);
+    L.tab = take(3 * (size_t)m);         // m/2 + m complex twiddles
     L.total = off;
     return L;
 }
@@ -319,8 +376,9 @@ namespace {
 bool pow2(int m) { return m > 0 && (m & (m - 1)) == 0; }
 
 // rows transforms of `mode` (T_DCT2 / T_DCT3 / T_DST3), FFT when m is a power of two
+// rows `nrows` of `in` transformed; output element k of row r at out[r * out_ld + k * ostr]
 cudaError_t rows(int mode, const float *in, int in_ld, int nrows, int kin, float in_scale, int m, int keep,
-                 float *out, int out_ld, cudaStream_t st) {
+                 float *out, int out_ld, int ostr, const float2 *tw, const float2 *qw, cudaStream_t st) {
     if (nrows <= 0) return cudaSuccess;
     cudaError_t e;
     if (pow2(m)) {
@@ -330,7 +388,7 @@ cudaError_t rows(int mode, const float *in, int in_ld, int nrows, int kin, float
         auto go = [&](auto kfn) {
             cudaError_t r = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             if (r != cudaSuccess) return r;
-            kfn<<<nrows, T_THREADS, smem, st>>>(in, in_ld, kin, in_scale, m, lg, keep, out, out_ld);
+            kfn<<<nrows, T_THREADS, smem, st>>>(in, in_ld, kin, in_scale, m, lg, keep, out, out_ld, ostr, tw, qw);
             return cudaGetLastError();
         };
         e = mode == T_DCT2 ? go(fft_rows_kernel<T_DCT2>)
@@ -340,7 +398,7 @@ cudaError_t rows(int mode, const float *in, int in_ld, int nrows, int kin, float
         auto go = [&](auto kfn) {
             cudaError_t r = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             if (r != cudaSuccess) return r;
-            kfn<<<nrows, T_THREADS, smem, st>>>(in, in_ld, kin, in_scale, m, keep, out, out_ld);
+            kfn<<<nrows, T_THREADS, smem, st>>>(in, in_ld, kin, in_scale, m, keep, out, out_ld, ostr);
             return cudaGetLastError();
         };
         e = mode == T_DCT2 ? go(direct_rows_kernel<T_DCT2>)
@@ -367,7 +425,8 @@ cudaError_t run_binned(const Launch &Lc, int dev, int m, bool tf32, unsigned cha
     float *R2 = (float *)(ws + B.R2), *a = a_out ? a_out : (float *)(ws + B.a);
     float *U = (float *)(ws + B.U), *Up = (float *)(ws + B.Up), *Ut = (float *)(ws + B.Ut);
     float *Upt = (float *)(ws + B.Upt);
-    float *psi = (float *)(ws + B.psi), *xix = (float *)(ws + B.xix), *xiy = (float *)(ws + B.xiy);
+    float *V = (float *)(ws + B.V);
+    float2 *tw = (float2 *)(ws + B.tab), *qw = tw + m / 2;
     cudaStream_t st = Lc.stream;
     *what = "binned scheme launch";
     cudaError_t e = cudaMemsetAsync(P, 0, (size_t)m * m * sizeof(float), st);
@@ -379,29 +438,34 @@ cudaError_t run_binned(const Launch &Lc, int dev, int m, bool tf32, unsigned cha
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     const float kW = (float)(3.141592653589793 / Lc.W), lH = (float)(3.141592653589793 / Lc.H);
+    if (pow2(m)) {
+        fft_tables_kernel<<<(m + 255) / 256, 256, 0, st>>>(m, tw, qw);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
 #define PP_STEP(expr)                              \
     do {                                           \
         if ((e = (expr)) != cudaSuccess) return e; \
     } while (0)
     // a' = Cx P Cy^T: along j (rows l of P), then along l
-    PP_STEP(rows(T_DCT2, P, m, m, m, 0.f, m, My, R1, My, st));
+    PP_STEP(rows(T_DCT2, P, m, m, m, 0.f, m, My, R1, My, 1, tw, qw, st));
     PP_STEP(transpose(R1, My, m, My, R1t, m, st));
-    PP_STEP(rows(T_DCT2, R1t, m, My, m, 0.f, m, Mx, R2, Mx, st));
+    PP_STEP(rows(T_DCT2, R1t, m, My, m, 0.f, m, Mx, R2, Mx, 1, tw, qw, st));
     scale_kernel<<<grid, 256, 0, st>>>(Mx, My, m, (float)Lc.W, (float)Lc.H, R2, a);
     PP_STEP(cudaGetLastError());
     // along v (rows u of a): U = a Cy (psi, xi_x), Up = (a o l) Sy (xi_y)
-    PP_STEP(rows(T_DCT3, a, My, Mx, My, 0.f, m, m, U, m, st));
-    PP_STEP(rows(T_DST3, a, My, Mx, My, lH, m, m, Up, m, st));
+    PP_STEP(rows(T_DCT3, a, My, Mx, My, 0.f, m, m, U, m, 1, tw, qw, st));
+    PP_STEP(rows(T_DST3, a, My, Mx, My, lH, m, m, Up, m, 1, tw, qw, st));
     PP_STEP(transpose(U, m, Mx, m, Ut, Mx, st));
     PP_STEP(transpose(Up, m, Mx, m, Upt, Mx, st));
-    // along u (rows j): psi = Cx^T U, xi_x = Sx^T (k o U), xi_y = Cx^T Up; stored [j][l]
-    PP_STEP(rows(T_DCT3, Ut, Mx, m, Mx, 0.f, m, m, psi, m, st));
-    PP_STEP(rows(T_DST3, Ut, Mx, m, Mx, kW, m, m, xix, m, st));
-    PP_STEP(rows(T_DCT3, Upt, Mx, m, Mx, 0.f, m, m, xiy, m, st));
+    // along u (rows j): psi = Cx^T U, xi_x = Sx^T (k o U), xi_y = Cx^T Up, stored interleaved
+    // as V[j][l] = (psi, xi_x, xi_y, unused) so that the interpolation reads one float4 per corner
+    PP_STEP(rows(T_DCT3, Ut, Mx, m, Mx, 0.f, m, m, V + 0, 4 * m, 4, tw, qw, st));
+    PP_STEP(rows(T_DST3, Ut, Mx, m, Mx, kW, m, m, V + 1, 4 * m, 4, tw, qw, st));
+    PP_STEP(rows(T_DCT3, Upt, Mx, m, Mx, 0.f, m, m, V + 2, 4 * m, 4, tw, qw, st));
 #undef PP_STEP
     if (n > 0) {
         interp_kernel<<<grid, 256, 0, st>>>(Lc.x, Lc.y, Lc.w, Lc.h, Lc.c, n, m, (float)(m / Lc.W),
-                                            (float)(m / Lc.H), psi, xix, xiy, e_block, gx, gy, e_total);
+                                            (float)(m / Lc.H), (const float4 *)V, e_block, gx, gy, e_total);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     return cudaSuccess;
