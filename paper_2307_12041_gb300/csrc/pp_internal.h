@@ -55,8 +55,9 @@ constexpr int kSimtKU = 32;     // u chunk of the FP32 energy kernel
 constexpr int kSimtKV = 128;    // v tile of the FP32 energy kernel
 inline int round_up(int a, int b) { return (a + b - 1) / b * b; }
 
-// Tensor-core path (pp_tc.cu).  Coefficient tiles are 256 x 256 (padded extents
-// Mxc, Myc); the energy operand is padded to (Mxe = 32k, Mye = 256k).  Blocks are
+// Tensor-core path (pp_tc.cu).  Coefficient tiles are 256 x 256, or 512 x 256 on
+// SM pairs when Mx exceeds 256 (padded extents Mxc, Myc); the energy operand is
+// padded to (Mxe = 32k, Mye = 256k).  Blocks are
 // cut into `slices` of slice_len for the persistent coefficient kernel; the plan
 // depends only on the problem (kPlanSMs sets the target of two units per SM).
 constexpr int kPlanSMs = 152;
@@ -71,6 +72,7 @@ inline int energy_boundaries(int n) {
 }
 struct TcPlan {
     int Mxc, Myc, Mxe, Mye, tiles, slices, slice_len;
+    int pair;             // 1: the coefficient kernel runs on SM pairs (512 x 256 tiles)
 };
 TcPlan tc_plan(int n, int Mx, int My);
 cudaError_t launch_coeff_tc(const Launch &L, int prec, const TcPlan &P, float *part);

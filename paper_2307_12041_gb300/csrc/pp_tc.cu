@@ -543,6 +543,533 @@ __global__ void __launch_bounds__(C_THREADS, 1) tc_coeff_kernel(const CoeffArgs 
 }
 
 // ===========================================================================
+// Coefficient contraction on SM pairs
+// ===========================================================================
+// The pair kernel runs the same contraction with the two CTAs of a cluster on two
+// SMs issuing M = 256 MMAs together (cta_group::2): per MMA each CTA supplies 128
+// rows of Xt (A) and half of the 256 columns of Yt (B) from its own shared memory,
+// and its tensor memory receives its 128 rows of the 256 x 256 result.  A CTA pair
+// covers a 512 (u) x 256 (v) tile with two such accumulators per CTA.  Compared with
+// one CTA per 256 x 256 tile, each SM generates and reads only half of the Yt
+// operand: 112 KB of shared-memory traffic per 32-block stage instead of 160 KB,
+// which is what bounds the single-CTA kernel.
+//
+// Rows of the pair tile held by CTA rank rk (0 or 1), accumulator acc (TMEM lane i):
+// TF32 mode tile_u0 + 256 acc + 2 i + rk (the two CTAs' rows interleaved, so that
+// each CTA's 256 A rows are one progression of step 2 that one recurrence chain per
+// generator thread covers), BF16x3 tile_u0 + 256 acc + 128 rk + i; its B columns are
+// v = tile_v0 + 128 rk + [0, 128).  The even CTA's thread 0 of warp 0 issues every MMA; its `full` and
+// `acc_empty` barriers count the warps of both CTAs, which arrive through cluster
+// addresses, and its commits arrive on the barriers of both CTAs (multicast).
+constexpr int P_STAGES = 4;
+constexpr int P_A_BYTES = 32768;                // 256 rows x 32 blocks
+constexpr int P_B_BYTES = 16384;                // 128 rows x 32 blocks
+constexpr int P_STAGE_BYTES = P_A_BYTES + P_B_BYTES;
+constexpr int P_TILE_U = 512;
+constexpr int P_TILE_V = 256;
+
+struct PairBars {
+    uint64_t full[P_STAGES];       // even CTA: generator warps of both CTAs
+    uint64_t empty[P_STAGES];      // both: MMA commit (multicast)
+    uint64_t recs_full[P_STAGES];  // local: record copies
+    uint64_t gen_done[P_STAGES];   // local: this CTA's generators are done with the records
+    uint64_t acc_full;             // both: MMA commit at the end of a chain (multicast)
+    uint64_t acc_empty;            // even CTA: epilogue warps of both CTAs
+    uint64_t drain;                // even CTA: every MMA complete
+    uint32_t tmem_slot;
+    int abort_flag;
+};
+constexpr int P_SMEM = P_STAGES * (P_STAGE_BYTES + C_REC_BYTES) + 1024 + (int)sizeof(PairBars);
+static_assert(P_SMEM <= 232448, "pair kernel shared memory");
+
+// TF32 rows for the pair kernel: segment g (g < nseg) holds 128 consecutive modes
+// from mb[g] as operand rows 128 g + r + 8 j' (j' < 16), generated as 16-step chains
+// of the signed three-term recurrence (as gen_coeff_tf32, one chain per segment).
+__device__ __forceinline__ void gen_pair_tf32(unsigned char *op, const AxisRec *recs, int nvalid, int mb0,
+                                              int mb1, int nseg, int gg) {
+    const int lane = gg & 31, w = gg >> 5;
+    const int r = lane & 7, pp = (lane >> 3) & 1, k4 = 2 * w + (lane >> 4);
+    const int b0 = 4 * k4 + 2 * pp;
+    unsigned char *base = op + k4 * 128 + r * 16 + pp * 8;
+#pragma unroll 1
+    for (int g = 0; g < nseg; ++g) {
+        const unsigned long long m0 = (unsigned long long)((g ? mb1 : mb0) + r);
+        float z0[2], zm[2], t0[2], tm[2], cz[2], ct[2], v0[2];
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+            const int k = b0 + b;
+            if (k < nvalid) {
+                const AxisRec &R = recs[k];
+                const float2 AZ = gen::phase_sfu(m0, R.s), AT = gen::phase_sfu(m0, R.t);
+                const float2 hZ = R.es8, hT = R.et8;
+                z0[b] = AZ.x;
+                zm[b] = -fmaf(AZ.x, hZ.x, AZ.y * hZ.y);
+                t0[b] = R.c * AT.y;
+                tm[b] = -R.c * fmaf(AT.y, hT.x, -AT.x * hT.y);
+                cz[b] = 2.f * hZ.x;
+                ct[b] = 2.f * hT.x;
+                v0[b] = R.v0;
+            } else {
+                z0[b] = zm[b] = t0[b] = tm[b] = cz[b] = ct[b] = v0[b] = 0.f;
+            }
+        }
+        f2 Z = gen::pk(z0[0], z0[1]), Zp = gen::pk(zm[0], zm[1]);
+        f2 T = gen::pk(t0[0], t0[1]), Tp = gen::pk(tm[0], tm[1]);
+        const f2 CZ = gen::pk(cz[0], cz[1]), NCZ = gen::pk(-cz[0], -cz[1]);
+        const f2 CT = gen::pk(ct[0], ct[1]), NCT = gen::pk(-ct[0], -ct[1]);
+        unsigned char *sb = base + g * 16 * 1024;
+        auto put = [&](int j) {
+            float a, b;
+            gen::upk(gen::mul2(Z, T), a, b);
+            *reinterpret_cast<float2 *>(sb + j * 1024) = make_float2(to_tf32_mma(a), to_tf32_mma(b));
+        };
+#pragma unroll 4
+        for (int j = 0; j < 16; j += 2) {
+            put(j);
+            f2 nz = gen::fma2(CZ, Z, Zp), nt = gen::fma2(CT, T, Tp);
+            Zp = Z;
+            Z = nz;
+            Tp = T;
+            T = nt;
+            put(j + 1);
+            nz = gen::fma2(NCZ, Z, Zp);
+            nt = gen::fma2(NCT, T, Tp);
+            Zp = Z;
+            Z = nz;
+            Tp = T;
+            T = nt;
+        }
+        if (m0 == 0) *reinterpret_cast<float2 *>(sb) = make_float2(to_tf32_mma(v0[0]), to_tf32_mma(v0[1]));
+    }
+}
+
+// TF32 A rows for the pair kernel with the modes interleaved between the two CTAs:
+// row R of CTA rank rk holds mode mb + rk + 2 R (R < 256), so that each CTA's 256
+// rows are one progression of step 2 and one chain per thread covers them: thread
+// (block pair, residue r) generates rows r + 8 j (modes m0 + 16 j, m0 = mb + rk + 2 r)
+// for j < 32 by the signed three-term recurrence with step 16 pi s, one anchor.
+__device__ __forceinline__ void gen_pair_tf32_interleaved(unsigned char *op, const AxisRec *recs, int nvalid,
+                                                          int m_first, int gg) {
+    const int lane = gg & 31, w = gg >> 5;
+    const int r = lane & 7, pp = (lane >> 3) & 1, k4 = 2 * w + (lane >> 4);
+    const int b0 = 4 * k4 + 2 * pp;
+    const unsigned long long m0 = (unsigned long long)(m_first + 2 * r);
+    float z0[2], zm[2], t0[2], tm[2], cz[2], ct[2], v0[2];
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+        const int k = b0 + b;
+        if (k < nvalid) {
+            const AxisRec &R = recs[k];
+            const float2 AZ = gen::phase_sfu(m0, R.s), AT = gen::phase_sfu(m0, R.t);
+            const float2 hZ = rot(R.es8, R.es8), hT = rot(R.et8, R.et8);     // 16-mode steps
+            z0[b] = AZ.x;
+            zm[b] = -fmaf(AZ.x, hZ.x, AZ.y * hZ.y);                // -cos(pi (m0 - 16) s)
+            t0[b] = R.c * AT.y;
+            tm[b] = -R.c * fmaf(AT.y, hT.x, -AT.x * hT.y);         // -c sin(pi (m0 - 16) t)
+            cz[b] = 2.f * hZ.x;
+            ct[b] = 2.f * hT.x;
+            v0[b] = R.v0;
+        } else {
+            z0[b] = zm[b] = t0[b] = tm[b] = cz[b] = ct[b] = v0[b] = 0.f;
+        }
+    }
+    f2 Z = gen::pk(z0[0], z0[1]), Zp = gen::pk(zm[0], zm[1]);
+    f2 T = gen::pk(t0[0], t0[1]), Tp = gen::pk(tm[0], tm[1]);
+    const f2 CZ = gen::pk(cz[0], cz[1]), NCZ = gen::pk(-cz[0], -cz[1]);
+    const f2 CT = gen::pk(ct[0], ct[1]), NCT = gen::pk(-ct[0], -ct[1]);
+    unsigned char *base = op + k4 * 128 + r * 16 + pp * 8;
+    auto put = [&](int j) {
+        float a, b;
+        gen::upk(gen::mul2(Z, T), a, b);
+        *reinterpret_cast<float2 *>(base + j * 1024) = make_float2(to_tf32_mma(a), to_tf32_mma(b));
+    };
+#pragma unroll 4
+    for (int j = 0; j < 32; j += 2) {
+        put(j);
+        f2 nz = gen::fma2(CZ, Z, Zp), nt = gen::fma2(CT, T, Tp);
+        Zp = Z;
+        Z = nz;
+        Tp = T;
+        T = nt;
+        put(j + 1);
+        nz = gen::fma2(NCZ, Z, Zp);
+        nt = gen::fma2(NCT, T, Tp);
+        Zp = Z;
+        Z = nz;
+        Tp = T;
+        T = nt;
+    }
+    if (m0 == 0) *reinterpret_cast<float2 *>(base) = make_float2(to_tf32_mma(v0[0]), to_tf32_mma(v0[1]));
+}
+
+// BF16 rows for the pair kernel (MN-major, bf16 hi and lo): segment 0 = 128 modes from
+// mb0 as mode groups 0..15, segment 1 (nseg == 2) = 128 modes from mb0 + 256 as groups
+// 16..31.  Element (mode group q, block k) at q * 128 + (k / 8) * lbo + (k % 8) * 16.
+__device__ __forceinline__ void gen_pair_bf16(unsigned char *op_hi, unsigned char *op_lo, const AxisRec *recs,
+                                              int nvalid, int mb0, int nseg, int lbo, int g) {
+    const int lane = g & 31, wq = (g >> 5) & 3;
+    const int k = (lane & 7) + 8 * wq;
+    const int lg = lane >> 3;
+    float2 za = make_float2(0.f, 0.f), ta = za, es = make_float2(1.f, 0.f), et = es, es8 = es, et8 = es;
+    float v0 = 0.f;
+    if (k < nvalid) {
+        const AxisRec &R = recs[k];
+        const unsigned long long m0 = (unsigned long long)(mb0 + 8 * lg);
+        za = gen::phase_poly(m0, R.s);
+        ta = gen::phase_poly(m0, R.t);
+        ta.x *= R.c;
+        ta.y *= R.c;
+        es = R.es;
+        et = R.et;
+        es8 = R.es8;
+        et8 = R.et8;
+        v0 = R.v0;
+    }
+    c2 GS = gen::make_c2(za, rot(za, es)), GT = gen::make_c2(ta, rot(ta, et));
+    const float2 es2 = rot(es, es), et2 = rot(et, et);
+    const float2 s16 = rot(es8, es8), t16 = rot(et8, et8);
+    const gen::rot2_step S32 = gen::make_step(rot(s16, s16), rot(s16, s16));
+    const gen::rot2_step T32 = gen::make_step(rot(t16, t16), rot(t16, t16));
+    const size_t koff = (size_t)(k >> 3) * lbo + (k & 7) * 16;
+    // segment 1 starts 256 modes after segment 0: e^{i pi 256 s} by squarings of e^{i pi 16 s}
+    const float2 s64 = rot(rot(s16, s16), rot(s16, s16)), t64 = rot(rot(t16, t16), rot(t16, t16));
+    const float2 s256 = rot(rot(s64, s64), rot(s64, s64)), t256 = rot(rot(t64, t64), rot(t64, t64));
+    const gen::rot2_step S256 = gen::make_step(s256, s256);
+    const gen::rot2_step T256 = gen::make_step(t256, t256);
+    c2 HS = gen::rot2(GS, S256), HT = gen::rot2(GT, T256);
+    const f2 KZ = gen::pk(2.f * es2.x, 2.f * es2.x), NKZ = gen::pk(-2.f * es2.x, -2.f * es2.x);
+    const f2 KT = gen::pk(2.f * et2.x, 2.f * et2.x), NKT = gen::pk(-2.f * et2.x, -2.f * et2.x);
+    const f2 E2X = gen::pk(es2.x, es2.x), E2Y = gen::pk(es2.y, es2.y);
+    const f2 F2X = gen::pk(et2.x, et2.x), NF2Y = gen::pk(-et2.y, -et2.y);
+    auto start = [&](const c2 &z, const c2 &t, f2 &Z, f2 &Zp, f2 &T, f2 &Tp) {
+        Z = z.re;
+        T = t.im;
+        const f2 zr = gen::fma2(z.re, E2X, gen::mul2(z.im, E2Y));
+        const f2 ti = gen::fma2(t.im, F2X, gen::mul2(t.re, NF2Y));
+        Zp = gen::pk(-zr.v.x, -zr.v.y);
+        Tp = gen::pk(-ti.v.x, -ti.v.y);
+    };
+#pragma unroll 1
+    for (int q = 0; q < 4; ++q) {
+        const int grp0 = lg + 4 * q, grp1 = grp0 + 16;
+        f2 Z0, Zp0, T0, Tp0, Z1, Zp1, T1, Tp1;
+        start(GS, GT, Z0, Zp0, T0, Tp0);
+        start(HS, HT, Z1, Zp1, T1, Tp1);
+        uint32_t hi0[4], lo0[4], hi1[4], lo1[4];
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj) {
+            float a, b, c, d;
+            gen::upk(gen::mul2(Z0, T0), a, b);
+            gen::upk(gen::mul2(Z1, T1), c, d);
+            if (jj == 0 && mb0 + 8 * grp0 == 0) a = v0;
+            split2(a, b, hi0[jj], lo0[jj]);
+            split2(c, d, hi1[jj], lo1[jj]);
+            const f2 kz = (jj & 1) ? NKZ : KZ, kt = (jj & 1) ? NKT : KT;
+            const f2 nz0 = gen::fma2(kz, Z0, Zp0), nt0 = gen::fma2(kt, T0, Tp0);
+            const f2 nz1 = gen::fma2(kz, Z1, Zp1), nt1 = gen::fma2(kt, T1, Tp1);
+            Zp0 = Z0;
+            Z0 = nz0;
+            Tp0 = T0;
+            T0 = nt0;
+            Zp1 = Z1;
+            Z1 = nz1;
+            Tp1 = T1;
+            T1 = nt1;
+        }
+        const size_t off0 = (size_t)grp0 * 128 + koff, off1 = (size_t)grp1 * 128 + koff;
+        *reinterpret_cast<uint4 *>(op_hi + off0) = make_uint4(hi0[0], hi0[1], hi0[2], hi0[3]);
+        *reinterpret_cast<uint4 *>(op_lo + off0) = make_uint4(lo0[0], lo0[1], lo0[2], lo0[3]);
+        if (nseg > 1) {
+            *reinterpret_cast<uint4 *>(op_hi + off1) = make_uint4(hi1[0], hi1[1], hi1[2], hi1[3]);
+            *reinterpret_cast<uint4 *>(op_lo + off1) = make_uint4(lo1[0], lo1[1], lo1[2], lo1[3]);
+        }
+        GS = gen::rot2(GS, S32);
+        GT = gen::rot2(GT, T32);
+        HS = gen::rot2(HS, S32);
+        HT = gen::rot2(HT, T32);
+    }
+}
+
+struct PairArgs {
+    const AxisRec *xr, *yr;
+    int n, tiles_v, slices, slice_len, units;
+    int Mxc, Myc;         // padded extents of the partial tiles (multiples of 512, 256)
+    float *part;          // [slices][Mxc][Myc]
+    unsigned *status;
+};
+
+template <int PREC>
+__global__ void __launch_bounds__(C_THREADS, 1) tc_coeff_pair_kernel(const PairArgs args) {
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char *smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+    unsigned char *recs_base = smem + P_STAGES * P_STAGE_BYTES;
+    PairBars &bars = *reinterpret_cast<PairBars *>(recs_base + P_STAGES * C_REC_BYTES);
+    volatile int *abort_flag = &bars.abort_flag;
+    const uint32_t rank = cluster_ctarank();           // 0: issues the MMAs
+    const int pair = blockIdx.x >> 1, npairs = gridDim.x >> 1;
+    constexpr int GEN_WARPS_PER_GROUP = C_GEN_WARPS / C_GEN_GROUPS;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < P_STAGES; ++s) {
+            mbar_init(&bars.full[s], 2 * GEN_WARPS_PER_GROUP);      // one group of each CTA per stage
+            mbar_init(&bars.empty[s], 1);
+            mbar_init(&bars.recs_full[s], 1);
+            mbar_init(&bars.gen_done[s], GEN_WARPS_PER_GROUP);
+        }
+        mbar_init(&bars.acc_full, 1);
+        mbar_init(&bars.acc_empty, 2 * C_EPI_WARPS);
+        mbar_init(&bars.drain, 1);
+        bars.abort_flag = 0;
+        mbar_fence_init();
+    }
+    // both CTAs' barriers exist before any arrival from the peer
+    cluster_sync();
+    pdl_wait();                        // the block records come from the preparation kernel
+    if (warp == 0) {
+        tmem_alloc_pair(&bars.tmem_slot, 512);
+        tmem_relinquish_pair();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    pdl_trigger();
+    const uint32_t tmem = bars.tmem_slot;
+    // cluster addresses of the even CTA's barriers that both CTAs arrive on
+    const uint32_t acc_empty0 = mapa_shared(smem_u32(&bars.acc_empty), 0);
+    const int tiles_v = args.tiles_v;
+
+    if (warp == 0) {
+        // ---------------- MMA issuer (even CTA) ----------------
+        if (rank == 0 && lane == 0) {
+            constexpr bool BF = PREC == 2;
+            const uint32_t idesc = instr_desc(BF ? kFmtBF16 : kFmtTF32, 256, 256, BF, BF);
+            uint32_t it = 0, dc = 0;
+            for (int unit = pair; unit < args.units && !*abort_flag; unit += npairs) {
+                const int slice = unit % args.slices;
+                const int b0 = slice * args.slice_len;
+                const int b1 = min(args.n, b0 + args.slice_len);
+                const int nst = (b1 - b0 + C_KB - 1) / C_KB;
+                const int cst = chain_stages<PREC>(nst);
+                for (int st = 0; st < nst; ++st, ++it) {
+                    const int s = it % P_STAGES;
+                    const int sc = st % cst;
+                    if (sc == 0) {
+                        if (dc > 0) {
+                            bool ok = mbar_try_wait_cluster(&bars.acc_empty, (dc - 1) & 1);
+                            const uint64_t t0 = ok ? 0 : globaltimer_ns();
+                            for (uint32_t i = 1; !ok && !*abort_flag; ++i) {
+                                ok = mbar_try_wait_cluster(&bars.acc_empty, (dc - 1) & 1);
+                                if (!ok && (i & 63) == 0 && globaltimer_ns() - t0 > kWaitLimit) break;
+                            }
+                            if (!ok) {
+                                raise_timeout(args.status, abort_flag);
+                                break;
+                            }
+                        }
+                        tc_fence_after();
+                    }
+                    {
+                        bool ok = mbar_try_wait_cluster(&bars.full[s], (it / P_STAGES) & 1);
+                        const uint64_t t0 = ok ? 0 : globaltimer_ns();
+                        for (uint32_t i = 1; !ok && !*abort_flag; ++i) {
+                            ok = mbar_try_wait_cluster(&bars.full[s], (it / P_STAGES) & 1);
+                            if (!ok && (i & 63) == 0 && globaltimer_ns() - t0 > kWaitLimit) break;
+                        }
+                        if (!ok) {
+                            raise_timeout(args.status, abort_flag);
+                            break;
+                        }
+                    }
+                    tc_fence_after();
+                    const uint32_t sb = smem_u32(smem + s * P_STAGE_BYTES);
+                    if (!BF) {
+                        // A: 256 rows x 32 blocks (LBO 128, SBO 1024); B: 128 rows, same layout
+                        const uint32_t A = sb, B = sb + P_A_BYTES;
+#pragma unroll
+                        for (int kk = 0; kk < 4; ++kk) {
+                            const uint64_t bd = smem_desc(B + kk * 256, 128, 1024);
+#pragma unroll
+                            for (int acc = 0; acc < 2; ++acc) {
+                                const uint64_t ad = smem_desc(A + acc * 16384 + kk * 256, 128, 1024);
+                                mma_tf32_pair(tmem + acc * 256, ad, bd, idesc, sc > 0 || kk > 0);
+                            }
+                        }
+                    } else {
+                        // MN-major bf16: A (256 modes) block groups 4096 B apart, B (128 modes) 2048
+                        const uint32_t Ah = sb, Al = sb + 16384, Bh = sb + P_A_BYTES, Bl = Bh + 8192;
+#pragma unroll
+                        for (int kk = 0; kk < 2; ++kk) {
+                            const uint64_t bh = smem_desc(Bh + kk * 4096, 2048, 128);
+                            const uint64_t bl = smem_desc(Bl + kk * 4096, 2048, 128);
+#pragma unroll
+                            for (int acc = 0; acc < 2; ++acc) {
+                                const uint32_t ao = acc * 2048 + kk * 8192;
+                                const uint64_t ah = smem_desc(Ah + ao, 4096, 128);
+                                const uint64_t al = smem_desc(Al + ao, 4096, 128);
+                                const bool accum = sc > 0 || kk > 0;
+                                mma_bf16_pair(tmem + acc * 256, al, bh, idesc, accum);
+                                mma_bf16_pair(tmem + acc * 256, ah, bl, idesc, true);
+                                mma_bf16_pair(tmem + acc * 256, ah, bh, idesc, true);
+                            }
+                        }
+                    }
+                    mma_commit_pair(&bars.empty[s], 0x3);
+                    if (sc == cst - 1 || st == nst - 1) {
+                        mma_commit_pair(&bars.acc_full, 0x3);
+                        ++dc;
+                    }
+                }
+            }
+            mma_commit_pair(&bars.drain, 0x1);
+            if (!mbar_wait(&bars.drain, 0, kWaitLimit, nullptr)) raise_timeout(args.status, abort_flag);
+        }
+        __syncwarp();
+    } else if (warp <= C_EPI_WARPS) {
+        // ---------------- epilogue: this CTA's 128 rows of each accumulator ----------------
+        const int quarter = warp & 3, acc = (warp - 1) >> 2;
+        const int rsub = lane >> 2, csub = 2 * (lane & 3);
+        uint32_t dc = 0;
+        for (int unit = pair; unit < args.units; unit += npairs) {
+            if (*abort_flag) break;
+            const int tile = unit / args.slices, slice = unit % args.slices;
+            const int tu = tile / tiles_v, tv = tile % tiles_v;
+            const int b0 = slice * args.slice_len;
+            const int nst = (min(args.n, b0 + args.slice_len) - b0 + C_KB - 1) / C_KB;
+            const int nch = (nst + chain_stages<PREC>(nst) - 1) / chain_stages<PREC>(nst);
+#pragma unroll 1
+            for (int ch = 0; ch < nch; ++ch, ++dc) {
+                if (!mbar_wait(&bars.acc_full, dc & 1, kWaitLimit, abort_flag)) {
+                    raise_timeout(args.status, abort_flag);
+                    break;
+                }
+                tc_fence_after();
+#pragma unroll 1
+                for (int half = 0; half < 2; ++half) {
+                    const int r0 = quarter * 32 + half * 16;
+                    // TMEM lane i of accumulator acc: mode tile_u0 + 256 acc + 2 i + rank (TF32,
+                    // interleaved rows) or tile_u0 + 256 acc + 128 rank + i (BF16x3)
+                    const int i0 = r0 + rsub;
+                    const int u = PREC == 1 ? tu * P_TILE_U + acc * 256 + 2 * i0 + (int)rank
+                                            : tu * P_TILE_U + acc * 256 + (int)rank * 128 + i0;
+                    float *dst0 = args.part + ((size_t)slice * args.Mxc + u) * args.Myc + tv * P_TILE_V + csub;
+                    float *dst1 = dst0 + (size_t)(PREC == 1 ? 16 : 8) * args.Myc;      // lane i0 + 8
+#pragma unroll 1
+                    for (int c = 0; c < 256; c += 64) {
+                        float v[32];
+                        tmem_ld_16x256b_x8(tmem + ((uint32_t)r0 << 16) + acc * 256 + c, v);
+                        tmem_ld_wait_regs32(v);
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) {
+                            float *p0 = dst0 + c + 8 * j, *p1 = dst1 + c + 8 * j;
+                            if (ch == 0) {
+                                *reinterpret_cast<float2 *>(p0) = make_float2(v[4 * j], v[4 * j + 1]);
+                                *reinterpret_cast<float2 *>(p1) = make_float2(v[4 * j + 2], v[4 * j + 3]);
+                            } else {
+                                red_add2(p0, v[4 * j], v[4 * j + 1]);
+                                red_add2(p1, v[4 * j + 2], v[4 * j + 3]);
+                            }
+                        }
+                    }
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive_cluster(acc_empty0);
+            }
+        }
+    } else if (warp < C_LOADER_WARP) {
+        // ---------------- basis generators ----------------
+        const int g = threadIdx.x - 32 * (1 + C_EPI_WARPS);    // 0..511
+        const int gr = g >> 8;
+        const int which = (g >> 7) & 1;                        // 0: Xt (A), 1: Yt (B)
+        const int gg = g & 127;
+        uint32_t it = 0;
+        for (int unit = pair; unit < args.units; unit += npairs) {
+            const int tile = unit / args.slices, slice = unit % args.slices;
+            const int tu = tile / tiles_v, tv = tile % tiles_v;
+            const int b0 = slice * args.slice_len;
+            const int b1 = min(args.n, b0 + args.slice_len);
+            const int nst = (b1 - b0 + C_KB - 1) / C_KB;
+            for (int st = 0; st < nst; ++st, ++it) {
+                if (*abort_flag) break;
+                if ((int)(it % C_GEN_GROUPS) != gr) continue;
+                const int s = it % P_STAGES;
+                // empty first (the MMAs of this slot's previous use are complete, so both
+                // generator groups are past it), then this use's records
+                if ((it >= P_STAGES &&
+                     !mbar_wait(&bars.empty[s], ((it / P_STAGES) - 1) & 1, kWaitLimit, abort_flag)) ||
+                    !mbar_wait(&bars.recs_full[s], (it / P_STAGES) & 1, kWaitLimit, abort_flag)) {
+                    raise_timeout(args.status, abort_flag);
+                    break;
+                }
+                unsigned char *sb = smem + s * P_STAGE_BYTES;
+                const AxisRec *recs =
+                    reinterpret_cast<const AxisRec *>(recs_base + s * C_REC_BYTES) + which * C_KB;
+                const int nvalid = min(C_KB, b1 - (b0 + st * C_KB));
+                if (which == 0) {
+                    if (PREC == 1) {
+                        gen_pair_tf32_interleaved(sb, recs, nvalid, tu * P_TILE_U + (int)rank, gg);
+                    } else {
+                        const int mb0 = tu * P_TILE_U + (int)rank * 128;
+                        gen_pair_bf16(sb, sb + 16384, recs, nvalid, mb0, 2, 4096, gg);
+                    }
+                } else {
+                    const int mb = tv * P_TILE_V + (int)rank * 128;
+                    if (PREC == 1)
+                        gen_pair_tf32(sb + P_A_BYTES, recs, nvalid, mb, 0, 1, gg);
+                    else
+                        gen_pair_bf16(sb + P_A_BYTES, sb + P_A_BYTES + 8192, recs, nvalid, mb, 1, 2048, gg);
+                }
+                fence_proxy_async_smem();
+                __syncwarp();
+                if (lane == 0) {
+                    mbar_arrive(&bars.gen_done[s]);
+                    mbar_arrive_cluster(mapa_shared(smem_u32(&bars.full[s]), 0));
+                }
+            }
+            if (*abort_flag) break;
+        }
+    } else {
+        // ---------------- record loader (each CTA its own copy of the stage's records) ----------------
+        if (lane == 0) {
+            uint32_t it = 0;
+            for (int unit = pair; unit < args.units; unit += npairs) {
+                const int slice = unit % args.slices;
+                const int b0 = slice * args.slice_len;
+                const int b1 = min(args.n, b0 + args.slice_len);
+                const int nst = (b1 - b0 + C_KB - 1) / C_KB;
+                for (int st = 0; st < nst; ++st, ++it) {
+                    if (*abort_flag) break;
+                    const int s = it % P_STAGES;
+                    if (it >= P_STAGES &&
+                        !mbar_wait(&bars.gen_done[s], ((it / P_STAGES) - 1) & 1, kWaitLimit, abort_flag)) {
+                        raise_timeout(args.status, abort_flag);
+                        break;
+                    }
+                    const int blk0 = b0 + st * C_KB;
+                    const uint32_t bytes = (uint32_t)min(C_KB, b1 - blk0) * (uint32_t)sizeof(AxisRec);
+                    unsigned char *dst = recs_base + s * C_REC_BYTES;
+                    mbar_arrive_expect_tx(&bars.recs_full[s], 2 * bytes);
+                    bulk_load(dst, args.xr + blk0, bytes, &bars.recs_full[s]);
+                    bulk_load(dst + C_KB * sizeof(AxisRec), args.yr + blk0, bytes, &bars.recs_full[s]);
+                }
+                if (*abort_flag) break;
+            }
+        }
+        __syncwarp();
+    }
+    // both CTAs are done with the tensor memory and the even CTA's MMAs (which read
+    // the odd CTA's shared memory) are complete before either CTA frees or exits
+    tc_fence_before();
+    __syncthreads();
+    cluster_sync();
+    if (warp == 0) {
+        tc_fence_after();
+        tmem_dealloc_pair(tmem, 512);
+    }
+}
+
+// ===========================================================================
 // Finish: FP64 sum of the slice partials -> a, K in the energy operand layout
 // ===========================================================================
 // Sum of one double per thread over the CTA, added to *dst (one atomic per CTA).
@@ -1460,13 +1987,16 @@ cudaError_t launch_wait_probe(uint64_t limit_ns, unsigned *status, cudaStream_t 
 
 TcPlan tc_plan(int n, int Mx, int My) {
     TcPlan p{};
-    p.Mxc = round_up(Mx, C_TILE);
+    // SM pairs (512 x 256 tiles) once the u extent fills one; else one CTA per 256 x 256 tile
+    p.pair = round_up(Mx, C_TILE) >= P_TILE_U ? 1 : 0;
+    p.Mxc = round_up(Mx, p.pair ? P_TILE_U : C_TILE);
     p.Myc = round_up(My, C_TILE);
     p.Mxe = round_up(Mx, E_KS);
     p.Mye = round_up(My, E_VC);
-    const int tiles = (p.Mxc / C_TILE) * (p.Myc / C_TILE);
-    // Slice count s: the kernel takes ceil(tiles * s / SMs) unit times of n / s
-    // blocks each, so pick the s that minimises ceil(tiles * s / SMs) / s (the
+    const int tiles = (p.Mxc / (p.pair ? P_TILE_U : C_TILE)) * (p.Myc / C_TILE);
+    const int slots = p.pair ? kPlanSMs / 2 : kPlanSMs;      // units in flight
+    // Slice count s: the kernel takes ceil(tiles * s / slots) unit times of n / s
+    // blocks each, so pick the s that minimises ceil(tiles * s / slots) / s (the
     // smallest such s: fewest partial tiles to sum), with slices of >= 512 blocks.
     int max_slices = (n + 511) / 512;
     if (max_slices > 4 * kPlanSMs) max_slices = 4 * kPlanSMs;
@@ -1474,7 +2004,7 @@ TcPlan tc_plan(int n, int Mx, int My) {
     int slices = 1;
     double best = 1e300;
     for (int sc = 1; sc <= max_slices; ++sc) {
-        const double waves = (double)(((long long)tiles * sc + kPlanSMs - 1) / kPlanSMs);
+        const double waves = (double)(((long long)tiles * sc + slots - 1) / slots);
         const double t = waves / sc;
         if (t < best * (1.0 - 1e-9)) {
             best = t;
@@ -1488,8 +2018,54 @@ TcPlan tc_plan(int n, int Mx, int My) {
     return p;
 }
 
+// Pair kernel launch: clusters of two CTAs (one per SM), as many pairs as can be
+// resident at once (at most one per unit), with programmatic dependent launch.
+template <int PREC>
+cudaError_t launch_coeff_pair(const Launch &L, const TcPlan &P, float *part) {
+    PairArgs a{};
+    a.xr = L.xrec;
+    a.yr = L.yrec;
+    a.n = L.n;
+    a.tiles_v = P.Myc / P_TILE_V;
+    a.slices = P.slices;
+    a.slice_len = P.slice_len;
+    a.units = P.tiles * P.slices;
+    a.Mxc = P.Mxc;
+    a.Myc = P.Myc;
+    a.part = part;
+    a.status = L.status;
+    auto kfn = tc_coeff_pair_kernel<PREC>;
+    cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, P_SMEM);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg{};
+    cudaLaunchAttribute attr[2];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[1].val.programmaticStreamSerializationAllowed = 1;
+    cfg.blockDim = dim3(C_THREADS);
+    cfg.dynamicSmemBytes = P_SMEM;
+    cfg.stream = L.stream;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int pairs = L.sm_count / 2;
+    cfg.gridDim = dim3(2 * pairs);
+    int active = 0;
+    if (cudaOccupancyMaxActiveClusters(&active, kfn, &cfg) == cudaSuccess && active > 0 && active < pairs)
+        pairs = active;
+    cudaGetLastError();
+    if (pairs > a.units) pairs = a.units;
+    if (pairs < 1) pairs = 1;
+    cfg.gridDim = dim3(2 * pairs);
+    cfg.numAttrs = 2;
+    return cudaLaunchKernelEx(&cfg, kfn, a);
+}
+
 cudaError_t launch_coeff_tc(const Launch &L, int prec, const TcPlan &P, float *part) {
     if (L.n == 0) return cudaSuccess;
+    if (P.pair) return prec == 1 ? launch_coeff_pair<1>(L, P, part) : launch_coeff_pair<2>(L, P, part);
     CoeffArgs a{};
     a.xr = L.xrec;
     a.yr = L.yrec;
