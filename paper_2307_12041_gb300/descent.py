@@ -57,6 +57,24 @@ def evaluate_chunked(x, y, w, h, c, W, H, Mx, My, prec="tf32", chunk: Optional[i
     return gx, gy, binding.energy_from_coeffs(a, W, H)
 
 
+def block_energies_chunked(x, y, w, h, c, W, H, Mx, My, prec="tf32", chunk: Optional[int] = None):
+    """Per-block energies N_i of the whole placement, chunked as evaluate_chunked."""
+    n = x.numel()
+    if not chunk or chunk >= n:
+        return binding.energy(x, y, w, h, c, W, H, Mx, My, prec)[0]
+    cuts = list(range(0, n, chunk)) + [n]
+    sl = lambda t, a, b: None if t is None else t[a:b]
+    a64 = torch.zeros((Mx, My), dtype=torch.float64, device=x.device)
+    a = torch.empty((Mx, My), dtype=torch.float32, device=x.device)
+    for k, (s, e) in enumerate(zip(cuts[:-1], cuts[1:])):
+        binding.coeffs_accumulate(x[s:e], y[s:e], w[s:e], h[s:e], sl(c, s, e), W, H, Mx, My, a64, prec,
+                                  a_out=a if k == len(cuts) - 2 else None)
+    eb = torch.empty_like(x)
+    for s, e in zip(cuts[:-1], cuts[1:]):
+        eb[s:e] = binding.energy(x[s:e], y[s:e], w[s:e], h[s:e], sl(c, s, e), W, H, Mx, My, prec, a=a)[0]
+    return eb
+
+
 def descend(p: synth.Placement, steps: int, lr: float = 1e-4, jitter: float = 1e-6,
             seed: int = synth.BASE_SEED, prec: str = "tf32", chunk: Optional[int] = None,
             device="cuda", callback: Optional[Callable] = None) -> DescentResult:
@@ -86,6 +104,40 @@ def descend(p: synth.Placement, steps: int, lr: float = 1e-4, jitter: float = 1e
     return res
 
 
+def ulp_steps(x0: np.ndarray, x1: np.ndarray) -> np.ndarray:
+    """(x1 - x0) in units of half the float32 ulp of x0, as exact int64 integers: a
+    float32 x1 in the binade of x0 or an adjacent one is a multiple of that unit, so
+    x1 = float32(x0 + k * spacing(x0) / 2) recovers it from x0 alone (checked here)."""
+    x0 = np.asarray(x0, np.float32)
+    x1 = np.asarray(x1, np.float32)
+    unit = 0.5 * np.spacing(np.abs(x0)).astype(np.float64)
+    k = (x1.astype(np.float64) - x0.astype(np.float64)) / unit
+    ki = np.rint(k).astype(np.int64)
+    if not np.array_equal(ki.astype(np.float64), k):
+        raise ValueError("positions are not a whole number of units apart")
+    return ki
+
+
+def save_checkpoint(path: str, step: int, p, x, y, gx, gy, eb, E, sample, positions: bool):
+    """A record of step `step` for a later FP64 check: the GPU's gradient and per-block
+    energy on the sample blocks and E; with `positions`, every block's position as
+    ulp steps from its starting position (lzma-compressed int32/int64)."""
+    import lzma
+    import os
+    os.makedirs(os.path.dirname(os.path.abspath(path)), exist_ok=True)
+    idx = torch.from_numpy(sample).to(x.device)
+    rec = {"step": step, "n": p.n, "Mx": p.Mx, "My": p.My, "E": float(E),
+           "sample": sample.astype(np.int64), "gx": gx[idx].cpu().numpy(), "gy": gy[idx].cpu().numpy(),
+           "N": eb[idx].cpu().numpy()}
+    if positions:
+        for name, start, now in (("dx", p.x, x), ("dy", p.y, y)):
+            k = ulp_steps(start, now.cpu().numpy())
+            dt = np.int32 if np.abs(k).max(initial=0) < 2 ** 31 else np.int64
+            rec[name] = lzma.compress(k.astype(dt).tobytes(), preset=6)
+            rec[name + "_dtype"] = np.dtype(dt).str
+    np.savez(path, **{k: (np.frombuffer(v, np.uint8) if isinstance(v, bytes) else v) for k, v in rec.items()})
+
+
 def _main(argv=None) -> int:
     """Run the descent loop on a synthetic workload and print one JSON line:
     time per step, block-mode^2 terms/s, the energy trace, and the same first
@@ -103,6 +155,10 @@ def _main(argv=None) -> int:
     ap.add_argument("--fp32-steps", type=int, default=2, help="FP32-plain evaluations to time")
     ap.add_argument("--check-every", type=int, default=0,
                     help="also evaluate E in FP32 plain at the current positions every K steps")
+    ap.add_argument("--save-dir", default=None,
+                    help="save records for an FP64 check of the first and last steps (the GPU's "
+                         "gradient and N on --sample blocks, E, and the last positions)")
+    ap.add_argument("--sample", type=int, default=10000, help="sample blocks of the saved records")
     a = ap.parse_args(argv)
     p = synth.workload(a.workload, n=a.n)
     dev = torch.device("cuda")
@@ -117,6 +173,24 @@ def _main(argv=None) -> int:
                 Ep = evaluate_chunked(xk, yk, wk, hk, ck, p.W, p.H, p.Mx, p.My, "fp32", a.chunk)[2]
                 checks.append((k, float(Ek.item()), float(Ep.item())))
         descend(p, a.steps, a.lr, a.jitter, prec=a.prec, chunk=a.chunk, callback=cb)
+    saved = []
+    if a.save_dir:
+        # a separate run (saving would perturb the timing): records of the first and last steps
+        import os
+        sample = np.sort(np.random.default_rng(synth.BASE_SEED + 99).choice(p.n, min(a.sample, p.n),
+                                                                           replace=False))
+        last = a.steps - 1
+
+        def cb_save(k, xk, yk, gxk, gyk, Ek):
+            if k not in (0, last):
+                return
+            wk, hk, ck = binding.to_device(p, dev)[2:]
+            ebk = block_energies_chunked(xk, yk, wk, hk, ck, p.W, p.H, p.Mx, p.My, a.prec, a.chunk)
+            path = os.path.join(a.save_dir, f"step{k:03d}.npz")
+            save_checkpoint(path, k, p, xk, yk, gxk, gyk, ebk, Ek.item(), sample, positions=k == last)
+            saved.append(path)
+
+        descend(p, a.steps, a.lr, a.jitter, prec=a.prec, chunk=a.chunk, callback=cb_save)
     res = descend(p, a.steps, a.lr, a.jitter, prec=a.prec, chunk=a.chunk)
     x, y, w, h, c = binding.to_device(p, dev)
     x, y = res.x, res.y                                 # compare at the final positions
@@ -142,7 +216,7 @@ def _main(argv=None) -> int:
         "fp32_plain_ms_per_eval": fp32_ms, "speedup_vs_fp32_plain": fp32_ms / res.ms_per_step,
         "grad_gap_vs_fp32_plain": gap / scale if scale > 0 else gap,
         "E_gap_vs_fp32_plain": abs(float(g_mixed[2]) - float(g_plain[2])) / abs(float(g_plain[2])),
-        "E_checks": checks,
+        "E_checks": checks, "saved": saved,
     }), flush=True)
     return 0
 
