@@ -285,6 +285,16 @@ __device__ __forceinline__ void red_add2(float *p, float a, float b) {
     asm volatile("red.global.add.v2.f32 [%0], {%1, %2};" ::"l"(p), "f"(a), "f"(b) : "memory");
 }
 
+// At teardown: wait (bounded) until the copies this thread issued for the last uses of
+// each stage slot have landed (their completion barrier `done[s]`, completed by the
+// copies' bytes alone), so that the CTA never exits while a copy still writes into
+// its shared memory; `issued` copies were issued, slot it % stages, phase it / stages.
+__device__ __forceinline__ void wait_copies_landed(uint64_t *done, int stages, uint32_t issued) {
+    const uint32_t first = issued > (uint32_t)stages ? issued - (uint32_t)stages : 0u;
+    for (uint32_t k = first; k < issued; ++k)
+        mbar_wait(&done[k % stages], (k / stages) & 1, kWaitLimit, nullptr);
+}
+
 // Most blocks accumulated in one TMEM chain.  Each MMA step may truncate the FP32
 // accumulator by up to one unit in the last place, in a consistent direction:
 // 8192 TF32 blocks are 1024 steps of K = 8, a relative bias below 1.3e-4, small
@@ -531,6 +541,7 @@ __global__ void __launch_bounds__(C_THREADS, 1) tc_coeff_kernel(const CoeffArgs 
                 }
                 if (*abort_flag) break;
             }
+            wait_copies_landed(bars.recs_full, C_STAGES, it);
         }
         __syncwarp();
     }
@@ -1055,6 +1066,7 @@ __global__ void __launch_bounds__(C_THREADS, 1) tc_coeff_pair_kernel(const PairA
                 }
                 if (*abort_flag) break;
             }
+            wait_copies_landed(bars.recs_full, P_STAGES, it);
         }
         __syncwarp();
     }
@@ -1187,7 +1199,8 @@ constexpr int E_DRAIN_THREADS = 32 * E_EPI_WARPS;
 constexpr int E_DRAIN_COLS = E_VC / 2;
 
 struct EnergyBars {
-    uint64_t full[E_STAGES];
+    uint64_t full[E_STAGES];        // generator group of the stage
+    uint64_t kfull[E_STAGES];       // the stage's K tile (TMA bytes)
     uint64_t empty[E_STAGES];
     uint64_t acc_full;
     uint64_t acc_empty;
@@ -1729,8 +1742,8 @@ tc_energy_kernel(const __grid_constant__ CUtensorMap tm_hi, const __grid_constan
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < E_STAGES; ++s) {
-            // one generator group (128 threads) + the TMA producer per stage
-            mbar_init(&bars.full[s], (E_GEN_WARPS / 2) * 32 + 1);
+            mbar_init(&bars.full[s], (E_GEN_WARPS / 2) * 32);     // one generator group (128 threads)
+            mbar_init(&bars.kfull[s], 1);                         // the TMA producer + its bytes
             mbar_init(&bars.empty[s], 1);
         }
         mbar_init(&bars.acc_full, 1);
@@ -1763,7 +1776,8 @@ tc_energy_kernel(const __grid_constant__ CUtensorMap tm_hi, const __grid_constan
                     tc_fence_after();
                     for (int ks = 0; ks < nks; ++ks, ++it) {
                         const int s = it % E_STAGES;
-                        if (!mbar_wait(&bars.full[s], (it / E_STAGES) & 1, kWaitLimit, abort_flag)) {
+                        if (!mbar_wait(&bars.full[s], (it / E_STAGES) & 1, kWaitLimit, abort_flag) ||
+                            !mbar_wait(&bars.kfull[s], (it / E_STAGES) & 1, kWaitLimit, abort_flag)) {
                             raise_timeout(args.status, abort_flag);
                             break;
                         }
@@ -1828,12 +1842,13 @@ tc_energy_kernel(const __grid_constant__ CUtensorMap tm_hi, const __grid_constan
                         unsigned char *sb = smem + s * E_STAGE_BYTES + 32768;
                         // stage start in 1 KB rows: ((vc*(Mxe/T) + ks*(32/T)) * 4 KB) / 1 KB
                         const int row = 4 * (vc * (args.Mxe / T) + ks * (E_KS / T));
-                        mbar_arrive_expect_tx(&bars.full[s], bytes);
-                        tma_load_2d(sb, &tm_hi, 0, row, &bars.full[s]);
-                        if (BF) tma_load_2d(sb + 16384, &tm_lo, 0, row, &bars.full[s]);
+                        mbar_arrive_expect_tx(&bars.kfull[s], bytes);
+                        tma_load_2d(sb, &tm_hi, 0, row, &bars.kfull[s]);
+                        if (BF) tma_load_2d(sb + 16384, &tm_lo, 0, row, &bars.kfull[s]);
                     }
                 }
             }
+            wait_copies_landed(bars.kfull, E_STAGES, (uint32_t)it);
         }
         __syncwarp();
     } else if (warp < 2 + E_EPI_WARPS) {
