@@ -569,9 +569,15 @@ __global__ void __launch_bounds__(C_THREADS, 1) tc_coeff_kernel(const CoeffArgs 
 // TF32 mode tile_u0 + 256 acc + 2 i + rk (the two CTAs' rows interleaved, so that
 // each CTA's 256 A rows are one progression of step 2 that one recurrence chain per
 // generator thread covers), BF16x3 tile_u0 + 256 acc + 128 rk + i; its B columns are
-// v = tile_v0 + 128 rk + [0, 128).  The even CTA's thread 0 of warp 0 issues every MMA; its `full` and
-// `acc_empty` barriers count the warps of both CTAs, which arrive through cluster
-// addresses, and its commits arrive on the barriers of both CTAs (multicast).
+// v = tile_v0 + 128 rk + [0, 128).  The even CTA's thread 0 of warp 0 issues every MMA; its commits
+// arrive on the barriers of both CTAs (multicast).  Its `acc_empty` barrier counts the
+// epilogue warps of both CTAs, which arrive through cluster addresses.  Its `full[s]`
+// counts its own generator warps (local arrivals) and one relay from the odd CTA: there
+// the generator warps arrive on their local `gen_done[s]` and thread 0 of warp 0 (idle
+// otherwise) waits for that phase and passes it on with one cluster-scope release.  With
+// a cluster-scope release by every generator warp, a per-stage trace showed ~0.8 us
+// between a warp's last store of a stage and its next stage's start, on the critical
+// path of the odd CTA's A generators.
 constexpr int P_STAGES = 4;
 constexpr int P_A_BYTES = 32768;                // 256 rows x 32 blocks
 constexpr int P_B_BYTES = 16384;                // 128 rows x 32 blocks
@@ -580,7 +586,7 @@ constexpr int P_TILE_U = 512;
 constexpr int P_TILE_V = 256;
 
 struct PairBars {
-    uint64_t full[P_STAGES];       // even CTA: generator warps of both CTAs
+    uint64_t full[P_STAGES];       // even CTA: its generator warps + the odd CTA's relay
     uint64_t empty[P_STAGES];      // both: MMA commit (multicast)
     uint64_t recs_full[P_STAGES];  // local: record copies
     uint64_t gen_done[P_STAGES];   // local: this CTA's generators are done with the records
@@ -823,7 +829,7 @@ __global__ void __launch_bounds__(C_THREADS, 1) tc_coeff_pair_kernel(const PairA
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
         for (int s = 0; s < P_STAGES; ++s) {
-            mbar_init(&bars.full[s], 2 * GEN_WARPS_PER_GROUP);      // one group of each CTA per stage
+            mbar_init(&bars.full[s], GEN_WARPS_PER_GROUP + 1);      // even CTA's group + relay
             mbar_init(&bars.empty[s], 1);
             mbar_init(&bars.recs_full[s], 1);
             mbar_init(&bars.gen_done[s], GEN_WARPS_PER_GROUP);
@@ -934,6 +940,23 @@ __global__ void __launch_bounds__(C_THREADS, 1) tc_coeff_pair_kernel(const PairA
             }
             mma_commit_pair(&bars.drain, 0x1);
             if (!mbar_wait(&bars.drain, 0, kWaitLimit, nullptr)) raise_timeout(args.status, abort_flag);
+        } else if (rank == 1 && lane == 0) {
+            // ---------------- relay (odd CTA): gen_done[s] complete -> even CTA's full[s] ----------------
+            uint32_t it = 0;
+            for (int unit = pair; unit < args.units && !*abort_flag; unit += npairs) {
+                const int slice = unit % args.slices;
+                const int b0 = slice * args.slice_len;
+                const int nst = (min(args.n, b0 + args.slice_len) - b0 + C_KB - 1) / C_KB;
+                for (int st = 0; st < nst; ++st, ++it) {
+                    const int s = it % P_STAGES;
+                    // phase it / P_STAGES of gen_done[s]: the next one needs this relay first
+                    if (!mbar_wait(&bars.gen_done[s], (it / P_STAGES) & 1, kWaitLimit, abort_flag)) {
+                        raise_timeout(args.status, abort_flag);
+                        break;
+                    }
+                    mbar_arrive_cluster(mapa_shared(smem_u32(&bars.full[s]), 0));
+                }
+            }
         }
         __syncwarp();
     } else if (warp <= C_EPI_WARPS) {
@@ -1034,8 +1057,8 @@ __global__ void __launch_bounds__(C_THREADS, 1) tc_coeff_pair_kernel(const PairA
                 fence_proxy_async_smem();
                 __syncwarp();
                 if (lane == 0) {
-                    mbar_arrive(&bars.gen_done[s]);
-                    mbar_arrive_cluster(mapa_shared(smem_u32(&bars.full[s]), 0));
+                    mbar_arrive(&bars.gen_done[s]);          // odd CTA: relayed by warp 0
+                    if (rank == 0) mbar_arrive(&bars.full[s]);
                 }
             }
             if (*abort_flag) break;
