@@ -109,6 +109,26 @@ pp_status pp_grad(const pp_problem *prob, pp_precision prec, pp_sample sample,
                   const float *a, float *gx, float *gy, float *e_block, double *e_total,
                   void *ws, size_t ws_bytes, void *stream);
 
+/* pp_grad (a = NULL) for a placement held in HOST memory, results written to
+ * HOST memory: the evaluation of Sec. III-C (Eq. aup, ksi) as pp_grad computes it,
+ * with the transfers inside the call.
+ *  - prob->x, y, w, h, c (c may be NULL) and gx, gy (required when n > 0),
+ *    e_block (n float32, may be NULL), e_total (one double, may be NULL) are host
+ *    pointers; device pointers of the current device are accepted as well.
+ *  - Pinned (page-locked) host memory is read and written in place by the
+ *    kernels, through its device mapping (each input read once, each output
+ *    written once); pageable memory is copied through the workspace with
+ *    cudaMemcpyAsync.  E is copied out at the end.  The caller owns every buffer
+ *    and keeps it valid until `stream` has passed the call.
+ *  - Workspace: pp_grad_host_workspace_size(prob, prec) bytes (pp_workspace_size,
+ *    then 256 B for E and 8 staging arrays of n float32).
+ *  - Errors as pp_grad (PP_EINVAL, PP_ENOMEM_WS, PP_ENOTSUP, PP_ECUDA); the
+ *    outputs are defined only after synchronizing `stream`. */
+size_t pp_grad_host_workspace_size(const pp_problem *prob, pp_precision prec);
+pp_status pp_grad_host(const pp_problem *prob, pp_precision prec, pp_sample sample,
+                       float *gx, float *gy, float *e_block, double *e_total,
+                       void *ws, size_t ws_bytes, void *stream);
+
 /* Adjoint of the energies for an upstream gradient (the backward pass of
  *   L = g_total * E + sum_i g_block_i N_i,   E = 1/2 sum_i N_i   (Sec. II-B)
  * with respect to the block centres).  N_i = sum_uv X_iu a_uv Y_iv depends on x_j

@@ -64,7 +64,8 @@ EXPORTS = ("pp_workspace_size", "pp_coeffs", "pp_energy", "pp_grad", "pp_sync_st
            "pp_energy_from_coeffs", "pp_descent_step",
            "pp_wirelength_workspace_size", "pp_wirelength", "pp_place_combine", "pp_step_norms",
            "pp_nesterov_step", "pp_overflow", "pp_place_workspace_size", "pp_place_iteration",
-           "pp_check_wait_timeout", "pp_grad_adjoint", "pp_coeffs_accumulate")
+           "pp_check_wait_timeout", "pp_grad_adjoint", "pp_coeffs_accumulate",
+           "pp_grad_host_workspace_size", "pp_grad_host")
 
 
 def lib_path() -> str:
@@ -133,6 +134,10 @@ def lib() -> ctypes.CDLL:
         L.pp_grad_adjoint.restype = i
         L.pp_coeffs_accumulate.argtypes = [P, i, vp, vp, vp, sz, vp]
         L.pp_coeffs_accumulate.restype = i
+        L.pp_grad_host_workspace_size.argtypes = [P, i]
+        L.pp_grad_host_workspace_size.restype = sz
+        L.pp_grad_host.argtypes = [P, i, i, vp, vp, vp, vp, vp, sz, vp]
+        L.pp_grad_host.restype = i
         L.pp_grad_noalloc.argtypes = [P, i, vp, vp, vp, vp, vp]
         L.pp_grad_noalloc.restype = i
         L.pp_timing_enable.argtypes = [i]
@@ -254,6 +259,46 @@ def grad(x, y, w, h, c, W, H, Mx, My, prec="fp32", sample="rect", a=None, want_e
                          _ptr(gx) if n else None, _ptr(gy) if n else None,
                          _ptr(eb) if (eb is not None and n) else None, _ptr(et),
                          ws.data_ptr(), ws.numel(), _stream_handle(dev)))
+    return gx, gy, eb, et
+
+
+_WS_HOST = {}
+
+
+def grad_host(x, y, w, h, c, W, H, Mx, My, prec="fp32", sample="rect", out=None, device=None):
+    """pp_grad_host: the evaluation of `grad` for a placement in host memory, the
+    results written to host memory.  x, y, w, h, c (c may be None): contiguous
+    float32 CPU tensors of n; out: (gx, gy, N_i, E) CPU tensors (float32 n x3,
+    float64 1), allocated pinned when None.  Pinned tensors are read and written in
+    place by the kernels; pageable ones are staged.  Asynchronous on the current
+    stream of `device` (default: the current CUDA device): synchronize it before
+    reading the outputs."""
+    n = x.numel()
+    for name, t in (("x", x), ("y", y), ("w", w), ("h", h), ("c", c)):
+        if t is None:
+            continue
+        if t.dtype != torch.float32 or not t.is_contiguous() or t.numel() != n or t.device.type != "cpu":
+            raise ValueError(f"{name} must be a contiguous float32 CPU tensor of {n} elements")
+    dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+    prob = Problem(float(W), float(H), n, _ptr(x) if n else None, _ptr(y) if n else None,
+                   _ptr(w) if n else None, _ptr(h) if n else None,
+                   _ptr(c) if (c is not None and n) else None, int(Mx), int(My))
+    if out is None:
+        out = (torch.empty(n, dtype=torch.float32).pin_memory(), torch.empty(n, dtype=torch.float32).pin_memory(),
+               torch.empty(n, dtype=torch.float32).pin_memory(), torch.empty(1, dtype=torch.float64).pin_memory())
+    gx, gy, eb, et = out
+    need = lib().pp_grad_host_workspace_size(ctypes.byref(prob), PRECISIONS[prec])
+    if need == 0:
+        _check(1)
+    key = (dev.index, torch.cuda.current_stream(dev).cuda_stream)
+    ws = _WS_HOST.get(key)
+    if ws is None or ws.numel() < need:
+        ws = torch.empty(need, dtype=torch.uint8, device=dev)
+        _WS_HOST[key] = ws
+    _check(lib().pp_grad_host(ctypes.byref(prob), PRECISIONS[prec], SAMPLES[sample],
+                              _ptr(gx) if n else None, _ptr(gy) if n else None,
+                              _ptr(eb) if (eb is not None and n) else None, _ptr(et),
+                              ws.data_ptr(), ws.numel(), _stream_handle(dev)))
     return gx, gy, eb, et
 
 

@@ -4,6 +4,8 @@
 //   pp_coeffs : prep -> coefficient contraction -> finish(a)
 //   pp_energy : prep -> [coefficients -> finish(K)] or finish(K from a) -> energy
 //   pp_grad   : same as pp_energy, the energy kernel also writing dE/dx, dE/dy
+//   pp_grad_host : pp_grad on host buffers (pinned: read and written in place by the
+//                  kernels; pageable: staged through the workspace)
 #include <atomic>
 #include <cmath>
 #include <cstdarg>
@@ -168,8 +170,10 @@ struct Ctx {
     char *base;
 };
 
+// host_io: the block arrays were already resolved by pp_grad_host to pointers the
+// kernels can use (device memory, or pinned host memory mapped for the device).
 pp_status setup(const pp_problem *p, pp_precision prec, void *ws, size_t ws_bytes, void *stream,
-                Ctx *ctx) {
+                Ctx *ctx, bool host_io = false) {
     pp_status st = check_problem(p, prec);
     if (st != PP_OK) return st;
     int sm = 0;
@@ -192,7 +196,7 @@ pp_status setup(const pp_problem *p, pp_precision prec, void *ws, size_t ws_byte
         for (int i = 0; i < 5; ++i) {
             if (!ptrs[i]) continue;
             if (((uintptr_t)ptrs[i] & 3) != 0) return fail(PP_EINVAL, "%s is not 4-byte aligned", names[i]);
-            if ((st = check_dev_ptr(ptrs[i], ctx->dev, names[i])) != PP_OK) return st;
+            if (!host_io && (st = check_dev_ptr(ptrs[i], ctx->dev, names[i])) != PP_OK) return st;
         }
     }
     Launch &L = ctx->L;
@@ -222,11 +226,44 @@ pp_status setup(const pp_problem *p, pp_precision prec, void *ws, size_t ws_byte
     return PP_OK;
 }
 
-pp_status out_ptr(const void *ptr, int dev, const char *name, bool required) {
+pp_status out_ptr(const void *ptr, int dev, const char *name, bool required, bool host_io = false) {
     if (!ptr) return required ? fail(PP_EINVAL, "%s must be non-NULL", name) : PP_OK;
     if (((uintptr_t)ptr & 3) != 0) return fail(PP_EINVAL, "%s is not 4-byte aligned", name);
-    return check_dev_ptr(ptr, dev, name);
+    return host_io ? PP_OK : check_dev_ptr(ptr, dev, name);
 }
+
+// Where pp_grad_host's kernels find one caller array: device memory of this device or
+// pinned host memory (its device mapping) in place; pageable host memory is staged.
+struct HostArg {
+    void *dev;       // what the kernels read or write
+    bool staged;     // pageable: copied through the workspace
+};
+pp_status resolve_host_arg(const void *ptr, int dev, const char *name, void *staging, HostArg *out) {
+    out->dev = nullptr;
+    out->staged = false;
+    if (!ptr) return PP_OK;
+    if (((uintptr_t)ptr & 3) != 0) return fail(PP_EINVAL, "%s is not 4-byte aligned", name);
+    cudaPointerAttributes at;
+    cudaError_t e = cudaPointerGetAttributes(&at, ptr);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        at.type = cudaMemoryTypeUnregistered;
+    }
+    if (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) {
+        if (at.device != dev)
+            return fail(PP_EINVAL, "%s: lives on device %d, current device is %d", name, at.device, dev);
+        out->dev = const_cast<void *>(ptr);
+    } else if (at.type == cudaMemoryTypeHost && at.devicePointer) {
+        out->dev = at.devicePointer;
+    } else {
+        out->dev = staging;
+        out->staged = true;
+    }
+    return PP_OK;
+}
+
+// pp_grad_host's workspace: [pp_workspace_size bytes][E, 256 B][staging: x y w h c gx gy N, 4n B each]
+size_t host_extra_bytes(int64_t n) { return 256 + 8 * align256((size_t)n * sizeof(float)); }
 
 #define PP_TRY(expr, what)                                  \
     do {                                                    \
@@ -348,19 +385,19 @@ pp_status accumulate_coefficients(Ctx &c, double *a64, float *a_out) {
 
 pp_status energy_common(const pp_problem *p, pp_precision prec, pp_sample sample, const float *a,
                         float *gx, float *gy, float *e_block, double *e_total, void *ws,
-                        size_t ws_bytes, void *stream, bool want_grad) {
+                        size_t ws_bytes, void *stream, bool want_grad, bool host_io = false) {
     Ctx c;
-    pp_status st = setup(p, prec, ws, ws_bytes, stream, &c);
+    pp_status st = setup(p, prec, ws, ws_bytes, stream, &c, host_io);
     if (st != PP_OK) return st;
     if (sample != PP_RECT && sample != PP_CENTER) return fail(PP_EINVAL, "unknown sample mode %d", (int)sample);
     const bool has_blocks = p->n > 0;   // per-block arrays may be NULL when n = 0
     if (want_grad) {
-        if ((st = out_ptr(gx, c.dev, "gx", has_blocks)) != PP_OK) return st;
-        if ((st = out_ptr(gy, c.dev, "gy", has_blocks)) != PP_OK) return st;
+        if ((st = out_ptr(gx, c.dev, "gx", has_blocks, host_io)) != PP_OK) return st;
+        if ((st = out_ptr(gy, c.dev, "gy", has_blocks, host_io)) != PP_OK) return st;
     } else if (!e_block && !e_total && has_blocks) {
         return fail(PP_EINVAL, "e_block and e_total are both NULL");
     }
-    if ((st = out_ptr(e_block, c.dev, "e_block", false)) != PP_OK) return st;
+    if ((st = out_ptr(e_block, c.dev, "e_block", false, host_io)) != PP_OK) return st;
     if (e_total) {
         if (((uintptr_t)e_total & 7) != 0) return fail(PP_EINVAL, "e_total is not 8-byte aligned");
         if ((st = check_dev_ptr(e_total, c.dev, "e_total")) != PP_OK) return st;
@@ -423,6 +460,61 @@ pp_status pp_grad(const pp_problem *prob, pp_precision prec, pp_sample sample, c
                   float *gx, float *gy, float *e_block, double *e_total, void *ws, size_t ws_bytes,
                   void *stream) {
     return energy_common(prob, prec, sample, a, gx, gy, e_block, e_total, ws, ws_bytes, stream, true);
+}
+
+size_t pp_grad_host_workspace_size(const pp_problem *prob, pp_precision prec) {
+    if (check_shape(prob, prec) != PP_OK) return 0;
+    return layout(prob, prec).total + host_extra_bytes(prob->n);
+}
+
+pp_status pp_grad_host(const pp_problem *prob, pp_precision prec, pp_sample sample, float *gx, float *gy,
+                       float *e_block, double *e_total, void *ws, size_t ws_bytes, void *stream) {
+    pp_status st = check_problem(prob, prec);
+    if (st != PP_OK) return st;
+    const size_t core = layout(prob, prec).total, need = core + host_extra_bytes(prob->n);
+    if (!ws || ws_bytes < need)
+        return fail(PP_ENOMEM_WS, "workspace of %zu bytes needed, %zu given%s", need, ws ? ws_bytes : (size_t)0,
+                    ws ? "" : " (NULL)");
+    if (((uintptr_t)ws & 255) != 0) return fail(PP_EINVAL, "workspace must be 256-byte aligned");
+    int dev, sm, ccm;
+    unsigned *status;
+    if ((st = device_info(&dev, &sm, &status, &ccm)) != PP_OK) return st;
+    if ((st = check_dev_ptr(ws, dev, "ws")) != PP_OK) return st;
+    const bool has_blocks = prob->n > 0;
+    if (has_blocks && (!gx || !gy)) return fail(PP_EINVAL, "gx and gy must be non-NULL when n > 0");
+    if (e_total && ((uintptr_t)e_total & 7) != 0) return fail(PP_EINVAL, "e_total is not 8-byte aligned");
+    char *extra = (char *)ws + core;
+    double *e_dev = (double *)extra;
+    const size_t arr = align256((size_t)prob->n * sizeof(float)), bytes = (size_t)prob->n * sizeof(float);
+    char *stg = extra + 256;
+    const void *ins[5] = {prob->x, prob->y, prob->w, prob->h, prob->c};
+    const char *in_names[5] = {"x", "y", "w", "h", "c"};
+    HostArg in[5], out[3];
+    for (int i = 0; i < 5; ++i)
+        if ((st = resolve_host_arg(has_blocks ? ins[i] : nullptr, dev, in_names[i], stg + i * arr, &in[i])) != PP_OK)
+            return st;
+    void *outs[3] = {gx, gy, e_block};
+    const char *out_names[3] = {"gx", "gy", "e_block"};
+    for (int i = 0; i < 3; ++i)
+        if ((st = resolve_host_arg(has_blocks ? outs[i] : nullptr, dev, out_names[i], stg + (5 + i) * arr,
+                                   &out[i])) != PP_OK)
+            return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    for (int i = 0; i < 5; ++i)
+        if (in[i].staged) PP_TRY(cudaMemcpyAsync(in[i].dev, ins[i], bytes, cudaMemcpyHostToDevice, s), "stage input");
+    pp_problem p = *prob;
+    p.x = (const float *)in[0].dev;
+    p.y = (const float *)in[1].dev;
+    p.w = (const float *)in[2].dev;
+    p.h = (const float *)in[3].dev;
+    p.c = (const float *)in[4].dev;
+    st = energy_common(&p, prec, sample, nullptr, (float *)out[0].dev, (float *)out[1].dev, (float *)out[2].dev,
+                       e_total ? e_dev : nullptr, ws, core, stream, true, true);
+    if (st != PP_OK) return st;
+    for (int i = 0; i < 3; ++i)
+        if (out[i].staged) PP_TRY(cudaMemcpyAsync(outs[i], out[i].dev, bytes, cudaMemcpyDeviceToHost, s), "read output");
+    if (e_total) PP_TRY(cudaMemcpyAsync(e_total, e_dev, sizeof(double), cudaMemcpyDefault, s), "read E");
+    return PP_OK;
 }
 
 pp_status pp_grad_adjoint(const pp_problem *prob, pp_precision prec, pp_sample sample, const double *g_total,

@@ -136,3 +136,15 @@ def test_struct_layouts_match_the_header(tmp_path):
         assert got[f"{sname}.sizeof"] == ctypes.sizeof(cls), sname
         for fname, _ in cls._fields_:
             assert got[f"{sname}.{fname}"] == getattr(cls, fname).offset, (sname, fname)
+
+
+def test_host_workspace_adds_the_staging_arrays(L):
+    for prec in (0, 1, 2):
+        for n in (0, 1000, 12345):
+            p = _prob(n=n)
+            core = L.pp_workspace_size(ctypes.byref(p), prec)
+            host = L.pp_grad_host_workspace_size(ctypes.byref(p), prec)
+            per = ((4 * n + 255) // 256) * 256
+            assert host == core + 256 + 8 * per, (prec, n)
+    assert L.pp_grad_host_workspace_size(ctypes.byref(_prob(W=0.0)), 0) == 0
+    assert L.pp_grad_host_workspace_size(ctypes.byref(_prob()), 7) == 0
