@@ -1141,30 +1141,35 @@ __global__ void tc_finish_kernel(const float *__restrict__ part, int slices, int
     // FP32 throughout (FP64 is a narrow pipe on this GPU): the slice partials are
     // summed with Kahan compensation; the operand is TF32 or bf16 anyway.
     float e_acc = 0.f;                 // this thread's few terms; summed across the CTA in FP64
-    const size_t total = (size_t)Mxe * Mye;
-    for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
-         idx += (size_t)gridDim.x * blockDim.x) {
-        const int u = (int)(idx / Mye), v = (int)(idx % Mye);
+    // 32-bit indices (Mxe * Mye <= 4096^2); Mye is a multiple of 256
+    const int total = Mxe * Mye, mye_sh = 31 - __clz(Mye & -Mye), mye_odd = Mye >> mye_sh;
+    const size_t sstride = (size_t)Mxc * Myc;
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
+        // u = idx / Mye, v = idx % Mye with Mye = mye_odd * 2^mye_sh (mye_odd is 1 for
+        // the powers of two of every workload, else a 32-bit division)
+        const int q = idx >> mye_sh;
+        const int u = mye_odd == 1 ? q : q / mye_odd;
+        const int v = idx - u * Mye;
         float kv = 0.f;
         if (u < Mx && v < My) {
-            const float f = 2.0f / (piW * (float)(u > 0 ? u : 1));     // 2W / (pi max(u,1))
-            const float g = 2.0f / (piH * (float)(v > 0 ? v : 1));
+            const float uf = (float)(u > 0 ? u : 1), vf = (float)(v > 0 ? v : 1);
+            // f g = (2W / (pi u')) (2H / (pi v')) = 4 / (piW piH u' v'), u' v' < 2^24 exact
+            const float fg = 4.0f / (piW * piH * (uf * vf));
             float av;
             if (a_in) {
                 av = a_in[(size_t)u * My + v];
             } else {
                 // slices in order (Kahan), their loads issued eight at a time
                 float S = 0.f, comp = 0.f;
-                const size_t sstride = (size_t)Mxc * Myc;
                 const float *src = part + (size_t)u * Myc + v;
                 int s = 0;
                 for (; s + 8 <= slices; s += 8) {
                     float pv[8];
 #pragma unroll
-                    for (int q = 0; q < 8; ++q) pv[q] = __ldcg(src + (size_t)(s + q) * sstride);
+                    for (int q8 = 0; q8 < 8; ++q8) pv[q8] = __ldcg(src + (size_t)(s + q8) * sstride);
 #pragma unroll
-                    for (int q = 0; q < 8; ++q) {
-                        const float y = pv[q] - comp;
+                    for (int q8 = 0; q8 < 8; ++q8) {
+                        const float y = pv[q8] - comp;
                         const float t = S + y;
                         comp = (t - S) - y;
                         S = t;
@@ -1179,7 +1184,7 @@ __global__ void tc_finish_kernel(const float *__restrict__ part, int slices, int
                 const float ku = (float)u * piW, lv = (float)v * piH;
                 const float eps = (u ? 2.f : 1.f) * (v ? 2.f : 1.f);
                 const float G = (u == 0 && v == 0) ? 0.f : eps * invWH / (ku * ku + lv * lv);
-                av = G * f * g * S;
+                av = G * fg * S;
                 if (a64) {                      // running FP64 sum over calls (chunks, ranks)
                     const double t = a64[(size_t)u * My + v] + (double)av;
                     a64[(size_t)u * My + v] = t;
@@ -1187,17 +1192,17 @@ __global__ void tc_finish_kernel(const float *__restrict__ part, int slices, int
                 } else if (a_out) {
                     a_out[(size_t)u * My + v] = av;
                 }
-                e_acc = fmaf(0.5f * av, f * g * S, e_acc);
+                e_acc = fmaf(0.5f * av, fg * S, e_acc);
             }
-            kv = f * av * g;
+            kv = fg * av;
         }
         if (!Kop) continue;
         const int vb = v >> 8, vi = v & 255;
         if (PREC == 1) {
-            const size_t off = (((size_t)vb * (Mxe / 4) + (u >> 2)) * 256 + vi) * 4 + (u & 3);
+            const int off = ((vb * (Mxe >> 2) + (u >> 2)) * 256 + vi) * 4 + (u & 3);
             reinterpret_cast<float *>(Kop)[off] = to_tf32(kv);
         } else {
-            const size_t off = (((size_t)vb * (Mxe / 8) + (u >> 3)) * 256 + vi) * 8 + (u & 7);
+            const int off = ((vb * (Mxe >> 3) + (u >> 3)) * 256 + vi) * 8 + (u & 7);
             __nv_bfloat16 hi, lo;
             split_bf16(kv, hi, lo);
             reinterpret_cast<__nv_bfloat16 *>(Kop)[off] = hi;
