@@ -153,6 +153,10 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint
     return d;
 }
 
+// The descriptor of an operand `bytes` further on in shared memory (a multiple of 16;
+// the start address field holds address / 16 below 256 KB, so the add cannot carry).
+__device__ __forceinline__ uint64_t desc_add(uint64_t d, uint32_t bytes) { return d + (uint64_t)(bytes >> 4); }
+
 // Instruction descriptor for kind::tf32 (fmt 2) or kind::f16 with bf16 (fmt 1),
 // FP32 accumulation, dense.  a_mn / b_mn select MN-major operands.
 __host__ __device__ constexpr uint32_t instr_desc(uint32_t ab_fmt, int M, int N, bool a_mn, bool b_mn) {
