@@ -1804,7 +1804,14 @@ tc_energy_kernel(const __grid_constant__ CUtensorMap tm_hi, const __grid_constan
         // ---------------- MMA issuer ----------------
         if (lane == 0) {
             const uint32_t idesc = instr_desc(BF ? kFmtBF16 : kFmtTF32, 128, 256, false, false);
+            // stage 0's operand descriptors (A: LBO 128 (u cores), SBO 1024 (TF32) / 512 (bf16)
+            // row groups; B: [u/T][256 v][T] K-major, LBO 4096, SBO 128); the others are byte
+            // offsets from them, so that the issue loop keeps to adds and compares
+            const uint32_t s0 = smem_u32(smem);
+            const uint64_t dA = BF ? smem_desc(s0, 128, 512) : smem_desc(s0, 128, 1024);
+            const uint64_t dB = smem_desc(s0 + 32768, 4096, 128);
             int it = 0, pc = 0;       // stages consumed, accumulator passes
+            int s = 0, ph = 0;        // it % E_STAGES, (it / E_STAGES) & 1
             for (int un = ub; un < ue && !*abort_flag; ++un, ++pc) {
                 {
                     if (pc > 0 && !mbar_wait(&bars.acc_empty, (pc - 1) & 1, kWaitLimit, abort_flag)) {
@@ -1812,41 +1819,37 @@ tc_energy_kernel(const __grid_constant__ CUtensorMap tm_hi, const __grid_constan
                         break;
                     }
                     tc_fence_after();
-                    for (int ks = 0; ks < nks; ++ks, ++it) {
-                        const int s = it % E_STAGES;
-                        if (!mbar_wait(&bars.full[s], (it / E_STAGES) & 1, kWaitLimit, abort_flag) ||
-                            !mbar_wait(&bars.kfull[s], (it / E_STAGES) & 1, kWaitLimit, abort_flag)) {
+                    for (int ks = 0; ks < nks; ++ks, ++it, ph ^= (s + 1 == E_STAGES), s = (s + 1 == E_STAGES ? 0 : s + 1)) {
+                        if (!mbar_wait(&bars.full[s], ph, kWaitLimit, abort_flag) ||
+                            !mbar_wait(&bars.kfull[s], ph, kWaitLimit, abort_flag)) {
                             raise_timeout(args.status, abort_flag);
                             break;
                         }
                         tc_fence_after();
-                        const uint32_t sb = smem_u32(smem + s * E_STAGE_BYTES);
+                        const uint32_t so = (uint32_t)s * E_STAGE_BYTES;
                         if (!BF) {
-                            const uint32_t At = sb, Ah = sb + 16384, B = sb + 32768;
+                            // Xt at +0, Xh at +16 KB, K at +32 KB
 #pragma unroll
                             for (int kk = 0; kk < 4; ++kk) {
-                                // A: LBO 128 (u cores), SBO 1024 (row groups); B: [u/4][256 v][4]
-                                const uint64_t bd = smem_desc(B + kk * 8192, 4096, 128);
+                                const uint64_t bd = desc_add(dB, so + kk * 8192);
                                 const bool accum = ks > 0 || kk > 0;
-                                mma_tf32(tmem, smem_desc(At + kk * 256, 128, 1024), bd, idesc, accum);
-                                mma_tf32(tmem + 256, smem_desc(Ah + kk * 256, 128, 1024), bd, idesc, accum);
+                                mma_tf32(tmem, desc_add(dA, so + kk * 256), bd, idesc, accum);
+                                mma_tf32(tmem + 256, desc_add(dA, so + 16384 + kk * 256), bd, idesc, accum);
                             }
                         } else {
-                            const uint32_t Th = sb, Tl = sb + 8192, Hh = sb + 16384, Hl = sb + 24576;
-                            const uint32_t Bh = sb + 32768, Bl = sb + 49152;
+                            // Xt hi / lo at +0 / +8 KB, Xh hi / lo at +16 / +24 KB, K hi / lo at +32 / +48 KB
 #pragma unroll
                             for (int kk = 0; kk < 2; ++kk) {
-                                // A: LBO 128, SBO 512; B: [u/8][256 v][8]: LBO 4096, SBO 128
-                                const uint64_t bh = smem_desc(Bh + kk * 8192, 4096, 128);
-                                const uint64_t bl = smem_desc(Bl + kk * 8192, 4096, 128);
+                                const uint64_t bh = desc_add(dB, so + kk * 8192);
+                                const uint64_t bl = desc_add(dB, so + 16384 + kk * 8192);
                                 const bool accum = ks > 0 || kk > 0;
-                                const uint32_t ao = kk * 256;
-                                mma_bf16(tmem, smem_desc(Tl + ao, 128, 512), bh, idesc, accum);
-                                mma_bf16(tmem, smem_desc(Th + ao, 128, 512), bl, idesc, true);
-                                mma_bf16(tmem, smem_desc(Th + ao, 128, 512), bh, idesc, true);
-                                mma_bf16(tmem + 256, smem_desc(Hl + ao, 128, 512), bh, idesc, accum);
-                                mma_bf16(tmem + 256, smem_desc(Hh + ao, 128, 512), bl, idesc, true);
-                                mma_bf16(tmem + 256, smem_desc(Hh + ao, 128, 512), bh, idesc, true);
+                                const uint32_t ao = so + kk * 256;
+                                mma_bf16(tmem, desc_add(dA, ao + 8192), bh, idesc, accum);
+                                mma_bf16(tmem, desc_add(dA, ao), bl, idesc, true);
+                                mma_bf16(tmem, desc_add(dA, ao), bh, idesc, true);
+                                mma_bf16(tmem + 256, desc_add(dA, ao + 24576), bh, idesc, accum);
+                                mma_bf16(tmem + 256, desc_add(dA, ao + 16384), bl, idesc, true);
+                                mma_bf16(tmem + 256, desc_add(dA, ao + 16384), bh, idesc, true);
                             }
                         }
                         mma_commit(&bars.empty[s]);
