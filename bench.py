@@ -500,9 +500,13 @@ def run_ours(args):
     ms_per_step = total_ms / args.steps
 
     peaks, peak_src = load_peaks()
-    if ktimes is None:      # binned mode: 13 kernels per step (density, 7 transforms, 3 transposes,
-        ktimes = {"coeff": (0, 0.0), "energy": (0, 0.0)}        # scale, interpolation), not counted
-        launches = 13 * args.steps                              # by the library's counters
+    if ktimes is None:      # binned mode: the library's counters do not count these kernels
+        ktimes = {"coeff": (0, 0.0), "energy": (0, 0.0)}
+        m = args.bins or max(p.Mx, p.My)
+        # density, row prefix sums and interpolation (n > 0), FFT tables (m a power of two),
+        # 7 row transforms, 3 transposes, scaling
+        per_step = (3 if p.n > 0 else 0) + (1 if m & (m - 1) == 0 else 0) + 7 + 3 + 1
+        launches = per_step * args.steps
     else:
         launches = int(sum(v[0] for v in counts.values()))     # our kernels in the timed steps
     extra_lines = {}

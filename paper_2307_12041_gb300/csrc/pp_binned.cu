@@ -1,5 +1,7 @@
 // The paper's binned fast scheme (Sec. III-D) on the GPU:
-//   bin_density_kernel    P_lj = sum_i c_i area(block i ∩ bin lj) / area(bin)
+//   bin_density_kernel    P_lj = sum_i c_i area(block i ∩ bin lj) / area(bin) (the
+//                         interiors of large blocks through a row difference array,
+//                         summed by row_prefix_add_kernel)
 //   transform kernels     the cosine / sine transforms of Eq. (disa), (dis-psi1) and
 //                         (dis-ksi) along one grid axis at a time, one CTA per row:
 //                           a'   = Cx P Cy^T            (DCT-II along j, then along l)
@@ -53,13 +55,18 @@ __device__ __forceinline__ long long fixed_bins(float x, double k) {
 // Blocks covering at most kSmallBins bins are binned by their own thread; larger ones
 // (macros: up to thousands of bins) by the whole warp, which takes them one at a time
 // (found by a ballot) and shares out their bins, so that one large block does not
-// hold its warp for thousands of serial additions.
+// hold its warp for thousands of serial additions.  With a difference array D, a large
+// block spans at least 3 bin columns: the bins strictly inside its column range are
+// covered fully along y, so row l of the block adds the same c fx(l) to each of them.
+// It adds +c fx(l) at D[l][j0 + 1] and -c fx(l) at D[l][j1] instead, its two edge
+// columns directly, and row_prefix_add_kernel adds the prefix sums of D's rows to P:
+// four additions per row of the block instead of one per bin.
 constexpr int kSmallBins = 8;
 
 __global__ void bin_density_kernel(const float *__restrict__ x, const float *__restrict__ y,
                                    const float *__restrict__ w, const float *__restrict__ h,
                                    const float *__restrict__ c, int n, int m, double inv_wb,
-                                   double inv_hb, float *__restrict__ P) {
+                                   double inv_hb, float *__restrict__ P, float *__restrict__ D) {
     constexpr int F = 40;                                 // fraction bits of a bin coordinate
     constexpr long long ONE = 1ll << F;
     const float unit = 0x1p-40f;
@@ -111,8 +118,25 @@ __global__ void bin_density_kernel(const float *__restrict__ x, const float *__r
             const long long bx0 = __shfl_sync(0xffffffffu, x0, src), bx1 = __shfl_sync(0xffffffffu, x1, src);
             const long long by0 = __shfl_sync(0xffffffffu, y0, src), by1 = __shfl_sync(0xffffffffu, y1, src);
             const int bl0 = __shfl_sync(0xffffffffu, l0, src), bj0 = __shfl_sync(0xffffffffu, j0, src);
-            const long long bnj = __shfl_sync(0xffffffffu, nj, src), tot = bnj * __shfl_sync(0xffffffffu, nl, src);
+            const long long bnl = __shfl_sync(0xffffffffu, nl, src);
+            const long long bnj = __shfl_sync(0xffffffffu, nj, src), tot = bnj * bnl;
             const float bc = __shfl_sync(0xffffffffu, ci, src);
+            if (D && bnj >= 3) {
+                const int ja = bj0, jb = bj0 + (int)bnj - 1;
+                const float fa = (float)overlap(by0, by1, ja) * unit, fb = (float)overlap(by0, by1, jb) * unit;
+                for (long long r = lane; r < bnl; r += 32) {
+                    const int l = bl0 + (int)r;
+                    const long long ox = overlap(bx0, bx1, l);
+                    if (ox <= 0) continue;
+                    const float cx = bc * ((float)ox * unit);
+                    float *Pr = P + (size_t)l * m, *Dr = D + (size_t)l * m;
+                    if (fa > 0.f) atomicAdd(Pr + ja, cx * fa);
+                    if (fb > 0.f) atomicAdd(Pr + jb, cx * fb);
+                    atomicAdd(Dr + ja + 1, cx);
+                    atomicAdd(Dr + jb, -cx);
+                }
+                continue;
+            }
             for (long long k = lane; k < tot; k += 32) {
                 const int l = bl0 + (int)(k / bnj), j = bj0 + (int)(k % bnj);
                 const long long ox = overlap(bx0, bx1, l), oy = overlap(by0, by1, j);
@@ -120,6 +144,45 @@ __global__ void bin_density_kernel(const float *__restrict__ x, const float *__r
                     atomicAdd(&P[(size_t)l * m + j], bc * ((float)ox * unit) * ((float)oy * unit));
             }
         }
+    }
+}
+
+// P[l][j] += sum_{j' <= j} D[l][j'] (one CTA of 256 threads per row l, the row in chunks
+// of 1,024 in order, each an inclusive scan: 4 values per thread, then the warp and
+// block partial sums); D is left as it was.
+__global__ void __launch_bounds__(256) row_prefix_add_kernel(const float *__restrict__ D, float *__restrict__ P,
+                                                             int m) {
+    __shared__ float wsum[8];
+    const float *dr = D + (size_t)blockIdx.x * m;
+    float *pr = P + (size_t)blockIdx.x * m;
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    float carry = 0.f;
+    for (int base = 0; base < m; base += 1024) {
+        const int j = base + 4 * threadIdx.x;
+        float v[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) v[q] = j + q < m ? dr[j + q] : 0.f;
+        v[1] += v[0];
+        v[2] += v[1];
+        v[3] += v[2];
+        float t = v[3];                                   // this thread's total; inclusive scan over the warp
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const float o = __shfl_up_sync(0xffffffffu, t, off);
+            if (lane >= off) t += o;
+        }
+        if (lane == 31) wsum[wp] = t;
+        __syncthreads();
+        float before = carry;                             // chunks before, warps before, lanes before
+        for (int k = 0; k < wp; ++k) before += wsum[k];
+        before += t - v[3];
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            if (j + q < m) pr[j + q] += before + v[q];
+        float chunk = 0.f;
+        for (int k = 0; k < 8; ++k) chunk += wsum[k];
+        carry += chunk;
+        __syncthreads();                                  // wsum is rewritten by the next chunk
     }
 }
 
@@ -350,6 +413,7 @@ BinnedLayout binned_layout(int m, int Mx, int My) {
     };
     const size_t mm = (size_t)m * m;
     L.P = take(mm);
+    L.D = take(mm);
     L.R1 = take((size_t)m * My);
     L.R1t = take((size_t)My * m);
     L.R2 = take((size_t)My * Mx);
@@ -367,7 +431,7 @@ BinnedLayout binned_layout(int m, int Mx, int My) {
 cudaError_t launch_bin_density(const float *x, const float *y, const float *w, const float *h, const float *c,
                                int n, int m, double W, double H, float *P, int sm_count, cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
-    bin_density_kernel<<<8 * sm_count, 256, 0, st>>>(x, y, w, h, c, n, m, m / W, m / H, P);
+    bin_density_kernel<<<8 * sm_count, 256, 0, st>>>(x, y, w, h, c, n, m, m / W, m / H, P, nullptr);
     return cudaGetLastError();
 }
 
@@ -429,12 +493,16 @@ cudaError_t run_binned(const Launch &Lc, int dev, int m, bool tf32, unsigned cha
     float2 *tw = (float2 *)(ws + B.tab), *qw = tw + m / 2;
     cudaStream_t st = Lc.stream;
     *what = "binned scheme launch";
+    float *D = (float *)(ws + B.D);
     cudaError_t e = cudaMemsetAsync(P, 0, (size_t)m * m * sizeof(float), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(D, 0, (size_t)m * m * sizeof(float), st);
     if (e != cudaSuccess) return e;
     if (e_total && (e = cudaMemsetAsync(e_total, 0, sizeof(double), st)) != cudaSuccess) return e;
     const int grid = 8 * Lc.sm_count;
     if (n > 0) {
-        bin_density_kernel<<<grid, 256, 0, st>>>(Lc.x, Lc.y, Lc.w, Lc.h, Lc.c, n, m, m / Lc.W, m / Lc.H, P);
+        bin_density_kernel<<<grid, 256, 0, st>>>(Lc.x, Lc.y, Lc.w, Lc.h, Lc.c, n, m, m / Lc.W, m / Lc.H, P, D);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        row_prefix_add_kernel<<<m, 256, 0, st>>>(D, P, m);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     const float kW = (float)(3.141592653589793 / Lc.W), lH = (float)(3.141592653589793 / Lc.H);
