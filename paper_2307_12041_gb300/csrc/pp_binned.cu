@@ -307,6 +307,115 @@ __global__ void __launch_bounds__(T_THREADS) fft_rows_kernel(const float *__rest
     }
 }
 
+// The same transforms for m = 32 R (R = 16, 32), one warp per row and no block-wide
+// barrier after the tables: the four-step FFT with n = R n1 + n2 and k = k1 + 32 k2,
+//   Y_k = sum_n y_n W^{nk} = sum_{n2} W_R^{n2 k2} W_m^{n2 k1} sum_{n1} y_{R n1 + n2} W_32^{n1 k1}
+// (W = e^{-2 pi i / m}, conjugated for the inverse transforms).  Lane n1 holds y_{R n1 + n2}
+// for every n2 in registers; the 32-point transforms run across the lanes (decimation in
+// frequency by shuffles, leaving lane L with k1 = bitreverse5(L)); then the twiddle, then
+// an R-point decimation-in-frequency transform in registers (leaving k2 bit-reversed).
+// The row comes in and the results go out through the warp's shared-memory buffer, padded
+// by one word per 32 (pad()), so that global accesses are coalesced and the lanes' strided
+// shared-memory accesses fall in distinct banks.  The pre- and post-processing of the
+// DCT-II / DCT-III / DST-III are those of fft_rows_kernel.
+__device__ __forceinline__ int pad(int i) { return i + (i >> 5); }
+
+template <int MODE, int R>
+__global__ void __launch_bounds__(128) fft_rows_warp_kernel(const float *__restrict__ in, int in_ld, int kin,
+                                                           float in_scale, int nrows, int keep,
+                                                           float *__restrict__ out, int out_ld, int ostr,
+                                                           const float2 *__restrict__ tw_g,
+                                                           const float2 *__restrict__ qw_g) {
+    constexpr int m = 32 * R, half = m / 2, mp = m + m / 32;
+    constexpr bool INV = MODE != T_DCT2;
+    __shared__ float2 tw[half];                              // e^{-2 pi i k / m}
+    __shared__ float2 qw[mp];                                // (cos, sin)(pi u / 2m) at pad(u)
+    __shared__ float xs[4][mp];                              // one row per warp, at pad(i)
+    for (int k = threadIdx.x; k < half; k += blockDim.x) tw[k] = tw_g[k];
+    for (int k = threadIdx.x; k < m; k += blockDim.x) qw[pad(k)] = qw_g[k];
+    __syncthreads();
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    const int r = blockIdx.x * 4 + wp;
+    if (r >= nrows) return;                                  // no block-wide barrier below
+    float *xw = xs[wp];
+    const float *row = in + (size_t)r * in_ld;
+    for (int i = lane; i < kin; i += 32) {
+        const float v = row[i];
+        xw[pad(i)] = (MODE != T_DCT2 && in_scale != 0.f) ? v * ((float)i * in_scale) : v;   // s_u c_u
+    }
+    __syncwarp();
+    auto W = [&](int j) -> float2 {                          // W^j, any j >= 0
+        j &= m - 1;
+        float2 w = j < half ? tw[j] : make_float2(-tw[j - half].x, -tw[j - half].y);
+        if (INV) w.y = -w.y;
+        return w;
+    };
+    auto coef = [&](int u) -> float { return u >= 0 && u < kin ? xw[pad(u)] : 0.f; };
+    float2 a[R];
+#pragma unroll
+    for (int n2 = 0; n2 < R; ++n2) {
+        const int n = R * lane + n2;
+        if (MODE == T_DCT2) {
+            const int src = n < half ? 2 * n : 2 * (m - 1 - n) + 1;
+            a[n2] = make_float2(coef(src), 0.f);
+        } else {
+            const float cu = MODE == T_DCT3 ? coef(n) : (n == 0 ? 0.f : coef(m - n));
+            const float cmu = n == 0 ? 0.f : (MODE == T_DCT3 ? coef(m - n) : coef(n));
+            const float2 q = qw[pad(n)];
+            a[n2] = make_float2(q.x * cu + q.y * cmu, q.y * cu - q.x * cmu);
+        }
+    }
+    const float c0 = MODE == T_DCT3 ? coef(0) : 0.f;
+    // 32-point transforms across the lanes: pairs (i, i + h), i with bit h clear:
+    // y_i <- y_i + y_{i+h}, y_{i+h} <- (y_i - y_{i+h}) W_{2h}^{i mod h}
+#pragma unroll
+    for (int h = 16; h >= 1; h >>= 1) {
+        const bool hi = (lane & h) != 0;
+        const float2 w = W((lane & (h - 1)) * (m / (2 * h)));
+#pragma unroll
+        for (int n2 = 0; n2 < R; ++n2) {
+            const float ox = __shfl_xor_sync(0xffffffffu, a[n2].x, h);
+            const float oy = __shfl_xor_sync(0xffffffffu, a[n2].y, h);
+            a[n2] = hi ? cmul(make_float2(ox - a[n2].x, oy - a[n2].y), w)
+                       : make_float2(a[n2].x + ox, a[n2].y + oy);
+        }
+    }
+    const int k1 = (int)(__brev((unsigned)lane) >> 27);
+#pragma unroll
+    for (int n2 = 1; n2 < R; ++n2) a[n2] = cmul(a[n2], W(n2 * k1));
+    // R-point transforms in registers, the same butterflies with compile-time indices
+#pragma unroll
+    for (int h = R / 2; h >= 1; h >>= 1) {
+#pragma unroll
+        for (int i = 0; i < R; ++i) {
+            if (i & h) continue;
+            const float2 u = a[i], v = a[i + h];
+            a[i] = make_float2(u.x + v.x, u.y + v.y);
+            a[i + h] = cmul(make_float2(u.x - v.x, u.y - v.y), W((i & (h - 1)) * (m / (2 * h))));
+        }
+    }
+    // a[j] = Y_k, k = k1 + 32 bitreverse(j) over log2 R bits: results to the warp buffer at
+    // their output positions, then out in order
+    constexpr int LR = R == 16 ? 4 : 5;
+    __syncwarp();                                            // every lane has read its inputs
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+        const int k = k1 + 32 * (int)(__brev((unsigned)j) >> (32 - LR));
+        if (MODE == T_DCT2) {
+            const float2 q = qw[pad(k)];
+            xw[pad(k)] = a[j].x * q.x + a[j].y * q.y;
+        } else {
+            const int l = k < half ? 2 * k : 2 * (m - 1 - k) + 1;
+            const float t = 0.5f * (a[j].x + c0);
+            xw[pad(l)] = (MODE == T_DST3 && (l & 1)) ? -t : t;
+        }
+    }
+    __syncwarp();
+    float *orow = out + (size_t)r * out_ld;
+    const int nout = MODE == T_DCT2 ? keep : m;
+    for (int i = lane; i < nout; i += 32) orow[(size_t)i * ostr] = xw[pad(i)];
+}
+
 // The same transforms for any m: direct sums over a table cos(pi q / 2m), q < 4m
 // (sin(pi q / 2m) = cos(pi (q - m) / 2m)); the phase u (2l + 1) is kept mod 4m in
 // integers.
@@ -440,12 +549,26 @@ namespace {
 bool pow2(int m) { return m > 0 && (m & (m - 1)) == 0; }
 
 // rows transforms of `mode` (T_DCT2 / T_DCT3 / T_DST3), FFT when m is a power of two
+// (one warp per row for m = 512, 1024; one CTA per row otherwise)
 // rows `nrows` of `in` transformed; output element k of row r at out[r * out_ld + k * ostr]
 cudaError_t rows(int mode, const float *in, int in_ld, int nrows, int kin, float in_scale, int m, int keep,
                  float *out, int out_ld, int ostr, const float2 *tw, const float2 *qw, cudaStream_t st) {
     if (nrows <= 0) return cudaSuccess;
     cudaError_t e;
-    if (pow2(m)) {
+    if (m == 512 || m == 1024) {
+        auto go = [&](auto kfn) {
+            kfn<<<(nrows + 3) / 4, 128, 0, st>>>(in, in_ld, kin, in_scale, nrows, keep, out, out_ld, ostr, tw, qw);
+            return cudaGetLastError();
+        };
+        if (m == 512)
+            e = mode == T_DCT2 ? go(fft_rows_warp_kernel<T_DCT2, 16>)
+                               : (mode == T_DCT3 ? go(fft_rows_warp_kernel<T_DCT3, 16>)
+                                                 : go(fft_rows_warp_kernel<T_DST3, 16>));
+        else
+            e = mode == T_DCT2 ? go(fft_rows_warp_kernel<T_DCT2, 32>)
+                               : (mode == T_DCT3 ? go(fft_rows_warp_kernel<T_DCT3, 32>)
+                                                 : go(fft_rows_warp_kernel<T_DST3, 32>));
+    } else if (pow2(m)) {
         int lg = 0;
         while ((1 << lg) < m) ++lg;
         const size_t smem = (size_t)(m + m / 2) * sizeof(float2);

@@ -20,7 +20,9 @@ CASES = [
     (500, 64, 64, 64, 1.3, 0.8, True, "uniform"),
     (3000, 100, 90, 128, 1.0, 1.0, False, "mix"),
     (1, 2, 2, 2, 1.0, 1.0, False, "uniform"),
-    (20000, 256, 200, 512, 1.0, 1.0, False, "mix"),          # FFT, 9 radix-2 stages
+    (20000, 256, 200, 512, 1.0, 1.0, False, "mix"),          # warp FFT, R = 16
+    (30000, 300, 260, 1024, 1.1, 0.9, True, "mix"),           # warp FFT, R = 32
+    (2000, 100, 120, 256, 1.0, 1.0, False, "mix"),            # block FFT, 8 radix-2 stages
     (700, 50, 60, 96, 1.2, 0.9, True, "uniform"),             # m not a power of two: direct sums
     (5, 3, 3, 3, 1.0, 1.0, False, "uniform"),
     (4000, 90, 100, 100, 1.0, 1.0, False, "mix"),
