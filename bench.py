@@ -503,9 +503,11 @@ def run_ours(args):
     if ktimes is None:      # binned mode: the library's counters do not count these kernels
         ktimes = {"coeff": (0, 0.0), "energy": (0, 0.0)}
         m = args.bins or max(p.Mx, p.My)
-        # density, row prefix sums and interpolation (n > 0), FFT tables (m a power of two),
-        # 7 row transforms, 3 transposes, scaling
-        per_step = (3 if p.n > 0 else 0) + (1 if m & (m - 1) == 0 else 0) + 7 + 3 + 1
+        # density and interpolation (n > 0), the row prefix sums of the difference array
+        # (n > 0, folded into the first row transform for m = 512, 1024), FFT tables (m a
+        # power of two), 7 row transforms, 3 transposes, scaling
+        per_step = ((2 + (0 if m in (512, 1024) else 1)) if p.n > 0 else 0) \
+            + (1 if m & (m - 1) == 0 else 0) + 7 + 3 + 1
         launches = per_step * args.steps
     else:
         launches = int(sum(v[0] for v in counts.values()))     # our kernels in the timed steps

@@ -325,7 +325,8 @@ __global__ void __launch_bounds__(128) fft_rows_warp_kernel(const float *__restr
                                                            float in_scale, int nrows, int keep,
                                                            float *__restrict__ out, int out_ld, int ostr,
                                                            const float2 *__restrict__ tw_g,
-                                                           const float2 *__restrict__ qw_g) {
+                                                           const float2 *__restrict__ qw_g,
+                                                           const float *__restrict__ dif) {
     constexpr int m = 32 * R, half = m / 2, mp = m + m / 32;
     constexpr bool INV = MODE != T_DCT2;
     __shared__ float2 tw[half];                              // e^{-2 pi i k / m}
@@ -342,6 +343,32 @@ __global__ void __launch_bounds__(128) fft_rows_warp_kernel(const float *__restr
     for (int i = lane; i < kin; i += 32) {
         const float v = row[i];
         xw[pad(i)] = (MODE != T_DCT2 && in_scale != 0.f) ? v * ((float)i * in_scale) : v;   // s_u c_u
+    }
+    if (MODE == T_DCT2 && dif) {
+        // the bin density's row: plus the prefix sums of the difference array's row (the
+        // large blocks' interiors, bin_density_kernel); lane L sums entries R L .. R L + R - 1
+        __syncwarp();
+        const float4 *d4 = reinterpret_cast<const float4 *>(dif + (size_t)r * in_ld + R * lane);
+        float pre[R];
+#pragma unroll
+        for (int q = 0; q < R / 4; ++q) {
+            const float4 v = d4[q];
+            pre[4 * q] = v.x;
+            pre[4 * q + 1] = v.y;
+            pre[4 * q + 2] = v.z;
+            pre[4 * q + 3] = v.w;
+        }
+#pragma unroll
+        for (int q = 1; q < R; ++q) pre[q] += pre[q - 1];
+        float t = pre[R - 1];                                // inclusive scan of the lanes' totals
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const float o = __shfl_up_sync(0xffffffffu, t, off);
+            if (lane >= off) t += o;
+        }
+        const float before = t - pre[R - 1];
+#pragma unroll
+        for (int q = 0; q < R; ++q) xw[pad(R * lane + q)] += before + pre[q];
     }
     __syncwarp();
     auto W = [&](int j) -> float2 {                          // W^j, any j >= 0
@@ -547,17 +574,21 @@ cudaError_t launch_bin_density(const float *x, const float *y, const float *w, c
 namespace {
 
 bool pow2(int m) { return m > 0 && (m & (m - 1)) == 0; }
+bool warp_fft(int m) { return m == 512 || m == 1024; }
 
 // rows transforms of `mode` (T_DCT2 / T_DCT3 / T_DST3), FFT when m is a power of two
 // (one warp per row for m = 512, 1024; one CTA per row otherwise)
 // rows `nrows` of `in` transformed; output element k of row r at out[r * out_ld + k * ostr]
+// dif (DCT-II with the warp FFT only): row prefix sums added to the input rows
 cudaError_t rows(int mode, const float *in, int in_ld, int nrows, int kin, float in_scale, int m, int keep,
-                 float *out, int out_ld, int ostr, const float2 *tw, const float2 *qw, cudaStream_t st) {
+                 float *out, int out_ld, int ostr, const float2 *tw, const float2 *qw, cudaStream_t st,
+                 const float *dif = nullptr) {
     if (nrows <= 0) return cudaSuccess;
     cudaError_t e;
-    if (m == 512 || m == 1024) {
+    if (warp_fft(m)) {
         auto go = [&](auto kfn) {
-            kfn<<<(nrows + 3) / 4, 128, 0, st>>>(in, in_ld, kin, in_scale, nrows, keep, out, out_ld, ostr, tw, qw);
+            kfn<<<(nrows + 3) / 4, 128, 0, st>>>(in, in_ld, kin, in_scale, nrows, keep, out, out_ld, ostr, tw, qw,
+                                                 dif);
             return cudaGetLastError();
         };
         if (m == 512)
@@ -617,16 +648,18 @@ cudaError_t run_binned(const Launch &Lc, int dev, int m, bool tf32, unsigned cha
     cudaStream_t st = Lc.stream;
     *what = "binned scheme launch";
     float *D = (float *)(ws + B.D);
-    cudaError_t e = cudaMemsetAsync(P, 0, (size_t)m * m * sizeof(float), st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(D, 0, (size_t)m * m * sizeof(float), st);
+    // P and D are consecutive: one memset for both
+    cudaError_t e = cudaMemsetAsync(P, 0, B.D - B.P + (size_t)m * m * sizeof(float), st);
     if (e != cudaSuccess) return e;
     if (e_total && (e = cudaMemsetAsync(e_total, 0, sizeof(double), st)) != cudaSuccess) return e;
     const int grid = 8 * Lc.sm_count;
     if (n > 0) {
         bin_density_kernel<<<grid, 256, 0, st>>>(Lc.x, Lc.y, Lc.w, Lc.h, Lc.c, n, m, m / Lc.W, m / Lc.H, P, D);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        row_prefix_add_kernel<<<m, 256, 0, st>>>(D, P, m);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        if (!warp_fft(m)) {        // else added by the first row transform
+            row_prefix_add_kernel<<<m, 256, 0, st>>>(D, P, m);
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        }
     }
     const float kW = (float)(3.141592653589793 / Lc.W), lH = (float)(3.141592653589793 / Lc.H);
     if (pow2(m)) {
@@ -638,7 +671,7 @@ cudaError_t run_binned(const Launch &Lc, int dev, int m, bool tf32, unsigned cha
         if ((e = (expr)) != cudaSuccess) return e; \
     } while (0)
     // a' = Cx P Cy^T: along j (rows l of P), then along l
-    PP_STEP(rows(T_DCT2, P, m, m, m, 0.f, m, My, R1, My, 1, tw, qw, st));
+    PP_STEP(rows(T_DCT2, P, m, m, m, 0.f, m, My, R1, My, 1, tw, qw, st, n > 0 ? D : nullptr));
     PP_STEP(transpose(R1, My, m, My, R1t, m, st));
     PP_STEP(rows(T_DCT2, R1t, m, My, m, 0.f, m, Mx, R2, Mx, 1, tw, qw, st));
     scale_kernel<<<grid, 256, 0, st>>>(Mx, My, m, (float)Lc.W, (float)Lc.H, R2, a);
