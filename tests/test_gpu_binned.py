@@ -54,6 +54,25 @@ def test_binned_matches_oracle(pp, case, prec):
     assert abs(float(E.item()) - ref["E"]) <= tol * abs(ref["E"])
 
 
+@pytest.mark.parametrize("m", [512, 1024, 256, 100])
+def test_binned_out_of_die_blocks_match_oracle(pp, m):
+    """Blocks overhanging the die, wider than it, or outside it (only the part inside
+    the die is binned, in the oracle as on the GPU): large blocks take the difference
+    array with their column range clamped to the grid; m = 512, 1024 add its prefix
+    sums in the first row transform, 256 in the separate kernel, 100 uses direct sums."""
+    p = synth.out_of_die_blocks(3000, 64, 48, seed=40 + m, W=1.2, H=0.9)
+    ref = B.evaluate(p.W, p.H, p.x, p.y, p.w, p.h, p.c, 64, 48, m)
+    x, y, w, h, c = pp.binding.to_device(p, torch.device("cuda"))
+    gx, gy, N, E, a = pp.binding.binned_grad(x, y, w, h, c, p.W, p.H, 64, 48, m, "fp32")
+    pp.binding.sync_status()
+    tol = BINNED_TOL["fp32"]
+    assert nerr(a.cpu().numpy(), ref["a"]) <= tol
+    assert nerr(N.cpu().numpy(), ref["N"]) <= tol
+    g = np.concatenate([gx.cpu().numpy(), gy.cpu().numpy()])
+    assert nerr(g, np.concatenate([ref["gx"], ref["gy"]])) <= tol
+    assert abs(float(E.item()) - ref["E"]) <= tol * abs(ref["E"])
+
+
 def test_binned_rejects_bad_bins(pp):
     p = synth.uniform_blocks(10, 8, 8, seed=1)
     x, y, w, h, c = pp.binding.to_device(p, torch.device("cuda"))
