@@ -329,11 +329,15 @@ __global__ void __launch_bounds__(128) fft_rows_warp_kernel(const float *__restr
                                                            const float *__restrict__ dif) {
     constexpr int m = 32 * R, half = m / 2, mp = m + m / 32;
     constexpr bool INV = MODE != T_DCT2;
-    __shared__ float2 tw[half];                              // e^{-2 pi i k / m}
+    __shared__ float2 tw[m];                                 // W^k (e^{-+2 pi i k / m}), k < m
     __shared__ float2 qw[mp];                                // (cos, sin)(pi u / 2m) at pad(u)
     __shared__ float xs[4][mp];                              // one row per warp, at pad(i)
-    for (int k = threadIdx.x; k < half; k += blockDim.x) tw[k] = tw_g[k];
-    for (int k = threadIdx.x; k < m; k += blockDim.x) qw[pad(k)] = qw_g[k];
+    for (int k = threadIdx.x; k < m; k += blockDim.x) {
+        float2 w = k < half ? tw_g[k] : make_float2(-tw_g[k - half].x, -tw_g[k - half].y);
+        if (INV) w.y = -w.y;
+        tw[k] = w;
+        qw[pad(k)] = qw_g[k];
+    }
     __syncthreads();
     const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
     const int r = blockIdx.x * 4 + wp;
@@ -371,12 +375,7 @@ __global__ void __launch_bounds__(128) fft_rows_warp_kernel(const float *__restr
         for (int q = 0; q < R; ++q) xw[pad(R * lane + q)] += before + pre[q];
     }
     __syncwarp();
-    auto W = [&](int j) -> float2 {                          // W^j, any j >= 0
-        j &= m - 1;
-        float2 w = j < half ? tw[j] : make_float2(-tw[j - half].x, -tw[j - half].y);
-        if (INV) w.y = -w.y;
-        return w;
-    };
+    auto W = [&](int j) -> float2 { return tw[j & (m - 1)]; };   // W^j, any j >= 0
     auto coef = [&](int u) -> float { return u >= 0 && u < kin ? xw[pad(u)] : 0.f; };
     float2 a[R];
 #pragma unroll
@@ -397,14 +396,15 @@ __global__ void __launch_bounds__(128) fft_rows_warp_kernel(const float *__restr
     // y_i <- y_i + y_{i+h}, y_{i+h} <- (y_i - y_{i+h}) W_{2h}^{i mod h}
 #pragma unroll
     for (int h = 16; h >= 1; h >>= 1) {
+        // y_i + y_{i+h} = (o + a) * 1 on the lanes with bit h clear, (o - a) W otherwise
         const bool hi = (lane & h) != 0;
-        const float2 w = W((lane & (h - 1)) * (m / (2 * h)));
+        const float sg = hi ? -1.f : 1.f;
+        const float2 w = hi ? W((lane & (h - 1)) * (m / (2 * h))) : make_float2(1.f, 0.f);
 #pragma unroll
         for (int n2 = 0; n2 < R; ++n2) {
             const float ox = __shfl_xor_sync(0xffffffffu, a[n2].x, h);
             const float oy = __shfl_xor_sync(0xffffffffu, a[n2].y, h);
-            a[n2] = hi ? cmul(make_float2(ox - a[n2].x, oy - a[n2].y), w)
-                       : make_float2(a[n2].x + ox, a[n2].y + oy);
+            a[n2] = cmul(make_float2(fmaf(sg, a[n2].x, ox), fmaf(sg, a[n2].y, oy)), w);
         }
     }
     const int k1 = (int)(__brev((unsigned)lane) >> 27);
@@ -441,6 +441,150 @@ __global__ void __launch_bounds__(128) fft_rows_warp_kernel(const float *__restr
     float *orow = out + (size_t)r * out_ld;
     const int nout = MODE == T_DCT2 ? keep : m;
     for (int i = lane; i < nout; i += 32) orow[(size_t)i * ostr] = xw[pad(i)];
+}
+
+// m = 1024 with two warps per row (twice the warps of fft_rows_warp_kernel, half the
+// registers each).  Warp h of a row holds n2 in [16 h, 16 h + 16) and runs the 32-point
+// transforms across the lanes and the twiddle for those.  The 32-point transform over n2
+// begins with the butterflies (n2, n2 + 16), which pair the two warps, so they exchange
+// their values once through shared memory:
+//   warp 0:  u_i = y_i + y_{i+16}                 -> Y_{k1 + 32 (2q)},     16-point over i
+//   warp 1:  v_i = (y_i - y_{i+16}) W_32^i        -> Y_{k1 + 32 (2q + 1)}, 16-point over i
+// (i < 16).  Named barrier 1 + (row within the CTA) joins the row's two warps.
+template <int MODE>
+__global__ void __launch_bounds__(128) fft_rows_pair_kernel(const float *__restrict__ in, int in_ld, int kin,
+                                                           float in_scale, int nrows, int keep,
+                                                           float *__restrict__ out, int out_ld, int ostr,
+                                                           const float2 *__restrict__ tw_g,
+                                                           const float2 *__restrict__ qw_g,
+                                                           const float *__restrict__ dif) {
+    constexpr int R = 32, H = 16, m = 32 * R, half = m / 2, mp = m + m / 32;
+    constexpr bool INV = MODE != T_DCT2;
+    __shared__ float2 tw[m];                                 // W^k (e^{-+2 pi i k / m}), k < m
+    __shared__ float2 qw[mp];                                // (cos, sin)(pi u / 2m) at pad(u)
+    __shared__ float xs[2][mp];                              // one row per warp pair, at pad(i)
+    __shared__ float2 xch[2][2][H][32];                      // [row][warp][i][lane]
+    for (int k = threadIdx.x; k < m; k += blockDim.x) {
+        float2 w = k < half ? tw_g[k] : make_float2(-tw_g[k - half].x, -tw_g[k - half].y);
+        if (INV) w.y = -w.y;
+        tw[k] = w;
+        qw[pad(k)] = qw_g[k];
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    const int rr = wp >> 1, h = wp & 1;                      // row within the CTA, warp within the row
+    const int r = blockIdx.x * 2 + rr;
+    if (r >= nrows) return;                                  // both warps of the row together
+    const int bar = 1 + rr;
+    auto row_sync = [&]() { asm volatile("bar.sync %0, 64;" ::"r"(bar) : "memory"); };
+    float *xw = xs[rr];
+    const float *row = in + (size_t)r * in_ld;
+    for (int i = threadIdx.x & 63; i < kin; i += 64) {
+        const float v = row[i];
+        xw[pad(i)] = (MODE != T_DCT2 && in_scale != 0.f) ? v * ((float)i * in_scale) : v;   // s_u c_u
+    }
+    if (MODE == T_DCT2 && dif) {
+        // the difference array's row prefix sums (as fft_rows_warp_kernel), by warp 0 of the row
+        row_sync();
+        if (h == 0) {
+            const float4 *d4 = reinterpret_cast<const float4 *>(dif + (size_t)r * in_ld + R * lane);
+            float pre[R];
+#pragma unroll
+            for (int q = 0; q < R / 4; ++q) {
+                const float4 v = d4[q];
+                pre[4 * q] = v.x;
+                pre[4 * q + 1] = v.y;
+                pre[4 * q + 2] = v.z;
+                pre[4 * q + 3] = v.w;
+            }
+#pragma unroll
+            for (int q = 1; q < R; ++q) pre[q] += pre[q - 1];
+            float t = pre[R - 1];
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                const float o = __shfl_up_sync(0xffffffffu, t, off);
+                if (lane >= off) t += o;
+            }
+            const float before = t - pre[R - 1];
+#pragma unroll
+            for (int q = 0; q < R; ++q) xw[pad(R * lane + q)] += before + pre[q];
+        }
+    }
+    row_sync();
+    auto W = [&](int j) -> float2 { return tw[j & (m - 1)]; };   // W^j, any j >= 0
+    auto coef = [&](int u) -> float { return u >= 0 && u < kin ? xw[pad(u)] : 0.f; };
+    float2 a[H];
+#pragma unroll
+    for (int i = 0; i < H; ++i) {
+        const int n = R * lane + H * h + i;
+        if (MODE == T_DCT2) {
+            const int src = n < half ? 2 * n : 2 * (m - 1 - n) + 1;
+            a[i] = make_float2(coef(src), 0.f);
+        } else {
+            const float cu = MODE == T_DCT3 ? coef(n) : (n == 0 ? 0.f : coef(m - n));
+            const float cmu = n == 0 ? 0.f : (MODE == T_DCT3 ? coef(m - n) : coef(n));
+            const float2 q = qw[pad(n)];
+            a[i] = make_float2(q.x * cu + q.y * cmu, q.y * cu - q.x * cmu);
+        }
+    }
+    const float c0 = MODE == T_DCT3 ? coef(0) : 0.f;
+#pragma unroll
+    for (int hh = 16; hh >= 1; hh >>= 1) {
+        const bool hi = (lane & hh) != 0;
+        const float sg = hi ? -1.f : 1.f;
+        const float2 w = hi ? W((lane & (hh - 1)) * (m / (2 * hh))) : make_float2(1.f, 0.f);
+#pragma unroll
+        for (int i = 0; i < H; ++i) {
+            const float ox = __shfl_xor_sync(0xffffffffu, a[i].x, hh);
+            const float oy = __shfl_xor_sync(0xffffffffu, a[i].y, hh);
+            a[i] = cmul(make_float2(fmaf(sg, a[i].x, ox), fmaf(sg, a[i].y, oy)), w);
+        }
+    }
+    const int k1 = (int)(__brev((unsigned)lane) >> 27);
+#pragma unroll
+    for (int i = 0; i < H; ++i) {
+        const int n2 = H * h + i;
+        if (n2 > 0) a[i] = cmul(a[i], W(n2 * k1));
+    }
+    // the first butterflies of the 32-point transform over n2, across the row's two warps
+#pragma unroll
+    for (int i = 0; i < H; ++i) xch[rr][h][i][lane] = a[i];
+    row_sync();
+#pragma unroll
+    for (int i = 0; i < H; ++i) {
+        const float2 o = xch[rr][1 - h][i][lane];
+        if (h == 0) a[i] = make_float2(a[i].x + o.x, a[i].y + o.y);                          // y_i + y_{i+16}
+        else a[i] = cmul(make_float2(o.x - a[i].x, o.y - a[i].y), W(i * (m / 32)));          // (y_i - y_{i+16}) W_32^i
+    }
+    // 16-point transforms in registers (W_16 = W_m^{m/16})
+#pragma unroll
+    for (int hh = H / 2; hh >= 1; hh >>= 1) {
+#pragma unroll
+        for (int i = 0; i < H; ++i) {
+            if (i & hh) continue;
+            const float2 u = a[i], v = a[i + hh];
+            a[i] = make_float2(u.x + v.x, u.y + v.y);
+            a[i + hh] = cmul(make_float2(u.x - v.x, u.y - v.y), W((i & (hh - 1)) * (m / (2 * hh))));
+        }
+    }
+    // a[j] = Y_k, k = k1 + 32 (2 bitreverse4(j) + h); every lane of both warps has read its
+    // inputs (before the exchange barrier), so the row buffer takes the results
+#pragma unroll
+    for (int j = 0; j < H; ++j) {
+        const int k = k1 + 32 * (2 * (int)(__brev((unsigned)j) >> 28) + h);
+        if (MODE == T_DCT2) {
+            const float2 q = qw[pad(k)];
+            xw[pad(k)] = a[j].x * q.x + a[j].y * q.y;
+        } else {
+            const int l = k < half ? 2 * k : 2 * (m - 1 - k) + 1;
+            const float t = 0.5f * (a[j].x + c0);
+            xw[pad(l)] = (MODE == T_DST3 && (l & 1)) ? -t : t;
+        }
+    }
+    row_sync();
+    float *orow = out + (size_t)r * out_ld;
+    const int nout = MODE == T_DCT2 ? keep : m;
+    for (int i = threadIdx.x & 63; i < nout; i += 64) orow[(size_t)i * ostr] = xw[pad(i)];
 }
 
 // The same transforms for any m: direct sums over a table cos(pi q / 2m), q < 4m
@@ -591,14 +735,19 @@ cudaError_t rows(int mode, const float *in, int in_ld, int nrows, int kin, float
                                                  dif);
             return cudaGetLastError();
         };
+        auto go2 = [&](auto kfn) {
+            kfn<<<(nrows + 1) / 2, 128, 0, st>>>(in, in_ld, kin, in_scale, nrows, keep, out, out_ld, ostr, tw, qw,
+                                                 dif);
+            return cudaGetLastError();
+        };
         if (m == 512)
             e = mode == T_DCT2 ? go(fft_rows_warp_kernel<T_DCT2, 16>)
                                : (mode == T_DCT3 ? go(fft_rows_warp_kernel<T_DCT3, 16>)
                                                  : go(fft_rows_warp_kernel<T_DST3, 16>));
         else
-            e = mode == T_DCT2 ? go(fft_rows_warp_kernel<T_DCT2, 32>)
-                               : (mode == T_DCT3 ? go(fft_rows_warp_kernel<T_DCT3, 32>)
-                                                 : go(fft_rows_warp_kernel<T_DST3, 32>));
+            e = mode == T_DCT2 ? go2(fft_rows_pair_kernel<T_DCT2>)
+                               : (mode == T_DCT3 ? go2(fft_rows_pair_kernel<T_DCT3>)
+                                                 : go2(fft_rows_pair_kernel<T_DST3>));
     } else if (pow2(m)) {
         int lg = 0;
         while ((1 << lg) < m) ++lg;
