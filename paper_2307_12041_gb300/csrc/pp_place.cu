@@ -53,10 +53,32 @@ __global__ void lse_net_kernel(int n_nets, const int32_t *__restrict__ net_ptr,
         inv_gamma = 1.f / gamma;
     }
     double wl = 0.0, hp = 0.0;
+    // the first KP pins of a net are gathered together (their loads in flight at once)
+    // and kept in registers for the second pass; longer nets read the rest twice
+    constexpr int KP = 8;
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n_nets; e += gridDim.x * blockDim.x) {
-        const int p0 = net_ptr[e], p1 = net_ptr[e + 1];
+        const int p0 = net_ptr[e], p1 = net_ptr[e + 1], np = p1 - p0;
         float hx = -INFINITY, lx = INFINITY, hy = -INFINITY, ly = INFINITY;
-        for (int p = p0; p < p1; ++p) {
+        float px[KP], py[KP];
+#pragma unroll
+        for (int k = 0; k < KP; ++k) {
+            px[k] = py[k] = 0.f;
+            if (k < np) {
+                const int i = net_pin[p0 + k];
+                px[k] = x[i];
+                py[k] = y[i];
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < KP; ++k) {
+            if (k < np) {
+                hx = fmaxf(hx, px[k]);
+                lx = fminf(lx, px[k]);
+                hy = fmaxf(hy, py[k]);
+                ly = fminf(ly, py[k]);
+            }
+        }
+        for (int p = p0 + KP; p < p1; ++p) {
             const int i = net_pin[p];
             const float xi = x[i], yi = y[i];
             hx = fmaxf(hx, xi);
@@ -65,7 +87,16 @@ __global__ void lse_net_kernel(int n_nets, const int32_t *__restrict__ net_ptr,
             ly = fminf(ly, yi);
         }
         float spx = 0.f, snx = 0.f, spy = 0.f, sny = 0.f;
-        for (int p = p0; p < p1; ++p) {
+#pragma unroll
+        for (int k = 0; k < KP; ++k) {
+            if (k < np) {
+                spx += expf((px[k] - hx) * inv_gamma);
+                snx += expf((lx - px[k]) * inv_gamma);
+                spy += expf((py[k] - hy) * inv_gamma);
+                sny += expf((ly - py[k]) * inv_gamma);
+            }
+        }
+        for (int p = p0 + KP; p < p1; ++p) {
             const int i = net_pin[p];
             const float xi = x[i], yi = y[i];
             spx += expf((xi - hx) * inv_gamma);
@@ -95,10 +126,30 @@ __global__ void lse_cell_kernel(int n_cells, const int32_t *__restrict__ cell_pt
                                 const float4 *__restrict__ stats, float *__restrict__ gx,
                                 float *__restrict__ gy) {
     if (scal) inv_gamma = 1.f / scal[1];
+    // the first KC nets of a cell gathered together (their loads in flight at once)
+    constexpr int KC = 4;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_cells; i += gridDim.x * blockDim.x) {
         const float xi = x[i], yi = y[i];
+        const int k0 = cell_ptr[i], k1 = cell_ptr[i + 1];
         float ax = 0.f, ay = 0.f;
-        for (int k = cell_ptr[i]; k < cell_ptr[i + 1]; ++k) {
+        float4 sxs[KC], sys[KC];
+#pragma unroll
+        for (int q = 0; q < KC; ++q) {
+            if (k0 + q < k1) {
+                const int e = cell_net[k0 + q];
+                sxs[q] = stats[2 * e];
+                sys[q] = stats[2 * e + 1];
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < KC; ++q) {
+            if (k0 + q < k1) {
+                const float4 sx = sxs[q], sy = sys[q];
+                ax += expf((xi - sx.x) * inv_gamma) * sx.z - expf((sx.y - xi) * inv_gamma) * sx.w;
+                ay += expf((yi - sy.x) * inv_gamma) * sy.z - expf((sy.y - yi) * inv_gamma) * sy.w;
+            }
+        }
+        for (int k = k0 + KC; k < k1; ++k) {
             const int e = cell_net[k];
             const float4 sx = stats[2 * e], sy = stats[2 * e + 1];
             ax += expf((xi - sx.x) * inv_gamma) * sx.z - expf((sx.y - xi) * inv_gamma) * sx.w;
