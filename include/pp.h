@@ -385,6 +385,76 @@ typedef struct {
 size_t pp_place_workspace_size(const pp_place_iteration_args *args);
 pp_status pp_place_iteration(const pp_place_iteration_args *args, void *ws, size_t ws_bytes, void *stream);
 
+/* ---- the loop itself on the device ----
+ * pp_place_run runs iterations 1, 2, ... of the loop (the first, whose lambda_0 and
+ * step length need reductions over the whole placement, is the caller's) without
+ * returning to the host between them: one CUDA graph whose conditional WHILE node
+ * repeats { pp_place_iteration; the scalar update below } until a stop condition
+ * holds.  The scalar update is the loop's host arithmetic made in FP64 by one device
+ * thread, in this order, after iteration k:
+ *   tau      = stats[0] * bin_area / area_mov           (the overflow ratio)
+ *   record k = {k, tau, W_LSE, HPWL, E, lambda, gamma}    (the values it used)
+ *   a_k      <- (1 + sqrt(4 a_k^2 + 1)) / 2
+ *   lambda   <- lambda * clamp(1.1^(1 - (HPWL - hpwl_prev) / d_ref), 0.75, 1.1)
+ *   hpwl_prev <- HPWL;  gamma <- 8 bin_w 10^((20/9)(tau - 0.1) - 1);  k <- k + 1
+ * and the next iteration's float32 scalars {lambda, gamma, 0, (a_k - 1) / a_{k+1}}.
+ * The loop stops (state.stop, below) once tau < tau_stop, k reaches max_iters, a
+ * scalar is not finite (or lambda < 0, gamma <= 0 in float32), or the library's
+ * device status word is set (a bounded wait gave up; pp_sync_status reports it).
+ * Every body execution ends in the update, and the update stops the loop after at
+ * most max_iters executions of one launch, so the graph always ends. */
+typedef enum {
+    PP_PLACE_RUNNING = 0,
+    PP_PLACE_CONVERGED = 1,     /* tau < tau_stop */
+    PP_PLACE_MAX_ITERS = 2,     /* k reached max_iters */
+    PP_PLACE_NONFINITE = 3,     /* a scalar of the next iteration is not finite or out of range */
+    PP_PLACE_DEVICE_ERROR = 4,  /* the device status word was set */
+    PP_PLACE_BAD_STATE = 5      /* the state given to pp_place_run cannot start: k < 1, d_ref <= 0, ... */
+} pp_place_stop;
+
+typedef struct {
+    int32_t max_iters;          /* iterations in all (the last record is k = max_iters - 1); [1, 2^24] */
+    int32_t reserved;           /* 0 */
+    double tau_stop;            /* stop once the overflow ratio drops below this */
+    double bin_area;            /* area of one of the M x M bins */
+    double area_mov;            /* area of the movable blocks counted in the overflow (> 0) */
+    double bin_w;               /* bin width, the scale of gamma */
+} pp_place_schedule;
+
+/* The loop's state in device memory (80 bytes, 16-byte aligned).  The caller writes
+ * it after iteration 0; pp_place_run reads and updates it in place. */
+typedef struct {
+    double lambda, gamma;       /* used by the next iteration */
+    double a_k;                 /* Nesterov sequence before the next iteration (>= 1) */
+    double hpwl_prev;           /* HPWL of the last iteration */
+    double d_ref;               /* dHPWL_ref of the penalty update (> 0) */
+    double tau;                 /* overflow ratio after the last iteration */
+    int64_t k;                  /* index of the next iteration (>= 1) */
+    int32_t stop;               /* pp_place_stop; the run starts only from PP_PLACE_RUNNING */
+    int32_t run_count;          /* iterations made by the last pp_place_run */
+    float scalars[4];           /* {lambda, gamma, alpha0 = 0, coef} the kernels read */
+} pp_place_state;
+
+/* One iteration's record (64 bytes); stop is the state's stop code after it. */
+typedef struct {
+    int64_t k;
+    int32_t stop, reserved;
+    double tau, w_lse, hpwl, e, lambda, gamma;
+} pp_place_record;
+
+/* Runs the loop from `state` (device) on `stream` as described above; record k is
+ * written to trace[k] (device array of max_iters records; entries before the
+ * state's k are not touched).  args and ws as for pp_place_iteration; the run's
+ * own state->scalars replace args->scalars.  The graph is built, instantiated and
+ * launched here and released after it has run; the call returns once it is
+ * launched (asynchronous like the other entry points).  PP_EINVAL for a bad
+ * schedule (max_iters outside [1, 2^24], a non-finite tau_stop, bin_area,
+ * area_mov or bin_w <= 0), state or trace NULL, host or misaligned; PP_ECUDA
+ * when the graph cannot be built (for instance, library timing enabled: event
+ * records cannot sit in a conditional body); the errors of pp_place_iteration. */
+pp_status pp_place_run(const pp_place_iteration_args *args, const pp_place_schedule *sched, pp_place_state *state,
+                       pp_place_record *trace, void *ws, size_t ws_bytes, void *stream);
+
 /* Failure-path check (no counterpart in the paper).  Launches, on `stream`, one
  * kernel whose thread waits on a shared-memory mbarrier that nothing completes,
  * through the same time-bounded wait the tensor-core kernels use between their

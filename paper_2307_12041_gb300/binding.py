@@ -57,6 +57,28 @@ class PlaceIterationArgs(ctypes.Structure):
               [("stats", ctypes.c_void_p), ("scalars", ctypes.c_void_p)]
 
 
+class PlaceSchedule(ctypes.Structure):
+    """pp_place_schedule (the loop's stop rule and the constants of its scalar update)."""
+    _fields_ = [("max_iters", ctypes.c_int32), ("reserved", ctypes.c_int32), ("tau_stop", ctypes.c_double),
+                ("bin_area", ctypes.c_double), ("area_mov", ctypes.c_double), ("bin_w", ctypes.c_double)]
+
+
+class PlaceState(ctypes.Structure):
+    """pp_place_state (the loop's scalars between iterations; lives on the device)."""
+    _fields_ = [("lam", ctypes.c_double), ("gamma", ctypes.c_double), ("a_k", ctypes.c_double),
+                ("hpwl_prev", ctypes.c_double), ("d_ref", ctypes.c_double), ("tau", ctypes.c_double),
+                ("k", ctypes.c_int64), ("stop", ctypes.c_int32), ("run_count", ctypes.c_int32),
+                ("scalars", ctypes.c_float * 4)]
+
+
+class PlaceRecord(ctypes.Structure):
+    """pp_place_record (one iteration of a device-resident run)."""
+    _fields_ = [("k", ctypes.c_int64), ("stop", ctypes.c_int32), ("reserved", ctypes.c_int32)] + \
+               [(f, ctypes.c_double) for f in ("tau", "w_lse", "hpwl", "e", "lam", "gamma")]
+
+
+PLACE_STOP = {0: "running", 1: "converged", 2: "max_iters", 3: "nonfinite", 4: "device_error", 5: "bad_state"}
+
 _LIB = None
 EXPORTS = ("pp_workspace_size", "pp_coeffs", "pp_energy", "pp_grad", "pp_sync_status",
            "pp_last_error", "pp_version", "pp_timing_enable", "pp_timing_collect",
@@ -65,7 +87,7 @@ EXPORTS = ("pp_workspace_size", "pp_coeffs", "pp_energy", "pp_grad", "pp_sync_st
            "pp_wirelength_workspace_size", "pp_wirelength", "pp_place_combine", "pp_step_norms",
            "pp_nesterov_step", "pp_overflow", "pp_place_workspace_size", "pp_place_iteration",
            "pp_check_wait_timeout", "pp_grad_adjoint", "pp_coeffs_accumulate",
-           "pp_grad_host_workspace_size", "pp_grad_host")
+           "pp_grad_host_workspace_size", "pp_grad_host", "pp_place_run")
 
 
 def lib_path() -> str:
@@ -124,6 +146,8 @@ def lib() -> ctypes.CDLL:
         L.pp_place_workspace_size.restype = sz
         L.pp_place_iteration.argtypes = [PA, vp, sz, vp]
         L.pp_place_iteration.restype = i
+        L.pp_place_run.argtypes = [PA, ctypes.POINTER(PlaceSchedule), vp, vp, vp, sz, vp]
+        L.pp_place_run.restype = i
         L.pp_check_wait_timeout.argtypes = [ctypes.c_uint64, vp]
         L.pp_check_wait_timeout.restype = i
         L.pp_last_error.argtypes = []
@@ -670,6 +694,24 @@ class PlaceIteration:
         self.scal_dev.copy_(src, non_blocking=True)
         self.graph.replay()
         return self.stats
+
+    def run(self, state: PlaceState, sched: PlaceSchedule):
+        """pp_place_run: iterations state.k, state.k + 1, ... on the device until a stop
+        condition holds.  Returns (the state after the run, the records made, in order).
+        One graph launch; the host waits for it once, at the end."""
+        dev = self.ws.device
+        st_dev = torch.frombuffer(bytearray(bytes(state)), dtype=torch.uint8).to(dev)
+        k0 = int(state.k)
+        trace = torch.zeros((max(int(sched.max_iters), 1), ctypes.sizeof(PlaceRecord)), dtype=torch.uint8,
+                            device=dev)
+        _check(lib().pp_place_run(ctypes.byref(self.a), ctypes.byref(sched), _ptr(st_dev), _ptr(trace), _ptr(self.ws),
+                                  self.ws.numel(), _stream_handle(dev)))
+        out = PlaceState.from_buffer_copy(bytes(st_dev.cpu().numpy()))
+        k1 = min(int(out.k), int(sched.max_iters))
+        raw = bytes(trace[k0:k1].cpu().numpy()) if k1 > k0 else b""
+        sz = ctypes.sizeof(PlaceRecord)
+        recs = [PlaceRecord.from_buffer_copy(raw[i * sz:(i + 1) * sz]) for i in range(k1 - k0)]
+        return out, recs
 
 
 def overflow(x, y, w, h, W, H, m: int, target: float = 1.0, bins=None, out=None):

@@ -1008,6 +1008,102 @@ pp_status pp_place_iteration(const pp_place_iteration_args *a, void *ws, size_t 
     return pp_overflow(&over, a->M, a->target, bins, stats, stream);
 }
 
+namespace {
+// The graph objects of one pp_place_run, released on every path out of it.
+struct LoopGraph {
+    cudaStream_t cap = nullptr;         // capture stream (nothing runs on it)
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    bool capturing = false;
+    ~LoopGraph() {
+        if (capturing) {
+            cudaGraph_t g = nullptr;
+            cudaStreamEndCapture(cap, &g);
+            cudaGetLastError();
+        }
+        if (exec) cudaGraphExecDestroy(exec);   // freed once the launched graph has run
+        if (graph) cudaGraphDestroy(graph);
+        if (cap) cudaStreamDestroy(cap);
+    }
+};
+}  // namespace
+
+pp_status pp_place_run(const pp_place_iteration_args *a, const pp_place_schedule *sc, pp_place_state *state,
+                       pp_place_record *trace, void *ws, size_t ws_bytes, void *stream) {
+    PlaceLayout L;
+    pp_status st = place_layout(a, &L);
+    if (st != PP_OK) return st;
+    if (!sc) return fail(PP_EINVAL, "schedule is NULL");
+    if (sc->max_iters < 1 || sc->max_iters > (1 << 24))
+        return fail(PP_EINVAL, "max_iters=%d must be in [1, 2^24]", (int)sc->max_iters);
+    if (!std::isfinite(sc->tau_stop)) return fail(PP_EINVAL, "tau_stop must be finite");
+    if (!(std::isfinite(sc->bin_area) && sc->bin_area > 0 && std::isfinite(sc->area_mov) && sc->area_mov > 0 &&
+          std::isfinite(sc->bin_w) && sc->bin_w > 0))
+        return fail(PP_EINVAL, "bin_area, area_mov and bin_w must be finite and > 0");
+    if (!state || ((uintptr_t)state & 15) != 0) return fail(PP_EINVAL, "state must be 16-byte aligned device memory");
+    if (!trace || ((uintptr_t)trace & 7) != 0) return fail(PP_EINVAL, "trace must be 8-byte aligned device memory");
+    if (!a->stats) return fail(PP_EINVAL, "stats is NULL");
+    if (!ws || ws_bytes < L.total)
+        return fail(PP_ENOMEM_WS, "workspace of %zu bytes needed, %zu given", L.total, ws ? ws_bytes : (size_t)0);
+    if (((uintptr_t)ws & 255) != 0) return fail(PP_EINVAL, "workspace must be 256-byte aligned");
+    int dev, sm, ccm;
+    unsigned *status;
+    if ((st = device_info(&dev, &sm, &status, &ccm)) != PP_OK) return st;
+    if ((st = check_dev_ptr(state, dev, "state")) != PP_OK) return st;
+    if ((st = check_dev_ptr(trace, dev, "trace")) != PP_OK) return st;
+    pp_place_iteration_args it = *a;
+    it.scalars = reinterpret_cast<const float *>(reinterpret_cast<const unsigned char *>(state) +
+                                                 offsetof(pp_place_state, scalars));   // inside the state
+    it.alpha0 = 0.f;
+
+    LoopGraph G;
+    cudaError_t e = cudaStreamCreateWithFlags(&G.cap, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return cuda_fail(e, "capture stream");
+    if ((e = cudaGraphCreate(&G.graph, 0)) != cudaSuccess) return cuda_fail(e, "cudaGraphCreate");
+    cudaGraphConditionalHandle cond;
+    if ((e = cudaGraphConditionalHandleCreate(&cond, G.graph, 0, cudaGraphCondAssignDefault)) != cudaSuccess)
+        return cuda_fail(e, "conditional handle");
+    // the begin kernel: the graph's first node
+    if ((e = cudaStreamBeginCaptureToGraph(G.cap, G.graph, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal)) !=
+        cudaSuccess)
+        return cuda_fail(e, "capture (begin)");
+    G.capturing = true;
+    e = launch_place_loop_begin(state, sc->max_iters, cond, G.cap);
+    G.capturing = false;
+    cudaGraph_t got = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(G.cap, &got);
+    if (e != cudaSuccess) return cuda_fail(e, "loop begin launch");
+    if (e2 != cudaSuccess) return cuda_fail(e2, "capture (begin) end");
+    cudaGraphNode_t first;
+    size_t n_nodes = 1;
+    if ((e = cudaGraphGetNodes(G.graph, &first, &n_nodes)) != cudaSuccess || n_nodes != 1)
+        return e != cudaSuccess ? cuda_fail(e, "cudaGraphGetNodes") : fail(PP_ECUDA, "loop begin: %zu nodes", n_nodes);
+    // the WHILE node after it; its body is one iteration and the step kernel
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = cond;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t loop;
+    if ((e = cudaGraphAddNode(&loop, G.graph, &first, nullptr, 1, &cp)) != cudaSuccess)
+        return cuda_fail(e, "conditional node");
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    if ((e = cudaStreamBeginCaptureToGraph(G.cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal)) !=
+        cudaSuccess)
+        return cuda_fail(e, "capture (body)");
+    G.capturing = true;
+    st = pp_place_iteration(&it, ws, ws_bytes, G.cap);
+    if (st != PP_OK) return st;                 // ~LoopGraph ends the capture
+    e = launch_place_loop_step(a->stats, state, trace, *sc, status, cond, G.cap);
+    G.capturing = false;
+    e2 = cudaStreamEndCapture(G.cap, &got);
+    if (e != cudaSuccess) return cuda_fail(e, "loop step launch");
+    if (e2 != cudaSuccess) return cuda_fail(e2, "capture (body) end");
+    if ((e = cudaGraphInstantiate(&G.exec, G.graph, 0)) != cudaSuccess) return cuda_fail(e, "graph instantiate");
+    if ((e = cudaGraphLaunch(G.exec, (cudaStream_t)stream)) != cudaSuccess) return cuda_fail(e, "graph launch");
+    return PP_OK;
+}
+
 pp_status pp_check_wait_timeout(uint64_t limit_ns, void *stream) {
     int dev, sm, ccm;
     unsigned *status;

@@ -14,6 +14,8 @@
 //   nesterov_kernel     u' = clamp(v - alpha g), v' = clamp(u' + coef (u' - u)),
 //                       alpha = |v - v_prev| / |g - g_prev| read on the device
 //   overflow_kernel     sum_b max(P_b - rho_t, 0) of a bin density P
+//   place_loop_*_kernel the loop's scalar update between iterations (one thread, FP64)
+//                       when the loop runs on the device (pp_place_run)
 //
 // The loop's scalars (lambda, gamma, alpha0, coef) come either as kernel arguments or,
 // when `scal` is non-NULL, from device memory {lambda, gamma, alpha0, coef} read when
@@ -240,6 +242,93 @@ __global__ void overflow_kernel(int64_t cells, const float *__restrict__ P, floa
     block_add(s, out);
 }
 
+// ---- the loop's scalar update on the device (pp_place_run) ----
+
+// The scalar update rounds every operation on its own (no contraction into FMAs),
+// in the order the host loop evaluates it, so that both make the same roundings
+// (pow aside).
+__device__ __forceinline__ double a_next_of(double a) {
+    return __dadd_rn(1.0, sqrt(__dadd_rn(__dmul_rn(__dmul_rn(4.0, a), a), 1.0))) / 2.0;
+}
+
+// ePlace's smoothing schedule gamma(tau) = 8 w_b 10^{(20/9)(tau - 0.1) - 1}
+__device__ double gamma_of_tau(double tau, double bin_w) {
+    const double ex = __dsub_rn(__dmul_rn(20.0 / 9.0, __dsub_rn(tau, 0.1)), 1.0);
+    return __dmul_rn(__dmul_rn(8.0, bin_w), pow(10.0, ex));
+}
+
+// The next iteration's float32 scalars {lambda, gamma, alpha0 = 0, coef} from the
+// state, coef = (a_k - 1) / a_{k+1}; the stop code when one is out of range.
+__device__ int32_t next_scalars(pp_place_state *st) {
+    const double a = st->a_k;
+    const double a_next = a_next_of(a);
+    const float lam = (float)st->lambda, gam = (float)st->gamma, coef = (float)((a - 1.0) / a_next);
+    if (!(isfinite(lam) && lam >= 0.f && isfinite(gam) && gam > 0.f && isfinite(coef) && isfinite(a) && a >= 1.0))
+        return PP_PLACE_NONFINITE;
+    st->scalars[0] = lam;
+    st->scalars[1] = gam;
+    st->scalars[2] = 0.f;
+    st->scalars[3] = coef;
+    return PP_PLACE_RUNNING;
+}
+
+// Before the loop: check that the state can start and set the first scalars; the
+// WHILE node's condition is 1 only if it can.
+__global__ void place_loop_begin_kernel(pp_place_state *st, int32_t max_iters, cudaGraphConditionalHandle cond) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    st->run_count = 0;
+    int32_t stop = st->stop;
+    if (stop == PP_PLACE_RUNNING) {
+        if (st->k >= max_iters)
+            stop = PP_PLACE_MAX_ITERS;
+        else if (!(st->k >= 1 && st->d_ref > 0.0 && isfinite(st->d_ref) && isfinite(st->hpwl_prev)))
+            stop = PP_PLACE_BAD_STATE;
+        else
+            stop = next_scalars(st);
+    }
+    st->stop = stop;
+    cudaGraphSetConditional(cond, stop == PP_PLACE_RUNNING ? 1u : 0u);
+}
+
+// After iteration k: its record, the penalty and smoothing updates, the stop test and
+// the next scalars; the WHILE node's condition for the next body execution.
+__global__ void place_loop_step_kernel(const double *__restrict__ stats, pp_place_state *st,
+                                       pp_place_record *trace, pp_place_schedule sc,
+                                       const unsigned *__restrict__ status, cudaGraphConditionalHandle cond) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const int64_t k = st->k;
+    pp_place_record r;
+    r.k = k;
+    r.reserved = 0;
+    r.tau = __dmul_rn(stats[0], sc.bin_area) / sc.area_mov;
+    r.w_lse = stats[1];
+    r.hpwl = stats[2];
+    r.e = stats[3];
+    r.lambda = st->lambda;
+    r.gamma = st->gamma;
+    st->a_k = a_next_of(st->a_k);
+    const double mu = pow(1.1, 1.0 - (r.hpwl - st->hpwl_prev) / st->d_ref);
+    st->lambda = __dmul_rn(st->lambda, fmin(1.1, fmax(0.75, mu)));
+    st->hpwl_prev = r.hpwl;
+    st->tau = r.tau;
+    st->gamma = gamma_of_tau(r.tau, sc.bin_w);
+    st->k = k + 1;
+    const int32_t runs = ++st->run_count;
+    int32_t stop = PP_PLACE_RUNNING;
+    if (r.tau < sc.tau_stop)
+        stop = PP_PLACE_CONVERGED;
+    else if (k + 1 >= sc.max_iters || runs >= sc.max_iters)
+        stop = PP_PLACE_MAX_ITERS;
+    else if (*status != 0u)
+        stop = PP_PLACE_DEVICE_ERROR;
+    else
+        stop = next_scalars(st);
+    st->stop = stop;
+    r.stop = stop;
+    if (k >= 0 && k < sc.max_iters) trace[k] = r;
+    cudaGraphSetConditional(cond, stop == PP_PLACE_RUNNING ? 1u : 0u);
+}
+
 int grid_for(int64_t n, int cap) {
     int64_t b = (n + 255) / 256;
     if (b < 1) b = 1;
@@ -299,6 +388,19 @@ cudaError_t launch_overflow(int m, const float *P, float target, double *out, in
     if (e != cudaSuccess) return e;
     const int64_t cells = (int64_t)m * m;
     overflow_kernel<<<grid_for(cells, 2 * sm_count), 256, 0, st>>>(cells, P, target, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_place_loop_begin(pp_place_state *st, int32_t max_iters, cudaGraphConditionalHandle cond,
+                                    cudaStream_t s) {
+    place_loop_begin_kernel<<<1, 32, 0, s>>>(st, max_iters, cond);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_place_loop_step(const double *stats, pp_place_state *st, pp_place_record *trace,
+                                   const pp_place_schedule &sc, const unsigned *status,
+                                   cudaGraphConditionalHandle cond, cudaStream_t s) {
+    place_loop_step_kernel<<<1, 32, 0, s>>>(stats, st, trace, sc, status, cond);
     return cudaGetLastError();
 }
 

@@ -5,6 +5,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "pp.h"
+
 namespace pp {
 
 // pp_place.cu: the placement loop's kernels (log-sum-exp wirelength, gradient
@@ -26,5 +28,13 @@ cudaError_t launch_step_norms(int64_t n, const float *vx, const float *vy, const
                               const float *gx, const float *gy, const float *gpx, const float *gpy,
                               double *norms, int sm_count, cudaStream_t st);
 cudaError_t launch_overflow(int m, const float *P, float target, double *out, int sm_count, cudaStream_t st);
+// the loop's scalar update when the loop runs on the device (pp_place_run): the begin
+// kernel sets the first scalars and the WHILE condition, the step kernel runs after
+// each iteration (record, updates, stop test, next scalars, condition)
+cudaError_t launch_place_loop_begin(pp_place_state *st, int32_t max_iters, cudaGraphConditionalHandle cond,
+                                    cudaStream_t s);
+cudaError_t launch_place_loop_step(const double *stats, pp_place_state *st, pp_place_record *trace,
+                                   const pp_place_schedule &sc, const unsigned *status,
+                                   cudaGraphConditionalHandle cond, cudaStream_t s);
 
 }  // namespace pp

@@ -25,9 +25,12 @@ the readings used here (each a parameter of `place`):
   started uniformly over the die; they take part in the density term only (not in
   the wirelength, nor in the overflow, which measures the given blocks).
 
-Every per-iteration step runs in the library's kernels through the C ABI; the host
-keeps the scalars (lambda, gamma, a_k) and reads one small vector back per
-iteration (overflow, W_LSE, HPWL, E).
+Every per-iteration step runs in the library's kernels through the C ABI.  In the
+host loop the host keeps the scalars (lambda, gamma, a_k) and reads one small vector
+back per iteration (overflow, W_LSE, HPWL, E); in the device loop (the default after
+the first iteration when no callback is given) the library makes the same scalar
+updates on the device between iterations (pp_place_run, one CUDA graph with a
+conditional WHILE node) and the host reads the records once, at the end.
 """
 from __future__ import annotations
 
@@ -50,6 +53,9 @@ class PlaceResult:
     ms_per_iter: float = 0.0
     graph: bool = False                 # iterations after the first replayed a CUDA graph
     graph_error: Optional[str] = None   # why the capture failed, if it did
+    device_loop: bool = False           # iterations after the first ran as one device-resident loop
+    device_loop_error: Optional[str] = None   # why pp_place_run was refused, if it was
+    stop: Optional[str] = None          # the device loop's stop code (converged, max_iters, ...)
 
 
 def gamma_of(tau: float, bin_w: float) -> float:
@@ -98,6 +104,7 @@ class Placer:
         self.gamma = gamma_of(self.tau, self.bin_w)
         self.lam, self.a_k, self.hp_prev, self.d_ref, self.k = None, 1.0, None, None, 0
         self.fused, self.use_graph, self._it = fused, graph, None
+        self.stop = None
 
     def overflow_now(self):
         nr = self.n_real
@@ -160,6 +167,23 @@ class Placer:
         self.k += 1
         return rec
 
+    def run_device(self, iters: int, tau_stop: float) -> List[dict]:
+        """Iterations k, k + 1, ... (k >= 1: the first step is the host's) on the device
+        through pp_place_run, until tau < tau_stop or k = iters; the records in the
+        format of step(), and the state (lambda, gamma, a_k, ...) taken back."""
+        if self.k < 1 or self.lam is None or self.d_ref is None:
+            raise RuntimeError("run_device continues a started loop: make the first step with step()")
+        st = binding.PlaceState(lam=self.lam, gamma=self.gamma, a_k=self.a_k, hpwl_prev=self.hp_prev,
+                                d_ref=self.d_ref, tau=self.tau, k=self.k, stop=0, run_count=0)
+        sc = binding.PlaceSchedule(max_iters=int(iters), reserved=0, tau_stop=float(tau_stop),
+                                   bin_area=self.bin_area, area_mov=self.area_mov, bin_w=self.bin_w)
+        out, recs = self._fused().run(st, sc)
+        self.lam, self.gamma, self.a_k, self.hp_prev = out.lam, out.gamma, out.a_k, out.hpwl_prev
+        self.tau, self.k = out.tau, int(out.k)
+        self.stop = binding.PLACE_STOP.get(int(out.stop), str(out.stop))
+        return [{"k": int(r.k), "tau": r.tau, "W_lse": r.w_lse, "hpwl": r.hpwl, "E": r.e, "lambda": r.lam,
+                 "gamma": r.gamma} for r in recs]
+
 
 def with_fillers(p: synth.Placement, target: float, seed: int) -> synth.Placement:
     """p followed by filler cells (see the module notes): movable, no charge factor."""
@@ -185,16 +209,30 @@ def with_fillers(p: synth.Placement, target: float, seed: int) -> synth.Placemen
 def place(p: synth.Placement, net_ptr, net_pin, iters: int = 200, prec: str = "tf32",
           tau_stop: float = 0.1, target: float = 1.0, d_hpwl_frac: float = 3.5e-3,
           device="cuda", callback: Optional[Callable] = None, density: str = "exact",
-          fillers: bool = False, fused: bool = True, graph: bool = True) -> PlaceResult:
+          fillers: bool = False, fused: bool = True, graph: bool = True,
+          device_loop: bool = True) -> PlaceResult:
     """Run up to `iters` iterations; callback(k, rec, x_eval, y_eval, ux, uy) after
-    each, with the positions at which W_LSE and E of `rec` were evaluated."""
+    each, with the positions at which W_LSE and E of `rec` were evaluated.  With
+    device_loop (and fused, and no callback) every iteration after the first runs in
+    one pp_place_run call; if the library refuses it (res.device_loop_error says
+    why) the host loop carries on from the same state."""
     pl = Placer(p, net_ptr, net_pin, prec, target, d_hpwl_frac, device, density, fillers, fused=fused,
                 graph=graph)
     res = PlaceResult()
     dev = torch.device(device)
+    use_dev = device_loop and fused and callback is None
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
-    for _ in range(iters):
+    while pl.k < iters:
+        if use_dev and pl.k >= 1:
+            try:
+                recs = pl.run_device(iters, tau_stop)
+            except binding.PPError as e:  # nothing ran: continue on the host
+                res.device_loop_error, use_dev = str(e), False
+                continue
+            res.trace.extend(recs)
+            res.device_loop, res.stop, res.iterations = True, pl.stop, pl.k
+            break
         rec = pl.step()
         res.trace.append(rec)
         if callback is not None:          # vpx, vpy: the positions this iteration evaluated
@@ -227,10 +265,13 @@ def _main(argv=None) -> int:
     ap.add_argument("--fillers", action="store_true")
     ap.add_argument("--unfused", action="store_true", help="one entry point per step of an iteration")
     ap.add_argument("--no-graph", action="store_true", help="issue the fused call each iteration")
+    ap.add_argument("--host-loop", action="store_true",
+                    help="update the scalars on the host after each iteration instead of on the device")
     a = ap.parse_args(argv)
     p = synth.placement_cells(a.n, a.modes, a.seed)
     ptr, pins = synth.netlist(a.n, a.seed + 1)
-    kw = dict(prec=a.prec, density=a.density, fillers=a.fillers, fused=not a.unfused, graph=not a.no_graph)
+    kw = dict(prec=a.prec, density=a.density, fillers=a.fillers, fused=not a.unfused, graph=not a.no_graph,
+              device_loop=not a.host_loop)
     place(p, ptr, pins, iters=3, **kw)      # warm-up
     r = place(p, ptr, pins, iters=a.iters, **kw)
     t = r.trace
@@ -238,7 +279,8 @@ def _main(argv=None) -> int:
     print(json.dumps({
         "workload": p.name, "n": p.n, "nets": len(ptr) - 1, "pins": int(len(pins)), "modes": a.modes,
         "precision": a.prec, "density": a.density, "fillers": a.fillers, "fused": not a.unfused,
-        "graph": r.graph, "graph_error": r.graph_error,
+        "graph": r.graph, "graph_error": r.graph_error, "device_loop": r.device_loop,
+        "device_loop_error": r.device_loop_error, "stop": r.stop,
         "iterations": r.iterations,
         "ms_per_iter": r.ms_per_iter,
         "density_terms_per_s": p.n * a.modes * a.modes / (r.ms_per_iter / 1e3),

@@ -103,20 +103,50 @@ def test_place_workspace_size_host_only(L):
     assert L.pp_place_workspace_size(None) == 0
 
 
+def test_place_run_rejects_bad_schedules_on_the_host(L):
+    """pp_place_run checks its schedule and pointers before any CUDA call: these
+    refusals need no GPU."""
+    from paper_2307_12041_gb300.binding import Netlist, PlaceIterationArgs, PlaceSchedule
+    nl = Netlist(1000, 300, None, None, None, None)
+    a = PlaceIterationArgs(ctypes.pointer(nl), 1.0, 1.0, 64, 1, 0, 0, 1000)
+    a.stats = 1 << 20
+    good = dict(max_iters=100, tau_stop=0.1, bin_area=1.0 / 4096, area_mov=0.5, bin_w=1.0 / 64)
+    fake = 1 << 20                                  # 16-byte aligned; refused before it is used
+
+    def run(sched, state=fake, trace=fake):
+        return L.pp_place_run(ctypes.byref(a), sched, state, trace, fake, 1 << 40, None)
+
+    assert run(None) == 1
+    for bad in (dict(max_iters=0), dict(max_iters=(1 << 24) + 1), dict(tau_stop=float("nan")),
+                dict(bin_area=0.0), dict(area_mov=-1.0), dict(bin_w=float("inf"))):
+        sc = PlaceSchedule(**dict(good, **bad))
+        assert run(ctypes.byref(sc)) == 1, bad
+        assert L.pp_last_error().decode() != ""
+    sc = PlaceSchedule(**good)
+    assert run(ctypes.byref(sc), state=None) == 1
+    assert run(ctypes.byref(sc), state=fake + 8) == 1           # state must be 16-byte aligned
+    assert run(ctypes.byref(sc), trace=None) == 1
+    assert run(ctypes.byref(sc), trace=fake + 4) == 1           # trace must be 8-byte aligned
+    assert L.pp_place_run(ctypes.byref(a), ctypes.byref(sc), fake, fake, fake, 256, None) == 2   # workspace
+
+
 def test_struct_layouts_match_the_header(tmp_path):
-    """The binding's ctypes mirrors of pp_problem, pp_netlist and
-    pp_place_iteration_args have the header's size and field offsets (a C program
-    compiled against include/pp.h prints them)."""
+    """The binding's ctypes mirrors of pp_problem, pp_netlist, pp_place_iteration_args
+    and the device loop's schedule, state and record have the header's size and field
+    offsets (a C program compiled against include/pp.h prints them)."""
     import json
     import shutil
     import subprocess
-    from paper_2307_12041_gb300.binding import Netlist, PlaceIterationArgs, Problem
+    from paper_2307_12041_gb300.binding import (Netlist, PlaceIterationArgs, PlaceRecord, PlaceSchedule, PlaceState,
+                                                Problem)
     cc = shutil.which("gcc") or shutil.which("cc")
     if cc is None:
         pytest.skip("no C compiler")
-    mirrors = {"pp_problem": Problem, "pp_netlist": Netlist, "pp_place_iteration_args": PlaceIterationArgs}
+    mirrors = {"pp_problem": Problem, "pp_netlist": Netlist, "pp_place_iteration_args": PlaceIterationArgs,
+               "pp_place_schedule": PlaceSchedule, "pp_place_state": PlaceState, "pp_place_record": PlaceRecord}
     # the C names of the fields the binding renames
-    c_name = {("pp_place_iteration_args", "lam"): "lambda"}
+    c_name = {("pp_place_iteration_args", "lam"): "lambda", ("pp_place_state", "lam"): "lambda",
+              ("pp_place_record", "lam"): "lambda"}
     lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "pp.h"', 'int main(void) {', 'printf("{");']
     first = True
     for sname, cls in mirrors.items():

@@ -270,3 +270,129 @@ def test_fused_iteration_rejects_bad_arguments(pp):
     with pytest.raises(b.PPError):                       # the same check in the library call
         eager._fused()(eager.lam, 0.0, 0.1)
     b.sync_status()
+
+
+@pytest.mark.parametrize("density", ["exact", "binned"])
+def test_device_loop_updates_match_the_host_loop(pp, density):
+    """pp_place_run's scalar update (record, penalty and smoothing updates, Nesterov
+    sequence) is the host loop's: one device iteration at a time (max_iters = k + 1)
+    from the host placer's state, compared with the host placer's own step."""
+    n, M = 8000, 64
+    p = synth.placement_cells(n, M, 61)
+    ptr, pins = synth.netlist(n, 62)
+    A = place.Placer(p, ptr, pins, "fp32", density=density)
+    B = place.Placer(p, ptr, pins, "fp32", density=density, fused=False)
+    A.step(), B.step()
+    for k in range(1, 7):
+        for name in STATE:
+            getattr(A, name).copy_(getattr(B, name))
+        A.lam, A.gamma, A.a_k, A.hp_prev, A.d_ref, A.tau = B.lam, B.gamma, B.a_k, B.hp_prev, B.d_ref, B.tau
+        recs = A.run_device(k + 1, tau_stop=-1.0)
+        rb = B.step()
+        assert len(recs) == 1 and recs[0]["k"] == k == rb["k"], (k, recs)
+        assert A.stop == "max_iters" and A.k == B.k == k + 1
+        ra = recs[0]
+        for key in ("lambda", "gamma"):                  # the values the iteration used
+            assert ra[key] == rb[key], (k, key, ra[key], rb[key])
+        for key in ("tau", "W_lse", "hpwl", "E"):
+            assert ra[key] == pytest.approx(rb[key], rel=1e-6, abs=1e-12), (k, key, ra[key], rb[key])
+        for name in ("lam", "gamma", "hp_prev", "tau"):  # the updated scalars
+            assert getattr(A, name) == pytest.approx(getattr(B, name), rel=1e-5), (k, name)
+        assert A.a_k == B.a_k                            # sqrt is correctly rounded on both sides
+        for name in ("ux", "uy", "vx", "vy"):
+            d = (getattr(A, name) - getattr(B, name)).abs().max().item()
+            assert d <= 1e-6, (k, name, d)
+
+
+@pytest.mark.parametrize("density", ["exact", "binned"])
+def test_device_loop_runs_to_the_overflow_stop(pp, density):
+    """The whole loop after the first iteration in one pp_place_run: it stops at the
+    first iteration whose overflow is below tau_stop, with the trajectory of the host
+    loop (iteration counts within two of each other, the same final HPWL to 2%)."""
+    n, M = 8000, 64
+    p = synth.placement_cells(n, M, 81)
+    ptr, pins = synth.netlist(n, 82)
+    rd = place.place(p, ptr, pins, iters=400, prec="fp32", tau_stop=0.12, density=density)
+    rh = place.place(p, ptr, pins, iters=400, prec="fp32", tau_stop=0.12, density=density, device_loop=False)
+    assert rd.device_loop and not rh.device_loop, rd.device_loop_error
+    assert rd.stop == "converged"
+    assert [r["k"] for r in rd.trace] == list(range(rd.iterations))
+    assert rd.trace[-1]["tau"] < 0.12 <= min(r["tau"] for r in rd.trace[:-1])
+    assert abs(rd.iterations - rh.iterations) <= 2, (rd.iterations, rh.iterations)
+    assert rd.trace[-1]["hpwl"] == pytest.approx(rh.trace[-1]["hpwl"], rel=2e-2)
+    for a, b in zip(rd.trace[:5], rh.trace[:5]):         # the start of the trajectory agrees closely
+        assert a["hpwl"] == pytest.approx(b["hpwl"], rel=1e-4), (a, b)
+    # the iteration cap: exactly `iters` records, the last one k = iters - 1
+    rc = place.place(p, ptr, pins, iters=9, prec="fp32", tau_stop=0.0, density=density)
+    assert rc.device_loop and rc.stop == "max_iters" and rc.iterations == 9
+    assert [r["k"] for r in rc.trace] == list(range(9))
+
+
+def test_device_loop_stop_codes_and_rejections(pp):
+    n, M = 2000, 32
+    p = synth.placement_cells(n, M, 91)
+    ptr, pins = synth.netlist(n, 92)
+    b = pp.binding
+    pl = place.Placer(p, ptr, pins, "fp32", density="binned")
+    pl.step()
+    it = pl._fused()
+
+    def run(**kw):
+        st = b.PlaceState(lam=pl.lam, gamma=pl.gamma, a_k=pl.a_k, hpwl_prev=pl.hp_prev, d_ref=pl.d_ref,
+                          tau=pl.tau, k=pl.k, stop=0, run_count=0)
+        sc = b.PlaceSchedule(max_iters=50, reserved=0, tau_stop=0.0, bin_area=pl.bin_area, area_mov=pl.area_mov,
+                             bin_w=pl.bin_w)
+        for key, v in kw.items():
+            setattr(st if hasattr(st, key) else sc, key, v)
+        return it.run(st, sc)
+
+    ux = pl.ux.clone()
+    for bad_state, code in ((dict(k=0), 5), (dict(d_ref=0.0), 5), (dict(lam=float("nan")), 3),
+                            (dict(gamma=1e-60), 3), (dict(stop=1), 1), (dict(k=50), 2)):
+        out, recs = run(**bad_state)                     # refused on the device: no iteration runs
+        assert out.stop == code and out.run_count == 0 and recs == [], (bad_state, out.stop)
+    assert torch.equal(pl.ux, ux)
+    for bad in (dict(max_iters=0), dict(max_iters=(1 << 24) + 1), dict(bin_area=0.0), dict(area_mov=-1.0),
+                dict(bin_w=float("inf")), dict(tau_stop=float("nan"))):
+        with pytest.raises(b.PPError):                   # refused on the host
+            run(**bad)
+    st = b.PlaceState(lam=pl.lam, gamma=pl.gamma, a_k=pl.a_k, hpwl_prev=pl.hp_prev, d_ref=pl.d_ref, tau=pl.tau,
+                      k=pl.k)
+    sc = b.PlaceSchedule(max_iters=5, tau_stop=0.0, bin_area=pl.bin_area, area_mov=pl.area_mov, bin_w=pl.bin_w)
+    trace = torch.zeros((5, 64), dtype=torch.uint8, device="cuda")
+    sdev = torch.zeros(96, dtype=torch.uint8, device="cuda")
+    L = b.lib()
+    with pytest.raises(b.PPError):                       # state must be 16-byte aligned device memory
+        b._check(L.pp_place_run(b.ctypes.byref(it.a), b.ctypes.byref(sc), sdev.data_ptr() + 8, trace.data_ptr(),
+                                it.ws.data_ptr(), it.ws.numel(), None))
+    with pytest.raises(b.PPError):                       # host memory
+        b._check(L.pp_place_run(b.ctypes.byref(it.a), b.ctypes.byref(sc), b.ctypes.addressof(st), trace.data_ptr(),
+                                it.ws.data_ptr(), it.ws.numel(), None))
+    with pytest.raises(b.PPError):                       # trace NULL
+        b._check(L.pp_place_run(b.ctypes.byref(it.a), b.ctypes.byref(sc), sdev.data_ptr(), None,
+                                it.ws.data_ptr(), it.ws.numel(), None))
+    with pytest.raises(b.PPError):                       # workspace too small
+        b._check(L.pp_place_run(b.ctypes.byref(it.a), b.ctypes.byref(sc), sdev.data_ptr(), trace.data_ptr(),
+                                it.ws.data_ptr(), it.ws.numel() - 256, None))
+    torch.cuda.synchronize()
+    b.sync_status()
+
+
+def test_device_loop_stops_on_the_device_status_word(pp):
+    """A bounded wait that ran out (the library's failure-path probe) leaves the status
+    word set; the device loop makes the iteration in flight, then stops with
+    device_error instead of carrying on, and pp_sync_status reports the timeout."""
+    n, M = 2000, 32
+    p = synth.placement_cells(n, M, 93)
+    ptr, pins = synth.netlist(n, 94)
+    pp.binding.sync_status()
+    pl = place.Placer(p, ptr, pins, "fp32", density="binned")
+    pl.step()
+    pp.binding.check_wait_timeout(1_000_000)
+    recs = pl.run_device(100, tau_stop=0.0)
+    assert pl.stop == "device_error" and len(recs) == 1 and recs[0]["k"] == 1, (pl.stop, len(recs))
+    with pytest.raises(pp.binding.PPError) as err:
+        pp.binding.sync_status()
+    assert err.value.status == 4
+    recs = pl.run_device(5, tau_stop=0.0)                # cleared: the loop runs on
+    assert pl.stop == "max_iters" and [r["k"] for r in recs] == [2, 3, 4]
