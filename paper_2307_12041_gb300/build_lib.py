@@ -18,7 +18,7 @@ ROOT = os.path.dirname(HERE)
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libpp.so")
 SOURCES = ["pp_api.cu", "pp_simt.cu", "pp_static.cu", "pp_tc.cu", "pp_binned.cu", "pp_place.cu"]
-HEADERS = ["pp_device.cuh", "pp_internal.h", "pp_place.h", "pp_tc.cuh", "pp_gen.cuh"]
+HEADERS = ["pp_device.cuh", "pp_internal.h", "pp_place.h", "pp_tc.cuh", "pp_gen.cuh", "pp_sum.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ARCH + ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC",
                 "-I" + os.path.join(ROOT, "include")]

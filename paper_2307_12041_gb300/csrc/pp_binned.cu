@@ -23,6 +23,7 @@
 #include <cmath>
 
 #include "pp_internal.h"
+#include "pp_sum.cuh"
 
 namespace pp {
 namespace {
@@ -188,22 +189,35 @@ __global__ void __launch_bounds__(256) row_prefix_add_kernel(const float *__rest
 
 // a = prefactor o a' (Eq. disa-a..d), FP32; a' arrives transposed (apt[p][u], row
 // stride Mx), a leaves u-major (a[u][p]).
+// a[u][p] = f(u, p) a'[p][u] (a' = R2 is [My][Mx]): a transpose through a padded
+// 32 x 32 shared tile (reads and writes both coalesced) with the prefactor applied on
+// the way out; the sines of the tile's 32 u and 32 p are formed once per tile.
 __global__ void scale_kernel(int Mx, int My, int m, float W, float H, const float *__restrict__ apt,
                              float *__restrict__ a) {
+    __shared__ float t[32][33];
+    __shared__ float s_u[32], s_p[32];
     const float PI = 3.14159265358979f;
     const float inv_pi3 = 1.f / (PI * PI * PI), inv_pi4 = inv_pi3 / PI;
-    const long long total = (long long)Mx * My;
-    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < total;
-         k += (long long)gridDim.x * blockDim.x) {
-        const int u = (int)(k / My), p = (int)(k % My);
+    const int u0 = blockIdx.x * 32, p0 = blockIdx.y * 32;
+    const int tid = threadIdx.y * 32 + threadIdx.x;
+    if (tid < 32) s_u[tid] = sinpif((float)(u0 + tid) / (2.f * m));
+    else if (tid < 64) s_p[tid - 32] = sinpif((float)(p0 + tid - 32) / (2.f * m));
+    for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+        const int p = p0 + k, u = u0 + threadIdx.x;
+        if (p < My && u < Mx) t[k][threadIdx.x] = apt[(size_t)p * Mx + u];
+    }
+    __syncthreads();
+    for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+        const int u = u0 + k, p = p0 + threadIdx.x;
+        if (u >= Mx || p >= My) continue;
         const float fu = (float)u, fp = (float)p;
-        const float su = sinpif(fu / (2.f * m)), sp = sinpif(fp / (2.f * m));
+        const float su = s_u[k], sp = s_p[threadIdx.x];
         float f = 0.f;
         if (u == 0 && p > 0) f = 4.f * H * H * inv_pi3 / (fp * fp * fp * (float)m) * sp;
         else if (p == 0 && u > 0) f = 4.f * W * W * inv_pi3 / (fu * fu * fu * (float)m) * su;
         else if (u > 0 && p > 0)
             f = 16.f * (W * W) * (H * H) * inv_pi4 / (fu * fp * (fu * fu * H * H + fp * fp * W * W)) * su * sp;
-        a[k] = f * apt[(size_t)p * Mx + u];
+        a[(size_t)u * My + p] = f * t[threadIdx.x][k];
     }
 }
 
@@ -654,7 +668,7 @@ __global__ void interp_kernel(const float *__restrict__ x, const float *__restri
                               const float *__restrict__ c, int n, int m, float inv_wb, float inv_hb,
                               const float4 *__restrict__ V, float *__restrict__ e_block,
                               float *__restrict__ gx, float *__restrict__ gy, double *__restrict__ e_total) {
-    double e = 0.0;
+    Sum2 e;                            // sum of N_i (compensated); E = half of it
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const float fx = fminf(fmaxf(x[i] * inv_wb - 0.5f, 0.f), (float)(m - 1));
         const float fy = fminf(fmaxf(y[i] * inv_hb - 0.5f, 0.f), (float)(m - 1));
@@ -672,13 +686,9 @@ __global__ void interp_kernel(const float *__restrict__ x, const float *__restri
         if (e_block) e_block[i] = Ni;
         if (gx) gx[i] = -q * xix;
         if (gy) gy[i] = -q * xiy;
-        e += 0.5 * (double)Ni;
+        add2(e, Ni);
     }
-    if (e_total) {
-#pragma unroll
-        for (int off = 16; off >= 1; off >>= 1) e += __shfl_xor_sync(0xffffffffu, e, off);
-        if ((threadIdx.x & 31) == 0) atomicAdd(e_total, e);
-    }
+    if (e_total) block_add2(e, e_total, 0.5);      // one atomic per CTA
 }
 
 }  // namespace
@@ -823,7 +833,8 @@ cudaError_t run_binned(const Launch &Lc, int dev, int m, bool tf32, unsigned cha
     PP_STEP(rows(T_DCT2, P, m, m, m, 0.f, m, My, R1, My, 1, tw, qw, st, n > 0 ? D : nullptr));
     PP_STEP(transpose(R1, My, m, My, R1t, m, st));
     PP_STEP(rows(T_DCT2, R1t, m, My, m, 0.f, m, Mx, R2, Mx, 1, tw, qw, st));
-    scale_kernel<<<grid, 256, 0, st>>>(Mx, My, m, (float)Lc.W, (float)Lc.H, R2, a);
+    scale_kernel<<<dim3((Mx + 31) / 32, (My + 31) / 32), dim3(32, 8), 0, st>>>(Mx, My, m, (float)Lc.W, (float)Lc.H,
+                                                                             R2, a);
     PP_STEP(cudaGetLastError());
     // along v (rows u of a): U = a Cy (psi, xi_x), Up = (a o l) Sy (xi_y)
     PP_STEP(rows(T_DCT3, a, My, Mx, My, 0.f, m, m, U, m, 1, tw, qw, st));

@@ -25,24 +25,10 @@
 
 #include "pp_internal.h"
 #include "pp_place.h"
+#include "pp_sum.cuh"
 
 namespace pp {
 namespace {
-
-// Sum of one double per thread over the CTA, added to *dst (one atomic per CTA).
-__device__ __forceinline__ void block_add(double v, double *dst) {
-    __shared__ double part[32];
-#pragma unroll
-    for (int off = 16; off >= 1; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = v;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double t = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += part[w];
-        atomicAdd(dst, t);
-    }
-    __syncthreads();
-}
 
 // stats[e] = {max x, min x, 1 / sum exp((x - max)/g), 1 / sum exp((min - x)/g), same for y}
 __global__ void lse_net_kernel(int n_nets, const int32_t *__restrict__ net_ptr,
@@ -54,10 +40,11 @@ __global__ void lse_net_kernel(int n_nets, const int32_t *__restrict__ net_ptr,
         gamma = scal[1];
         inv_gamma = 1.f / gamma;
     }
-    double wl = 0.0, hp = 0.0;
+    Sum2 wl, hp;
     // the first KP pins of a net are gathered together (their loads in flight at once)
-    // and kept in registers for the second pass; longer nets read the rest twice
-    constexpr int KP = 8;
+    // and kept in registers for the second pass; longer nets gather the rest KT at a
+    // time, in both passes
+    constexpr int KP = 8, KT = 4;
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n_nets; e += gridDim.x * blockDim.x) {
         const int p0 = net_ptr[e], p1 = net_ptr[e + 1], np = p1 - p0;
         float hx = -INFINITY, lx = INFINITY, hy = -INFINITY, ly = INFINITY;
@@ -80,13 +67,25 @@ __global__ void lse_net_kernel(int n_nets, const int32_t *__restrict__ net_ptr,
                 ly = fminf(ly, py[k]);
             }
         }
-        for (int p = p0 + KP; p < p1; ++p) {
-            const int i = net_pin[p];
-            const float xi = x[i], yi = y[i];
-            hx = fmaxf(hx, xi);
-            lx = fminf(lx, xi);
-            hy = fmaxf(hy, yi);
-            ly = fminf(ly, yi);
+        for (int b = p0 + KP; b < p1; b += KT) {
+            float tx[KT], ty[KT];
+#pragma unroll
+            for (int k = 0; k < KT; ++k) {
+                if (b + k < p1) {
+                    const int i = net_pin[b + k];
+                    tx[k] = x[i];
+                    ty[k] = y[i];
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < KT; ++k) {
+                if (b + k < p1) {
+                    hx = fmaxf(hx, tx[k]);
+                    lx = fminf(lx, tx[k]);
+                    hy = fmaxf(hy, ty[k]);
+                    ly = fminf(ly, ty[k]);
+                }
+            }
         }
         float spx = 0.f, snx = 0.f, spy = 0.f, sny = 0.f;
 #pragma unroll
@@ -98,28 +97,45 @@ __global__ void lse_net_kernel(int n_nets, const int32_t *__restrict__ net_ptr,
                 sny += expf((ly - py[k]) * inv_gamma);
             }
         }
-        for (int p = p0 + KP; p < p1; ++p) {
-            const int i = net_pin[p];
-            const float xi = x[i], yi = y[i];
-            spx += expf((xi - hx) * inv_gamma);
-            snx += expf((lx - xi) * inv_gamma);
-            spy += expf((yi - hy) * inv_gamma);
-            sny += expf((ly - yi) * inv_gamma);
+        for (int b = p0 + KP; b < p1; b += KT) {
+            float tx[KT], ty[KT];
+#pragma unroll
+            for (int k = 0; k < KT; ++k) {
+                if (b + k < p1) {
+                    const int i = net_pin[b + k];
+                    tx[k] = x[i];
+                    ty[k] = y[i];
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < KT; ++k) {
+                if (b + k < p1) {
+                    spx += expf((tx[k] - hx) * inv_gamma);
+                    snx += expf((lx - tx[k]) * inv_gamma);
+                    spy += expf((ty[k] - hy) * inv_gamma);
+                    sny += expf((ly - ty[k]) * inv_gamma);
+                }
+            }
         }
         if (p1 - p0 >= 2) {
             stats[2 * e] = make_float4(hx, lx, 1.f / spx, 1.f / snx);
             stats[2 * e + 1] = make_float4(hy, ly, 1.f / spy, 1.f / sny);
-            hp += (double)(hx - lx) + (double)(hy - ly);
-            wl += (double)(hx - lx) + (double)(hy - ly) +
-                  (double)gamma * ((double)logf(spx) + logf(snx) + logf(spy) + logf(sny));
+            add2(hp, hx - lx);
+            add2(hp, hy - ly);
+            add2(wl, hx - lx);
+            add2(wl, hy - ly);
+            add_prod(wl, gamma, logf(spx));
+            add_prod(wl, gamma, logf(snx));
+            add_prod(wl, gamma, logf(spy));
+            add_prod(wl, gamma, logf(sny));
         } else {       // a net of fewer than two pins adds nothing: both exponentials
                        // of its gradient terms are exp(-inf) = 0 (no inf * 0)
             stats[2 * e] = make_float4(INFINITY, -INFINITY, 0.f, 0.f);
             stats[2 * e + 1] = make_float4(INFINITY, -INFINITY, 0.f, 0.f);
         }
     }
-    block_add(wl, out);
-    block_add(hp, out + 1);
+    block_add2(wl, out);
+    block_add2(hp, out + 1);
 }
 
 __global__ void lse_cell_kernel(int n_cells, const int32_t *__restrict__ cell_ptr,
@@ -151,11 +167,23 @@ __global__ void lse_cell_kernel(int n_cells, const int32_t *__restrict__ cell_pt
                 ay += expf((yi - sy.x) * inv_gamma) * sy.z - expf((sy.y - yi) * inv_gamma) * sy.w;
             }
         }
-        for (int k = k0 + KC; k < k1; ++k) {
-            const int e = cell_net[k];
-            const float4 sx = stats[2 * e], sy = stats[2 * e + 1];
-            ax += expf((xi - sx.x) * inv_gamma) * sx.z - expf((sx.y - xi) * inv_gamma) * sx.w;
-            ay += expf((yi - sy.x) * inv_gamma) * sy.z - expf((sy.y - yi) * inv_gamma) * sy.w;
+        for (int b = k0 + KC; b < k1; b += KC) {      // the rest KC at a time, in order
+#pragma unroll
+            for (int q = 0; q < KC; ++q) {
+                if (b + q < k1) {
+                    const int e = cell_net[b + q];
+                    sxs[q] = stats[2 * e];
+                    sys[q] = stats[2 * e + 1];
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < KC; ++q) {
+                if (b + q < k1) {
+                    const float4 sx = sxs[q], sy = sys[q];
+                    ax += expf((xi - sx.x) * inv_gamma) * sx.z - expf((sx.y - xi) * inv_gamma) * sx.w;
+                    ay += expf((yi - sy.x) * inv_gamma) * sy.z - expf((sy.y - yi) * inv_gamma) * sy.w;
+                }
+            }
         }
         gx[i] = ax;
         gy[i] = ay;
@@ -185,14 +213,33 @@ __global__ void step_norms_kernel(int64_t n, const float *__restrict__ vx, const
                                   const float *__restrict__ gx, const float *__restrict__ gy,
                                   const float *__restrict__ gpx, const float *__restrict__ gpy,
                                   double *__restrict__ norms) {
-    double dv = 0.0, dg = 0.0;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const float a = vx[i] - vpx[i], b = vy[i] - vpy[i], c = gx[i] - gpx[i], d = gy[i] - gpy[i];
-        dv += (double)a * a + (double)b * b;
-        dg += (double)c * c + (double)d * d;
+    Sum2 dv, dg;
+    // U strided elements per thread and round, their loads in flight together
+    constexpr int U = 4;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < n; b += U * stride) {
+        float a[U], c[U], d[U], e[U];
+#pragma unroll
+        for (int k = 0; k < U; ++k) {
+            const int64_t i = b + k * stride;
+            a[k] = c[k] = d[k] = e[k] = 0.f;
+            if (i < n) {
+                a[k] = vx[i] - vpx[i];
+                c[k] = vy[i] - vpy[i];
+                d[k] = gx[i] - gpx[i];
+                e[k] = gy[i] - gpy[i];
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < U; ++k) {
+            add_prod(dv, a[k], a[k]);
+            add_prod(dv, c[k], c[k]);
+            add_prod(dg, d[k], d[k]);
+            add_prod(dg, e[k], e[k]);
+        }
     }
-    block_add(dv, norms);
-    block_add(dg, norms + 1);
+    block_add2(dv, norms);
+    block_add2(dg, norms + 1);
 }
 
 __global__ void nesterov_kernel(int64_t n, float *__restrict__ ux, float *__restrict__ uy, float *__restrict__ vx,
@@ -236,10 +283,17 @@ __global__ void nesterov_kernel(int64_t n, float *__restrict__ ux, float *__rest
 }
 
 __global__ void overflow_kernel(int64_t cells, const float *__restrict__ P, float target, double *__restrict__ out) {
-    double s = 0.0;
-    for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < cells; b += (int64_t)gridDim.x * blockDim.x)
-        s += (double)fmaxf(P[b] - target, 0.f);
-    block_add(s, out);
+    Sum2 s;
+    constexpr int U = 4;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < cells; b += U * stride) {
+        float v[U];
+#pragma unroll
+        for (int k = 0; k < U; ++k) v[k] = b + k * stride < cells ? P[b + k * stride] : target;
+#pragma unroll
+        for (int k = 0; k < U; ++k) add2(s, fmaxf(v[k] - target, 0.f));
+    }
+    block_add2(s, out);
 }
 
 // ---- the loop's scalar update on the device (pp_place_run) ----
