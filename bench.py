@@ -505,9 +505,10 @@ def run_ours(args):
         m = args.bins or max(p.Mx, p.My)
         # density and interpolation (n > 0), the row prefix sums of the difference array
         # (n > 0, folded into the first row transform for m = 512, 1024), FFT tables (m a
-        # power of two), 7 row transforms, 3 transposes, scaling
+        # power of two), 7 row transforms (those followed by a step along the other axis
+        # write transposed), scaling
         per_step = ((2 + (0 if m in (512, 1024) else 1)) if p.n > 0 else 0) \
-            + (1 if m & (m - 1) == 0 else 0) + 7 + 3 + 1
+            + (1 if m & (m - 1) == 0 else 0) + 7 + 1
         launches = per_step * args.steps
     else:
         launches = int(sum(v[0] for v in counts.values()))     # our kernels in the timed steps

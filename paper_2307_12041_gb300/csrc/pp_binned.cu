@@ -13,8 +13,10 @@
 //                         FFT in shared memory (the paper computes these transforms with
 //                         the FFT: O(m^2 log m) per 2-D transform); other m use a direct
 //                         sum over a shared-memory table of cos(pi q / 2m), q < 4m.
-//   transpose_kernel      between the two axes of a 2-D transform
-//   scale_kernel          a = (Eq. disa prefactors) o a'
+//                         A transform whose next step runs along the other axis
+//                         writes each row's outputs down a column of that step's
+//                         input (no separate transpose).
+//   scale_kernel          a = (Eq. disa prefactors) o a', transposing a' to u-major
 //   interp_kernel         bilinear weighting of the bin-centre values at each block
 //                         centre: N_i = q_i psi_i, grad = -q_i xi_i, E = 1/2 sum N_i
 // Every transform runs in FP32.
@@ -187,9 +189,8 @@ __global__ void __launch_bounds__(256) row_prefix_add_kernel(const float *__rest
     }
 }
 
-// a = prefactor o a' (Eq. disa-a..d), FP32; a' arrives transposed (apt[p][u], row
-// stride Mx), a leaves u-major (a[u][p]).
-// a[u][p] = f(u, p) a'[p][u] (a' = R2 is [My][Mx]): a transpose through a padded
+// a = prefactor o a' (Eq. disa-a..d), FP32: a[u][p] = f(u, p) a'[p][u] (a' = R2 is
+// [My][Mx], a leaves u-major): a transpose through a padded
 // 32 x 32 shared tile (reads and writes both coalesced) with the prefactor applied on
 // the way out; the sines of the tile's 32 u and 32 p are formed once per tile.
 __global__ void scale_kernel(int Mx, int My, int m, float W, float H, const float *__restrict__ apt,
@@ -647,22 +648,6 @@ __global__ void __launch_bounds__(T_THREADS) direct_rows_kernel(const float *__r
     }
 }
 
-// out[c][r] = in[r][c] for r < R, c < C (32 x 32 tiles through shared memory)
-__global__ void transpose_kernel(const float *__restrict__ in, int in_ld, int R, int C, float *__restrict__ out,
-                                 int out_ld) {
-    __shared__ float t[32][33];
-    const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
-    for (int k = threadIdx.y; k < 32; k += blockDim.y) {
-        const int r = r0 + k, c = c0 + threadIdx.x;
-        if (r < R && c < C) t[k][threadIdx.x] = in[(size_t)r * in_ld + c];
-    }
-    __syncthreads();
-    for (int k = threadIdx.y; k < 32; k += blockDim.y) {
-        const int c = c0 + k, r = r0 + threadIdx.x;
-        if (r < R && c < C) out[(size_t)c * out_ld + r] = t[threadIdx.x][k];
-    }
-}
-
 __global__ void interp_kernel(const float *__restrict__ x, const float *__restrict__ y,
                               const float *__restrict__ w, const float *__restrict__ h,
                               const float *__restrict__ c, int n, int m, float inv_wb, float inv_hb,
@@ -704,12 +689,9 @@ BinnedLayout binned_layout(int m, int Mx, int My) {
     const size_t mm = (size_t)m * m;
     L.P = take(mm);
     L.D = take(mm);
-    L.R1 = take((size_t)m * My);
     L.R1t = take((size_t)My * m);
     L.R2 = take((size_t)My * Mx);
     L.a = take((size_t)Mx * My);
-    L.U = take((size_t)Mx * m);
-    L.Up = take((size_t)Mx * m);
     L.Ut = take((size_t)m * Mx);
     L.Upt = take((size_t)m * Mx);
     L.V = take(4 * mm);
@@ -784,12 +766,6 @@ cudaError_t rows(int mode, const float *in, int in_ld, int nrows, int kin, float
     return e;
 }
 
-cudaError_t transpose(const float *in, int in_ld, int R, int C, float *out, int out_ld, cudaStream_t st) {
-    dim3 grid((C + 31) / 32, (R + 31) / 32), block(32, 8);
-    transpose_kernel<<<grid, block, 0, st>>>(in, in_ld, R, C, out, out_ld);
-    return cudaGetLastError();
-}
-
 }  // namespace
 
 cudaError_t run_binned(const Launch &Lc, int dev, int m, bool tf32, unsigned char *ws, float *a_out, float *e_block,
@@ -798,9 +774,9 @@ cudaError_t run_binned(const Launch &Lc, int dev, int m, bool tf32, unsigned cha
     (void)tf32;                        // the transforms are FP32 FFTs (or direct sums) in either precision
     const int Mx = Lc.Mx, My = Lc.My, n = Lc.n;
     const BinnedLayout B = binned_layout(m, Mx, My);
-    float *P = (float *)(ws + B.P), *R1 = (float *)(ws + B.R1), *R1t = (float *)(ws + B.R1t);
+    float *P = (float *)(ws + B.P), *R1t = (float *)(ws + B.R1t);
     float *R2 = (float *)(ws + B.R2), *a = a_out ? a_out : (float *)(ws + B.a);
-    float *U = (float *)(ws + B.U), *Up = (float *)(ws + B.Up), *Ut = (float *)(ws + B.Ut);
+    float *Ut = (float *)(ws + B.Ut);
     float *Upt = (float *)(ws + B.Upt);
     float *V = (float *)(ws + B.V);
     float2 *tw = (float2 *)(ws + B.tab), *qw = tw + m / 2;
@@ -829,18 +805,17 @@ cudaError_t run_binned(const Launch &Lc, int dev, int m, bool tf32, unsigned cha
     do {                                           \
         if ((e = (expr)) != cudaSuccess) return e; \
     } while (0)
-    // a' = Cx P Cy^T: along j (rows l of P), then along l
-    PP_STEP(rows(T_DCT2, P, m, m, m, 0.f, m, My, R1, My, 1, tw, qw, st, n > 0 ? D : nullptr));
-    PP_STEP(transpose(R1, My, m, My, R1t, m, st));
+    // a' = Cx P Cy^T: along j (rows l of P, each row's outputs written down a column of
+    // R1t, so that no transpose is needed), then along l
+    PP_STEP(rows(T_DCT2, P, m, m, m, 0.f, m, My, R1t, 1, m, tw, qw, st, n > 0 ? D : nullptr));
     PP_STEP(rows(T_DCT2, R1t, m, My, m, 0.f, m, Mx, R2, Mx, 1, tw, qw, st));
     scale_kernel<<<dim3((Mx + 31) / 32, (My + 31) / 32), dim3(32, 8), 0, st>>>(Mx, My, m, (float)Lc.W, (float)Lc.H,
                                                                              R2, a);
     PP_STEP(cudaGetLastError());
-    // along v (rows u of a): U = a Cy (psi, xi_x), Up = (a o l) Sy (xi_y)
-    PP_STEP(rows(T_DCT3, a, My, Mx, My, 0.f, m, m, U, m, 1, tw, qw, st));
-    PP_STEP(rows(T_DST3, a, My, Mx, My, lH, m, m, Up, m, 1, tw, qw, st));
-    PP_STEP(transpose(U, m, Mx, m, Ut, Mx, st));
-    PP_STEP(transpose(Up, m, Mx, m, Upt, Mx, st));
+    // along v (rows u of a): U = a Cy (psi, xi_x), Up = (a o l) Sy (xi_y), written
+    // transposed (Ut[j][u], Upt[j][u])
+    PP_STEP(rows(T_DCT3, a, My, Mx, My, 0.f, m, m, Ut, 1, Mx, tw, qw, st));
+    PP_STEP(rows(T_DST3, a, My, Mx, My, lH, m, m, Upt, 1, Mx, tw, qw, st));
     // along u (rows j): psi = Cx^T U, xi_x = Sx^T (k o U), xi_y = Cx^T Up, stored interleaved
     // as V[j][l] = (psi, xi_x, xi_y, unused) so that the interpolation reads one float4 per corner
     PP_STEP(rows(T_DCT3, Ut, Mx, m, Mx, 0.f, m, m, V + 0, 4 * m, 4, tw, qw, st));

@@ -89,7 +89,7 @@ cudaError_t launch_energy_tc(const Launch &L, int prec, int sample, const TcPlan
 void set_last_error(const char *msg);
 // Binned fast scheme (pp_binned.cu): workspace offsets (bytes) and the pipeline.
 struct BinnedLayout {
-    size_t P, D, R1, R1t, R2, a, U, Up, Ut, Upt, V, tab, total;
+    size_t P, D, R1t, R2, a, Ut, Upt, V, tab, total;
 };
 BinnedLayout binned_layout(int m, int Mx, int My);
 // `what` names the failing step on error
