@@ -506,9 +506,10 @@ def run_ours(args):
         # density and interpolation (n > 0), the row prefix sums of the difference array
         # (n > 0, folded into the first row transform for m = 512, 1024), FFT tables (m a
         # power of two), 7 row transforms (those followed by a step along the other axis
-        # write transposed), scaling
+        # write transposed; for m = 512, 1024 the independent ones share a launch: 4
+        # launches), scaling
         per_step = ((2 + (0 if m in (512, 1024) else 1)) if p.n > 0 else 0) \
-            + (1 if m & (m - 1) == 0 else 0) + 7 + 1
+            + (1 if m & (m - 1) == 0 else 0) + (4 if m in (512, 1024) else 7) + 1
         launches = per_step * args.steps
     else:
         launches = int(sum(v[0] for v in counts.values()))     # our kernels in the timed steps

@@ -237,6 +237,21 @@ __global__ void scale_kernel(int Mx, int My, int m, float W, float H, const floa
 // 0) with alternating signs.
 // ---------------------------------------------------------------------------
 enum { T_DCT2 = 0, T_DCT3 = 1, T_DST3 = 2 };
+
+// Up to three independent row passes of the same sizes in one launch of the warp FFT
+// kernels (blockIdx.y picks one): each with its input, output, input scale and, for the
+// inverse kernels, its kind (DCT-III, or DST-III when dst is set).  Independent passes
+// side by side give the GPU several times the warps of one pass.
+struct RowJobs {
+    const float *in[3];
+    float *out[3];
+    float in_scale[3];
+    int dst[3];
+};
+template <typename T>
+__device__ __forceinline__ T pick3(const T (&v)[3], int j) {
+    return j == 0 ? v[0] : (j == 1 ? v[1] : v[2]);
+}
 constexpr int T_THREADS = 256;
 
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
@@ -336,14 +351,17 @@ __global__ void __launch_bounds__(T_THREADS) fft_rows_kernel(const float *__rest
 __device__ __forceinline__ int pad(int i) { return i + (i >> 5); }
 
 template <int MODE, int R>
-__global__ void __launch_bounds__(128) fft_rows_warp_kernel(const float *__restrict__ in, int in_ld, int kin,
-                                                           float in_scale, int nrows, int keep,
-                                                           float *__restrict__ out, int out_ld, int ostr,
+__global__ void __launch_bounds__(128) fft_rows_warp_kernel(const RowJobs jobs, int in_ld, int kin, int nrows,
+                                                           int keep, int out_ld, int ostr,
                                                            const float2 *__restrict__ tw_g,
                                                            const float2 *__restrict__ qw_g,
                                                            const float *__restrict__ dif) {
     constexpr int m = 32 * R, half = m / 2, mp = m + m / 32;
     constexpr bool INV = MODE != T_DCT2;
+    const float *__restrict__ in = pick3(jobs.in, blockIdx.y);
+    float *__restrict__ out = pick3(jobs.out, blockIdx.y);
+    const float in_scale = pick3(jobs.in_scale, blockIdx.y);
+    const bool DST = INV && pick3(jobs.dst, blockIdx.y) != 0;
     __shared__ float2 tw[m];                                 // W^k (e^{-+2 pi i k / m}), k < m
     __shared__ float2 qw[mp];                                // (cos, sin)(pi u / 2m) at pad(u)
     __shared__ float xs[4][mp];                              // one row per warp, at pad(i)
@@ -400,13 +418,13 @@ __global__ void __launch_bounds__(128) fft_rows_warp_kernel(const float *__restr
             const int src = n < half ? 2 * n : 2 * (m - 1 - n) + 1;
             a[n2] = make_float2(coef(src), 0.f);
         } else {
-            const float cu = MODE == T_DCT3 ? coef(n) : (n == 0 ? 0.f : coef(m - n));
-            const float cmu = n == 0 ? 0.f : (MODE == T_DCT3 ? coef(m - n) : coef(n));
+            const float cu = !DST ? coef(n) : (n == 0 ? 0.f : coef(m - n));
+            const float cmu = n == 0 ? 0.f : (!DST ? coef(m - n) : coef(n));
             const float2 q = qw[pad(n)];
             a[n2] = make_float2(q.x * cu + q.y * cmu, q.y * cu - q.x * cmu);
         }
     }
-    const float c0 = MODE == T_DCT3 ? coef(0) : 0.f;
+    const float c0 = INV && !DST ? coef(0) : 0.f;
     // 32-point transforms across the lanes: pairs (i, i + h), i with bit h clear:
     // y_i <- y_i + y_{i+h}, y_{i+h} <- (y_i - y_{i+h}) W_{2h}^{i mod h}
 #pragma unroll
@@ -449,7 +467,7 @@ __global__ void __launch_bounds__(128) fft_rows_warp_kernel(const float *__restr
         } else {
             const int l = k < half ? 2 * k : 2 * (m - 1 - k) + 1;
             const float t = 0.5f * (a[j].x + c0);
-            xw[pad(l)] = (MODE == T_DST3 && (l & 1)) ? -t : t;
+            xw[pad(l)] = (DST && (l & 1)) ? -t : t;
         }
     }
     __syncwarp();
@@ -467,14 +485,17 @@ __global__ void __launch_bounds__(128) fft_rows_warp_kernel(const float *__restr
 //   warp 1:  v_i = (y_i - y_{i+16}) W_32^i        -> Y_{k1 + 32 (2q + 1)}, 16-point over i
 // (i < 16).  Named barrier 1 + (row within the CTA) joins the row's two warps.
 template <int MODE>
-__global__ void __launch_bounds__(128) fft_rows_pair_kernel(const float *__restrict__ in, int in_ld, int kin,
-                                                           float in_scale, int nrows, int keep,
-                                                           float *__restrict__ out, int out_ld, int ostr,
+__global__ void __launch_bounds__(128) fft_rows_pair_kernel(const RowJobs jobs, int in_ld, int kin, int nrows,
+                                                           int keep, int out_ld, int ostr,
                                                            const float2 *__restrict__ tw_g,
                                                            const float2 *__restrict__ qw_g,
                                                            const float *__restrict__ dif) {
     constexpr int R = 32, H = 16, m = 32 * R, half = m / 2, mp = m + m / 32;
     constexpr bool INV = MODE != T_DCT2;
+    const float *__restrict__ in = pick3(jobs.in, blockIdx.y);
+    float *__restrict__ out = pick3(jobs.out, blockIdx.y);
+    const float in_scale = pick3(jobs.in_scale, blockIdx.y);
+    const bool DST = INV && pick3(jobs.dst, blockIdx.y) != 0;
     __shared__ float2 tw[m];                                 // W^k (e^{-+2 pi i k / m}), k < m
     __shared__ float2 qw[mp];                                // (cos, sin)(pi u / 2m) at pad(u)
     __shared__ float xs[2][mp];                              // one row per warp pair, at pad(i)
@@ -536,13 +557,13 @@ __global__ void __launch_bounds__(128) fft_rows_pair_kernel(const float *__restr
             const int src = n < half ? 2 * n : 2 * (m - 1 - n) + 1;
             a[i] = make_float2(coef(src), 0.f);
         } else {
-            const float cu = MODE == T_DCT3 ? coef(n) : (n == 0 ? 0.f : coef(m - n));
-            const float cmu = n == 0 ? 0.f : (MODE == T_DCT3 ? coef(m - n) : coef(n));
+            const float cu = !DST ? coef(n) : (n == 0 ? 0.f : coef(m - n));
+            const float cmu = n == 0 ? 0.f : (!DST ? coef(m - n) : coef(n));
             const float2 q = qw[pad(n)];
             a[i] = make_float2(q.x * cu + q.y * cmu, q.y * cu - q.x * cmu);
         }
     }
-    const float c0 = MODE == T_DCT3 ? coef(0) : 0.f;
+    const float c0 = INV && !DST ? coef(0) : 0.f;
 #pragma unroll
     for (int hh = 16; hh >= 1; hh >>= 1) {
         const bool hi = (lane & hh) != 0;
@@ -593,7 +614,7 @@ __global__ void __launch_bounds__(128) fft_rows_pair_kernel(const float *__restr
         } else {
             const int l = k < half ? 2 * k : 2 * (m - 1 - k) + 1;
             const float t = 0.5f * (a[j].x + c0);
-            xw[pad(l)] = (MODE == T_DST3 && (l & 1)) ? -t : t;
+            xw[pad(l)] = (DST && (l & 1)) ? -t : t;
         }
     }
     row_sync();
@@ -712,58 +733,65 @@ namespace {
 bool pow2(int m) { return m > 0 && (m & (m - 1)) == 0; }
 bool warp_fft(int m) { return m == 512 || m == 1024; }
 
-// rows transforms of `mode` (T_DCT2 / T_DCT3 / T_DST3), FFT when m is a power of two
-// (one warp per row for m = 512, 1024; one CTA per row otherwise)
-// rows `nrows` of `in` transformed; output element k of row r at out[r * out_ld + k * ostr]
-// dif (DCT-II with the warp FFT only): row prefix sums added to the input rows
-cudaError_t rows(int mode, const float *in, int in_ld, int nrows, int kin, float in_scale, int m, int keep,
-                 float *out, int out_ld, int ostr, const float2 *tw, const float2 *qw, cudaStream_t st,
+// Row transforms, FFT when m is a power of two (one warp per row for m = 512, two for
+// m = 1024, all jobs in one launch; one CTA per row and one launch per job otherwise).
+// `fwd`: DCT-II; else each job's DCT-III or DST-III (RowJobs::dst).  Rows `nrows` of
+// each job's input transformed; output element k of row r at out[r * out_ld + k * ostr].
+// dif (DCT-II with the warp FFT only): row prefix sums added to the input rows.
+cudaError_t rows(bool fwd, const RowJobs &J, int njobs, int in_ld, int nrows, int kin, int m, int keep,
+                 int out_ld, int ostr, const float2 *tw, const float2 *qw, cudaStream_t st,
                  const float *dif = nullptr) {
-    if (nrows <= 0) return cudaSuccess;
-    cudaError_t e;
+    if (nrows <= 0 || njobs <= 0) return cudaSuccess;
+    if (njobs > 3) return cudaErrorInvalidValue;
     if (warp_fft(m)) {
-        auto go = [&](auto kfn) {
-            kfn<<<(nrows + 3) / 4, 128, 0, st>>>(in, in_ld, kin, in_scale, nrows, keep, out, out_ld, ostr, tw, qw,
-                                                 dif);
-            return cudaGetLastError();
-        };
-        auto go2 = [&](auto kfn) {
-            kfn<<<(nrows + 1) / 2, 128, 0, st>>>(in, in_ld, kin, in_scale, nrows, keep, out, out_ld, ostr, tw, qw,
-                                                 dif);
-            return cudaGetLastError();
-        };
-        if (m == 512)
-            e = mode == T_DCT2 ? go(fft_rows_warp_kernel<T_DCT2, 16>)
-                               : (mode == T_DCT3 ? go(fft_rows_warp_kernel<T_DCT3, 16>)
-                                                 : go(fft_rows_warp_kernel<T_DST3, 16>));
-        else
-            e = mode == T_DCT2 ? go2(fft_rows_pair_kernel<T_DCT2>)
-                               : (mode == T_DCT3 ? go2(fft_rows_pair_kernel<T_DCT3>)
-                                                 : go2(fft_rows_pair_kernel<T_DST3>));
-    } else if (pow2(m)) {
-        int lg = 0;
-        while ((1 << lg) < m) ++lg;
-        const size_t smem = (size_t)(m + m / 2) * sizeof(float2);
-        auto go = [&](auto kfn) {
-            cudaError_t r = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            if (r != cudaSuccess) return r;
-            kfn<<<nrows, T_THREADS, smem, st>>>(in, in_ld, kin, in_scale, m, lg, keep, out, out_ld, ostr, tw, qw);
-            return cudaGetLastError();
-        };
-        e = mode == T_DCT2 ? go(fft_rows_kernel<T_DCT2>)
-                           : (mode == T_DCT3 ? go(fft_rows_kernel<T_DCT3>) : go(fft_rows_kernel<T_DST3>));
-    } else {
-        const size_t smem = (size_t)(4 * m + kin) * sizeof(float);
-        auto go = [&](auto kfn) {
-            cudaError_t r = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            if (r != cudaSuccess) return r;
-            kfn<<<nrows, T_THREADS, smem, st>>>(in, in_ld, kin, in_scale, m, keep, out, out_ld, ostr);
-            return cudaGetLastError();
-        };
-        e = mode == T_DCT2 ? go(direct_rows_kernel<T_DCT2>)
-                           : (mode == T_DCT3 ? go(direct_rows_kernel<T_DCT3>) : go(direct_rows_kernel<T_DST3>));
+        const int per_cta = m == 512 ? 4 : 2;
+        const dim3 grid((nrows + per_cta - 1) / per_cta, njobs);
+        if (m == 512) {
+            if (fwd) fft_rows_warp_kernel<T_DCT2, 16><<<grid, 128, 0, st>>>(J, in_ld, kin, nrows, keep, out_ld, ostr,
+                                                                            tw, qw, dif);
+            else fft_rows_warp_kernel<T_DCT3, 16><<<grid, 128, 0, st>>>(J, in_ld, kin, nrows, keep, out_ld, ostr, tw,
+                                                                        qw, dif);
+        } else {
+            if (fwd) fft_rows_pair_kernel<T_DCT2><<<grid, 128, 0, st>>>(J, in_ld, kin, nrows, keep, out_ld, ostr, tw,
+                                                                        qw, dif);
+            else fft_rows_pair_kernel<T_DCT3><<<grid, 128, 0, st>>>(J, in_ld, kin, nrows, keep, out_ld, ostr, tw, qw,
+                                                                    dif);
+        }
+        return cudaGetLastError();
     }
-    return e;
+    for (int j = 0; j < njobs; ++j) {
+        const int mode = fwd ? T_DCT2 : (J.dst[j] ? T_DST3 : T_DCT3);
+        const float *in = J.in[j];
+        float *out = J.out[j];
+        const float in_scale = J.in_scale[j];
+        cudaError_t e;
+        if (pow2(m)) {
+            int lg = 0;
+            while ((1 << lg) < m) ++lg;
+            const size_t smem = (size_t)(m + m / 2) * sizeof(float2);
+            auto go = [&](auto kfn) {
+                cudaError_t r = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                if (r != cudaSuccess) return r;
+                kfn<<<nrows, T_THREADS, smem, st>>>(in, in_ld, kin, in_scale, m, lg, keep, out, out_ld, ostr, tw,
+                                                    qw);
+                return cudaGetLastError();
+            };
+            e = mode == T_DCT2 ? go(fft_rows_kernel<T_DCT2>)
+                               : (mode == T_DCT3 ? go(fft_rows_kernel<T_DCT3>) : go(fft_rows_kernel<T_DST3>));
+        } else {
+            const size_t smem = (size_t)(4 * m + kin) * sizeof(float);
+            auto go = [&](auto kfn) {
+                cudaError_t r = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                if (r != cudaSuccess) return r;
+                kfn<<<nrows, T_THREADS, smem, st>>>(in, in_ld, kin, in_scale, m, keep, out, out_ld, ostr);
+                return cudaGetLastError();
+            };
+            e = mode == T_DCT2 ? go(direct_rows_kernel<T_DCT2>)
+                               : (mode == T_DCT3 ? go(direct_rows_kernel<T_DCT3>) : go(direct_rows_kernel<T_DST3>));
+        }
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 }  // namespace
@@ -807,20 +835,28 @@ cudaError_t run_binned(const Launch &Lc, int dev, int m, bool tf32, unsigned cha
     } while (0)
     // a' = Cx P Cy^T: along j (rows l of P, each row's outputs written down a column of
     // R1t, so that no transpose is needed), then along l
-    PP_STEP(rows(T_DCT2, P, m, m, m, 0.f, m, My, R1t, 1, m, tw, qw, st, n > 0 ? D : nullptr));
-    PP_STEP(rows(T_DCT2, R1t, m, My, m, 0.f, m, Mx, R2, Mx, 1, tw, qw, st));
+    {
+        const RowJobs j1{{P}, {R1t}, {0.f}, {0}};
+        PP_STEP(rows(true, j1, 1, m, m, m, m, My, 1, m, tw, qw, st, n > 0 ? D : nullptr));
+        const RowJobs j2{{R1t}, {R2}, {0.f}, {0}};
+        PP_STEP(rows(true, j2, 1, m, My, m, m, Mx, Mx, 1, tw, qw, st));
+    }
     scale_kernel<<<dim3((Mx + 31) / 32, (My + 31) / 32), dim3(32, 8), 0, st>>>(Mx, My, m, (float)Lc.W, (float)Lc.H,
                                                                              R2, a);
     PP_STEP(cudaGetLastError());
-    // along v (rows u of a): U = a Cy (psi, xi_x), Up = (a o l) Sy (xi_y), written
-    // transposed (Ut[j][u], Upt[j][u])
-    PP_STEP(rows(T_DCT3, a, My, Mx, My, 0.f, m, m, Ut, 1, Mx, tw, qw, st));
-    PP_STEP(rows(T_DST3, a, My, Mx, My, lH, m, m, Upt, 1, Mx, tw, qw, st));
-    // along u (rows j): psi = Cx^T U, xi_x = Sx^T (k o U), xi_y = Cx^T Up, stored interleaved
-    // as V[j][l] = (psi, xi_x, xi_y, unused) so that the interpolation reads one float4 per corner
-    PP_STEP(rows(T_DCT3, Ut, Mx, m, Mx, 0.f, m, m, V + 0, 4 * m, 4, tw, qw, st));
-    PP_STEP(rows(T_DST3, Ut, Mx, m, Mx, kW, m, m, V + 1, 4 * m, 4, tw, qw, st));
-    PP_STEP(rows(T_DCT3, Upt, Mx, m, Mx, 0.f, m, m, V + 2, 4 * m, 4, tw, qw, st));
+    // along v (rows u of a), both in one launch: U = a Cy (psi, xi_x), Up = (a o l) Sy
+    // (xi_y), written transposed (Ut[j][u], Upt[j][u])
+    {
+        const RowJobs j3{{a, a}, {Ut, Upt}, {0.f, lH}, {0, 1}};
+        PP_STEP(rows(false, j3, 2, My, Mx, My, m, m, 1, Mx, tw, qw, st));
+    }
+    // along u (rows j), the three in one launch: psi = Cx^T U, xi_x = Sx^T (k o U),
+    // xi_y = Cx^T Up, stored interleaved as V[j][l] = (psi, xi_x, xi_y, unused) so that the
+    // interpolation reads one float4 per corner
+    {
+        const RowJobs j4{{Ut, Ut, Upt}, {V + 0, V + 1, V + 2}, {0.f, kW, 0.f}, {0, 1, 0}};
+        PP_STEP(rows(false, j4, 3, Mx, m, Mx, m, m, 4 * m, 4, tw, qw, st));
+    }
 #undef PP_STEP
     if (n > 0) {
         interp_kernel<<<grid, 256, 0, st>>>(Lc.x, Lc.y, Lc.w, Lc.h, Lc.c, n, m, (float)(m / Lc.W),
