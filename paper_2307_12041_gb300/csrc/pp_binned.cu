@@ -102,15 +102,20 @@ __global__ void bin_density_kernel(const float *__restrict__ x, const float *__r
         }
         const long long nl = l1 >= l0 ? l1 - l0 + 1 : 0, nj = j1 >= j0 ? j1 - j0 + 1 : 0;
         const bool large = nl * nj > kSmallBins;
-        if (!large) {
+        if (!large && nl > 0 && nj > 0) {
+            // along each axis only the first and the last bin can be partly covered; the
+            // bins between get the whole bin (1 in bin units), so the 2^-40-unit overlaps
+            // are formed and converted twice per axis, not once per bin
+            const float ax0 = (float)overlap(x0, x1, l0) * unit, ax1 = (float)overlap(x0, x1, l1) * unit;
+            const float ay0 = (float)overlap(y0, y1, j0) * unit, ay1 = (float)overlap(y0, y1, j1) * unit;
             for (int l = l0; l <= l1; ++l) {
-                const long long ox = overlap(x0, x1, l);
-                if (ox <= 0) continue;
-                const float cox = ci * ((float)ox * unit);
+                const float fx = l == l0 ? ax0 : (l == l1 ? ax1 : 1.f);
+                if (!(fx > 0.f)) continue;
+                const float cox = ci * fx;
                 for (int j = j0; j <= j1; ++j) {
-                    const long long oy = overlap(y0, y1, j);
-                    if (oy <= 0) continue;
-                    atomicAdd(&P[(size_t)l * m + j], cox * ((float)oy * unit));   // area / bin area
+                    const float fy = j == j0 ? ay0 : (j == j1 ? ay1 : 1.f);
+                    if (!(fy > 0.f)) continue;
+                    atomicAdd(&P[(size_t)l * m + j], cox * fy);   // area / bin area
                 }
             }
         }

@@ -40,6 +40,8 @@ __global__ void lse_net_kernel(int n_nets, const int32_t *__restrict__ net_ptr,
         gamma = scal[1];
         inv_gamma = 1.f / gamma;
     }
+    // e^{d / gamma} = 2^{d k2}: one multiply and the hardware base-2 exponential
+    const float k2 = inv_gamma * 1.44269504088896341f;
     Sum2 wl, hp;
     // the first KP pins of a net are gathered together (their loads in flight at once)
     // and kept in registers for the second pass; longer nets gather the rest KT at a
@@ -91,10 +93,10 @@ __global__ void lse_net_kernel(int n_nets, const int32_t *__restrict__ net_ptr,
 #pragma unroll
         for (int k = 0; k < KP; ++k) {
             if (k < np) {
-                spx += expf((px[k] - hx) * inv_gamma);
-                snx += expf((lx - px[k]) * inv_gamma);
-                spy += expf((py[k] - hy) * inv_gamma);
-                sny += expf((ly - py[k]) * inv_gamma);
+                spx += exp2f((px[k] - hx) * k2);
+                snx += exp2f((lx - px[k]) * k2);
+                spy += exp2f((py[k] - hy) * k2);
+                sny += exp2f((ly - py[k]) * k2);
             }
         }
         for (int b = p0 + KP; b < p1; b += KT) {
@@ -110,10 +112,10 @@ __global__ void lse_net_kernel(int n_nets, const int32_t *__restrict__ net_ptr,
 #pragma unroll
             for (int k = 0; k < KT; ++k) {
                 if (b + k < p1) {
-                    spx += expf((tx[k] - hx) * inv_gamma);
-                    snx += expf((lx - tx[k]) * inv_gamma);
-                    spy += expf((ty[k] - hy) * inv_gamma);
-                    sny += expf((ly - ty[k]) * inv_gamma);
+                    spx += exp2f((tx[k] - hx) * k2);
+                    snx += exp2f((lx - tx[k]) * k2);
+                    spy += exp2f((ty[k] - hy) * k2);
+                    sny += exp2f((ly - ty[k]) * k2);
                 }
             }
         }
@@ -144,6 +146,7 @@ __global__ void lse_cell_kernel(int n_cells, const int32_t *__restrict__ cell_pt
                                 const float4 *__restrict__ stats, float *__restrict__ gx,
                                 float *__restrict__ gy) {
     if (scal) inv_gamma = 1.f / scal[1];
+    const float k2 = inv_gamma * 1.44269504088896341f;   // e^{d / gamma} = 2^{d k2}
     // the first KC nets of a cell gathered together (their loads in flight at once)
     constexpr int KC = 4;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_cells; i += gridDim.x * blockDim.x) {
@@ -163,8 +166,8 @@ __global__ void lse_cell_kernel(int n_cells, const int32_t *__restrict__ cell_pt
         for (int q = 0; q < KC; ++q) {
             if (k0 + q < k1) {
                 const float4 sx = sxs[q], sy = sys[q];
-                ax += expf((xi - sx.x) * inv_gamma) * sx.z - expf((sx.y - xi) * inv_gamma) * sx.w;
-                ay += expf((yi - sy.x) * inv_gamma) * sy.z - expf((sy.y - yi) * inv_gamma) * sy.w;
+                ax += exp2f((xi - sx.x) * k2) * sx.z - exp2f((sx.y - xi) * k2) * sx.w;
+                ay += exp2f((yi - sy.x) * k2) * sy.z - exp2f((sy.y - yi) * k2) * sy.w;
             }
         }
         for (int b = k0 + KC; b < k1; b += KC) {      // the rest KC at a time, in order
@@ -180,8 +183,8 @@ __global__ void lse_cell_kernel(int n_cells, const int32_t *__restrict__ cell_pt
             for (int q = 0; q < KC; ++q) {
                 if (b + q < k1) {
                     const float4 sx = sxs[q], sy = sys[q];
-                    ax += expf((xi - sx.x) * inv_gamma) * sx.z - expf((sx.y - xi) * inv_gamma) * sx.w;
-                    ay += expf((yi - sy.x) * inv_gamma) * sy.z - expf((sy.y - yi) * inv_gamma) * sy.w;
+                    ax += exp2f((xi - sx.x) * k2) * sx.z - exp2f((sx.y - xi) * k2) * sx.w;
+                    ay += exp2f((yi - sy.x) * k2) * sy.z - exp2f((sy.y - yi) * k2) * sy.w;
                 }
             }
         }
