@@ -44,14 +44,13 @@ SM_COUNT_GB300 = 152
 
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the
-# tensor-core kernels on this workload, from one `ncu --set full` capture each
-# (profiles/tc_coeff_tf32_cellmix-200k-512x512.md and
-# profiles/tc_energy_tf32_cellmix-200k-512x512.md), valid only while the kernel
-# sources hash to the digest they were captured with.
+# tensor-core kernels on this workload, from one ncu capture of the bench command
+# (profiles/tc_traffic_cellmix-200k-512x512.md), valid only while the kernel sources
+# hash to the digest they were captured with.
 NCU_TRAFFIC = {
-    "digest": "a7f795751c479221",
-    ("tf32", "coeff"): 25.635328e6 + 0.703488e6,
-    ("tf32", "energy"): 26.686976e6 + 0.0,
+    "digest": "224fa4164969ab3b",
+    ("tf32", "coeff"): 25.636096e6 + 0.367616e6,
+    ("tf32", "energy"): 26.693632e6 + 0.0,
 }
 
 

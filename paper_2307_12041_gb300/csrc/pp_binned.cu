@@ -379,106 +379,126 @@ __global__ void __launch_bounds__(128) fft_rows_warp_kernel(const RowJobs jobs, 
     __syncthreads();
     const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
     const int r = blockIdx.x * 4 + wp;
-    if (r >= nrows) return;                                  // no block-wide barrier below
-    float *xw = xs[wp];
-    const float *row = in + (size_t)r * in_ld;
-    for (int i = lane; i < kin; i += 32) {
-        const float v = row[i];
-        xw[pad(i)] = (MODE != T_DCT2 && in_scale != 0.f) ? v * ((float)i * in_scale) : v;   // s_u c_u
-    }
-    if (MODE == T_DCT2 && dif) {
-        // the bin density's row: plus the prefix sums of the difference array's row (the
-        // large blocks' interiors, bin_density_kernel); lane L sums entries R L .. R L + R - 1
+    const bool live = r < nrows;                             // warp-uniform
+    if (live) {
+        float *xw = xs[wp];
+        const float *row = in + (size_t)r * in_ld;
+        for (int i = lane; i < kin; i += 32) {
+            const float v = row[i];
+            xw[pad(i)] = (MODE != T_DCT2 && in_scale != 0.f) ? v * ((float)i * in_scale) : v;   // s_u c_u
+        }
+        if (MODE == T_DCT2 && dif) {
+            // the bin density's row: plus the prefix sums of the difference array's row (the
+            // large blocks' interiors, bin_density_kernel); lane L sums entries R L .. R L + R - 1
+            __syncwarp();
+            const float4 *d4 = reinterpret_cast<const float4 *>(dif + (size_t)r * in_ld + R * lane);
+            float pre[R];
+    #pragma unroll
+            for (int q = 0; q < R / 4; ++q) {
+                const float4 v = d4[q];
+                pre[4 * q] = v.x;
+                pre[4 * q + 1] = v.y;
+                pre[4 * q + 2] = v.z;
+                pre[4 * q + 3] = v.w;
+            }
+    #pragma unroll
+            for (int q = 1; q < R; ++q) pre[q] += pre[q - 1];
+            float t = pre[R - 1];                                // inclusive scan of the lanes' totals
+    #pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                const float o = __shfl_up_sync(0xffffffffu, t, off);
+                if (lane >= off) t += o;
+            }
+            const float before = t - pre[R - 1];
+    #pragma unroll
+            for (int q = 0; q < R; ++q) xw[pad(R * lane + q)] += before + pre[q];
+        }
         __syncwarp();
-        const float4 *d4 = reinterpret_cast<const float4 *>(dif + (size_t)r * in_ld + R * lane);
-        float pre[R];
-#pragma unroll
-        for (int q = 0; q < R / 4; ++q) {
-            const float4 v = d4[q];
-            pre[4 * q] = v.x;
-            pre[4 * q + 1] = v.y;
-            pre[4 * q + 2] = v.z;
-            pre[4 * q + 3] = v.w;
-        }
-#pragma unroll
-        for (int q = 1; q < R; ++q) pre[q] += pre[q - 1];
-        float t = pre[R - 1];                                // inclusive scan of the lanes' totals
-#pragma unroll
-        for (int off = 1; off < 32; off <<= 1) {
-            const float o = __shfl_up_sync(0xffffffffu, t, off);
-            if (lane >= off) t += o;
-        }
-        const float before = t - pre[R - 1];
-#pragma unroll
-        for (int q = 0; q < R; ++q) xw[pad(R * lane + q)] += before + pre[q];
-    }
-    __syncwarp();
-    auto W = [&](int j) -> float2 { return tw[j & (m - 1)]; };   // W^j, any j >= 0
-    auto coef = [&](int u) -> float { return u >= 0 && u < kin ? xw[pad(u)] : 0.f; };
-    float2 a[R];
-#pragma unroll
-    for (int n2 = 0; n2 < R; ++n2) {
-        const int n = R * lane + n2;
-        if (MODE == T_DCT2) {
-            const int src = n < half ? 2 * n : 2 * (m - 1 - n) + 1;
-            a[n2] = make_float2(coef(src), 0.f);
-        } else {
-            const float cu = !DST ? coef(n) : (n == 0 ? 0.f : coef(m - n));
-            const float cmu = n == 0 ? 0.f : (!DST ? coef(m - n) : coef(n));
-            const float2 q = qw[pad(n)];
-            a[n2] = make_float2(q.x * cu + q.y * cmu, q.y * cu - q.x * cmu);
-        }
-    }
-    const float c0 = INV && !DST ? coef(0) : 0.f;
-    // 32-point transforms across the lanes: pairs (i, i + h), i with bit h clear:
-    // y_i <- y_i + y_{i+h}, y_{i+h} <- (y_i - y_{i+h}) W_{2h}^{i mod h}
-#pragma unroll
-    for (int h = 16; h >= 1; h >>= 1) {
-        // y_i + y_{i+h} = (o + a) * 1 on the lanes with bit h clear, (o - a) W otherwise
-        const bool hi = (lane & h) != 0;
-        const float sg = hi ? -1.f : 1.f;
-        const float2 w = hi ? W((lane & (h - 1)) * (m / (2 * h))) : make_float2(1.f, 0.f);
-#pragma unroll
+        auto W = [&](int j) -> float2 { return tw[j & (m - 1)]; };   // W^j, any j >= 0
+        auto coef = [&](int u) -> float { return u >= 0 && u < kin ? xw[pad(u)] : 0.f; };
+        float2 a[R];
+    #pragma unroll
         for (int n2 = 0; n2 < R; ++n2) {
-            const float ox = __shfl_xor_sync(0xffffffffu, a[n2].x, h);
-            const float oy = __shfl_xor_sync(0xffffffffu, a[n2].y, h);
-            a[n2] = cmul(make_float2(fmaf(sg, a[n2].x, ox), fmaf(sg, a[n2].y, oy)), w);
+            const int n = R * lane + n2;
+            if (MODE == T_DCT2) {
+                const int src = n < half ? 2 * n : 2 * (m - 1 - n) + 1;
+                a[n2] = make_float2(coef(src), 0.f);
+            } else {
+                const float cu = !DST ? coef(n) : (n == 0 ? 0.f : coef(m - n));
+                const float cmu = n == 0 ? 0.f : (!DST ? coef(m - n) : coef(n));
+                const float2 q = qw[pad(n)];
+                a[n2] = make_float2(q.x * cu + q.y * cmu, q.y * cu - q.x * cmu);
+            }
         }
-    }
-    const int k1 = (int)(__brev((unsigned)lane) >> 27);
-#pragma unroll
-    for (int n2 = 1; n2 < R; ++n2) a[n2] = cmul(a[n2], W(n2 * k1));
-    // R-point transforms in registers, the same butterflies with compile-time indices
-#pragma unroll
-    for (int h = R / 2; h >= 1; h >>= 1) {
-#pragma unroll
-        for (int i = 0; i < R; ++i) {
-            if (i & h) continue;
-            const float2 u = a[i], v = a[i + h];
-            a[i] = make_float2(u.x + v.x, u.y + v.y);
-            a[i + h] = cmul(make_float2(u.x - v.x, u.y - v.y), W((i & (h - 1)) * (m / (2 * h))));
+        const float c0 = INV && !DST ? coef(0) : 0.f;
+        // 32-point transforms across the lanes: pairs (i, i + h), i with bit h clear:
+        // y_i <- y_i + y_{i+h}, y_{i+h} <- (y_i - y_{i+h}) W_{2h}^{i mod h}
+    #pragma unroll
+        for (int h = 16; h >= 1; h >>= 1) {
+            // y_i + y_{i+h} = (o + a) * 1 on the lanes with bit h clear, (o - a) W otherwise
+            const bool hi = (lane & h) != 0;
+            const float sg = hi ? -1.f : 1.f;
+            const float2 w = hi ? W((lane & (h - 1)) * (m / (2 * h))) : make_float2(1.f, 0.f);
+    #pragma unroll
+            for (int n2 = 0; n2 < R; ++n2) {
+                const float ox = __shfl_xor_sync(0xffffffffu, a[n2].x, h);
+                const float oy = __shfl_xor_sync(0xffffffffu, a[n2].y, h);
+                a[n2] = cmul(make_float2(fmaf(sg, a[n2].x, ox), fmaf(sg, a[n2].y, oy)), w);
+            }
         }
-    }
-    // a[j] = Y_k, k = k1 + 32 bitreverse(j) over log2 R bits: results to the warp buffer at
-    // their output positions, then out in order
-    constexpr int LR = R == 16 ? 4 : 5;
-    __syncwarp();                                            // every lane has read its inputs
-#pragma unroll
-    for (int j = 0; j < R; ++j) {
-        const int k = k1 + 32 * (int)(__brev((unsigned)j) >> (32 - LR));
-        if (MODE == T_DCT2) {
-            const float2 q = qw[pad(k)];
-            xw[pad(k)] = a[j].x * q.x + a[j].y * q.y;
-        } else {
-            const int l = k < half ? 2 * k : 2 * (m - 1 - k) + 1;
-            const float t = 0.5f * (a[j].x + c0);
-            xw[pad(l)] = (DST && (l & 1)) ? -t : t;
+        const int k1 = (int)(__brev((unsigned)lane) >> 27);
+    #pragma unroll
+        for (int n2 = 1; n2 < R; ++n2) a[n2] = cmul(a[n2], W(n2 * k1));
+        // R-point transforms in registers, the same butterflies with compile-time indices
+    #pragma unroll
+        for (int h = R / 2; h >= 1; h >>= 1) {
+    #pragma unroll
+            for (int i = 0; i < R; ++i) {
+                if (i & h) continue;
+                const float2 u = a[i], v = a[i + h];
+                a[i] = make_float2(u.x + v.x, u.y + v.y);
+                a[i + h] = cmul(make_float2(u.x - v.x, u.y - v.y), W((i & (h - 1)) * (m / (2 * h))));
+            }
         }
+        // a[j] = Y_k, k = k1 + 32 bitreverse(j) over log2 R bits: results to the warp buffer at
+        // their output positions, then out in order
+        constexpr int LR = R == 16 ? 4 : 5;
+        __syncwarp();                                            // every lane has read its inputs
+    #pragma unroll
+        for (int j = 0; j < R; ++j) {
+            const int k = k1 + 32 * (int)(__brev((unsigned)j) >> (32 - LR));
+            if (MODE == T_DCT2) {
+                const float2 q = qw[pad(k)];
+                xw[pad(k)] = a[j].x * q.x + a[j].y * q.y;
+            } else {
+                const int l = k < half ? 2 * k : 2 * (m - 1 - k) + 1;
+                const float t = 0.5f * (a[j].x + c0);
+                xw[pad(l)] = (DST && (l & 1)) ? -t : t;
+            }
+        }
+        __syncwarp();
     }
-    __syncwarp();
-    float *orow = out + (size_t)r * out_ld;
     const int nout = MODE == T_DCT2 ? keep : m;
-    for (int i = lane; i < nout; i += 32) orow[(size_t)i * ostr] = xw[pad(i)];
+    if (out_ld != 1) {
+        if (live) {
+            float *orow = out + (size_t)r * out_ld;
+            for (int i = lane; i < nout; i += 32) orow[(size_t)i * ostr] = xs[wp][pad(i)];
+        }
+        return;
+    }
+    // transposed output (out_ld = 1: row r's outputs go down column r): the CTA's four
+    // rows are adjacent there and are written together, 16 bytes per output index
+    __syncthreads();
+    const int r0 = blockIdx.x * 4;
+    const bool vec = r0 + 3 < nrows && (ostr & 3) == 0 && ((uintptr_t)out & 15) == 0;
+    for (int i = threadIdx.x; i < nout; i += blockDim.x) {
+        float *o = out + (size_t)i * ostr + r0;
+        if (vec) {
+            *reinterpret_cast<float4 *>(o) = make_float4(xs[0][pad(i)], xs[1][pad(i)], xs[2][pad(i)], xs[3][pad(i)]);
+        } else {
+            for (int q = 0; q < 4 && r0 + q < nrows; ++q) o[q] = xs[q][pad(i)];
+        }
+    }
 }
 
 // m = 1024 with two warps per row (twice the warps of fft_rows_warp_kernel, half the
@@ -515,117 +535,137 @@ __global__ void __launch_bounds__(128) fft_rows_pair_kernel(const RowJobs jobs, 
     const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
     const int rr = wp >> 1, h = wp & 1;                      // row within the CTA, warp within the row
     const int r = blockIdx.x * 2 + rr;
-    if (r >= nrows) return;                                  // both warps of the row together
-    const int bar = 1 + rr;
-    auto row_sync = [&]() { asm volatile("bar.sync %0, 64;" ::"r"(bar) : "memory"); };
-    float *xw = xs[rr];
-    const float *row = in + (size_t)r * in_ld;
-    for (int i = threadIdx.x & 63; i < kin; i += 64) {
-        const float v = row[i];
-        xw[pad(i)] = (MODE != T_DCT2 && in_scale != 0.f) ? v * ((float)i * in_scale) : v;   // s_u c_u
-    }
-    if (MODE == T_DCT2 && dif) {
-        // the difference array's row prefix sums (as fft_rows_warp_kernel), by warp 0 of the row
+    const bool live = r < nrows;                             // the same for the row's two warps
+    if (live) {
+        const int bar = 1 + rr;
+        auto row_sync = [&]() { asm volatile("bar.sync %0, 64;" ::"r"(bar) : "memory"); };
+        float *xw = xs[rr];
+        const float *row = in + (size_t)r * in_ld;
+        for (int i = threadIdx.x & 63; i < kin; i += 64) {
+            const float v = row[i];
+            xw[pad(i)] = (MODE != T_DCT2 && in_scale != 0.f) ? v * ((float)i * in_scale) : v;   // s_u c_u
+        }
+        if (MODE == T_DCT2 && dif) {
+            // the difference array's row prefix sums (as fft_rows_warp_kernel), by warp 0 of the row
+            row_sync();
+            if (h == 0) {
+                const float4 *d4 = reinterpret_cast<const float4 *>(dif + (size_t)r * in_ld + R * lane);
+                float pre[R];
+    #pragma unroll
+                for (int q = 0; q < R / 4; ++q) {
+                    const float4 v = d4[q];
+                    pre[4 * q] = v.x;
+                    pre[4 * q + 1] = v.y;
+                    pre[4 * q + 2] = v.z;
+                    pre[4 * q + 3] = v.w;
+                }
+    #pragma unroll
+                for (int q = 1; q < R; ++q) pre[q] += pre[q - 1];
+                float t = pre[R - 1];
+    #pragma unroll
+                for (int off = 1; off < 32; off <<= 1) {
+                    const float o = __shfl_up_sync(0xffffffffu, t, off);
+                    if (lane >= off) t += o;
+                }
+                const float before = t - pre[R - 1];
+    #pragma unroll
+                for (int q = 0; q < R; ++q) xw[pad(R * lane + q)] += before + pre[q];
+            }
+        }
         row_sync();
-        if (h == 0) {
-            const float4 *d4 = reinterpret_cast<const float4 *>(dif + (size_t)r * in_ld + R * lane);
-            float pre[R];
-#pragma unroll
-            for (int q = 0; q < R / 4; ++q) {
-                const float4 v = d4[q];
-                pre[4 * q] = v.x;
-                pre[4 * q + 1] = v.y;
-                pre[4 * q + 2] = v.z;
-                pre[4 * q + 3] = v.w;
-            }
-#pragma unroll
-            for (int q = 1; q < R; ++q) pre[q] += pre[q - 1];
-            float t = pre[R - 1];
-#pragma unroll
-            for (int off = 1; off < 32; off <<= 1) {
-                const float o = __shfl_up_sync(0xffffffffu, t, off);
-                if (lane >= off) t += o;
-            }
-            const float before = t - pre[R - 1];
-#pragma unroll
-            for (int q = 0; q < R; ++q) xw[pad(R * lane + q)] += before + pre[q];
-        }
-    }
-    row_sync();
-    auto W = [&](int j) -> float2 { return tw[j & (m - 1)]; };   // W^j, any j >= 0
-    auto coef = [&](int u) -> float { return u >= 0 && u < kin ? xw[pad(u)] : 0.f; };
-    float2 a[H];
-#pragma unroll
-    for (int i = 0; i < H; ++i) {
-        const int n = R * lane + H * h + i;
-        if (MODE == T_DCT2) {
-            const int src = n < half ? 2 * n : 2 * (m - 1 - n) + 1;
-            a[i] = make_float2(coef(src), 0.f);
-        } else {
-            const float cu = !DST ? coef(n) : (n == 0 ? 0.f : coef(m - n));
-            const float cmu = n == 0 ? 0.f : (!DST ? coef(m - n) : coef(n));
-            const float2 q = qw[pad(n)];
-            a[i] = make_float2(q.x * cu + q.y * cmu, q.y * cu - q.x * cmu);
-        }
-    }
-    const float c0 = INV && !DST ? coef(0) : 0.f;
-#pragma unroll
-    for (int hh = 16; hh >= 1; hh >>= 1) {
-        const bool hi = (lane & hh) != 0;
-        const float sg = hi ? -1.f : 1.f;
-        const float2 w = hi ? W((lane & (hh - 1)) * (m / (2 * hh))) : make_float2(1.f, 0.f);
-#pragma unroll
+        auto W = [&](int j) -> float2 { return tw[j & (m - 1)]; };   // W^j, any j >= 0
+        auto coef = [&](int u) -> float { return u >= 0 && u < kin ? xw[pad(u)] : 0.f; };
+        float2 a[H];
+    #pragma unroll
         for (int i = 0; i < H; ++i) {
-            const float ox = __shfl_xor_sync(0xffffffffu, a[i].x, hh);
-            const float oy = __shfl_xor_sync(0xffffffffu, a[i].y, hh);
-            a[i] = cmul(make_float2(fmaf(sg, a[i].x, ox), fmaf(sg, a[i].y, oy)), w);
+            const int n = R * lane + H * h + i;
+            if (MODE == T_DCT2) {
+                const int src = n < half ? 2 * n : 2 * (m - 1 - n) + 1;
+                a[i] = make_float2(coef(src), 0.f);
+            } else {
+                const float cu = !DST ? coef(n) : (n == 0 ? 0.f : coef(m - n));
+                const float cmu = n == 0 ? 0.f : (!DST ? coef(m - n) : coef(n));
+                const float2 q = qw[pad(n)];
+                a[i] = make_float2(q.x * cu + q.y * cmu, q.y * cu - q.x * cmu);
+            }
         }
-    }
-    const int k1 = (int)(__brev((unsigned)lane) >> 27);
-#pragma unroll
-    for (int i = 0; i < H; ++i) {
-        const int n2 = H * h + i;
-        if (n2 > 0) a[i] = cmul(a[i], W(n2 * k1));
-    }
-    // the first butterflies of the 32-point transform over n2, across the row's two warps
-#pragma unroll
-    for (int i = 0; i < H; ++i) xch[rr][h][i][lane] = a[i];
-    row_sync();
-#pragma unroll
-    for (int i = 0; i < H; ++i) {
-        const float2 o = xch[rr][1 - h][i][lane];
-        if (h == 0) a[i] = make_float2(a[i].x + o.x, a[i].y + o.y);                          // y_i + y_{i+16}
-        else a[i] = cmul(make_float2(o.x - a[i].x, o.y - a[i].y), W(i * (m / 32)));          // (y_i - y_{i+16}) W_32^i
-    }
-    // 16-point transforms in registers (W_16 = W_m^{m/16})
-#pragma unroll
-    for (int hh = H / 2; hh >= 1; hh >>= 1) {
-#pragma unroll
+        const float c0 = INV && !DST ? coef(0) : 0.f;
+    #pragma unroll
+        for (int hh = 16; hh >= 1; hh >>= 1) {
+            const bool hi = (lane & hh) != 0;
+            const float sg = hi ? -1.f : 1.f;
+            const float2 w = hi ? W((lane & (hh - 1)) * (m / (2 * hh))) : make_float2(1.f, 0.f);
+    #pragma unroll
+            for (int i = 0; i < H; ++i) {
+                const float ox = __shfl_xor_sync(0xffffffffu, a[i].x, hh);
+                const float oy = __shfl_xor_sync(0xffffffffu, a[i].y, hh);
+                a[i] = cmul(make_float2(fmaf(sg, a[i].x, ox), fmaf(sg, a[i].y, oy)), w);
+            }
+        }
+        const int k1 = (int)(__brev((unsigned)lane) >> 27);
+    #pragma unroll
         for (int i = 0; i < H; ++i) {
-            if (i & hh) continue;
-            const float2 u = a[i], v = a[i + hh];
-            a[i] = make_float2(u.x + v.x, u.y + v.y);
-            a[i + hh] = cmul(make_float2(u.x - v.x, u.y - v.y), W((i & (hh - 1)) * (m / (2 * hh))));
+            const int n2 = H * h + i;
+            if (n2 > 0) a[i] = cmul(a[i], W(n2 * k1));
         }
-    }
-    // a[j] = Y_k, k = k1 + 32 (2 bitreverse4(j) + h); every lane of both warps has read its
-    // inputs (before the exchange barrier), so the row buffer takes the results
-#pragma unroll
-    for (int j = 0; j < H; ++j) {
-        const int k = k1 + 32 * (2 * (int)(__brev((unsigned)j) >> 28) + h);
-        if (MODE == T_DCT2) {
-            const float2 q = qw[pad(k)];
-            xw[pad(k)] = a[j].x * q.x + a[j].y * q.y;
-        } else {
-            const int l = k < half ? 2 * k : 2 * (m - 1 - k) + 1;
-            const float t = 0.5f * (a[j].x + c0);
-            xw[pad(l)] = (DST && (l & 1)) ? -t : t;
+        // the first butterflies of the 32-point transform over n2, across the row's two warps
+    #pragma unroll
+        for (int i = 0; i < H; ++i) xch[rr][h][i][lane] = a[i];
+        row_sync();
+    #pragma unroll
+        for (int i = 0; i < H; ++i) {
+            const float2 o = xch[rr][1 - h][i][lane];
+            if (h == 0) a[i] = make_float2(a[i].x + o.x, a[i].y + o.y);                          // y_i + y_{i+16}
+            else a[i] = cmul(make_float2(o.x - a[i].x, o.y - a[i].y), W(i * (m / 32)));          // (y_i - y_{i+16}) W_32^i
         }
+        // 16-point transforms in registers (W_16 = W_m^{m/16})
+    #pragma unroll
+        for (int hh = H / 2; hh >= 1; hh >>= 1) {
+    #pragma unroll
+            for (int i = 0; i < H; ++i) {
+                if (i & hh) continue;
+                const float2 u = a[i], v = a[i + hh];
+                a[i] = make_float2(u.x + v.x, u.y + v.y);
+                a[i + hh] = cmul(make_float2(u.x - v.x, u.y - v.y), W((i & (hh - 1)) * (m / (2 * hh))));
+            }
+        }
+        // a[j] = Y_k, k = k1 + 32 (2 bitreverse4(j) + h); every lane of both warps has read its
+        // inputs (before the exchange barrier), so the row buffer takes the results
+    #pragma unroll
+        for (int j = 0; j < H; ++j) {
+            const int k = k1 + 32 * (2 * (int)(__brev((unsigned)j) >> 28) + h);
+            if (MODE == T_DCT2) {
+                const float2 q = qw[pad(k)];
+                xw[pad(k)] = a[j].x * q.x + a[j].y * q.y;
+            } else {
+                const int l = k < half ? 2 * k : 2 * (m - 1 - k) + 1;
+                const float t = 0.5f * (a[j].x + c0);
+                xw[pad(l)] = (DST && (l & 1)) ? -t : t;
+            }
+        }
+        row_sync();
     }
-    row_sync();
-    float *orow = out + (size_t)r * out_ld;
     const int nout = MODE == T_DCT2 ? keep : m;
-    for (int i = threadIdx.x & 63; i < nout; i += 64) orow[(size_t)i * ostr] = xw[pad(i)];
+    if (out_ld != 1) {
+        if (live) {
+            float *orow = out + (size_t)r * out_ld;
+            for (int i = threadIdx.x & 63; i < nout; i += 64) orow[(size_t)i * ostr] = xs[rr][pad(i)];
+        }
+        return;
+    }
+    // transposed output (out_ld = 1: row r's outputs go down column r): the CTA's two
+    // rows are adjacent there and are written together, 8 bytes per output index
+    __syncthreads();
+    const int r0 = blockIdx.x * 2;
+    const bool vec = r0 + 1 < nrows && (ostr & 1) == 0 && ((uintptr_t)out & 7) == 0;
+    for (int i = threadIdx.x; i < nout; i += blockDim.x) {
+        float *o = out + (size_t)i * ostr + r0;
+        if (vec) {
+            *reinterpret_cast<float2 *>(o) = make_float2(xs[0][pad(i)], xs[1][pad(i)]);
+        } else {
+            for (int q = 0; q < 2 && r0 + q < nrows; ++q) o[q] = xs[q][pad(i)];
+        }
+    }
 }
 
 // The same transforms for any m: direct sums over a table cos(pi q / 2m), q < 4m
