@@ -126,17 +126,22 @@ __global__ void bin_density_kernel(const float *__restrict__ x, const float *__r
             const long long bx0 = __shfl_sync(0xffffffffu, x0, src), bx1 = __shfl_sync(0xffffffffu, x1, src);
             const long long by0 = __shfl_sync(0xffffffffu, y0, src), by1 = __shfl_sync(0xffffffffu, y1, src);
             const int bl0 = __shfl_sync(0xffffffffu, l0, src), bj0 = __shfl_sync(0xffffffffu, j0, src);
-            const long long bnl = __shfl_sync(0xffffffffu, nl, src);
-            const long long bnj = __shfl_sync(0xffffffffu, nj, src), tot = bnj * bnl;
+            const int bnl = (int)__shfl_sync(0xffffffffu, nl, src), bnj = (int)__shfl_sync(0xffffffffu, nj, src);
             const float bc = __shfl_sync(0xffffffffu, ci, src);
+            const int bl1 = bl0 + bnl - 1, bj1 = bj0 + bnj - 1;
+            // as for small blocks, only the edge bins of each axis can be partly covered
+            const float ax0 = (float)overlap(bx0, bx1, bl0) * unit, ax1 = (float)overlap(bx0, bx1, bl1) * unit;
+            const float ay0 = (float)overlap(by0, by1, bj0) * unit, ay1 = (float)overlap(by0, by1, bj1) * unit;
+            auto fx_of = [&](int l) { return l == bl0 ? ax0 : (l == bl1 ? ax1 : 1.f); };
+            auto fy_of = [&](int j) { return j == bj0 ? ay0 : (j == bj1 ? ay1 : 1.f); };
             if (D && bnj >= 3) {
-                const int ja = bj0, jb = bj0 + (int)bnj - 1;
-                const float fa = (float)overlap(by0, by1, ja) * unit, fb = (float)overlap(by0, by1, jb) * unit;
-                for (long long r = lane; r < bnl; r += 32) {
-                    const int l = bl0 + (int)r;
-                    const long long ox = overlap(bx0, bx1, l);
-                    if (ox <= 0) continue;
-                    const float cx = bc * ((float)ox * unit);
+                const int ja = bj0, jb = bj1;
+                const float fa = ay0, fb = ay1;
+                for (int r = lane; r < bnl; r += 32) {
+                    const int l = bl0 + r;
+                    const float fx = fx_of(l);
+                    if (!(fx > 0.f)) continue;
+                    const float cx = bc * fx;
                     float *Pr = P + (size_t)l * m, *Dr = D + (size_t)l * m;
                     if (fa > 0.f) atomicAdd(Pr + ja, cx * fa);
                     if (fb > 0.f) atomicAdd(Pr + jb, cx * fb);
@@ -145,11 +150,27 @@ __global__ void bin_density_kernel(const float *__restrict__ x, const float *__r
                 }
                 continue;
             }
-            for (long long k = lane; k < tot; k += 32) {
-                const int l = bl0 + (int)(k / bnj), j = bj0 + (int)(k % bnj);
-                const long long ox = overlap(bx0, bx1, l), oy = overlap(by0, by1, j);
-                if (ox > 0 && oy > 0)
-                    atomicAdd(&P[(size_t)l * m + j], bc * ((float)ox * unit) * ((float)oy * unit));
+            // the block's bins shared out over the lanes: rows of up to 32 bins take
+            // 32 / bnj rows per round (lane = row offset * bnj + column), longer rows
+            // their columns 32 at a time
+            if (bnj <= 32) {
+                const int per = 32 / bnj, lr = lane / bnj, j = bj0 + (lane - lr * bnj);
+                if (lr < per) {
+                    const float fy = fy_of(j);
+                    for (int r = lr; r < bnl; r += per) {
+                        const int l = bl0 + r;
+                        const float fx = fx_of(l);
+                        if (fx > 0.f && fy > 0.f) atomicAdd(&P[(size_t)l * m + j], bc * fx * fy);
+                    }
+                }
+            } else {
+                for (int l = bl0; l <= bl1; ++l) {
+                    const float fx = fx_of(l);
+                    for (int j = bj0 + lane; j <= bj1; j += 32) {
+                        const float fy = fy_of(j);
+                        if (fx > 0.f && fy > 0.f) atomicAdd(&P[(size_t)l * m + j], bc * fx * fy);
+                    }
+                }
             }
         }
     }
