@@ -174,7 +174,8 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // Coefficient contraction, FP32: CTA tile 128 (u) x 128 (v), a slice of blocks.
 // ---------------------------------------------------------------------------
 constexpr int CT = 128;   // tile edge
-constexpr int CKC = 16;   // blocks per shared-memory chunk
+constexpr int CKC = 32;   // blocks per shared-memory chunk
+constexpr int CKS = 32;   // blocks summed in plain FP32 before each compensated add (divides CKC)
 
 struct CoeffSmem {
     float Xs[2][CKC][CT];
@@ -205,21 +206,26 @@ coeff_simt_kernel(const AxisRec *__restrict__ xr, const AxisRec *__restrict__ yr
     // generator mapping: chunk row gk, modes gm..gm+7
     const int gk = tid >> 4, gm = (tid & 15) * 8;
 
-    // Each chunk of CKC blocks is summed into fresh registers, then added to a
+    // Every CKS blocks of a chunk are summed into fresh registers, then added to a
     // compensated running sum (hi in registers, lo in shared memory; error-free
-    // two-sum), so the FP32 rounding does not grow with the slice length.
-    float hi[8][8];
+    // two-sum), so the FP32 rounding does not grow with the slice length.  Both run
+    // on pairs of adjacent v (packed f32x2 FMA and add: one instruction per two
+    // lanes' worth of FMA-pipe work, each half rounded exactly as the scalar
+    // operation), which leaves issue slots for the loads, the generator and the sums.
+    const float2 m1 = make_float2(-1.f, -1.f);            // fma(x, -1, y) = y - x, one rounding
+    float2 hi[8][4];
+    float2 *lo_s2 = reinterpret_cast<float2 *>(lo_s);     // [i*4+jj][thread]
 #pragma unroll
     for (int i = 0; i < 8; ++i)
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            hi[i][j] = 0.f;
-            lo_s[(i * 8 + j) * 256 + tid] = 0.f;
+        for (int jj = 0; jj < 4; ++jj) {
+            hi[i][jj] = make_float2(0.f, 0.f);
+            lo_s2[(i * 4 + jj) * 256 + tid] = make_float2(0.f, 0.f);
         }
 
     const int nchunks = (b1 - b0 + CKC - 1) / CKC;
     // The records of chunk ch + 1 are copied to shared memory (cp.async) while
-    // chunk ch is multiplied: 16 blocks x 2 axes x 64 bytes = 128 x 16-byte pieces.
+    // chunk ch is multiplied: 32 blocks x 2 axes x 64 bytes = 256 x 16-byte pieces.
     auto fetch_recs = [&](int ch, int buf) {
         if (tid < 2 * CKC * 4) {
             const int axis = tid / (CKC * 4), r = tid % (CKC * 4);
@@ -238,57 +244,76 @@ coeff_simt_kernel(const AxisRec *__restrict__ xr, const AxisRec *__restrict__ yr
         const int buf = ch & 1;
         cp_async_wait_all();
         __syncthreads();
-        float vx[8], vy[8];
-        if (b0 + ch * CKC + gk < b1) {
-            rect_run8(Rs[buf][0][gk], u_base + gm, vx);
-            rect_run8(Rs[buf][1][gk], v_base + gm, vy);
-        } else {
 #pragma unroll
-            for (int j = 0; j < 8; ++j) vx[j] = vy[j] = 0.f;
+        for (int g2 = 0; g2 < CKC; g2 += 16) {             // chunk rows gk and gk + 16
+            const int row = gk + g2;
+            float vx[8], vy[8];
+            if (b0 + ch * CKC + row < b1) {
+                rect_run8(Rs[buf][0][row], u_base + gm, vx);
+                rect_run8(Rs[buf][1][row], v_base + gm, vy);
+            } else {
+#pragma unroll
+                for (int j = 0; j < 8; ++j) vx[j] = vy[j] = 0.f;
+            }
+            *reinterpret_cast<float4 *>(&Xs[buf][row][gm]) = make_float4(vx[0], vx[1], vx[2], vx[3]);
+            *reinterpret_cast<float4 *>(&Xs[buf][row][gm + 4]) = make_float4(vx[4], vx[5], vx[6], vx[7]);
+            *reinterpret_cast<float4 *>(&Ys[buf][row][gm]) = make_float4(vy[0], vy[1], vy[2], vy[3]);
+            *reinterpret_cast<float4 *>(&Ys[buf][row][gm + 4]) = make_float4(vy[4], vy[5], vy[6], vy[7]);
         }
         if (ch + 1 < nchunks) fetch_recs(ch + 1, buf ^ 1);
-        *reinterpret_cast<float4 *>(&Xs[buf][gk][gm]) = make_float4(vx[0], vx[1], vx[2], vx[3]);
-        *reinterpret_cast<float4 *>(&Xs[buf][gk][gm + 4]) = make_float4(vx[4], vx[5], vx[6], vx[7]);
-        *reinterpret_cast<float4 *>(&Ys[buf][gk][gm]) = make_float4(vy[0], vy[1], vy[2], vy[3]);
-        *reinterpret_cast<float4 *>(&Ys[buf][gk][gm + 4]) = make_float4(vy[4], vy[5], vy[6], vy[7]);
         __syncthreads();
-        float acc[8][8];
-#pragma unroll
-        for (int i = 0; i < 8; ++i)
-#pragma unroll
-            for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
-#pragma unroll 4
-        for (int k = 0; k < CKC; ++k) {
-            const float4 a0 = *reinterpret_cast<const float4 *>(&Xs[buf][k][ty * 4]);
-            const float4 a1 = *reinterpret_cast<const float4 *>(&Xs[buf][k][64 + ty * 4]);
-            const float4 c0 = *reinterpret_cast<const float4 *>(&Ys[buf][k][tx * 4]);
-            const float4 c1 = *reinterpret_cast<const float4 *>(&Ys[buf][k][64 + tx * 4]);
-            const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-            const float bv[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
+#pragma unroll 1
+        for (int k0 = 0; k0 < CKC; k0 += CKS) {
+            float2 acc[8][4];
 #pragma unroll
             for (int i = 0; i < 8; ++i)
 #pragma unroll
-                for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
-        }
+                for (int jj = 0; jj < 4; ++jj) acc[i][jj] = make_float2(0.f, 0.f);
+#pragma unroll 4
+            for (int k = k0; k < k0 + CKS; ++k) {
+                const float4 a0 = *reinterpret_cast<const float4 *>(&Xs[buf][k][ty * 4]);
+                const float4 a1 = *reinterpret_cast<const float4 *>(&Xs[buf][k][64 + ty * 4]);
+                const float4 c0 = *reinterpret_cast<const float4 *>(&Ys[buf][k][tx * 4]);
+                const float4 c1 = *reinterpret_cast<const float4 *>(&Ys[buf][k][64 + tx * 4]);
+                const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+                const float2 bp[4] = {make_float2(c0.x, c0.y), make_float2(c0.z, c0.w), make_float2(c1.x, c1.y),
+                                      make_float2(c1.z, c1.w)};
 #pragma unroll
-        for (int i = 0; i < 8; ++i)
+                for (int i = 0; i < 8; ++i) {
+                    const float2 ai = make_float2(av[i], av[i]);
 #pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                const float s = hi[i][j] + acc[i][j];
-                const float bb = s - hi[i][j];
-                lo_s[(i * 8 + j) * 256 + tid] += (hi[i][j] - (s - bb)) + (acc[i][j] - bb);
-                hi[i][j] = s;
+                    for (int jj = 0; jj < 4; ++jj) acc[i][jj] = __ffma2_rn(ai, bp[jj], acc[i][jj]);
+                }
             }
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+#pragma unroll
+                for (int jj = 0; jj < 4; ++jj) {
+                    const float2 h = hi[i][jj], a = acc[i][jj];
+                    const float2 sum = __fadd2_rn(h, a);
+                    const float2 bb = __ffma2_rn(h, m1, sum);                                // sum - hi
+                    const float2 e = __fadd2_rn(__ffma2_rn(__ffma2_rn(bb, m1, sum), m1, h),  // hi - (sum - bb)
+                                                __ffma2_rn(bb, m1, a));                       // + (acc - bb)
+                    float2 &l = lo_s2[(i * 4 + jj) * 256 + tid];
+                    l = __fadd2_rn(l, e);
+                    hi[i][jj] = sum;
+                }
+        }
     }
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
         const int u = u_base + (i < 4 ? ty * 4 + i : 64 + ty * 4 + i - 4);
         if (u >= Mx) continue;
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            const int v = v_base + (j < 4 ? tx * 4 + j : 64 + tx * 4 + j - 4);
-            if (v < My)
-                atomicAdd(&S64[(size_t)u * My + v], (double)hi[i][j] + (double)lo_s[(i * 8 + j) * 256 + tid]);
+        for (int jj = 0; jj < 4; ++jj) {
+            const float2 h = hi[i][jj], l = lo_s2[(i * 4 + jj) * 256 + tid];
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                const int j = 2 * jj + q;
+                const int v = v_base + (j < 4 ? tx * 4 + j : 64 + tx * 4 + j - 4);
+                if (v < My)
+                    atomicAdd(&S64[(size_t)u * My + v], (double)(q ? h.y : h.x) + (double)(q ? l.y : l.x));
+            }
         }
     }
 }
@@ -461,7 +486,8 @@ energy_simt_kernel(const AxisRec *__restrict__ xr, const AxisRec *__restrict__ y
     const int total = nuc * nvt;
 
     float eN[4] = {0.f, 0.f, 0.f, 0.f}, eX[4] = {0.f, 0.f, 0.f, 0.f}, eY[4] = {0.f, 0.f, 0.f, 0.f};
-    float T[4][8], Tp[4][8];
+    // T, T' on pairs of adjacent v (packed f32x2 FMAs, each half rounded as fmaf)
+    float2 T[4][4], Tp[4][4];
 
     const bool g_valid = blk0 + g_blk < n;
     AxisRec grec;
@@ -495,7 +521,7 @@ energy_simt_kernel(const AxisRec *__restrict__ xr, const AxisRec *__restrict__ y
 #pragma unroll
             for (int i = 0; i < 4; ++i)
 #pragma unroll
-                for (int j = 0; j < 8; ++j) T[i][j] = Tp[i][j] = 0.f;
+                for (int jj = 0; jj < 4; ++jj) T[i][jj] = Tp[i][jj] = make_float2(0.f, 0.f);
         }
         // basis chunk
         {
@@ -523,14 +549,17 @@ energy_simt_kernel(const AxisRec *__restrict__ xr, const AxisRec *__restrict__ y
             const float4 k1 = *reinterpret_cast<const float4 *>(&Ks[buf][k][64 + vt * 4]);
             const float av[4] = {a.x, a.y, a.z, a.w};
             const float bv[4] = {b.x, b.y, b.z, b.w};
-            const float kv[8] = {k0.x, k0.y, k0.z, k0.w, k1.x, k1.y, k1.z, k1.w};
+            const float2 kp[4] = {make_float2(k0.x, k0.y), make_float2(k0.z, k0.w), make_float2(k1.x, k1.y),
+                                  make_float2(k1.z, k1.w)};
 #pragma unroll
-            for (int i = 0; i < 4; ++i)
+            for (int i = 0; i < 4; ++i) {
+                const float2 ai = make_float2(av[i], av[i]), bi = make_float2(bv[i], bv[i]);
 #pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    T[i][j] = fmaf(av[i], kv[j], T[i][j]);
-                    Tp[i][j] = fmaf(bv[i], kv[j], Tp[i][j]);
+                for (int jj = 0; jj < 4; ++jj) {
+                    T[i][jj] = __ffma2_rn(ai, kp[jj], T[i][jj]);
+                    Tp[i][jj] = __ffma2_rn(bi, kp[jj], Tp[i][jj]);
                 }
+            }
         }
         if (uc == 0) {
             // row dots for this v tile (highest v first)
@@ -547,7 +576,8 @@ energy_simt_kernel(const AxisRec *__restrict__ xr, const AxisRec *__restrict__ y
 #pragma unroll
                     for (int j = 3; j >= 0; --j) {
                         if (v0 + j < My) {
-                            const float t = T[i][half * 4 + j], tp = Tp[i][half * 4 + j];
+                            const float2 t2 = T[i][half * 2 + (j >> 1)], tp2 = Tp[i][half * 2 + (j >> 1)];
+                            const float t = (j & 1) ? t2.y : t2.x, tp = (j & 1) ? tp2.y : tp2.x;
                             eN[i] = fmaf(t, yt[j], eN[i]);
                             eY[i] = fmaf(t, yh[j], eY[i]);
                             eX[i] = fmaf(tp, yt[j], eX[i]);
