@@ -46,8 +46,10 @@ SM_COUNT_GB300 = 152
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the
 # tensor-core kernels on this workload, from one ncu capture of the bench command
 # (profiles/tc_traffic_cellmix-200k-512x512.md), valid only while the kernel sources
-# hash to the digest they were captured with.
+# hash to the digest they were captured with, and only for that workload (its
+# block·mode² terms N Mx My).
 NCU_TRAFFIC = {
+    "terms": 200_000 * 512 * 512,
     "digest": "224fa4164969ab3b",
     ("tf32", "coeff"): 25.636096e6 + 0.367616e6,
     ("tf32", "energy"): 26.693632e6 + 0.0,
@@ -68,8 +70,8 @@ def kernel_source_digest() -> str:
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(prec: str, kernel: str):
-    if kernel_source_digest() != NCU_TRAFFIC["digest"]:
+def ncu_traffic(prec: str, kernel: str, terms: float):
+    if kernel_source_digest() != NCU_TRAFFIC["digest"] or terms != NCU_TRAFFIC["terms"]:
         return None
     return NCU_TRAFFIC.get((prec, kernel))
 
@@ -438,7 +440,7 @@ def roofline(prec, ktimes, terms, peaks, peak_src):
         note = f"{peak_src} bf16 burst peak / 3 (three bf16 products per term)"
     achieved = flops / (dom_ms * 1e-3) / 1e12
     return {"bound": bound, "kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": achieved / peak, "traffic": ncu_traffic(prec, dom), "peak_source": note,
+            "frac": achieved / peak, "traffic": ncu_traffic(prec, dom, terms), "peak_source": note,
             "flops_per_launch": flops, "kernel_ms": dom_ms}
 
 
