@@ -335,8 +335,9 @@ pp_status pp_nesterov_step(int64_t n, double W, double H, float *ux, float *uy, 
 pp_status pp_overflow(const pp_problem *prob, int32_t m, float target, float *bins, double *out, void *stream);
 
 /* One iteration of the loop after the first, in one call: the work of the calls
- * below, made one after the other on `stream` (the same kernels in the same
- * order), with their scratch carved from one workspace.
+ * below, made one after the other on `stream`, with their scratch carved from one
+ * workspace.  Steps 2 (its per-cell part), 3 and 4 run as one kernel: g is what
+ * the separate calls give, the norms differ only in the order of their sums.
  *   1. gn, E      density gradient and energy at v: the exact series on M x M modes
  *                 (pp_grad, PP_RECT) or the binned scheme of Sec. III-D on M x M
  *                 bins (pp_binned_grad; prec PP_FP32 or PP_TF32);

@@ -779,10 +779,10 @@ pp_status wirelength_impl(const pp_netlist *nl, const float *x, const float *y, 
     if ((st = check_dev_ptr(ws, dev, "ws")) != PP_OK) return st;
     if ((st = check_dev_ptr(out, dev, "out")) != PP_OK) return st;
     if (((uintptr_t)out & 7) != 0) return fail(PP_EINVAL, "out is not 8-byte aligned");
-    if (nl->n_cells > 0) {
+    if (nl->n_cells > 0) {            // gx == gy == NULL: the per-net pass only (internal use)
         const void *ptrs[4] = {x, y, gx, gy};
         const char *names[4] = {"x", "y", "gx", "gy"};
-        if ((st = check_arrays(dev, 4, ptrs, names)) != PP_OK) return st;
+        if ((st = check_arrays(dev, gx ? 4 : 2, ptrs, names)) != PP_OK) return st;
     }
     cudaError_t e = launch_wirelength(nl->n_nets, nl->n_cells, nl->net_ptr, nl->net_pin, nl->cell_ptr,
                                       nl->cell_net, x, y, gamma, scal, (float *)ws, gx, gy, out, sm,
@@ -861,6 +861,7 @@ pp_status pp_step_norms(int64_t n, const float *vx, const float *vy, const float
 
 pp_status pp_wirelength(const pp_netlist *nl, const float *x, const float *y, float gamma, float *gx, float *gy,
                         double *out, void *ws, size_t ws_bytes, void *stream) {
+    if (nl && nl->n_cells > 0 && (!gx || !gy)) return fail(PP_EINVAL, "gx, gy must not be NULL");
     return wirelength_impl(nl, x, y, gamma, nullptr, gx, gy, out, ws, ws_bytes, stream);
 }
 
@@ -980,7 +981,7 @@ pp_status pp_place_iteration(const pp_place_iteration_args *a, void *ws, size_t 
     unsigned char *base = (unsigned char *)ws;
     float *vec[6];
     for (int k = 0; k < 6; ++k) vec[k] = (float *)(base + L.vec + k * L.vec_bytes);
-    float *gnx = vec[0], *gny = vec[1], *gwx = vec[2], *gwy = vec[3], *gx = vec[4], *gy = vec[5];
+    float *gnx = vec[0], *gny = vec[1], *gx = vec[4], *gy = vec[5];   // vec[2], vec[3]: unused since the fused cell pass
     double *norms = (double *)(base + L.norms);
     float *bins = (float *)(base + L.bins);
     double *stats = a->stats;
@@ -993,14 +994,27 @@ pp_status pp_place_iteration(const pp_place_iteration_args *a, void *ws, size_t 
         st = pp_binned_grad(&prob, (pp_precision)a->prec, a->M, nullptr, gnx, gny, nullptr, stats + 3,
                             base + L.dens, L.dens_bytes, stream);
     if (st != PP_OK) return st;
-    if ((st = wirelength_impl(nl, a->vx, a->vy, a->gamma, scal, gwx, gwy, stats + 1, base + L.wl, L.wl_bytes,
-                              stream)) != PP_OK)
+    // the wirelength's per-net pass, then one kernel for its per-cell gradient, the
+    // combination and the step norms (the same values as pp_wirelength,
+    // pp_place_combine and pp_step_norms; gw never leaves registers)
+    if ((st = wirelength_impl(nl, a->vx, a->vy, a->gamma, scal, nullptr, nullptr, stats + 1, base + L.wl,
+                              L.wl_bytes, stream)) != PP_OK)
         return st;
-    if ((st = combine_impl(n, gwx, gwy, gnx, gny, nl->cell_ptr, a->q, a->movable, a->lambda, scal, gx, gy,
-                           stream)) != PP_OK)
-        return st;
-    if ((st = pp_step_norms(n, a->vx, a->vy, a->vpx, a->vpy, gx, gy, a->gpx, a->gpy, norms, stream)) != PP_OK)
-        return st;
+    {
+        int dev, sm, ccm;
+        unsigned *status;
+        if ((st = device_info(&dev, &sm, &status, &ccm)) != PP_OK) return st;
+        if (n > 0) {
+            const void *ptrs[6] = {a->q, a->vpx, a->vpy, a->gpx, a->gpy, a->vx};
+            const char *names[6] = {"q", "vpx", "vpy", "gpx", "gpy", "vx"};
+            if ((st = check_arrays(dev, 6, ptrs, names)) != PP_OK) return st;
+            if (a->movable && (st = check_dev_ptr(a->movable, dev, "movable")) != PP_OK) return st;
+        }
+        cudaError_t e = launch_cell_step((int)n, nl->cell_ptr, nl->cell_net, a->vx, a->vy, a->gamma, a->lambda, scal,
+                                         (const float *)(base + L.wl), gnx, gny, a->q, a->movable, a->vpx, a->vpy,
+                                         a->gpx, a->gpy, gx, gy, norms, sm, (cudaStream_t)stream);
+        if (e != cudaSuccess) return cuda_fail(e, "cell step launch");
+    }
     if ((st = nesterov_impl(n, a->W, a->H, a->ux, a->uy, a->vx, a->vy, a->vpx, a->vpy, gx, gy, a->gpx, a->gpy,
                             a->w, a->h, a->movable, norms, a->alpha0, a->coef, scal, stream)) != PP_OK)
         return st;

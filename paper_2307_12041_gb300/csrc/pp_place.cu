@@ -14,6 +14,8 @@
 //   nesterov_kernel     u' = clamp(v - alpha g), v' = clamp(u' + coef (u' - u)),
 //                       alpha = |v - v_prev| / |g - g_prev| read on the device
 //   overflow_kernel     sum_b max(P_b - rho_t, 0) of a bin density P
+//   cell_step_kernel    the one-call iteration's cell pass: the three kernels above
+//                       (per-cell wirelength gradient, combination, step norms) fused
 //   place_loop_*_kernel the loop's scalar update between iterations (one thread, FP64)
 //                       when the loop runs on the device (pp_place_run)
 //
@@ -211,6 +213,68 @@ __global__ void combine_kernel(int64_t n, const float *__restrict__ gwx, const f
     }
 }
 
+// The one-call iteration's cell pass: the per-cell wirelength gradient (as
+// lse_cell_kernel), the preconditioned combination with the density gradient (as
+// combine_kernel) and the step norms (as step_norms_kernel) in one kernel, so that the
+// wirelength gradient never leaves registers.  g equals what the separate kernels
+// write; the norms differ from theirs only in the order of their compensated sums.
+__global__ void cell_step_kernel(int n_cells, const int32_t *__restrict__ cell_ptr,
+                                 const int32_t *__restrict__ cell_net, const float *__restrict__ x,
+                                 const float *__restrict__ y, float inv_gamma, float lambda,
+                                 const float *__restrict__ scal, const float4 *__restrict__ stats,
+                                 const float *__restrict__ gnx, const float *__restrict__ gny,
+                                 const float *__restrict__ q, const uint8_t *__restrict__ movable,
+                                 const float *__restrict__ vpx, const float *__restrict__ vpy,
+                                 const float *__restrict__ gpx, const float *__restrict__ gpy,
+                                 float *__restrict__ gx, float *__restrict__ gy, double *__restrict__ norms) {
+    if (scal) {
+        lambda = scal[0];
+        inv_gamma = 1.f / scal[1];
+    }
+    const float k2 = inv_gamma * 1.44269504088896341f;   // e^{d / gamma} = 2^{d k2}
+    constexpr int KC = 4;
+    Sum2 dv, dg;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_cells; i += gridDim.x * blockDim.x) {
+        const float xi = x[i], yi = y[i];
+        const int k0 = cell_ptr[i], k1 = cell_ptr[i + 1];
+        float ax = 0.f, ay = 0.f;
+        float4 sxs[KC], sys[KC];
+        for (int b = k0; b < k1; b += KC) {                 // the cell's nets KC at a time, in order
+#pragma unroll
+            for (int c = 0; c < KC; ++c) {
+                if (b + c < k1) {
+                    const int e = cell_net[b + c];
+                    sxs[c] = stats[2 * e];
+                    sys[c] = stats[2 * e + 1];
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < KC; ++c) {
+                if (b + c < k1) {
+                    const float4 sx = sxs[c], sy = sys[c];
+                    ax += exp2f((xi - sx.x) * k2) * sx.z - exp2f((sx.y - xi) * k2) * sx.w;
+                    ay += exp2f((yi - sy.x) * k2) * sy.z - exp2f((sy.y - yi) * k2) * sy.w;
+                }
+            }
+        }
+        float g0 = 0.f, g1 = 0.f;
+        if (!movable || movable[i]) {
+            const float inv = 1.f / fmaxf(1.f, (float)(k1 - k0) + lambda * q[i]);
+            g0 = (ax + lambda * gnx[i]) * inv;
+            g1 = (ay + lambda * gny[i]) * inv;
+        }
+        gx[i] = g0;
+        gy[i] = g1;
+        const float a = xi - vpx[i], c = yi - vpy[i], d = g0 - gpx[i], e = g1 - gpy[i];
+        add_prod(dv, a, a);
+        add_prod(dv, c, c);
+        add_prod(dg, d, d);
+        add_prod(dg, e, e);
+    }
+    block_add2(dv, norms);
+    block_add2(dg, norms + 1);
+}
+
 __global__ void step_norms_kernel(int64_t n, const float *__restrict__ vx, const float *__restrict__ vy,
                                   const float *__restrict__ vpx, const float *__restrict__ vpy,
                                   const float *__restrict__ gx, const float *__restrict__ gy,
@@ -404,10 +468,23 @@ cudaError_t launch_wirelength(int n_nets, int n_cells, const int32_t *net_ptr, c
         lse_net_kernel<<<grid_for(n_nets, 16 * sm_count), 256, 0, st>>>(
             n_nets, net_ptr, net_pin, x, y, gamma, 1.f / gamma, scal, reinterpret_cast<float4 *>(stats), out);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    if (n_cells > 0)
+    if (n_cells > 0 && gx)
         lse_cell_kernel<<<grid_for(n_cells, 16 * sm_count), 256, 0, st>>>(
             n_cells, cell_ptr, cell_net, x, y, 1.f / gamma, scal, reinterpret_cast<const float4 *>(stats), gx,
             gy);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cell_step(int n_cells, const int32_t *cell_ptr, const int32_t *cell_net, const float *x,
+                             const float *y, float gamma, float lambda, const float *scal, const float *stats,
+                             const float *gnx, const float *gny, const float *q, const uint8_t *movable,
+                             const float *vpx, const float *vpy, const float *gpx, const float *gpy, float *gx,
+                             float *gy, double *norms, int sm_count, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(norms, 0, 2 * sizeof(double), st);
+    if (e != cudaSuccess || n_cells <= 0) return e;
+    cell_step_kernel<<<grid_for(n_cells, 16 * sm_count), 256, 0, st>>>(
+        n_cells, cell_ptr, cell_net, x, y, 1.f / gamma, lambda, scal, reinterpret_cast<const float4 *>(stats),
+        gnx, gny, q, movable, vpx, vpy, gpx, gpy, gx, gy, norms);
     return cudaGetLastError();
 }
 

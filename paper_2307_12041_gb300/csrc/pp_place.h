@@ -17,6 +17,14 @@ cudaError_t launch_wirelength(int n_nets, int n_cells, const int32_t *net_ptr, c
                               const int32_t *cell_ptr, const int32_t *cell_net, const float *x,
                               const float *y, float gamma, const float *scal, float *stats, float *gx,
                               float *gy, double *out, int sm_count, cudaStream_t st);
+// (launch_wirelength with gx == NULL runs the per-net pass only.)  The one-call
+// iteration's cell pass: g = combination of the per-cell wirelength gradient with gn,
+// written to gx, gy, and norms = {|v - vp|^2, |g - gp|^2} (zeroed here)
+cudaError_t launch_cell_step(int n_cells, const int32_t *cell_ptr, const int32_t *cell_net, const float *x,
+                             const float *y, float gamma, float lambda, const float *scal, const float *stats,
+                             const float *gnx, const float *gny, const float *q, const uint8_t *movable,
+                             const float *vpx, const float *vpy, const float *gpx, const float *gpy, float *gx,
+                             float *gy, double *norms, int sm_count, cudaStream_t st);
 cudaError_t launch_combine(int64_t n, const float *gwx, const float *gwy, const float *gnx, const float *gny,
                            const int32_t *cell_ptr, const float *q, const uint8_t *movable, float lambda,
                            const float *scal, float *gx, float *gy, cudaStream_t st);
