@@ -504,13 +504,15 @@ def run_ours(args):
     if ktimes is None:      # binned mode: the library's counters do not count these kernels
         ktimes = {"coeff": (0, 0.0), "energy": (0, 0.0)}
         m = args.bins or max(p.Mx, p.My)
-        # density and interpolation (n > 0), the row prefix sums of the difference array
-        # (n > 0, folded into the first row transform for m = 512, 1024), FFT tables (m a
-        # power of two), 7 row transforms (those followed by a step along the other axis
-        # write transposed; for m = 512, 1024 the independent ones share a launch: 4
-        # launches), scaling
-        per_step = ((2 + (0 if m in (512, 1024) else 1)) if p.n > 0 else 0) \
-            + (1 if m & (m - 1) == 0 else 0) + (4 if m in (512, 1024) else 7) + 1
+        # density and interpolation (n > 0); the row prefix sums of the difference array
+        # (FP32 atomics: n > 0 and m not 512 or 1024, else folded into the first row
+        # transform; exact fixed-point density (fp32): always, with its conversion); FFT
+        # tables (m a power of two); 7 row transforms (those followed by a step along the
+        # other axis write transposed; for m = 512, 1024 the independent ones share a
+        # launch: 4 launches); scaling
+        warp = m in (512, 1024)
+        prefix = 1 if prec == "fp32" else (1 if (p.n > 0 and not warp) else 0)
+        per_step = (2 if p.n > 0 else 0) + prefix + (1 if m & (m - 1) == 0 else 0) + (4 if warp else 7) + 1
         launches = per_step * args.steps
     else:
         launches = int(sum(v[0] for v in counts.values()))     # our kernels in the timed steps

@@ -227,10 +227,13 @@ pp_status pp_phase_eval(const float *x, double L, const int32_t *m, int64_t coun
  *           block centre (clamped to the outermost centres).
  * The paper leaves its local-smoothness weighting of the density and its weighting
  * of the surrounding bins unstated; these are the readings taken.  The transforms
- * are dense GEMMs with the m-point cosine / sine matrices (cuBLAS): prec PP_FP32
- * (FP32) or PP_TF32 (TF32 tensor cores); PP_BF16X3 gives PP_ENOTSUP.  The density
- * is accumulated with FP32 atomics (summation order, and so the last bits, may vary
- * between runs).  a_out (Mx x My, optional), gx, gy (required when n > 0), e_block,
+ * run along one grid axis at a time as FP32 FFTs (m a power of two; direct sums
+ * otherwise) in both precisions; prec selects how the density is summed:
+ * PP_FP32 exactly, in 64-bit fixed point (each addition rounded to 2^-32 bin
+ * areas; the results are the same from run to run; |P| < 2^31 bin areas),
+ * PP_TF32 with FP32 atomics (faster; the rounding of the sums, and so the last
+ * bits of the results, follows the order the atomics land in).  PP_BF16X3 gives
+ * PP_ENOTSUP.  a_out (Mx x My, optional), gx, gy (required when n > 0), e_block,
  * e_total (optional): device arrays.  2 <= m <= 4096.  Workspace: at least
  * pp_binned_workspace_size() bytes, 256-byte aligned; 0 for invalid arguments. */
 size_t pp_binned_workspace_size(const pp_problem *prob, int32_t m);

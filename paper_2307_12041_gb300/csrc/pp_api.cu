@@ -911,8 +911,8 @@ pp_status pp_overflow(const pp_problem *prob, int32_t m, float target, float *bi
 }
 
 namespace {
-// Scratch of one placement iteration: the density and wirelength workspaces, six
-// float arrays of n (gn, gw, g per axis), the two norms and the M x M bins.
+// Scratch of one placement iteration: the density and wirelength workspaces, four
+// float arrays of n (gn and g per axis), the two norms and the M x M bins.
 struct PlaceLayout {
     size_t dens, dens_bytes, wl, wl_bytes, vec, vec_bytes, norms, bins, total;
 };
@@ -937,7 +937,7 @@ pp_status place_layout(const pp_place_iteration_args *a, PlaceLayout *L) {
     L->dens = 0;
     L->wl = round256(L->dens_bytes);
     L->vec = L->wl + round256(L->wl_bytes);
-    L->norms = L->vec + 6 * L->vec_bytes;
+    L->norms = L->vec + 4 * L->vec_bytes;
     L->bins = L->norms + 256;
     L->total = L->bins + round256((size_t)a->M * (size_t)a->M * sizeof(float));
     return PP_OK;
@@ -979,9 +979,9 @@ pp_status pp_place_iteration(const pp_place_iteration_args *a, void *ws, size_t 
     const pp_netlist *nl = a->netlist;
     const int64_t n = nl->n_cells;
     unsigned char *base = (unsigned char *)ws;
-    float *vec[6];
-    for (int k = 0; k < 6; ++k) vec[k] = (float *)(base + L.vec + k * L.vec_bytes);
-    float *gnx = vec[0], *gny = vec[1], *gx = vec[4], *gy = vec[5];   // vec[2], vec[3]: unused since the fused cell pass
+    float *vec[4];
+    for (int k = 0; k < 4; ++k) vec[k] = (float *)(base + L.vec + k * L.vec_bytes);
+    float *gnx = vec[0], *gny = vec[1], *gx = vec[2], *gy = vec[3];
     double *norms = (double *)(base + L.norms);
     float *bins = (float *)(base + L.bins);
     double *stats = a->stats;

@@ -1,7 +1,11 @@
 // The paper's binned fast scheme (Sec. III-D) on the GPU:
 //   bin_density_kernel    P_lj = sum_i c_i area(block i ∩ bin lj) / area(bin) (the
-//                         interiors of large blocks through a row difference array,
-//                         summed by row_prefix_add_kernel)
+//                         interiors of large blocks through a row difference array),
+//                         by FP32 atomics, or exactly in 64-bit fixed point
+//   row_prefix_add_kernel the difference array's row prefix sums added to P (FP32 path;
+//                         the first row transform does it for m = 512, 1024)
+//   density_finish_kernel P = the fixed-point accumulators plus the difference array's
+//                         row prefix sums, as float (exact path)
 //   transform kernels     the cosine / sine transforms of Eq. (disa), (dis-psi1) and
 //                         (dis-ksi) along one grid axis at a time, one CTA per row:
 //                           a'   = Cx P Cy^T            (DCT-II along j, then along l)
@@ -62,14 +66,30 @@ __device__ __forceinline__ long long fixed_bins(float x, double k) {
 // block spans at least 3 bin columns: the bins strictly inside its column range are
 // covered fully along y, so row l of the block adds the same c fx(l) to each of them.
 // It adds +c fx(l) at D[l][j0 + 1] and -c fx(l) at D[l][j1] instead, its two edge
-// columns directly, and row_prefix_add_kernel adds the prefix sums of D's rows to P:
-// four additions per row of the block instead of one per bin.
+// columns directly, and the prefix sums of D's rows are added to P afterwards
+// (row_prefix_add_kernel, the first row transform, or density_finish_kernel): four
+// additions per row of the block instead of one per bin.
 constexpr int kSmallBins = 8;
 
+// FIXED: each addition is rounded once to 2^-32 bin areas and summed in 64-bit integers
+// (P and D int64), so that the sums are exact and do not depend on the order in which
+// the atomics land (FP32 atomics round each partial sum, by an amount that follows that
+// order); |P| < 2^31 bin areas.  Else FP32 atomics into float P and D.
+constexpr float kFix = 0x1p32f, kUnfix = 0x1p-32f;
+
+template <bool FIXED>
+__device__ __forceinline__ void add_bin(void *base, size_t idx, float v) {
+    if (FIXED)
+        atomicAdd(reinterpret_cast<unsigned long long *>(base) + idx, (unsigned long long)__float2ll_rn(v * kFix));
+    else
+        atomicAdd(reinterpret_cast<float *>(base) + idx, v);
+}
+
+template <bool FIXED>
 __global__ void bin_density_kernel(const float *__restrict__ x, const float *__restrict__ y,
                                    const float *__restrict__ w, const float *__restrict__ h,
                                    const float *__restrict__ c, int n, int m, double inv_wb,
-                                   double inv_hb, float *__restrict__ P, float *__restrict__ D) {
+                                   double inv_hb, void *__restrict__ P, void *__restrict__ D) {
     constexpr int F = 40;                                 // fraction bits of a bin coordinate
     constexpr long long ONE = 1ll << F;
     const float unit = 0x1p-40f;
@@ -115,7 +135,7 @@ __global__ void bin_density_kernel(const float *__restrict__ x, const float *__r
                 for (int j = j0; j <= j1; ++j) {
                     const float fy = j == j0 ? ay0 : (j == j1 ? ay1 : 1.f);
                     if (!(fy > 0.f)) continue;
-                    atomicAdd(&P[(size_t)l * m + j], cox * fy);   // area / bin area
+                    add_bin<FIXED>(P, (size_t)l * m + j, cox * fy);   // area / bin area
                 }
             }
         }
@@ -142,11 +162,11 @@ __global__ void bin_density_kernel(const float *__restrict__ x, const float *__r
                     const float fx = fx_of(l);
                     if (!(fx > 0.f)) continue;
                     const float cx = bc * fx;
-                    float *Pr = P + (size_t)l * m, *Dr = D + (size_t)l * m;
-                    if (fa > 0.f) atomicAdd(Pr + ja, cx * fa);
-                    if (fb > 0.f) atomicAdd(Pr + jb, cx * fb);
-                    atomicAdd(Dr + ja + 1, cx);
-                    atomicAdd(Dr + jb, -cx);
+                    const size_t row = (size_t)l * m;
+                    if (fa > 0.f) add_bin<FIXED>(P, row + ja, cx * fa);
+                    if (fb > 0.f) add_bin<FIXED>(P, row + jb, cx * fb);
+                    add_bin<FIXED>(D, row + ja + 1, cx);
+                    add_bin<FIXED>(D, row + jb, -cx);
                 }
                 continue;
             }
@@ -160,7 +180,7 @@ __global__ void bin_density_kernel(const float *__restrict__ x, const float *__r
                     for (int r = lr; r < bnl; r += per) {
                         const int l = bl0 + r;
                         const float fx = fx_of(l);
-                        if (fx > 0.f && fy > 0.f) atomicAdd(&P[(size_t)l * m + j], bc * fx * fy);
+                        if (fx > 0.f && fy > 0.f) add_bin<FIXED>(P, (size_t)l * m + j, bc * fx * fy);
                     }
                 }
             } else {
@@ -168,7 +188,7 @@ __global__ void bin_density_kernel(const float *__restrict__ x, const float *__r
                     const float fx = fx_of(l);
                     for (int j = bj0 + lane; j <= bj1; j += 32) {
                         const float fy = fy_of(j);
-                        if (fx > 0.f && fy > 0.f) atomicAdd(&P[(size_t)l * m + j], bc * fx * fy);
+                        if (fx > 0.f && fy > 0.f) add_bin<FIXED>(P, (size_t)l * m + j, bc * fx * fy);
                     }
                 }
             }
@@ -209,6 +229,47 @@ __global__ void __launch_bounds__(256) row_prefix_add_kernel(const float *__rest
         for (int q = 0; q < 4; ++q)
             if (j + q < m) pr[j + q] += before + v[q];
         float chunk = 0.f;
+        for (int k = 0; k < 8; ++k) chunk += wsum[k];
+        carry += chunk;
+        __syncthreads();                                  // wsum is rewritten by the next chunk
+    }
+}
+
+// P[l][j] = (Pq[l][j] + sum_{j' <= j} Dq[l][j']) 2^-32 as float (one CTA of 256 threads
+// per row l, the row in chunks of 1,024 in order, each an inclusive scan of 4 values per
+// thread, then the warp and block partial sums; in 64-bit integers, so exact).
+__global__ void __launch_bounds__(256) density_finish_kernel(const long long *__restrict__ Pq,
+                                                             const long long *__restrict__ Dq,
+                                                             float *__restrict__ P, int m) {
+    __shared__ long long wsum[8];
+    const long long *dr = Dq + (size_t)blockIdx.x * m;
+    const long long *qr = Pq + (size_t)blockIdx.x * m;
+    float *pr = P + (size_t)blockIdx.x * m;
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    long long carry = 0;
+    for (int base = 0; base < m; base += 1024) {
+        const int j = base + 4 * threadIdx.x;
+        long long v[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) v[q] = j + q < m ? dr[j + q] : 0ll;
+        v[1] += v[0];
+        v[2] += v[1];
+        v[3] += v[2];
+        long long t = v[3];                               // this thread's total; inclusive scan over the warp
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const long long o = __shfl_up_sync(0xffffffffu, t, off);
+            if (lane >= off) t += o;
+        }
+        if (lane == 31) wsum[wp] = t;
+        __syncthreads();
+        long long before = carry;                         // chunks before, warps before, lanes before
+        for (int k = 0; k < wp; ++k) before += wsum[k];
+        before += t - v[3];
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            if (j + q < m) pr[j + q] = __ll2float_rn(qr[j + q] + before + v[q]) * kUnfix;
+        long long chunk = 0;
         for (int k = 0; k < 8; ++k) chunk += wsum[k];
         carry += chunk;
         __syncthreads();                                  // wsum is rewritten by the next chunk
@@ -774,8 +835,8 @@ BinnedLayout binned_layout(int m, int Mx, int My) {
         return o;
     };
     const size_t mm = (size_t)m * m;
-    L.P = take(mm);
-    L.D = take(mm);
+    L.P = take(mm);                      // the density, float
+    L.D = take(4 * mm);                  // float D, or the int64 accumulators Pq, Dq (exact sums)
     L.R1t = take((size_t)My * m);
     L.R2 = take((size_t)My * Mx);
     L.a = take((size_t)Mx * My);
@@ -790,7 +851,7 @@ BinnedLayout binned_layout(int m, int Mx, int My) {
 cudaError_t launch_bin_density(const float *x, const float *y, const float *w, const float *h, const float *c,
                                int n, int m, double W, double H, float *P, int sm_count, cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
-    bin_density_kernel<<<8 * sm_count, 256, 0, st>>>(x, y, w, h, c, n, m, m / W, m / H, P, nullptr);
+    bin_density_kernel<false><<<8 * sm_count, 256, 0, st>>>(x, y, w, h, c, n, m, m / W, m / H, P, nullptr);
     return cudaGetLastError();
 }
 
@@ -865,7 +926,9 @@ cudaError_t rows(bool fwd, const RowJobs &J, int njobs, int in_ld, int nrows, in
 cudaError_t run_binned(const Launch &Lc, int dev, int m, bool tf32, unsigned char *ws, float *a_out, float *e_block,
                        float *gx, float *gy, double *e_total, const char **what) {
     (void)dev;
-    (void)tf32;                        // the transforms are FP32 FFTs (or direct sums) in either precision
+    // the transforms are FP32 FFTs (or direct sums) in either precision; PP_FP32 sums the
+    // density exactly in 64-bit fixed point (deterministic), PP_TF32 by FP32 atomics
+    const bool exact = !tf32;
     const int Mx = Lc.Mx, My = Lc.My, n = Lc.n;
     const BinnedLayout B = binned_layout(m, Mx, My);
     float *P = (float *)(ws + B.P), *R1t = (float *)(ws + B.R1t);
@@ -876,20 +939,35 @@ cudaError_t run_binned(const Launch &Lc, int dev, int m, bool tf32, unsigned cha
     float2 *tw = (float2 *)(ws + B.tab), *qw = tw + m / 2;
     cudaStream_t st = Lc.stream;
     *what = "binned scheme launch";
-    float *D = (float *)(ws + B.D);
-    // P and D are consecutive: one memset for both
-    cudaError_t e = cudaMemsetAsync(P, 0, B.D - B.P + (size_t)m * m * sizeof(float), st);
-    if (e != cudaSuccess) return e;
-    if (e_total && (e = cudaMemsetAsync(e_total, 0, sizeof(double), st)) != cudaSuccess) return e;
+    float *D = (float *)(ws + B.D);                             // float path
+    long long *Pq = (long long *)(ws + B.D), *Dq = Pq + (size_t)m * m;   // exact path
+    cudaError_t e;
     const int grid = 8 * Lc.sm_count;
-    if (n > 0) {
-        bin_density_kernel<<<grid, 256, 0, st>>>(Lc.x, Lc.y, Lc.w, Lc.h, Lc.c, n, m, m / Lc.W, m / Lc.H, P, D);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        if (!warp_fft(m)) {        // else added by the first row transform
-            row_prefix_add_kernel<<<m, 256, 0, st>>>(D, P, m);
+    if (exact) {
+        // int64 accumulators (bin areas x 2^32; Dq the large blocks' row differences),
+        // summed exactly, then P = float(Pq + row prefix sums of Dq) 2^-32
+        if ((e = cudaMemsetAsync(Pq, 0, 2 * (size_t)m * m * sizeof(long long), st)) != cudaSuccess) return e;
+        if (n > 0) {
+            bin_density_kernel<true><<<grid, 256, 0, st>>>(Lc.x, Lc.y, Lc.w, Lc.h, Lc.c, n, m, m / Lc.W,
+                                                           m / Lc.H, Pq, Dq);
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
         }
+        density_finish_kernel<<<m, 256, 0, st>>>(Pq, Dq, P, m);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    } else {
+        // P and D are consecutive: one memset for both
+        if ((e = cudaMemsetAsync(P, 0, B.D - B.P + (size_t)m * m * sizeof(float), st)) != cudaSuccess) return e;
+        if (n > 0) {
+            bin_density_kernel<false><<<grid, 256, 0, st>>>(Lc.x, Lc.y, Lc.w, Lc.h, Lc.c, n, m, m / Lc.W,
+                                                            m / Lc.H, P, D);
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+            if (!warp_fft(m)) {        // else added by the first row transform
+                row_prefix_add_kernel<<<m, 256, 0, st>>>(D, P, m);
+                if ((e = cudaGetLastError()) != cudaSuccess) return e;
+            }
+        }
     }
+    if (e_total && (e = cudaMemsetAsync(e_total, 0, sizeof(double), st)) != cudaSuccess) return e;
     const float kW = (float)(3.141592653589793 / Lc.W), lH = (float)(3.141592653589793 / Lc.H);
     if (pow2(m)) {
         fft_tables_kernel<<<(m + 255) / 256, 256, 0, st>>>(m, tw, qw);
@@ -903,7 +981,7 @@ cudaError_t run_binned(const Launch &Lc, int dev, int m, bool tf32, unsigned cha
     // R1t, so that no transpose is needed), then along l
     {
         const RowJobs j1{{P}, {R1t}, {0.f}, {0}};
-        PP_STEP(rows(true, j1, 1, m, m, m, m, My, 1, m, tw, qw, st, n > 0 ? D : nullptr));
+        PP_STEP(rows(true, j1, 1, m, m, m, m, My, 1, m, tw, qw, st, (n > 0 && !exact) ? D : nullptr));
         const RowJobs j2{{R1t}, {R2}, {0.f}, {0}};
         PP_STEP(rows(true, j2, 1, m, My, m, m, Mx, Mx, 1, tw, qw, st));
     }

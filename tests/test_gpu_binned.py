@@ -73,6 +73,22 @@ def test_binned_out_of_die_blocks_match_oracle(pp, m):
     assert abs(float(E.item()) - ref["E"]) <= tol * abs(ref["E"])
 
 
+@pytest.mark.parametrize("m", [512, 100])
+def test_binned_density_is_deterministic(pp, m):
+    """The bin density is summed in 64-bit fixed point, so the order in which the
+    atomics land does not matter: two runs give the same coefficients, per-block
+    energies and gradients bit for bit (E, a sum over CTAs in FP64, to rounding)."""
+    p = synth.out_of_die_blocks(3000, 64, 48, seed=40 + m, W=1.2, H=0.9)
+    x, y, w, h, c = pp.binding.to_device(p, torch.device("cuda"))
+    r1 = pp.binding.binned_grad(x, y, w, h, c, p.W, p.H, 64, 48, m, "fp32")
+    r2 = pp.binding.binned_grad(x, y, w, h, c, p.W, p.H, 64, 48, m, "fp32")
+    for name, a, b in zip(("gx", "gy", "N", "E", "a"), r1, r2):
+        if name == "E":
+            assert float(a.item()) == pytest.approx(float(b.item()), rel=1e-13)
+        else:
+            assert torch.equal(a, b), name
+
+
 def test_binned_rejects_bad_bins(pp):
     p = synth.uniform_blocks(10, 8, 8, seed=1)
     x, y, w, h, c = pp.binding.to_device(p, torch.device("cuda"))
