@@ -45,97 +45,129 @@ __global__ void lse_net_kernel(int n_nets, const int32_t *__restrict__ net_ptr,
     // e^{d / gamma} = 2^{d k2}: one multiply and the hardware base-2 exponential
     const float k2 = inv_gamma * 1.44269504088896341f;
     Sum2 wl, hp;
-    // the first KP pins of a net are gathered together (their loads in flight at once)
-    // and kept in registers for the second pass; longer nets gather the rest KT at a
-    // time, in both passes
-    constexpr int KP = 8, KT = 4;
-    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n_nets; e += gridDim.x * blockDim.x) {
-        const int p0 = net_ptr[e], p1 = net_ptr[e + 1], np = p1 - p0;
-        float hx = -INFINITY, lx = INFINITY, hy = -INFINITY, ly = INFINITY;
-        float px[KP], py[KP];
-#pragma unroll
-        for (int k = 0; k < KP; ++k) {
-            px[k] = py[k] = 0.f;
-            if (k < np) {
-                const int i = net_pin[p0 + k];
-                px[k] = x[i];
-                py[k] = y[i];
-            }
+    // A net of up to KP pins is taken by its own thread: its pins gathered together (their
+    // loads in flight at once) and kept in registers for the second pass.  Longer nets
+    // are taken by the whole warp afterwards, one at a time, a pin per lane, with warp
+    // reductions, so that no lane's long net holds its warp.  The warps run the loop in
+    // step (e = base + lane), every lane reaching the warp-wide steps.
+    constexpr int KP = 8;
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const int nwarps = (int)((gridDim.x * blockDim.x) >> 5);
+    auto finish = [&](int e, float hx, float lx, float hy, float ly, float spx, float snx, float spy, float sny) {
+        stats[2 * e] = make_float4(hx, lx, 1.f / spx, 1.f / snx);
+        stats[2 * e + 1] = make_float4(hy, ly, 1.f / spy, 1.f / sny);
+        add2(hp, hx - lx);
+        add2(hp, hy - ly);
+        add2(wl, hx - lx);
+        add2(wl, hy - ly);
+        add_prod(wl, gamma, logf(spx));
+        add_prod(wl, gamma, logf(snx));
+        add_prod(wl, gamma, logf(spy));
+        add_prod(wl, gamma, logf(sny));
+    };
+    for (int base = ((int)(blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; base < n_nets; base += nwarps * 32) {
+        const int e = base + lane;
+        int p0 = 0, p1 = 0;
+        if (e < n_nets) {
+            p0 = net_ptr[e];
+            p1 = net_ptr[e + 1];
         }
+        const int np = p1 - p0;
+        if (e < n_nets && np <= KP) {
+            float hx = -INFINITY, lx = INFINITY, hy = -INFINITY, ly = INFINITY;
+            float px[KP], py[KP];
 #pragma unroll
-        for (int k = 0; k < KP; ++k) {
-            if (k < np) {
-                hx = fmaxf(hx, px[k]);
-                lx = fminf(lx, px[k]);
-                hy = fmaxf(hy, py[k]);
-                ly = fminf(ly, py[k]);
-            }
-        }
-        for (int b = p0 + KP; b < p1; b += KT) {
-            float tx[KT], ty[KT];
-#pragma unroll
-            for (int k = 0; k < KT; ++k) {
-                if (b + k < p1) {
-                    const int i = net_pin[b + k];
-                    tx[k] = x[i];
-                    ty[k] = y[i];
+            for (int k = 0; k < KP; ++k) {
+                px[k] = py[k] = 0.f;
+                if (k < np) {
+                    const int i = net_pin[p0 + k];
+                    px[k] = x[i];
+                    py[k] = y[i];
                 }
             }
 #pragma unroll
-            for (int k = 0; k < KT; ++k) {
-                if (b + k < p1) {
-                    hx = fmaxf(hx, tx[k]);
-                    lx = fminf(lx, tx[k]);
-                    hy = fmaxf(hy, ty[k]);
-                    ly = fminf(ly, ty[k]);
+            for (int k = 0; k < KP; ++k) {
+                if (k < np) {
+                    hx = fmaxf(hx, px[k]);
+                    lx = fminf(lx, px[k]);
+                    hy = fmaxf(hy, py[k]);
+                    ly = fminf(ly, py[k]);
                 }
             }
-        }
-        float spx = 0.f, snx = 0.f, spy = 0.f, sny = 0.f;
+            float spx = 0.f, snx = 0.f, spy = 0.f, sny = 0.f;
 #pragma unroll
-        for (int k = 0; k < KP; ++k) {
-            if (k < np) {
-                spx += exp2f((px[k] - hx) * k2);
-                snx += exp2f((lx - px[k]) * k2);
-                spy += exp2f((py[k] - hy) * k2);
-                sny += exp2f((ly - py[k]) * k2);
-            }
-        }
-        for (int b = p0 + KP; b < p1; b += KT) {
-            float tx[KT], ty[KT];
-#pragma unroll
-            for (int k = 0; k < KT; ++k) {
-                if (b + k < p1) {
-                    const int i = net_pin[b + k];
-                    tx[k] = x[i];
-                    ty[k] = y[i];
+            for (int k = 0; k < KP; ++k) {
+                if (k < np) {
+                    spx += exp2f((px[k] - hx) * k2);
+                    snx += exp2f((lx - px[k]) * k2);
+                    spy += exp2f((py[k] - hy) * k2);
+                    sny += exp2f((ly - py[k]) * k2);
                 }
             }
-#pragma unroll
-            for (int k = 0; k < KT; ++k) {
-                if (b + k < p1) {
-                    spx += exp2f((tx[k] - hx) * k2);
-                    snx += exp2f((lx - tx[k]) * k2);
-                    spy += exp2f((ty[k] - hy) * k2);
-                    sny += exp2f((ly - ty[k]) * k2);
-                }
-            }
-        }
-        if (p1 - p0 >= 2) {
-            stats[2 * e] = make_float4(hx, lx, 1.f / spx, 1.f / snx);
-            stats[2 * e + 1] = make_float4(hy, ly, 1.f / spy, 1.f / sny);
-            add2(hp, hx - lx);
-            add2(hp, hy - ly);
-            add2(wl, hx - lx);
-            add2(wl, hy - ly);
-            add_prod(wl, gamma, logf(spx));
-            add_prod(wl, gamma, logf(snx));
-            add_prod(wl, gamma, logf(spy));
-            add_prod(wl, gamma, logf(sny));
-        } else {       // a net of fewer than two pins adds nothing: both exponentials
+            if (np >= 2) {
+                finish(e, hx, lx, hy, ly, spx, snx, spy, sny);
+            } else {   // a net of fewer than two pins adds nothing: both exponentials
                        // of its gradient terms are exp(-inf) = 0 (no inf * 0)
-            stats[2 * e] = make_float4(INFINITY, -INFINITY, 0.f, 0.f);
-            stats[2 * e + 1] = make_float4(INFINITY, -INFINITY, 0.f, 0.f);
+                stats[2 * e] = make_float4(INFINITY, -INFINITY, 0.f, 0.f);
+                stats[2 * e + 1] = make_float4(INFINITY, -INFINITY, 0.f, 0.f);
+            }
+        }
+        // the warp's long nets, one at a time over the whole warp
+        unsigned todo = __ballot_sync(full, e < n_nets && np > KP);
+        while (todo) {
+            const int src = __ffs(todo) - 1;
+            todo &= todo - 1;
+            const int q0 = __shfl_sync(full, p0, src), q1 = __shfl_sync(full, p1, src);
+            // pass 1: max and min; the first 32 pins stay in registers for pass 2
+            float hx = -INFINITY, lx = INFINITY, hy = -INFINITY, ly = INFINITY, fx = 0.f, fy = 0.f;
+            const bool first = q0 + lane < q1;
+            if (first) {
+                const int i = net_pin[q0 + lane];
+                fx = x[i];
+                fy = y[i];
+                hx = lx = fx;
+                hy = ly = fy;
+            }
+            for (int p = q0 + 32 + lane; p < q1; p += 32) {
+                const int i = net_pin[p];
+                const float xi = x[i], yi = y[i];
+                hx = fmaxf(hx, xi);
+                lx = fminf(lx, xi);
+                hy = fmaxf(hy, yi);
+                ly = fminf(ly, yi);
+            }
+#pragma unroll
+            for (int off = 16; off >= 1; off >>= 1) {
+                hx = fmaxf(hx, __shfl_xor_sync(full, hx, off));
+                lx = fminf(lx, __shfl_xor_sync(full, lx, off));
+                hy = fmaxf(hy, __shfl_xor_sync(full, hy, off));
+                ly = fminf(ly, __shfl_xor_sync(full, ly, off));
+            }
+            // pass 2: the shifted exponential sums
+            float spx = 0.f, snx = 0.f, spy = 0.f, sny = 0.f;
+            if (first) {
+                spx = exp2f((fx - hx) * k2);
+                snx = exp2f((lx - fx) * k2);
+                spy = exp2f((fy - hy) * k2);
+                sny = exp2f((ly - fy) * k2);
+            }
+            for (int p = q0 + 32 + lane; p < q1; p += 32) {
+                const int i = net_pin[p];
+                const float xi = x[i], yi = y[i];
+                spx += exp2f((xi - hx) * k2);
+                snx += exp2f((lx - xi) * k2);
+                spy += exp2f((yi - hy) * k2);
+                sny += exp2f((ly - yi) * k2);
+            }
+#pragma unroll
+            for (int off = 16; off >= 1; off >>= 1) {
+                spx += __shfl_xor_sync(full, spx, off);
+                snx += __shfl_xor_sync(full, snx, off);
+                spy += __shfl_xor_sync(full, spy, off);
+                sny += __shfl_xor_sync(full, sny, off);
+            }
+            if (lane == src) finish(base + src, hx, lx, hy, ly, spx, snx, spy, sny);
         }
     }
     block_add2(wl, out);

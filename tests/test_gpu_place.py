@@ -40,6 +40,29 @@ def test_wirelength_matches_oracle(pp, small_netlist, gamma):
     assert np.abs(g - r).max() <= 2e-5 * np.abs(r).max(), np.abs(g - r).max()
 
 
+@pytest.mark.parametrize("gamma", [0.02, 1e-3])
+def test_wirelength_with_long_nets_matches_oracle(pp, gamma):
+    """Nets of 9 to 3,000 pins (taken by a whole warp, a pin per lane, beyond 32 pins in
+    several rounds) next to short ones, against the FP64 oracle."""
+    n = 6000
+    p = synth.placement_cells(n, 64, 21, start_sigma=0.2)
+    ptr, pins = synth.netlist(n, 22)
+    g = np.random.default_rng(23)
+    big = [g.choice(n, d, replace=False) for d in (9, 31, 32, 33, 64, 65, 300, 3000)]
+    pins = np.concatenate([pins] + big)
+    ptr = np.concatenate([ptr, ptr[-1] + np.cumsum([len(b) for b in big])])
+    nl = pp.binding.DeviceNetlist(p.n, ptr, pins)
+    x, y = torch.from_numpy(p.x).cuda(), torch.from_numpy(p.y).cuda()
+    gx, gy, out = pp.binding.wirelength(nl, x, y, gamma)
+    W, hp, rgx, rgy = OP.lse_wirelength(p.x, p.y, ptr, pins, gamma)
+    o = out.cpu().numpy()
+    assert abs(o[0] - W) <= 2e-6 * W, (o[0], W)
+    assert abs(o[1] - hp) <= 1e-6 * hp, (o[1], hp)
+    gg = np.concatenate([gx.double().cpu().numpy(), gy.double().cpu().numpy()])
+    r = np.concatenate([rgx, rgy])
+    assert np.abs(gg - r).max() <= 2e-5 * np.abs(r).max(), np.abs(gg - r).max()
+
+
 def test_wirelength_edge_cases(pp):
     # one-pin and empty nets add nothing; a two-pin net gives +-tanh(d / 2 gamma)
     ptr = np.array([0, 1, 1, 3])
