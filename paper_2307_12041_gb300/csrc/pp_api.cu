@@ -476,7 +476,7 @@ pp_status pp_grad_host(const pp_problem *prob, pp_precision prec, pp_sample samp
         return fail(PP_ENOMEM_WS, "workspace of %zu bytes needed, %zu given%s", need, ws ? ws_bytes : (size_t)0,
                     ws ? "" : " (NULL)");
     if (((uintptr_t)ws & 255) != 0) return fail(PP_EINVAL, "workspace must be 256-byte aligned");
-    int dev, sm, ccm;
+    int dev = 0, sm = 0, ccm = 0;
     unsigned *status;
     if ((st = device_info(&dev, &sm, &status, &ccm)) != PP_OK) return st;
     if ((st = check_dev_ptr(ws, dev, "ws")) != PP_OK) return st;
@@ -593,7 +593,7 @@ pp_status pp_coeffs_accumulate(const pp_problem *prob, pp_precision prec, double
 }
 
 pp_status pp_sync_status(void *stream) {
-    int dev, sm, ccm;
+    int dev = 0, sm = 0, ccm = 0;
     unsigned *status;
     pp_status st = device_info(&dev, &sm, &status, &ccm);
     if (st != PP_OK) return st;
@@ -613,7 +613,7 @@ pp_status pp_sync_status(void *stream) {
 
 pp_status pp_phase_eval(const float *x, double L, const int32_t *m, int64_t count, int evaluator,
                         float *out, void *stream) {
-    int dev, sm, ccm;
+    int dev = 0, sm = 0, ccm = 0;
     unsigned *status;
     pp_status st = device_info(&dev, &sm, &status, &ccm);
     if (st != PP_OK) return st;
@@ -648,7 +648,7 @@ pp_status pp_binned_grad(const pp_problem *prob, pp_precision prec, int32_t m, f
                     (int)prec);
     const size_t need = pp_binned_workspace_size(prob, m);
     if (need == 0) return PP_EINVAL;
-    int dev, sm, ccm;
+    int dev = 0, sm = 0, ccm = 0;
     unsigned *status;
     if ((st = device_info(&dev, &sm, &status, &ccm)) != PP_OK) return st;
     if (!ws || ws_bytes < need)
@@ -693,7 +693,7 @@ pp_status pp_binned_grad(const pp_problem *prob, pp_precision prec, int32_t m, f
 
 pp_status pp_energy_from_coeffs(const float *a, int32_t Mx, int32_t My, double W, double H, double *e_total,
                                 void *stream) {
-    int dev, sm, ccm;
+    int dev = 0, sm = 0, ccm = 0;
     unsigned *status;
     pp_status st = device_info(&dev, &sm, &status, &ccm);
     if (st != PP_OK) return st;
@@ -712,7 +712,7 @@ pp_status pp_energy_from_coeffs(const float *a, int32_t Mx, int32_t My, double W
 pp_status pp_descent_step(double W, double H, int64_t n, float *x, float *y, const float *w,
                           const float *h, const float *gx, const float *gy, const uint8_t *movable,
                           float lr, float sigma, uint64_t seed, uint64_t step, void *stream) {
-    int dev, sm, ccm;
+    int dev = 0, sm = 0, ccm = 0;
     unsigned *status;
     pp_status st = device_info(&dev, &sm, &status, &ccm);
     if (st != PP_OK) return st;
@@ -766,7 +766,7 @@ namespace {
 // scalar is checked only when scal is NULL.
 pp_status wirelength_impl(const pp_netlist *nl, const float *x, const float *y, float gamma, const float *scal,
                           float *gx, float *gy, double *out, void *ws, size_t ws_bytes, void *stream) {
-    int dev, sm, ccm;
+    int dev = 0, sm = 0, ccm = 0;
     unsigned *status;
     pp_status st = device_info(&dev, &sm, &status, &ccm);
     if (st != PP_OK) return st;
@@ -794,7 +794,7 @@ pp_status wirelength_impl(const pp_netlist *nl, const float *x, const float *y, 
 pp_status combine_impl(int64_t n, const float *gwx, const float *gwy, const float *gnx, const float *gny,
                        const int32_t *cell_ptr, const float *q, const uint8_t *movable, float lambda,
                        const float *scal, float *gx, float *gy, void *stream) {
-    int dev, sm, ccm;
+    int dev = 0, sm = 0, ccm = 0;
     unsigned *status;
     pp_status st = device_info(&dev, &sm, &status, &ccm);
     if (st != PP_OK) return st;
@@ -817,7 +817,7 @@ pp_status nesterov_impl(int64_t n, double W, double H, float *ux, float *uy, flo
                         float *vpy, const float *gx, const float *gy, float *gpx, float *gpy, const float *w,
                         const float *h, const uint8_t *movable, const double *norms, float alpha0, float coef,
                         const float *scal, void *stream) {
-    int dev, sm, ccm;
+    int dev = 0, sm = 0, ccm = 0;
     unsigned *status;
     pp_status st = device_info(&dev, &sm, &status, &ccm);
     if (st != PP_OK) return st;
@@ -842,7 +842,7 @@ pp_status nesterov_impl(int64_t n, double W, double H, float *ux, float *uy, flo
 pp_status pp_step_norms(int64_t n, const float *vx, const float *vy, const float *vpx, const float *vpy,
                         const float *gx, const float *gy, const float *gpx, const float *gpy, double *norms,
                         void *stream) {
-    int dev, sm, ccm;
+    int dev = 0, sm = 0, ccm = 0;
     unsigned *status;
     pp_status st = device_info(&dev, &sm, &status, &ccm);
     if (st != PP_OK) return st;
@@ -880,7 +880,7 @@ pp_status pp_nesterov_step(int64_t n, double W, double H, float *ux, float *uy, 
 }
 
 pp_status pp_overflow(const pp_problem *prob, int32_t m, float target, float *bins, double *out, void *stream) {
-    int dev, sm, ccm;
+    int dev = 0, sm = 0, ccm = 0;
     unsigned *status;
     pp_status st = device_info(&dev, &sm, &status, &ccm);
     if (st != PP_OK) return st;
@@ -945,12 +945,12 @@ pp_status place_layout(const pp_place_iteration_args *a, PlaceLayout *L) {
 }  // namespace
 
 size_t pp_place_workspace_size(const pp_place_iteration_args *a) {
-    PlaceLayout L;
+    PlaceLayout L{};
     return place_layout(a, &L) == PP_OK ? L.total : 0;
 }
 
 pp_status pp_place_iteration(const pp_place_iteration_args *a, void *ws, size_t ws_bytes, void *stream) {
-    PlaceLayout L;
+    PlaceLayout L{};
     pp_status st = place_layout(a, &L);
     if (st != PP_OK) return st;
     if (!ws || ws_bytes < L.total)
@@ -963,7 +963,7 @@ pp_status pp_place_iteration(const pp_place_iteration_args *a, void *ws, size_t 
     const float *scal = a->scalars;
     if (scal) {
         if (((uintptr_t)scal & 15) != 0) return fail(PP_EINVAL, "scalars must be 16-byte aligned");
-        int dev, sm, ccm;
+        int dev = 0, sm = 0, ccm = 0;
         unsigned *status;
         if ((st = device_info(&dev, &sm, &status, &ccm)) != PP_OK) return st;
         if ((st = check_dev_ptr(scal, dev, "scalars")) != PP_OK) return st;
@@ -1001,7 +1001,7 @@ pp_status pp_place_iteration(const pp_place_iteration_args *a, void *ws, size_t 
                               L.wl_bytes, stream)) != PP_OK)
         return st;
     {
-        int dev, sm, ccm;
+        int dev = 0, sm = 0, ccm = 0;
         unsigned *status;
         if ((st = device_info(&dev, &sm, &status, &ccm)) != PP_OK) return st;
         if (n > 0) {
@@ -1044,7 +1044,7 @@ struct LoopGraph {
 
 pp_status pp_place_run(const pp_place_iteration_args *a, const pp_place_schedule *sc, pp_place_state *state,
                        pp_place_record *trace, void *ws, size_t ws_bytes, void *stream) {
-    PlaceLayout L;
+    PlaceLayout L{};
     pp_status st = place_layout(a, &L);
     if (st != PP_OK) return st;
     if (!sc) return fail(PP_EINVAL, "schedule is NULL");
@@ -1060,7 +1060,7 @@ pp_status pp_place_run(const pp_place_iteration_args *a, const pp_place_schedule
     if (!ws || ws_bytes < L.total)
         return fail(PP_ENOMEM_WS, "workspace of %zu bytes needed, %zu given", L.total, ws ? ws_bytes : (size_t)0);
     if (((uintptr_t)ws & 255) != 0) return fail(PP_EINVAL, "workspace must be 256-byte aligned");
-    int dev, sm, ccm;
+    int dev = 0, sm = 0, ccm = 0;
     unsigned *status;
     if ((st = device_info(&dev, &sm, &status, &ccm)) != PP_OK) return st;
     if ((st = check_dev_ptr(state, dev, "state")) != PP_OK) return st;
@@ -1119,7 +1119,7 @@ pp_status pp_place_run(const pp_place_iteration_args *a, const pp_place_schedule
 }
 
 pp_status pp_check_wait_timeout(uint64_t limit_ns, void *stream) {
-    int dev, sm, ccm;
+    int dev = 0, sm = 0, ccm = 0;
     unsigned *status;
     pp_status st = device_info(&dev, &sm, &status, &ccm);
     if (st != PP_OK) return st;
